@@ -1,0 +1,319 @@
+"""FP64 CPU oracle of the WaterLily time step.
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's
+cpu_baseline / reference legs are the only callers.  The product path (the CUDA
+library and its binding) never imports this package.
+
+The arithmetic lives in ``wl_oracle.cpp`` (plain double-precision loops); this
+module builds it with the host compiler and wraps it with ctypes.  Each wrapper
+names the routine of the paper it stands for (Section 2 and Table 2 of the
+WaterLily paper); the readings where the paper is silent are listed in the C++
+header comment.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "wl_oracle.cpp")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_D = ctypes.c_double
+_I = ctypes.c_int
+_P = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (OpenMP on).  Returns the library path."""
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        sig = {
+            "or_create": (_P, [_I, _IP, _D, _DP, ctypes.c_uint, _I, _DP, _D, _D, _D, _I, _D]),
+            "or_destroy": (None, [_P]),
+            "or_nlevels": (_I, [_P]),
+            "or_level_dims": (None, [_P, _I, _IP]),
+            "or_get_level_L": (None, [_P, _I, _DP]),
+            "or_get_mu0": (None, [_P, _DP]),
+            "or_get_mu1": (None, [_P, _DP]),
+            "or_set_u": (None, [_P, _DP]),
+            "or_get_u": (None, [_P, _DP]),
+            "or_npad": (ctypes.c_long, [_P]),
+            "or_get_u_padded": (None, [_P, _DP]),
+            "or_set_p": (None, [_P, _DP]),
+            "or_get_p": (None, [_P, _DP]),
+            "or_get_dt": (_D, [_P]),
+            "or_set_dt": (None, [_P, _D]),
+            "or_get_time": (_D, [_P]),
+            "or_last_iters": (_I, [_P]),
+            "or_last_resid": (_D, [_P]),
+            "or_set_ic": (None, [_P, _I, _D]),
+            "or_convdiff": (None, [_P, _DP, _DP]),
+            "or_bdim_stage": (None, [_P, _I, _D, _DP, _DP, _DP]),
+            "or_divergence": (None, [_P, _DP]),
+            "or_poisson_apply": (None, [_P, _I, _DP, _DP]),
+            "or_poisson_diag": (None, [_P, _I, _DP]),
+            "or_pcg": (_I, [_P, _I, _DP, _DP, _D, _I, _DP]),
+            "or_dense_solve": (_I, [_P, _I, _DP, _DP]),
+            "or_vcycle": (_D, [_P, _DP, _DP, _I, _I]),
+            "or_rb_sweep": (None, [_P, _I, _DP, _DP]),
+            "or_project": (None, [_P, _D, _D, _D, _I, _I]),
+            "or_step": (None, [_P, _I, _D, _I, _D, _I]),
+            "or_cfl": (_D, [_P]),
+            "or_forces": (None, [_P, _DP]),
+            "or_kinetic_energy": (_D, [_P]),
+            "or_K0": (_D, [_D]),
+            "or_K1": (_D, [_D]),
+            "or_face_value": (_D, [_D, _D, _D]),
+            "or_psi": (_D, [_D]),
+            "or_sdf": (_D, [_P, _DP, _DP]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def K0(s: float) -> float:
+    """Zeroth moment of the cosine kernel (BDIM, Section 2)."""
+    return _load().or_K0(float(s))
+
+
+def K1(s: float) -> float:
+    """First moment of the cosine kernel over [s, 1] (BDIM, Section 2)."""
+    return _load().or_K1(float(s))
+
+
+def face_value(u: float, c: float, d: float) -> float:
+    """Koren-limited kappa=1/3 face value from upwind u, centre c, downwind d."""
+    return _load().or_face_value(float(u), float(c), float(d))
+
+
+def psi(r: float) -> float:
+    """Koren limiter psi(r) = max(0, min(2r, (2+r)/3, 2))."""
+    return _load().or_psi(float(r))
+
+
+class Oracle:
+    """One simulation held by the oracle.
+
+    dims are given x first; fields are returned as numpy arrays shaped
+    (D, [nz,] ny, nx) for velocity and ([nz,] ny, nx) for scalars.
+    """
+
+    def __init__(self, dims, nu, U=None, periodic=0, body=None, eps=1.0, advect=True,
+                 dt_cap=10.0):
+        self.lib = _load()
+        self.D = len(dims)
+        self.dims = tuple(int(d) for d in dims)
+        U = list(U) if U is not None else [0.0] * self.D
+        U = (U + [0.0] * 3)[:3]
+        kind, center, r1, r2 = 0, [0.0, 0.0, 0.0], 0.0, 0.0
+        if body is not None:
+            kind = int(body.get("kind", 1))
+            center = (list(body["center"]) + [0.0] * 3)[:3]
+            r1 = float(body.get("radius", 0.0))
+            r2 = float(body.get("radius2", 0.0))
+        d3 = (ctypes.c_int * 3)(*(list(self.dims) + [1] * (3 - self.D)))
+        self.h = self.lib.or_create(self.D, d3, float(nu), (ctypes.c_double * 3)(*U),
+                                    int(periodic), kind, (ctypes.c_double * 3)(*center),
+                                    r1, r2, float(eps), int(bool(advect)), float(dt_cap))
+        if not self.h:
+            raise ValueError("oracle: bad arguments")
+        self.ncell = int(np.prod(self.dims))
+        self.shape = tuple(reversed(self.dims))
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            self.lib.or_destroy(h)
+            self.h = None
+
+    # ----- geometry / hierarchy
+    def nlevels(self) -> int:
+        return self.lib.or_nlevels(self.h)
+
+    def level_dims(self, l):
+        d = (ctypes.c_int * 3)()
+        self.lib.or_level_dims(self.h, l, d)
+        return tuple(d[i] for i in range(self.D))
+
+    def level_L(self, l):
+        dims = self.level_dims(l)
+        n = int(np.prod(dims))
+        out = np.zeros(self.D * n)
+        self.lib.or_get_level_L(self.h, l, _dp(out))
+        return out.reshape((self.D,) + tuple(reversed(dims)))
+
+    def mu0(self):
+        out = np.zeros(self.D * self.ncell)
+        self.lib.or_get_mu0(self.h, _dp(out))
+        return out.reshape((self.D,) + self.shape)
+
+    def mu1(self):
+        out = np.zeros(self.D * self.D * self.ncell)
+        self.lib.or_get_mu1(self.h, _dp(out))
+        return out.reshape((self.D, self.D) + self.shape)
+
+    def sdf(self, x):
+        xx = np.zeros(3)
+        xx[: len(x)] = x
+        n = np.zeros(3)
+        d = self.lib.or_sdf(self.h, _dp(xx), _dp(n))
+        return d, n[: self.D]
+
+    # ----- state
+    def set_u(self, u):
+        a = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        assert a.size == self.D * self.ncell
+        self.lib.or_set_u(self.h, _dp(a))
+
+    def get_u(self):
+        out = np.zeros(self.D * self.ncell)
+        self.lib.or_get_u(self.h, _dp(out))
+        return out.reshape((self.D,) + self.shape)
+
+    def get_u_padded(self):
+        npad = self.lib.or_npad(self.h)
+        out = np.zeros(self.D * npad)
+        self.lib.or_get_u_padded(self.h, _dp(out))
+        pshape = tuple(n + 4 for n in reversed(self.dims))
+        return out.reshape((self.D,) + pshape)
+
+    def set_p(self, p):
+        a = np.ascontiguousarray(p, dtype=np.float64).reshape(-1)
+        assert a.size == self.ncell
+        self.lib.or_set_p(self.h, _dp(a))
+
+    def get_p(self):
+        out = np.zeros(self.ncell)
+        self.lib.or_get_p(self.h, _dp(out))
+        return out.reshape(self.shape)
+
+    @property
+    def dt(self) -> float:
+        return self.lib.or_get_dt(self.h)
+
+    @dt.setter
+    def dt(self, v: float):
+        self.lib.or_set_dt(self.h, float(v))
+
+    @property
+    def time(self) -> float:
+        return self.lib.or_get_time(self.h)
+
+    def set_ic(self, kind=0, amp=1.0):
+        """kind 0: uniform U; kind 1: Taylor-Green vortex of amplitude amp."""
+        self.lib.or_set_ic(self.h, int(kind), float(amp))
+
+    # ----- routines of the step (Table 2)
+    def convdiff(self, u):
+        a = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        out = np.zeros(self.D * self.ncell)
+        self.lib.or_convdiff(self.h, _dp(a), _dp(out))
+        return out.reshape((self.D,) + self.shape)
+
+    def bdim_stage(self, stage, dt, u0, u1=None):
+        a = np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
+        b = None if u1 is None else np.ascontiguousarray(u1, dtype=np.float64).reshape(-1)
+        out = np.zeros(self.D * self.ncell)
+        self.lib.or_bdim_stage(self.h, int(stage), float(dt), _dp(a),
+                               _dp(b) if b is not None else None, _dp(out))
+        return out.reshape((self.D,) + self.shape)
+
+    def divergence(self):
+        out = np.zeros(self.ncell)
+        self.lib.or_divergence(self.h, _dp(out))
+        return out.reshape(self.shape)
+
+    def poisson_apply(self, x, level=0):
+        dims = self.level_dims(level)
+        a = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        out = np.zeros(int(np.prod(dims)))
+        self.lib.or_poisson_apply(self.h, level, _dp(a), _dp(out))
+        return out.reshape(tuple(reversed(dims)))
+
+    def poisson_diag(self, level=0):
+        dims = self.level_dims(level)
+        out = np.zeros(int(np.prod(dims)))
+        self.lib.or_poisson_diag(self.h, level, _dp(out))
+        return out.reshape(tuple(reversed(dims)))
+
+    def pcg(self, z, x0=None, tol=1e-10, maxit=100000, level=0):
+        dims = self.level_dims(level)
+        n = int(np.prod(dims))
+        x = np.zeros(n) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).reshape(-1).copy()
+        zz = np.ascontiguousarray(z, dtype=np.float64).reshape(-1)
+        res = ctypes.c_double(0.0)
+        it = self.lib.or_pcg(self.h, level, _dp(x), _dp(zz), float(tol), int(maxit), ctypes.byref(res))
+        return x.reshape(tuple(reversed(dims))), it, res.value
+
+    def dense_solve(self, z, level=0):
+        dims = self.level_dims(level)
+        n = int(np.prod(dims))
+        x = np.zeros(n)
+        zz = np.ascontiguousarray(z, dtype=np.float64).reshape(-1)
+        rc = self.lib.or_dense_solve(self.h, level, _dp(x), _dp(zz))
+        if rc != 0:
+            raise RuntimeError("dense solve failed")
+        return x.reshape(tuple(reversed(dims)))
+
+    def vcycle(self, x, z, pre=0, post=4):
+        xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1).copy()
+        zz = np.ascontiguousarray(z, dtype=np.float64).reshape(-1)
+        r = self.lib.or_vcycle(self.h, _dp(xx), _dp(zz), int(pre), int(post))
+        return xx.reshape(self.shape), r
+
+    def rb_sweep(self, x, z, level=0):
+        dims = self.level_dims(level)
+        xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1).copy()
+        zz = np.ascontiguousarray(z, dtype=np.float64).reshape(-1)
+        self.lib.or_rb_sweep(self.h, level, _dp(xx), _dp(zz))
+        return xx.reshape(tuple(reversed(dims)))
+
+    def project(self, w, dt, tol=1e-10, maxit=100000, solver=0):
+        """solver 0: Jacobi-PCG (reference); 1: multigrid V(0,4) cycles (maxit = cycles)."""
+        self.lib.or_project(self.h, float(w), float(dt), float(tol), int(maxit), int(solver))
+        return self.lib.or_last_iters(self.h), self.lib.or_last_resid(self.h)
+
+    def step(self, n=1, tol=1e-10, maxit=100000, dt_fixed=0.0, solver=0):
+        self.lib.or_step(self.h, int(n), float(tol), int(maxit), float(dt_fixed), int(solver))
+
+    def cfl(self) -> float:
+        return self.lib.or_cfl(self.h)
+
+    def forces(self):
+        F = np.zeros(3)
+        self.lib.or_forces(self.h, _dp(F))
+        return F[: self.D]
+
+    def kinetic_energy(self) -> float:
+        return self.lib.or_kinetic_energy(self.h)

@@ -1,0 +1,975 @@
+// FP64 CPU oracle of the WaterLily time step (convection-diffusion, BDIM blend,
+// pressure projection, CFL, pressure force).
+//
+// TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+// cpu_baseline / reference legs of bench.py may load this library.  The GPU
+// library shares no code, header or constant with it.
+//
+// Everything here is plain loops in double precision, written to be checked by
+// eye against the method, not to be fast.  Grid units throughout: cell width 1,
+// cell I (0-based, I_d in [0,n_d)) has its centre at I + 1/2, and u_c[I] is the
+// velocity component c on the lower c-face of cell I (the staggered indexing of
+// the pressure-gradient loop in Section 2: u[I,i] -= coeff[I,i]*(p[I]-p[I-del(i)])).
+//
+// Sources (the paper states the method only by name, Section 2):
+//   * incompressible Navier-Stokes on a uniform staggered Cartesian grid, a
+//     third-order finite-volume convection scheme with implicit LES (Section 2);
+//     reading: kappa=1/3 upwind-biased face value limited by Koren's (1993) TVD
+//     limiter; viscous flux by central difference;
+//   * explicit adaptive time stepping (Section 2); reading: Heun predictor-corrector
+//     with a projection after each stage, dt from the convective out-flux CFL rule;
+//   * Boundary Data Immersion Method (Section 2, Weymouth & Yue 2011): u = mu0*f +
+//     mu1 . grad f with the zeroth/first moments of the cosine kernel of half-width eps;
+//   * BDIM-modified Poisson matrix (Section 2, Lauber 2022): face coefficients = mu0;
+//   * geometric multigrid Poisson solver (Section 2, Weymouth 2022) - the oracle's
+//     reference projection uses Jacobi-preconditioned CG to a tight tolerance; the
+//     V-cycle below exists to check the GPU V-cycle one cycle at a time;
+//   * the step's routines convdiff!, BDIM!, BC!, project!, CFL! (Table 2).
+//
+// Parity pins for every function are in tests/test_oracle_*.py.
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace {
+
+typedef std::vector<double> vec;
+
+struct Level {
+  int n[3];
+  long ncell;
+  vec L[3];  // L[c][cell]: coefficient of the lower c-face of each cell
+};
+
+struct OSim {
+  int D;
+  int n[3];           // interior cells per direction (n[2] = 1 in 2-D)
+  int g[3];           // ghost width per direction (2, or 0 for the unused z of 2-D)
+  int np[3];          // padded extents
+  long ncell, npad;
+  unsigned periodic;  // bit d set: direction d is periodic
+  double nu;
+  double U[3];
+  int body_kind;      // 0 none, 1 circle/sphere, 2 torus
+  double center[3], radius, radius2, eps;
+  int advect;         // 1: full convection-diffusion; 0: diffusion only (Stokes checks)
+  double dt, dt_cap, t;
+  long nsteps;
+  vec u[3];           // padded velocity, BC applied
+  vec p;              // pressure, cells
+  vec mu0[3];         // cells (lower faces)
+  vec mu1[3][3];      // mu1[c][j][cell]: component j of mu1*n at the lower c-face
+  std::vector<Level> lev;  // lev[0].L = Poisson face coefficients of the fine grid
+  int last_iters;
+  double last_resid;
+};
+
+inline bool is_per(const OSim& s, int d) { return (s.periodic >> d) & 1u; }
+
+inline long cidx(const OSim& s, int i, int j, int k) {
+  return i + (long)s.n[0] * (j + (long)s.n[1] * k);
+}
+inline long pidx(const OSim& s, int i, int j, int k) {
+  return (i + s.g[0]) + (long)s.np[0] * ((j + s.g[1]) + (long)s.np[1] * (k + s.g[2]));
+}
+inline long pidx(const OSim& s, const int* I) { return pidx(s, I[0], I[1], I[2]); }
+
+// ---------------------------------------------------------------------------
+// Kernel moments of the cosine kernel K(s) = (1 + cos(pi s))/2 on [-1, 1]
+// (BDIM, Section 2): K0(s) = int_{-1}^{s} K, K1(s) = int_{s}^{1} t K(t) dt.
+// Outside the kernel's support the integrals are exactly 0 or 1.
+double K0(double s) {
+  if (s <= -1.0) return 0.0;
+  if (s >= 1.0) return 1.0;
+  return 0.5 + 0.5 * s + std::sin(M_PI * s) / (2.0 * M_PI);
+}
+double K1(double s) {
+  if (s <= -1.0 || s >= 1.0) return 0.0;
+  return 0.25 * (1.0 - s * s) - (s * std::sin(M_PI * s) + (1.0 + std::cos(M_PI * s)) / M_PI) / (2.0 * M_PI);
+}
+
+// Signed distance and outward unit normal of the body at point x (D coordinates).
+double sdf(const OSim& s, const double* x, double* nrm) {
+  for (int d = 0; d < 3; ++d) nrm[d] = 0.0;
+  if (s.body_kind == 1) {  // circle (2-D) / sphere (3-D)
+    double r2 = 0.0;
+    for (int d = 0; d < s.D; ++d) r2 += (x[d] - s.center[d]) * (x[d] - s.center[d]);
+    double r = std::sqrt(r2);
+    if (r > 0.0)
+      for (int d = 0; d < s.D; ++d) nrm[d] = (x[d] - s.center[d]) / r;
+    return r - s.radius;
+  }
+  if (s.body_kind == 2 && s.D == 3) {  // torus: ring radius `radius` in the y-z plane, tube radius `radius2`
+    double a = x[0] - s.center[0], b = x[1] - s.center[1], c = x[2] - s.center[2];
+    double rho = std::sqrt(b * b + c * c);
+    double q0 = a, q1 = rho - s.radius;
+    double dq = std::sqrt(q0 * q0 + q1 * q1);
+    if (dq > 0.0) {
+      double e1 = (rho > 0.0) ? b / rho : 0.0, e2 = (rho > 0.0) ? c / rho : 0.0;
+      nrm[0] = q0 / dq;
+      nrm[1] = q1 / dq * e1;
+      nrm[2] = q1 / dq * e2;
+    }
+    return dq - s.radius2;
+  }
+  return 1e30;  // no body: everything is fluid
+}
+
+// ---------------------------------------------------------------------------
+// BC! (Table 2).  Applied direction by direction, each over the full padded range
+// of the other directions.  Non-periodic direction d: the normal component u_d
+// takes the boundary value U_d on both boundary faces (index 0 and n_d) and on the
+// ghost faces outside them; the other components copy the nearest interior value
+// (zero gradient).  Periodic direction d: every component wraps.
+void apply_bc(const OSim& s, vec* f) {
+  for (int d = 0; d < s.D; ++d) {
+    const int lo[3] = {-s.g[0], -s.g[1], -s.g[2]};
+    const int hi[3] = {s.n[0] + s.g[0], s.n[1] + s.g[1], s.n[2] + s.g[2]};
+    for (int c = 0; c < s.D; ++c) {
+      vec& a = f[c];
+      int I[3];
+      for (I[2] = lo[2]; I[2] < hi[2]; ++I[2])
+        for (I[1] = lo[1]; I[1] < hi[1]; ++I[1])
+          for (I[0] = lo[0]; I[0] < hi[0]; ++I[0]) {
+            int q = I[d];
+            bool ghost = (q < 0 || q >= s.n[d]);
+            bool bface = (!is_per(s, d) && c == d && q == 0);
+            if (!ghost && !bface) continue;
+            int J[3] = {I[0], I[1], I[2]};
+            if (is_per(s, d)) {
+              J[d] = ((q % s.n[d]) + s.n[d]) % s.n[d];
+              a[pidx(s, I)] = a[pidx(s, J)];
+            } else if (c == d) {
+              a[pidx(s, I)] = s.U[c];
+            } else {
+              J[d] = std::max(0, std::min(s.n[d] - 1, q));
+              a[pidx(s, I)] = a[pidx(s, J)];
+            }
+          }
+    }
+  }
+}
+
+// A face (c, I) is updated by the momentum step unless it is a boundary face of a
+// non-periodic direction (I_c = 0 there; the face n_c is outside the stored range).
+inline bool updated(const OSim& s, int c, const int* I) {
+  return is_per(s, c) || I[c] >= 1;
+}
+
+// kappa = 1/3 upwind-biased face value with Koren's limiter: phi = c + psi(r)(d - c)/2,
+// r = (c - u)/(d - c), psi(r) = max(0, min(2r, (2 + r)/3, 2)); phi = c when d == c.
+double face_value(double uu, double cc, double dd) {
+  if (dd == cc) return cc;
+  double r = (cc - uu) / (dd - cc);
+  double psi = std::max(0.0, std::min(std::min(2.0 * r, (2.0 + r) / 3.0), 2.0));
+  return cc + 0.5 * psi * (dd - cc);
+}
+
+// Momentum flux of component c through the lower j-face of the u_c control volume
+// at face index I (I may be one past the interior in direction j).
+double flux(const OSim& s, const vec* u, int c, int j, const int* I) {
+  auto at = [&](int comp, int dj, int dc) {
+    int J[3] = {I[0], I[1], I[2]};
+    J[j] += dj;
+    J[c] += dc;
+    return u[comp][pidx(s, J)];
+  };
+  double diff = -s.nu * (at(c, 0, 0) - at(c, -1, 0));
+  if (!s.advect) return diff;
+  // advecting velocity at the face: mean of u_j at I and at I - e_c
+  double a = 0.5 * (at(j, 0, 0) + at(j, 0, -1));
+  double phi;
+  if (a > 0.0)
+    phi = face_value(at(c, -2, 0), at(c, -1, 0), at(c, 0, 0));
+  else
+    phi = face_value(at(c, 1, 0), at(c, 0, 0), at(c, -1, 0));
+  return a * phi + diff;
+}
+
+// convdiff! (Table 2): r_c[I] = sum_j F_cj[I] - F_cj[I + e_j] on updated faces, 0 elsewhere.
+void convdiff(const OSim& s, const vec* u, vec* r) {
+  for (int c = 0; c < s.D; ++c) {
+    r[c].assign(s.ncell, 0.0);
+#pragma omp parallel for collapse(2)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (!updated(s, c, I)) continue;
+          double sum = 0.0;
+          for (int d = 0; d < s.D; ++d) {
+            int Ip[3] = {i, j, k};
+            Ip[d] += 1;
+            sum += flux(s, u, c, d, I) - flux(s, u, c, d, Ip);
+          }
+          r[c][cidx(s, i, j, k)] = sum;
+        }
+  }
+}
+
+// BDIM! (Table 2, Weymouth & Yue 2011) for one Heun stage.
+//   stage 1: f = u0 + dt r(u0);  out = mu0 f + sum_j mu1_j (f[I+e_j] - f[I-e_j])/2
+//   stage 2: f = u0 + dt r(u1);  out = (u1 + mu0 f + mu1 . grad f) / 2
+// f's boundary and ghost faces are filled with the same BC as u.  The body velocity
+// is zero.  `uin` is u0 in stage 1 and u1 in stage 2; `out` is padded, BC applied.
+void bdim_stage(const OSim& s, int stage, double dt, const vec* u0, const vec* u1, vec* out) {
+  const vec* uin = (stage == 1) ? u0 : u1;
+  vec r[3];
+  convdiff(s, uin, r);
+  vec f[3];
+  for (int c = 0; c < s.D; ++c) {
+    f[c] = u0[c];
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (!updated(s, c, I)) continue;
+          f[c][pidx(s, I)] = u0[c][pidx(s, I)] + dt * r[c][cidx(s, i, j, k)];
+        }
+  }
+  apply_bc(s, f);
+  for (int c = 0; c < s.D; ++c) {
+    out[c] = uin[c];
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (!updated(s, c, I)) continue;
+          long ci = cidx(s, i, j, k);
+          double v = s.mu0[c][ci] * f[c][pidx(s, I)];
+          for (int d = 0; d < s.D; ++d) {
+            int Ip[3] = {i, j, k}, Im[3] = {i, j, k};
+            Ip[d] += 1;
+            Im[d] -= 1;
+            v += s.mu1[c][d][ci] * 0.5 * (f[c][pidx(s, Ip)] - f[c][pidx(s, Im)]);
+          }
+          out[c][pidx(s, I)] = (stage == 1) ? v : 0.5 * (u1[c][pidx(s, I)] + v);
+        }
+  }
+  apply_bc(s, out);
+}
+
+// ---------------------------------------------------------------------------
+// Poisson operator with BDIM face coefficients (Section 2, Lauber 2022):
+//   (A x)[I] = sum_c L_c[I+e_c] (x[I+e_c] - x[I]) + L_c[I] (x[I-e_c] - x[I]).
+// Face n_c of a periodic direction is face 0; of a non-periodic direction it has L = 0.
+struct Op {
+  int D;
+  int n[3];
+  unsigned periodic;
+  const vec* L;
+  long ncell;
+  long idx(int i, int j, int k) const { return i + (long)n[0] * (j + (long)n[1] * k); }
+  // neighbour of cell I in direction c (dir = +1/-1), -1 when outside a non-periodic side
+  long nb(const int* I, int c, int dir) const {
+    int J[3] = {I[0], I[1], I[2]};
+    J[c] += dir;
+    if (J[c] < 0 || J[c] >= n[c]) {
+      if (!((periodic >> c) & 1u)) return -1;
+      J[c] = (J[c] + n[c]) % n[c];
+    }
+    return idx(J[0], J[1], J[2]);
+  }
+  double Lupper(const int* I, int c) const {  // coefficient of the upper c-face of cell I
+    long q = nb(I, c, +1);
+    return q < 0 ? 0.0 : L[c][q];
+  }
+  double Llower(const int* I, int c) const { return L[c][idx(I[0], I[1], I[2])]; }
+  double diag(const int* I) const {
+    double s = 0.0;
+    for (int c = 0; c < D; ++c) s += Lupper(I, c) + Llower(I, c);
+    return s;
+  }
+  void apply(const vec& x, vec& y) const {
+    y.assign(ncell, 0.0);
+#pragma omp parallel for collapse(2)
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          int I[3] = {i, j, k};
+          long q = idx(i, j, k);
+          double s = 0.0;
+          for (int c = 0; c < D; ++c) {
+            long qp = nb(I, c, +1), qm = nb(I, c, -1);
+            if (qp >= 0) s += Lupper(I, c) * (x[qp] - x[q]);
+            if (qm >= 0) s += Llower(I, c) * (x[qm] - x[q]);
+          }
+          y[q] = s;
+        }
+  }
+  void diagonal(vec& dg) const {
+    dg.assign(ncell, 0.0);
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          int I[3] = {i, j, k};
+          dg[idx(i, j, k)] = diag(I);
+        }
+  }
+};
+
+Op make_op(const OSim& s, const Level& l) {
+  Op o;
+  o.D = s.D;
+  for (int d = 0; d < 3; ++d) o.n[d] = l.n[d];
+  o.periodic = s.periodic;
+  o.L = l.L;
+  o.ncell = l.ncell;
+  return o;
+}
+
+double norm_inf(const vec& a) {
+  double m = 0.0;
+  for (double v : a) m = std::max(m, std::fabs(v));
+  return m;
+}
+
+// Remove the mean over active cells (diagonal > 0); inactive cells are set to 0.
+void remove_mean_active(vec& a, const vec& dg) {
+  double sum = 0.0;
+  long cnt = 0;
+  for (size_t q = 0; q < a.size(); ++q)
+    if (dg[q] > 0.0) {
+      sum += a[q];
+      ++cnt;
+    }
+  double m = cnt ? sum / cnt : 0.0;
+  for (size_t q = 0; q < a.size(); ++q) a[q] = (dg[q] > 0.0) ? a[q] - m : 0.0;
+}
+
+// Jacobi-preconditioned conjugate gradients on -A x = -z over the active cells,
+// started from x, stopped when ||z - A x||_inf <= tol.  z is first projected onto
+// the range of A (its mean over active cells removed).  Returns iterations used.
+int pcg(const Op& A, vec& x, const vec& zin, double tol, int maxit, double* resid) {
+  vec dg;
+  A.diagonal(dg);
+  vec z = zin;
+  remove_mean_active(z, dg);
+  for (long q = 0; q < A.ncell; ++q)
+    if (dg[q] <= 0.0) x[q] = 0.0;
+  vec Ax, r(A.ncell), zz(A.ncell), pp(A.ncell), Ap;
+  A.apply(x, Ax);
+  for (long q = 0; q < A.ncell; ++q) r[q] = (dg[q] > 0.0) ? (z[q] - Ax[q]) : 0.0;  // r = z - Ax
+  double rn = norm_inf(r);
+  int it = 0;
+  if (rn <= tol) {
+    if (resid) *resid = rn;
+    return 0;
+  }
+  // work with B = -A (positive semi-definite), b = -z, residual rho = b - Bx = -(z - Ax) = -r
+  for (long q = 0; q < A.ncell; ++q) {
+    zz[q] = (dg[q] > 0.0) ? -r[q] / dg[q] : 0.0;
+    pp[q] = zz[q];
+  }
+  double rz = 0.0;
+  for (long q = 0; q < A.ncell; ++q) rz += -r[q] * zz[q];
+  for (it = 1; it <= maxit; ++it) {
+    A.apply(pp, Ap);  // A p ; B p = -A p
+    double pBp = 0.0;
+    for (long q = 0; q < A.ncell; ++q) pBp += pp[q] * (-Ap[q]);
+    if (pBp <= 0.0) break;
+    double alpha = rz / pBp;
+    for (long q = 0; q < A.ncell; ++q) {
+      x[q] += alpha * pp[q];
+      r[q] -= alpha * Ap[q];  // r = z - A x
+    }
+    rn = norm_inf(r);
+    if (rn <= tol) {
+      A.apply(x, Ax);  // confirm with the true residual
+      for (long q = 0; q < A.ncell; ++q) r[q] = (dg[q] > 0.0) ? (z[q] - Ax[q]) : 0.0;
+      rn = norm_inf(r);
+      if (rn <= tol) break;
+    }
+    double rz2 = 0.0;
+    for (long q = 0; q < A.ncell; ++q) {
+      zz[q] = (dg[q] > 0.0) ? -r[q] / dg[q] : 0.0;
+      rz2 += -r[q] * zz[q];
+    }
+    double beta = rz2 / rz;
+    rz = rz2;
+    for (long q = 0; q < A.ncell; ++q) pp[q] = zz[q] + beta * pp[q];
+  }
+  if (resid) *resid = rn;
+  return it;
+}
+
+// Dense solve of A x = z on the active cells with the constraint sum(x) = 0, by
+// Gaussian elimination with partial pivoting on the bordered matrix [A 1; 1^T 0].
+// z is first projected onto the range (mean removed).  For small grids only.
+int dense_solve(const Op& A, vec& x, const vec& zin) {
+  vec dg;
+  A.diagonal(dg);
+  vec z = zin;
+  remove_mean_active(z, dg);
+  std::vector<long> act;
+  std::vector<long> pos(A.ncell, -1);
+  for (long q = 0; q < A.ncell; ++q)
+    if (dg[q] > 0.0) {
+      pos[q] = (long)act.size();
+      act.push_back(q);
+    }
+  long m = (long)act.size();
+  long N = m + 1;
+  vec M((size_t)N * N, 0.0), b(N, 0.0);
+  vec e(A.ncell, 0.0), col;
+  for (long a = 0; a < m; ++a) {  // column a of A restricted to active cells
+    e[act[a]] = 1.0;
+    A.apply(e, col);
+    e[act[a]] = 0.0;
+    for (long r = 0; r < m; ++r) M[r * N + a] = col[act[r]];
+    M[a * N + m] = 1.0;
+    M[m * N + a] = 1.0;
+    b[a] = z[act[a]];
+  }
+  for (long k = 0; k < N; ++k) {  // elimination
+    long piv = k;
+    for (long r = k + 1; r < N; ++r)
+      if (std::fabs(M[r * N + k]) > std::fabs(M[piv * N + k])) piv = r;
+    if (M[piv * N + k] == 0.0) return -1;
+    if (piv != k) {
+      for (long c = 0; c < N; ++c) std::swap(M[k * N + c], M[piv * N + c]);
+      std::swap(b[k], b[piv]);
+    }
+    for (long r = k + 1; r < N; ++r) {
+      double f = M[r * N + k] / M[k * N + k];
+      if (f == 0.0) continue;
+      for (long c = k; c < N; ++c) M[r * N + c] -= f * M[k * N + c];
+      b[r] -= f * b[k];
+    }
+  }
+  vec y(N, 0.0);
+  for (long k = N - 1; k >= 0; --k) {
+    double sum = b[k];
+    for (long c = k + 1; c < N; ++c) sum -= M[k * N + c] * y[c];
+    y[k] = sum / M[k * N + k];
+  }
+  x.assign(A.ncell, 0.0);
+  for (long a = 0; a < m; ++a) x[act[a]] = y[a];
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid hierarchy (Section 2, Weymouth 2022).  Reading: halve while every
+// direction is even and larger than 4; coarse face coefficient = half the sum of
+// the 2^(D-1) fine faces it covers; restriction sums the 2^D children; prolongation
+// is piecewise constant; the coarse initial guess is zero; the coarsest level is
+// solved exactly (mean zero over active cells); smoothing is red-black Gauss-Seidel
+// (red: i+j+k even, updated first).
+void build_levels(OSim& s) {
+  while (true) {
+    Level& f = s.lev.back();
+    bool ok = true;
+    for (int d = 0; d < s.D; ++d)
+      if (f.n[d] % 2 != 0 || f.n[d] <= 4) ok = false;
+    if (!ok) break;
+    Level c;
+    for (int d = 0; d < 3; ++d) c.n[d] = (d < s.D) ? f.n[d] / 2 : 1;
+    c.ncell = (long)c.n[0] * c.n[1] * c.n[2];
+    for (int cc = 0; cc < s.D; ++cc) {
+      c.L[cc].assign(c.ncell, 0.0);
+      for (int k = 0; k < c.n[2]; ++k)
+        for (int j = 0; j < c.n[1]; ++j)
+          for (int i = 0; i < c.n[0]; ++i) {
+            int J[3] = {i, j, k};
+            double sum = 0.0;
+            // fine faces: index 2J_cc in direction cc, children 2J_d..2J_d+1 in the others
+            int a0 = (cc == 0) ? 1 : 2, a1 = (cc == 1 || s.D < 2) ? 1 : 2, a2 = (cc == 2 || s.D < 3) ? 1 : 2;
+            for (int dk = 0; dk < a2; ++dk)
+              for (int dj = 0; dj < a1; ++dj)
+                for (int di = 0; di < a0; ++di) {
+                  int I[3] = {2 * J[0] + di, (s.D > 1 ? 2 * J[1] : 0) + dj, (s.D > 2 ? 2 * J[2] : 0) + dk};
+                  sum += f.L[cc][I[0] + (long)f.n[0] * (I[1] + (long)f.n[1] * I[2])];
+                }
+            c.L[cc][i + (long)c.n[0] * (j + (long)c.n[1] * k)] = 0.5 * sum;
+          }
+    }
+    s.lev.push_back(c);
+  }
+}
+
+void rb_sweep(const Op& A, vec& x, const vec& z) {
+  for (int color = 0; color < 2; ++color)
+    for (int k = 0; k < A.n[2]; ++k)
+      for (int j = 0; j < A.n[1]; ++j)
+        for (int i = 0; i < A.n[0]; ++i) {
+          if (((i + j + k) & 1) != color) continue;
+          int I[3] = {i, j, k};
+          double dgn = A.diag(I);
+          if (dgn <= 0.0) continue;
+          double sum = 0.0;
+          for (int c = 0; c < A.D; ++c) {
+            long qp = A.nb(I, c, +1), qm = A.nb(I, c, -1);
+            if (qp >= 0) sum += A.Lupper(I, c) * x[qp];
+            if (qm >= 0) sum += A.Llower(I, c) * x[qm];
+          }
+          x[A.idx(i, j, k)] = (sum - z[A.idx(i, j, k)]) / dgn;
+        }
+}
+
+void vcycle(const OSim& s, int l, vec& x, const vec& z, int pre, int post) {
+  Op A = make_op(s, s.lev[l]);
+  if (l == (int)s.lev.size() - 1) {
+    vec dg;
+    A.diagonal(dg);
+    long nact = 0;
+    for (double v : dg) nact += (v > 0.0);
+    if (nact <= 2048) {
+      dense_solve(A, x, z);
+    } else {
+      x.assign(A.ncell, 0.0);
+      double zn = norm_inf(z);
+      pcg(A, x, z, 1e-14 * std::max(zn, 1e-300), 100000, nullptr);
+      remove_mean_active(x, dg);
+    }
+    return;
+  }
+  for (int it = 0; it < pre; ++it) rb_sweep(A, x, z);
+  vec Ax;
+  A.apply(x, Ax);
+  const Level& c = s.lev[l + 1];
+  vec zc(c.ncell, 0.0), xc(c.ncell, 0.0);
+  for (int k = 0; k < A.n[2]; ++k)
+    for (int j = 0; j < A.n[1]; ++j)
+      for (int i = 0; i < A.n[0]; ++i) {
+        long q = A.idx(i, j, k);
+        int ci = i / 2, cj = (s.D > 1) ? j / 2 : 0, ck = (s.D > 2) ? k / 2 : 0;
+        zc[ci + (long)c.n[0] * (cj + (long)c.n[1] * ck)] += z[q] - Ax[q];
+      }
+  vcycle(s, l + 1, xc, zc, pre, post);
+  // piecewise-constant prolongation of the correction onto the active cells
+  // (cells with a zero row have no equation and keep x = 0)
+  for (int k = 0; k < A.n[2]; ++k)
+    for (int j = 0; j < A.n[1]; ++j)
+      for (int i = 0; i < A.n[0]; ++i) {
+        int I[3] = {i, j, k};
+        if (A.diag(I) <= 0.0) continue;
+        int ci = i / 2, cj = (s.D > 1) ? j / 2 : 0, ck = (s.D > 2) ? k / 2 : 0;
+        x[A.idx(i, j, k)] += xc[ci + (long)c.n[0] * (cj + (long)c.n[1] * ck)];
+      }
+  for (int it = 0; it < post; ++it) rb_sweep(A, x, z);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry (measure, Section 2): mu0 = K0(d/eps), mu1 = eps K1(d/eps) n at every
+// face; Poisson coefficient L = mu0 except L = 0 on non-periodic boundary faces.
+void measure(OSim& s) {
+  for (int c = 0; c < s.D; ++c) {
+    s.mu0[c].assign(s.ncell, 1.0);
+    for (int d = 0; d < 3; ++d) s.mu1[c][d].assign(s.ncell, 0.0);
+  }
+  if (s.body_kind != 0) {
+    for (int c = 0; c < s.D; ++c)
+      for (int k = 0; k < s.n[2]; ++k)
+        for (int j = 0; j < s.n[1]; ++j)
+          for (int i = 0; i < s.n[0]; ++i) {
+            double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+            x[c] -= 0.5;  // lower c-face
+            double nrm[3];
+            double d = sdf(s, x, nrm);
+            long q = cidx(s, i, j, k);
+            s.mu0[c][q] = K0(d / s.eps);
+            for (int jj = 0; jj < s.D; ++jj) s.mu1[c][jj][q] = s.eps * K1(d / s.eps) * nrm[jj];
+          }
+  }
+  Level l0;
+  for (int d = 0; d < 3; ++d) l0.n[d] = s.n[d];
+  l0.ncell = s.ncell;
+  for (int c = 0; c < s.D; ++c) l0.L[c] = s.mu0[c];
+  // zero the non-periodic boundary faces
+  for (int c = 0; c < s.D; ++c) {
+    if (is_per(s, c)) continue;
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (I[c] == 0) l0.L[c][cidx(s, i, j, k)] = 0.0;
+        }
+  }
+  s.lev.clear();
+  s.lev.push_back(l0);
+  build_levels(s);
+}
+
+// Divergence z[I] = sum_c u_c[I+e_c] - u_c[I] (u padded with BC applied).
+void divergence(const OSim& s, const vec* u, vec& z) {
+  z.assign(s.ncell, 0.0);
+  for (int k = 0; k < s.n[2]; ++k)
+    for (int j = 0; j < s.n[1]; ++j)
+      for (int i = 0; i < s.n[0]; ++i) {
+        double sum = 0.0;
+        for (int c = 0; c < s.D; ++c) {
+          int I[3] = {i, j, k}, Ip[3] = {i, j, k};
+          Ip[c] += 1;
+          sum += u[c][pidx(s, Ip)] - u[c][pidx(s, I)];
+        }
+        z[cidx(s, i, j, k)] = sum;
+      }
+}
+
+// project! (Table 2) with weight w: x0 = p w dt; solve A x = div u; subtract the
+// mean of x over active cells; u_c[I] -= L_c[I] (x[I] - x[I-e_c]) (Section 2 listing);
+// BC; p = x / (w dt).
+// solver 0: Jacobi-PCG (the reference projection); solver 1: V(0,post) cycles of the
+// multigrid hierarchy until ||z - A x||_inf <= tol or maxit cycles.
+void project(OSim& s, vec* u, double w, double dt, double tol, int maxit, int solver = 0, int post = 4) {
+  Op A = make_op(s, s.lev[0]);
+  vec z, dg;
+  divergence(s, u, z);
+  A.diagonal(dg);
+  vec x(s.ncell);
+  for (long q = 0; q < s.ncell; ++q) x[q] = s.p[q] * w * dt;
+  double res = 0.0;
+  if (solver == 0) {
+    s.last_iters = pcg(A, x, z, tol, maxit, &res);
+  } else {
+    int it = 0;
+    vec Ax;
+    while (true) {
+      A.apply(x, Ax);
+      res = 0.0;
+      for (long q = 0; q < s.ncell; ++q) res = std::max(res, std::fabs(z[q] - Ax[q]));
+      if (res <= tol || it >= maxit) break;
+      vcycle(s, 0, x, z, 0, post);
+      ++it;
+    }
+    s.last_iters = it;
+  }
+  s.last_resid = res;
+  remove_mean_active(x, dg);
+  for (int c = 0; c < s.D; ++c)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          long qm = A.nb(I, c, -1);
+          long q = cidx(s, i, j, k);
+          double L = A.Llower(I, c);
+          if (qm >= 0 && L != 0.0) u[c][pidx(s, I)] -= L * (x[q] - x[qm]);
+        }
+  apply_bc(s, u);
+  for (long q = 0; q < s.ncell; ++q) s.p[q] = x[q] / (w * dt);
+}
+
+// CFL! (Table 2): dt = min(dt_cap, 1/(max_I sum_c [max(0,u_c[I+e_c]) + max(0,-u_c[I])] + 2 D nu)).
+double cfl(const OSim& s) {
+  double m = 0.0;
+  for (int k = 0; k < s.n[2]; ++k)
+    for (int j = 0; j < s.n[1]; ++j)
+      for (int i = 0; i < s.n[0]; ++i) {
+        double sum = 0.0;
+        for (int c = 0; c < s.D; ++c) {
+          int I[3] = {i, j, k}, Ip[3] = {i, j, k};
+          Ip[c] += 1;
+          sum += std::max(0.0, s.u[c][pidx(s, Ip)]) + std::max(0.0, -s.u[c][pidx(s, I)]);
+        }
+        m = std::max(m, sum);
+      }
+  return std::min(s.dt_cap, 1.0 / (m + 2.0 * s.D * s.nu));
+}
+
+}  // namespace
+
+// ===========================================================================
+// C interface (ctypes).  Fields cross the interface as interior arrays, x fastest:
+// velocity as D consecutive blocks of ncell doubles (the lower faces of each cell),
+// scalars as ncell doubles.
+extern "C" {
+
+void* or_create(int D, const int* dims, double nu, const double* U, unsigned periodic, int body_kind,
+                const double* center, double radius, double radius2, double eps, int advect, double dt_cap) {
+  if (D < 2 || D > 3) return nullptr;
+  OSim* s = new OSim();
+  s->D = D;
+  for (int d = 0; d < 3; ++d) {
+    s->n[d] = (d < D) ? dims[d] : 1;
+    s->g[d] = (d < D) ? 2 : 0;
+    s->np[d] = s->n[d] + 2 * s->g[d];
+    s->U[d] = (d < D) ? U[d] : 0.0;
+    s->center[d] = (center && d < D) ? center[d] : 0.0;
+  }
+  s->ncell = (long)s->n[0] * s->n[1] * s->n[2];
+  s->npad = (long)s->np[0] * s->np[1] * s->np[2];
+  s->periodic = periodic;
+  s->nu = nu;
+  s->body_kind = body_kind;
+  s->radius = radius;
+  s->radius2 = radius2;
+  s->eps = eps;
+  s->advect = advect;
+  s->dt_cap = dt_cap;
+  s->t = 0.0;
+  s->nsteps = 0;
+  s->last_iters = 0;
+  s->last_resid = 0.0;
+  for (int c = 0; c < D; ++c) s->u[c].assign(s->npad, 0.0);
+  s->p.assign(s->ncell, 0.0);
+  measure(*s);
+  s->dt = 0.0;
+  return s;
+}
+
+void or_destroy(void* h) { delete (OSim*)h; }
+
+int or_nlevels(void* h) { return (int)((OSim*)h)->lev.size(); }
+void or_level_dims(void* h, int l, int* dims) {
+  OSim* s = (OSim*)h;
+  for (int d = 0; d < 3; ++d) dims[d] = s->lev[l].n[d];
+}
+// Face coefficients of level l: D blocks of that level's ncell.
+void or_get_level_L(void* h, int l, double* out) {
+  OSim* s = (OSim*)h;
+  const Level& lv = s->lev[l];
+  for (int c = 0; c < s->D; ++c) std::memcpy(out + c * lv.ncell, lv.L[c].data(), lv.ncell * sizeof(double));
+}
+void or_get_mu0(void* h, double* out) {
+  OSim* s = (OSim*)h;
+  for (int c = 0; c < s->D; ++c) std::memcpy(out + c * s->ncell, s->mu0[c].data(), s->ncell * sizeof(double));
+}
+// mu1: D*D blocks, block (c*D + j) = component j of mu1 n at the lower c-faces.
+void or_get_mu1(void* h, double* out) {
+  OSim* s = (OSim*)h;
+  for (int c = 0; c < s->D; ++c)
+    for (int j = 0; j < s->D; ++j)
+      std::memcpy(out + (c * s->D + j) * s->ncell, s->mu1[c][j].data(), s->ncell * sizeof(double));
+}
+
+void or_set_u(void* h, const double* in) {
+  OSim* s = (OSim*)h;
+  for (int c = 0; c < s->D; ++c)
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) s->u[c][pidx(*s, i, j, k)] = in[c * s->ncell + cidx(*s, i, j, k)];
+  apply_bc(*s, s->u);
+}
+void or_get_u(void* h, double* out) {
+  OSim* s = (OSim*)h;
+  for (int c = 0; c < s->D; ++c)
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) out[c * s->ncell + cidx(*s, i, j, k)] = s->u[c][pidx(*s, i, j, k)];
+}
+// Padded velocity with every ghost and boundary face (for BC checks): D blocks of npad.
+long or_npad(void* h) { return ((OSim*)h)->npad; }
+void or_get_u_padded(void* h, double* out) {
+  OSim* s = (OSim*)h;
+  for (int c = 0; c < s->D; ++c) std::memcpy(out + c * s->npad, s->u[c].data(), s->npad * sizeof(double));
+}
+void or_set_p(void* h, const double* in) {
+  OSim* s = (OSim*)h;
+  std::memcpy(s->p.data(), in, s->ncell * sizeof(double));
+}
+void or_get_p(void* h, double* out) {
+  OSim* s = (OSim*)h;
+  std::memcpy(out, s->p.data(), s->ncell * sizeof(double));
+}
+double or_get_dt(void* h) { return ((OSim*)h)->dt; }
+void or_set_dt(void* h, double dt) { ((OSim*)h)->dt = dt; }
+double or_get_time(void* h) { return ((OSim*)h)->t; }
+int or_last_iters(void* h) { return ((OSim*)h)->last_iters; }
+double or_last_resid(void* h) { return ((OSim*)h)->last_resid; }
+
+// Initial condition: kind 0 uniform U; kind 1 Taylor-Green vortex sampled at each
+// component's own face positions with wavenumber k = 2 pi / n_0 and amplitude `amp`.
+// Then BC and the initial dt from the CFL rule.
+void or_set_ic(void* h, int kind, double amp) {
+  OSim* s = (OSim*)h;
+  double kw = 2.0 * M_PI / s->n[0];
+  for (int c = 0; c < s->D; ++c)
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) {
+          double v = s->U[c];
+          if (kind == 1) {
+            double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+            x[c] -= 0.5;
+            double cz = (s->D == 3) ? std::cos(kw * x[2]) : 1.0;
+            if (c == 0) v = amp * std::sin(kw * x[0]) * std::cos(kw * x[1]) * cz;
+            else if (c == 1) v = -amp * std::cos(kw * x[0]) * std::sin(kw * x[1]) * cz;
+            else v = 0.0;
+          }
+          s->u[c][pidx(*s, i, j, k)] = v;
+        }
+  apply_bc(*s, s->u);
+  std::fill(s->p.begin(), s->p.end(), 0.0);
+  s->dt = cfl(*s);
+  s->t = 0.0;
+  s->nsteps = 0;
+}
+
+// r = convdiff(u) for an interior velocity u (BC applied internally).
+void or_convdiff(void* h, const double* uin, double* rout) {
+  OSim* s = (OSim*)h;
+  vec u[3], r[3];
+  for (int c = 0; c < s->D; ++c) {
+    u[c].assign(s->npad, 0.0);
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) u[c][pidx(*s, i, j, k)] = uin[c * s->ncell + cidx(*s, i, j, k)];
+  }
+  apply_bc(*s, u);
+  convdiff(*s, u, r);
+  for (int c = 0; c < s->D; ++c) std::memcpy(rout + c * s->ncell, r[c].data(), s->ncell * sizeof(double));
+}
+
+// One BDIM stage on interior arrays: stage 1 uses u0 only; stage 2 uses u0 and u1.
+void or_bdim_stage(void* h, int stage, double dt, const double* u0in, const double* u1in, double* out) {
+  OSim* s = (OSim*)h;
+  vec u0[3], u1[3], o[3];
+  for (int c = 0; c < s->D; ++c) {
+    u0[c].assign(s->npad, 0.0);
+    u1[c].assign(s->npad, 0.0);
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) {
+          long q = c * s->ncell + cidx(*s, i, j, k);
+          u0[c][pidx(*s, i, j, k)] = u0in[q];
+          if (u1in) u1[c][pidx(*s, i, j, k)] = u1in[q];
+        }
+  }
+  apply_bc(*s, u0);
+  apply_bc(*s, u1);
+  bdim_stage(*s, stage, dt, u0, u1, o);
+  for (int c = 0; c < s->D; ++c)
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) out[c * s->ncell + cidx(*s, i, j, k)] = o[c][pidx(*s, i, j, k)];
+}
+
+void or_divergence(void* h, double* z) {
+  OSim* s = (OSim*)h;
+  vec zz;
+  divergence(*s, s->u, zz);
+  std::memcpy(z, zz.data(), s->ncell * sizeof(double));
+}
+
+// y = A_l x on level l.
+void or_poisson_apply(void* h, int l, const double* x, double* y) {
+  OSim* s = (OSim*)h;
+  Op A = make_op(*s, s->lev[l]);
+  vec xx(x, x + A.ncell), yy;
+  A.apply(xx, yy);
+  std::memcpy(y, yy.data(), A.ncell * sizeof(double));
+}
+void or_poisson_diag(void* h, int l, double* dg) {
+  OSim* s = (OSim*)h;
+  Op A = make_op(*s, s->lev[l]);
+  vec d;
+  A.diagonal(d);
+  std::memcpy(dg, d.data(), A.ncell * sizeof(double));
+}
+int or_pcg(void* h, int l, double* x, const double* z, double tol, int maxit, double* resid) {
+  OSim* s = (OSim*)h;
+  Op A = make_op(*s, s->lev[l]);
+  vec xx(x, x + A.ncell), zz(z, z + A.ncell);
+  int it = pcg(A, xx, zz, tol, maxit, resid);
+  std::memcpy(x, xx.data(), A.ncell * sizeof(double));
+  return it;
+}
+int or_dense_solve(void* h, int l, double* x, const double* z) {
+  OSim* s = (OSim*)h;
+  Op A = make_op(*s, s->lev[l]);
+  vec xx, zz(z, z + A.ncell);
+  int rc = dense_solve(A, xx, zz);
+  std::memcpy(x, xx.data(), A.ncell * sizeof(double));
+  return rc;
+}
+// One V-cycle on the fine level: x updated in place; returns ||z - A x||_inf after it.
+double or_vcycle(void* h, double* x, const double* z, int pre, int post) {
+  OSim* s = (OSim*)h;
+  vec xx(x, x + s->ncell), zz(z, z + s->ncell);
+  vcycle(*s, 0, xx, zz, pre, post);
+  std::memcpy(x, xx.data(), s->ncell * sizeof(double));
+  Op A = make_op(*s, s->lev[0]);
+  vec Ax;
+  A.apply(xx, Ax);
+  double m = 0.0;
+  for (long q = 0; q < s->ncell; ++q) m = std::max(m, std::fabs(zz[q] - Ax[q]));
+  return m;
+}
+void or_rb_sweep(void* h, int l, double* x, const double* z) {
+  OSim* s = (OSim*)h;
+  Op A = make_op(*s, s->lev[l]);
+  vec xx(x, x + A.ncell), zz(z, z + A.ncell);
+  rb_sweep(A, xx, zz);
+  std::memcpy(x, xx.data(), A.ncell * sizeof(double));
+}
+
+// project! on the state velocity with weight w and the given dt.
+void or_project(void* h, double w, double dt, double tol, int maxit, int solver) {
+  OSim* s = (OSim*)h;
+  project(*s, s->u, w, dt, tol, maxit, solver);
+}
+
+// One full time step (Heun; see the header).  dt_fixed > 0 keeps dt fixed.
+void or_step(void* h, int nsteps, double tol, int maxit, double dt_fixed, int solver) {
+  OSim* s = (OSim*)h;
+  for (int it = 0; it < nsteps; ++it) {
+    double dt = (dt_fixed > 0.0) ? dt_fixed : s->dt;
+    vec u0[3], u1[3];
+    for (int c = 0; c < s->D; ++c) u0[c] = s->u[c];
+    bdim_stage(*s, 1, dt, u0, u0, u1);
+    project(*s, u1, 1.0, dt, tol, maxit, solver);
+    bdim_stage(*s, 2, dt, u0, u1, s->u);
+    project(*s, s->u, 0.5, dt, tol, maxit, solver);
+    s->t += dt;
+    s->nsteps += 1;
+    s->dt = (dt_fixed > 0.0) ? dt_fixed : cfl(*s);
+  }
+}
+
+double or_cfl(void* h) { return cfl(*(OSim*)h); }
+
+// Pressure force F_d = -sum_cells (p - mean_active p) n_d K_eps(d), K_eps = (1 + cos(pi d/eps))/(2 eps)
+// for |d| < eps (cell centres, volume 1).
+void or_forces(void* h, double* F) {
+  OSim* s = (OSim*)h;
+  Op A = make_op(*s, s->lev[0]);
+  vec dg;
+  A.diagonal(dg);
+  double sum = 0.0;
+  long cnt = 0;
+  for (long q = 0; q < s->ncell; ++q)
+    if (dg[q] > 0.0) {
+      sum += s->p[q];
+      ++cnt;
+    }
+  double pm = cnt ? sum / cnt : 0.0;
+  for (int d = 0; d < 3; ++d) F[d] = 0.0;
+  if (s->body_kind == 0) return;
+  for (int k = 0; k < s->n[2]; ++k)
+    for (int j = 0; j < s->n[1]; ++j)
+      for (int i = 0; i < s->n[0]; ++i) {
+        double x[3] = {i + 0.5, j + 0.5, k + 0.5}, nrm[3];
+        double d = sdf(*s, x, nrm);
+        if (std::fabs(d) >= s->eps) continue;
+        double K = (1.0 + std::cos(M_PI * d / s->eps)) / (2.0 * s->eps);
+        double pp = s->p[cidx(*s, i, j, k)] - pm;
+        for (int dd = 0; dd < s->D; ++dd) F[dd] -= pp * nrm[dd] * K;
+      }
+}
+
+// Kinetic energy E = 1/2 sum_faces sum_c u_c^2 / ncell (stored lower faces).
+double or_kinetic_energy(void* h) {
+  OSim* s = (OSim*)h;
+  double e = 0.0;
+  for (int c = 0; c < s->D; ++c)
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j)
+        for (int i = 0; i < s->n[0]; ++i) {
+          double v = s->u[c][pidx(*s, i, j, k)];
+          e += v * v;
+        }
+  return 0.5 * e / s->ncell;
+}
+
+double or_K0(double x) { return K0(x); }
+double or_K1(double x) { return K1(x); }
+double or_face_value(double uu, double cc, double dd) { return face_value(uu, cc, dd); }
+double or_psi(double r) { return std::max(0.0, std::min(std::min(2.0 * r, (2.0 + r) / 3.0), 2.0)); }
+double or_sdf(void* h, const double* x, double* nrm) { return sdf(*(OSim*)h, x, nrm); }
+
+}  // extern "C"
