@@ -1,0 +1,184 @@
+/*
+ * wl.h - C ABI of the GB300 WaterLily time-step library (libwl.so).
+ *
+ * One simulation ("sim") is an incompressible viscous flow on a uniform staggered
+ * Cartesian grid of n_0 x n_1 [x n_2] cells (grid units: cell width 1).  One time
+ * step (the paper's simstep!, Section 3 and Table 2) is:
+ *   convdiff!  third-order upwind-biased finite-volume convection + viscous flux
+ *              (Section 2; kappa = 1/3 face value with Koren's limiter),
+ *   BDIM!      Boundary Data Immersion blend with the body's signed-distance field
+ *              (Section 2, Weymouth & Yue 2011),
+ *   BC!        domain boundary conditions (Table 2),
+ *   project!   pressure projection with a geometric-multigrid Poisson solve on the
+ *              BDIM-modified matrix (Section 2, Lauber 2022, Weymouth 2022),
+ *   CFL!       adaptive time step (Section 2, Table 2),
+ * arranged as a Heun predictor-corrector with a projection after each stage.
+ *
+ * Layout of every field that crosses this interface: interior cells only, float32,
+ * x fastest: scalar index i + n_0*(j + n_1*k); a velocity is D consecutive blocks
+ * of n_0*n_1*n_2 values, block c holding u_c on the LOWER c-face of each cell
+ * (the staggered convention of the pressure-gradient loop of Section 2,
+ * u[I,i] -= coeff[I,i]*(p[I]-p[I-del(i)])).  The upper boundary face of a
+ * non-periodic direction is not stored: it always carries the boundary value U_c.
+ *
+ * Ownership: the library owns every device buffer of a sim.  They come from one
+ * workspace: either allocated by the library (cudaMallocAsync on the sim's stream)
+ * or supplied by the caller through wl_opts.workspace (size from
+ * wl_workspace_bytes), in which case the caller keeps ownership and must keep it
+ * alive until wl_destroy.  Callers own every dst/src pointer they pass.
+ *
+ * Streams: every call enqueues its work on wl_opts.stream (NULL = the legacy
+ * default stream) and returns without waiting, except where a host output is
+ * written (noted per call); those synchronise the stream.  A handle is not
+ * thread-safe.
+ *
+ * Errors: every int-returning call returns WL_OK (0), a negative error or a
+ * positive warning.  wl_last_error() gives a one-line message.  After
+ * WL_ENONFINITE the sim is poisoned and further steps return it again.
+ */
+#ifndef WL_H
+#define WL_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WL_OK 0
+#define WL_EINVAL (-1)     /* bad argument (dims, sizes, null pointers, field ids) */
+#define WL_ENOMEM (-2)     /* allocation failed or supplied workspace too small */
+#define WL_ECUDA (-3)      /* a CUDA runtime call failed; see wl_last_error */
+#define WL_ENONFINITE (-4) /* a non-finite dt or residual was produced */
+#define WL_ETIMEOUT (-5)   /* a device-side bounded wait gave up */
+#define WL_WNOTCONV 1      /* multigrid hit max_vcycles before tol; state stays valid */
+
+/* field ids for wl_get_field / wl_set_field */
+#define WL_FIELD_U 0    /* velocity, D blocks (read/write) */
+#define WL_FIELD_P 1    /* pressure p (read/write); also the multigrid unknown */
+#define WL_FIELD_DIV 2  /* divergence of the current velocity, sum_c u_c[I+e_c]-u_c[I] (read) */
+#define WL_FIELD_MU0 3  /* BDIM zeroth moment = Poisson face coefficient, D blocks (read) */
+#define WL_FIELD_Z 4    /* right-hand side of the fine multigrid system (read/write) */
+#define WL_FIELD_UPRED 5 /* projected predictor velocity u' that stage 2 reads, D blocks (read/write) */
+#define WL_FIELD_USTAGE 6 /* output of the last wl_stage call, D blocks (read) */
+
+/* body kinds */
+#define WL_BODY_NONE 0
+#define WL_BODY_SPHERE 1 /* circle in 2-D, sphere in 3-D: centre, radius */
+#define WL_BODY_TORUS 2  /* 3-D: ring of radius `radius` in the y-z plane about the x axis, tube radius `radius2` */
+
+typedef struct wl_sim* wl_handle;
+
+/* Immersed body, given by its analytic signed-distance function (Section 2: the
+ * body is defined by a signed distance; its normals and kernel moments are taken
+ * from it).  Positions in grid units (cell I spans [I, I+1)). */
+typedef struct {
+  int kind;
+  double center[3];
+  double radius;
+  double radius2;
+} wl_body;
+
+typedef struct {
+  double tol;            /* Poisson tolerance on ||div u - A x||_inf with x = p*w*dt (default 1e-6) */
+  int max_vcycles;       /* per projection (default 32) */
+  int post;              /* red-black Gauss-Seidel sweeps after each coarse correction (default 4) */
+  double eps;            /* BDIM kernel half-width in cells (default 1) */
+  double dt_cap;         /* upper bound on dt (default 10) */
+  double dt_fixed;       /* > 0: use this dt and skip the CFL rule (default 0) */
+  unsigned periodic_mask;/* bit d: direction d periodic (default 0) */
+  int advect;            /* 1: convection on (default); 0: diffusion only */
+  int precision;         /* 0: FP32 (default); 1: FP64 iterative refinement of the fine-level pressure */
+  int use_graph;         /* 1: wl_step runs as a CUDA graph with device-side V-cycle loops (default) */
+  void* stream;          /* cudaStream_t for all work (default NULL) */
+  void* workspace;       /* optional caller-owned device buffer of wl_workspace_bytes() */
+  size_t workspace_bytes;
+} wl_opts;
+
+/* Fill *o with the defaults listed above. */
+void wl_default_opts(wl_opts* o);
+
+/* Bytes of device workspace one sim of these dimensions needs (ndim 2 or 3;
+ * dims[d] >= 2).  Returns 0 on bad arguments. */
+size_t wl_workspace_bytes(const int* dims, int ndim, const wl_opts* opts);
+
+/* Create a sim (measure step of the method: evaluates the body's signed distance
+ * at every face to give the BDIM moments mu0 = K0(d/eps) and the Poisson
+ * coefficients L = mu0, zero on non-periodic boundary faces (Section 2); builds the
+ * multigrid hierarchy).  nu: kinematic viscosity in grid units; U: D boundary /
+ * free-stream velocities; body may be NULL (no body); opts NULL = defaults.
+ * The velocity starts uniform U, p = 0, dt from the CFL rule.  Synchronises. */
+int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_body* body,
+              const wl_opts* opts, wl_handle* out);
+
+/* Initial condition.  kind 0: uniform U; kind 1: Taylor-Green vortex of amplitude
+ * `amp` (u = amp sin kx cos ky cos kz, v = -amp cos kx sin ky cos kz, w = 0,
+ * k = 2 pi / n_0, each component sampled at its own faces); kind 2: the velocity
+ * in src (D blocks, host or device per src_is_device).  Resets p = 0 and the
+ * clock, and sets dt from the CFL rule.  Synchronises. */
+int wl_set_ic(wl_handle h, int kind, double amp, const float* src, int src_is_device);
+
+/* Advance nsteps full time steps (Heun + two projections + CFL; simstep! of
+ * Section 3).  Asynchronous.  Convergence and non-finite checks are recorded on
+ * the device; wl_status() reads them. */
+int wl_step(wl_handle h, int nsteps);
+
+/* One Heun stage of convdiff! + BDIM! + BC! (Table 2) with the current dt, written
+ * to the stage buffer (WL_FIELD_USTAGE): stage 1 maps u0 = WL_FIELD_U to
+ * mu0 f + mu1.grad f with f = u0 + dt r(u0); stage 2 maps (u0 = WL_FIELD_U,
+ * u' = WL_FIELD_UPRED) to (u' + mu0 f + mu1.grad f)/2 with f = u0 + dt r(u').
+ * r is the finite-volume convection-diffusion residual, mu0/mu1 the BDIM moments
+ * (Section 2).  Does not change the sim's state.  Asynchronous. */
+int wl_stage(wl_handle h, int stage);
+
+/* project! (Table 2) of the current velocity with weight w (1 after stage 1, 1/2
+ * after stage 2): x0 = p w dt, multigrid V-cycles until ||div u - A x||_inf <= tol
+ * or max_vcycles, u_c -= L_c (x[I] - x[I-e_c]) (Section 2), p = x/(w dt).
+ * Writes the V-cycles used and the final residual (x units) to the host outputs
+ * (either may be NULL); synchronises.  Returns WL_WNOTCONV if not converged. */
+int wl_project(wl_handle h, double w, int* vcycles_out, double* resid_out);
+
+/* One multigrid V(0,post) cycle on the fine system A p = z held in the sim
+ * (fields WL_FIELD_P and WL_FIELD_Z, p units): restrict the residual by summing
+ * 2^D children, coarse faces = half the sum of the 2^(D-1) fine faces, coarsest
+ * level solved in FP64, piecewise-constant prolongation, red-black Gauss-Seidel
+ * smoothing (Section 2: GMG, Weymouth 2022).  Writes ||z - A p||_inf after the
+ * cycle to *resid_inf_out (may be NULL); synchronises. */
+int wl_gmg_vcycle(wl_handle h, double* resid_inf_out);
+
+/* Pressure force on the body, F_d = -sum_cells (p - pbar) n_d K_eps(d), with the
+ * cosine kernel K_eps = (1 + cos(pi d/eps))/(2 eps) over |d| < eps and pbar the
+ * mean pressure over cells with a nonzero Poisson row; accumulated in FP64.
+ * F receives D values.  Synchronises. */
+int wl_forces(wl_handle h, double* F);
+
+/* Copy a field (WL_FIELD_*) to dst (host or device).  Synchronises when dst is on
+ * the host. */
+int wl_get_field(wl_handle h, int which, void* dst, int dst_is_device);
+/* Overwrite a writable field from src (host or device).  Synchronises. */
+int wl_set_field(wl_handle h, int which, const void* src, int src_is_device);
+
+/* Current dt (the one the next step uses), simulated time and steps taken.
+ * Synchronise. */
+int wl_get_dt(wl_handle h, double* dt);
+int wl_set_dt(wl_handle h, double dt);
+int wl_get_time(wl_handle h, double* t, long long* steps);
+
+/* Device-recorded status of the steps since the last call: V-cycles used by the
+ * two projections of the last step, total V-cycles, and the worst final residual
+ * (x units).  Returns WL_ENONFINITE / WL_WNOTCONV if any step saw that.
+ * Synchronises. */
+int wl_status(wl_handle h, int* last_vcycles /*[2]*/, long long* total_vcycles, double* worst_resid);
+
+/* Levels of the multigrid hierarchy and the dims of level l (dims[3]). */
+int wl_levels(wl_handle h, int* nlevels);
+int wl_level_dims(wl_handle h, int l, int* dims);
+
+void wl_destroy(wl_handle h);
+const char* wl_last_error(wl_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WL_H */

@@ -81,11 +81,14 @@ inline long pidx(const OSim& s, const int* I) { return pidx(s, I[0], I[1], I[2])
 // ---------------------------------------------------------------------------
 // Kernel moments of the cosine kernel K(s) = (1 + cos(pi s))/2 on [-1, 1]
 // (BDIM, Section 2): K0(s) = int_{-1}^{s} K, K1(s) = int_{s}^{1} t K(t) dt.
-// Outside the kernel's support the integrals are exactly 0 or 1.
+// Outside the kernel's support the integrals are exactly 0 or 1; K0 is the integral
+// of a non-negative kernel of unit mass, so it is kept in [0, 1] where rounding of the
+// closed form near s = -1 (a cancellation) could step outside.
 double K0(double s) {
   if (s <= -1.0) return 0.0;
   if (s >= 1.0) return 1.0;
-  return 0.5 + 0.5 * s + std::sin(M_PI * s) / (2.0 * M_PI);
+  double v = 0.5 + 0.5 * s + std::sin(M_PI * s) / (2.0 * M_PI);
+  return std::max(0.0, std::min(1.0, v));
 }
 double K1(double s) {
   if (s <= -1.0 || s >= 1.0) return 0.0;

@@ -1,0 +1,760 @@
+// Host runtime and C ABI of libwl.so (declared in include/wl.h).
+//
+// A sim owns one device workspace carved into: three velocity buffers (A: the state
+// and start-of-step u0, B: stage output, C: projected predictor), the multigrid
+// levels (face coefficients, right-hand side, iterate and a ping-pong iterate), the
+// device-resident scalars (DevState), the coarsest-level CG vectors and the force
+// partial sums.  One time step (simstep!, Section 3) is enqueued as
+//   stage 1 (A -> B), project w=1 (B, corrected into C),
+//   stage 2 (C, A -> B), project w=1/2 (B, corrected into A, with the CFL maximum),
+//   step end (clock, next dt).
+// Each projection's V-cycle loop is a CUDA-graph conditional WHILE node whose
+// condition a one-thread kernel sets from the residual after every cycle, so a
+// whole step runs without a host round trip.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "wl.h"
+#include "wl_kernels.h"
+
+using namespace wl;
+
+namespace {
+
+struct LevelBuf {
+  Grid g;
+  float* L[3];
+  float* z;
+  float* x;
+  float* x2;
+};
+
+constexpr int kMaxLevels = 16;
+constexpr int kForceParts = 1024;
+
+}  // namespace
+
+struct wl_sim {
+  int D = 0;
+  Grid g{};
+  double nu = 0.0;
+  Body body{};
+  wl_opts o{};
+  cudaStream_t st = nullptr;  // caller's stream
+  cudaStream_t cs = nullptr;  // private stream used only for graph capture
+  int nlev = 0;
+  LevelBuf lev[kMaxLevels]{};
+  float* ua[3]{};
+  float* ub[3]{};
+  float* uc[3]{};
+  DevState* ds = nullptr;
+  DevState* hs = nullptr;     // pinned host mirror
+  double* cg_work = nullptr;
+  double* fpart = nullptr;
+  double* fout = nullptr;
+  double* p64 = nullptr;      // precision mode 1: FP64 fine pressure
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle hc[2]{};
+  bool poisoned = false;
+  std::string err;
+};
+
+namespace {
+
+int fail(wl_sim* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  return code;
+}
+
+int cuda_check(wl_sim* s, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return WL_OK;
+  return fail(s, WL_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define WL_CUDA(s, call)                                 \
+  do {                                                   \
+    int _rc = cuda_check((s), (call), #call);            \
+    if (_rc != WL_OK) return _rc;                        \
+  } while (0)
+
+// Multigrid levels: halve while every direction is even and larger than 4.
+int plan_levels(const int* n, int D, int out[][3]) {
+  int l = 0;
+  int cur[3] = {n[0], n[1], D == 3 ? n[2] : 1};
+  while (true) {
+    for (int d = 0; d < 3; ++d) out[l][d] = cur[d];
+    ++l;
+    bool ok = l < kMaxLevels;
+    for (int d = 0; d < D; ++d)
+      if (cur[d] % 2 != 0 || cur[d] <= 4) ok = false;
+    if (!ok) break;
+    for (int d = 0; d < D; ++d) cur[d] /= 2;
+  }
+  return l;
+}
+
+struct Carver {
+  char* base;
+  size_t off = 0;
+  void* take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  }
+};
+
+// Walks the workspace layout; with base == nullptr only measures it.
+size_t layout(wl_sim* s, int D, const int* dims, int precision, char* base) {
+  int ld[kMaxLevels][3];
+  const int nlev = plan_levels(dims, D, ld);
+  Carver cv{base};
+  const long long nc = (long long)ld[0][0] * ld[0][1] * ld[0][2];
+  float** bufs[3] = {s ? s->ua : nullptr, s ? s->ub : nullptr, s ? s->uc : nullptr};
+  for (int b = 0; b < 3; ++b)
+    for (int c = 0; c < D; ++c) {
+      void* p = cv.take(sizeof(float) * nc);
+      if (s) bufs[b][c] = (float*)p;
+    }
+  for (int l = 0; l < nlev; ++l) {
+    const long long n = (long long)ld[l][0] * ld[l][1] * ld[l][2];
+    for (int c = 0; c < D; ++c) {
+      void* p = cv.take(sizeof(float) * n);
+      if (s) s->lev[l].L[c] = (float*)p;
+    }
+    void* z = cv.take(sizeof(float) * n);
+    void* x = cv.take(sizeof(float) * n);
+    void* x2 = cv.take(sizeof(float) * n);
+    if (s) {
+      s->lev[l].z = (float*)z;
+      s->lev[l].x = (float*)x;
+      s->lev[l].x2 = (float*)x2;
+    }
+  }
+  void* ds = cv.take(sizeof(DevState));
+  const long long ncoarse = (long long)ld[nlev - 1][0] * ld[nlev - 1][1] * ld[nlev - 1][2];
+  void* cg = cv.take(sizeof(double) * 5 * ncoarse);
+  void* fp = cv.take(sizeof(double) * 2 * kForceParts);
+  void* fo = cv.take(sizeof(double) * 4);
+  void* p64 = precision == 1 ? cv.take(sizeof(double) * nc) : nullptr;
+  if (s) {
+    s->ds = (DevState*)ds;
+    s->cg_work = (double*)cg;
+    s->fpart = (double*)fp;
+    s->fout = (double*)fo;
+    s->p64 = (double*)p64;
+    s->nlev = nlev;
+    for (int l = 0; l < nlev; ++l) {
+      Grid& g = s->lev[l].g;
+      g = s->g;
+      for (int d = 0; d < 3; ++d) g.n[d] = ld[l][d];
+      g.nc = (long long)ld[l][0] * ld[l][1] * ld[l][2];
+    }
+    for (int b = 0; b < 3; ++b)
+      for (int c = D; c < 3; ++c) bufs[b][c] = bufs[b][D - 1];  // 2-D: unused slot aliases a valid pointer
+    for (int l = 0; l < nlev; ++l)
+      for (int c = D; c < 3; ++c) s->lev[l].L[c] = s->lev[l].L[D - 1];
+  }
+  return cv.off;
+}
+
+// ------------------------------------------------------------------- enqueue helpers
+StageArgs stage_args(wl_sim* s, int stage) {
+  StageArgs a{};
+  for (int c = 0; c < 3; ++c) {
+    a.u[c] = stage == 1 ? s->ua[c] : s->uc[c];
+    a.u0[c] = s->ua[c];
+    a.mu0[c] = s->lev[0].L[c];
+    a.out[c] = s->ub[c];
+  }
+  a.g = s->g;
+  a.dt = &s->ds->dt;
+  a.nu = (float)s->nu;
+  a.stage = stage;
+  a.advect = s->o.advect;
+  return a;
+}
+
+void enq_stage(wl_sim* s, int stage, cudaStream_t st) { launch_stage(s->D, stage_args(s, stage), s->body, st); }
+
+ResArgs res_args(wl_sim* s, int l, int mode) {
+  ResArgs a{};
+  const LevelBuf& L = s->lev[l];
+  for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
+  a.x = L.x;
+  a.z = L.z;
+  a.zc = (l + 1 < s->nlev) ? s->lev[l + 1].z : nullptr;
+  a.g = L.g;
+  if (l + 1 < s->nlev)
+    for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
+  a.dt = &s->ds->dt;
+  a.w = 1.f;
+  a.st = s->ds;
+  a.mode = mode;
+  return a;
+}
+
+// divergence of u (scaled by 1/(w dt)), first residual, restriction, first decision
+void enq_proj_head(wl_sim* s, float* const* u, float w, int proj, cudaStream_t st, int use_h) {
+  ResArgs a = res_args(s, 0, RES_DIVERGENCE);
+  for (int c = 0; c < 3; ++c) a.u[c] = u[c];
+  a.w = w;
+  launch_residual(s->D, a, st);
+  launch_decide(s->ds, s->hc[proj], use_h, 1, proj, w, s->o.tol, s->o.max_vcycles, st);
+}
+
+// post sweeps on level l with the coarse correction of level l+1 prolonged into the
+// first one; the result lands in lev[l].x
+void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
+  LevelBuf& L = s->lev[l];
+  const int P = s->o.post;
+  SweepArgs a{};
+  for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
+  a.z = L.z;
+  a.g = L.g;
+  for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
+  float* bufs[2] = {L.x, L.x2};
+  int cur;  // index of the buffer holding the current iterate
+  if (l == 0) {
+    a.x_in = L.x;
+    a.xc = s->lev[1].x;
+    a.x_out = L.x2;
+    launch_sweep(s->D, a, st);
+    cur = 1;
+  } else {
+    a.x_in = nullptr;
+    a.xc = s->lev[l + 1].x;
+    cur = (P % 2 == 1) ? 0 : 1;
+    a.x_out = bufs[cur];
+    launch_sweep(s->D, a, st);
+  }
+  a.xc = nullptr;
+  for (int it = 1; it < P; ++it) {
+    a.x_in = bufs[cur];
+    a.x_out = bufs[cur ^ 1];
+    launch_sweep(s->D, a, st);
+    cur ^= 1;
+  }
+  if (cur != 0) cudaMemcpyAsync(L.x, L.x2, sizeof(float) * L.g.nc, cudaMemcpyDeviceToDevice, st);
+}
+
+void enq_coarsest(wl_sim* s, int l, cudaStream_t st) {
+  CoarseArgs a{};
+  LevelBuf& L = s->lev[l];
+  a.z = L.z;
+  for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
+  a.x = L.x;
+  a.g = L.g;
+  a.work = s->cg_work;
+  a.maxit = (int)std::min<long long>(4 * L.g.nc + 100, 100000);
+  a.rtol = 1e-12;
+  launch_coarse(s->D, a, st);
+}
+
+// restriction down the coarse levels, coarsest solve, prolongation + smoothing up to
+// the fine level (whose right-hand side and restricted residual are already set)
+void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
+  const int Lv = s->nlev;
+  if (Lv == 1) {
+    enq_coarsest(s, 0, st);  // no coarse level: solve the fine level directly
+    return;
+  }
+  for (int l = 1; l + 1 < Lv; ++l) launch_residual(s->D, res_args(s, l, RES_RESTRICT), st);
+  enq_coarsest(s, Lv - 1, st);
+  for (int l = Lv - 2; l >= 0; --l) enq_smooth(s, l, st);
+}
+
+void enq_vcycle(wl_sim* s, float w, int proj, cudaStream_t st, int use_h) {
+  enq_vcycle_core(s, st);
+  launch_residual(s->D, res_args(s, 0, RES_RESIDUAL), st);
+  launch_decide(s->ds, s->hc[proj], use_h, 0, proj, w, s->o.tol, s->o.max_vcycles, st);
+}
+
+void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int cfl, cudaStream_t st) {
+  CorrArgs a{};
+  for (int c = 0; c < 3; ++c) {
+    a.u_in[c] = uin[c];
+    a.u_out[c] = uout[c];
+    a.L[c] = s->lev[0].L[c];
+  }
+  a.x = s->lev[0].x;
+  a.g = s->g;
+  a.dt = &s->ds->dt;
+  a.w = w;
+  a.cfl = cfl;
+  a.st = s->ds;
+  launch_correct(s->D, a, st);
+}
+
+int sync_state(wl_sim* s) {
+  WL_CUDA(s, cudaMemcpyAsync(s->hs, s->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  return WL_OK;
+}
+
+// projection loop driven from the host (used outside graphs)
+int host_projection(wl_sim* s, float* const* u, float w, int proj) {
+  enq_proj_head(s, u, w, proj, s->st, 0);
+  int rc = sync_state(s);
+  if (rc) return rc;
+  while (s->hs->cond) {
+    enq_vcycle(s, w, proj, s->st, 0);
+    rc = sync_state(s);
+    if (rc) return rc;
+  }
+  return WL_OK;
+}
+
+int host_step(wl_sim* s) {
+  enq_stage(s, 1, s->st);
+  int rc = host_projection(s, s->ub, 1.f, 0);
+  if (rc) return rc;
+  enq_correct(s, s->ub, s->uc, 1.f, 0, s->st);
+  enq_stage(s, 2, s->st);
+  rc = host_projection(s, s->ub, 0.5f, 1);
+  if (rc) return rc;
+  enq_correct(s, s->ub, s->ua, 0.5f, 1, s->st);
+  launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->st);
+  return cuda_check(s, cudaGetLastError(), "step launch");
+}
+
+int capture_leaf(wl_sim* s, std::vector<cudaGraphNode_t>& leaf) {
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  WL_CUDA(s, cudaStreamGetCaptureInfo(s->cs, &cst, nullptr, nullptr, &deps, nullptr, &nd));
+  leaf.assign(deps, deps + nd);
+  return WL_OK;
+}
+
+int add_while(wl_sim* s, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, int proj, float w,
+              cudaGraphNode_t* node) {
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = s->hc[proj];
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  WL_CUDA(s, cudaGraphAddNode(node, g, deps.data(), nullptr, deps.size(), &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enq_vcycle(s, w, proj, s->cs, 1);
+  cudaGraph_t out = nullptr;
+  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
+  return WL_OK;
+}
+
+// One step as a graph: three captured segments joined by two WHILE nodes.
+int build_step_graph(wl_sim* s) {
+  cudaGraph_t g = nullptr;
+  WL_CUDA(s, cudaGraphCreate(&g, 0));
+  for (int p = 0; p < 2; ++p) WL_CUDA(s, cudaGraphConditionalHandleCreate(&s->hc[p], g, 0, 0));
+  std::vector<cudaGraphNode_t> leaf;
+  cudaGraph_t out = nullptr;
+  cudaGraphNode_t w1, w2;
+  // segment 1: stage 1, divergence + first residual
+  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  enq_stage(s, 1, s->cs);
+  enq_proj_head(s, s->ub, 1.f, 0, s->cs, 1);
+  int rc = capture_leaf(s, leaf);
+  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
+  if (rc) return rc;
+  rc = add_while(s, g, leaf, 0, 1.f, &w1);
+  if (rc) return rc;
+  // segment 2: correction, stage 2, divergence + first residual
+  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w1, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  enq_correct(s, s->ub, s->uc, 1.f, 0, s->cs);
+  enq_stage(s, 2, s->cs);
+  enq_proj_head(s, s->ub, 0.5f, 1, s->cs, 1);
+  rc = capture_leaf(s, leaf);
+  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
+  if (rc) return rc;
+  rc = add_while(s, g, leaf, 1, 0.5f, &w2);
+  if (rc) return rc;
+  // segment 3: correction with the CFL maximum, step end
+  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w2, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  enq_correct(s, s->ub, s->ua, 0.5f, 1, s->cs);
+  launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->cs);
+  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
+  WL_CUDA(s, cudaGraphInstantiate(&s->exec, g, 0));
+  s->graph = g;
+  return WL_OK;
+}
+
+int set_dt_from_ic(wl_sim* s) {
+  const float* u[3] = {s->ua[0], s->ua[1], s->ua[2]};
+  launch_cfl_only(s->D, s->g, u, s->ds, s->st);
+  launch_set_dt_from_cfl(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->st);
+  return cuda_check(s, cudaGetLastError(), "initial dt");
+}
+
+int reset_state(wl_sim* s) {
+  WL_CUDA(s, cudaMemsetAsync(s->ds, 0, sizeof(DevState), s->st));
+  WL_CUDA(s, cudaMemsetAsync(s->lev[0].x, 0, sizeof(float) * s->g.nc, s->st));
+  return WL_OK;
+}
+
+bool valid_field(int which) { return which >= WL_FIELD_U && which <= WL_FIELD_USTAGE; }
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+void wl_default_opts(wl_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-6;
+  o->max_vcycles = 32;
+  o->post = 4;
+  o->eps = 1.0;
+  o->dt_cap = 10.0;
+  o->dt_fixed = 0.0;
+  o->periodic_mask = 0u;
+  o->advect = 1;
+  o->precision = 0;
+  o->use_graph = 1;
+  o->stream = nullptr;
+  o->workspace = nullptr;
+  o->workspace_bytes = 0;
+}
+
+size_t wl_workspace_bytes(const int* dims, int ndim, const wl_opts* opts) {
+  if (!dims || (ndim != 2 && ndim != 3)) return 0;
+  for (int d = 0; d < ndim; ++d)
+    if (dims[d] < 2) return 0;
+  return layout(nullptr, ndim, dims, opts ? opts->precision : 0, nullptr);
+}
+
+int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_body* body, const wl_opts* opts,
+              wl_handle* out) {
+  if (!out) return WL_EINVAL;
+  *out = nullptr;
+  if (!dims || !U || (ndim != 2 && ndim != 3)) return WL_EINVAL;
+  for (int d = 0; d < ndim; ++d)
+    if (dims[d] < 2 || dims[d] > (1 << 20)) return WL_EINVAL;
+  const long long nc = (long long)dims[0] * dims[1] * (ndim == 3 ? dims[2] : 1);
+  if (nc > (1LL << 31)) return WL_EINVAL;
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return WL_EINVAL;
+  wl_opts o;
+  wl_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.tol > 0.0) || o.max_vcycles < 0 || o.post < 1 || !(o.eps > 0.0) || !(o.dt_cap > 0.0) ||
+      o.precision < 0 || o.precision > 1)
+    return WL_EINVAL;
+  if (o.precision == 1) return WL_EINVAL;  // FP64 refinement path not built in this library version
+  if (body && (body->kind < 0 || body->kind > 2 || (body->kind == 2 && ndim != 3))) return WL_EINVAL;
+  wl_sim* s = new wl_sim();
+  s->D = ndim;
+  s->o = o;
+  s->nu = nu;
+  s->st = (cudaStream_t)o.stream;
+  for (int d = 0; d < 3; ++d) {
+    s->g.n[d] = d < ndim ? dims[d] : 1;
+    s->g.U[d] = d < ndim ? (float)U[d] : 0.f;
+    if (d < ndim && !std::isfinite(U[d])) {
+      delete s;
+      return WL_EINVAL;
+    }
+  }
+  s->g.per = o.periodic_mask & ((1u << ndim) - 1u);
+  s->g.nc = nc;
+  s->body.kind = body ? body->kind : 0;
+  for (int d = 0; d < 3; ++d) s->body.c[d] = body ? body->center[d] : 0.0;
+  s->body.r1 = body ? body->radius : 0.0;
+  s->body.r2 = body ? body->radius2 : 0.0;
+  s->body.eps = o.eps;
+  const size_t need = layout(nullptr, ndim, dims, o.precision, nullptr);
+  if (o.workspace) {
+    if (o.workspace_bytes < need || ((uintptr_t)o.workspace & 255u)) {
+      delete s;
+      return WL_ENOMEM;
+    }
+    s->ws = (char*)o.workspace;
+    s->own_ws = false;
+  } else {
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return WL_ENOMEM;
+    }
+    s->ws = (char*)p;
+    s->own_ws = true;
+  }
+  s->ws_bytes = need;
+  layout(s, ndim, dims, o.precision, s->ws);
+  int rc = WL_OK;
+  if (cudaMallocHost(&s->hs, sizeof(DevState)) != cudaSuccess) rc = fail(s, WL_ENOMEM, "pinned host state");
+  if (!rc) rc = cuda_check(s, cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking), "capture stream");
+  if (!rc) {
+    launch_measure(ndim, s->g, s->body, s->lev[0].L, s->st);
+    for (int l = 1; l < s->nlev; ++l) {
+      const float* Lf[3] = {s->lev[l - 1].L[0], s->lev[l - 1].L[1], s->lev[l - 1].L[2]};
+      launch_coarsen(ndim, s->lev[l - 1].g, Lf, s->lev[l].g, s->lev[l].L, s->st);
+    }
+    for (int l = 0; l < s->nlev; ++l) {
+      cudaMemsetAsync(s->lev[l].x, 0, sizeof(float) * s->lev[l].g.nc, s->st);
+      cudaMemsetAsync(s->lev[l].z, 0, sizeof(float) * s->lev[l].g.nc, s->st);
+    }
+    rc = reset_state(s);
+  }
+  if (!rc) {
+    launch_set_ic(ndim, s->g, 0, 0.0, s->ua, s->st);
+    rc = set_dt_from_ic(s);
+  }
+  if (!rc) rc = cuda_check(s, cudaStreamSynchronize(s->st), "create");
+  if (rc) {
+    wl_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return WL_OK;
+}
+
+void wl_destroy(wl_handle s) {
+  if (!s) return;
+  if (s->st) cudaStreamSynchronize(s->st);
+  else cudaDeviceSynchronize();
+  if (s->exec) cudaGraphExecDestroy(s->exec);
+  if (s->graph) cudaGraphDestroy(s->graph);
+  if (s->cs) cudaStreamDestroy(s->cs);
+  if (s->hs) cudaFreeHost(s->hs);
+  if (s->own_ws && s->ws) cudaFree(s->ws);
+  delete s;
+}
+
+const char* wl_last_error(wl_handle s) { return s ? s->err.c_str() : "null handle"; }
+
+int wl_set_ic(wl_handle s, int kind, double amp, const float* src, int src_is_device) {
+  if (!s) return WL_EINVAL;
+  if (kind < 0 || kind > 2 || (kind == 2 && !src)) return fail(s, WL_EINVAL, "wl_set_ic: bad kind/source");
+  if (kind == 2) {
+    for (int c = 0; c < s->D; ++c)
+      WL_CUDA(s, cudaMemcpyAsync(s->ua[c], src + (size_t)c * s->g.nc, sizeof(float) * s->g.nc,
+                                 src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+    launch_fix_bfaces(s->D, s->g, s->ua, s->st);
+  } else {
+    launch_set_ic(s->D, s->g, kind, amp, s->ua, s->st);
+  }
+  int rc = reset_state(s);
+  if (rc) return rc;
+  rc = set_dt_from_ic(s);
+  if (rc) return rc;
+  s->poisoned = false;
+  return cuda_check(s, cudaStreamSynchronize(s->st), "wl_set_ic");
+}
+
+int wl_step(wl_handle s, int nsteps) {
+  if (!s || nsteps < 0) return WL_EINVAL;
+  if (s->poisoned) return fail(s, WL_ENONFINITE, "sim is poisoned by a non-finite value");
+  if (s->o.precision == 1) {
+    for (int n = 0; n < nsteps; ++n) {
+      int rc = host_step(s);
+      if (rc) return rc;
+    }
+    return WL_OK;
+  }
+  if (!s->o.use_graph) {
+    for (int n = 0; n < nsteps; ++n) {
+      int rc = host_step(s);
+      if (rc) return rc;
+    }
+    return WL_OK;
+  }
+  if (!s->exec) {
+    int rc = build_step_graph(s);
+    if (rc) return rc;
+  }
+  for (int n = 0; n < nsteps; ++n) WL_CUDA(s, cudaGraphLaunch(s->exec, s->st));
+  return WL_OK;
+}
+
+int wl_stage(wl_handle s, int stage) {
+  if (!s || (stage != 1 && stage != 2)) return WL_EINVAL;
+  enq_stage(s, stage, s->st);
+  return cuda_check(s, cudaGetLastError(), "wl_stage");
+}
+
+int wl_project(wl_handle s, double w, int* vcycles_out, double* resid_out) {
+  if (!s || !(w > 0.0)) return WL_EINVAL;
+  int rc = host_projection(s, s->ua, (float)w, 0);
+  if (rc) return rc;
+  enq_correct(s, s->ua, s->ua, (float)w, 0, s->st);  // no neighbour reads: in place is safe
+  rc = sync_state(s);
+  if (rc) return rc;
+  if (vcycles_out) *vcycles_out = s->hs->last_iters[0];
+  if (resid_out) *resid_out = s->hs->last_res[0];
+  if (!std::isfinite(s->hs->last_res[0])) {
+    s->poisoned = true;
+    return fail(s, WL_ENONFINITE, "non-finite residual");
+  }
+  return (s->hs->last_res[0] > s->o.tol) ? WL_WNOTCONV : WL_OK;
+}
+
+int wl_gmg_vcycle(wl_handle s, double* resid_inf_out) {
+  if (!s) return WL_EINVAL;
+  // restrict the residual of the held system, run one cycle, measure the residual
+  ResArgs a = res_args(s, 0, RES_RESIDUAL);
+  launch_residual(s->D, a, s->st);
+  enq_vcycle_core(s, s->st);
+  WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
+  ResArgs b = res_args(s, 0, RES_RESIDUAL);
+  b.zc = nullptr;
+  launch_residual(s->D, b, s->st);
+  int rc = sync_state(s);
+  if (rc) return rc;
+  const float r = reinterpret_cast<const float&>(s->hs->norm_bits);
+  WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
+  if (resid_inf_out) *resid_inf_out = r;
+  return cuda_check(s, cudaStreamSynchronize(s->st), "wl_gmg_vcycle");
+}
+
+int wl_forces(wl_handle s, double* F) {
+  if (!s || !F) return WL_EINVAL;
+  const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
+  launch_forces(s->D, s->g, s->body, s->lev[0].x, L, s->fpart, kForceParts, s->fout, s->st);
+  double h[4];
+  WL_CUDA(s, cudaMemcpyAsync(h, s->fout, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  for (int d = 0; d < s->D; ++d) F[d] = h[d];
+  return WL_OK;
+}
+
+int wl_get_field(wl_handle s, int which, void* dst, int dst_is_device) {
+  if (!s || !dst || !valid_field(which)) return WL_EINVAL;
+  const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  const size_t nb = sizeof(float) * s->g.nc;
+  char* d = (char*)dst;
+  switch (which) {
+    case WL_FIELD_U:
+      for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(d + c * nb, s->ua[c], nb, kind, s->st));
+      break;
+    case WL_FIELD_P:
+      WL_CUDA(s, cudaMemcpyAsync(d, s->lev[0].x, nb, kind, s->st));
+      break;
+    case WL_FIELD_DIV: {
+      ResArgs a = res_args(s, 0, RES_DIV_ONLY);
+      for (int c = 0; c < 3; ++c) a.u[c] = s->ua[c];
+      a.z = s->lev[0].x2;
+      a.zc = nullptr;
+      launch_residual(s->D, a, s->st);
+      WL_CUDA(s, cudaMemcpyAsync(d, s->lev[0].x2, nb, kind, s->st));
+      break;
+    }
+    case WL_FIELD_MU0:
+      for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(d + c * nb, s->lev[0].L[c], nb, kind, s->st));
+      break;
+    case WL_FIELD_Z:
+      WL_CUDA(s, cudaMemcpyAsync(d, s->lev[0].z, nb, kind, s->st));
+      break;
+    case WL_FIELD_UPRED:
+      for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(d + c * nb, s->uc[c], nb, kind, s->st));
+      break;
+    case WL_FIELD_USTAGE:
+      for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(d + c * nb, s->ub[c], nb, kind, s->st));
+      break;
+    default:
+      return WL_EINVAL;
+  }
+  if (!dst_is_device) WL_CUDA(s, cudaStreamSynchronize(s->st));
+  return cuda_check(s, cudaGetLastError(), "wl_get_field");
+}
+
+int wl_set_field(wl_handle s, int which, const void* src, int src_is_device) {
+  if (!s || !src) return WL_EINVAL;
+  const cudaMemcpyKind kind = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const size_t nb = sizeof(float) * s->g.nc;
+  const char* p = (const char*)src;
+  switch (which) {
+    case WL_FIELD_U:
+      for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(s->ua[c], p + c * nb, nb, kind, s->st));
+      launch_fix_bfaces(s->D, s->g, s->ua, s->st);
+      break;
+    case WL_FIELD_P:
+      WL_CUDA(s, cudaMemcpyAsync(s->lev[0].x, p, nb, kind, s->st));
+      break;
+    case WL_FIELD_Z:
+      WL_CUDA(s, cudaMemcpyAsync(s->lev[0].z, p, nb, kind, s->st));
+      break;
+    case WL_FIELD_UPRED:
+      for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(s->uc[c], p + c * nb, nb, kind, s->st));
+      launch_fix_bfaces(s->D, s->g, s->uc, s->st);
+      break;
+    default:
+      return fail(s, WL_EINVAL, "field is read-only");
+  }
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  return cuda_check(s, cudaGetLastError(), "wl_set_field");
+}
+
+int wl_get_dt(wl_handle s, double* dt) {
+  if (!s || !dt) return WL_EINVAL;
+  int rc = sync_state(s);
+  if (rc) return rc;
+  *dt = s->hs->dt;
+  return WL_OK;
+}
+
+int wl_set_dt(wl_handle s, double dt) {
+  if (!s || !(dt > 0.0) || !std::isfinite(dt)) return WL_EINVAL;
+  WL_CUDA(s, cudaMemcpyAsync(&s->ds->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  return WL_OK;
+}
+
+int wl_get_time(wl_handle s, double* t, long long* steps) {
+  if (!s) return WL_EINVAL;
+  int rc = sync_state(s);
+  if (rc) return rc;
+  if (t) *t = s->hs->time;
+  if (steps) *steps = s->hs->steps;
+  return WL_OK;
+}
+
+int wl_status(wl_handle s, int* last_vcycles, long long* total_vcycles, double* worst_resid) {
+  if (!s) return WL_EINVAL;
+  int rc = sync_state(s);
+  if (rc) return rc;
+  const DevState h = *s->hs;
+  if (last_vcycles) {
+    last_vcycles[0] = h.last_iters[0];
+    last_vcycles[1] = h.last_iters[1];
+  }
+  if (total_vcycles) *total_vcycles = h.total_vcycles;
+  if (worst_resid) *worst_resid = h.worst_res;
+  // clear the sticky flags for the next interval
+  int zero = 0;
+  float fz = 0.f;
+  WL_CUDA(s, cudaMemcpyAsync(&s->ds->status, &zero, sizeof(int), cudaMemcpyHostToDevice, s->st));
+  WL_CUDA(s, cudaMemcpyAsync(&s->ds->worst_res, &fz, sizeof(float), cudaMemcpyHostToDevice, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  if (h.status & 1) {
+    s->poisoned = true;
+    return fail(s, WL_ENONFINITE, "non-finite dt or residual");
+  }
+  if (h.status & 2) return WL_WNOTCONV;
+  return WL_OK;
+}
+
+int wl_levels(wl_handle s, int* nlevels) {
+  if (!s || !nlevels) return WL_EINVAL;
+  *nlevels = s->nlev;
+  return WL_OK;
+}
+
+int wl_level_dims(wl_handle s, int l, int* dims) {
+  if (!s || !dims || l < 0 || l >= s->nlev) return WL_EINVAL;
+  for (int d = 0; d < 3; ++d) dims[d] = s->lev[l].g.n[d];
+  return WL_OK;
+}
+
+}  // extern "C"

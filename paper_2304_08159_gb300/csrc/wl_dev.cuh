@@ -1,0 +1,173 @@
+// Device-side building blocks shared by the kernels of libwl.so.
+//
+// Storage: every field is float32, interior cells only, x fastest.  There are no
+// ghost cells in memory: the domain boundary conditions (BC!, Table 2) are applied
+// on the fly by mapping an out-of-range index to the value the BC defines
+// ("virtual ghosts").  This removes the separate BC kernel and its traffic.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wl {
+
+struct Grid {
+  int n[3];        // cells per direction (n[2] = 1 in 2-D)
+  unsigned per;    // bit d: direction d periodic
+  float U[3];      // boundary velocity (normal component on non-periodic sides)
+  long long nc;    // cells
+};
+
+__device__ __forceinline__ bool is_per(const Grid& g, int d) { return (g.per >> d) & 1u; }
+
+__device__ __forceinline__ long long cell_index(const Grid& g, int i, int j, int k) {
+  return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
+}
+
+// Velocity component c at face index (i,j,k), which may lie up to two cells outside
+// the interior in any direction.  BC (Table 2): along a non-periodic direction d the
+// normal component (c == d) takes U_c on the boundary faces (index 0 and n_d) and
+// beyond; the tangential components copy the nearest interior value; periodic
+// directions wrap.  Requires n_d >= 2.
+template <int D>
+__device__ __forceinline__ float load_u_bc(const float* __restrict__ uc, int c, const Grid& g, int i, int j,
+                                           int k) {
+  int I[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int q = I[d];
+    const int n = g.n[d];
+    if (is_per(g, d)) {
+      q = (q < 0) ? q + n : ((q >= n) ? q - n : q);
+    } else {
+      if (d == c && (q <= 0 || q >= n)) return g.U[c];
+      q = q < 0 ? 0 : (q >= n ? n - 1 : q);
+    }
+    I[d] = q;
+  }
+  return __ldg(uc + cell_index(g, I[0], I[1], D == 3 ? I[2] : 0));
+}
+
+// Momentum flux through the lower j-face of the u_c control volume:
+//   F = a*phi - nu*(p0 - m1),  a = a2/2,
+// where (m2, m1, p0, p1) = u_c at I-2e_j, I-e_j, I, I+e_j and a2 = u_j[I] + u_j[I-e_c].
+// phi is the kappa = 1/3 upwind-biased face value limited by Koren's limiter
+// (third-order convection with implicit LES, Section 2): with upwind/centre/
+// downwind (u, c, d) taken on the side a comes from, phi = c + psi(r)(d - c)/2,
+// r = (c - u)/(d - c), psi = max(0, min(2r, (2+r)/3, 2)).  Written without the
+// division: for (c-u)(d-c) > 0, psi*(d-c) = sign(d-c) min(2|c-u|, (2|d-c|+|c-u|)/3,
+// 2|d-c|); otherwise 0.
+__device__ __forceinline__ float mom_flux(float m2, float m1, float p0, float p1, float a2, float nu,
+                                          bool advect) {
+  float diff = nu * (p0 - m1);
+  if (!advect) return -diff;
+  const bool pos = a2 > 0.f;
+  const float uu = pos ? m2 : p1;
+  const float cc = pos ? m1 : p0;
+  const float dd = pos ? p0 : m1;
+  const float dD = dd - cc, dU = cc - uu;
+  const float ad = fabsf(dD), au = fabsf(dU);
+  const float t = fminf(fminf(2.f * au, (2.f * ad + au) * (1.f / 3.f)), 2.f * ad);
+  const float lim = (dU * dD > 0.f) ? copysignf(t, dD) : 0.f;
+  const float phi = fmaf(0.5f, lim, cc);
+  return fmaf(0.5f * a2, phi, -diff);
+}
+
+// ---------------------------------------------------------------------------
+// Immersed body: analytic signed distance and outward unit normal (Section 2: the
+// geometry is a signed-distance function; normals are its gradient).
+struct Body {
+  int kind;          // 0 none, 1 circle/sphere, 2 torus (3-D)
+  double c[3];
+  double r1, r2;     // radius; torus tube radius
+  double eps;        // BDIM kernel half-width
+};
+
+template <int D>
+__device__ __forceinline__ double body_sdf(const Body& b, const double* x, double* n) {
+  n[0] = n[1] = n[2] = 0.0;
+  if (b.kind == 1) {
+    double r2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) r2 += (x[d] - b.c[d]) * (x[d] - b.c[d]);
+    double r = sqrt(r2);
+    if (r > 0.0) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) n[d] = (x[d] - b.c[d]) / r;
+    }
+    return r - b.r1;
+  }
+  if (b.kind == 2 && D == 3) {
+    double a = x[0] - b.c[0], bb = x[1] - b.c[1], cc = x[2] - b.c[2];
+    double rho = sqrt(bb * bb + cc * cc);
+    double q1 = rho - b.r1;
+    double dq = sqrt(a * a + q1 * q1);
+    if (dq > 0.0) {
+      double e1 = rho > 0.0 ? bb / rho : 0.0, e2 = rho > 0.0 ? cc / rho : 0.0;
+      n[0] = a / dq;
+      n[1] = q1 / dq * e1;
+      n[2] = q1 / dq * e2;
+    }
+    return dq - b.r2;
+  }
+  return 1e30;
+}
+
+// Moments of the cosine kernel K(s) = (1 + cos(pi s))/2 on [-1, 1] (BDIM, Section 2;
+// Weymouth & Yue 2011): K0(s) = int_{-1}^s K  (a CDF, kept in [0, 1]) and
+// K1(s) = int_s^1 t K(t) dt.  Evaluated in FP64: near s = -1, K0 ~ pi^2 (s+1)^3/12
+// comes out of a cancellation that FP32 cannot resolve.
+__device__ __forceinline__ double kernel_K0(double s) {
+  if (s <= -1.0) return 0.0;
+  if (s >= 1.0) return 1.0;
+  double v = 0.5 + 0.5 * s + sinpi(s) * (0.5 / 3.141592653589793);
+  return v < 0.0 ? 0.0 : (v > 1.0 ? 1.0 : v);
+}
+__device__ __forceinline__ double kernel_K1(double s) {
+  if (s <= -1.0 || s >= 1.0) return 0.0;
+  const double ip = 1.0 / 3.141592653589793;
+  return 0.25 * (1.0 - s * s) - (s * sinpi(s) + (1.0 + cospi(s)) * ip) * (0.5 * ip);
+}
+
+// ---------------------------------------------------------------------------
+// Device-resident scalars of one sim (dt and the convergence bookkeeping live on
+// the device so a step never waits for the host).
+struct DevState {
+  double dt;              // dt of the next step
+  double time;            // simulated time
+  long long steps;
+  unsigned norm_bits;     // running max |residual| (float bits; non-negative floats order as uints)
+  unsigned cfl_bits;      // running max out-flux (float bits)
+  int iter;               // V-cycles of the projection in progress
+  int cond;               // 1 while the projection loop continues
+  float res_x;            // last residual in x = p*w*dt units
+  int last_iters[2];      // V-cycles of the two projections of the last step
+  float last_res[2];
+  long long total_vcycles;
+  float worst_res;
+  int status;             // bit 0: non-finite seen; bit 1: max_vcycles hit
+  int proj_index;         // 0 / 1: which projection of the step is running
+};
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned* addr, float v) {
+  // |v| of a finite or non-finite float: NaN and Inf order above every finite value
+  atomicMax(addr, __float_as_uint(fabsf(v)));
+}
+
+// Block-wide maximum of non-negative float bit patterns (NaN and Inf order above
+// every finite value, so a non-finite residual is never hidden).
+template <int NT>
+__device__ __forceinline__ unsigned block_max_bits(unsigned v, unsigned* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < NT / 32) ? sh[l] : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;  // valid in thread 0
+}
+
+}  // namespace wl

@@ -1,0 +1,90 @@
+// Internal launch interface between the host runtime (wl_api.cu) and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include "wl_dev.cuh"
+
+namespace wl {
+
+struct StageArgs {
+  const float* u[3];    // velocity whose convection-diffusion residual is taken
+  const float* u0[3];   // start-of-step velocity
+  const float* mu0[3];  // BDIM zeroth moment on updated faces (= Poisson coefficient there)
+  float* out[3];
+  Grid g;
+  const double* dt;     // device scalar
+  float nu;
+  int stage;            // 1 or 2
+  int advect;
+};
+
+// residual / divergence / restriction modes of k_residual
+enum { RES_RESIDUAL = 0, RES_DIVERGENCE = 1, RES_RESTRICT = 2, RES_DIV_ONLY = 3 };
+
+struct ResArgs {
+  const float* u[3];   // RES_DIVERGENCE / RES_DIV_ONLY: velocity
+  const float* x;      // current unknown (RES_RESIDUAL / RES_DIVERGENCE)
+  const float* L[3];   // face coefficients of this level
+  float* z;            // right-hand side of this level (written by the divergence modes)
+  float* zc;           // restricted residual for the next level (may be null)
+  Grid g;
+  int cn[3];           // next level's dims
+  const double* dt;    // divergence modes: z = div u / (w dt)
+  float w;
+  DevState* st;        // receives max |residual|
+  int mode;
+};
+
+struct SweepArgs {
+  const float* x_in;   // current iterate, or null for zero
+  const float* xc;     // coarse correction added by piecewise-constant prolongation, or null
+  const float* z;
+  const float* L[3];
+  float* x_out;
+  Grid g;
+  int cn[3];
+};
+
+struct CoarseArgs {
+  const float* z;
+  const float* L[3];
+  float* x;
+  Grid g;
+  double* work;        // 5 * g.nc doubles
+  int maxit;
+  double rtol;
+};
+
+struct CorrArgs {
+  const float* u_in[3];
+  float* u_out[3];
+  const float* x;      // pressure p
+  const float* L[3];
+  Grid g;
+  const double* dt;
+  float w;
+  int cfl;             // also accumulate the CFL out-flux maximum
+  DevState* st;
+};
+
+int launch_stage(int D, const StageArgs& a, const Body& b, cudaStream_t s);
+int launch_residual(int D, const ResArgs& a, cudaStream_t s);
+int launch_sweep(int D, const SweepArgs& a, cudaStream_t s);
+int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s);
+int launch_correct(int D, const CorrArgs& a, cudaStream_t s);
+int launch_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, int first, int proj, float w,
+                  double tol, int maxit, cudaStream_t s);
+int launch_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s);
+int launch_measure(int D, const Grid& g, const Body& b, float* const* L, cudaStream_t s);
+int launch_coarsen(int D, const Grid& fine, const float* const* Lf, const Grid& coarse, float* const* Lc,
+                   cudaStream_t s);
+int launch_set_ic(int D, const Grid& g, int kind, double amp, float* const* u, cudaStream_t s);
+int launch_cfl_only(int D, const Grid& g, const float* const* u, DevState* st, cudaStream_t s);
+int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* const* L, double* partials,
+                  int npart, double* out, cudaStream_t s);
+
+}  // namespace wl
+
+namespace wl {
+int launch_set_dt_from_cfl(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s);
+int launch_fix_bfaces(int D, const Grid& g, float* const* u, cudaStream_t s);
+}  // namespace wl

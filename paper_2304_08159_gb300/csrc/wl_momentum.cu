@@ -1,0 +1,267 @@
+// Momentum stage kernels: convdiff! fused with BDIM! and BC! (Table 2).
+//
+// One Heun stage (Section 2: explicit adaptive time stepping; the Heun form is this
+// library's reading):
+//   stage 1: f = u0 + dt r(u0),  u' = mu0 f + mu1 . grad f
+//   stage 2: f = u0 + dt r(u'),  u  = (u' + mu0 f + mu1 . grad f) / 2
+// with r(u)_c[I] = sum_j F_cj[I] - F_cj[I+e_j] the finite-volume convection-diffusion
+// residual and (mu0, mu1) the BDIM moments (Section 2, Weymouth & Yue 2011).  The
+// body velocity is zero.  k_stage computes everything but the mu1 term, which is
+// non-zero only in the thin band |d| < eps around the body and is added by
+// k_bdim_band over the body's bounding box.
+#include "wl_dev.cuh"
+#include "wl_kernels.h"
+
+namespace wl {
+
+constexpr int ST_TX = 32, ST_TY = 8, ST_TZ = 32;
+constexpr int ST_HX = ST_TX + 4, ST_HY = ST_TY + 4;
+
+// Tile of ST_TX x ST_TY columns marching upward through ST_TZ planes.  The velocity
+// of planes k-1..k+2 (with a 2-cell in-plane halo) sits in a 4-plane shared ring.
+// Each thread computes the lower x-, y- and z-face fluxes of its cell; the upper x/y
+// fluxes come from the neighbour through shared memory, the upper z flux is carried
+// in registers to the next plane, so every face flux is evaluated once.
+template <int D>
+__global__ void __launch_bounds__(256) k_stage(StageArgs a) {
+  constexpr int NP = (D == 3) ? 4 : 1;
+  __shared__ float s_u[D][NP][ST_HY][ST_HX];
+  __shared__ float s_fx[D][ST_TY][ST_TX + 1];
+  __shared__ float s_fy[D][ST_TY + 1][ST_TX];
+  const Grid& g = a.g;
+  const int tid = threadIdx.x, tx = tid % ST_TX, ty = tid / ST_TX;
+  const int i0 = blockIdx.x * ST_TX, j0 = blockIdx.y * ST_TY;
+  const int k0 = (D == 3) ? blockIdx.z * ST_TZ : 0;
+  const int k1 = (D == 3) ? min(k0 + ST_TZ, g.n[2]) : 1;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = (i < g.n[0]) && (j < g.n[1]);
+  const float dt = (float)(*a.dt);
+  const bool adv = a.advect != 0;
+  const float nu = a.nu;
+
+  auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
+  auto S = [&](int c, int sl, int jj, int ii) -> float { return s_u[c][sl][jj + 2][ii + 2]; };
+
+  auto load_plane = [&](int kk) {
+    const int sl = slot(kk);
+    const bool inner = (i0 >= 2) && (i0 + ST_TX + 2 <= g.n[0]) && (j0 >= 2) && (j0 + ST_TY + 2 <= g.n[1]) &&
+                       (D == 2 || (kk >= 0 && kk < g.n[2]));
+    for (int e = tid; e < ST_HY * ST_HX; e += 256) {
+      const int row = e / ST_HX, col = e - row * ST_HX;
+      const int gi = i0 - 2 + col, gj = j0 - 2 + row;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float v;
+        if (inner)
+          v = __ldg(a.u[c] + cell_index(g, gi, gj, D == 3 ? kk : 0));
+        else
+          v = load_u_bc<D>(a.u[c], c, g, gi, gj, kk);
+        s_u[c][sl][row][col] = v;
+      }
+    }
+  };
+
+  // lower x-face flux of the u_c control volume at tile position (ii, jj) in plane slot sl
+  // (slm: slot of the plane below, for the advecting velocity of c = z)
+  auto flux_x = [&](int c, int ii, int jj, int sl, int slm) -> float {
+    const float a2 = S(0, sl, jj, ii) + (c == 0 ? S(0, sl, jj, ii - 1) : (c == 1 ? S(0, sl, jj - 1, ii) : S(0, slm, jj, ii)));
+    return mom_flux(S(c, sl, jj, ii - 2), S(c, sl, jj, ii - 1), S(c, sl, jj, ii), S(c, sl, jj, ii + 1), a2, nu, adv);
+  };
+  auto flux_y = [&](int c, int ii, int jj, int sl, int slm) -> float {
+    const float a2 = S(1, sl, jj, ii) + (c == 0 ? S(1, sl, jj, ii - 1) : (c == 1 ? S(1, sl, jj - 1, ii) : S(1, slm, jj, ii)));
+    return mom_flux(S(c, sl, jj - 2, ii), S(c, sl, jj - 1, ii), S(c, sl, jj, ii), S(c, sl, jj + 1, ii), a2, nu, adv);
+  };
+  // lower z-face flux at plane kf
+  auto flux_z = [&](int c, int ii, int jj, int kf) -> float {
+    const int s2 = slot(kf - 2), s1 = slot(kf - 1), s0 = slot(kf), sp = slot(kf + 1);
+    const float a2 = S(2 % D, s0, jj, ii) +
+                     (c == 0 ? S(2 % D, s0, jj, ii - 1) : (c == 1 ? S(2 % D, s0, jj - 1, ii) : S(2 % D, s1, jj, ii)));
+    return mom_flux(S(c, s2, jj, ii), S(c, s1, jj, ii), S(c, s0, jj, ii), S(c, sp, jj, ii), a2, nu, adv);
+  };
+
+  float fzl[3] = {0.f, 0.f, 0.f};
+  if (D == 3) {
+    load_plane(k0 - 2);
+    load_plane(k0 - 1);
+    load_plane(k0);
+    load_plane(k0 + 1);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < D; ++c) fzl[c] = flux_z(c, tx, ty, k0);
+    __syncthreads();
+  }
+
+  for (int k = k0; k < k1; ++k) {
+    load_plane(D == 3 ? k + 2 : 0);
+    __syncthreads();
+    const int sk = slot(k), skm = slot(k - 1);
+    float fzu[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      s_fx[c][ty][tx] = flux_x(c, tx, ty, sk, skm);
+      s_fy[c][ty][tx] = flux_y(c, tx, ty, sk, skm);
+      if (D == 3) fzu[c] = flux_z(c, tx, ty, k + 1);
+    }
+    // fluxes through the upper edge faces of the tile
+    if (tid < D * ST_TY) {
+      const int c = tid / ST_TY, row = tid - c * ST_TY;
+      s_fx[c][row][ST_TX] = flux_x(c, ST_TX, row, sk, skm);
+    } else if (tid < D * ST_TY + D * ST_TX) {
+      const int t = tid - D * ST_TY;
+      const int c = t / ST_TX, col = t - c * ST_TX;
+      s_fy[c][ST_TY][col] = flux_y(c, col, ST_TY, sk, skm);
+    }
+    __syncthreads();
+    if (own) {
+      const long long q = cell_index(g, i, j, k);
+      const int I[3] = {i, j, k};
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        float r = (s_fx[c][ty][tx] - s_fx[c][ty][tx + 1]) + (s_fy[c][ty][tx] - s_fy[c][ty + 1][tx]);
+        if (D == 3) r += fzl[c] - fzu[c];
+        const bool upd = is_per(g, c) || I[c] >= 1;
+        float o;
+        if (!upd) {
+          o = g.U[c];
+        } else {
+          const float uc = S(c, sk, ty, tx);
+          const float u0 = (a.stage == 1) ? uc : __ldg(a.u0[c] + q);
+          const float f = fmaf(dt, r, u0);
+          const float m = __ldg(a.mu0[c] + q);
+          o = (a.stage == 1) ? m * f : 0.5f * (uc + m * f);
+        }
+        a.out[c][q] = o;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < D; ++c) fzl[c] = fzu[c];
+  }
+}
+
+// convdiff residual r_c at face (i,j,k) (which must be an updated face), read
+// straight from global memory with the BC mapping; used for the few band faces.
+template <int D>
+__device__ float conv_residual(const float* const* u, int c, const Grid& g, int i, int j, int k, float nu,
+                               bool adv) {
+  auto U = [&](int comp, int ii, int jj, int kk) { return load_u_bc<D>(u[comp], comp, g, ii, jj, kk); };
+  float r = 0.f;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      int J[3] = {i, j, k};
+      J[d] += side;
+      int e[3] = {0, 0, 0};
+      e[d] = 1;
+      int ec[3] = {0, 0, 0};
+      ec[c] = 1;
+      const float a2 = U(d, J[0], J[1], J[2]) + U(d, J[0] - ec[0], J[1] - ec[1], J[2] - ec[2]);
+      const float F = mom_flux(U(c, J[0] - 2 * e[0], J[1] - 2 * e[1], J[2] - 2 * e[2]),
+                               U(c, J[0] - e[0], J[1] - e[1], J[2] - e[2]), U(c, J[0], J[1], J[2]),
+                               U(c, J[0] + e[0], J[1] + e[1], J[2] + e[2]), a2, nu, adv);
+      r += side ? -F : F;
+    }
+  }
+  return r;
+}
+
+// f_c = u0 + dt r(u) at a face that may lie outside the interior: the same BC as the
+// velocity gives its value there (Dirichlet faces carry U_c; others map inward).
+template <int D>
+__device__ float f_at(const StageArgs& a, int c, int i, int j, int k, float dt) {
+  const Grid& g = a.g;
+  int I[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    int q = I[d];
+    const int n = g.n[d];
+    if (is_per(g, d)) {
+      q = (q < 0) ? q + n : ((q >= n) ? q - n : q);
+    } else {
+      if (d == c && (q <= 0 || q >= n)) return g.U[c];
+      q = q < 0 ? 0 : (q >= n ? n - 1 : q);
+    }
+    I[d] = q;
+  }
+  const float r = conv_residual<D>(a.u, c, g, I[0], I[1], I[2], a.nu, a.advect != 0);
+  return fmaf(dt, r, __ldg(a.u0[c] + cell_index(g, I[0], I[1], I[2])));
+}
+
+// mu1 term of BDIM over the body's bounding box: out_c[I] += s * sum_j mu1_j (f[I+e_j]
+// - f[I-e_j]) / 2 with mu1 = eps K1(d/eps) n at the face (s = 1 in stage 1, 1/2 in
+// stage 2).  mu1 vanishes for |d| >= eps, so only band faces do work.
+template <int D>
+__global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0, int lo1, int lo2, int bx,
+                                                    int by, int bz) {
+  const long long nbox = (long long)bx * by * bz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nbox * D) return;
+  const int c = (int)(t / nbox);
+  long long rem = t - (long long)c * nbox;
+  const int i = lo0 + (int)(rem % bx);
+  rem /= bx;
+  const int j = lo1 + (int)(rem % by);
+  const int k = lo2 + (int)(rem / by);
+  const Grid& g = a.g;
+  const int I[3] = {i, j, k};
+  if (!(is_per(g, c) || I[c] >= 1)) return;
+  double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+  x[c] -= 0.5;
+  double nrm[3];
+  const double d = body_sdf<D>(b, x, nrm);
+  if (!(fabs(d) < b.eps)) return;
+  const double k1 = b.eps * kernel_K1(d / b.eps);
+  const float dt = (float)(*a.dt);
+  float acc = 0.f;
+#pragma unroll
+  for (int jd = 0; jd < D; ++jd) {
+    int P[3] = {i, j, k}, M[3] = {i, j, k};
+    P[jd] += 1;
+    M[jd] -= 1;
+    const float fp = f_at<D>(a, c, P[0], P[1], P[2], dt);
+    const float fm = f_at<D>(a, c, M[0], M[1], M[2], dt);
+    acc += (float)(k1 * nrm[jd]) * 0.5f * (fp - fm);
+  }
+  const long long q = cell_index(g, i, j, k);
+  a.out[c][q] += (a.stage == 1 ? 1.f : 0.5f) * acc;
+}
+
+// ---------------------------------------------------------------------------
+int launch_stage(int D, const StageArgs& a, const Body& b, cudaStream_t s) {
+  const Grid& g = a.g;
+  dim3 blk(256);
+  if (D == 3) {
+    dim3 grd((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_TY - 1) / ST_TY, (g.n[2] + ST_TZ - 1) / ST_TZ);
+    k_stage<3><<<grd, blk, 0, s>>>(a);
+  } else {
+    dim3 grd((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_TY - 1) / ST_TY, 1);
+    k_stage<2><<<grd, blk, 0, s>>>(a);
+  }
+  if (b.kind != 0) {
+    // bounding box of the faces within eps of the surface
+    double ext = b.r1 + b.eps + 2.0;
+    if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 2.0;
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+      if (d >= D) {
+        lo[d] = 0;
+        hi[d] = 1;
+        continue;
+      }
+      double l = b.c[d] - ext, h = b.c[d] + ext;
+      lo[d] = (int)fmax(0.0, floor(l));
+      hi[d] = (int)fmin((double)g.n[d], ceil(h) + 1.0);
+      if (hi[d] <= lo[d]) return 0;  // body outside the grid: no band
+    }
+    const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
+    const long long n = (long long)bx * by * bz * D;
+    const int nb = (int)((n + 255) / 256);
+    if (D == 3)
+      k_bdim_band<3><<<nb, 256, 0, s>>>(a, b, lo[0], lo[1], lo[2], bx, by, bz);
+    else
+      k_bdim_band<2><<<nb, 256, 0, s>>>(a, b, lo[0], lo[1], lo[2], bx, by, bz);
+  }
+  return 0;
+}
+
+}  // namespace wl

@@ -1,0 +1,846 @@
+// Pressure projection (project!, Table 2) and the geometric-multigrid Poisson solve
+// on the BDIM-modified matrix (Section 2; Lauber 2022; Weymouth 2022), the CFL time
+// step (CFL!, Table 2), the body measure and the pressure force.
+//
+// Poisson operator with face coefficients L (Section 2):
+//   (A x)[I] = sum_c L_c[I+e_c] (x[I+e_c] - x[I]) + L_c[I] (x[I-e_c] - x[I]),
+// L = mu0 at faces and 0 on non-periodic boundary faces.  The solver works on the
+// pressure itself: A p = div(u)/(w dt), which is the system A x = div(u) with
+// x = p w dt scaled by 1/(w dt); the tolerance test converts back to x units.
+//
+// Multigrid cycle V(0, post): residual + restriction (sum of the 2^D children) in one
+// pass, recursive coarse levels with zero initial guess, coarse face coefficient =
+// half the sum of the 2^(D-1) fine faces it covers, the coarsest level solved by
+// FP64 conjugate gradients, piecewise-constant prolongation fused into the first
+// smoothing sweep, red-black Gauss-Seidel sweeps (red: i+j+k even, first).  Cells
+// whose row is zero (all faces blocked by the body) carry x = 0.
+#include "wl_dev.cuh"
+#include "wl_kernels.h"
+
+namespace wl {
+
+__device__ __forceinline__ void cell_coords(int D, int blk_y, int tid, int& tx, int& ty, int& tz) {
+  tx = tid & 31;
+  if (D == 3) {
+    ty = (tid >> 5) & 3;
+    tz = tid >> 7;
+  } else {
+    ty = tid >> 5;
+    tz = 0;
+  }
+  (void)blk_y;
+}
+
+// Upper/lower neighbour of linear cell q along c (wrapping periodic sides); `has` is
+// false on a non-periodic side, where the face coefficient is zero.
+__device__ __forceinline__ long long nb_up(const Grid& g, int c, int Ic, long long q, long long stc, bool& has) {
+  if (Ic + 1 < g.n[c]) {
+    has = true;
+    return q + stc;
+  }
+  has = is_per(g, c);
+  return has ? q - (long long)(g.n[c] - 1) * stc : q;
+}
+__device__ __forceinline__ long long nb_dn(const Grid& g, int c, int Ic, long long q, long long stc) {
+  if (Ic > 0) return q - stc;
+  return is_per(g, c) ? q + (long long)(g.n[c] - 1) * stc : q;
+}
+
+// ---------------------------------------------------------------------------
+// k_residual: one pass over a level computing (per mode)
+//   RES_DIVERGENCE: z = div(u)/(w dt) (stored), r = z - A x, max|r|, restrict r
+//   RES_RESIDUAL:   r = z - A x, max|r|, restrict r
+//   RES_RESTRICT:   restrict z (coarse levels whose iterate is still zero)
+//   RES_DIV_ONLY:   z = div(u) (raw, for inspection)
+// Block = 32 x 4 x 2 cells (3-D) or 32 x 8 (2-D), so each block holds whole 2^D
+// families of children for the restriction.
+template <int D>
+__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
+  __shared__ float s_r[256];
+  __shared__ unsigned s_m[8];
+  const Grid& g = a.g;
+  const int tid = threadIdx.x;
+  int tx, ty, tz;
+  cell_coords(D, 0, tid, tx, ty, tz);
+  const int i = blockIdx.x * 32 + tx;
+  const int j = blockIdx.y * (D == 3 ? 4 : 8) + ty;
+  const int k = (D == 3) ? blockIdx.z * 2 + tz : 0;
+  const bool in = i < g.n[0] && j < g.n[1] && k < g.n[2];
+  float v = 0.f;
+  if (in) {
+    const long long q = cell_index(g, i, j, k);
+    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+    const int I[3] = {i, j, k};
+    float z;
+    if (a.mode == RES_DIVERGENCE || a.mode == RES_DIV_ONLY) {
+      float div = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        bool has;
+        const long long qu = nb_up(g, c, I[c], q, st[c], has);
+        const float up = (I[c] + 1 < g.n[c] || has) ? __ldg(a.u[c] + qu) : g.U[c];
+        div += up - __ldg(a.u[c] + q);
+      }
+      z = (a.mode == RES_DIV_ONLY) ? div : (float)((double)div / ((double)a.w * *a.dt));
+      a.z[q] = z;
+    } else {
+      z = a.z[q];
+    }
+    if (a.mode == RES_RESTRICT) {
+      v = z;
+    } else if (a.mode != RES_DIV_ONLY) {
+      const float x0 = __ldg(a.x + q);
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < D; ++c) {
+        bool has;
+        const long long qu = nb_up(g, c, I[c], q, st[c], has);
+        const long long qm = nb_dn(g, c, I[c], q, st[c]);
+        const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
+        const float Ll = __ldg(a.L[c] + q);
+        acc += Lu * (__ldg(a.x + qu) - x0) + Ll * (__ldg(a.x + qm) - x0);
+      }
+      v = z - acc;
+    }
+  }
+  if (a.mode == RES_RESIDUAL || a.mode == RES_DIVERGENCE) {
+    const unsigned m = block_max_bits<256>(__float_as_uint(fabsf(v)), s_m);
+    if (tid == 0 && m) atomicMax(&a.st->norm_bits, m);
+  }
+  if (a.zc) {
+    const float w2 = v + __shfl_xor_sync(0xffffffffu, v, 1);
+    s_r[tid] = w2;
+    __syncthreads();
+    if (D == 3) {
+      if (tid < 32) {
+        const int cx = tid & 15, cy = tid >> 4;
+        const float sum = (s_r[2 * cx + 32 * (2 * cy)] + s_r[2 * cx + 32 * (2 * cy + 1)]) +
+                          (s_r[2 * cx + 32 * (2 * cy + 4)] + s_r[2 * cx + 32 * (2 * cy + 5)]);
+        const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 2 + cy, K = blockIdx.z;
+        if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
+          a.zc[(long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K)] = sum;
+      }
+    } else {
+      if (tid < 64) {
+        const int cx = tid & 15, cy = tid >> 4;
+        const float sum = s_r[2 * cx + 32 * (2 * cy)] + s_r[2 * cx + 32 * (2 * cy + 1)];
+        const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 4 + cy;
+        if (I < a.cn[0] && J < a.cn[1]) a.zc[(long long)I + (long long)a.cn[0] * J] = sum;
+      }
+    }
+  }
+}
+
+int launch_residual(int D, const ResArgs& a, cudaStream_t s) {
+  const Grid& g = a.g;
+  if (D == 3) {
+    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + 1) / 2);
+    k_residual<3><<<grd, 256, 0, s>>>(a);
+  } else {
+    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
+    k_residual<2><<<grd, 256, 0, s>>>(a);
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// k_sweep: one red-black Gauss-Seidel sweep (all red cells, then all black cells),
+// out of place (x_in -> x_out), with the prolongation of a coarse correction fused
+// into the read of x_in.  A tile of 64 x 8 cells marches up through SW_TZ planes;
+// planes k-1..k+2 of the iterate (2-cell in-plane halo) sit in a 4-plane shared ring.
+// At plane k: red cells of plane k+1 are relaxed on the tile plus a 1-cell halo
+// (using old black values), then black cells of plane k on the tile (using the new
+// red values), and plane k is written.  Halo red cells are recomputed by every tile
+// that needs them, from the same inputs, so tiles never exchange data.
+constexpr int SW_TX = 64, SW_TY = 8, SW_TZ = 32;
+constexpr int SW_HX = SW_TX + 4, SW_HY = SW_TY + 4;
+
+template <int D>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+  constexpr int NP = (D == 3) ? 4 : 1;
+  __shared__ float s_x[NP][SW_HY][SW_HX];
+  const Grid& g = a.g;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int i0 = blockIdx.x * SW_TX, j0 = blockIdx.y * SW_TY;
+  const int k0 = (D == 3) ? blockIdx.z * SW_TZ : 0;
+  const int k1 = (D == 3) ? min(k0 + SW_TZ, g.n[2]) : 1;
+  const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+
+  auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
+  auto map = [&](int* I) -> bool {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int n = g.n[d];
+      if (I[d] < 0 || I[d] >= n) {
+        if (!is_per(g, d)) return false;
+        I[d] = I[d] < 0 ? I[d] + n : I[d] - n;
+      }
+    }
+    return true;
+  };
+  auto load_plane = [&](int kk) {
+    const int sl = slot(kk);
+    for (int e = tid; e < SW_HY * SW_HX; e += 256) {
+      const int row = e / SW_HX, col = e - row * SW_HX;
+      int I[3] = {i0 - 2 + col, j0 - 2 + row, D == 3 ? kk : 0};
+      float v = 0.f;
+      if (map(I)) {
+        const long long q = cell_index(g, I[0], I[1], I[2]);
+        if (a.x_in) v = __ldg(a.x_in + q);
+        if (a.xc)
+          v += __ldg(a.xc + (long long)(I[0] >> 1) +
+                     (long long)a.cn[0] * ((long long)(I[1] >> 1) + (long long)a.cn[1] * (D == 3 ? (I[2] >> 1) : 0)));
+      }
+      s_x[sl][row][col] = v;
+    }
+  };
+  // Gauss-Seidel value of the cell at tile position (ii, jj) of plane kk from the
+  // shared neighbours; false when the cell lies outside a non-periodic side.
+  auto relax = [&](int ii, int jj, int kk, float& out) -> bool {
+    int I[3] = {i0 + ii, j0 + jj, D == 3 ? kk : 0};
+    if (!map(I)) return false;
+    const long long q = cell_index(g, I[0], I[1], I[2]);
+    const int sl = slot(kk);
+    float sum = 0.f, dg = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
+      const float Ll = __ldg(a.L[c] + q);
+      float xu, xd;
+      if (c == 0) {
+        xu = s_x[sl][jj + 2][ii + 3];
+        xd = s_x[sl][jj + 2][ii + 1];
+      } else if (c == 1) {
+        xu = s_x[sl][jj + 3][ii + 2];
+        xd = s_x[sl][jj + 1][ii + 2];
+      } else {
+        xu = s_x[slot(kk + 1)][jj + 2][ii + 2];
+        xd = s_x[slot(kk - 1)][jj + 2][ii + 2];
+      }
+      sum += Lu * xu + Ll * xd;
+      dg += Lu + Ll;
+    }
+    out = (dg > 0.f) ? (sum - __ldg(a.z + q)) / dg : 0.f;
+    return true;
+  };
+  auto red_phase = [&](int kr) {
+    const int sl = slot(kr);
+    constexpr int RW = (SW_TX + 2) / 2;
+    for (int e = tid; e < (SW_TY + 2) * RW; e += 256) {
+      const int row = e / RW, m = e - row * RW;
+      const int jj = row - 1;
+      const int o = (i0 - 1 + j0 + jj + kr) & 1;
+      const int ii = -1 + 2 * m + o;
+      float v;
+      if (relax(ii, jj, kr, v)) s_x[sl][jj + 2][ii + 2] = v;
+    }
+  };
+
+  if (D == 3) {
+    load_plane(k0 - 2);
+    load_plane(k0 - 1);
+    load_plane(k0);
+    load_plane(k0 + 1);
+    __syncthreads();
+    red_phase(k0 - 1);
+    red_phase(k0);
+    __syncthreads();
+  }
+  for (int k = k0; k < k1; ++k) {
+    if (D == 3) {
+      load_plane(k + 2);
+      __syncthreads();
+      red_phase(k + 1);
+    } else {
+      load_plane(0);
+      __syncthreads();
+      red_phase(0);
+    }
+    __syncthreads();
+    // black cells of plane k on the tile, one per thread
+    const int P = (i0 + j0 + ty + k) & 1;  // parity of cell 2*tx
+    const int ib = 2 * tx + (P ^ 1);
+    const int gj = j0 + ty;
+    float vb = 0.f;
+    bool okb = false;
+    if (i0 + ib < g.n[0] && gj < g.n[1]) okb = relax(ib, ty, k, vb);
+    const int ir = 2 * tx + P;
+    const float vr = s_x[slot(k)][ty + 2][ir + 2];
+    const int gi = i0 + 2 * tx;
+    if (gj < g.n[1]) {
+      const long long q = cell_index(g, gi, gj, D == 3 ? k : 0);
+      const float v0 = P ? vb : vr, v1 = P ? vr : vb;
+      if (gi + 1 < g.n[0] && ((g.n[0] & 1) == 0)) {
+        reinterpret_cast<float2*>(a.x_out + q)[0] = make_float2(v0, v1);
+      } else {
+        if (gi < g.n[0]) a.x_out[q] = v0;
+        if (gi + 1 < g.n[0]) a.x_out[q + 1] = v1;
+      }
+    }
+    (void)okb;
+    __syncthreads();
+  }
+}
+
+int launch_sweep(int D, const SweepArgs& a, cudaStream_t s) {
+  const Grid& g = a.g;
+  if (D == 3) {
+    dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, (g.n[2] + SW_TZ - 1) / SW_TZ);
+    k_sweep<3><<<grd, 256, 0, s>>>(a);
+  } else {
+    dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, 1);
+    k_sweep<2><<<grd, 256, 0, s>>>(a);
+  }
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Coarsest level: Jacobi-preconditioned conjugate gradients in FP64 by one block,
+// on B = -A (positive semi-definite) with the right-hand side projected onto the
+// range (mean over active cells removed) and the solution returned with zero mean.
+__device__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+    sh[8] = t;
+  }
+  __syncthreads();
+  return sh[8];
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_coarse_cg(CoarseArgs a) {
+  __shared__ double sh[9];
+  const Grid& g = a.g;
+  const long long nc = g.nc;
+  double* xr = a.work;
+  double* rr = a.work + nc;
+  double* pr = a.work + 2 * nc;
+  double* ap = a.work + 3 * nc;
+  double* dgv = a.work + 4 * nc;
+  const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+  auto coords = [&](long long q, int* I) {
+    I[0] = (int)(q % g.n[0]);
+    long long t = q / g.n[0];
+    I[1] = (int)(t % g.n[1]);
+    I[2] = (int)(t / g.n[1]);
+  };
+  // B v at cell q (B = -A)
+  auto applyB = [&](const double* v, long long q) -> double {
+    int I[3];
+    coords(q, I);
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      const long long qm = nb_dn(g, c, I[c], q, st[c]);
+      const double Lu = has ? (double)a.L[c][qu] : 0.0;
+      const double Ll = (double)a.L[c][q];
+      s += Lu * (v[q] - v[qu]) + Ll * (v[q] - v[qm]);
+    }
+    return s;
+  };
+  double bs = 0.0, cnt = 0.0;
+  for (long long q = threadIdx.x; q < nc; q += blockDim.x) {
+    int I[3];
+    coords(q, I);
+    double dg = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      dg += (has ? (double)a.L[c][qu] : 0.0) + (double)a.L[c][q];
+    }
+    dgv[q] = dg;
+    xr[q] = 0.0;
+    if (dg > 0.0) {
+      bs += (double)a.z[q];
+      cnt += 1.0;
+    }
+  }
+  bs = block_sum_d(bs, sh);
+  cnt = block_sum_d(cnt, sh);
+  const double mean = cnt > 0.0 ? bs / cnt : 0.0;
+  double rz = 0.0, bb = 0.0;
+  for (long long q = threadIdx.x; q < nc; q += blockDim.x) {
+    if (dgv[q] > 0.0) {
+      const double r = -((double)a.z[q] - mean);  // b - B*0 with b = -(z - mean)
+      rr[q] = r;
+      const double zz = r / dgv[q];
+      pr[q] = zz;
+      rz += r * zz;
+      bb += r * r;
+    } else {
+      rr[q] = 0.0;
+      pr[q] = 0.0;
+    }
+  }
+  rz = block_sum_d(rz, sh);
+  bb = block_sum_d(bb, sh);
+  if (bb > 0.0) {
+    for (int it = 0; it < a.maxit; ++it) {
+      __syncthreads();
+      double pap = 0.0;
+      for (long long q = threadIdx.x; q < nc; q += blockDim.x) {
+        const double s = (dgv[q] > 0.0) ? applyB(pr, q) : 0.0;
+        ap[q] = s;
+        pap += pr[q] * s;
+      }
+      pap = block_sum_d(pap, sh);
+      if (!(pap > 0.0)) break;
+      const double alpha = rz / pap;
+      double r2 = 0.0;
+      for (long long q = threadIdx.x; q < nc; q += blockDim.x) {
+        xr[q] += alpha * pr[q];
+        rr[q] -= alpha * ap[q];
+        r2 += rr[q] * rr[q];
+      }
+      r2 = block_sum_d(r2, sh);
+      if (r2 <= a.rtol * a.rtol * bb) break;
+      double rz2 = 0.0;
+      for (long long q = threadIdx.x; q < nc; q += blockDim.x) {
+        const double zz = (dgv[q] > 0.0) ? rr[q] / dgv[q] : 0.0;
+        ap[q] = zz;
+        rz2 += rr[q] * zz;
+      }
+      rz2 = block_sum_d(rz2, sh);
+      const double beta = rz2 / rz;
+      rz = rz2;
+      for (long long q = threadIdx.x; q < nc; q += blockDim.x) pr[q] = ap[q] + beta * pr[q];
+    }
+  }
+  __syncthreads();
+  double xs = 0.0;
+  for (long long q = threadIdx.x; q < nc; q += blockDim.x)
+    if (dgv[q] > 0.0) xs += xr[q];
+  xs = block_sum_d(xs, sh);
+  const double xm = cnt > 0.0 ? xs / cnt : 0.0;
+  for (long long q = threadIdx.x; q < nc; q += blockDim.x) a.x[q] = (dgv[q] > 0.0) ? (float)(xr[q] - xm) : 0.f;
+}
+
+int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s) {
+  if (D == 3)
+    k_coarse_cg<3><<<1, 256, 0, s>>>(a);
+  else
+    k_coarse_cg<2><<<1, 256, 0, s>>>(a);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// k_correct: u_c[I] -= w dt L_c[I] (p[I] - p[I-e_c]) (the pressure-gradient loop of
+// Section 2, all components in one pass) and, after the last projection of a step,
+// the CFL out-flux max_I sum_c max(0, u_c[I+e_c]) + max(0, -u_c[I]) of the corrected
+// field (upper faces corrected on the fly, so no second pass).
+template <int D>
+__global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
+  __shared__ unsigned s_m[8];
+  const Grid& g = a.g;
+  const int tid = threadIdx.x;
+  int tx, ty, tz;
+  cell_coords(D, 0, tid, tx, ty, tz);
+  const int i = blockIdx.x * 32 + tx;
+  const int j = blockIdx.y * (D == 3 ? 4 : 8) + ty;
+  const int k = (D == 3) ? blockIdx.z * 2 + tz : 0;
+  const bool in = i < g.n[0] && j < g.n[1] && k < g.n[2];
+  const float s = (float)((double)a.w * *a.dt);
+  float m = 0.f;
+  if (in) {
+    const long long q = cell_index(g, i, j, k);
+    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+    const int I[3] = {i, j, k};
+    const float x0 = __ldg(a.x + q);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const long long qm = nb_dn(g, c, I[c], q, st[c]);
+      const float Ll = __ldg(a.L[c] + q);
+      const float ulo = __ldg(a.u_in[c] + q) - s * Ll * (x0 - __ldg(a.x + qm));
+      a.u_out[c][q] = ulo;
+      if (a.cfl) {
+        bool has;
+        const long long qu = nb_up(g, c, I[c], q, st[c], has);
+        float uup;
+        if (has)
+          uup = __ldg(a.u_in[c] + qu) - s * __ldg(a.L[c] + qu) * (__ldg(a.x + qu) - x0);
+        else
+          uup = g.U[c];
+        m += fmaxf(0.f, uup) + fmaxf(0.f, -ulo);
+      }
+    }
+  }
+  if (a.cfl) {
+    const unsigned mb = block_max_bits<256>(__float_as_uint(fabsf(m)), s_m);
+    if (tid == 0) atomicMax(&a.st->cfl_bits, mb);
+  }
+}
+
+int launch_correct(int D, const CorrArgs& a, cudaStream_t s) {
+  const Grid& g = a.g;
+  if (D == 3) {
+    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + 1) / 2);
+    k_correct<3><<<grd, 256, 0, s>>>(a);
+  } else {
+    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
+    k_correct<2><<<grd, 256, 0, s>>>(a);
+  }
+  return 0;
+}
+
+// CFL out-flux maximum of a velocity field without a correction (initial dt).
+template <int D>
+__global__ void __launch_bounds__(256) k_cfl_only(Grid g, const float* u0, const float* u1, const float* u2,
+                                                   DevState* st) {
+  __shared__ unsigned s_m[8];
+  const float* u[3] = {u0, u1, u2};
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  float m = 0.f;
+  if (q < g.nc) {
+    const long long stv[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+    int I[3];
+    I[0] = (int)(q % g.n[0]);
+    long long t = q / g.n[0];
+    I[1] = (int)(t % g.n[1]);
+    I[2] = (int)(t / g.n[1]);
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, stv[c], has);
+      const float uup = has ? u[c][qu] : g.U[c];
+      m += fmaxf(0.f, uup) + fmaxf(0.f, -u[c][q]);
+    }
+  }
+  const unsigned mb = block_max_bits<256>(__float_as_uint(fabsf(m)), s_m);
+  if (threadIdx.x == 0) atomicMax(&st->cfl_bits, mb);
+}
+
+int launch_cfl_only(int D, const Grid& g, const float* const* u, DevState* st, cudaStream_t s) {
+  const int nb = (int)((g.nc + 255) / 256);
+  if (D == 3)
+    k_cfl_only<3><<<nb, 256, 0, s>>>(g, u[0], u[1], u[2], st);
+  else
+    k_cfl_only<2><<<nb, 256, 0, s>>>(g, u[0], u[1], u[1], st);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Device-side control of the V-cycle loop: reads the residual maximum of the pass
+// just finished, converts it to x units (times w dt), counts V-cycles, records the
+// outcome and sets the graph's while-condition.  No host round trip.
+__global__ void k_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, int first, int proj, float w,
+                         double tol, int maxit) {
+  const float nrm = __uint_as_float(st->norm_bits);
+  st->norm_bits = 0u;
+  const float res = (float)((double)nrm * (double)w * st->dt);
+  if (first) {
+    st->iter = 0;
+  } else {
+    st->iter += 1;
+    st->total_vcycles += 1;
+  }
+  const bool finite = isfinite(res);
+  const bool cont = finite && (double)res > tol && st->iter < maxit;
+  if (!finite) st->status |= 1;
+  if (!cont) {
+    st->last_iters[proj] = st->iter;
+    st->last_res[proj] = res;
+    if (finite && (double)res > tol) st->status |= 2;
+    if (!(res <= st->worst_res)) st->worst_res = res;
+  }
+  st->res_x = res;
+  st->cond = cont ? 1 : 0;
+  if (use_handle) cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+int launch_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, int first, int proj, float w,
+                  double tol, int maxit, cudaStream_t s) {
+  k_decide<<<1, 1, 0, s>>>(st, h, use_handle, first, proj, w, tol, maxit);
+  return 0;
+}
+
+// End of a step: advance the clock and take the next dt from the CFL maximum
+// (dt = min(dt_cap, 1/(max out-flux + 2 D nu)), CFL! of Table 2), or keep dt fixed.
+// advance = 0: only set dt (initial condition).
+__global__ void k_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, int advance) {
+  const double used = st->dt;
+  if (advance) {
+    st->time += used;
+    st->steps += 1;
+  }
+  double dn;
+  if (dt_fixed > 0.0) {
+    dn = dt_fixed;
+  } else {
+    const double m = (double)__uint_as_float(st->cfl_bits);
+    dn = fmin(dt_cap, 1.0 / (m + 2.0 * D * nu));
+  }
+  if (!isfinite(dn) || !(dn > 0.0)) {
+    st->status |= 1;
+    dn = used;
+  }
+  st->dt = dn;
+  st->cfl_bits = 0u;
+}
+
+int launch_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s) {
+  k_step_end<<<1, 1, 0, s>>>(st, D, nu, dt_cap, dt_fixed, 1);
+  return 0;
+}
+
+int launch_set_dt_from_cfl(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s) {
+  k_step_end<<<1, 1, 0, s>>>(st, D, nu, dt_cap, dt_fixed, 0);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Body measure (once per sim): L_c = mu0 = K0(d/eps) at each lower c-face, with d
+// the signed distance of the face centre (Section 2), zero on non-periodic boundary
+// faces.  FP64 evaluation, stored as float.
+template <int D>
+__global__ void k_measure(Grid g, Body b, float* L0, float* L1, float* L2) {
+  float* L[3] = {L0, L1, L2};
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= g.nc) return;
+  int I[3];
+  I[0] = (int)(q % g.n[0]);
+  long long t = q / g.n[0];
+  I[1] = (int)(t % g.n[1]);
+  I[2] = (int)(t / g.n[1]);
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    double v = 1.0;
+    if (b.kind != 0) {
+      double x[3] = {I[0] + 0.5, I[1] + 0.5, I[2] + 0.5}, n[3];
+      x[c] -= 0.5;
+      const double d = body_sdf<D>(b, x, n);
+      v = kernel_K0(d / b.eps);
+    }
+    if (!is_per(g, c) && I[c] == 0) v = 0.0;
+    L[c][q] = (float)v;
+  }
+}
+
+int launch_measure(int D, const Grid& g, const Body& b, float* const* L, cudaStream_t s) {
+  const int nb = (int)((g.nc + 255) / 256);
+  if (D == 3)
+    k_measure<3><<<nb, 256, 0, s>>>(g, b, L[0], L[1], L[2]);
+  else
+    k_measure<2><<<nb, 256, 0, s>>>(g, b, L[0], L[1], L[1]);
+  return 0;
+}
+
+// Coarse face coefficient = half the sum of the 2^(D-1) fine faces it covers.
+template <int D>
+__global__ void k_coarsen(Grid f, const float* F0, const float* F1, const float* F2, Grid c, float* C0, float* C1,
+                          float* C2) {
+  const float* Fl[3] = {F0, F1, F2};
+  float* Cl[3] = {C0, C1, C2};
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= c.nc) return;
+  int J[3];
+  J[0] = (int)(q % c.n[0]);
+  long long t = q / c.n[0];
+  J[1] = (int)(t % c.n[1]);
+  J[2] = (int)(t / c.n[1]);
+#pragma unroll
+  for (int cc = 0; cc < D; ++cc) {
+    double sum = 0.0;
+    const int a0 = (cc == 0) ? 1 : 2, a1 = (cc == 1) ? 1 : 2, a2 = (D == 3 && cc != 2) ? 2 : 1;
+    for (int dk = 0; dk < a2; ++dk)
+      for (int dj = 0; dj < a1; ++dj)
+        for (int di = 0; di < a0; ++di) {
+          const int I0 = 2 * J[0] + di, I1 = 2 * J[1] + dj, I2 = (D == 3) ? 2 * J[2] + dk : 0;
+          sum += (double)Fl[cc][(long long)I0 + (long long)f.n[0] * ((long long)I1 + (long long)f.n[1] * I2)];
+        }
+    Cl[cc][q] = (float)(0.5 * sum);
+  }
+}
+
+int launch_coarsen(int D, const Grid& fine, const float* const* Lf, const Grid& coarse, float* const* Lc,
+                   cudaStream_t s) {
+  const int nb = (int)((coarse.nc + 255) / 256);
+  if (D == 3)
+    k_coarsen<3><<<nb, 256, 0, s>>>(fine, Lf[0], Lf[1], Lf[2], coarse, Lc[0], Lc[1], Lc[2]);
+  else
+    k_coarsen<2><<<nb, 256, 0, s>>>(fine, Lf[0], Lf[1], Lf[1], coarse, Lc[0], Lc[1], Lc[1]);
+  return 0;
+}
+
+// Initial velocity: kind 0 uniform U; kind 1 Taylor-Green vortex (k = 2 pi / n_0),
+// each component sampled at its own face centres.
+template <int D>
+__global__ void k_set_ic(Grid g, int kind, double amp, float* u0, float* u1, float* u2) {
+  float* u[3] = {u0, u1, u2};
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= g.nc) return;
+  int I[3];
+  I[0] = (int)(q % g.n[0]);
+  long long t = q / g.n[0];
+  I[1] = (int)(t % g.n[1]);
+  I[2] = (int)(t / g.n[1]);
+  const double kw = 2.0 * 3.141592653589793 / g.n[0];
+#pragma unroll
+  for (int c = 0; c < D; ++c) {
+    double v = g.U[c];
+    if (kind == 1) {
+      double x[3] = {I[0] + 0.5, I[1] + 0.5, I[2] + 0.5};
+      x[c] -= 0.5;
+      const double cz = (D == 3) ? cos(kw * x[2]) : 1.0;
+      if (c == 0)
+        v = amp * sin(kw * x[0]) * cos(kw * x[1]) * cz;
+      else if (c == 1)
+        v = -amp * cos(kw * x[0]) * sin(kw * x[1]) * cz;
+      else
+        v = 0.0;
+    }
+    if (!is_per(g, c) && I[c] == 0) v = g.U[c];  // boundary faces always carry U
+    u[c][q] = (float)v;
+  }
+}
+
+int launch_set_ic(int D, const Grid& g, int kind, double amp, float* const* u, cudaStream_t s) {
+  const int nb = (int)((g.nc + 255) / 256);
+  if (D == 3)
+    k_set_ic<3><<<nb, 256, 0, s>>>(g, kind, amp, u[0], u[1], u[2]);
+  else
+    k_set_ic<2><<<nb, 256, 0, s>>>(g, kind, amp, u[0], u[1], u[1]);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Pressure force F_d = -sum_cells (p - pbar) n_d K_eps(d) (FP64).  Pass 1: per-block
+// partial sums of p and of the active-cell count over a fixed grid (deterministic).
+// Pass 2 (one block): pbar from the partials in a fixed order, then the band sum over
+// the body's bounding box.
+template <int D>
+__global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, const float* L0, const float* L1,
+                                                         const float* L2, double* part) {
+  __shared__ double sh[9];
+  const float* L[3] = {L0, L1, L2};
+  const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+  double sp = 0.0, sc = 0.0;
+  for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < g.nc; q += (long long)gridDim.x * 256) {
+    int I[3];
+    I[0] = (int)(q % g.n[0]);
+    long long t = q / g.n[0];
+    I[1] = (int)(t % g.n[1]);
+    I[2] = (int)(t / g.n[1]);
+    float dg = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      dg += (has ? L[c][qu] : 0.f) + L[c][q];
+    }
+    if (dg > 0.f) {
+      sp += (double)p[q];
+      sc += 1.0;
+    }
+  }
+  sp = block_sum_d(sp, sh);
+  sc = block_sum_d(sc, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = sp;
+    part[2 * blockIdx.x + 1] = sc;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float* p, const double* part, int npart,
+                                                      int lo0, int lo1, int lo2, int bx, int by, int bz,
+                                                      double* out) {
+  __shared__ double sh[9];
+  double sp = 0.0, sc = 0.0;
+  for (int k = threadIdx.x; k < npart; k += 256) {
+    sp += part[2 * k];
+    sc += part[2 * k + 1];
+  }
+  sp = block_sum_d(sp, sh);
+  sc = block_sum_d(sc, sh);
+  const double pbar = sc > 0.0 ? sp / sc : 0.0;
+  double F[3] = {0.0, 0.0, 0.0};
+  const long long nbox = (long long)bx * by * bz;
+  for (long long t = threadIdx.x; t < nbox; t += 256) {
+    const int i = lo0 + (int)(t % bx);
+    const long long r = t / bx;
+    const int j = lo1 + (int)(r % by);
+    const int k = lo2 + (int)(r / by);
+    double x[3] = {i + 0.5, j + 0.5, k + 0.5}, n[3];
+    const double d = body_sdf<D>(b, x, n);
+    if (!(fabs(d) < b.eps)) continue;
+    const double K = (1.0 + cospi(d / b.eps)) / (2.0 * b.eps);
+    const double pp = (double)p[cell_index(g, i, j, k)] - pbar;
+#pragma unroll
+    for (int dd = 0; dd < D; ++dd) F[dd] -= pp * n[dd] * K;
+  }
+  for (int dd = 0; dd < D; ++dd) {
+    const double v = block_sum_d(F[dd], sh);
+    if (threadIdx.x == 0) out[dd] = v;
+  }
+  if (threadIdx.x == 0) out[3] = pbar;
+}
+
+int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* const* L, double* partials,
+                  int npart, double* out, cudaStream_t s) {
+  if (D == 3)
+    k_force_partials<3><<<npart, 256, 0, s>>>(g, p, L[0], L[1], L[2], partials);
+  else
+    k_force_partials<2><<<npart, 256, 0, s>>>(g, p, L[0], L[1], L[1], partials);
+  double ext = b.r1 + b.eps + 1.0;
+  if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 1.0;
+  int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  if (b.kind != 0) {
+    for (int d = 0; d < D; ++d) {
+      lo[d] = (int)fmax(0.0, floor(b.c[d] - ext));
+      hi[d] = (int)fmin((double)g.n[d], ceil(b.c[d] + ext) + 1.0);
+      if (hi[d] < lo[d]) hi[d] = lo[d];
+    }
+  } else {
+    hi[0] = lo[0];
+  }
+  const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
+  if (D == 3)
+    k_force_final<3><<<1, 256, 0, s>>>(g, b, p, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
+  else
+    k_force_final<2><<<1, 256, 0, s>>>(g, b, p, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
+  return 0;
+}
+
+}  // namespace wl
+
+namespace wl {
+
+// Boundary faces of non-periodic directions always carry U_c (used after a caller
+// overwrites the velocity).
+template <int D>
+__global__ void k_fix_bfaces(Grid g, float* u0, float* u1, float* u2) {
+  float* u[3] = {u0, u1, u2};
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= g.nc) return;
+  int I[3];
+  I[0] = (int)(q % g.n[0]);
+  long long t = q / g.n[0];
+  I[1] = (int)(t % g.n[1]);
+  I[2] = (int)(t / g.n[1]);
+#pragma unroll
+  for (int c = 0; c < D; ++c)
+    if (!is_per(g, c) && I[c] == 0) u[c][q] = g.U[c];
+}
+
+int launch_fix_bfaces(int D, const Grid& g, float* const* u, cudaStream_t s) {
+  const int nb = (int)((g.nc + 255) / 256);
+  if (D == 3)
+    k_fix_bfaces<3><<<nb, 256, 0, s>>>(g, u[0], u[1], u[2]);
+  else
+    k_fix_bfaces<2><<<nb, 256, 0, s>>>(g, u[0], u[1], u[1]);
+  return 0;
+}
+
+}  // namespace wl

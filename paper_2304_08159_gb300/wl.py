@@ -1,0 +1,352 @@
+"""ctypes binding of libwl.so (include/wl.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does nothing
+but convert arguments; all of the time step runs in the library's CUDA kernels.
+PyTorch supplies device memory (the sim workspace, device-side field buffers) and
+the CUDA stream.  If libwl.so has not been built the import of the library fails
+loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwl.so")
+
+WL_OK = 0
+WL_EINVAL = -1
+WL_ENOMEM = -2
+WL_ECUDA = -3
+WL_ENONFINITE = -4
+WL_ETIMEOUT = -5
+WL_WNOTCONV = 1
+
+WL_FIELD_U = 0
+WL_FIELD_P = 1
+WL_FIELD_DIV = 2
+WL_FIELD_MU0 = 3
+WL_FIELD_Z = 4
+WL_FIELD_UPRED = 5
+WL_FIELD_USTAGE = 6
+
+WL_BODY_NONE = 0
+WL_BODY_SPHERE = 1
+WL_BODY_TORUS = 2
+
+# every symbol include/wl.h declares
+EXPORTS = (
+    "wl_default_opts", "wl_workspace_bytes", "wl_create", "wl_set_ic", "wl_step", "wl_stage",
+    "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_get_field", "wl_set_field", "wl_get_dt",
+    "wl_set_dt", "wl_get_time", "wl_status", "wl_levels", "wl_level_dims", "wl_destroy",
+    "wl_last_error",
+)
+
+
+class WlBody(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3),
+                ("radius", ctypes.c_double), ("radius2", ctypes.c_double)]
+
+
+class WlOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_vcycles", ctypes.c_int), ("post", ctypes.c_int),
+                ("eps", ctypes.c_double), ("dt_cap", ctypes.c_double), ("dt_fixed", ctypes.c_double),
+                ("periodic_mask", ctypes.c_uint), ("advect", ctypes.c_int), ("precision", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+class WLError(RuntimeError):
+    def __init__(self, rc, msg):
+        super().__init__(f"libwl error {rc}: {msg}")
+        self.rc = rc
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwl.so (raises if it is missing) and declare every signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    I, D, P = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+    IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "wl_default_opts": (None, [ctypes.POINTER(WlOpts)]),
+        "wl_workspace_bytes": (ctypes.c_size_t, [IP, I, ctypes.POINTER(WlOpts)]),
+        "wl_create": (I, [IP, I, D, DP, ctypes.POINTER(WlBody), ctypes.POINTER(WlOpts), ctypes.POINTER(H)]),
+        "wl_set_ic": (I, [H, I, D, P, I]),
+        "wl_step": (I, [H, I]),
+        "wl_stage": (I, [H, I]),
+        "wl_project": (I, [H, D, IP, DP]),
+        "wl_gmg_vcycle": (I, [H, DP]),
+        "wl_forces": (I, [H, DP]),
+        "wl_get_field": (I, [H, I, P, I]),
+        "wl_set_field": (I, [H, I, P, I]),
+        "wl_get_dt": (I, [H, DP]),
+        "wl_set_dt": (I, [H, D]),
+        "wl_get_time": (I, [H, DP, ctypes.POINTER(ctypes.c_longlong)]),
+        "wl_status": (I, [H, IP, ctypes.POINTER(ctypes.c_longlong), DP]),
+        "wl_levels": (I, [H, IP]),
+        "wl_level_dims": (I, [H, I, IP]),
+        "wl_destroy": (None, [H]),
+        "wl_last_error": (ctypes.c_char_p, [H]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------------- C entry points
+def wl_default_opts() -> WlOpts:
+    o = WlOpts()
+    load().wl_default_opts(ctypes.byref(o))
+    return o
+
+
+def wl_workspace_bytes(dims, opts: WlOpts | None = None) -> int:
+    d = (ctypes.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    return load().wl_workspace_bytes(d, len(dims), ctypes.byref(opts) if opts is not None else None)
+
+
+def wl_create(dims, nu, U, body: WlBody | None, opts: WlOpts | None):
+    d = (ctypes.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    u = (ctypes.c_double * 3)(*(list(U) + [0.0] * (3 - len(U))))
+    h = ctypes.c_void_p()
+    rc = load().wl_create(d, len(dims), float(nu), u, ctypes.byref(body) if body is not None else None,
+                          ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return rc, h
+
+
+def wl_set_ic(h, kind, amp=1.0, src_ptr=None, src_is_device=0):
+    return load().wl_set_ic(h, int(kind), float(amp), src_ptr, int(src_is_device))
+
+
+def wl_step(h, nsteps=1):
+    return load().wl_step(h, int(nsteps))
+
+
+def wl_stage(h, stage):
+    return load().wl_stage(h, int(stage))
+
+
+def wl_project(h, w):
+    it = ctypes.c_int(0)
+    r = ctypes.c_double(0.0)
+    rc = load().wl_project(h, float(w), ctypes.byref(it), ctypes.byref(r))
+    return rc, it.value, r.value
+
+
+def wl_gmg_vcycle(h):
+    r = ctypes.c_double(0.0)
+    rc = load().wl_gmg_vcycle(h, ctypes.byref(r))
+    return rc, r.value
+
+
+def wl_forces(h, D):
+    F = (ctypes.c_double * 3)()
+    rc = load().wl_forces(h, F)
+    return rc, [F[i] for i in range(D)]
+
+
+def wl_get_field(h, which, dst_ptr, dst_is_device):
+    return load().wl_get_field(h, int(which), dst_ptr, int(dst_is_device))
+
+
+def wl_set_field(h, which, src_ptr, src_is_device):
+    return load().wl_set_field(h, int(which), src_ptr, int(src_is_device))
+
+
+def wl_get_dt(h):
+    v = ctypes.c_double(0.0)
+    rc = load().wl_get_dt(h, ctypes.byref(v))
+    return rc, v.value
+
+
+def wl_set_dt(h, dt):
+    return load().wl_set_dt(h, float(dt))
+
+
+def wl_get_time(h):
+    t = ctypes.c_double(0.0)
+    n = ctypes.c_longlong(0)
+    rc = load().wl_get_time(h, ctypes.byref(t), ctypes.byref(n))
+    return rc, t.value, n.value
+
+
+def wl_status(h):
+    it = (ctypes.c_int * 2)()
+    tot = ctypes.c_longlong(0)
+    worst = ctypes.c_double(0.0)
+    rc = load().wl_status(h, it, ctypes.byref(tot), ctypes.byref(worst))
+    return rc, (it[0], it[1]), tot.value, worst.value
+
+
+def wl_levels(h):
+    n = ctypes.c_int(0)
+    rc = load().wl_levels(h, ctypes.byref(n))
+    return rc, n.value
+
+
+def wl_level_dims(h, l):
+    d = (ctypes.c_int * 3)()
+    rc = load().wl_level_dims(h, int(l), d)
+    return rc, (d[0], d[1], d[2])
+
+
+def wl_destroy(h):
+    load().wl_destroy(h)
+
+
+def wl_last_error(h) -> str:
+    s = load().wl_last_error(h)
+    return s.decode() if s else ""
+
+
+# ----------------------------------------------------------------- convenience wrapper
+class Sim:
+    """One simulation: workspace from torch's caching allocator, work on torch's
+    current CUDA stream, fields exchanged as torch tensors or numpy arrays.
+    Every method is a direct call of the C entry point of the same name."""
+
+    def __init__(self, dims, nu, U, body=None, periodic=0, tol=1e-6, max_vcycles=32, post=4, eps=1.0,
+                 dt_cap=10.0, dt_fixed=0.0, advect=True, precision=0, use_graph=True, device=None):
+        import torch
+
+        self.torch = torch
+        self.dims = tuple(int(d) for d in dims)
+        self.D = len(self.dims)
+        self.ncell = int(np.prod(self.dims))
+        self.shape = tuple(reversed(self.dims))
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        o = wl_default_opts()
+        o.tol, o.max_vcycles, o.post, o.eps = float(tol), int(max_vcycles), int(post), float(eps)
+        o.dt_cap, o.dt_fixed, o.periodic_mask = float(dt_cap), float(dt_fixed), int(periodic)
+        o.advect, o.precision, o.use_graph = int(bool(advect)), int(precision), int(bool(use_graph))
+        with torch.cuda.device(self.device):
+            o.stream = torch.cuda.current_stream().cuda_stream
+            nbytes = wl_workspace_bytes(self.dims, o)
+            if nbytes == 0:
+                raise WLError(WL_EINVAL, "bad dimensions")
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            o.workspace = self.workspace.data_ptr()
+            o.workspace_bytes = nbytes
+            b = None
+            if body is not None:
+                b = WlBody()
+                b.kind = int(body.get("kind", WL_BODY_SPHERE))
+                c = list(body["center"]) + [0.0] * 3
+                for i in range(3):
+                    b.center[i] = float(c[i])
+                b.radius = float(body.get("radius", 0.0))
+                b.radius2 = float(body.get("radius2", 0.0))
+            rc, h = wl_create(self.dims, nu, U, b, o)
+        if rc != WL_OK:
+            raise WLError(rc, "wl_create failed")
+        self.h = h
+        self.opts = o
+
+    def _check(self, rc, what):
+        if rc < 0:
+            raise WLError(rc, f"{what}: {wl_last_error(self.h)}")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            wl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # fields
+    def _nblocks(self, which):
+        return self.D if which in (WL_FIELD_U, WL_FIELD_MU0, WL_FIELD_UPRED, WL_FIELD_USTAGE) else 1
+
+    def get(self, which, device=False):
+        """Field as a float32 tensor on the GPU (device=True) or a numpy array."""
+        nb = self._nblocks(which)
+        shape = ((nb,) if nb > 1 else ()) + self.shape
+        if device:
+            t = self.torch.empty(shape, dtype=self.torch.float32, device=self.device)
+            self._check(wl_get_field(self.h, which, t.data_ptr(), 1), "wl_get_field")
+            return t
+        a = np.empty(shape, dtype=np.float32)
+        self._check(wl_get_field(self.h, which, a.ctypes.data, 0), "wl_get_field")
+        return a
+
+    def set(self, which, value):
+        if isinstance(value, np.ndarray):
+            a = np.ascontiguousarray(value, dtype=np.float32)
+            assert a.size == self._nblocks(which) * self.ncell
+            self._check(wl_set_field(self.h, which, a.ctypes.data, 0), "wl_set_field")
+        else:
+            t = value.to(device=self.device, dtype=self.torch.float32).contiguous()
+            assert t.numel() == self._nblocks(which) * self.ncell
+            self._check(wl_set_field(self.h, which, t.data_ptr(), 1), "wl_set_field")
+
+    # routines
+    def set_ic(self, kind=0, amp=1.0, u=None):
+        if kind == 2:
+            a = np.ascontiguousarray(u, dtype=np.float32)
+            return self._check(wl_set_ic(self.h, 2, amp, a.ctypes.data, 0), "wl_set_ic")
+        return self._check(wl_set_ic(self.h, kind, amp), "wl_set_ic")
+
+    def step(self, n=1):
+        return self._check(wl_step(self.h, n), "wl_step")
+
+    def stage(self, stage):
+        return self._check(wl_stage(self.h, stage), "wl_stage")
+
+    def project(self, w):
+        rc, it, r = wl_project(self.h, w)
+        self._check(rc, "wl_project")
+        return rc, it, r
+
+    def gmg_vcycle(self):
+        rc, r = wl_gmg_vcycle(self.h)
+        self._check(rc, "wl_gmg_vcycle")
+        return r
+
+    def forces(self):
+        rc, F = wl_forces(self.h, self.D)
+        self._check(rc, "wl_forces")
+        return np.array(F)
+
+    @property
+    def dt(self):
+        rc, v = wl_get_dt(self.h)
+        self._check(rc, "wl_get_dt")
+        return v
+
+    @dt.setter
+    def dt(self, v):
+        self._check(wl_set_dt(self.h, v), "wl_set_dt")
+
+    def time(self):
+        rc, t, n = wl_get_time(self.h)
+        self._check(rc, "wl_get_time")
+        return t, n
+
+    def status(self):
+        rc, last, tot, worst = wl_status(self.h)
+        self._check(rc, "wl_status")
+        return rc, last, tot, worst
+
+    def levels(self):
+        rc, n = wl_levels(self.h)
+        self._check(rc, "wl_levels")
+        return [wl_level_dims(self.h, l)[1][: self.D] for l in range(n)]

@@ -1,0 +1,72 @@
+"""The C-ABI library loads and exports every entry point include/wl.h declares
+(no GPU needed: nothing here launches work)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2304_08159_gb300 import build, wl
+
+    build.build()
+    return wl.load()
+
+
+def _declared():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", h)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"\b(wl_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert len(declared) >= 19
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_header():
+    from paper_2304_08159_gb300 import wl
+
+    assert sorted(wl.EXPORTS) == _declared()
+
+
+def test_workspace_bytes_host_only(lib):
+    from paper_2304_08159_gb300 import wl
+
+    small = wl.wl_workspace_bytes((128, 64))
+    big = wl.wl_workspace_bytes((512, 256, 256))
+    assert small > 0 and big > 0
+    # 3 velocity buffers + (3 coefficients + z, x, x2) on the fine level, + about 1/7 for coarse levels
+    nc = 512 * 256 * 256
+    assert 4 * nc * (9 + 6) <= big <= 4 * nc * (9 + 6 * 8 / 7) + (1 << 20)
+    assert wl.wl_workspace_bytes((1, 64)) == 0
+    assert wl.wl_workspace_bytes((8,)) == 0
+
+
+def test_default_opts(lib):
+    from paper_2304_08159_gb300 import wl
+
+    o = wl.wl_default_opts()
+    assert o.tol == 1e-6 and o.max_vcycles == 32 and o.post == 4 and o.eps == 1.0
+    assert o.dt_cap == 10.0 and o.advect == 1 and o.use_graph == 1
+
+
+def test_product_path_does_not_import_oracle():
+    """The library package never imports the oracle."""
+    pkg = os.path.join(ROOT, "paper_2304_08159_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "liboracle" not in text and "wl_oracle" not in text, f
