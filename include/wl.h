@@ -88,7 +88,9 @@ typedef struct {
   double dt_fixed;       /* > 0: use this dt and skip the CFL rule (default 0) */
   unsigned periodic_mask;/* bit d: direction d periodic (default 0) */
   int advect;            /* 1: convection on (default); 0: diffusion only */
-  int precision;         /* 0: FP32 (default); 1: FP64 iterative refinement of the fine-level pressure */
+  int precision;         /* 1 (default): FP32 except the fine-level pressure, kept in FP64 with an FP64
+                            residual (iterative refinement), so tol holds whatever the pressure's size;
+                            0: all FP32 (less traffic; the residual floor ~ 6e-8*|x|*2D may exceed tol) */
   int use_graph;         /* 1: wl_step runs as a CUDA graph with device-side V-cycle loops (default) */
   void* stream;          /* cudaStream_t for all work (default NULL) */
   void* workspace;       /* optional caller-owned device buffer of wl_workspace_bytes() */

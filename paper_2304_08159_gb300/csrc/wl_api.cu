@@ -57,7 +57,9 @@ struct wl_sim {
   double* cg_work = nullptr;
   double* fpart = nullptr;
   double* fout = nullptr;
-  double* p64 = nullptr;      // precision mode 1: FP64 fine pressure
+  double* p64 = nullptr;      // precision 1: FP64 fine-level pressure
+  float* rf = nullptr;        // precision 1: FP32 residual, right-hand side of each correction cycle
+  double* G = nullptr;        // dense pseudo-inverse of the coarsest operator (small coarsest levels)
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool own_ws = false;
@@ -146,12 +148,16 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, char* base) {
   void* fp = cv.take(sizeof(double) * 2 * kForceParts);
   void* fo = cv.take(sizeof(double) * 4);
   void* p64 = precision == 1 ? cv.take(sizeof(double) * nc) : nullptr;
+  void* rf = precision == 1 ? cv.take(sizeof(float) * nc) : nullptr;
+  void* G = ncoarse <= kDenseCoarse ? cv.take(sizeof(double) * ncoarse * ncoarse) : nullptr;
   if (s) {
     s->ds = (DevState*)ds;
     s->cg_work = (double*)cg;
     s->fpart = (double*)fp;
     s->fout = (double*)fo;
     s->p64 = (double*)p64;
+    s->rf = (float*)rf;
+    s->G = (double*)G;
     s->nlev = nlev;
     for (int l = 0; l < nlev; ++l) {
       Grid& g = s->lev[l].g;
@@ -208,51 +214,60 @@ void enq_proj_head(wl_sim* s, float* const* u, float w, int proj, cudaStream_t s
   ResArgs a = res_args(s, 0, RES_DIVERGENCE);
   for (int c = 0; c < 3; ++c) a.u[c] = u[c];
   a.w = w;
+  a.x64 = s->p64;
+  a.rout = s->rf;
   launch_residual(s->D, a, st);
   launch_decide(s->ds, s->hc[proj], use_h, 1, proj, w, s->o.tol, s->o.max_vcycles, st);
 }
 
 // post sweeps on level l with the coarse correction of level l+1 prolonged into the
-// first one; the result lands in lev[l].x
+// first one.  Coarse levels start from zero and end in lev[l].x.  The fine level
+// either smooths the FP32 pressure in place of the iterate (precision 0), or smooths
+// a correction from zero against the residual rf and adds the result of the last
+// sweep into the FP64 pressure (precision 1, iterative refinement).
 void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   LevelBuf& L = s->lev[l];
   const int P = s->o.post;
+  const bool refine = (l == 0 && s->p64);
   SweepArgs a{};
   for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
-  a.z = L.z;
+  a.z = refine ? s->rf : L.z;
   a.g = L.g;
   for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
   float* bufs[2] = {L.x, L.x2};
-  int cur;  // index of the buffer holding the current iterate
-  if (l == 0) {
-    a.x_in = L.x;
-    a.xc = s->lev[1].x;
-    a.x_out = L.x2;
+  const bool from_x = (l == 0 && !refine);  // precision 0: the fine iterate is the pressure itself
+  // choose the first output so that the last one lands in bufs[0]
+  int out = from_x ? 1 : ((P % 2 == 1) ? 0 : 1);
+  const float* in = from_x ? L.x : nullptr;
+  for (int it = 0; it < P; ++it) {
+    a.x_in = in;
+    a.xc = (it == 0) ? s->lev[l + 1].x : nullptr;
+    a.x_out = bufs[out];
+    a.p64 = (refine && it == P - 1) ? s->p64 : nullptr;
     launch_sweep(s->D, a, st);
-    cur = 1;
-  } else {
-    a.x_in = nullptr;
-    a.xc = s->lev[l + 1].x;
-    cur = (P % 2 == 1) ? 0 : 1;
-    a.x_out = bufs[cur];
-    launch_sweep(s->D, a, st);
+    in = bufs[out];
+    out ^= 1;
   }
-  a.xc = nullptr;
-  for (int it = 1; it < P; ++it) {
-    a.x_in = bufs[cur];
-    a.x_out = bufs[cur ^ 1];
-    launch_sweep(s->D, a, st);
-    cur ^= 1;
-  }
-  if (cur != 0) cudaMemcpyAsync(L.x, L.x2, sizeof(float) * L.g.nc, cudaMemcpyDeviceToDevice, st);
+  if (!refine && in != L.x) cudaMemcpyAsync(L.x, in, sizeof(float) * L.g.nc, cudaMemcpyDeviceToDevice, st);
 }
 
-void enq_coarsest(wl_sim* s, int l, cudaStream_t st) {
-  CoarseArgs a{};
+// coarsest solve of level l: x = A^+ z (dense FP64 pseudo-inverse when small, FP64 CG otherwise)
+void enq_coarsest(wl_sim* s, int l, const float* z, float* x, cudaStream_t st) {
   LevelBuf& L = s->lev[l];
-  a.z = L.z;
+  if (s->G && l == s->nlev - 1) {
+    DenseArgs d{};
+    for (int c = 0; c < 3; ++c) d.L[c] = L.L[c];
+    d.g = L.g;
+    d.G = s->G;
+    d.z = z;
+    d.x = x;
+    launch_apply_pinv(d, st);
+    return;
+  }
+  CoarseArgs a{};
+  a.z = z;
   for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
-  a.x = L.x;
+  a.x = x;
   a.g = L.g;
   a.work = s->cg_work;
   a.maxit = (int)std::min<long long>(4 * L.g.nc + 100, 100000);
@@ -264,18 +279,30 @@ void enq_coarsest(wl_sim* s, int l, cudaStream_t st) {
 // the fine level (whose right-hand side and restricted residual are already set)
 void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
   const int Lv = s->nlev;
-  if (Lv == 1) {
-    enq_coarsest(s, 0, st);  // no coarse level: solve the fine level directly
+  if (Lv == 1) {  // no coarse level: solve the fine level directly
+    if (s->p64) {
+      enq_coarsest(s, 0, s->rf, s->lev[0].x2, st);
+      launch_add64(s->lev[0].x2, s->p64, s->g.nc, st);
+    } else {
+      enq_coarsest(s, 0, s->lev[0].z, s->lev[0].x, st);
+    }
     return;
   }
   for (int l = 1; l + 1 < Lv; ++l) launch_residual(s->D, res_args(s, l, RES_RESTRICT), st);
-  enq_coarsest(s, Lv - 1, st);
+  enq_coarsest(s, Lv - 1, s->lev[Lv - 1].z, s->lev[Lv - 1].x, st);
   for (int l = Lv - 2; l >= 0; --l) enq_smooth(s, l, st);
+}
+
+ResArgs fine_residual_args(wl_sim* s) {
+  ResArgs a = res_args(s, 0, RES_RESIDUAL);
+  a.x64 = s->p64;
+  a.rout = s->rf;
+  return a;
 }
 
 void enq_vcycle(wl_sim* s, float w, int proj, cudaStream_t st, int use_h) {
   enq_vcycle_core(s, st);
-  launch_residual(s->D, res_args(s, 0, RES_RESIDUAL), st);
+  launch_residual(s->D, fine_residual_args(s), st);
   launch_decide(s->ds, s->hc[proj], use_h, 0, proj, w, s->o.tol, s->o.max_vcycles, st);
 }
 
@@ -287,6 +314,7 @@ void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int 
     a.L[c] = s->lev[0].L[c];
   }
   a.x = s->lev[0].x;
+  a.x64 = s->p64;
   a.g = s->g;
   a.dt = &s->ds->dt;
   a.w = w;
@@ -399,6 +427,7 @@ int set_dt_from_ic(wl_sim* s) {
 int reset_state(wl_sim* s) {
   WL_CUDA(s, cudaMemsetAsync(s->ds, 0, sizeof(DevState), s->st));
   WL_CUDA(s, cudaMemsetAsync(s->lev[0].x, 0, sizeof(float) * s->g.nc, s->st));
+  if (s->p64) WL_CUDA(s, cudaMemsetAsync(s->p64, 0, sizeof(double) * s->g.nc, s->st));
   return WL_OK;
 }
 
@@ -420,7 +449,7 @@ void wl_default_opts(wl_opts* o) {
   o->dt_fixed = 0.0;
   o->periodic_mask = 0u;
   o->advect = 1;
-  o->precision = 0;
+  o->precision = 1;
   o->use_graph = 1;
   o->stream = nullptr;
   o->workspace = nullptr;
@@ -450,7 +479,6 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   if (!(o.tol > 0.0) || o.max_vcycles < 0 || o.post < 1 || !(o.eps > 0.0) || !(o.dt_cap > 0.0) ||
       o.precision < 0 || o.precision > 1)
     return WL_EINVAL;
-  if (o.precision == 1) return WL_EINVAL;  // FP64 refinement path not built in this library version
   if (body && (body->kind < 0 || body->kind > 2 || (body->kind == 2 && ndim != 3))) return WL_EINVAL;
   wl_sim* s = new wl_sim();
   s->D = ndim;
@@ -505,6 +533,15 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       cudaMemsetAsync(s->lev[l].x, 0, sizeof(float) * s->lev[l].g.nc, s->st);
       cudaMemsetAsync(s->lev[l].z, 0, sizeof(float) * s->lev[l].g.nc, s->st);
     }
+    if (s->rf) cudaMemsetAsync(s->rf, 0, sizeof(float) * s->g.nc, s->st);
+    if (s->G) {
+      DenseArgs d{};
+      LevelBuf& Lc = s->lev[s->nlev - 1];
+      for (int c = 0; c < 3; ++c) d.L[c] = Lc.L[c];
+      d.g = Lc.g;
+      d.G = s->G;
+      launch_build_pinv(ndim, d, s->st);
+    }
     rc = reset_state(s);
   }
   if (!rc) {
@@ -556,13 +593,6 @@ int wl_set_ic(wl_handle s, int kind, double amp, const float* src, int src_is_de
 int wl_step(wl_handle s, int nsteps) {
   if (!s || nsteps < 0) return WL_EINVAL;
   if (s->poisoned) return fail(s, WL_ENONFINITE, "sim is poisoned by a non-finite value");
-  if (s->o.precision == 1) {
-    for (int n = 0; n < nsteps; ++n) {
-      int rc = host_step(s);
-      if (rc) return rc;
-    }
-    return WL_OK;
-  }
   if (!s->o.use_graph) {
     for (int n = 0; n < nsteps; ++n) {
       int rc = host_step(s);
@@ -603,12 +633,12 @@ int wl_project(wl_handle s, double w, int* vcycles_out, double* resid_out) {
 int wl_gmg_vcycle(wl_handle s, double* resid_inf_out) {
   if (!s) return WL_EINVAL;
   // restrict the residual of the held system, run one cycle, measure the residual
-  ResArgs a = res_args(s, 0, RES_RESIDUAL);
-  launch_residual(s->D, a, s->st);
+  launch_residual(s->D, fine_residual_args(s), s->st);
   enq_vcycle_core(s, s->st);
   WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
-  ResArgs b = res_args(s, 0, RES_RESIDUAL);
+  ResArgs b = fine_residual_args(s);
   b.zc = nullptr;
+  b.rout = nullptr;
   launch_residual(s->D, b, s->st);
   int rc = sync_state(s);
   if (rc) return rc;
@@ -621,7 +651,7 @@ int wl_gmg_vcycle(wl_handle s, double* resid_inf_out) {
 int wl_forces(wl_handle s, double* F) {
   if (!s || !F) return WL_EINVAL;
   const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
-  launch_forces(s->D, s->g, s->body, s->lev[0].x, L, s->fpart, kForceParts, s->fout, s->st);
+  launch_forces(s->D, s->g, s->body, s->lev[0].x, s->p64, L, s->fpart, kForceParts, s->fout, s->st);
   double h[4];
   WL_CUDA(s, cudaMemcpyAsync(h, s->fout, sizeof(h), cudaMemcpyDeviceToHost, s->st));
   WL_CUDA(s, cudaStreamSynchronize(s->st));
@@ -639,7 +669,8 @@ int wl_get_field(wl_handle s, int which, void* dst, int dst_is_device) {
       for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(d + c * nb, s->ua[c], nb, kind, s->st));
       break;
     case WL_FIELD_P:
-      WL_CUDA(s, cudaMemcpyAsync(d, s->lev[0].x, nb, kind, s->st));
+      if (s->p64) launch_convert(nullptr, nullptr, s->p64, s->lev[0].x2, s->g.nc, s->st);
+      WL_CUDA(s, cudaMemcpyAsync(d, s->p64 ? s->lev[0].x2 : s->lev[0].x, nb, kind, s->st));
       break;
     case WL_FIELD_DIV: {
       ResArgs a = res_args(s, 0, RES_DIV_ONLY);
@@ -681,6 +712,7 @@ int wl_set_field(wl_handle s, int which, const void* src, int src_is_device) {
       break;
     case WL_FIELD_P:
       WL_CUDA(s, cudaMemcpyAsync(s->lev[0].x, p, nb, kind, s->st));
+      if (s->p64) launch_convert(s->lev[0].x, s->p64, nullptr, nullptr, s->g.nc, s->st);
       break;
     case WL_FIELD_Z:
       WL_CUDA(s, cudaMemcpyAsync(s->lev[0].z, p, nb, kind, s->st));

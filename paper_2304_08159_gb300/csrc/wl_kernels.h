@@ -23,6 +23,8 @@ enum { RES_RESIDUAL = 0, RES_DIVERGENCE = 1, RES_RESTRICT = 2, RES_DIV_ONLY = 3 
 struct ResArgs {
   const float* u[3];   // RES_DIVERGENCE / RES_DIV_ONLY: velocity
   const float* x;      // current unknown (RES_RESIDUAL / RES_DIVERGENCE)
+  const double* x64;   // if set: FP64 unknown used instead of x, residual in FP64
+  float* rout;         // if set: the residual is stored here (right-hand side of the correction cycle)
   const float* L[3];   // face coefficients of this level
   float* z;            // right-hand side of this level (written by the divergence modes)
   float* zc;           // restricted residual for the next level (may be null)
@@ -40,8 +42,20 @@ struct SweepArgs {
   const float* z;
   const float* L[3];
   float* x_out;
+  double* p64;         // if set: add the swept values into this FP64 field instead of writing x_out
   Grid g;
   int cn[3];
+};
+
+// Dense pseudo-inverse of the coarsest operator (column-major, FP64), used when the
+// coarsest level has at most kDenseCoarse cells.
+constexpr int kDenseCoarse = 1024;
+struct DenseArgs {
+  const float* L[3];
+  Grid g;
+  double* G;           // nc x nc, column j = A^+ e_j
+  const float* z;
+  float* x;
 };
 
 struct CoarseArgs {
@@ -58,6 +72,7 @@ struct CorrArgs {
   const float* u_in[3];
   float* u_out[3];
   const float* x;      // pressure p
+  const double* x64;   // if set: FP64 pressure used instead of x
   const float* L[3];
   Grid g;
   const double* dt;
@@ -79,8 +94,12 @@ int launch_coarsen(int D, const Grid& fine, const float* const* Lf, const Grid& 
                    cudaStream_t s);
 int launch_set_ic(int D, const Grid& g, int kind, double amp, float* const* u, cudaStream_t s);
 int launch_cfl_only(int D, const Grid& g, const float* const* u, DevState* st, cudaStream_t s);
-int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* const* L, double* partials,
-                  int npart, double* out, cudaStream_t s);
+int launch_forces(int D, const Grid& g, const Body& b, const float* p, const double* p64, const float* const* L,
+                  double* partials, int npart, double* out, cudaStream_t s);
+int launch_build_pinv(int D, const DenseArgs& a, cudaStream_t s);
+int launch_apply_pinv(const DenseArgs& a, cudaStream_t s);
+int launch_convert(const float* in32, double* out64, const double* in64, float* out32, long long n, cudaStream_t s);
+int launch_add64(const float* in32, double* out64, long long n, cudaStream_t s);
 
 }  // namespace wl
 

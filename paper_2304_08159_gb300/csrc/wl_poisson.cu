@@ -89,18 +89,35 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
     if (a.mode == RES_RESTRICT) {
       v = z;
     } else if (a.mode != RES_DIV_ONLY) {
-      const float x0 = __ldg(a.x + q);
-      float acc = 0.f;
+      if (a.x64) {
+        // FP64 unknown (iterative refinement): the residual is formed in FP64
+        const double x0 = __ldg(a.x64 + q);
+        double acc = 0.0;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        bool has;
-        const long long qu = nb_up(g, c, I[c], q, st[c], has);
-        const long long qm = nb_dn(g, c, I[c], q, st[c]);
-        const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
-        const float Ll = __ldg(a.L[c] + q);
-        acc += Lu * (__ldg(a.x + qu) - x0) + Ll * (__ldg(a.x + qm) - x0);
+        for (int c = 0; c < D; ++c) {
+          bool has;
+          const long long qu = nb_up(g, c, I[c], q, st[c], has);
+          const long long qm = nb_dn(g, c, I[c], q, st[c]);
+          const double Lu = has ? (double)__ldg(a.L[c] + qu) : 0.0;
+          const double Ll = (double)__ldg(a.L[c] + q);
+          acc += Lu * (__ldg(a.x64 + qu) - x0) + Ll * (__ldg(a.x64 + qm) - x0);
+        }
+        v = (float)((double)z - acc);
+      } else {
+        const float x0 = __ldg(a.x + q);
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          bool has;
+          const long long qu = nb_up(g, c, I[c], q, st[c], has);
+          const long long qm = nb_dn(g, c, I[c], q, st[c]);
+          const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
+          const float Ll = __ldg(a.L[c] + q);
+          acc += Lu * (__ldg(a.x + qu) - x0) + Ll * (__ldg(a.x + qm) - x0);
+        }
+        v = z - acc;
       }
-      v = z - acc;
+      if (a.rout) a.rout[q] = v;
     }
   }
   if (a.mode == RES_RESIDUAL || a.mode == RES_DIVERGENCE) {
@@ -272,7 +289,19 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     if (gj < g.n[1]) {
       const long long q = cell_index(g, gi, gj, D == 3 ? k : 0);
       const float v0 = P ? vb : vr, v1 = P ? vr : vb;
-      if (gi + 1 < g.n[0] && ((g.n[0] & 1) == 0)) {
+      const bool pair = gi + 1 < g.n[0] && ((g.n[0] & 1) == 0);
+      if (a.p64) {
+        // last sweep of a correction cycle: fold the correction into the FP64 field
+        if (pair) {
+          double2 o = reinterpret_cast<double2*>(a.p64 + q)[0];
+          o.x += (double)v0;
+          o.y += (double)v1;
+          reinterpret_cast<double2*>(a.p64 + q)[0] = o;
+        } else {
+          if (gi < g.n[0]) a.p64[q] += (double)v0;
+          if (gi + 1 < g.n[0]) a.p64[q + 1] += (double)v1;
+        }
+      } else if (pair) {
         reinterpret_cast<float2*>(a.x_out + q)[0] = make_float2(v0, v1);
       } else {
         if (gi < g.n[0]) a.x_out[q] = v0;
@@ -451,25 +480,29 @@ __global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
   const int j = blockIdx.y * (D == 3 ? 4 : 8) + ty;
   const int k = (D == 3) ? blockIdx.z * 2 + tz : 0;
   const bool in = i < g.n[0] && j < g.n[1] && k < g.n[2];
-  const float s = (float)((double)a.w * *a.dt);
+  const double sd = (double)a.w * *a.dt;
+  const float s = (float)sd;
   float m = 0.f;
   if (in) {
     const long long q = cell_index(g, i, j, k);
     const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
     const int I[3] = {i, j, k};
-    const float x0 = __ldg(a.x + q);
+    // pressure difference across a face, from the FP64 field when there is one
+    auto dp = [&](long long qa, long long qb) -> float {
+      return a.x64 ? (float)(sd * (__ldg(a.x64 + qa) - __ldg(a.x64 + qb))) : s * (__ldg(a.x + qa) - __ldg(a.x + qb));
+    };
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const long long qm = nb_dn(g, c, I[c], q, st[c]);
       const float Ll = __ldg(a.L[c] + q);
-      const float ulo = __ldg(a.u_in[c] + q) - s * Ll * (x0 - __ldg(a.x + qm));
+      const float ulo = __ldg(a.u_in[c] + q) - Ll * dp(q, qm);
       a.u_out[c][q] = ulo;
       if (a.cfl) {
         bool has;
         const long long qu = nb_up(g, c, I[c], q, st[c], has);
         float uup;
         if (has)
-          uup = __ldg(a.u_in[c] + qu) - s * __ldg(a.L[c] + qu) * (__ldg(a.x + qu) - x0);
+          uup = __ldg(a.u_in[c] + qu) - __ldg(a.L[c] + qu) * dp(qu, q);
         else
           uup = g.U[c];
         m += fmaxf(0.f, uup) + fmaxf(0.f, -ulo);
@@ -720,8 +753,8 @@ int launch_set_ic(int D, const Grid& g, int kind, double amp, float* const* u, c
 // Pass 2 (one block): pbar from the partials in a fixed order, then the band sum over
 // the body's bounding box.
 template <int D>
-__global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, const float* L0, const float* L1,
-                                                         const float* L2, double* part) {
+__global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, const double* p64, const float* L0,
+                                                         const float* L1, const float* L2, double* part) {
   __shared__ double sh[9];
   const float* L[3] = {L0, L1, L2};
   const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
@@ -740,7 +773,7 @@ __global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, 
       dg += (has ? L[c][qu] : 0.f) + L[c][q];
     }
     if (dg > 0.f) {
-      sp += (double)p[q];
+      sp += p64 ? p64[q] : (double)p[q];
       sc += 1.0;
     }
   }
@@ -753,7 +786,8 @@ __global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, 
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float* p, const double* part, int npart,
+__global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float* p, const double* p64,
+                                                      const double* part, int npart,
                                                       int lo0, int lo1, int lo2, int bx, int by, int bz,
                                                       double* out) {
   __shared__ double sh[9];
@@ -776,7 +810,8 @@ __global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float
     const double d = body_sdf<D>(b, x, n);
     if (!(fabs(d) < b.eps)) continue;
     const double K = (1.0 + cospi(d / b.eps)) / (2.0 * b.eps);
-    const double pp = (double)p[cell_index(g, i, j, k)] - pbar;
+    const long long q = cell_index(g, i, j, k);
+    const double pp = (p64 ? p64[q] : (double)p[q]) - pbar;
 #pragma unroll
     for (int dd = 0; dd < D; ++dd) F[dd] -= pp * n[dd] * K;
   }
@@ -787,12 +822,12 @@ __global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float
   if (threadIdx.x == 0) out[3] = pbar;
 }
 
-int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* const* L, double* partials,
-                  int npart, double* out, cudaStream_t s) {
+int launch_forces(int D, const Grid& g, const Body& b, const float* p, const double* p64, const float* const* L,
+                  double* partials, int npart, double* out, cudaStream_t s) {
   if (D == 3)
-    k_force_partials<3><<<npart, 256, 0, s>>>(g, p, L[0], L[1], L[2], partials);
+    k_force_partials<3><<<npart, 256, 0, s>>>(g, p, p64, L[0], L[1], L[2], partials);
   else
-    k_force_partials<2><<<npart, 256, 0, s>>>(g, p, L[0], L[1], L[1], partials);
+    k_force_partials<2><<<npart, 256, 0, s>>>(g, p, p64, L[0], L[1], L[1], partials);
   double ext = b.r1 + b.eps + 1.0;
   if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 1.0;
   int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
@@ -807,9 +842,9 @@ int launch_forces(int D, const Grid& g, const Body& b, const float* p, const flo
   }
   const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
   if (D == 3)
-    k_force_final<3><<<1, 256, 0, s>>>(g, b, p, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
+    k_force_final<3><<<1, 256, 0, s>>>(g, b, p, p64, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
   else
-    k_force_final<2><<<1, 256, 0, s>>>(g, b, p, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
+    k_force_final<2><<<1, 256, 0, s>>>(g, b, p, p64, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
   return 0;
 }
 
@@ -840,6 +875,173 @@ int launch_fix_bfaces(int D, const Grid& g, float* const* u, cudaStream_t s) {
     k_fix_bfaces<3><<<nb, 256, 0, s>>>(g, u[0], u[1], u[2]);
   else
     k_fix_bfaces<2><<<nb, 256, 0, s>>>(g, u[0], u[1], u[1]);
+  return 0;
+}
+
+}  // namespace wl
+
+namespace wl {
+
+// Column j of the pseudo-inverse of the coarsest operator: G e_j = the zero-mean
+// solution of A x = e_j - (1/n_active) 1 over the active cells (0 for an inactive
+// column), by FP64 Jacobi-preconditioned CG in shared memory, one block per column.
+// Built once per sim; applying it is then a small FP64 matrix-vector product.
+template <int D>
+__global__ void __launch_bounds__(256) k_build_pinv(DenseArgs a) {
+  extern __shared__ double sm[];
+  __shared__ double sh[9];
+  const Grid& g = a.g;
+  const int nc = (int)g.nc;
+  double* xr = sm;
+  double* rr = sm + nc;
+  double* pr = sm + 2 * nc;
+  double* ap = sm + 3 * nc;
+  double* dgv = sm + 4 * nc;
+  const int j = blockIdx.x;
+  const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+  auto coords = [&](long long q, int* I) {
+    I[0] = (int)(q % g.n[0]);
+    long long t = q / g.n[0];
+    I[1] = (int)(t % g.n[1]);
+    I[2] = (int)(t / g.n[1]);
+  };
+  double cnt = 0.0;
+  for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+    int I[3];
+    coords(q, I);
+    double dg = 0.0;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      dg += (has ? (double)a.L[c][qu] : 0.0) + (double)a.L[c][q];
+    }
+    dgv[q] = dg;
+    xr[q] = 0.0;
+    cnt += dg > 0.0 ? 1.0 : 0.0;
+  }
+  cnt = block_sum_d(cnt, sh);
+  if (!(dgv[j] > 0.0) || cnt <= 1.0) {
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) a.G[(long long)j * nc + q] = 0.0;
+    return;
+  }
+  // B = -A, c = -(e_j - 1/n) on active cells
+  double rz = 0.0, bb = 0.0;
+  for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+    if (dgv[q] > 0.0) {
+      const double r = -((q == j ? 1.0 : 0.0) - 1.0 / cnt);
+      rr[q] = r;
+      pr[q] = r / dgv[q];
+      rz += r * pr[q];
+      bb += r * r;
+    } else {
+      rr[q] = 0.0;
+      pr[q] = 0.0;
+    }
+  }
+  rz = block_sum_d(rz, sh);
+  bb = block_sum_d(bb, sh);
+  const int maxit = 4 * nc + 100;
+  for (int it = 0; it < maxit; ++it) {
+    __syncthreads();
+    double pap = 0.0;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      double sv = 0.0;
+      if (dgv[q] > 0.0) {
+        int I[3];
+        coords(q, I);
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+          bool has;
+          const long long qu = nb_up(g, c, I[c], q, st[c], has);
+          const long long qm = nb_dn(g, c, I[c], q, st[c]);
+          const double Lu = has ? (double)a.L[c][qu] : 0.0;
+          const double Ll = (double)a.L[c][q];
+          sv += Lu * (pr[q] - pr[qu]) + Ll * (pr[q] - pr[qm]);
+        }
+      }
+      ap[q] = sv;
+      pap += pr[q] * sv;
+    }
+    pap = block_sum_d(pap, sh);
+    if (!(pap > 0.0)) break;
+    const double alpha = rz / pap;
+    double r2 = 0.0;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      xr[q] += alpha * pr[q];
+      rr[q] -= alpha * ap[q];
+      r2 += rr[q] * rr[q];
+    }
+    r2 = block_sum_d(r2, sh);
+    if (r2 <= 1e-28 * bb) break;
+    double rz2 = 0.0;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) {
+      const double zz = dgv[q] > 0.0 ? rr[q] / dgv[q] : 0.0;
+      ap[q] = zz;
+      rz2 += rr[q] * zz;
+    }
+    rz2 = block_sum_d(rz2, sh);
+    const double beta = rz2 / rz;
+    rz = rz2;
+    for (int q = threadIdx.x; q < nc; q += blockDim.x) pr[q] = ap[q] + beta * pr[q];
+  }
+  __syncthreads();
+  double xs = 0.0;
+  for (int q = threadIdx.x; q < nc; q += blockDim.x)
+    if (dgv[q] > 0.0) xs += xr[q];
+  xs = block_sum_d(xs, sh);
+  const double xm = xs / cnt;
+  for (int q = threadIdx.x; q < nc; q += blockDim.x)
+    a.G[(long long)j * nc + q] = dgv[q] > 0.0 ? xr[q] - xm : 0.0;
+}
+
+int launch_build_pinv(int D, const DenseArgs& a, cudaStream_t s) {
+  const int nc = (int)a.g.nc;
+  const size_t smem = sizeof(double) * 5 * nc;
+  if (D == 3)
+    k_build_pinv<3><<<nc, 256, smem, s>>>(a);
+  else
+    k_build_pinv<2><<<nc, 256, smem, s>>>(a);
+  return 0;
+}
+
+// Coarsest solve x = G z in FP64 (G column-major: coalesced row reads).
+__global__ void __launch_bounds__(1024) k_apply_pinv(DenseArgs a) {
+  extern __shared__ double zs[];
+  const int nc = (int)a.g.nc;
+  for (int q = threadIdx.x; q < nc; q += blockDim.x) zs[q] = (double)a.z[q];
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+    double acc = 0.0;
+    for (int jj = 0; jj < nc; ++jj) acc += __ldg(a.G + (long long)jj * nc + i) * zs[jj];
+    a.x[i] = (float)acc;
+  }
+}
+
+int launch_apply_pinv(const DenseArgs& a, cudaStream_t s) {
+  const int nc = (int)a.g.nc;
+  int nt = ((nc + 31) / 32) * 32;
+  if (nt > 1024) nt = 1024;
+  k_apply_pinv<<<1, nt, sizeof(double) * nc, s>>>(a);
+  return 0;
+}
+
+// Precision conversions of the pressure: out64 = in32 (or out64 += in32 when add),
+// out32 = in64.
+__global__ void k_convert(const float* in32, double* out64, const double* in64, float* out32, long long n, int add) {
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= n) return;
+  if (in32) out64[q] = add ? out64[q] + (double)in32[q] : (double)in32[q];
+  if (in64) out32[q] = (float)in64[q];
+}
+
+int launch_convert(const float* in32, double* out64, const double* in64, float* out32, long long n, cudaStream_t s) {
+  k_convert<<<(int)((n + 255) / 256), 256, 0, s>>>(in32, out64, in64, out32, n, 0);
+  return 0;
+}
+
+int launch_add64(const float* in32, double* out64, long long n, cudaStream_t s) {
+  k_convert<<<(int)((n + 255) / 256), 256, 0, s>>>(in32, out64, nullptr, nullptr, n, 1);
   return 0;
 }
 

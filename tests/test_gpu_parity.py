@@ -7,7 +7,7 @@ Bars (FP32 device arithmetic against FP64):
   * one multigrid V-cycle: max abs error <= 1e-5 * max|x|;
   * 10 full steps: velocity relative L2 <= 1e-5 (the stated bar), pressure
     (mean over active cells removed) relative L2 <= 2e-4 at Poisson tol 1e-6;
-    the 1e-5 pressure bar is checked at tol 1e-7 in test_pressure_parity_tight;
+    the 1e-5 pressure bar is checked at tol 5e-8 in test_pressure_parity_tight;
   * force coefficients relative <= 1e-4.
 """
 import numpy as np
@@ -179,10 +179,11 @@ def test_cylinder_10_steps_parity():
 
 
 def test_pressure_parity_tight():
-    """At Poisson tol 1e-7 the pressure meets the 1e-5 bar as well."""
+    """At Poisson tol 5e-8 (reachable with the FP64 fine-level pressure) the pressure
+    meets the 1e-5 bar as well."""
     case = dict(id="c1t", dims=(128, 64), nu=0.064, U=(1.0, 0.0), periodic=0,
                 body=dict(kind=1, center=(32.0, 32.0), radius=8.0))
-    sim, ref = make_pair(case, tol=1e-7)
+    sim, ref = make_pair(case, tol=5e-8)
     sim.step(10)
     ref.step(10, tol=1e-11)
     act = active_mask(ref)
@@ -227,3 +228,31 @@ def test_graph_and_host_loop_agree():
     assert np.array_equal(a.get(0), b.get(0))
     assert np.array_equal(a.get(1), b.get(1))
     assert a.dt == b.dt
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_precision_modes_tgv(precision):
+    """Both precision modes converge on the periodic TGV and match the oracle."""
+    N = 24
+    L = N / (2 * np.pi)
+    case = dict(id="tgvp", dims=(N, N, N), nu=L / 400.0, U=(0.0, 0.0, 0.0), periodic=7, body=None)
+    sim, ref = make_pair(case, precision=precision)
+    sim.set_ic(1, 1.0)
+    ref.set_ic(1, 1.0)
+    sim.step(3)
+    ref.step(3, tol=1e-10)
+    rc, last, tot, worst = sim.status()
+    assert rc == 0 and worst <= 1e-6
+    assert rel_l2(sim.get(0).astype(np.float64), ref.get_u()) <= 1e-5
+
+
+def test_impulsive_start_meets_tol_with_fp64_pressure():
+    """The first steps after an impulsive start carry a large pressure; with the FP64
+    fine-level pressure every projection still reaches tol 1e-6."""
+    case = dict(id="imp", dims=(96, 48, 48), nu=0.02, U=(1.0, 0.0, 0.0), periodic=0,
+                body=dict(kind=1, center=(24.0, 24.0, 24.0), radius=8.0))
+    sim, _ = make_pair(case, oracle=False)
+    for _ in range(3):
+        sim.step(1)
+        rc, last, tot, worst = sim.status()
+        assert rc == 0 and worst <= 1e-6 and max(last) < 32
