@@ -57,7 +57,8 @@ struct wl_sim {
   double* cg_work = nullptr;
   double* fpart = nullptr;
   double* fout = nullptr;
-  double* p64 = nullptr;      // precision 1: FP64 fine-level pressure
+  float* ph = nullptr;        // precision 1: fine-level pressure as the double-float ph + pl
+  float* pl = nullptr;
   float* rf = nullptr;        // precision 1: FP32 residual, right-hand side of each correction cycle
   double* G = nullptr;        // dense pseudo-inverse of the coarsest operator (small coarsest levels)
   char* ws = nullptr;
@@ -147,7 +148,8 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, char* base) {
   void* cg = cv.take(sizeof(double) * 5 * ncoarse);
   void* fp = cv.take(sizeof(double) * 2 * kForceParts);
   void* fo = cv.take(sizeof(double) * 4);
-  void* p64 = precision == 1 ? cv.take(sizeof(double) * nc) : nullptr;
+  void* ph = precision == 1 ? cv.take(sizeof(float) * nc) : nullptr;
+  void* pl = precision == 1 ? cv.take(sizeof(float) * nc) : nullptr;
   void* rf = precision == 1 ? cv.take(sizeof(float) * nc) : nullptr;
   void* G = ncoarse <= kDenseCoarse ? cv.take(sizeof(double) * ncoarse * ncoarse) : nullptr;
   if (s) {
@@ -155,7 +157,8 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, char* base) {
     s->cg_work = (double*)cg;
     s->fpart = (double*)fp;
     s->fout = (double*)fo;
-    s->p64 = (double*)p64;
+    s->ph = (float*)ph;
+    s->pl = (float*)pl;
     s->rf = (float*)rf;
     s->G = (double*)G;
     s->nlev = nlev;
@@ -183,7 +186,7 @@ StageArgs stage_args(wl_sim* s, int stage) {
     a.out[c] = s->ub[c];
   }
   a.g = s->g;
-  a.dt = &s->ds->dt;
+  a.dt = &s->ds->dtf;
   a.nu = (float)s->nu;
   a.stage = stage;
   a.advect = s->o.advect;
@@ -202,8 +205,7 @@ ResArgs res_args(wl_sim* s, int l, int mode) {
   a.g = L.g;
   if (l + 1 < s->nlev)
     for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
-  a.dt = &s->ds->dt;
-  a.w = 1.f;
+  a.inv_w = 1.f;
   a.st = s->ds;
   a.mode = mode;
   return a;
@@ -213,8 +215,9 @@ ResArgs res_args(wl_sim* s, int l, int mode) {
 void enq_proj_head(wl_sim* s, float* const* u, float w, int proj, cudaStream_t st, int use_h) {
   ResArgs a = res_args(s, 0, RES_DIVERGENCE);
   for (int c = 0; c < 3; ++c) a.u[c] = u[c];
-  a.w = w;
-  a.x64 = s->p64;
+  a.inv_w = 1.f / w;
+  a.ph = s->ph;
+  a.pl = s->pl;
   a.rout = s->rf;
   launch_residual(s->D, a, st);
   launch_decide(s->ds, s->hc[proj], use_h, 1, proj, w, s->o.tol, s->o.max_vcycles, st);
@@ -228,7 +231,7 @@ void enq_proj_head(wl_sim* s, float* const* u, float w, int proj, cudaStream_t s
 void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   LevelBuf& L = s->lev[l];
   const int P = s->o.post;
-  const bool refine = (l == 0 && s->p64);
+  const bool refine = (l == 0 && s->ph);
   SweepArgs a{};
   for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
   a.z = refine ? s->rf : L.z;
@@ -243,7 +246,8 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
     a.x_in = in;
     a.xc = (it == 0) ? s->lev[l + 1].x : nullptr;
     a.x_out = bufs[out];
-    a.p64 = (refine && it == P - 1) ? s->p64 : nullptr;
+    a.ph = (refine && it == P - 1) ? s->ph : nullptr;
+    a.pl = (refine && it == P - 1) ? s->pl : nullptr;
     launch_sweep(s->D, a, st);
     in = bufs[out];
     out ^= 1;
@@ -280,9 +284,9 @@ void enq_coarsest(wl_sim* s, int l, const float* z, float* x, cudaStream_t st) {
 void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
   const int Lv = s->nlev;
   if (Lv == 1) {  // no coarse level: solve the fine level directly
-    if (s->p64) {
+    if (s->ph) {
       enq_coarsest(s, 0, s->rf, s->lev[0].x2, st);
-      launch_add64(s->lev[0].x2, s->p64, s->g.nc, st);
+      launch_df_add(s->ph, s->pl, s->lev[0].x2, s->g.nc, st);
     } else {
       enq_coarsest(s, 0, s->lev[0].z, s->lev[0].x, st);
     }
@@ -295,7 +299,8 @@ void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
 
 ResArgs fine_residual_args(wl_sim* s) {
   ResArgs a = res_args(s, 0, RES_RESIDUAL);
-  a.x64 = s->p64;
+  a.ph = s->ph;
+  a.pl = s->pl;
   a.rout = s->rf;
   return a;
 }
@@ -314,9 +319,9 @@ void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int 
     a.L[c] = s->lev[0].L[c];
   }
   a.x = s->lev[0].x;
-  a.x64 = s->p64;
+  a.ph = s->ph;
+  a.pl = s->pl;
   a.g = s->g;
-  a.dt = &s->ds->dt;
   a.w = w;
   a.cfl = cfl;
   a.st = s->ds;
@@ -427,7 +432,8 @@ int set_dt_from_ic(wl_sim* s) {
 int reset_state(wl_sim* s) {
   WL_CUDA(s, cudaMemsetAsync(s->ds, 0, sizeof(DevState), s->st));
   WL_CUDA(s, cudaMemsetAsync(s->lev[0].x, 0, sizeof(float) * s->g.nc, s->st));
-  if (s->p64) WL_CUDA(s, cudaMemsetAsync(s->p64, 0, sizeof(double) * s->g.nc, s->st));
+  if (s->ph) WL_CUDA(s, cudaMemsetAsync(s->ph, 0, sizeof(float) * s->g.nc, s->st));
+  if (s->pl) WL_CUDA(s, cudaMemsetAsync(s->pl, 0, sizeof(float) * s->g.nc, s->st));
   return WL_OK;
 }
 
@@ -651,7 +657,8 @@ int wl_gmg_vcycle(wl_handle s, double* resid_inf_out) {
 int wl_forces(wl_handle s, double* F) {
   if (!s || !F) return WL_EINVAL;
   const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
-  launch_forces(s->D, s->g, s->body, s->lev[0].x, s->p64, L, s->fpart, kForceParts, s->fout, s->st);
+  launch_forces(s->D, s->g, s->body, s->ph ? s->ph : s->lev[0].x, s->pl, L, s->fpart, kForceParts, s->fout,
+                s->st);
   double h[4];
   WL_CUDA(s, cudaMemcpyAsync(h, s->fout, sizeof(h), cudaMemcpyDeviceToHost, s->st));
   WL_CUDA(s, cudaStreamSynchronize(s->st));
@@ -669,8 +676,8 @@ int wl_get_field(wl_handle s, int which, void* dst, int dst_is_device) {
       for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(d + c * nb, s->ua[c], nb, kind, s->st));
       break;
     case WL_FIELD_P:
-      if (s->p64) launch_convert(nullptr, nullptr, s->p64, s->lev[0].x2, s->g.nc, s->st);
-      WL_CUDA(s, cudaMemcpyAsync(d, s->p64 ? s->lev[0].x2 : s->lev[0].x, nb, kind, s->st));
+      if (s->ph) launch_df_round(s->ph, s->pl, s->lev[0].x2, s->g.nc, s->st);
+      WL_CUDA(s, cudaMemcpyAsync(d, s->ph ? s->lev[0].x2 : s->lev[0].x, nb, kind, s->st));
       break;
     case WL_FIELD_DIV: {
       ResArgs a = res_args(s, 0, RES_DIV_ONLY);
@@ -711,8 +718,8 @@ int wl_set_field(wl_handle s, int which, const void* src, int src_is_device) {
       launch_fix_bfaces(s->D, s->g, s->ua, s->st);
       break;
     case WL_FIELD_P:
-      WL_CUDA(s, cudaMemcpyAsync(s->lev[0].x, p, nb, kind, s->st));
-      if (s->p64) launch_convert(s->lev[0].x, s->p64, nullptr, nullptr, s->g.nc, s->st);
+      WL_CUDA(s, cudaMemcpyAsync(s->ph ? s->ph : s->lev[0].x, p, nb, kind, s->st));
+      if (s->pl) WL_CUDA(s, cudaMemsetAsync(s->pl, 0, nb, s->st));
       break;
     case WL_FIELD_Z:
       WL_CUDA(s, cudaMemcpyAsync(s->lev[0].z, p, nb, kind, s->st));
@@ -739,6 +746,7 @@ int wl_get_dt(wl_handle s, double* dt) {
 int wl_set_dt(wl_handle s, double dt) {
   if (!s || !(dt > 0.0) || !std::isfinite(dt)) return WL_EINVAL;
   WL_CUDA(s, cudaMemcpyAsync(&s->ds->dt, &dt, sizeof(double), cudaMemcpyHostToDevice, s->st));
+  launch_sync_dt(s->ds, s->st);
   WL_CUDA(s, cudaStreamSynchronize(s->st));
   return WL_OK;
 }

@@ -133,6 +133,8 @@ __device__ __forceinline__ double kernel_K1(double s) {
 // the device so a step never waits for the host).
 struct DevState {
   double dt;              // dt of the next step
+  float dtf;              // FP32 copies of dt and 1/dt read by the per-cell kernels
+  float inv_dtf;
   double time;            // simulated time
   long long steps;
   unsigned norm_bits;     // running max |residual| (float bits; non-negative floats order as uints)
@@ -168,6 +170,23 @@ __device__ __forceinline__ unsigned block_max_bits(unsigned v, unsigned* sh) {
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
   }
   return v;  // valid in thread 0
+}
+
+// Error-free transformations (Knuth's TwoSum; Dekker's product via FMA): s + e is
+// exactly a + b, p + e exactly a * b.  Used for the double-float pressure.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+  p = __fmul_rn(a, b);
+  e = fmaf(a, b, -p);
+}
+// renormalise hi + lo so that |lo| <= ulp(hi)/2 (requires |hi| >= |lo|)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
 }  // namespace wl

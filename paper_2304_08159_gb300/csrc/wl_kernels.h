@@ -11,7 +11,7 @@ struct StageArgs {
   const float* mu0[3];  // BDIM zeroth moment on updated faces (= Poisson coefficient there)
   float* out[3];
   Grid g;
-  const double* dt;     // device scalar
+  const float* dt;      // device scalar (FP32 copy of the step's dt)
   float nu;
   int stage;            // 1 or 2
   int advect;
@@ -20,19 +20,23 @@ struct StageArgs {
 // residual / divergence / restriction modes of k_residual
 enum { RES_RESIDUAL = 0, RES_DIVERGENCE = 1, RES_RESTRICT = 2, RES_DIV_ONLY = 3 };
 
+// The fine-level pressure of precision mode 1 is an unevaluated sum ph + pl of two
+// FP32 fields (a "double-float"); arithmetic on it uses error-free transformations,
+// so no FP64 instruction runs per cell (FP64 throughput is a small fraction of FP32
+// on this GPU).
 struct ResArgs {
   const float* u[3];   // RES_DIVERGENCE / RES_DIV_ONLY: velocity
-  const float* x;      // current unknown (RES_RESIDUAL / RES_DIVERGENCE)
-  const double* x64;   // if set: FP64 unknown used instead of x, residual in FP64
+  const float* x;      // current unknown (RES_RESIDUAL / RES_DIVERGENCE), unless ph is set
+  const float* ph;     // if set: unknown = ph + pl, residual formed in double-float
+  const float* pl;
   float* rout;         // if set: the residual is stored here (right-hand side of the correction cycle)
   const float* L[3];   // face coefficients of this level
   float* z;            // right-hand side of this level (written by the divergence modes)
   float* zc;           // restricted residual for the next level (may be null)
   Grid g;
   int cn[3];           // next level's dims
-  const double* dt;    // divergence modes: z = div u / (w dt)
-  float w;
-  DevState* st;        // receives max |residual|
+  float inv_w;         // divergence modes: z = div u * inv_w / dt
+  DevState* st;        // dt and the running max |residual|
   int mode;
 };
 
@@ -42,9 +46,11 @@ struct SweepArgs {
   const float* z;
   const float* L[3];
   float* x_out;
-  double* p64;         // if set: add the swept values into this FP64 field instead of writing x_out
+  float* ph;           // if set: add the swept values into the double-float field ph + pl
+  float* pl;           //   instead of writing x_out
   Grid g;
   int cn[3];
+  int tz;              // planes per block (3-D)
 };
 
 // Dense pseudo-inverse of the coarsest operator (column-major, FP64), used when the
@@ -71,14 +77,14 @@ struct CoarseArgs {
 struct CorrArgs {
   const float* u_in[3];
   float* u_out[3];
-  const float* x;      // pressure p
-  const double* x64;   // if set: FP64 pressure used instead of x
+  const float* x;      // pressure p (plain FP32), unless ph is set
+  const float* ph;     // double-float pressure ph + pl
+  const float* pl;
   const float* L[3];
   Grid g;
-  const double* dt;
   float w;
   int cfl;             // also accumulate the CFL out-flux maximum
-  DevState* st;
+  DevState* st;        // dt and the CFL maximum
 };
 
 int launch_stage(int D, const StageArgs& a, const Body& b, cudaStream_t s);
@@ -94,12 +100,15 @@ int launch_coarsen(int D, const Grid& fine, const float* const* Lf, const Grid& 
                    cudaStream_t s);
 int launch_set_ic(int D, const Grid& g, int kind, double amp, float* const* u, cudaStream_t s);
 int launch_cfl_only(int D, const Grid& g, const float* const* u, DevState* st, cudaStream_t s);
-int launch_forces(int D, const Grid& g, const Body& b, const float* p, const double* p64, const float* const* L,
+int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* pl, const float* const* L,
                   double* partials, int npart, double* out, cudaStream_t s);
 int launch_build_pinv(int D, const DenseArgs& a, cudaStream_t s);
 int launch_apply_pinv(const DenseArgs& a, cudaStream_t s);
-int launch_convert(const float* in32, double* out64, const double* in64, float* out32, long long n, cudaStream_t s);
-int launch_add64(const float* in32, double* out64, long long n, cudaStream_t s);
+// ph + pl -> out (FP32 rounding of the double-float pressure)
+int launch_df_round(const float* ph, const float* pl, float* out, long long n, cudaStream_t s);
+// (ph, pl) += e (double-float accumulate)
+int launch_df_add(float* ph, float* pl, const float* e, long long n, cudaStream_t s);
+int launch_sync_dt(DevState* st, cudaStream_t s);
 
 }  // namespace wl
 

@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
   const int k1 = (D == 3) ? min(k0 + ST_TZ, g.n[2]) : 1;
   const int i = i0 + tx, j = j0 + ty;
   const bool own = (i < g.n[0]) && (j < g.n[1]);
-  const float dt = (float)(*a.dt);
+  const float dt = *a.dt;
   const bool adv = a.advect != 0;
   const float nu = a.nu;
 
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0,
   const double d = body_sdf<D>(b, x, nrm);
   if (!(fabs(d) < b.eps)) return;
   const double k1 = b.eps * kernel_K1(d / b.eps);
-  const float dt = (float)(*a.dt);
+  const float dt = *a.dt;
   float acc = 0.f;
 #pragma unroll
   for (int jd = 0; jd < D; ++jd) {

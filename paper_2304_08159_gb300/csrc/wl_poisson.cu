@@ -52,106 +52,122 @@ __device__ __forceinline__ long long nb_dn(const Grid& g, int c, int Ic, long lo
 //   RES_RESIDUAL:   r = z - A x, max|r|, restrict r
 //   RES_RESTRICT:   restrict z (coarse levels whose iterate is still zero)
 //   RES_DIV_ONLY:   z = div(u) (raw, for inspection)
-// Block = 32 x 4 x 2 cells (3-D) or 32 x 8 (2-D), so each block holds whole 2^D
-// families of children for the restriction.
+// A block is 32 x 8 cell columns walking RS_ZP pairs of planes (3-D), so each
+// block holds whole 2^D families of children for the restriction (the z pair is
+// summed in registers, x pairs by a shuffle, y pairs through shared memory) and
+// issues a single atomic for the norm.
+constexpr int RS_ZP = 8;
+
+template <int D>
+__device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, int k, unsigned& mbits) {
+  const Grid& g = a.g;
+  const long long q = cell_index(g, i, j, k);
+  const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+  const int I[3] = {i, j, k};
+  float z;
+  if (a.mode == RES_DIVERGENCE || a.mode == RES_DIV_ONLY) {
+    float div = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      const float up = has ? __ldg(a.u[c] + qu) : g.U[c];
+      div += up - __ldg(a.u[c] + q);
+    }
+    z = (a.mode == RES_DIV_ONLY) ? div : div * a.inv_w * a.st->inv_dtf;
+    a.z[q] = z;
+    if (a.mode == RES_DIV_ONLY) return 0.f;
+  } else {
+    z = a.z[q];
+  }
+  if (a.mode == RES_RESTRICT) return z;
+  float r;
+  if (a.ph) {
+    // r = z - sum_f L_f (p_nb - p_0) with p = ph + pl in double-float arithmetic
+    const float h0 = __ldg(a.ph + q), l0 = __ldg(a.pl + q);
+    float ah = 0.f, al = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      const long long qm = nb_dn(g, c, I[c], q, st[c]);
+      const float Lf[2] = {has ? __ldg(a.L[c] + qu) : 0.f, __ldg(a.L[c] + q)};
+      const long long qn[2] = {qu, qm};
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        float dh, dl, th, tl, sh, sl;
+        two_sum(__ldg(a.ph + qn[sd]), -h0, dh, dl);
+        dl += __ldg(a.pl + qn[sd]) - l0;
+        two_prod(Lf[sd], dh, th, tl);
+        tl = fmaf(Lf[sd], dl, tl);
+        two_sum(ah, th, sh, sl);
+        ah = sh;
+        al += sl + tl;
+      }
+    }
+    float rh, rl;
+    two_sum(z, -ah, rh, rl);
+    r = rh + (rl - al);
+  } else {
+    const float x0 = __ldg(a.x + q);
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      bool has;
+      const long long qu = nb_up(g, c, I[c], q, st[c], has);
+      const long long qm = nb_dn(g, c, I[c], q, st[c]);
+      const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
+      const float Ll = __ldg(a.L[c] + q);
+      acc += Lu * (__ldg(a.x + qu) - x0) + Ll * (__ldg(a.x + qm) - x0);
+    }
+    r = z - acc;
+  }
+  if (a.rout) a.rout[q] = r;
+  mbits = max(mbits, __float_as_uint(fabsf(r)));
+  return r;
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
-  __shared__ float s_r[256];
+  __shared__ float s_r[8][32];
   __shared__ unsigned s_m[8];
   const Grid& g = a.g;
-  const int tid = threadIdx.x;
-  int tx, ty, tz;
-  cell_coords(D, 0, tid, tx, ty, tz);
-  const int i = blockIdx.x * 32 + tx;
-  const int j = blockIdx.y * (D == 3 ? 4 : 8) + ty;
-  const int k = (D == 3) ? blockIdx.z * 2 + tz : 0;
-  const bool in = i < g.n[0] && j < g.n[1] && k < g.n[2];
-  float v = 0.f;
-  if (in) {
-    const long long q = cell_index(g, i, j, k);
-    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
-    const int I[3] = {i, j, k};
-    float z;
-    if (a.mode == RES_DIVERGENCE || a.mode == RES_DIV_ONLY) {
-      float div = 0.f;
-#pragma unroll
-      for (int c = 0; c < D; ++c) {
-        bool has;
-        const long long qu = nb_up(g, c, I[c], q, st[c], has);
-        const float up = (I[c] + 1 < g.n[c] || has) ? __ldg(a.u[c] + qu) : g.U[c];
-        div += up - __ldg(a.u[c] + q);
-      }
-      z = (a.mode == RES_DIV_ONLY) ? div : (float)((double)div / ((double)a.w * *a.dt));
-      a.z[q] = z;
-    } else {
-      z = a.z[q];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int i = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + ty;
+  const bool inxy = i < g.n[0] && j < g.n[1];
+  const int kb = (D == 3) ? blockIdx.z * 2 * RS_ZP : 0;
+  const int ke = (D == 3) ? min(kb + 2 * RS_ZP, g.n[2]) : 1;
+  unsigned mbits = 0u;
+  for (int k = kb; k < ke; k += (D == 3 ? 2 : 1)) {
+    float v = 0.f;
+    if (inxy) {
+      v = residual_cell<D>(a, i, j, k, mbits);
+      if (D == 3 && k + 1 < ke) v += residual_cell<D>(a, i, j, k + 1, mbits);
     }
-    if (a.mode == RES_RESTRICT) {
-      v = z;
-    } else if (a.mode != RES_DIV_ONLY) {
-      if (a.x64) {
-        // FP64 unknown (iterative refinement): the residual is formed in FP64
-        const double x0 = __ldg(a.x64 + q);
-        double acc = 0.0;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          bool has;
-          const long long qu = nb_up(g, c, I[c], q, st[c], has);
-          const long long qm = nb_dn(g, c, I[c], q, st[c]);
-          const double Lu = has ? (double)__ldg(a.L[c] + qu) : 0.0;
-          const double Ll = (double)__ldg(a.L[c] + q);
-          acc += Lu * (__ldg(a.x64 + qu) - x0) + Ll * (__ldg(a.x64 + qm) - x0);
-        }
-        v = (float)((double)z - acc);
-      } else {
-        const float x0 = __ldg(a.x + q);
-        float acc = 0.f;
-#pragma unroll
-        for (int c = 0; c < D; ++c) {
-          bool has;
-          const long long qu = nb_up(g, c, I[c], q, st[c], has);
-          const long long qm = nb_dn(g, c, I[c], q, st[c]);
-          const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
-          const float Ll = __ldg(a.L[c] + q);
-          acc += Lu * (__ldg(a.x + qu) - x0) + Ll * (__ldg(a.x + qm) - x0);
-        }
-        v = z - acc;
-      }
-      if (a.rout) a.rout[q] = v;
-    }
-  }
-  if (a.mode == RES_RESIDUAL || a.mode == RES_DIVERGENCE) {
-    const unsigned m = block_max_bits<256>(__float_as_uint(fabsf(v)), s_m);
-    if (tid == 0 && m) atomicMax(&a.st->norm_bits, m);
-  }
-  if (a.zc) {
-    const float w2 = v + __shfl_xor_sync(0xffffffffu, v, 1);
-    s_r[tid] = w2;
-    __syncthreads();
-    if (D == 3) {
-      if (tid < 32) {
+    if (a.zc) {
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      s_r[ty][tx] = v;
+      __syncthreads();
+      if (tid < 64) {
         const int cx = tid & 15, cy = tid >> 4;
-        const float sum = (s_r[2 * cx + 32 * (2 * cy)] + s_r[2 * cx + 32 * (2 * cy + 1)]) +
-                          (s_r[2 * cx + 32 * (2 * cy + 4)] + s_r[2 * cx + 32 * (2 * cy + 5)]);
-        const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 2 + cy, K = blockIdx.z;
+        const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
+        const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 4 + cy, K = (D == 3) ? (k >> 1) : 0;
         if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
           a.zc[(long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K)] = sum;
       }
-    } else {
-      if (tid < 64) {
-        const int cx = tid & 15, cy = tid >> 4;
-        const float sum = s_r[2 * cx + 32 * (2 * cy)] + s_r[2 * cx + 32 * (2 * cy + 1)];
-        const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 4 + cy;
-        if (I < a.cn[0] && J < a.cn[1]) a.zc[(long long)I + (long long)a.cn[0] * J] = sum;
-      }
+      __syncthreads();
     }
+  }
+  if (a.mode == RES_RESIDUAL || a.mode == RES_DIVERGENCE) {
+    const unsigned m = block_max_bits<256>(mbits, s_m);
+    if (tid == 0 && m) atomicMax(&a.st->norm_bits, m);
   }
 }
 
 int launch_residual(int D, const ResArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
   if (D == 3) {
-    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + 1) / 2);
+    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + 2 * RS_ZP - 1) / (2 * RS_ZP));
     k_residual<3><<<grd, 256, 0, s>>>(a);
   } else {
     dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
@@ -163,14 +179,24 @@ int launch_residual(int D, const ResArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // k_sweep: one red-black Gauss-Seidel sweep (all red cells, then all black cells),
 // out of place (x_in -> x_out), with the prolongation of a coarse correction fused
-// into the read of x_in.  A tile of 64 x 8 cells marches up through SW_TZ planes;
+// into the read of x_in.  A tile of 64 x 8 cells marches up through `tz` planes;
 // planes k-1..k+2 of the iterate (2-cell in-plane halo) sit in a 4-plane shared ring.
 // At plane k: red cells of plane k+1 are relaxed on the tile plus a 1-cell halo
 // (using old black values), then black cells of plane k on the tile (using the new
 // red values), and plane k is written.  Halo red cells are recomputed by every tile
-// that needs them, from the same inputs, so tiles never exchange data.
-constexpr int SW_TX = 64, SW_TY = 8, SW_TZ = 32;
+// that needs them, from the same inputs, so tiles never exchange data.  All global
+// loads of an iteration (the new plane of the iterate and the coefficients and
+// right-hand side of the cells relaxed in it) are issued together, before the
+// first barrier, so each plane pays one memory latency.
+constexpr int SW_TX = 64, SW_TY = 8;
 constexpr int SW_HX = SW_TX + 4, SW_HY = SW_TY + 4;
+constexpr int SW_RED = (SW_TY + 2) * (SW_TX + 2) / 2;  // red cells of the tile plus halo, per plane
+constexpr int SW_LOADS = (SW_HY * SW_HX + 255) / 256;
+
+struct RelaxIn {
+  float z, Lu[3], Ll[3];
+  bool ok;
+};
 
 template <int D>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
@@ -179,8 +205,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const Grid& g = a.g;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int i0 = blockIdx.x * SW_TX, j0 = blockIdx.y * SW_TY;
-  const int k0 = (D == 3) ? blockIdx.z * SW_TZ : 0;
-  const int k1 = (D == 3) ? min(k0 + SW_TZ, g.n[2]) : 1;
+  const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
+  const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
   const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
 
   auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
@@ -195,63 +221,76 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     }
     return true;
   };
-  auto load_plane = [&](int kk) {
-    const int sl = slot(kk);
-    for (int e = tid; e < SW_HY * SW_HX; e += 256) {
-      const int row = e / SW_HX, col = e - row * SW_HX;
-      int I[3] = {i0 - 2 + col, j0 - 2 + row, D == 3 ? kk : 0};
-      float v = 0.f;
-      if (map(I)) {
-        const long long q = cell_index(g, I[0], I[1], I[2]);
-        if (a.x_in) v = __ldg(a.x_in + q);
-        if (a.xc)
-          v += __ldg(a.xc + (long long)(I[0] >> 1) +
-                     (long long)a.cn[0] * ((long long)(I[1] >> 1) + (long long)a.cn[1] * (D == 3 ? (I[2] >> 1) : 0)));
-      }
-      s_x[sl][row][col] = v;
+  // iterate value at tile position (col, row) of plane kk (with the prolonged correction)
+  auto xeff = [&](int col, int row, int kk) -> float {
+    int I[3] = {i0 - 2 + col, j0 - 2 + row, D == 3 ? kk : 0};
+    float v = 0.f;
+    if (map(I)) {
+      const long long q = cell_index(g, I[0], I[1], I[2]);
+      if (a.x_in) v = __ldg(a.x_in + q);
+      if (a.xc)
+        v += __ldg(a.xc + (long long)(I[0] >> 1) +
+                   (long long)a.cn[0] * ((long long)(I[1] >> 1) + (long long)a.cn[1] * (D == 3 ? (I[2] >> 1) : 0)));
+    }
+    return v;
+  };
+  // right-hand side and face coefficients of the cell at tile position (ii, jj), plane kk
+  auto fetch = [&](int ii, int jj, int kk, RelaxIn& c) {
+    int I[3] = {i0 + ii, j0 + jj, D == 3 ? kk : 0};
+    c.ok = map(I);
+    if (!c.ok) return;
+    const long long q = cell_index(g, I[0], I[1], I[2]);
+    c.z = __ldg(a.z + q);
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      bool has;
+      const long long qu = nb_up(g, d, I[d], q, st[d], has);
+      c.Lu[d] = has ? __ldg(a.L[d] + qu) : 0.f;
+      c.Ll[d] = __ldg(a.L[d] + q);
     }
   };
-  // Gauss-Seidel value of the cell at tile position (ii, jj) of plane kk from the
-  // shared neighbours; false when the cell lies outside a non-periodic side.
-  auto relax = [&](int ii, int jj, int kk, float& out) -> bool {
-    int I[3] = {i0 + ii, j0 + jj, D == 3 ? kk : 0};
-    if (!map(I)) return false;
-    const long long q = cell_index(g, I[0], I[1], I[2]);
+  // Gauss-Seidel value from the shared neighbours (0 for a cell with no equation)
+  auto relax = [&](const RelaxIn& c, int ii, int jj, int kk) -> float {
     const int sl = slot(kk);
     float sum = 0.f, dg = 0.f;
 #pragma unroll
-    for (int c = 0; c < D; ++c) {
-      bool has;
-      const long long qu = nb_up(g, c, I[c], q, st[c], has);
-      const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
-      const float Ll = __ldg(a.L[c] + q);
+    for (int d = 0; d < D; ++d) {
       float xu, xd;
-      if (c == 0) {
+      if (d == 0) {
         xu = s_x[sl][jj + 2][ii + 3];
         xd = s_x[sl][jj + 2][ii + 1];
-      } else if (c == 1) {
+      } else if (d == 1) {
         xu = s_x[sl][jj + 3][ii + 2];
         xd = s_x[sl][jj + 1][ii + 2];
       } else {
         xu = s_x[slot(kk + 1)][jj + 2][ii + 2];
         xd = s_x[slot(kk - 1)][jj + 2][ii + 2];
       }
-      sum += Lu * xu + Ll * xd;
-      dg += Lu + Ll;
+      sum += c.Lu[d] * xu + c.Ll[d] * xd;
+      dg += c.Lu[d] + c.Ll[d];
     }
-    out = (dg > 0.f) ? (sum - __ldg(a.z + q)) / dg : 0.f;
-    return true;
+    return (dg > 0.f) ? (sum - c.z) / dg : 0.f;
   };
-  auto red_phase = [&](int kr) {
-    const int sl = slot(kr);
+  auto red_pos = [&](int e, int kr, int& ii, int& jj) {
     constexpr int RW = (SW_TX + 2) / 2;
-    for (int e = tid; e < (SW_TY + 2) * RW; e += 256) {
-      const int row = e / RW, m = e - row * RW;
-      const int jj = row - 1;
-      const int o = (i0 - 1 + j0 + jj + kr) & 1;
-      const int ii = -1 + 2 * m + o;
-      float v;
-      if (relax(ii, jj, kr, v)) s_x[sl][jj + 2][ii + 2] = v;
+    const int row = e / RW, m = e - row * RW;
+    jj = row - 1;
+    ii = -1 + 2 * m + ((i0 - 1 + j0 + jj + kr) & 1);
+  };
+  // load a whole plane of the iterate into the ring (prologue)
+  auto load_plane = [&](int kk) {
+    for (int e = tid; e < SW_HY * SW_HX; e += 256) {
+      const int row = e / SW_HX, col = e - row * SW_HX;
+      s_x[slot(kk)][row][col] = xeff(col, row, kk);
+    }
+  };
+  auto red_plane = [&](int kr) {
+    for (int e = tid; e < SW_RED; e += 256) {
+      int ii, jj;
+      red_pos(e, kr, ii, jj);
+      RelaxIn c;
+      fetch(ii, jj, kr, c);
+      if (c.ok) s_x[slot(kr)][jj + 2][ii + 2] = relax(c, ii, jj, kr);
     }
   };
 
@@ -261,45 +300,76 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     load_plane(k0);
     load_plane(k0 + 1);
     __syncthreads();
-    red_phase(k0 - 1);
-    red_phase(k0);
+    red_plane(k0 - 1);
+    red_plane(k0);
     __syncthreads();
   }
+  const int P0 = (i0 + j0 + ty) & 1;  // parity of column 2*tx in plane 0
   for (int k = k0; k < k1; ++k) {
-    if (D == 3) {
-      load_plane(k + 2);
-      __syncthreads();
-      red_phase(k + 1);
-    } else {
-      load_plane(0);
-      __syncthreads();
-      red_phase(0);
+    // ---- issue every global load of this iteration
+    float xv[SW_LOADS];
+    const int kn = (D == 3) ? k + 2 : 0;
+#pragma unroll
+    for (int m = 0; m < SW_LOADS; ++m) {
+      const int e = tid + 256 * m;
+      xv[m] = 0.f;
+      if (e < SW_HY * SW_HX) {
+        const int row = e / SW_HX, col = e - row * SW_HX;
+        xv[m] = xeff(col, row, kn);
+      }
+    }
+    const int kr = (D == 3) ? k + 1 : 0;
+    RelaxIn rc[2];
+    int rii[2], rjj[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int e = tid + 256 * m;
+      rc[m].ok = false;
+      if (e < SW_RED) {
+        red_pos(e, kr, rii[m], rjj[m]);
+        fetch(rii[m], rjj[m], kr, rc[m]);
+      }
+    }
+    const int P = (P0 + k) & 1;
+    const int ib = 2 * tx + (P ^ 1), ir = 2 * tx + P;
+    RelaxIn bc;
+    bc.ok = false;
+    if (i0 + ib < g.n[0] && j0 + ty < g.n[1]) fetch(ib, ty, k, bc);
+    // ---- new plane into the ring (2-D: the only plane)
+#pragma unroll
+    for (int m = 0; m < SW_LOADS; ++m) {
+      const int e = tid + 256 * m;
+      if (e < SW_HY * SW_HX) {
+        const int row = e / SW_HX, col = e - row * SW_HX;
+        s_x[slot(kn)][row][col] = xv[m];
+      }
     }
     __syncthreads();
-    // black cells of plane k on the tile, one per thread
-    const int P = (i0 + j0 + ty + k) & 1;  // parity of cell 2*tx
-    const int ib = 2 * tx + (P ^ 1);
-    const int gj = j0 + ty;
-    float vb = 0.f;
-    bool okb = false;
-    if (i0 + ib < g.n[0] && gj < g.n[1]) okb = relax(ib, ty, k, vb);
-    const int ir = 2 * tx + P;
+    // ---- red cells of plane kr on the tile plus halo
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+      if (rc[m].ok) s_x[slot(kr)][rjj[m] + 2][rii[m] + 2] = relax(rc[m], rii[m], rjj[m], kr);
+    __syncthreads();
+    // ---- black cells of plane k on the tile, one per thread; write plane k
+    const float vb = bc.ok ? relax(bc, ib, ty, k) : 0.f;
     const float vr = s_x[slot(k)][ty + 2][ir + 2];
-    const int gi = i0 + 2 * tx;
+    const int gi = i0 + 2 * tx, gj = j0 + ty;
     if (gj < g.n[1]) {
       const long long q = cell_index(g, gi, gj, D == 3 ? k : 0);
       const float v0 = P ? vb : vr, v1 = P ? vr : vb;
       const bool pair = gi + 1 < g.n[0] && ((g.n[0] & 1) == 0);
-      if (a.p64) {
-        // last sweep of a correction cycle: fold the correction into the FP64 field
-        if (pair) {
-          double2 o = reinterpret_cast<double2*>(a.p64 + q)[0];
-          o.x += (double)v0;
-          o.y += (double)v1;
-          reinterpret_cast<double2*>(a.p64 + q)[0] = o;
-        } else {
-          if (gi < g.n[0]) a.p64[q] += (double)v0;
-          if (gi + 1 < g.n[0]) a.p64[q + 1] += (double)v1;
+      if (a.ph) {
+        // last sweep of a correction cycle: fold the correction into ph + pl
+        const float vv[2] = {v0, v1};
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (gi + t >= g.n[0]) continue;
+          float sh, sl, nh, nl;
+          two_sum(a.ph[q + t], vv[t], sh, sl);
+          sl += a.pl[q + t];
+          fast_two_sum(sh, sl, nh, nl);
+          a.ph[q + t] = nh;
+          a.pl[q + t] = nl;
         }
       } else if (pair) {
         reinterpret_cast<float2*>(a.x_out + q)[0] = make_float2(v0, v1);
@@ -308,17 +378,23 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         if (gi + 1 < g.n[0]) a.x_out[q + 1] = v1;
       }
     }
-    (void)okb;
     __syncthreads();
   }
 }
 
-int launch_sweep(int D, const SweepArgs& a, cudaStream_t s) {
+int launch_sweep(int D, const SweepArgs& a_in, cudaStream_t s) {
+  SweepArgs a = a_in;
   const Grid& g = a.g;
   if (D == 3) {
-    dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, (g.n[2] + SW_TZ - 1) / SW_TZ);
+    // planes per block: enough blocks to fill the GPU, at most 32 planes per march
+    const long long tiles = (long long)((g.n[0] + SW_TX - 1) / SW_TX) * ((g.n[1] + SW_TY - 1) / SW_TY);
+    int tz = (int)((tiles * g.n[2] + 1215) / 1216);
+    tz = tz < 2 ? 2 : (tz > 32 ? 32 : tz);
+    a.tz = tz;
+    dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, (g.n[2] + tz - 1) / tz);
     k_sweep<3><<<grd, 256, 0, s>>>(a);
   } else {
+    a.tz = 1;
     dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, 1);
     k_sweep<2><<<grd, 256, 0, s>>>(a);
   }
@@ -468,46 +544,46 @@ int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s) {
 // k_correct: u_c[I] -= w dt L_c[I] (p[I] - p[I-e_c]) (the pressure-gradient loop of
 // Section 2, all components in one pass) and, after the last projection of a step,
 // the CFL out-flux max_I sum_c max(0, u_c[I+e_c]) + max(0, -u_c[I]) of the corrected
-// field (upper faces corrected on the fly, so no second pass).
+// field (upper faces corrected on the fly, so no second pass).  32 x 8 columns per
+// block walking CR_Z planes; one atomic per block.
+constexpr int CR_Z = 16;
+
 template <int D>
 __global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
   __shared__ unsigned s_m[8];
   const Grid& g = a.g;
-  const int tid = threadIdx.x;
-  int tx, ty, tz;
-  cell_coords(D, 0, tid, tx, ty, tz);
-  const int i = blockIdx.x * 32 + tx;
-  const int j = blockIdx.y * (D == 3 ? 4 : 8) + ty;
-  const int k = (D == 3) ? blockIdx.z * 2 + tz : 0;
-  const bool in = i < g.n[0] && j < g.n[1] && k < g.n[2];
-  const double sd = (double)a.w * *a.dt;
-  const float s = (float)sd;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int i = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + ty;
+  const bool inxy = i < g.n[0] && j < g.n[1];
+  const int kb = (D == 3) ? blockIdx.z * CR_Z : 0;
+  const int ke = (D == 3) ? min(kb + CR_Z, g.n[2]) : 1;
+  const float s = a.w * a.st->dtf;
+  const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+  // pressure difference p[qa] - p[qb]; for the double-float pressure the hi parts
+  // are subtracted first (exact when they are within a factor 2 of each other)
+  auto dp = [&](long long qa, long long qb) -> float {
+    if (a.ph) return (__ldg(a.ph + qa) - __ldg(a.ph + qb)) + (__ldg(a.pl + qa) - __ldg(a.pl + qb));
+    return __ldg(a.x + qa) - __ldg(a.x + qb);
+  };
   float m = 0.f;
-  if (in) {
+  for (int k = kb; k < ke && inxy; ++k) {
     const long long q = cell_index(g, i, j, k);
-    const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
     const int I[3] = {i, j, k};
-    // pressure difference across a face, from the FP64 field when there is one
-    auto dp = [&](long long qa, long long qb) -> float {
-      return a.x64 ? (float)(sd * (__ldg(a.x64 + qa) - __ldg(a.x64 + qb))) : s * (__ldg(a.x + qa) - __ldg(a.x + qb));
-    };
+    float mc = 0.f;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       const long long qm = nb_dn(g, c, I[c], q, st[c]);
       const float Ll = __ldg(a.L[c] + q);
-      const float ulo = __ldg(a.u_in[c] + q) - Ll * dp(q, qm);
+      const float ulo = __ldg(a.u_in[c] + q) - s * Ll * dp(q, qm);
       a.u_out[c][q] = ulo;
       if (a.cfl) {
         bool has;
         const long long qu = nb_up(g, c, I[c], q, st[c], has);
-        float uup;
-        if (has)
-          uup = __ldg(a.u_in[c] + qu) - __ldg(a.L[c] + qu) * dp(qu, q);
-        else
-          uup = g.U[c];
-        m += fmaxf(0.f, uup) + fmaxf(0.f, -ulo);
+        const float uup = has ? __ldg(a.u_in[c] + qu) - s * __ldg(a.L[c] + qu) * dp(qu, q) : g.U[c];
+        mc += fmaxf(0.f, uup) + fmaxf(0.f, -ulo);
       }
     }
+    m = fmaxf(m, mc);
   }
   if (a.cfl) {
     const unsigned mb = block_max_bits<256>(__float_as_uint(fabsf(m)), s_m);
@@ -518,7 +594,7 @@ __global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
 int launch_correct(int D, const CorrArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
   if (D == 3) {
-    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 3) / 4, (g.n[2] + 1) / 2);
+    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + CR_Z - 1) / CR_Z);
     k_correct<3><<<grd, 256, 0, s>>>(a);
   } else {
     dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
@@ -619,7 +695,20 @@ __global__ void k_step_end(DevState* st, int D, double nu, double dt_cap, double
     dn = used;
   }
   st->dt = dn;
+  st->dtf = (float)dn;
+  st->inv_dtf = (float)(1.0 / dn);
   st->cfl_bits = 0u;
+}
+
+// refresh the FP32 copies after the host wrote dt
+__global__ void k_sync_dt(DevState* st) {
+  st->dtf = (float)st->dt;
+  st->inv_dtf = (float)(1.0 / st->dt);
+}
+
+int launch_sync_dt(DevState* st, cudaStream_t s) {
+  k_sync_dt<<<1, 1, 0, s>>>(st);
+  return 0;
 }
 
 int launch_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s) {
@@ -753,7 +842,7 @@ int launch_set_ic(int D, const Grid& g, int kind, double amp, float* const* u, c
 // Pass 2 (one block): pbar from the partials in a fixed order, then the band sum over
 // the body's bounding box.
 template <int D>
-__global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, const double* p64, const float* L0,
+__global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, const float* pl, const float* L0,
                                                          const float* L1, const float* L2, double* part) {
   __shared__ double sh[9];
   const float* L[3] = {L0, L1, L2};
@@ -773,7 +862,7 @@ __global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, 
       dg += (has ? L[c][qu] : 0.f) + L[c][q];
     }
     if (dg > 0.f) {
-      sp += p64 ? p64[q] : (double)p[q];
+      sp += (double)p[q] + (pl ? (double)pl[q] : 0.0);
       sc += 1.0;
     }
   }
@@ -786,7 +875,7 @@ __global__ void __launch_bounds__(256) k_force_partials(Grid g, const float* p, 
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float* p, const double* p64,
+__global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float* p, const float* pl,
                                                       const double* part, int npart,
                                                       int lo0, int lo1, int lo2, int bx, int by, int bz,
                                                       double* out) {
@@ -811,7 +900,7 @@ __global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float
     if (!(fabs(d) < b.eps)) continue;
     const double K = (1.0 + cospi(d / b.eps)) / (2.0 * b.eps);
     const long long q = cell_index(g, i, j, k);
-    const double pp = (p64 ? p64[q] : (double)p[q]) - pbar;
+    const double pp = ((double)p[q] + (pl ? (double)pl[q] : 0.0)) - pbar;
 #pragma unroll
     for (int dd = 0; dd < D; ++dd) F[dd] -= pp * n[dd] * K;
   }
@@ -822,12 +911,12 @@ __global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float
   if (threadIdx.x == 0) out[3] = pbar;
 }
 
-int launch_forces(int D, const Grid& g, const Body& b, const float* p, const double* p64, const float* const* L,
+int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* pl, const float* const* L,
                   double* partials, int npart, double* out, cudaStream_t s) {
   if (D == 3)
-    k_force_partials<3><<<npart, 256, 0, s>>>(g, p, p64, L[0], L[1], L[2], partials);
+    k_force_partials<3><<<npart, 256, 0, s>>>(g, p, pl, L[0], L[1], L[2], partials);
   else
-    k_force_partials<2><<<npart, 256, 0, s>>>(g, p, p64, L[0], L[1], L[1], partials);
+    k_force_partials<2><<<npart, 256, 0, s>>>(g, p, pl, L[0], L[1], L[1], partials);
   double ext = b.r1 + b.eps + 1.0;
   if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 1.0;
   int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
@@ -842,9 +931,9 @@ int launch_forces(int D, const Grid& g, const Body& b, const float* p, const dou
   }
   const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
   if (D == 3)
-    k_force_final<3><<<1, 256, 0, s>>>(g, b, p, p64, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
+    k_force_final<3><<<1, 256, 0, s>>>(g, b, p, pl, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
   else
-    k_force_final<2><<<1, 256, 0, s>>>(g, b, p, p64, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
+    k_force_final<2><<<1, 256, 0, s>>>(g, b, p, pl, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);
   return 0;
 }
 
@@ -1026,22 +1115,31 @@ int launch_apply_pinv(const DenseArgs& a, cudaStream_t s) {
   return 0;
 }
 
-// Precision conversions of the pressure: out64 = in32 (or out64 += in32 when add),
-// out32 = in64.
-__global__ void k_convert(const float* in32, double* out64, const double* in64, float* out32, long long n, int add) {
+// ph + pl rounded to FP32
+__global__ void k_df_round(const float* ph, const float* pl, float* out, long long n) {
   const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
-  if (q >= n) return;
-  if (in32) out64[q] = add ? out64[q] + (double)in32[q] : (double)in32[q];
-  if (in64) out32[q] = (float)in64[q];
+  if (q < n) out[q] = ph[q] + pl[q];
 }
 
-int launch_convert(const float* in32, double* out64, const double* in64, float* out32, long long n, cudaStream_t s) {
-  k_convert<<<(int)((n + 255) / 256), 256, 0, s>>>(in32, out64, in64, out32, n, 0);
+int launch_df_round(const float* ph, const float* pl, float* out, long long n, cudaStream_t s) {
+  k_df_round<<<(int)((n + 255) / 256), 256, 0, s>>>(ph, pl, out, n);
   return 0;
 }
 
-int launch_add64(const float* in32, double* out64, long long n, cudaStream_t s) {
-  k_convert<<<(int)((n + 255) / 256), 256, 0, s>>>(in32, out64, nullptr, nullptr, n, 1);
+// (ph, pl) += e
+__global__ void k_df_add(float* ph, float* pl, const float* e, long long n) {
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= n) return;
+  float sh, sl, nh, nl;
+  two_sum(ph[q], e[q], sh, sl);
+  sl += pl[q];
+  fast_two_sum(sh, sl, nh, nl);
+  ph[q] = nh;
+  pl[q] = nl;
+}
+
+int launch_df_add(float* ph, float* pl, const float* e, long long n, cudaStream_t s) {
+  k_df_add<<<(int)((n + 255) / 256), 256, 0, s>>>(ph, pl, e, n);
   return 0;
 }
 

@@ -220,7 +220,7 @@ class Sim:
     Every method is a direct call of the C entry point of the same name."""
 
     def __init__(self, dims, nu, U, body=None, periodic=0, tol=1e-6, max_vcycles=32, post=4, eps=1.0,
-                 dt_cap=10.0, dt_fixed=0.0, advect=True, precision=0, use_graph=True, device=None):
+                 dt_cap=10.0, dt_fixed=0.0, advect=True, precision=1, use_graph=True, device=None):
         import torch
 
         self.torch = torch
