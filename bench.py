@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 WaterLily time step (libwl.so through its C ABI).
+
+One "step" is one full time step (simstep!: two convection-diffusion + BDIM stages,
+two multigrid projections to Poisson tol 1e-6, the CFL time step) of the whole
+domain.  The metric is cells*steps/s; V-cycles/s and the roofline fraction of the
+dominant kernel are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+N > 1 is launched by torchrun, one rank per GPU; every rank advances an independent
+replica of the workload (the method has no data exchange between replicas), the
+value is all ranks' cells*steps divided by the slowest rank's time.
+The reference arm is the FP64 CPU oracle timed on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # 3-D flow past a sphere, radius 16 cells, Re = 3700 (diameter based), uniform inflow
+    "sphere512": dict(dims=(512, 256, 256), nu=32.0 / 3700.0, U=(1.0, 0.0, 0.0),
+                      body=dict(kind=1, center=(128.0, 128.0, 128.0), radius=16.0), periodic=0, ic=0,
+                      desc="3-D flow past a sphere R=16, Re=3700, 512x256x256 cells, uniform inflow, tol 1e-6"),
+    "sphere256": dict(dims=(256, 128, 128), nu=32.0 / 3700.0, U=(1.0, 0.0, 0.0),
+                      body=dict(kind=1, center=(64.0, 64.0, 64.0), radius=16.0), periodic=0, ic=0,
+                      desc="3-D flow past a sphere R=16, Re=3700, 256x128x128 cells, uniform inflow, tol 1e-6"),
+    "tgv128": dict(dims=(128, 128, 128), nu=(128.0 / (2 * 3.141592653589793)) / 1600.0, U=(0.0, 0.0, 0.0),
+                   body=None, periodic=7, ic=1,
+                   desc="3-D Taylor-Green vortex, 128^3 periodic, Re=1600, tol 1e-6"),
+    "cyl128x64": dict(dims=(128, 64), nu=0.064, U=(1.0, 0.0), body=dict(kind=1, center=(32.0, 32.0), radius=8.0),
+                      periodic=0, ic=0, desc="2-D flow past a circle R=8, Re=250, 128x64 cells, tol 1e-6"),
+}
+
+# Algorithmic bytes per fine-level cell of one launch of each kernel class (D
+# dimensions, FP32 fields, double-float fine pressure), each array read or written
+# once:
+#   sweep_fine : mean of the 4 sweeps of a cycle: first (coarse correction 4/2^D +
+#                rhs 4 + faces 4D + out 4), two middle (in 4 + rhs 4 + faces 4D +
+#                out 4), last (in 4 + rhs 4 + faces 4D + pressure hi/lo read and
+#                written 16)
+#   resid_fine : residual: pressure 8 + rhs 4 + faces 4D + residual out 4 +
+#                restricted 4/2^D; the projection's first pass also reads the
+#                velocity 4D and writes the rhs instead of reading it (same count)
+#   stage      : stage 1 reads u 4D + mu0 4D, writes 4D; stage 2 also reads u0 4D
+#   correct    : u 4D + faces 4D + pressure 8 in, u 4D out
+def algo_bytes(cls, D, n_div=0, n_res=0):
+    f = 4.0 * D
+    if cls == "sweep_fine":
+        first = 4.0 / 2**D + 4 + f + 4
+        mid = 4 + 4 + f + 4
+        last = 4 + 4 + f + 16
+        return (first + 2 * mid + last) / 4
+    if cls == "resid_fine":
+        res = 8 + 4 + f + 4 + 4.0 / 2**D
+        div = res + f
+        return (n_div * div + n_res * res) / max(n_div + n_res, 1)
+    if cls == "stage":
+        return (3 * f + 4 * f) / 2
+    if cls == "correct":
+        return 3 * f + 8
+    raise KeyError(cls)
+
+
+KERNEL_NAMES = {"sweep_fine": "k_sweep<3> (fine level)", "resid_fine": "k_residual<3> (fine level)",
+                "stage": "k_stage<3>", "correct": "k_correct<3>"}
+KERNEL_SRC = {"sweep_fine": "wl_poisson.cu", "resid_fine": "wl_poisson.cu", "stage": "wl_momentum.cu",
+              "correct": "wl_poisson.cu"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _src_sha(name):
+    path = os.path.join(ROOT, "paper_2304_08159_gb300", "csrc", name)
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def _traffic(cls, ncell):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary, scaled
+    to this workload's cells; None when the kernel source changed since."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)[cls]
+        if t["src_sha"] != _src_sha(KERNEL_SRC[cls]):
+            return None
+        return t["bytes_per_cell"] * ncell
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def _launches_per_step(nlev, post, has_body):
+    """Kernels one graph step launches outside the V-cycles, and per V-cycle."""
+    fixed = 2 * (1 + (1 if has_body else 0))  # stages (+ band)
+    fixed += 2 * 2  # per projection: divergence/residual + decision
+    fixed += 2 + 1  # corrections + step end
+    # restrictions, coarsest solve, sweeps of every level but the coarsest, fine
+    # residual, decision; a single-level hierarchy: solve, fold into the pressure,
+    # residual, decision
+    per_cycle = (nlev - 2) + 1 + (nlev - 1) * post + 2 if nlev > 1 else 4
+    return fixed, per_cycle
+
+
+def cpu_oracle_step_rate(w, steps=1):
+    """The FP64 oracle (as it is) on the host cores: setup, then `steps` timed full
+    time steps with multigrid projections at tol 1e-6.  Returns (cells*steps/s, s, cores)."""
+    import oracle as O
+
+    o = O.Oracle(w["dims"], w["nu"], U=w["U"], periodic=w["periodic"], body=w["body"])
+    o.set_ic(w["ic"], 1.0)
+    t0 = time.perf_counter()
+    o.step(steps, tol=1e-6, maxit=32, solver=1)
+    t = time.perf_counter() - t0
+    ncell = 1
+    for d in w["dims"]:
+        ncell *= d
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return ncell * steps / t, t, cores
+
+
+def run_reference(args, w, rank, ws):
+    if rank != 0:
+        return 0
+    ncell = 1
+    for d in w["dims"]:
+        ncell *= d
+    steps = max(1, min(args.steps, args.ref_steps))
+    if args.warmup > 0 and args.ref_warmup > 0:
+        cpu_oracle_step_rate(w, 1)
+    rate, t, cores = cpu_oracle_step_rate(w, steps)
+    sample = (f"{steps} full time step(s) of the {args.workload} workload by the FP64 oracle "
+              f"(multigrid V(0,4) projections to tol 1e-6) after its setup; the arm's --steps is capped "
+              f"at {args.ref_steps} to bound CPU time")
+    line = {"impl": "reference", "metric": "cells*steps/s", "value": rate, "unit": "cell*step/s",
+            "n_gpus": ws, "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "desc": w["desc"], "cells": ncell},
+            "cpu_baseline": {"value": rate, "unit": "cell*step/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "cell*step/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, w, dist, rank, ws, lrank):
+    import numpy as np
+    import torch
+
+    from paper_2304_08159_gb300 import Sim, wl
+
+    torch.cuda.set_device(lrank)
+    ncell = int(np.prod(w["dims"]))
+    D = len(w["dims"])
+    sim = Sim(w["dims"], w["nu"], w["U"], body=w["body"], periodic=w["periodic"], tol=args.tol)
+    if w["ic"]:
+        sim.set_ic(w["ic"], 1.0)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    sim.step(args.warmup)
+    sim.status()
+    barrier()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(lrank).uuid)
+    except Exception:
+        gpu_id = str(lrank)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    rc, last, vcycles, worst = sim.status()
+    tmax = t
+    vtot = vcycles
+    if dist is not None:
+        tt = torch.tensor([t, float(vcycles)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        tmax, vtot = mx[0].item(), tt[1].item()
+    value = ws * ncell * args.steps / tmax
+    nlev = len(sim.levels())
+    fixed, per_cycle = _launches_per_step(nlev, 4, w["body"] is not None)
+    launches = args.steps * fixed + vcycles * per_cycle
+
+    # ---- per-kernel device time (host-driven steps with events around each launch)
+    prof = sim.profile_step(args.prof_steps)
+    prof_steps = args.prof_steps
+    peak, peak_kind = _peaks()
+    cls = max(("sweep_fine", "resid_fine", "stage", "correct"), key=lambda k: prof[k][0])
+    ms_tot, n = prof[cls]
+    nd = min(2 * prof_steps, n)
+    bytes_launch = algo_bytes(cls, D, nd, n - nd) * ncell
+    avg_s = ms_tot / n / 1e3
+    achieved = bytes_launch / avg_s / 1e9
+    roof = {"bound": "hbm", "kernel": KERNEL_NAMES[cls], "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(cls, ncell),
+            "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3,
+            "share_of_step": ms_tot / sum(v[0] for v in prof.values())}
+    kern = {k: {"ms_per_step": v[0] / prof_steps, "launches_per_step": v[1] / prof_steps} for k, v in prof.items()}
+
+    # ---- end to end through the C ABI with pinned host buffers: state in, step, state out
+    host_u = torch.empty(D * ncell, dtype=torch.float32, pin_memory=True)
+    sim_u = sim.get(wl.WL_FIELD_U, device=True).reshape(-1)
+    host_u.copy_(sim_u)
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim._check(wl.wl_set_field(sim.h, wl.WL_FIELD_U, host_u.data_ptr(), 0), "wl_set_field")
+        sim.step(1)
+        sim._check(wl.wl_get_field(sim.h, wl.WL_FIELD_U, host_u.data_ptr(), 0), "wl_get_field")
+    barrier()
+    te = time.perf_counter() - t0
+    if dist is not None:
+        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = tt.item()
+    e2e = {"value": ws * ncell * e2e_steps / te, "unit": "cell*step/s", "h2d_bytes_per_step": 4 * D * ncell,
+           "d2h_bytes_per_step": 4 * D * ncell, "steps": e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, tcpu, cores = cpu_oracle_step_rate(w, 1)
+        cpu = {"value": rate, "unit": "cell*step/s", "cores": cores, "kind": "oracle",
+               "sample": f"1 full time step of the {args.workload} workload by the FP64 oracle (multigrid "
+                         f"V(0,4) projections to tol 1e-6) after its setup, {tcpu:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": "cells*steps/s", "value": value, "unit": "cell*step/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": args.workload, "desc": w["desc"], "cells": ncell, "dims": list(w["dims"]),
+                           "poisson_tol": args.tol, "replicas": ws,
+                           "l2": "inputs larger than L2 (working set %.1f GB)" % (sim.workspace.numel() / 1e9)},
+                "vcycles_per_s": vtot / tmax, "vcycles_per_step": vcycles / args.steps,
+                "converged": rc == 0, "worst_residual": worst,
+                "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
+                "gpu_launches": int(ws * launches)}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="sphere512", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--prof-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--ref-steps", type=int, default=2)
+    ap.add_argument("--ref-warmup", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        ws = int(os.environ.get("WORLD_SIZE", "1"))
+        rank = int(os.environ.get("RANK", "0"))
+        return run_reference(args, w, rank, ws)
+    dist, rank, ws, lrank = _dist()
+    try:
+        return run_ours(args, w, dist, rank, ws, lrank)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

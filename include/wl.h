@@ -172,6 +172,25 @@ int wl_get_time(wl_handle h, double* t, long long* steps);
  * Synchronises. */
 int wl_status(wl_handle h, int* last_vcycles /*[2]*/, long long* total_vcycles, double* worst_resid);
 
+/* kernel classes of wl_profile_step */
+#define WL_KCLASS_STAGE 0       /* convdiff + BDIM stage (mu0 part) */
+#define WL_KCLASS_BAND 1        /* BDIM mu1 term on the body band */
+#define WL_KCLASS_RESID_FINE 2  /* divergence / residual + restriction on the fine level */
+#define WL_KCLASS_RESTRICT 3    /* restriction between coarse levels */
+#define WL_KCLASS_SWEEP_FINE 4  /* red-black Gauss-Seidel sweep on the fine level */
+#define WL_KCLASS_SWEEP_COARSE 5 /* red-black Gauss-Seidel sweeps on coarse levels */
+#define WL_KCLASS_COARSEST 6    /* coarsest-level solve */
+#define WL_KCLASS_CORRECT 7     /* pressure-gradient correction (+ CFL maximum) */
+#define WL_KCLASS_CONTROL 8     /* one-thread control kernels (V-cycle decision, step end) */
+#define WL_KCLASS_COUNT 9
+
+/* Advance nsteps steps through the host-driven launch sequence (the same kernels
+ * as wl_step) with a pair of CUDA events on the sim's stream around every launch,
+ * and return per kernel class (WL_KCLASS_*) the summed device time in ms[] and the
+ * launch count in launches[] (arrays of WL_KCLASS_COUNT).  For measurement;
+ * synchronises. */
+int wl_profile_step(wl_handle h, int nsteps, double* ms, long long* launches);
+
 /* Levels of the multigrid hierarchy and the dims of level l (dims[3]). */
 int wl_levels(wl_handle h, int* nlevels);
 int wl_level_dims(wl_handle h, int l, int* dims);

@@ -134,10 +134,11 @@ void apply_bc(const OSim& s, vec* f) {
     const int hi[3] = {s.n[0] + s.g[0], s.n[1] + s.g[1], s.n[2] + s.g[2]};
     for (int c = 0; c < s.D; ++c) {
       vec& a = f[c];
-      int I[3];
-      for (I[2] = lo[2]; I[2] < hi[2]; ++I[2])
-        for (I[1] = lo[1]; I[1] < hi[1]; ++I[1])
-          for (I[0] = lo[0]; I[0] < hi[0]; ++I[0]) {
+#pragma omp parallel for collapse(2)
+      for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+          for (int i = lo[0]; i < hi[0]; ++i) {
+            int I[3] = {i, j, k};
             int q = I[d];
             bool ghost = (q < 0 || q >= s.n[d]);
             bool bface = (!is_per(s, d) && c == d && q == 0);
@@ -226,6 +227,7 @@ void bdim_stage(const OSim& s, int stage, double dt, const vec* u0, const vec* u
   vec f[3];
   for (int c = 0; c < s.D; ++c) {
     f[c] = u0[c];
+#pragma omp parallel for collapse(2)
     for (int k = 0; k < s.n[2]; ++k)
       for (int j = 0; j < s.n[1]; ++j)
         for (int i = 0; i < s.n[0]; ++i) {
@@ -237,6 +239,7 @@ void bdim_stage(const OSim& s, int stage, double dt, const vec* u0, const vec* u
   apply_bc(s, f);
   for (int c = 0; c < s.D; ++c) {
     out[c] = uin[c];
+#pragma omp parallel for collapse(2)
     for (int k = 0; k < s.n[2]; ++k)
       for (int j = 0; j < s.n[1]; ++j)
         for (int i = 0; i < s.n[0]; ++i) {
@@ -306,6 +309,7 @@ struct Op {
   }
   void diagonal(vec& dg) const {
     dg.assign(ncell, 0.0);
+#pragma omp parallel for collapse(2)
     for (int k = 0; k < n[2]; ++k)
       for (int j = 0; j < n[1]; ++j)
         for (int i = 0; i < n[0]; ++i) {
@@ -327,7 +331,9 @@ Op make_op(const OSim& s, const Level& l) {
 
 double norm_inf(const vec& a) {
   double m = 0.0;
-  for (double v : a) m = std::max(m, std::fabs(v));
+  const long n = (long)a.size();
+#pragma omp parallel for reduction(max : m)
+  for (long q = 0; q < n; ++q) m = std::max(m, std::fabs(a[q]));
   return m;
 }
 
@@ -335,13 +341,16 @@ double norm_inf(const vec& a) {
 void remove_mean_active(vec& a, const vec& dg) {
   double sum = 0.0;
   long cnt = 0;
-  for (size_t q = 0; q < a.size(); ++q)
+  const long n = (long)a.size();
+#pragma omp parallel for reduction(+ : sum, cnt)
+  for (long q = 0; q < n; ++q)
     if (dg[q] > 0.0) {
       sum += a[q];
       ++cnt;
     }
   double m = cnt ? sum / cnt : 0.0;
-  for (size_t q = 0; q < a.size(); ++q) a[q] = (dg[q] > 0.0) ? a[q] - m : 0.0;
+#pragma omp parallel for
+  for (long q = 0; q < n; ++q) a[q] = (dg[q] > 0.0) ? a[q] - m : 0.0;
 }
 
 // Jacobi-preconditioned conjugate gradients on -A x = -z over the active cells,
@@ -352,11 +361,13 @@ int pcg(const Op& A, vec& x, const vec& zin, double tol, int maxit, double* resi
   A.diagonal(dg);
   vec z = zin;
   remove_mean_active(z, dg);
-  for (long q = 0; q < A.ncell; ++q)
+  const long n = A.ncell;
+  for (long q = 0; q < n; ++q)
     if (dg[q] <= 0.0) x[q] = 0.0;
-  vec Ax, r(A.ncell), zz(A.ncell), pp(A.ncell), Ap;
+  vec Ax, r(n), zz(n), pp(n), Ap;
   A.apply(x, Ax);
-  for (long q = 0; q < A.ncell; ++q) r[q] = (dg[q] > 0.0) ? (z[q] - Ax[q]) : 0.0;  // r = z - Ax
+#pragma omp parallel for
+  for (long q = 0; q < n; ++q) r[q] = (dg[q] > 0.0) ? (z[q] - Ax[q]) : 0.0;  // r = z - Ax
   double rn = norm_inf(r);
   int it = 0;
   if (rn <= tol) {
@@ -364,37 +375,43 @@ int pcg(const Op& A, vec& x, const vec& zin, double tol, int maxit, double* resi
     return 0;
   }
   // work with B = -A (positive semi-definite), b = -z, residual rho = b - Bx = -(z - Ax) = -r
-  for (long q = 0; q < A.ncell; ++q) {
+  double rz = 0.0;
+#pragma omp parallel for reduction(+ : rz)
+  for (long q = 0; q < n; ++q) {
     zz[q] = (dg[q] > 0.0) ? -r[q] / dg[q] : 0.0;
     pp[q] = zz[q];
+    rz += -r[q] * zz[q];
   }
-  double rz = 0.0;
-  for (long q = 0; q < A.ncell; ++q) rz += -r[q] * zz[q];
   for (it = 1; it <= maxit; ++it) {
     A.apply(pp, Ap);  // A p ; B p = -A p
     double pBp = 0.0;
-    for (long q = 0; q < A.ncell; ++q) pBp += pp[q] * (-Ap[q]);
+#pragma omp parallel for reduction(+ : pBp)
+    for (long q = 0; q < n; ++q) pBp += pp[q] * (-Ap[q]);
     if (pBp <= 0.0) break;
     double alpha = rz / pBp;
-    for (long q = 0; q < A.ncell; ++q) {
+#pragma omp parallel for
+    for (long q = 0; q < n; ++q) {
       x[q] += alpha * pp[q];
       r[q] -= alpha * Ap[q];  // r = z - A x
     }
     rn = norm_inf(r);
     if (rn <= tol) {
       A.apply(x, Ax);  // confirm with the true residual
-      for (long q = 0; q < A.ncell; ++q) r[q] = (dg[q] > 0.0) ? (z[q] - Ax[q]) : 0.0;
+#pragma omp parallel for
+      for (long q = 0; q < n; ++q) r[q] = (dg[q] > 0.0) ? (z[q] - Ax[q]) : 0.0;
       rn = norm_inf(r);
       if (rn <= tol) break;
     }
     double rz2 = 0.0;
-    for (long q = 0; q < A.ncell; ++q) {
+#pragma omp parallel for reduction(+ : rz2)
+    for (long q = 0; q < n; ++q) {
       zz[q] = (dg[q] > 0.0) ? -r[q] / dg[q] : 0.0;
       rz2 += -r[q] * zz[q];
     }
     double beta = rz2 / rz;
     rz = rz2;
-    for (long q = 0; q < A.ncell; ++q) pp[q] = zz[q] + beta * pp[q];
+#pragma omp parallel for
+    for (long q = 0; q < n; ++q) pp[q] = zz[q] + beta * pp[q];
   }
   if (resid) *resid = rn;
   return it;
@@ -474,6 +491,7 @@ void build_levels(OSim& s) {
     c.ncell = (long)c.n[0] * c.n[1] * c.n[2];
     for (int cc = 0; cc < s.D; ++cc) {
       c.L[cc].assign(c.ncell, 0.0);
+#pragma omp parallel for collapse(2)
       for (int k = 0; k < c.n[2]; ++k)
         for (int j = 0; j < c.n[1]; ++j)
           for (int i = 0; i < c.n[0]; ++i) {
@@ -496,6 +514,7 @@ void build_levels(OSim& s) {
 
 void rb_sweep(const Op& A, vec& x, const vec& z) {
   for (int color = 0; color < 2; ++color)
+#pragma omp parallel for collapse(2)
     for (int k = 0; k < A.n[2]; ++k)
       for (int j = 0; j < A.n[1]; ++j)
         for (int i = 0; i < A.n[0]; ++i) {
@@ -535,16 +554,24 @@ void vcycle(const OSim& s, int l, vec& x, const vec& z, int pre, int post) {
   A.apply(x, Ax);
   const Level& c = s.lev[l + 1];
   vec zc(c.ncell, 0.0), xc(c.ncell, 0.0);
-  for (int k = 0; k < A.n[2]; ++k)
-    for (int j = 0; j < A.n[1]; ++j)
-      for (int i = 0; i < A.n[0]; ++i) {
-        long q = A.idx(i, j, k);
-        int ci = i / 2, cj = (s.D > 1) ? j / 2 : 0, ck = (s.D > 2) ? k / 2 : 0;
-        zc[ci + (long)c.n[0] * (cj + (long)c.n[1] * ck)] += z[q] - Ax[q];
+  // restriction: each coarse cell sums the residual of its 2^D children
+#pragma omp parallel for collapse(2)
+  for (int ck = 0; ck < c.n[2]; ++ck)
+    for (int cj = 0; cj < c.n[1]; ++cj)
+      for (int ci = 0; ci < c.n[0]; ++ci) {
+        double sum = 0.0;
+        for (int dk = 0; dk < (s.D > 2 ? 2 : 1); ++dk)
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+              long q = A.idx(2 * ci + di, 2 * cj + dj, (s.D > 2 ? 2 * ck : 0) + dk);
+              sum += z[q] - Ax[q];
+            }
+        zc[ci + (long)c.n[0] * (cj + (long)c.n[1] * ck)] = sum;
       }
   vcycle(s, l + 1, xc, zc, pre, post);
   // piecewise-constant prolongation of the correction onto the active cells
   // (cells with a zero row have no equation and keep x = 0)
+#pragma omp parallel for collapse(2)
   for (int k = 0; k < A.n[2]; ++k)
     for (int j = 0; j < A.n[1]; ++j)
       for (int i = 0; i < A.n[0]; ++i) {
@@ -566,6 +593,7 @@ void measure(OSim& s) {
   }
   if (s.body_kind != 0) {
     for (int c = 0; c < s.D; ++c)
+#pragma omp parallel for collapse(2)
       for (int k = 0; k < s.n[2]; ++k)
         for (int j = 0; j < s.n[1]; ++j)
           for (int i = 0; i < s.n[0]; ++i) {
@@ -600,6 +628,7 @@ void measure(OSim& s) {
 // Divergence z[I] = sum_c u_c[I+e_c] - u_c[I] (u padded with BC applied).
 void divergence(const OSim& s, const vec* u, vec& z) {
   z.assign(s.ncell, 0.0);
+#pragma omp parallel for collapse(2)
   for (int k = 0; k < s.n[2]; ++k)
     for (int j = 0; j < s.n[1]; ++j)
       for (int i = 0; i < s.n[0]; ++i) {
@@ -634,6 +663,7 @@ void project(OSim& s, vec* u, double w, double dt, double tol, int maxit, int so
     while (true) {
       A.apply(x, Ax);
       res = 0.0;
+#pragma omp parallel for reduction(max : res)
       for (long q = 0; q < s.ncell; ++q) res = std::max(res, std::fabs(z[q] - Ax[q]));
       if (res <= tol || it >= maxit) break;
       vcycle(s, 0, x, z, 0, post);
@@ -644,6 +674,7 @@ void project(OSim& s, vec* u, double w, double dt, double tol, int maxit, int so
   s.last_resid = res;
   remove_mean_active(x, dg);
   for (int c = 0; c < s.D; ++c)
+#pragma omp parallel for collapse(2)
     for (int k = 0; k < s.n[2]; ++k)
       for (int j = 0; j < s.n[1]; ++j)
         for (int i = 0; i < s.n[0]; ++i) {
@@ -660,6 +691,7 @@ void project(OSim& s, vec* u, double w, double dt, double tol, int maxit, int so
 // CFL! (Table 2): dt = min(dt_cap, 1/(max_I sum_c [max(0,u_c[I+e_c]) + max(0,-u_c[I])] + 2 D nu)).
 double cfl(const OSim& s) {
   double m = 0.0;
+#pragma omp parallel for collapse(2) reduction(max : m)
   for (int k = 0; k < s.n[2]; ++k)
     for (int j = 0; j < s.n[1]; ++j)
       for (int i = 0; i < s.n[0]; ++i) {

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "wl.h"
@@ -69,6 +70,8 @@ struct wl_sim {
   cudaGraphConditionalHandle hc[2]{};
   bool poisoned = false;
   std::string err;
+  // per-launch event pairs while wl_profile_step runs (class, start, stop)
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>>* prof = nullptr;
 };
 
 namespace {
@@ -87,6 +90,23 @@ int cuda_check(wl_sim* s, cudaError_t e, const char* what) {
   do {                                                   \
     int _rc = cuda_check((s), (call), #call);            \
     if (_rc != WL_OK) return _rc;                        \
+  } while (0)
+
+// Time one launch with a pair of events when profiling (host-driven steps only).
+void prof_begin(wl_sim* s, cudaStream_t st, int cls) {
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  cudaEventRecord(a, st);
+  s->prof->emplace_back(cls, a, b);
+}
+void prof_end(wl_sim* s, cudaStream_t st) { cudaEventRecord(std::get<2>(s->prof->back()), st); }
+
+#define PROF(s, st, cls, call)               \
+  do {                                       \
+    if ((s)->prof) prof_begin((s), (st), (cls)); \
+    call;                                    \
+    if ((s)->prof) prof_end((s), (st));      \
   } while (0)
 
 // Multigrid levels: halve while every direction is even and larger than 4.
@@ -193,7 +213,11 @@ StageArgs stage_args(wl_sim* s, int stage) {
   return a;
 }
 
-void enq_stage(wl_sim* s, int stage, cudaStream_t st) { launch_stage(s->D, stage_args(s, stage), s->body, st); }
+void enq_stage(wl_sim* s, int stage, cudaStream_t st) {
+  const StageArgs a = stage_args(s, stage);
+  PROF(s, st, WL_KCLASS_STAGE, launch_stage(s->D, a, st));
+  if (s->body.kind != 0) PROF(s, st, WL_KCLASS_BAND, launch_band(s->D, a, s->body, st));
+}
 
 ResArgs res_args(wl_sim* s, int l, int mode) {
   ResArgs a{};
@@ -219,8 +243,8 @@ void enq_proj_head(wl_sim* s, float* const* u, float w, int proj, cudaStream_t s
   a.ph = s->ph;
   a.pl = s->pl;
   a.rout = s->rf;
-  launch_residual(s->D, a, st);
-  launch_decide(s->ds, s->hc[proj], use_h, 1, proj, w, s->o.tol, s->o.max_vcycles, st);
+  PROF(s, st, WL_KCLASS_RESID_FINE, launch_residual(s->D, a, st));
+  PROF(s, st, WL_KCLASS_CONTROL, launch_decide(s->ds, s->hc[proj], use_h, 1, proj, w, s->o.tol, s->o.max_vcycles, st));
 }
 
 // post sweeps on level l with the coarse correction of level l+1 prolonged into the
@@ -248,7 +272,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
     a.x_out = bufs[out];
     a.ph = (refine && it == P - 1) ? s->ph : nullptr;
     a.pl = (refine && it == P - 1) ? s->pl : nullptr;
-    launch_sweep(s->D, a, st);
+    PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
     in = bufs[out];
     out ^= 1;
   }
@@ -265,7 +289,7 @@ void enq_coarsest(wl_sim* s, int l, const float* z, float* x, cudaStream_t st) {
     d.G = s->G;
     d.z = z;
     d.x = x;
-    launch_apply_pinv(d, st);
+    PROF(s, st, WL_KCLASS_COARSEST, launch_apply_pinv(d, st));
     return;
   }
   CoarseArgs a{};
@@ -276,7 +300,7 @@ void enq_coarsest(wl_sim* s, int l, const float* z, float* x, cudaStream_t st) {
   a.work = s->cg_work;
   a.maxit = (int)std::min<long long>(4 * L.g.nc + 100, 100000);
   a.rtol = 1e-12;
-  launch_coarse(s->D, a, st);
+  PROF(s, st, WL_KCLASS_COARSEST, launch_coarse(s->D, a, st));
 }
 
 // restriction down the coarse levels, coarsest solve, prolongation + smoothing up to
@@ -292,7 +316,7 @@ void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
     }
     return;
   }
-  for (int l = 1; l + 1 < Lv; ++l) launch_residual(s->D, res_args(s, l, RES_RESTRICT), st);
+  for (int l = 1; l + 1 < Lv; ++l) PROF(s, st, WL_KCLASS_RESTRICT, launch_residual(s->D, res_args(s, l, RES_RESTRICT), st));
   enq_coarsest(s, Lv - 1, s->lev[Lv - 1].z, s->lev[Lv - 1].x, st);
   for (int l = Lv - 2; l >= 0; --l) enq_smooth(s, l, st);
 }
@@ -307,8 +331,8 @@ ResArgs fine_residual_args(wl_sim* s) {
 
 void enq_vcycle(wl_sim* s, float w, int proj, cudaStream_t st, int use_h) {
   enq_vcycle_core(s, st);
-  launch_residual(s->D, fine_residual_args(s), st);
-  launch_decide(s->ds, s->hc[proj], use_h, 0, proj, w, s->o.tol, s->o.max_vcycles, st);
+  PROF(s, st, WL_KCLASS_RESID_FINE, launch_residual(s->D, fine_residual_args(s), st));
+  PROF(s, st, WL_KCLASS_CONTROL, launch_decide(s->ds, s->hc[proj], use_h, 0, proj, w, s->o.tol, s->o.max_vcycles, st));
 }
 
 void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int cfl, cudaStream_t st) {
@@ -325,7 +349,7 @@ void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int 
   a.w = w;
   a.cfl = cfl;
   a.st = s->ds;
-  launch_correct(s->D, a, st);
+  PROF(s, st, WL_KCLASS_CORRECT, launch_correct(s->D, a, st));
 }
 
 int sync_state(wl_sim* s) {
@@ -356,7 +380,7 @@ int host_step(wl_sim* s) {
   rc = host_projection(s, s->ub, 0.5f, 1);
   if (rc) return rc;
   enq_correct(s, s->ub, s->ua, 0.5f, 1, s->st);
-  launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->st);
+  PROF(s, s->st, WL_KCLASS_CONTROL, launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->st));
   return cuda_check(s, cudaGetLastError(), "step launch");
 }
 
@@ -783,6 +807,32 @@ int wl_status(wl_handle s, int* last_vcycles, long long* total_vcycles, double* 
   }
   if (h.status & 2) return WL_WNOTCONV;
   return WL_OK;
+}
+
+int wl_profile_step(wl_handle s, int nsteps, double* ms, long long* launches) {
+  if (!s || nsteps < 1 || !ms || !launches) return WL_EINVAL;
+  if (s->poisoned) return fail(s, WL_ENONFINITE, "sim is poisoned by a non-finite value");
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> rec;
+  rec.reserve(4096);
+  s->prof = &rec;
+  int rc = WL_OK;
+  for (int n = 0; n < nsteps && rc == WL_OK; ++n) rc = host_step(s);
+  s->prof = nullptr;
+  if (rc == WL_OK) rc = cuda_check(s, cudaStreamSynchronize(s->st), "wl_profile_step");
+  for (int k = 0; k < WL_KCLASS_COUNT; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (auto& t : rec) {
+    float e = 0.f;
+    if (rc == WL_OK && cudaEventElapsedTime(&e, std::get<1>(t), std::get<2>(t)) == cudaSuccess) {
+      ms[std::get<0>(t)] += e;
+      launches[std::get<0>(t)] += 1;
+    }
+    cudaEventDestroy(std::get<1>(t));
+    cudaEventDestroy(std::get<2>(t));
+  }
+  return rc;
 }
 
 int wl_levels(wl_handle s, int* nlevels) {

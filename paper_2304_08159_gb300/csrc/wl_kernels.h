@@ -87,7 +87,8 @@ struct CorrArgs {
   DevState* st;        // dt and the CFL maximum
 };
 
-int launch_stage(int D, const StageArgs& a, const Body& b, cudaStream_t s);
+int launch_stage(int D, const StageArgs& a, cudaStream_t s);
+int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s);
 int launch_residual(int D, const ResArgs& a, cudaStream_t s);
 int launch_sweep(int D, const SweepArgs& a, cudaStream_t s);
 int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s);

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0,
 }
 
 // ---------------------------------------------------------------------------
-int launch_stage(int D, const StageArgs& a, const Body& b, cudaStream_t s) {
+int launch_stage(int D, const StageArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
   dim3 blk(256);
   if (D == 3) {
@@ -237,6 +237,11 @@ int launch_stage(int D, const StageArgs& a, const Body& b, cudaStream_t s) {
     dim3 grd((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_TY - 1) / ST_TY, 1);
     k_stage<2><<<grd, blk, 0, s>>>(a);
   }
+  return 0;
+}
+
+int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s) {
+  const Grid& g = a.g;
   if (b.kind != 0) {
     // bounding box of the faces within eps of the surface
     double ext = b.r1 + b.eps + 2.0;

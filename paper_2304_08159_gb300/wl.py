@@ -40,9 +40,11 @@ WL_BODY_TORUS = 2
 EXPORTS = (
     "wl_default_opts", "wl_workspace_bytes", "wl_create", "wl_set_ic", "wl_step", "wl_stage",
     "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_get_field", "wl_set_field", "wl_get_dt",
-    "wl_set_dt", "wl_get_time", "wl_status", "wl_levels", "wl_level_dims", "wl_destroy",
-    "wl_last_error",
+    "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_levels", "wl_level_dims",
+    "wl_destroy", "wl_last_error",
 )
+KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coarse", "coarsest", "correct",
+            "control")
 
 
 class WlBody(ctypes.Structure):
@@ -94,6 +96,7 @@ def load(path: str = LIB_PATH):
         "wl_set_dt": (I, [H, D]),
         "wl_get_time": (I, [H, DP, ctypes.POINTER(ctypes.c_longlong)]),
         "wl_status": (I, [H, IP, ctypes.POINTER(ctypes.c_longlong), DP]),
+        "wl_profile_step": (I, [H, I, DP, ctypes.POINTER(ctypes.c_longlong)]),
         "wl_levels": (I, [H, IP]),
         "wl_level_dims": (I, [H, I, IP]),
         "wl_destroy": (None, [H]),
@@ -190,6 +193,13 @@ def wl_status(h):
     worst = ctypes.c_double(0.0)
     rc = load().wl_status(h, it, ctypes.byref(tot), ctypes.byref(worst))
     return rc, (it[0], it[1]), tot.value, worst.value
+
+
+def wl_profile_step(h, nsteps):
+    ms = (ctypes.c_double * len(KCLASSES))()
+    n = (ctypes.c_longlong * len(KCLASSES))()
+    rc = load().wl_profile_step(h, int(nsteps), ms, n)
+    return rc, {k: (ms[i], n[i]) for i, k in enumerate(KCLASSES)}
 
 
 def wl_levels(h):
@@ -345,6 +355,12 @@ class Sim:
         rc, last, tot, worst = wl_status(self.h)
         self._check(rc, "wl_status")
         return rc, last, tot, worst
+
+    def profile_step(self, nsteps=1):
+        """{kernel class: (total ms, launches)} over nsteps host-driven steps."""
+        rc, d = wl_profile_step(self.h, nsteps)
+        self._check(rc, "wl_profile_step")
+        return d
 
     def levels(self):
         rc, n = wl_levels(self.h)

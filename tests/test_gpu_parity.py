@@ -7,7 +7,7 @@ Bars (FP32 device arithmetic against FP64):
   * one multigrid V-cycle: max abs error <= 1e-5 * max|x|;
   * 10 full steps: velocity relative L2 <= 1e-5 (the stated bar), pressure
     (mean over active cells removed) relative L2 <= 2e-4 at Poisson tol 1e-6;
-    the 1e-5 pressure bar is checked at tol 5e-8 in test_pressure_parity_tight;
+    the 1e-5 pressure bar is checked at tol 1e-8 in test_pressure_parity_tight;
   * force coefficients relative <= 1e-4.
 """
 import numpy as np
@@ -101,6 +101,11 @@ def test_vcycle_parity(case):
     r_gpu = sim.gmg_vcycle()
     xg = sim.get(wl.WL_FIELD_P).astype(np.float64)
     xo, r_or = ref.vcycle(x32.astype(np.float64), z32.astype(np.float64), 0, 4)
+    if ref.nlevels() == 1:
+        # no coarse level: the cycle is the exact solve, defined up to a constant (the
+        # oracle returns the zero-mean solution, the GPU adds a zero-mean correction)
+        xg = (xg - xg[act].mean()) * act
+        xo = (xo - xo[act].mean()) * act
     scale = np.abs(xo).max()
     assert np.abs(xg - xo).max() <= 1e-5 * scale, (np.abs(xg - xo).max(), scale)
     assert abs(r_gpu - r_or) <= 1e-3 * abs(r_or) + 1e-5 * np.abs(z).max()
@@ -179,13 +184,13 @@ def test_cylinder_10_steps_parity():
 
 
 def test_pressure_parity_tight():
-    """At Poisson tol 5e-8 (reachable with the FP64 fine-level pressure) the pressure
-    meets the 1e-5 bar as well."""
+    """At Poisson tol 1e-8 (reachable with the double-float fine-level pressure) the
+    pressure meets the 1e-5 bar as well."""
     case = dict(id="c1t", dims=(128, 64), nu=0.064, U=(1.0, 0.0), periodic=0,
                 body=dict(kind=1, center=(32.0, 32.0), radius=8.0))
-    sim, ref = make_pair(case, tol=5e-8)
+    sim, ref = make_pair(case, tol=1e-8)
     sim.step(10)
-    ref.step(10, tol=1e-11)
+    ref.step(10, tol=1e-12)
     act = active_mask(ref)
     pg, po = sim.get(1).astype(np.float64), ref.get_p()
     pg = (pg - pg[act].mean()) * act
