@@ -56,7 +56,7 @@ __device__ __forceinline__ long long nb_dn(const Grid& g, int c, int Ic, long lo
 // block holds whole 2^D families of children for the restriction (the z pair is
 // summed in registers, x pairs by a shuffle, y pairs through shared memory) and
 // issues a single atomic for the norm.
-constexpr int RS_ZP = 8;
+constexpr int RS_ZP = 2;
 
 template <int D>
 __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, int k, unsigned& mbits) {
@@ -198,55 +198,77 @@ struct RelaxIn {
   bool ok;
 };
 
+// Offsets of the tile footprint's columns / rows / planes after the boundary mapping
+// (periodic wrap; -1 outside a non-periodic side), so that every load of the march
+// is a table read and two adds whether or not the tile touches the boundary.
 template <int D>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   constexpr int NP = (D == 3) ? 4 : 1;
   __shared__ float s_x[NP][SW_HY][SW_HX];
+  __shared__ int s_xo[SW_HX], s_yo[SW_HY], s_cxo[SW_HX], s_cyo[SW_HY];
   const Grid& g = a.g;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int i0 = blockIdx.x * SW_TX, j0 = blockIdx.y * SW_TY;
   const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
-  const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
-
-  auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
-  auto map = [&](int* I) -> bool {
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      const int n = g.n[d];
-      if (I[d] < 0 || I[d] >= n) {
-        if (!is_per(g, d)) return false;
-        I[d] = I[d] < 0 ? I[d] + n : I[d] - n;
-      }
-    }
-    return true;
+  const int n0 = g.n[0], nn = g.n[0] * g.n[1];
+  const int cn0 = a.cn[0], cnn = a.cn[0] * a.cn[1];
+  auto wrap = [&](int q, int d) -> int {  // mapped index along d, or -1
+    const int n = g.n[d];
+    if (q >= 0 && q < n) return q;
+    if (!is_per(g, d)) return -1;
+    return q < 0 ? q + n : q - n;
   };
-  // iterate value at tile position (col, row) of plane kk (with the prolonged correction)
-  auto xeff = [&](int col, int row, int kk) -> float {
-    int I[3] = {i0 - 2 + col, j0 - 2 + row, D == 3 ? kk : 0};
+  for (int t = tid; t < SW_HX + SW_HY; t += 256) {
+    if (t < SW_HX) {
+      const int m = wrap(i0 - 2 + t, 0);
+      s_xo[t] = m;
+      s_cxo[t] = m >= 0 ? (m >> 1) : -1;
+    } else {
+      const int r = t - SW_HX;
+      const int m = wrap(j0 - 2 + r, 1);
+      s_yo[r] = m >= 0 ? m * n0 : -1;
+      s_cyo[r] = m >= 0 ? (m >> 1) * cn0 : -1;
+    }
+  }
+  __syncthreads();
+  auto zoff = [&](int kk) -> int {
+    if (D == 2) return 0;
+    const int m = wrap(kk, 2);
+    return m >= 0 ? m * nn : -1;
+  };
+  auto czoff = [&](int kk) -> int {
+    if (D == 2) return 0;
+    const int m = wrap(kk, 2);
+    return m >= 0 ? (m >> 1) * cnn : -1;
+  };
+  auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
+  // iterate value at footprint position (col, row) of a plane (with the prolonged correction)
+  auto xeff = [&](int col, int row, int zo, int czo) -> float {
+    const int xo = s_xo[col], yo = s_yo[row];
     float v = 0.f;
-    if (map(I)) {
-      const long long q = cell_index(g, I[0], I[1], I[2]);
-      if (a.x_in) v = __ldg(a.x_in + q);
-      if (a.xc)
-        v += __ldg(a.xc + (long long)(I[0] >> 1) +
-                   (long long)a.cn[0] * ((long long)(I[1] >> 1) + (long long)a.cn[1] * (D == 3 ? (I[2] >> 1) : 0)));
+    if (xo >= 0 && yo >= 0 && zo >= 0) {
+      if (a.x_in) v = __ldg(a.x_in + (xo + yo + zo));
+      if (a.xc) v += __ldg(a.xc + (s_cxo[col] + s_cyo[row] + czo));
     }
     return v;
   };
-  // right-hand side and face coefficients of the cell at tile position (ii, jj), plane kk
-  auto fetch = [&](int ii, int jj, int kk, RelaxIn& c) {
-    int I[3] = {i0 + ii, j0 + jj, D == 3 ? kk : 0};
-    c.ok = map(I);
+  // right-hand side and face coefficients of the cell at tile position (ii, jj)
+  auto fetch = [&](int ii, int jj, int zo, int zou, RelaxIn& c) {
+    const int col = ii + 2, row = jj + 2;
+    const int xo = s_xo[col], yo = s_yo[row];
+    c.ok = xo >= 0 && yo >= 0 && zo >= 0;
     if (!c.ok) return;
-    const long long q = cell_index(g, I[0], I[1], I[2]);
+    const int q = xo + yo + zo;
     c.z = __ldg(a.z + q);
-#pragma unroll
-    for (int d = 0; d < D; ++d) {
-      bool has;
-      const long long qu = nb_up(g, d, I[d], q, st[d], has);
-      c.Lu[d] = has ? __ldg(a.L[d] + qu) : 0.f;
-      c.Ll[d] = __ldg(a.L[d] + q);
+    const int xu = s_xo[col + 1], yu = s_yo[row + 1];
+    c.Ll[0] = __ldg(a.L[0] + q);
+    c.Lu[0] = xu >= 0 ? __ldg(a.L[0] + (xu + yo + zo)) : 0.f;
+    c.Ll[1] = __ldg(a.L[1] + q);
+    c.Lu[1] = yu >= 0 ? __ldg(a.L[1] + (xo + yu + zo)) : 0.f;
+    if (D == 3) {
+      c.Ll[2] = __ldg(a.L[2] + q);
+      c.Lu[2] = zou >= 0 ? __ldg(a.L[2] + (xo + yo + zou)) : 0.f;
     }
   };
   // Gauss-Seidel value from the shared neighbours (0 for a cell with no equation)
@@ -266,10 +288,11 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         xu = s_x[slot(kk + 1)][jj + 2][ii + 2];
         xd = s_x[slot(kk - 1)][jj + 2][ii + 2];
       }
-      sum += c.Lu[d] * xu + c.Ll[d] * xd;
+      sum = fmaf(c.Lu[d], xu, sum);
+      sum = fmaf(c.Ll[d], xd, sum);
       dg += c.Lu[d] + c.Ll[d];
     }
-    return (dg > 0.f) ? (sum - c.z) / dg : 0.f;
+    return (dg > 0.f) ? __fdividef(sum - c.z, dg) : 0.f;
   };
   auto red_pos = [&](int e, int kr, int& ii, int& jj) {
     constexpr int RW = (SW_TX + 2) / 2;
@@ -277,19 +300,20 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     jj = row - 1;
     ii = -1 + 2 * m + ((i0 - 1 + j0 + jj + kr) & 1);
   };
-  // load a whole plane of the iterate into the ring (prologue)
   auto load_plane = [&](int kk) {
+    const int zo = zoff(kk), czo = czoff(kk);
     for (int e = tid; e < SW_HY * SW_HX; e += 256) {
       const int row = e / SW_HX, col = e - row * SW_HX;
-      s_x[slot(kk)][row][col] = xeff(col, row, kk);
+      s_x[slot(kk)][row][col] = xeff(col, row, zo, czo);
     }
   };
   auto red_plane = [&](int kr) {
+    const int zo = zoff(kr), zou = zoff(kr + 1);
     for (int e = tid; e < SW_RED; e += 256) {
       int ii, jj;
       red_pos(e, kr, ii, jj);
       RelaxIn c;
-      fetch(ii, jj, kr, c);
+      fetch(ii, jj, zo, zou, c);
       if (c.ok) s_x[slot(kr)][jj + 2][ii + 2] = relax(c, ii, jj, kr);
     }
   };
@@ -307,18 +331,20 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const int P0 = (i0 + j0 + ty) & 1;  // parity of column 2*tx in plane 0
   for (int k = k0; k < k1; ++k) {
     // ---- issue every global load of this iteration
-    float xv[SW_LOADS];
     const int kn = (D == 3) ? k + 2 : 0;
+    const int zn = zoff(kn), czn = czoff(kn);
+    float xv[SW_LOADS];
 #pragma unroll
     for (int m = 0; m < SW_LOADS; ++m) {
       const int e = tid + 256 * m;
       xv[m] = 0.f;
       if (e < SW_HY * SW_HX) {
         const int row = e / SW_HX, col = e - row * SW_HX;
-        xv[m] = xeff(col, row, kn);
+        xv[m] = xeff(col, row, zn, czn);
       }
     }
     const int kr = (D == 3) ? k + 1 : 0;
+    const int zr = zoff(kr), zru = zoff(kr + 1);
     RelaxIn rc[2];
     int rii[2], rjj[2];
 #pragma unroll
@@ -327,14 +353,15 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       rc[m].ok = false;
       if (e < SW_RED) {
         red_pos(e, kr, rii[m], rjj[m]);
-        fetch(rii[m], rjj[m], kr, rc[m]);
+        fetch(rii[m], rjj[m], zr, zru, rc[m]);
       }
     }
     const int P = (P0 + k) & 1;
     const int ib = 2 * tx + (P ^ 1), ir = 2 * tx + P;
+    const int zk = zoff(k);
     RelaxIn bc;
     bc.ok = false;
-    if (i0 + ib < g.n[0] && j0 + ty < g.n[1]) fetch(ib, ty, k, bc);
+    if (i0 + ib < g.n[0] && j0 + ty < g.n[1]) fetch(ib, ty, zk, zoff(k + 1), bc);
     // ---- new plane into the ring (2-D: the only plane)
 #pragma unroll
     for (int m = 0; m < SW_LOADS; ++m) {
@@ -354,16 +381,16 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     const float vb = bc.ok ? relax(bc, ib, ty, k) : 0.f;
     const float vr = s_x[slot(k)][ty + 2][ir + 2];
     const int gi = i0 + 2 * tx, gj = j0 + ty;
-    if (gj < g.n[1]) {
-      const long long q = cell_index(g, gi, gj, D == 3 ? k : 0);
+    if (gj < g.n[1] && gi < g.n[0]) {
+      const int q = gi + n0 * gj + zk;
       const float v0 = P ? vb : vr, v1 = P ? vr : vb;
-      const bool pair = gi + 1 < g.n[0] && ((g.n[0] & 1) == 0);
+      const bool two = gi + 1 < g.n[0];
       if (a.ph) {
         // last sweep of a correction cycle: fold the correction into ph + pl
         const float vv[2] = {v0, v1};
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
-          if (gi + t >= g.n[0]) continue;
+          if (t == 1 && !two) continue;
           float sh, sl, nh, nl;
           two_sum(a.ph[q + t], vv[t], sh, sl);
           sl += a.pl[q + t];
@@ -371,11 +398,11 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           a.ph[q + t] = nh;
           a.pl[q + t] = nl;
         }
-      } else if (pair) {
+      } else if (two && (n0 & 1) == 0) {
         reinterpret_cast<float2*>(a.x_out + q)[0] = make_float2(v0, v1);
       } else {
-        if (gi < g.n[0]) a.x_out[q] = v0;
-        if (gi + 1 < g.n[0]) a.x_out[q + 1] = v1;
+        a.x_out[q] = v0;
+        if (two) a.x_out[q + 1] = v1;
       }
     }
     __syncthreads();
@@ -546,7 +573,7 @@ int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s) {
 // the CFL out-flux max_I sum_c max(0, u_c[I+e_c]) + max(0, -u_c[I]) of the corrected
 // field (upper faces corrected on the fly, so no second pass).  32 x 8 columns per
 // block walking CR_Z planes; one atomic per block.
-constexpr int CR_Z = 16;
+constexpr int CR_Z = 4;
 
 template <int D>
 __global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
