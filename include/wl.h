@@ -50,7 +50,7 @@ extern "C" {
 #define WL_ENOMEM (-2)     /* allocation failed or supplied workspace too small */
 #define WL_ECUDA (-3)      /* a CUDA runtime call failed; see wl_last_error */
 #define WL_ENONFINITE (-4) /* a non-finite dt or residual was produced */
-#define WL_ETIMEOUT (-5)   /* a device-side bounded wait gave up */
+#define WL_ETIMEOUT (-5)   /* a device-side bounded wait gave up (a staged copy never arrived) */
 #define WL_WNOTCONV 1      /* multigrid hit max_vcycles before tol; state stays valid */
 
 /* field ids for wl_get_field / wl_set_field */

@@ -11,10 +11,13 @@
 // Each projection's V-cycle loop is a CUDA-graph conditional WHILE node whose
 // condition a one-thread kernel sets from the residual after every cycle, so a
 // whole step runs without a host round trip.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <tuple>
@@ -33,6 +36,8 @@ struct LevelBuf {
   float* z;
   float* x;
   float* x2;
+  bool tma;                       // tensor maps below are valid (n_0 % 4 == 0)
+  CUtensorMap mx, mx2, mz, mL[3];  // TMA descriptors of this level's fields
 };
 
 constexpr int kMaxLevels = 16;
@@ -60,6 +65,7 @@ struct wl_sim {
   double* fout = nullptr;
   float* ph = nullptr;        // precision 1: fine-level pressure as the double-float ph + pl
   float* pl = nullptr;
+  CUtensorMap mrf{};          // TMA descriptor of rf
   float* rf = nullptr;        // precision 1: FP32 residual, right-hand side of each correction cycle
   double* G = nullptr;        // dense pseudo-inverse of the coarsest operator (small coarsest levels)
   char* ws = nullptr;
@@ -123,6 +129,38 @@ int plan_levels(const int* n, int D, int out[][3]) {
     for (int d = 0; d < D; ++d) cur[d] /= 2;
   }
   return l;
+}
+
+// Tensor-map encoder from the driver (no link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// Box of 72 x 12 [x 1] floats over a level field (x fastest), zero fill out of range.
+// Needs n_0 % 4 == 0 (16-byte row pitch) and a 16-byte aligned base.
+bool make_field_map(CUtensorMap* m, const float* ptr, const Grid& g, int D) {
+  auto enc = tensor_map_encoder();
+  if (!enc || g.n[0] % 4 != 0 || ((uintptr_t)ptr & 15u)) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
+  cuuint64_t strides[2] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)g.n[0] * g.n[1] * 4};
+  cuuint32_t box[3] = {(cuuint32_t)(SWEEP_TX + 8), (cuuint32_t)(SWEEP_TY + 4), 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)D, (void*)ptr, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
 }
 
 struct Carver {
@@ -261,22 +299,47 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   a.z = refine ? s->rf : L.z;
   a.g = L.g;
   for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
+  a.tz = sweep_planes_per_block(L.g);
   float* bufs[2] = {L.x, L.x2};
+  const CUtensorMap* bmaps[2] = {&L.mx, &L.mx2};
   const bool from_x = (l == 0 && !refine);  // precision 0: the fine iterate is the pressure itself
   // choose the first output so that the last one lands in bufs[0]
   int out = from_x ? 1 : ((P % 2 == 1) ? 0 : 1);
-  const float* in = from_x ? L.x : nullptr;
+  int in = from_x ? 0 : -1;
   for (int it = 0; it < P; ++it) {
-    a.x_in = in;
+    a.x_in = in >= 0 ? bufs[in] : nullptr;
     a.xc = (it == 0) ? s->lev[l + 1].x : nullptr;
     a.x_out = bufs[out];
     a.ph = (refine && it == P - 1) ? s->ph : nullptr;
     a.pl = (refine && it == P - 1) ? s->pl : nullptr;
-    PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
-    in = bufs[out];
+    if (L.tma) {
+      SweepMaps m;
+      m.x = in >= 0 ? *bmaps[in] : L.mx;
+      m.z = refine ? s->mrf : L.mz;
+      m.L0 = L.mL[0];
+      m.L1 = L.mL[1];
+      m.L2 = L.mL[s->D == 3 ? 2 : 1];
+      SweepTmaArgs t{};
+      t.has_x = in >= 0;
+      t.xc = a.xc;
+      t.x_out = a.x_out;
+      t.ph = a.ph;
+      t.pl = a.pl;
+      t.g = a.g;
+      for (int d = 0; d < 3; ++d) t.cn[d] = a.cn[d];
+      t.tz = a.tz;
+      t.st = s->ds;
+      PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st));
+      a.only_wrapping = 1;  // tiles crossing a periodic side
+      if (L.g.per) PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
+    } else {
+      a.only_wrapping = 0;
+      PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
+    }
+    in = out;
     out ^= 1;
   }
-  if (!refine && in != L.x) cudaMemcpyAsync(L.x, in, sizeof(float) * L.g.nc, cudaMemcpyDeviceToDevice, st);
+  if (!refine && in != 0) cudaMemcpyAsync(L.x, bufs[in], sizeof(float) * L.g.nc, cudaMemcpyDeviceToDevice, st);
 }
 
 // coarsest solve of level l: x = A^+ z (dense FP64 pseudo-inverse when small, FP64 CG otherwise)
@@ -553,6 +616,16 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   int rc = WL_OK;
   if (cudaMallocHost(&s->hs, sizeof(DevState)) != cudaSuccess) rc = fail(s, WL_ENOMEM, "pinned host state");
   if (!rc) rc = cuda_check(s, cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking), "capture stream");
+  if (!rc && !std::getenv("WL_NO_TMA")) {  // tensor maps for the staged sweep
+    for (int l = 0; l < s->nlev; ++l) {
+      LevelBuf& L = s->lev[l];
+      bool ok = make_field_map(&L.mx, L.x, L.g, ndim) && make_field_map(&L.mx2, L.x2, L.g, ndim) &&
+                make_field_map(&L.mz, L.z, L.g, ndim);
+      for (int c = 0; c < ndim; ++c) ok = ok && make_field_map(&L.mL[c], L.L[c], L.g, ndim);
+      if (l == 0 && s->rf) ok = ok && make_field_map(&s->mrf, s->rf, L.g, ndim);
+      L.tma = ok;
+    }
+  }
   if (!rc) {
     launch_measure(ndim, s->g, s->body, s->lev[0].L, s->st);
     for (int l = 1; l < s->nlev; ++l) {
@@ -805,6 +878,7 @@ int wl_status(wl_handle s, int* last_vcycles, long long* total_vcycles, double* 
     s->poisoned = true;
     return fail(s, WL_ENONFINITE, "non-finite dt or residual");
   }
+  if (h.status & 4) return fail(s, WL_ETIMEOUT, "a staged copy of the sweep did not arrive in time");
   if (h.status & 2) return WL_WNOTCONV;
   return WL_OK;
 }

@@ -1,5 +1,6 @@
 // Internal launch interface between the host runtime (wl_api.cu) and the kernels.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "wl_dev.cuh"
 
@@ -51,6 +52,24 @@ struct SweepArgs {
   Grid g;
   int cn[3];
   int tz;              // planes per block (3-D)
+  int only_wrapping;   // 1: sweep only the tiles whose footprint crosses a periodic side
+};
+
+// TMA-staged sweep (wl_sweep_tma.cu): tensor maps of the fields of one level
+// (box 72 x 12 [x 1], x start 16-byte aligned, zero fill out of range).
+struct SweepMaps {
+  CUtensorMap x, z, L0, L1, L2;
+};
+struct SweepTmaArgs {
+  int has_x;           // stage the iterate (else it starts from zero)
+  const float* xc;     // coarse correction to prolong into it, or null
+  float* x_out;
+  float* ph;           // if set: fold the result into ph + pl instead of writing x_out
+  float* pl;
+  Grid g;
+  int cn[3];
+  int tz;
+  DevState* st;        // status bit 2 set if a staged copy never arrived
 };
 
 // Dense pseudo-inverse of the coarsest operator (column-major, FP64), used when the
@@ -91,6 +110,20 @@ int launch_stage(int D, const StageArgs& a, cudaStream_t s);
 int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s);
 int launch_residual(int D, const ResArgs& a, cudaStream_t s);
 int launch_sweep(int D, const SweepArgs& a, cudaStream_t s);
+int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s);
+int sweep_planes_per_block(const Grid& g);
+
+// Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.
+// A tile "wraps" when its TMA footprint (x i0-4..i0+67, y j0-2..j0+9, planes
+// k0-2..k1+1) crosses a periodic side: those tiles are swept by k_sweep, the others
+// by k_sweep_tma.
+constexpr int SWEEP_TX = 64, SWEEP_TY = 8;
+__host__ __device__ inline bool sweep_tile_wraps(const Grid& g, int D, int i0, int j0, int k0, int k1) {
+  if ((g.per & 1u) && (i0 - 4 < 0 || i0 + SWEEP_TX + 4 > g.n[0])) return true;
+  if ((g.per & 2u) && (j0 - 2 < 0 || j0 + SWEEP_TY + 2 > g.n[1])) return true;
+  if (D == 3 && (g.per & 4u) && (k0 - 2 < 0 || k1 + 2 > g.n[2])) return true;
+  return false;
+}
 int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s);
 int launch_correct(int D, const CorrArgs& a, cudaStream_t s);
 int launch_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, int first, int proj, float w,

@@ -211,6 +211,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const int i0 = blockIdx.x * SW_TX, j0 = blockIdx.y * SW_TY;
   const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
+  if (a.only_wrapping && !sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
   const int n0 = g.n[0], nn = g.n[0] * g.n[1];
   const int cn0 = a.cn[0], cnn = a.cn[0] * a.cn[1];
   auto wrap = [&](int q, int d) -> int {  // mapped index along d, or -1
@@ -409,19 +410,19 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   }
 }
 
-int launch_sweep(int D, const SweepArgs& a_in, cudaStream_t s) {
-  SweepArgs a = a_in;
+// planes per block: enough blocks to fill the GPU, at most 32 planes per march
+int sweep_planes_per_block(const Grid& g) {
+  const long long tiles = (long long)((g.n[0] + SW_TX - 1) / SW_TX) * ((g.n[1] + SW_TY - 1) / SW_TY);
+  int tz = (int)((tiles * g.n[2] + 1215) / 1216);
+  return tz < 2 ? 2 : (tz > 32 ? 32 : tz);
+}
+
+int launch_sweep(int D, const SweepArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
   if (D == 3) {
-    // planes per block: enough blocks to fill the GPU, at most 32 planes per march
-    const long long tiles = (long long)((g.n[0] + SW_TX - 1) / SW_TX) * ((g.n[1] + SW_TY - 1) / SW_TY);
-    int tz = (int)((tiles * g.n[2] + 1215) / 1216);
-    tz = tz < 2 ? 2 : (tz > 32 ? 32 : tz);
-    a.tz = tz;
-    dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, (g.n[2] + tz - 1) / tz);
+    dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, (g.n[2] + a.tz - 1) / a.tz);
     k_sweep<3><<<grd, 256, 0, s>>>(a);
   } else {
-    a.tz = 1;
     dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, 1);
     k_sweep<2><<<grd, 256, 0, s>>>(a);
   }

@@ -1,0 +1,247 @@
+// Red-black Gauss-Seidel sweep with TMA staging (the multigrid smoother of
+// project!, Section 2; red-black ordering is this library's reading of the
+// smoother).  Same arithmetic and result as k_sweep; the difference is how the data
+// reaches shared memory.
+//
+// A tile of 64 x 8 cells marches up through `tz` planes.  For every plane the five
+// fields it needs (iterate, right-hand side, the three face-coefficient fields) are
+// fetched by the tensor-memory accelerator as 72 x 12 boxes (tile + halo, x start
+// 16-byte aligned) into a ring of plane slots, one plane ahead of the plane being
+// relaxed, each slot completing on its own mbarrier.  Out-of-range elements are
+// zero-filled by the copy engine, which is exactly the value a non-periodic wall
+// needs (face coefficient 0 across it), so the relaxation itself carries no
+// boundary logic.  Tiles whose footprint would wrap across a periodic side are
+// left to k_sweep.
+#include <cuda.h>
+
+#include "wl_dev.cuh"
+#include "wl_kernels.h"
+
+namespace wl {
+
+namespace {
+
+constexpr int TX = SWEEP_TX, TY = SWEEP_TY;  // tile
+constexpr int BX = TX + 8, BY = TY + 4;  // box: x from i0-4 (aligned), y from j0-2
+constexpr int BOX = BX * BY;          // floats per field per plane
+constexpr int NF = 5;                 // fields: x, z, L0, L1, L2
+constexpr int RING = 5;               // plane slots (planes k-1 .. k+3)
+constexpr int RED = (TY + 2) * (TX + 2) / 2;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false if the phase did not complete within the limit
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar,
+                                         int rank) {
+  if (rank == 3)
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+}  // namespace
+
+template <int D>
+__global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  // 128-byte aligned slot buffers, then the mbarriers
+  float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)RING * NF * BOX);
+  const Grid& g = a.g;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
+  const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
+  if (sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
+  const int p_first = (D == 3) ? k0 - 2 : 0;  // first plane staged
+  const int p_last = (D == 3) ? k1 + 1 : 0;   // last plane needed
+  auto slot = [&](int p) { return (p - p_first) % RING; };
+  auto phase = [&](int p) { return (uint32_t)(((p - p_first) / RING) & 1); };
+  auto F = [&](int p, int f) -> float* { return base + ((size_t)slot(p) * NF + f) * BOX; };
+  const int nfields = a.has_x ? NF : NF - 1;
+  const int fields_loaded = (D == 3) ? nfields : nfields - 1;  // 2-D has no L2
+  const uint32_t bytes = (uint32_t)(fields_loaded * BOX * sizeof(float));
+  const CUtensorMap* maps[NF] = {&m.x, &m.z, &m.L0, &m.L1, &m.L2};
+
+  if (tid == 0) {
+    for (int s = 0; s < RING; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int p_issued = p_first - 1;  // (thread 0) last plane staged
+  auto issue = [&](int p) {     // thread 0: stage plane p
+    if (p > p_last) return;
+    p_issued = p;
+    const uint32_t bar = smem_addr(&bars[slot(p)]);
+    mbar_expect_tx(bar, bytes);
+    for (int f = a.has_x ? 0 : 1; f < NF; ++f) {
+      if (D == 2 && f == 4) continue;
+      tma_load(smem_addr(F(p, f)), maps[f], i0 - 4, j0 - 2, p, bar, D);
+    }
+  };
+  // wait for plane p; iterate := (staged iterate or 0) + prolonged coarse correction.
+  // Returns false (block-uniform) if a copy did not arrive in time.
+  auto ready = [&](int p) -> bool {
+    const bool ok = mbar_wait(smem_addr(&bars[slot(p)]), phase(p));
+    if (__syncthreads_or(!ok)) return false;
+    if (!a.has_x || a.xc) {
+      float* X = F(p, 0);
+      for (int e = tid; e < BOX; e += 256) {
+        const int row = e / BX, col = e - row * BX;
+        const int gi = i0 - 4 + col, gj = j0 - 2 + row;
+        float v = a.has_x ? X[e] : 0.f;
+        if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && p >= 0 && p < g.n[2])
+          v += __ldg(a.xc + (long long)(gi >> 1) +
+                     (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
+        X[e] = v;
+      }
+    }
+    return true;
+  };
+  // Gauss-Seidel value of the cell at tile position (ii, jj) of plane p (all operands
+  // staged; out-of-range faces carry 0, so cells outside the grid come out as 0)
+  auto relax = [&](int ii, int jj, int p) -> float {
+    const int e = (jj + 2) * BX + (ii + 4);
+    const float* X = F(p, 0);
+    const float* L0 = F(p, 2);
+    const float* L1 = F(p, 3);
+    float sum = L0[e + 1] * X[e + 1] + L0[e] * X[e - 1];
+    float dg = L0[e + 1] + L0[e];
+    sum = fmaf(L1[e + BX], X[e + BX], sum);
+    sum = fmaf(L1[e], X[e - BX], sum);
+    dg += L1[e + BX] + L1[e];
+    if (D == 3) {
+      const float lu = F(p + 1, 4)[e], ll = F(p, 4)[e];
+      sum = fmaf(lu, F(p + 1, 0)[e], sum);
+      sum = fmaf(ll, F(p - 1, 0)[e], sum);
+      dg += lu + ll;
+    }
+    return (dg > 0.f) ? __fdividef(sum - F(p, 1)[e], dg) : 0.f;
+  };
+  auto red_plane = [&](int p) {
+    float* X = F(p, 0);
+    for (int r = tid; r < RED; r += 256) {
+      constexpr int RW = (TX + 2) / 2;
+      const int row = r / RW, mm = r - row * RW;
+      const int jj = row - 1;
+      const int ii = -1 + 2 * mm + ((i0 - 1 + j0 + jj + p) & 1);
+      X[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, p);
+    }
+  };
+  // a copy timed out at plane p_fail: flag it, wait (bounded) for the planes still in
+  // flight so none lands after the block has left, then leave
+  auto bail = [&](int p_fail) {
+    if (tid == 0) {
+      atomicOr(&a.st->status, 4);
+      for (int p = p_fail; p <= p_issued; ++p) mbar_wait(smem_addr(&bars[slot(p)]), phase(p));
+    }
+    __syncthreads();
+  };
+
+  // ---- prologue: stage planes k0-2 .. k0+2, relax red cells of k0-1 and k0
+  if (tid == 0) {
+    for (int p = p_first; p <= min(p_first + RING - 1, p_last); ++p) issue(p);
+  }
+  if (D == 3) {
+    for (int p = k0 - 2; p <= k0 + 1; ++p)
+      if (!ready(p)) return bail(p);
+    __syncthreads();
+    red_plane(k0 - 1);
+    red_plane(k0);
+  }
+  const int P0 = (i0 + j0 + ty) & 1;
+  for (int k = k0; k < k1; ++k) {
+    const int pn = (D == 3) ? k + 2 : 0;
+    if (!ready(pn)) return bail(pn);
+    __syncthreads();
+    // every thread is past the last read of plane k-2 (its red and black uses were in
+    // the previous iteration and the prologue): stage plane k+3 into its slot
+    if (D == 3 && tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(k + 3);
+    }
+    const int pr = (D == 3) ? k + 1 : 0;
+    red_plane(pr);
+    __syncthreads();
+    // black cells of plane k, one per thread, then write the tile's plane k
+    const int P = (P0 + k) & 1;
+    const int ib = 2 * tx + (P ^ 1), ir = 2 * tx + P;
+    const float vb = relax(ib, ty, k);
+    const float vr = F(k, 0)[(ty + 2) * BX + (ir + 4)];
+    const int gi = i0 + 2 * tx, gj = j0 + ty;
+    if (gi < g.n[0] && gj < g.n[1]) {
+      const long long q = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * (D == 3 ? k : 0));
+      const float v0 = P ? vb : vr, v1 = P ? vr : vb;
+      const bool two = gi + 1 < g.n[0];
+      if (a.ph) {
+        const float vv[2] = {v0, v1};
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          if (t == 1 && !two) continue;
+          float sh, sl, nh, nl;
+          two_sum(a.ph[q + t], vv[t], sh, sl);
+          sl += a.pl[q + t];
+          fast_two_sum(sh, sl, nh, nl);
+          a.ph[q + t] = nh;
+          a.pl[q + t] = nl;
+        }
+      } else if (two) {
+        reinterpret_cast<float2*>(a.x_out + q)[0] = make_float2(v0, v1);
+      } else {
+        a.x_out[q] = v0;
+      }
+    }
+  }
+}
+
+size_t sweep_tma_smem() { return (size_t)RING * NF * BOX * sizeof(float) + RING * sizeof(uint64_t) + 128; }
+
+int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s) {
+  const Grid& g = a.g;
+  const size_t smem = sweep_tma_smem();
+  if (D == 3)
+    cudaFuncSetAttribute(k_sweep_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else
+    cudaFuncSetAttribute(k_sweep_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (D == 3) {
+    dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
+    k_sweep_tma<3><<<grd, 256, smem, s>>>(m, a);
+  } else {
+    dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, 1);
+    k_sweep_tma<2><<<grd, 256, smem, s>>>(m, a);
+  }
+  return 0;
+}
+
+}  // namespace wl

@@ -267,3 +267,17 @@ def test_impulsive_start_meets_tol_with_fp64_pressure():
         sim.step(1)
         rc, last, tot, worst = sim.status()
         assert rc == 0 and worst <= 1e-6 and max(last) < 32, (rc, last, tot, worst)
+
+
+@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[2], CASES_2D[0], CASES_2D[3]], ids=lambda c: c["id"])
+def test_tma_sweep_matches_table_sweep(case, monkeypatch):
+    """The TMA-staged sweep and the index-table sweep are the same arithmetic: three
+    steps give identical bits."""
+    a, _ = make_pair(case, oracle=False)
+    monkeypatch.setenv("WL_NO_TMA", "1")
+    b, _ = make_pair(case, oracle=False)
+    monkeypatch.delenv("WL_NO_TMA")
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.get(0), b.get(0))
+    assert np.array_equal(a.get(1), b.get(1))
