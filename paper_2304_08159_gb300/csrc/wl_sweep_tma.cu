@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
     const float* X = F(p, 0);
     const float* L0 = F(p, 2);
     const float* L1 = F(p, 3);
-    float sum = L0[e + 1] * X[e + 1] + L0[e] * X[e - 1];
+    // same operation order as k_sweep (upper then lower face, x, y, z), so both
+    // kernels produce the same bits
+    float sum = fmaf(L0[e + 1], X[e + 1], 0.f);
+    sum = fmaf(L0[e], X[e - 1], sum);
     float dg = L0[e + 1] + L0[e];
     sum = fmaf(L1[e + BX], X[e + BX], sum);
     sum = fmaf(L1[e], X[e - BX], sum);
