@@ -168,6 +168,24 @@ def _dist():
     return None, 0, 1, 0
 
 
+def reduce_replicas(dist, t, vcycles, device):
+    """Slowest rank's time and all ranks' V-cycles (t and vcycles of this rank)."""
+    if dist is None:
+        return t, vcycles
+    import torch
+
+    mx = torch.tensor([t], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(vcycles)], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.item(), sm.item()
+
+
+def job_value(world, ncell, steps, tmax):
+    """Whole-job cells*steps/s: every replica's cells*steps over the slowest time."""
+    return world * ncell * steps / tmax
+
+
 def _launches_per_step(nlev, post, has_body):
     """Kernels one graph step launches outside the V-cycles, and per V-cycle."""
     fixed = 2 * (1 + (1 if has_body else 0))  # stages (+ band)
@@ -258,15 +276,8 @@ def run_ours(args, w, dist, rank, ws, lrank):
     ck = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
     rc, last, vcycles, worst = sim.status()
-    tmax = t
-    vtot = vcycles
-    if dist is not None:
-        tt = torch.tensor([t, float(vcycles)], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        tmax, vtot = mx[0].item(), tt[1].item()
-    value = ws * ncell * args.steps / tmax
+    tmax, vtot = reduce_replicas(dist, t, vcycles, "cuda")
+    value = job_value(ws, ncell, args.steps, tmax)
     nlev = len(sim.levels())
     fixed, per_cycle = _launches_per_step(nlev, 4, w["body"] is not None)
     launches = args.steps * fixed + vcycles * per_cycle
@@ -301,11 +312,8 @@ def run_ours(args, w, dist, rank, ws, lrank):
         sim._check(wl.wl_get_field(sim.h, wl.WL_FIELD_U, host_u.data_ptr(), 0), "wl_get_field")
     barrier()
     te = time.perf_counter() - t0
-    if dist is not None:
-        tt = torch.tensor([te], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = tt.item()
-    e2e = {"value": ws * ncell * e2e_steps / te, "unit": "cell*step/s", "h2d_bytes_per_step": 4 * D * ncell,
+    te, _ = reduce_replicas(dist, te, 0, "cuda")
+    e2e = {"value": job_value(ws, ncell, e2e_steps, te), "unit": "cell*step/s", "h2d_bytes_per_step": 4 * D * ncell,
            "d2h_bytes_per_step": 4 * D * ncell, "steps": e2e_steps}
 
     cpu = None
