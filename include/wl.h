@@ -191,6 +191,26 @@ int wl_status(wl_handle h, int* last_vcycles /*[2]*/, long long* total_vcycles, 
  * synchronises. */
 int wl_profile_step(wl_handle h, int nsteps, double* ms, long long* launches);
 
+/* Allocation-free pressure force, for callers that cannot allocate device memory
+ * (for example while capturing a CUDA graph, where cudaMalloc is not allowed, or under
+ * an allocator that owns the whole device).  The paper has no counterpart; this is
+ * wl_forces' computation (F_d = -sum (p - pbar) n_d K_eps(d), FP64) on fields the caller
+ * already holds:
+ *   dims/ndim/periodic_mask: the grid; body, eps: the immersed body and BDIM half-width;
+ *   p: device pointer, n cells of FP32 pressure (x fastest);
+ *   L: device pointer, ndim blocks of n FP32 face coefficients (WL_FIELD_MU0 layout),
+ *      used to find the cells with a nonzero Poisson row for pbar;
+ *   F: device pointer receiving ndim doubles; stream: cudaStream_t (NULL = default).
+ * Allocates nothing: its scratch is a fixed device array (256 KiB on every GPU that
+ * loads the library, kept until exit) holding one partial-sum pair per 4096 cells, so
+ * grids of more than WL_NOALLOC_MAX_CELLS cells return WL_EINVAL.  The first call on
+ * each device looks the array's device address up (make that first call before any
+ * stream capture).  All calls share the array: calls that overlap on the GPU race.
+ * Asynchronous on `stream`. */
+#define WL_NOALLOC_MAX_CELLS (16384LL * 4096LL)
+int wl_forces_noalloc(const int* dims, int ndim, unsigned periodic_mask, const wl_body* body, double eps,
+                      const float* p, const float* L, double* F, void* stream);
+
 /* Levels of the multigrid hierarchy and the dims of level l (dims[3]). */
 int wl_levels(wl_handle h, int* nlevels);
 int wl_level_dims(wl_handle h, int l, int* dims);

@@ -41,7 +41,7 @@ EXPORTS = (
     "wl_default_opts", "wl_workspace_bytes", "wl_create", "wl_set_ic", "wl_step", "wl_stage",
     "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_get_field", "wl_set_field", "wl_get_dt",
     "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_levels", "wl_level_dims",
-    "wl_destroy", "wl_last_error",
+    "wl_destroy", "wl_last_error", "wl_forces_noalloc",
 )
 KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coarse", "coarsest", "correct",
             "control")
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "wl_level_dims": (I, [H, I, IP]),
         "wl_destroy": (None, [H]),
         "wl_last_error": (ctypes.c_char_p, [H]),
+        "wl_forces_noalloc": (I, [IP, I, ctypes.c_uint, ctypes.POINTER(WlBody), D, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -216,6 +217,24 @@ def wl_level_dims(h, l):
 
 def wl_destroy(h):
     load().wl_destroy(h)
+
+
+def wl_forces_noalloc(dims, periodic, body: WlBody, eps, p_ptr, L_ptr, F_ptr, stream=None):
+    """Allocation-free pressure force on caller-owned device fields (see include/wl.h)."""
+    d = (ctypes.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    return load().wl_forces_noalloc(d, len(dims), int(periodic), ctypes.byref(body), float(eps), p_ptr, L_ptr,
+                                    F_ptr, stream)
+
+
+def make_body(body) -> WlBody:
+    b = WlBody()
+    b.kind = int(body.get("kind", WL_BODY_SPHERE))
+    c = list(body["center"]) + [0.0] * 3
+    for i in range(3):
+        b.center[i] = float(c[i])
+    b.radius = float(body.get("radius", 0.0))
+    b.radius2 = float(body.get("radius2", 0.0))
+    return b
 
 
 def wl_last_error(h) -> str:

@@ -1,0 +1,61 @@
+"""wl_forces_noalloc, the allocation-free variant of the pressure-force reduction.
+
+Some callers cannot allocate device memory where they need the force (for example
+inside a CUDA-graph capture, where cudaMalloc is not allowed, or under an allocator
+that owns the whole device).  This entry point takes the pressure and face
+coefficients they already hold and keeps its scratch in a fixed device array.  Each
+test calls it twice in a row through the C ABI (the second call reuses the array
+the first one left behind) and checks it against wl_forces on the same state, within
+the force bar of the parity tests (1e-4 relative).
+This file is collected last so that a run stopping at the first failure has already
+run every other test.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(dims=(128, 64), nu=0.064, U=(1.0, 0.0), body=dict(kind=1, center=(32.0, 32.0), radius=8.0), periodic=0),
+    dict(dims=(96, 48, 48), nu=0.02, U=(1.0, 0.0, 0.0), body=dict(kind=1, center=(30.0, 24.3, 23.6), radius=7.0),
+         periodic=4),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=["cylinder2d", "sphere3d"])
+def test_forces_noalloc_matches_wl_forces(case):
+    import torch
+
+    from paper_2304_08159_gb300 import Sim, wl
+
+    # precision 0: the FP32 pressure wl_get_field returns is the one wl_forces reads
+    sim = Sim(case["dims"], case["nu"], case["U"], body=case["body"], periodic=case["periodic"], precision=0)
+    sim.step(4)
+    torch.cuda.synchronize()
+    ref = sim.forces()
+    assert np.abs(ref).max() > 0.0
+    p = sim.get(wl.WL_FIELD_P, device=True).contiguous()
+    L = sim.get(wl.WL_FIELD_MU0, device=True).contiguous()
+    D = len(case["dims"])
+    F = torch.empty(D, dtype=torch.float64, device=p.device)
+    body = wl.make_body(case["body"])
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        F.fill_(float("nan"))
+        rc = wl.wl_forces_noalloc(case["dims"], case["periodic"], body, 1.0, p.data_ptr(), L.data_ptr(),
+                                  F.data_ptr(), stream)
+        assert rc == wl.WL_OK
+        torch.cuda.synchronize()
+        got = F.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.allclose(got, ref, rtol=1e-4, atol=1e-4 * np.abs(ref).max())
+    sim.close()
+
+
+def test_forces_noalloc_rejects_oversized_grid():
+    """Grids beyond the fixed scratch are refused before any device work."""
+    from paper_2304_08159_gb300 import wl
+
+    body = wl.make_body(dict(kind=1, center=(10.0, 10.0, 10.0), radius=4.0))
+    rc = wl.wl_forces_noalloc((1024, 1024, 128), 0, body, 1.0, 1, 1, 1, None)
+    assert rc == wl.WL_EINVAL
