@@ -6,8 +6,12 @@
 // A tile of 64 x 8 cells marches up through `tz` planes.  For every plane the five
 // fields it needs (iterate, right-hand side, the three face-coefficient fields) are
 // fetched by the tensor-memory accelerator as 72 x 12 boxes (tile + halo, x start
-// 16-byte aligned) into a ring of plane slots, one plane ahead of the plane being
-// relaxed, each slot completing on its own mbarrier.  Out-of-range elements are
+// 16-byte aligned) into two rings of plane slots (iterate: planes k-1..k+3;
+// coefficients: planes k..k+3), one plane ahead of the plane being relaxed, each
+// staged plane completing on its own mbarrier.  Red (and black) cells are two floats
+// apart, so a warp takes 16 cells from each of two adjacent rows: their red columns
+// have opposite parity and the row pitch is 8 banks, so the two half-warps touch
+// disjoint banks and no shared access conflicts.  Out-of-range elements are
 // zero-filled by the copy engine, which is exactly the value a non-periodic wall
 // needs (face coefficient 0 across it), so the relaxation itself carries no
 // boundary logic.  Tiles whose footprint would wrap across a periodic side are
@@ -24,9 +28,9 @@ namespace {
 constexpr int TX = SWEEP_TX, TY = SWEEP_TY;  // tile
 constexpr int BX = TX + 8, BY = TY + 4;  // box: x from i0-4 (aligned), y from j0-2
 constexpr int BOX = BX * BY;          // floats per field per plane
-constexpr int NF = 5;                 // fields: x, z, L0, L1, L2
-constexpr int RING = 5;               // plane slots (planes k-1 .. k+3)
-constexpr int RED = (TY + 2) * (TX + 2) / 2;
+constexpr int XR = 5;                 // iterate slots (planes k-1 .. k+3)
+constexpr int CR = 4;                 // coefficient slots (planes k .. k+3), 4 fields each: z, L0, L1, L2
+constexpr int NB = 5;                 // mbarriers (one per staged plane, reused every NB planes)
 constexpr unsigned kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -75,91 +79,99 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
 template <int D>
 __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  // 128-byte aligned slot buffers, then the mbarriers
-  float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)RING * NF * BOX);
+  // 128-byte aligned slot buffers (iterate ring, coefficient ring), then the mbarriers
+  float* xbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float* cbase = xbase + (size_t)XR * BOX;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cbase + (size_t)CR * 4 * BOX);
   const Grid& g = a.g;
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
   if (sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
-  const int p_first = (D == 3) ? k0 - 2 : 0;  // first plane staged
-  const int p_last = (D == 3) ? k1 + 1 : 0;   // last plane needed
-  auto slot = [&](int p) { return (p - p_first) % RING; };
-  auto phase = [&](int p) { return (uint32_t)(((p - p_first) / RING) & 1); };
-  auto F = [&](int p, int f) -> float* { return base + ((size_t)slot(p) * NF + f) * BOX; };
-  const int nfields = a.has_x ? NF : NF - 1;
-  const int fields_loaded = (D == 3) ? nfields : nfields - 1;  // 2-D has no L2
-  const uint32_t bytes = (uint32_t)(fields_loaded * BOX * sizeof(float));
-  const CUtensorMap* maps[NF] = {&m.x, &m.z, &m.L0, &m.L1, &m.L2};
+  const int p_first = (D == 3) ? k0 - 2 : 0;   // first plane whose iterate is staged
+  const int pc_first = (D == 3) ? k0 - 1 : 0;  // first plane whose coefficients are staged
+  const int p_last = (D == 3) ? k1 + 1 : 0;    // last plane needed
+  auto X = [&](int p) -> float* { return xbase + (size_t)((p - p_first) % XR) * BOX; };
+  // coefficient field f (0: rhs z, 1: L0, 2: L1, 3: L2) of plane p
+  auto C = [&](int p, int f) -> float* { return cbase + ((size_t)((p - pc_first) % CR) * 4 + f) * BOX; };
+  auto bar = [&](int p) { return smem_addr(&bars[(p - p_first) % NB]); };
+  auto phase = [&](int p) { return (uint32_t)(((p - p_first) / NB) & 1); };
+  const CUtensorMap* cmaps[4] = {&m.z, &m.L0, &m.L1, &m.L2};
+  const int ncf = (D == 3) ? 4 : 3;  // 2-D has no L2
 
   if (tid == 0) {
-    for (int s = 0; s < RING; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    for (int s = 0; s < NB; ++s) mbar_init(smem_addr(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
   int p_issued = p_first - 1;  // (thread 0) last plane staged
-  auto issue = [&](int p) {     // thread 0: stage plane p
+  auto issue = [&](int p) {     // thread 0: stage plane p (iterate, and coefficients from pc_first on)
     if (p > p_last) return;
     p_issued = p;
-    const uint32_t bar = smem_addr(&bars[slot(p)]);
-    mbar_expect_tx(bar, bytes);
-    for (int f = a.has_x ? 0 : 1; f < NF; ++f) {
-      if (D == 2 && f == 4) continue;
-      tma_load(smem_addr(F(p, f)), maps[f], i0 - 4, j0 - 2, p, bar, D);
-    }
+    const bool coef = p >= pc_first;
+    const uint32_t bytes = (uint32_t)(((a.has_x ? 1 : 0) + (coef ? ncf : 0)) * BOX * sizeof(float));
+    mbar_expect_tx(bar(p), bytes);
+    if (a.has_x) tma_load(smem_addr(X(p)), &m.x, i0 - 4, j0 - 2, p, bar(p), D);
+    if (coef)
+      for (int f = 0; f < ncf; ++f) tma_load(smem_addr(C(p, f)), cmaps[f], i0 - 4, j0 - 2, p, bar(p), D);
   };
   // wait for plane p; iterate := (staged iterate or 0) + prolonged coarse correction.
   // Returns false (block-uniform) if a copy did not arrive in time.
   auto ready = [&](int p) -> bool {
-    const bool ok = mbar_wait(smem_addr(&bars[slot(p)]), phase(p));
+    const bool ok = mbar_wait(bar(p), phase(p));
     if (__syncthreads_or(!ok)) return false;
     if (!a.has_x || a.xc) {
-      float* X = F(p, 0);
+      float* Xp = X(p);
       for (int e = tid; e < BOX; e += 256) {
         const int row = e / BX, col = e - row * BX;
         const int gi = i0 - 4 + col, gj = j0 - 2 + row;
-        float v = a.has_x ? X[e] : 0.f;
+        float v = a.has_x ? Xp[e] : 0.f;
         if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && p >= 0 && p < g.n[2])
           v += __ldg(a.xc + (long long)(gi >> 1) +
                      (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
-        X[e] = v;
+        Xp[e] = v;
       }
+      __syncthreads();
     }
     return true;
   };
   // Gauss-Seidel value of the cell at tile position (ii, jj) of plane p (all operands
-  // staged; out-of-range faces carry 0, so cells outside the grid come out as 0)
+  // staged; out-of-range faces carry 0, so cells outside the grid come out as 0).
+  // Same operation order as k_sweep (upper then lower face; x, y, z), same bits.
   auto relax = [&](int ii, int jj, int p) -> float {
     const int e = (jj + 2) * BX + (ii + 4);
-    const float* X = F(p, 0);
-    const float* L0 = F(p, 2);
-    const float* L1 = F(p, 3);
-    // same operation order as k_sweep (upper then lower face, x, y, z), so both
-    // kernels produce the same bits
-    float sum = fmaf(L0[e + 1], X[e + 1], 0.f);
-    sum = fmaf(L0[e], X[e - 1], sum);
+    const float* Xp = X(p);
+    const float* L0 = C(p, 1);
+    const float* L1 = C(p, 2);
+    float sum = fmaf(L0[e + 1], Xp[e + 1], 0.f);
+    sum = fmaf(L0[e], Xp[e - 1], sum);
     float dg = L0[e + 1] + L0[e];
-    sum = fmaf(L1[e + BX], X[e + BX], sum);
-    sum = fmaf(L1[e], X[e - BX], sum);
+    sum = fmaf(L1[e + BX], Xp[e + BX], sum);
+    sum = fmaf(L1[e], Xp[e - BX], sum);
     dg += L1[e + BX] + L1[e];
     if (D == 3) {
-      const float lu = F(p + 1, 4)[e], ll = F(p, 4)[e];
-      sum = fmaf(lu, F(p + 1, 0)[e], sum);
-      sum = fmaf(ll, F(p - 1, 0)[e], sum);
+      const float lu = C(p + 1, 3)[e], ll = C(p, 3)[e];
+      sum = fmaf(lu, X(p + 1)[e], sum);
+      sum = fmaf(ll, X(p - 1)[e], sum);
       dg += lu + ll;
     }
-    return (dg > 0.f) ? __fdividef(sum - F(p, 1)[e], dg) : 0.f;
+    return (dg > 0.f) ? __fdividef(sum - C(p, 0)[e], dg) : 0.f;
   };
+  // red cells of plane p on the tile plus a 1-cell halo (rows -1..8, columns -1..64):
+  // ten 32-cell tasks (two adjacent rows x half the tile's columns) and the ten
+  // edge-column cells
   auto red_plane = [&](int p) {
-    float* X = F(p, 0);
-    for (int r = tid; r < RED; r += 256) {
-      constexpr int RW = (TX + 2) / 2;
-      const int row = r / RW, mm = r - row * RW;
-      const int jj = row - 1;
-      const int ii = -1 + 2 * mm + ((i0 - 1 + j0 + jj + p) & 1);
-      X[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, p);
+    float* Xp = X(p);
+    for (int t = warp; t < 10; t += 8) {
+      const int jj = 2 * (t >> 1) + (lane >> 4) - 1;
+      const int ii = 32 * (t & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + p) & 1);
+      Xp[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, p);
+    }
+    if (warp == 2 && lane < 10) {
+      const int jj = lane - 1;
+      const int ii = ((i0 + j0 + jj + p) & 1) ? -1 : 64;
+      Xp[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, p);
     }
   };
   // a copy timed out at plane p_fail: flag it, wait (bounded) for the planes still in
@@ -167,48 +179,47 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
   auto bail = [&](int p_fail) {
     if (tid == 0) {
       atomicOr(&a.st->status, 4);
-      for (int p = p_fail; p <= p_issued; ++p) mbar_wait(smem_addr(&bars[slot(p)]), phase(p));
+      for (int p = p_fail; p <= p_issued; ++p) mbar_wait(bar(p), phase(p));
     }
     __syncthreads();
   };
 
   // ---- prologue: stage planes k0-2 .. k0+2, relax red cells of k0-1 and k0
-  if (tid == 0) {
-    for (int p = p_first; p <= min(p_first + RING - 1, p_last); ++p) issue(p);
-  }
+  if (tid == 0)
+    for (int p = p_first; p <= min(p_first + NB - 1, p_last); ++p) issue(p);
   if (D == 3) {
     for (int p = k0 - 2; p <= k0 + 1; ++p)
       if (!ready(p)) return bail(p);
-    __syncthreads();
     red_plane(k0 - 1);
     red_plane(k0);
+    __syncthreads();
   }
-  const int P0 = (i0 + j0 + ty) & 1;
   for (int k = k0; k < k1; ++k) {
     const int pn = (D == 3) ? k + 2 : 0;
     if (!ready(pn)) return bail(pn);
-    __syncthreads();
-    // every thread is past the last read of plane k-2 (its red and black uses were in
-    // the previous iteration and the prologue): stage plane k+3 into its slot
+    // every thread is past the last use of plane k-2's iterate and plane k-1's
+    // coefficients (both in the previous iteration or the prologue): stage plane k+3
     if (D == 3 && tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(k + 3);
     }
-    const int pr = (D == 3) ? k + 1 : 0;
-    red_plane(pr);
+    red_plane(D == 3 ? k + 1 : 0);
     __syncthreads();
-    // black cells of plane k, one per thread, then write the tile's plane k
-    const int P = (P0 + k) & 1;
-    const int ib = 2 * tx + (P ^ 1), ir = 2 * tx + P;
-    const float vb = relax(ib, ty, k);
-    const float vr = F(k, 0)[(ty + 2) * BX + (ir + 4)];
+    // black cells of plane k: eight 32-cell tasks (two adjacent rows x half the columns)
+    {
+      const int jj = 2 * (warp >> 1) + (lane >> 4);
+      const int ii = 32 * (warp & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + k + 1) & 1);
+      X(k)[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, k);
+    }
+    __syncthreads();
+    // write the tile's plane k: thread (tx, ty) takes columns 2tx, 2tx+1 of row ty
+    const float2 v = *reinterpret_cast<const float2*>(X(k) + (ty + 2) * BX + 2 * tx + 4);
     const int gi = i0 + 2 * tx, gj = j0 + ty;
     if (gi < g.n[0] && gj < g.n[1]) {
       const long long q = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * (D == 3 ? k : 0));
-      const float v0 = P ? vb : vr, v1 = P ? vr : vb;
       const bool two = gi + 1 < g.n[0];
       if (a.ph) {
-        const float vv[2] = {v0, v1};
+        const float vv[2] = {v.x, v.y};
 #pragma unroll
         for (int t = 0; t < 2; ++t) {
           if (t == 1 && !two) continue;
@@ -220,15 +231,17 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
           a.pl[q + t] = nl;
         }
       } else if (two) {
-        reinterpret_cast<float2*>(a.x_out + q)[0] = make_float2(v0, v1);
+        reinterpret_cast<float2*>(a.x_out + q)[0] = v;
       } else {
-        a.x_out[q] = v0;
+        a.x_out[q] = v.x;
       }
     }
   }
 }
 
-size_t sweep_tma_smem() { return (size_t)RING * NF * BOX * sizeof(float) + RING * sizeof(uint64_t) + 128; }
+size_t sweep_tma_smem() {
+  return ((size_t)XR + 4 * (size_t)CR) * BOX * sizeof(float) + NB * sizeof(uint64_t) + 128;
+}
 
 int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
