@@ -66,6 +66,9 @@ struct wl_sim {
   float* ph = nullptr;        // precision 1: fine-level pressure as the double-float ph + pl
   float* pl = nullptr;
   CUtensorMap mrf{};          // TMA descriptor of rf
+  CUtensorMap mph{}, mpl{};   // TMA descriptors of the fine pressure (ph: hi part or FP32 pressure)
+  CUtensorMap mu[3][3]{};     // TMA descriptors of the velocity buffers A, B, C (components)
+  bool resid_tma = false;     // the fine residual uses the TMA-staged kernel
   float* rf = nullptr;        // precision 1: FP32 residual, right-hand side of each correction cycle
   double* G = nullptr;        // dense pseudo-inverse of the coarsest operator (small coarsest levels)
   char* ws = nullptr;
@@ -273,15 +276,53 @@ ResArgs res_args(wl_sim* s, int l, int mode) {
   return a;
 }
 
-// divergence of u (scaled by 1/(w dt)), first residual, restriction, first decision
-void enq_proj_head(wl_sim* s, float* const* u, float w, int proj, cudaStream_t st, int use_h) {
-  ResArgs a = res_args(s, 0, RES_DIVERGENCE);
-  for (int c = 0; c < 3; ++c) a.u[c] = u[c];
+// fine-level residual (mode RES_RESIDUAL) or divergence + residual (RES_DIVERGENCE,
+// of velocity buffer `ubuf` 0/1/2 = A/B/C), with the restriction and the max-norm
+void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) {
+  const LevelBuf& L = s->lev[0];
+  if (s->resid_tma) {
+    ResidMaps m{};
+    m.ph = s->mph;
+    m.pl = s->mpl;
+    m.z = L.mz;
+    m.L0 = L.mL[0];
+    m.L1 = L.mL[1];
+    m.L2 = L.mL[2];
+    if (mode == RES_DIVERGENCE) {
+      m.u0 = s->mu[ubuf][0];
+      m.u1 = s->mu[ubuf][1];
+      m.u2 = s->mu[ubuf][2];
+    }
+    ResidTmaArgs t{};
+    t.div = mode == RES_DIVERGENCE;
+    t.df = s->ph != nullptr;
+    t.z = L.z;
+    t.rout = s->rf;
+    t.zc = (s->nlev > 1) ? s->lev[1].z : nullptr;
+    t.g = L.g;
+    if (s->nlev > 1)
+      for (int d = 0; d < 3; ++d) t.cn[d] = s->lev[1].g.n[d];
+    const int tz = sweep_planes_per_block(L.g);
+    t.tz = tz + (tz & 1);
+    t.inv_w = 1.f / w;
+    t.st = s->ds;
+    PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st));
+    return;
+  }
+  ResArgs a = res_args(s, 0, mode);
+  float* const* ub[3] = {s->ua, s->ub, s->uc};
+  if (mode == RES_DIVERGENCE)
+    for (int c = 0; c < 3; ++c) a.u[c] = ub[ubuf][c];
   a.inv_w = 1.f / w;
   a.ph = s->ph;
   a.pl = s->pl;
   a.rout = s->rf;
   PROF(s, st, WL_KCLASS_RESID_FINE, launch_residual(s->D, a, st));
+}
+
+// divergence of u (scaled by 1/(w dt)), first residual, restriction, first decision
+void enq_proj_head(wl_sim* s, int ubuf, float w, int proj, cudaStream_t st, int use_h) {
+  enq_fine_residual(s, RES_DIVERGENCE, ubuf, w, st);
   PROF(s, st, WL_KCLASS_CONTROL, launch_decide(s->ds, s->hc[proj], use_h, 1, proj, w, s->o.tol, s->o.max_vcycles, st));
 }
 
@@ -384,17 +425,9 @@ void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
   for (int l = Lv - 2; l >= 0; --l) enq_smooth(s, l, st);
 }
 
-ResArgs fine_residual_args(wl_sim* s) {
-  ResArgs a = res_args(s, 0, RES_RESIDUAL);
-  a.ph = s->ph;
-  a.pl = s->pl;
-  a.rout = s->rf;
-  return a;
-}
-
 void enq_vcycle(wl_sim* s, float w, int proj, cudaStream_t st, int use_h) {
   enq_vcycle_core(s, st);
-  PROF(s, st, WL_KCLASS_RESID_FINE, launch_residual(s->D, fine_residual_args(s), st));
+  enq_fine_residual(s, RES_RESIDUAL, 0, 1.f, st);
   PROF(s, st, WL_KCLASS_CONTROL, launch_decide(s->ds, s->hc[proj], use_h, 0, proj, w, s->o.tol, s->o.max_vcycles, st));
 }
 
@@ -422,8 +455,8 @@ int sync_state(wl_sim* s) {
 }
 
 // projection loop driven from the host (used outside graphs)
-int host_projection(wl_sim* s, float* const* u, float w, int proj) {
-  enq_proj_head(s, u, w, proj, s->st, 0);
+int host_projection(wl_sim* s, int ubuf, float w, int proj) {
+  enq_proj_head(s, ubuf, w, proj, s->st, 0);
   int rc = sync_state(s);
   if (rc) return rc;
   while (s->hs->cond) {
@@ -436,11 +469,11 @@ int host_projection(wl_sim* s, float* const* u, float w, int proj) {
 
 int host_step(wl_sim* s) {
   enq_stage(s, 1, s->st);
-  int rc = host_projection(s, s->ub, 1.f, 0);
+  int rc = host_projection(s, 1, 1.f, 0);
   if (rc) return rc;
   enq_correct(s, s->ub, s->uc, 1.f, 0, s->st);
   enq_stage(s, 2, s->st);
-  rc = host_projection(s, s->ub, 0.5f, 1);
+  rc = host_projection(s, 1, 0.5f, 1);
   if (rc) return rc;
   enq_correct(s, s->ub, s->ua, 0.5f, 1, s->st);
   PROF(s, s->st, WL_KCLASS_CONTROL, launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->st));
@@ -483,7 +516,7 @@ int build_step_graph(wl_sim* s) {
   // segment 1: stage 1, divergence + first residual
   WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   enq_stage(s, 1, s->cs);
-  enq_proj_head(s, s->ub, 1.f, 0, s->cs, 1);
+  enq_proj_head(s, 1, 1.f, 0, s->cs, 1);
   int rc = capture_leaf(s, leaf);
   WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
   if (rc) return rc;
@@ -493,7 +526,7 @@ int build_step_graph(wl_sim* s) {
   WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w1, nullptr, 1, cudaStreamCaptureModeThreadLocal));
   enq_correct(s, s->ub, s->uc, 1.f, 0, s->cs);
   enq_stage(s, 2, s->cs);
-  enq_proj_head(s, s->ub, 0.5f, 1, s->cs, 1);
+  enq_proj_head(s, 1, 0.5f, 1, s->cs, 1);
   rc = capture_leaf(s, leaf);
   WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
   if (rc) return rc;
@@ -625,6 +658,15 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       if (l == 0 && s->rf) ok = ok && make_field_map(&s->mrf, s->rf, L.g, ndim);
       L.tma = ok;
     }
+    // fine residual: 3-D, no periodic side
+    LevelBuf& L0 = s->lev[0];
+    bool ok = L0.tma && ndim == 3 && s->g.per == 0;
+    if (ok) ok = make_field_map(&s->mph, s->ph ? s->ph : L0.x, L0.g, ndim);
+    if (ok && s->pl) ok = make_field_map(&s->mpl, s->pl, L0.g, ndim);
+    float** bufs[3] = {s->ua, s->ub, s->uc};
+    for (int b = 0; b < 3 && ok; ++b)
+      for (int c = 0; c < ndim && ok; ++c) ok = make_field_map(&s->mu[b][c], bufs[b][c], L0.g, ndim);
+    s->resid_tma = ok;
   }
   if (!rc) {
     launch_measure(ndim, s->g, s->body, s->lev[0].L, s->st);
@@ -719,7 +761,7 @@ int wl_stage(wl_handle s, int stage) {
 
 int wl_project(wl_handle s, double w, int* vcycles_out, double* resid_out) {
   if (!s || !(w > 0.0)) return WL_EINVAL;
-  int rc = host_projection(s, s->ua, (float)w, 0);
+  int rc = host_projection(s, 0, (float)w, 0);
   if (rc) return rc;
   enq_correct(s, s->ua, s->ua, (float)w, 0, s->st);  // no neighbour reads: in place is safe
   rc = sync_state(s);
@@ -736,13 +778,10 @@ int wl_project(wl_handle s, double w, int* vcycles_out, double* resid_out) {
 int wl_gmg_vcycle(wl_handle s, double* resid_inf_out) {
   if (!s) return WL_EINVAL;
   // restrict the residual of the held system, run one cycle, measure the residual
-  launch_residual(s->D, fine_residual_args(s), s->st);
+  enq_fine_residual(s, RES_RESIDUAL, 0, 1.f, s->st);
   enq_vcycle_core(s, s->st);
   WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
-  ResArgs b = fine_residual_args(s);
-  b.zc = nullptr;
-  b.rout = nullptr;
-  launch_residual(s->D, b, s->st);
+  enq_fine_residual(s, RES_RESIDUAL, 0, 1.f, s->st);
   int rc = sync_state(s);
   if (rc) return rc;
   const float r = reinterpret_cast<const float&>(s->hs->norm_bits);

@@ -111,6 +111,24 @@ int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s);
 int launch_residual(int D, const ResArgs& a, cudaStream_t s);
 int launch_sweep(int D, const SweepArgs& a, cudaStream_t s);
 int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s);
+
+// TMA-staged fine residual / divergence (3-D, levels with no periodic side)
+struct ResidMaps {
+  CUtensorMap ph, pl, z, u0, u1, u2, L0, L1, L2;  // ph: the pressure (hi part, or the FP32 pressure)
+};
+struct ResidTmaArgs {
+  int div;             // divergence mode: z = div u * inv_w / dt is formed and stored
+  int df;              // pressure is the double-float ph + pl
+  float* z;            // divergence mode: right-hand side out
+  float* rout;         // residual out (or null)
+  float* zc;           // restricted residual (or null)
+  Grid g;
+  int cn[3];
+  int tz;              // planes per block (even)
+  float inv_w;
+  DevState* st;        // dt, residual maximum, timeout flag
+};
+int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s);
 int sweep_planes_per_block(const Grid& g);
 
 // Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.

@@ -164,199 +164,8 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   }
 }
 
-// 3-D residual / divergence pass with one thread per cell column marching up R3_Z
-// planes: the column's pressure (hi, lo), its z-face coefficients and (divergence
-// mode) its z-velocity are kept in a sliding window over planes k-1..k+1; x
-// neighbours come from the adjacent lanes by shuffles (loaded only at the warp's and
-// the grid's edges); in-plane neighbour offsets are fixed per thread.  Same
-// arithmetic, in the same order, as residual_cell.
-constexpr int R3_Z = 16;
-
-template <bool DIV, bool DF>
-__global__ void __launch_bounds__(256) k_residual3(ResArgs a) {
-  __shared__ float s_r[8][32];
-  __shared__ unsigned s_m[8];
-  const Grid& g = a.g;
-  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  const int i = blockIdx.x * 32 + lane, j = blockIdx.y * 8 + ty;
-  const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
-  const bool inxy = i < n0 && j < n1;
-  const bool per0 = is_per(g, 0), per1 = is_per(g, 1), per2 = is_per(g, 2);
-  const long long nn = (long long)n0 * n1;
-  const int kb = blockIdx.z * R3_Z, ke = min(kb + R3_Z, n2);
-  const int ic = min(i, n0 - 1), jc = min(j, n1 - 1);
-  // in-plane offsets of the own column and of its four neighbours (mapped), and
-  // whether the upper faces exist (the lower boundary faces store L = 0)
-  const long long c0 = ic + (long long)n0 * jc;
-  const long long cxm = ((ic > 0) ? ic - 1 : (per0 ? n0 - 1 : ic)) + (long long)n0 * jc;
-  const long long cxp = ((ic + 1 < n0) ? ic + 1 : (per0 ? 0 : ic)) + (long long)n0 * jc;
-  const long long cym = ic + (long long)n0 * ((jc > 0) ? jc - 1 : (per1 ? n1 - 1 : jc));
-  const long long cyp = ic + (long long)n0 * ((jc + 1 < n1) ? jc + 1 : (per1 ? 0 : jc));
-  const bool hxp = (ic + 1 < n0) || per0, hyp = (jc + 1 < n1) || per1;
-  const bool edge_xm = (lane == 0) || (i == 0), edge_xp = (lane == 31) || (i + 1 >= n0);
-  auto zoff = [&](int k) -> long long {  // mapped plane offset (clamped where the face is absent)
-    if (k < 0) return (per2 ? k + n2 : 0) * nn;
-    if (k >= n2) return (per2 ? k - n2 : n2 - 1) * nn;
-    return (long long)k * nn;
-  };
-  const float* P = DF ? a.ph : a.x;
-  // window over planes k-1, k, k+1 of the own column
-  float wh[3], wl[3], lz[2], uz[2];
-  {
-    const long long o[3] = {zoff(kb - 1), zoff(kb), zoff(kb + 1)};
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      wh[t] = __ldg(P + o[t] + c0);
-      wl[t] = DF ? __ldg(a.pl + o[t] + c0) : 0.f;
-    }
-    lz[0] = __ldg(a.L[2] + o[1] + c0);
-    lz[1] = (kb + 1 < n2 || per2) ? __ldg(a.L[2] + o[2] + c0) : 0.f;
-    if (DIV) {
-      uz[0] = __ldg(a.u[2] + o[1] + c0);
-      uz[1] = (kb + 1 < n2 || per2) ? __ldg(a.u[2] + o[2] + c0) : g.U[2];
-    }
-  }
-  unsigned mbits = 0u;
-  float vpair = 0.f;
-  for (int k = kb; k < ke; ++k) {
-    const long long ok = zoff(k);
-    const long long q = ok + c0;
-    // x neighbours of the own column at plane k
-    float xmh = __shfl_up_sync(0xffffffffu, wh[1], 1), xml = __shfl_up_sync(0xffffffffu, wl[1], 1);
-    float xph = __shfl_down_sync(0xffffffffu, wh[1], 1), xpl = __shfl_down_sync(0xffffffffu, wl[1], 1);
-    const float L0own = __ldg(a.L[0] + q);
-    float L0up = __shfl_down_sync(0xffffffffu, L0own, 1);
-    float ux = 0.f, uxp = 0.f;
-    if (DIV) {
-      ux = __ldg(a.u[0] + q);
-      uxp = __shfl_down_sync(0xffffffffu, ux, 1);
-    }
-    if (edge_xm) {
-      xmh = __ldg(P + ok + cxm);
-      xml = DF ? __ldg(a.pl + ok + cxm) : 0.f;
-    }
-    if (edge_xp) {
-      xph = __ldg(P + ok + cxp);
-      xpl = DF ? __ldg(a.pl + ok + cxp) : 0.f;
-      L0up = __ldg(a.L[0] + ok + cxp);
-      if (DIV) uxp = __ldg(a.u[0] + ok + cxp);
-    }
-    if (!hxp) {
-      L0up = 0.f;
-      if (DIV) uxp = g.U[0];
-    }
-    const float ymh = __ldg(P + ok + cym), yml = DF ? __ldg(a.pl + ok + cym) : 0.f;
-    const float yph = __ldg(P + ok + cyp), ypl = DF ? __ldg(a.pl + ok + cyp) : 0.f;
-    const float L1own = __ldg(a.L[1] + q);
-    const float L1up = hyp ? __ldg(a.L[1] + ok + cyp) : 0.f;
-    const float Lzup = (k + 1 < n2 || per2) ? lz[1] : 0.f;
-    float z;
-    if (DIV) {
-      const float uy = __ldg(a.u[1] + q);
-      const float uyp = hyp ? __ldg(a.u[1] + ok + cyp) : g.U[1];
-      const float uzp = (k + 1 < n2 || per2) ? uz[1] : g.U[2];
-      float div = 0.f;
-      div += uxp - ux;
-      div += uyp - uy;
-      div += uzp - uz[0];
-      z = div * a.inv_w * a.st->inv_dtf;
-      if (inxy) a.z[q] = z;
-    } else {
-      z = __ldg(a.z + q);
-    }
-    float r;
-    if (DF) {
-      const float h0 = wh[1], l0 = wl[1];
-      float ah = 0.f, al = 0.f;
-      auto face = [&](float L, float hn, float ln) {
-        float dh, dl, th, tl, sh, sl;
-        two_sum(hn, -h0, dh, dl);
-        dl += ln - l0;
-        two_prod(L, dh, th, tl);
-        tl = fmaf(L, dl, tl);
-        two_sum(ah, th, sh, sl);
-        ah = sh;
-        al += sl + tl;
-      };
-      face(L0up, xph, xpl);
-      face(L0own, xmh, xml);
-      face(L1up, yph, ypl);
-      face(L1own, ymh, yml);
-      face(Lzup, wh[2], wl[2]);
-      face(lz[0], wh[0], wl[0]);
-      float rh, rl;
-      two_sum(z, -ah, rh, rl);
-      r = rh + (rl - al);
-    } else {
-      const float x0 = wh[1];
-      float acc = 0.f;
-      acc += L0up * (xph - x0) + L0own * (xmh - x0);
-      acc += L1up * (yph - x0) + L1own * (ymh - x0);
-      acc += Lzup * (wh[2] - x0) + lz[0] * (wh[0] - x0);
-      r = z - acc;
-    }
-    if (inxy) {
-      if (a.rout) a.rout[q] = r;
-      mbits = max(mbits, __float_as_uint(fabsf(r)));
-    } else {
-      r = 0.f;
-    }
-    // restriction: sum the plane pair in registers, x pairs by shuffle, y pairs in shared memory
-    if (a.zc) {
-      vpair = ((k - kb) & 1) ? vpair + r : r;
-      if (((k - kb) & 1) || k + 1 == ke) {
-        float v = vpair + __shfl_xor_sync(0xffffffffu, vpair, 1);
-        s_r[ty][lane] = v;
-        __syncthreads();
-        if (tid < 64) {
-          const int cx = tid & 15, cy = tid >> 4;
-          const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
-          const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 4 + cy, K = k >> 1;
-          if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
-            a.zc[(long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K)] = sum;
-        }
-        __syncthreads();
-      }
-    }
-    // slide the window up one plane
-    if (k + 1 < ke) {
-      const long long o2 = zoff(k + 2);
-      wh[0] = wh[1];
-      wl[0] = wl[1];
-      wh[1] = wh[2];
-      wl[1] = wl[2];
-      wh[2] = __ldg(P + o2 + c0);
-      wl[2] = DF ? __ldg(a.pl + o2 + c0) : 0.f;
-      lz[0] = lz[1];
-      lz[1] = (k + 2 < n2 || per2) ? __ldg(a.L[2] + o2 + c0) : 0.f;
-      if (DIV) {
-        uz[0] = uz[1];
-        uz[1] = (k + 2 < n2 || per2) ? __ldg(a.u[2] + o2 + c0) : g.U[2];
-      }
-    }
-  }
-  const unsigned m = block_max_bits<256>(mbits, s_m);
-  if (tid == 0 && m) atomicMax(&a.st->norm_bits, m);
-}
-
 int launch_residual(int D, const ResArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
-  if (D == 3 && (a.mode == RES_RESIDUAL || a.mode == RES_DIVERGENCE)) {
-    dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + R3_Z - 1) / R3_Z);
-    const bool df = a.ph != nullptr;
-    if (a.mode == RES_DIVERGENCE) {
-      if (df)
-        k_residual3<true, true><<<grd, 256, 0, s>>>(a);
-      else
-        k_residual3<true, false><<<grd, 256, 0, s>>>(a);
-    } else {
-      if (df)
-        k_residual3<false, true><<<grd, 256, 0, s>>>(a);
-      else
-        k_residual3<false, false><<<grd, 256, 0, s>>>(a);
-    }
-    return 0;
-  }
   if (D == 3) {
     dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + 2 * RS_ZP - 1) / (2 * RS_ZP));
     k_residual<3><<<grd, 256, 0, s>>>(a);

@@ -1,7 +1,7 @@
-// Red-black Gauss-Seidel sweep with TMA staging (the multigrid smoother of
-// project!, Section 2; red-black ordering is this library's reading of the
-// smoother).  Same arithmetic and result as k_sweep; the difference is how the data
-// reaches shared memory.
+// TMA-staged multigrid kernels of project! (Section 2): the red-black Gauss-Seidel
+// sweep (red-black ordering is this library's reading of the smoother) and the fine
+// residual / divergence pass.  Same arithmetic and results as k_sweep and
+// k_residual; the difference is how the data reaches shared memory.
 //
 // A tile of 64 x 8 cells marches up through `tz` planes.  For every plane the five
 // fields it needs (iterate, right-hand side, the three face-coefficient fields) are
@@ -237,6 +237,214 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Fine residual / divergence pass (3-D, no periodic side), TMA-staged.  Per plane the
+// fields go to two rings: "column" fields needed at planes k-1..k+1 (pressure hi/lo,
+// z-face coefficients, and in divergence mode the z-velocity) in 4 slots, "plane"
+// fields needed only at plane k (right-hand side or x/y velocities, x/y face
+// coefficients) in 3 slots; plane k+2 is staged while plane k is computed.  Each
+// thread computes cells (lane, row) and (lane + 32, row) of the 64 x 8 tile, so the
+// restriction pairs x neighbours by a shuffle, y neighbours through shared memory
+// and z neighbours in registers.  Zero fill supplies L = 0 across the walls; the
+// velocity on an upper wall face is the boundary value, patched explicitly.
+template <bool DIV, bool DF>
+__global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ ResidMaps m, ResidTmaArgs a) {
+  constexpr int NA = (DF ? 2 : 1) + 1 + (DIV ? 1 : 0);  // column fields: ph, [pl], L2, [u2]
+  constexpr int NBF = DIV ? 4 : 3;                        // plane fields: (z | u0, u1), L0, L1
+  constexpr int SA = 4, SB = 3, NBAR = 4;
+  extern __shared__ unsigned char smem_raw[];
+  float* abase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  float* bbase = abase + (size_t)SA * NA * BOX;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bbase + (size_t)SB * NBF * BOX);
+  __shared__ float s_r[8][64];
+  __shared__ unsigned s_m[8];
+  const Grid& g = a.g;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int kb = blockIdx.z * a.tz, ke = min(kb + a.tz, g.n[2]);
+  const int pa_first = kb - 1, pb_first = kb, p_last = ke;
+  // column field f of plane p: 0 ph, 1 pl (DF), then L2, then u2 (DIV)
+  auto A = [&](int p, int f) -> float* { return abase + ((size_t)((p - pa_first) % SA) * NA + f) * BOX; };
+  // plane field f of plane p: DIV: 0 u0, 1 u1, 2 L0, 3 L1; else 0 z, 1 L0, 2 L1
+  auto B = [&](int p, int f) -> float* { return bbase + ((size_t)((p - pb_first) % SB) * NBF + f) * BOX; };
+  auto bar = [&](int p) { return smem_addr(&bars[(p - pa_first) % NBAR]); };
+  auto phase = [&](int p) { return (uint32_t)(((p - pa_first) / NBAR) & 1); };
+  constexpr int fL2 = DF ? 2 : 1, fU2 = fL2 + 1;
+  constexpr int fL0 = DIV ? 2 : 1, fL1 = fL0 + 1;
+
+  if (tid == 0) {
+    for (int b = 0; b < NBAR; ++b) mbar_init(smem_addr(&bars[b]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  int p_issued = pa_first - 1;
+  auto issue = [&](int p) {  // thread 0: stage plane p
+    if (p > p_last) return;
+    p_issued = p;
+    const bool plane = p >= pb_first && p < ke;
+    const uint32_t bytes = (uint32_t)((NA + (plane ? NBF : 0)) * BOX * sizeof(float));
+    const uint32_t br = bar(p);
+    mbar_expect_tx(br, bytes);
+    const int x = i0 - 4, y = j0 - 2;
+    tma_load(smem_addr(A(p, 0)), &m.ph, x, y, p, br, 3);
+    if (DF) tma_load(smem_addr(A(p, 1)), &m.pl, x, y, p, br, 3);
+    tma_load(smem_addr(A(p, fL2)), &m.L2, x, y, p, br, 3);
+    if (DIV) tma_load(smem_addr(A(p, fU2)), &m.u2, x, y, p, br, 3);
+    if (plane) {
+      if (DIV) {
+        tma_load(smem_addr(B(p, 0)), &m.u0, x, y, p, br, 3);
+        tma_load(smem_addr(B(p, 1)), &m.u1, x, y, p, br, 3);
+      } else {
+        tma_load(smem_addr(B(p, 0)), &m.z, x, y, p, br, 3);
+      }
+      tma_load(smem_addr(B(p, fL0)), &m.L0, x, y, p, br, 3);
+      tma_load(smem_addr(B(p, fL1)), &m.L1, x, y, p, br, 3);
+    }
+  };
+  auto bail = [&](int p_fail) {
+    if (tid == 0) {
+      atomicOr(&a.st->status, 4);
+      for (int p = p_fail; p <= p_issued; ++p) mbar_wait(bar(p), phase(p));
+    }
+    __syncthreads();
+  };
+  if (tid == 0)
+    for (int p = pa_first; p <= min(pa_first + 2, p_last); ++p) issue(p);
+  for (int p = pa_first; p <= kb; ++p) {
+    const bool ok = mbar_wait(bar(p), phase(p));
+    if (__syncthreads_or(!ok)) return bail(p);
+  }
+  const float inv = DIV ? a.inv_w * a.st->inv_dtf : 0.f;
+  unsigned mbits = 0u;
+  float vpair[2] = {0.f, 0.f};
+  for (int k = kb; k < ke; ++k) {
+    {
+      const bool ok = mbar_wait(bar(k + 1), phase(k + 1));
+      if (__syncthreads_or(!ok)) return bail(k + 1);
+    }
+    // every thread is past plane k-2's column fields and plane k-1's plane fields
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(k + 2);
+    }
+    const float* ph0 = A(k, 0);
+    const float* pl0 = DF ? A(k, 1) : nullptr;
+    const float* phm = A(k - 1, 0);
+    const float* plm = DF ? A(k - 1, 1) : nullptr;
+    const float* php = A(k + 1, 0);
+    const float* plp = DF ? A(k + 1, 1) : nullptr;
+    const float* L0 = B(k, fL0);
+    const float* L1 = B(k, fL1);
+    const float* L2 = A(k, fL2);
+    const float* L2u = A(k + 1, fL2);
+    const int gj = j0 + ty;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int ii = lane + 32 * h;
+      const int gi = i0 + ii;
+      const int e = (ty + 2) * BX + ii + 4;
+      const bool in = gi < g.n[0] && gj < g.n[1];
+      float z;
+      if (DIV) {
+        const float* U0 = B(k, 0);
+        const float* U1 = B(k, 1);
+        const float uxp = (gi + 1 < g.n[0]) ? U0[e + 1] : g.U[0];
+        const float uyp = (gj + 1 < g.n[1]) ? U1[e + BX] : g.U[1];
+        const float uzp = (k + 1 < g.n[2]) ? A(k + 1, fU2)[e] : g.U[2];
+        float div = 0.f;
+        div += uxp - U0[e];
+        div += uyp - U1[e];
+        div += uzp - A(k, fU2)[e];
+        z = div * inv;
+        if (in) a.z[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = z;
+      } else {
+        z = B(k, 0)[e];
+      }
+      float r;
+      if (DF) {
+        const float h0 = ph0[e], l0 = pl0[e];
+        float ah = 0.f, al = 0.f;
+        auto face = [&](float L, float hn, float ln) {
+          float dh, dl, th, tl, sh, sl;
+          two_sum(hn, -h0, dh, dl);
+          dl += ln - l0;
+          two_prod(L, dh, th, tl);
+          tl = fmaf(L, dl, tl);
+          two_sum(ah, th, sh, sl);
+          ah = sh;
+          al += sl + tl;
+        };
+        // a missing neighbour across a wall reads 0 with a 0 coefficient: adds exactly 0
+        face(L0[e + 1], ph0[e + 1], pl0[e + 1]);
+        face(L0[e], ph0[e - 1], pl0[e - 1]);
+        face(L1[e + BX], ph0[e + BX], pl0[e + BX]);
+        face(L1[e], ph0[e - BX], pl0[e - BX]);
+        face(L2u[e], php[e], plp[e]);
+        face(L2[e], phm[e], plm[e]);
+        float rh, rl;
+        two_sum(z, -ah, rh, rl);
+        r = rh + (rl - al);
+      } else {
+        const float x0 = ph0[e];
+        float acc = 0.f;
+        acc += L0[e + 1] * (ph0[e + 1] - x0) + L0[e] * (ph0[e - 1] - x0);
+        acc += L1[e + BX] * (ph0[e + BX] - x0) + L1[e] * (ph0[e - BX] - x0);
+        acc += L2u[e] * (php[e] - x0) + L2[e] * (phm[e] - x0);
+        r = z - acc;
+      }
+      if (in) {
+        if (a.rout) a.rout[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = r;
+        mbits = max(mbits, __float_as_uint(fabsf(r)));
+      } else {
+        r = 0.f;
+      }
+      vpair[h] = ((k - kb) & 1) ? vpair[h] + r : r;
+    }
+    // restriction of each plane pair: x pairs by shuffle, y pairs in shared memory
+    if (a.zc && ((k - kb) & 1)) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) s_r[ty][lane + 32 * h] = vpair[h] + __shfl_xor_sync(0xffffffffu, vpair[h], 1);
+      __syncthreads();
+      if (tid < 128) {
+        const int cx = tid & 31, cy = tid >> 5;
+        const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
+        const int I = (i0 >> 1) + cx, J = (j0 >> 1) + cy, K = k >> 1;
+        if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
+          a.zc[(long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K)] = sum;
+      }
+    }
+    __syncthreads();
+  }
+  const unsigned mb = block_max_bits<256>(mbits, s_m);
+  if (tid == 0 && mb) atomicMax(&a.st->norm_bits, mb);
+}
+
+size_t resid_tma_smem(bool div, bool df) {
+  const int na = (df ? 2 : 1) + 1 + (div ? 1 : 0), nb = div ? 4 : 3;
+  return ((size_t)4 * na + (size_t)3 * nb) * BOX * sizeof(float) + 4 * sizeof(uint64_t) + 128;
+}
+
+int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s) {
+  const Grid& g = a.g;
+  const bool div = a.div != 0, df = a.df != 0;
+  const size_t smem = resid_tma_smem(div, df);
+  dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
+  if (div && df) {
+    cudaFuncSetAttribute(k_resid_tma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_resid_tma<true, true><<<grd, 256, smem, s>>>(m, a);
+  } else if (div) {
+    cudaFuncSetAttribute(k_resid_tma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_resid_tma<true, false><<<grd, 256, smem, s>>>(m, a);
+  } else if (df) {
+    cudaFuncSetAttribute(k_resid_tma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_resid_tma<false, true><<<grd, 256, smem, s>>>(m, a);
+  } else {
+    cudaFuncSetAttribute(k_resid_tma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_resid_tma<false, false><<<grd, 256, smem, s>>>(m, a);
+  }
+  return 0;
 }
 
 size_t sweep_tma_smem() {
