@@ -34,13 +34,18 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
   const int k0 = (D == 3) ? blockIdx.z * ST_TZ : 0;
   const int k1 = (D == 3) ? min(k0 + ST_TZ, g.n[2]) : 1;
   const int i = i0 + tx, j = j0 + ty;
-  const bool own = (i < g.n[0]) && (j < g.n[1]);
+  const bool own_cell = (i < g.n[0]) && (j < g.n[1]);
   const float dt = *a.dt;
   const bool adv = a.advect != 0;
   const float nu = a.nu;
 
   auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
-  auto S = [&](int c, int sl, int jj, int ii) -> float { return s_u[c][sl][jj + 2][ii + 2]; };
+  // flat shared-memory view: component c of plane kk starts at off(c, kk); a tile
+  // position (ii, jj) adds (jj + 2) * ST_HX + ii + 2
+  const float* sf = &s_u[0][0][0][0];
+  auto off = [&](int c, int kk) -> int { return (c * NP + slot(kk)) * (ST_HY * ST_HX); };
+  constexpr int HX = ST_HX;
+  int k_cur = k0;  // plane whose x- and y-face fluxes are being formed
 
   auto load_plane = [&](int kk) {
     const int sl = slot(kk);
@@ -61,23 +66,34 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
     }
   };
 
-  // lower x-face flux of the u_c control volume at tile position (ii, jj) in plane slot sl
-  // (slm: slot of the plane below, for the advecting velocity of c = z)
-  auto flux_x = [&](int c, int ii, int jj, int sl, int slm) -> float {
-    const float a2 = S(0, sl, jj, ii) + (c == 0 ? S(0, sl, jj, ii - 1) : (c == 1 ? S(0, sl, jj - 1, ii) : S(0, slm, jj, ii)));
-    return mom_flux(S(c, sl, jj, ii - 2), S(c, sl, jj, ii - 1), S(c, sl, jj, ii), S(c, sl, jj, ii + 1), a2, nu, adv);
+  // Lower x-face flux of the u_c control volume at flat position pos of plane k
+  // (o: component offsets of plane k; om2: offset of component z in plane k-1, for
+  // the advecting velocity of c = z).
+  auto flux_x = [&](int c, const int* o, int om2, int pos) -> float {
+    const float* U = sf + off(c, k_cur) + pos;
+    const float* A = sf + o[0] + pos;
+    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : sf[om2 - o[2] + o[0] + pos]));
+    return mom_flux(U[-2], U[-1], U[0], U[1], a2, nu, adv);
   };
-  auto flux_y = [&](int c, int ii, int jj, int sl, int slm) -> float {
-    const float a2 = S(1, sl, jj, ii) + (c == 0 ? S(1, sl, jj, ii - 1) : (c == 1 ? S(1, sl, jj - 1, ii) : S(1, slm, jj, ii)));
-    return mom_flux(S(c, sl, jj - 2, ii), S(c, sl, jj - 1, ii), S(c, sl, jj, ii), S(c, sl, jj + 1, ii), a2, nu, adv);
+  auto flux_y = [&](int c, const int* o, int om2, int pos) -> float {
+    const float* U = sf + off(c, k_cur) + pos;
+    const float* A = sf + o[1] + pos;
+    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : sf[om2 - o[2] + o[1] + pos]));
+    return mom_flux(U[-2 * HX], U[-HX], U[0], U[HX], a2, nu, adv);
   };
-  // lower z-face flux at plane kf
-  auto flux_z = [&](int c, int ii, int jj, int kf) -> float {
-    const int s2 = slot(kf - 2), s1 = slot(kf - 1), s0 = slot(kf), sp = slot(kf + 1);
-    const float a2 = S(2 % D, s0, jj, ii) +
-                     (c == 0 ? S(2 % D, s0, jj, ii - 1) : (c == 1 ? S(2 % D, s0, jj - 1, ii) : S(2 % D, s1, jj, ii)));
-    return mom_flux(S(c, s2, jj, ii), S(c, s1, jj, ii), S(c, s0, jj, ii), S(c, sp, jj, ii), a2, nu, adv);
+  // lower z-face flux at plane kf: q[t][c] = offsets of planes kf-2+t
+  auto flux_z = [&](int c, const int (*q)[3], int pos) -> float {
+    const float* A = sf + q[2][2] + pos;  // u_z at plane kf
+    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : sf[q[1][2] + pos]));
+    return mom_flux(sf[q[0][c] + pos], sf[q[1][c] + pos], sf[q[2][c] + pos], sf[q[3][c] + pos], a2, nu, adv);
   };
+  // offsets of the four planes kk-2 .. kk+1 (flux_z of face kk)
+  auto zoffs = [&](int kk, int (*q)[3]) {
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) q[t][c] = (c < D) ? off(c, kk - 2 + t) : 0;
+  };
+  const int own = (ty + 2) * HX + (tx + 2);
 
   float fzl[3] = {0.f, 0.f, 0.f};
   if (D == 3) {
@@ -86,51 +102,59 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
     load_plane(k0);
     load_plane(k0 + 1);
     __syncthreads();
+    int q[4][3];
+    zoffs(k0, q);
 #pragma unroll
-    for (int c = 0; c < D; ++c) fzl[c] = flux_z(c, tx, ty, k0);
+    for (int c = 0; c < D; ++c) fzl[c] = flux_z(c, q, own);
     __syncthreads();
   }
 
   for (int k = k0; k < k1; ++k) {
     load_plane(D == 3 ? k + 2 : 0);
     __syncthreads();
-    const int sk = slot(k), skm = slot(k - 1);
+    k_cur = k;
+    int o[3], om2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] = (c < D) ? off(c, k) : 0;
+    if (D == 3) om2 = off(2 % D, k - 1);
     float fzu[3] = {0.f, 0.f, 0.f};
+    int q[4][3];
+    if (D == 3) zoffs(k + 1, q);
 #pragma unroll
     for (int c = 0; c < D; ++c) {
-      s_fx[c][ty][tx] = flux_x(c, tx, ty, sk, skm);
-      s_fy[c][ty][tx] = flux_y(c, tx, ty, sk, skm);
-      if (D == 3) fzu[c] = flux_z(c, tx, ty, k + 1);
+      s_fx[c][ty][tx] = flux_x(c, o, om2, own);
+      s_fy[c][ty][tx] = flux_y(c, o, om2, own);
+      if (D == 3) fzu[c] = flux_z(c, q, own);
     }
     // fluxes through the upper edge faces of the tile
     if (tid < D * ST_TY) {
       const int c = tid / ST_TY, row = tid - c * ST_TY;
-      s_fx[c][row][ST_TX] = flux_x(c, ST_TX, row, sk, skm);
+      s_fx[c][row][ST_TX] = flux_x(c, o, om2, (row + 2) * HX + ST_TX + 2);
     } else if (tid < D * ST_TY + D * ST_TX) {
       const int t = tid - D * ST_TY;
       const int c = t / ST_TX, col = t - c * ST_TX;
-      s_fy[c][ST_TY][col] = flux_y(c, col, ST_TY, sk, skm);
+      s_fy[c][ST_TY][col] = flux_y(c, o, om2, (ST_TY + 2) * HX + col + 2);
     }
     __syncthreads();
-    if (own) {
-      const long long q = cell_index(g, i, j, k);
+    if (own_cell) {
+      const long long qg = cell_index(g, i, j, k);
       const int I[3] = {i, j, k};
 #pragma unroll
       for (int c = 0; c < D; ++c) {
         float r = (s_fx[c][ty][tx] - s_fx[c][ty][tx + 1]) + (s_fy[c][ty][tx] - s_fy[c][ty + 1][tx]);
         if (D == 3) r += fzl[c] - fzu[c];
         const bool upd = is_per(g, c) || I[c] >= 1;
-        float o;
+        float ov;
         if (!upd) {
-          o = g.U[c];
+          ov = g.U[c];
         } else {
-          const float uc = S(c, sk, ty, tx);
-          const float u0 = (a.stage == 1) ? uc : __ldg(a.u0[c] + q);
+          const float uc = sf[o[c] + own];
+          const float u0 = (a.stage == 1) ? uc : __ldg(a.u0[c] + qg);
           const float f = fmaf(dt, r, u0);
-          const float m = __ldg(a.mu0[c] + q);
-          o = (a.stage == 1) ? m * f : 0.5f * (uc + m * f);
+          const float m = __ldg(a.mu0[c] + qg);
+          ov = (a.stage == 1) ? m * f : 0.5f * (uc + m * f);
         }
-        a.out[c][q] = o;
+        a.out[c][qg] = ov;
       }
     }
 #pragma unroll

@@ -136,42 +136,57 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
     }
     return true;
   };
-  // Gauss-Seidel value of the cell at tile position (ii, jj) of plane p (all operands
-  // staged; out-of-range faces carry 0, so cells outside the grid come out as 0).
+  // operand planes of a relaxation at plane p, looked up once per phase
+  struct Planes {
+    const float *xm, *xp, *z, *l0, *l1, *l2, *l2u;
+    float* x0;
+  };
+  auto planes = [&](int p) -> Planes {
+    Planes P;
+    P.x0 = X(p);
+    P.xm = (D == 3) ? X(p - 1) : P.x0;
+    P.xp = (D == 3) ? X(p + 1) : P.x0;
+    P.z = C(p, 0);
+    P.l0 = C(p, 1);
+    P.l1 = C(p, 2);
+    P.l2 = (D == 3) ? C(p, 3) : P.l0;
+    P.l2u = (D == 3) ? C(p + 1, 3) : P.l0;
+    return P;
+  };
+  // Gauss-Seidel value of the cell at shared index e (all operands staged;
+  // out-of-range faces carry 0, so cells outside the grid come out as 0).
   // Same operation order as k_sweep (upper then lower face; x, y, z), same bits.
-  auto relax = [&](int ii, int jj, int p) -> float {
-    const int e = (jj + 2) * BX + (ii + 4);
-    const float* Xp = X(p);
-    const float* L0 = C(p, 1);
-    const float* L1 = C(p, 2);
-    float sum = fmaf(L0[e + 1], Xp[e + 1], 0.f);
-    sum = fmaf(L0[e], Xp[e - 1], sum);
-    float dg = L0[e + 1] + L0[e];
-    sum = fmaf(L1[e + BX], Xp[e + BX], sum);
-    sum = fmaf(L1[e], Xp[e - BX], sum);
-    dg += L1[e + BX] + L1[e];
+  auto relax = [&](const Planes& P, int e) -> float {
+    float sum = fmaf(P.l0[e + 1], P.x0[e + 1], 0.f);
+    sum = fmaf(P.l0[e], P.x0[e - 1], sum);
+    float dg = P.l0[e + 1] + P.l0[e];
+    sum = fmaf(P.l1[e + BX], P.x0[e + BX], sum);
+    sum = fmaf(P.l1[e], P.x0[e - BX], sum);
+    dg += P.l1[e + BX] + P.l1[e];
     if (D == 3) {
-      const float lu = C(p + 1, 3)[e], ll = C(p, 3)[e];
-      sum = fmaf(lu, X(p + 1)[e], sum);
-      sum = fmaf(ll, X(p - 1)[e], sum);
+      const float lu = P.l2u[e], ll = P.l2[e];
+      sum = fmaf(lu, P.xp[e], sum);
+      sum = fmaf(ll, P.xm[e], sum);
       dg += lu + ll;
     }
-    return (dg > 0.f) ? __fdividef(sum - C(p, 0)[e], dg) : 0.f;
+    return (dg > 0.f) ? __fdividef(sum - P.z[e], dg) : 0.f;
   };
   // red cells of plane p on the tile plus a 1-cell halo (rows -1..8, columns -1..64):
   // ten 32-cell tasks (two adjacent rows x half the tile's columns) and the ten
   // edge-column cells
   auto red_plane = [&](int p) {
-    float* Xp = X(p);
+    const Planes P = planes(p);
     for (int t = warp; t < 10; t += 8) {
       const int jj = 2 * (t >> 1) + (lane >> 4) - 1;
       const int ii = 32 * (t & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + p) & 1);
-      Xp[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, p);
+      const int e = (jj + 2) * BX + (ii + 4);
+      P.x0[e] = relax(P, e);
     }
     if (warp == 2 && lane < 10) {
       const int jj = lane - 1;
       const int ii = ((i0 + j0 + jj + p) & 1) ? -1 : 64;
-      Xp[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, p);
+      const int e = (jj + 2) * BX + (ii + 4);
+      P.x0[e] = relax(P, e);
     }
   };
   // a copy timed out at plane p_fail: flag it, wait (bounded) for the planes still in
@@ -207,9 +222,11 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
     __syncthreads();
     // black cells of plane k: eight 32-cell tasks (two adjacent rows x half the columns)
     {
+      const Planes P = planes(k);
       const int jj = 2 * (warp >> 1) + (lane >> 4);
       const int ii = 32 * (warp & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + k + 1) & 1);
-      X(k)[(jj + 2) * BX + (ii + 4)] = relax(ii, jj, k);
+      const int e = (jj + 2) * BX + (ii + 4);
+      P.x0[e] = relax(P, e);
     }
     __syncthreads();
     // write the tile's plane k: thread (tx, ty) takes columns 2tx, 2tx+1 of row ty
