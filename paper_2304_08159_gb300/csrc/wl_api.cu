@@ -38,6 +38,7 @@ struct LevelBuf {
   float* x2;
   bool tma;                       // tensor maps below are valid (n_0 % 4 == 0)
   CUtensorMap mx, mx2, mz, mL[3];  // TMA descriptors of this level's fields
+  CUtensorMap sz, sL[3];           // the sweep's shorter coefficient boxes
 };
 
 constexpr int kMaxLevels = 16;
@@ -65,7 +66,7 @@ struct wl_sim {
   double* fout = nullptr;
   float* ph = nullptr;        // precision 1: fine-level pressure as the double-float ph + pl
   float* pl = nullptr;
-  CUtensorMap mrf{};          // TMA descriptor of rf
+  CUtensorMap mrf{}, srf{};   // TMA descriptors of rf (residual box, sweep box)
   CUtensorMap mph{}, mpl{};   // TMA descriptors of the fine pressure (ph: hi part or FP32 pressure)
   CUtensorMap mu[3][3]{};     // TMA descriptors of the velocity buffers A, B, C (components)
   bool resid_tma = false;     // the fine residual uses the TMA-staged kernel
@@ -151,14 +152,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// Box of 72 x 12 [x 1] floats over a level field (x fastest), zero fill out of range.
-// Needs n_0 % 4 == 0 (16-byte row pitch) and a 16-byte aligned base.
-bool make_field_map(CUtensorMap* m, const float* ptr, const Grid& g, int D) {
+// Box of 72 x rows [x 1] floats over a level field (x fastest), zero fill out of
+// range.  Needs n_0 % 4 == 0 (16-byte row pitch) and a 16-byte aligned base.
+bool make_field_map(CUtensorMap* m, const float* ptr, const Grid& g, int D, int rows = SWEEP_TY + 4) {
   auto enc = tensor_map_encoder();
   if (!enc || g.n[0] % 4 != 0 || ((uintptr_t)ptr & 15u)) return false;
   cuuint64_t dims[3] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2]};
   cuuint64_t strides[2] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)g.n[0] * g.n[1] * 4};
-  cuuint32_t box[3] = {(cuuint32_t)(SWEEP_TX + 8), (cuuint32_t)(SWEEP_TY + 4), 1};
+  cuuint32_t box[3] = {(cuuint32_t)(SWEEP_TX + 8), (cuuint32_t)rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)D, (void*)ptr, dims, strides, box, es,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -356,10 +357,10 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
     if (L.tma) {
       SweepMaps m;
       m.x = in >= 0 ? *bmaps[in] : L.mx;
-      m.z = refine ? s->mrf : L.mz;
-      m.L0 = L.mL[0];
-      m.L1 = L.mL[1];
-      m.L2 = L.mL[s->D == 3 ? 2 : 1];
+      m.z = refine ? s->srf : L.sz;
+      m.L0 = L.sL[0];
+      m.L1 = L.sL[1];
+      m.L2 = L.sL[s->D == 3 ? 2 : 0];
       SweepTmaArgs t{};
       t.has_x = in >= 0;
       t.xc = a.xc;
@@ -653,9 +654,12 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
     for (int l = 0; l < s->nlev; ++l) {
       LevelBuf& L = s->lev[l];
       bool ok = make_field_map(&L.mx, L.x, L.g, ndim) && make_field_map(&L.mx2, L.x2, L.g, ndim) &&
-                make_field_map(&L.mz, L.z, L.g, ndim);
-      for (int c = 0; c < ndim; ++c) ok = ok && make_field_map(&L.mL[c], L.L[c], L.g, ndim);
-      if (l == 0 && s->rf) ok = ok && make_field_map(&s->mrf, s->rf, L.g, ndim);
+                make_field_map(&L.mz, L.z, L.g, ndim) && make_field_map(&L.sz, L.z, L.g, ndim, SWEEP_CROWS);
+      for (int c = 0; c < ndim; ++c)
+        ok = ok && make_field_map(&L.mL[c], L.L[c], L.g, ndim) &&
+             make_field_map(&L.sL[c], L.L[c], L.g, ndim, SWEEP_CROWS + (c == 1 ? 1 : 0));
+      if (l == 0 && s->rf)
+        ok = ok && make_field_map(&s->mrf, s->rf, L.g, ndim) && make_field_map(&s->srf, s->rf, L.g, ndim, SWEEP_CROWS);
       L.tma = ok;
     }
     // fine residual: 3-D, no periodic side

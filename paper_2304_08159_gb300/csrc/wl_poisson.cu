@@ -411,10 +411,32 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 }
 
 // planes per block: enough blocks to fill the GPU, at most 32 planes per march
+// Planes per block of both sweep kernels: the z-blocking that minimises the modelled
+// time, whole waves of blocks (three resident per SM) times the planes a block
+// marches through plus about 1.5 planes of prologue and epilogue work.
 int sweep_planes_per_block(const Grid& g) {
+  static int nsm = 0;
+  if (nsm <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        nsm <= 0) {
+      cudaGetLastError();
+      nsm = 152;
+    }
+  }
   const long long tiles = (long long)((g.n[0] + SW_TX - 1) / SW_TX) * ((g.n[1] + SW_TY - 1) / SW_TY);
-  int tz = (int)((tiles * g.n[2] + 1215) / 1216);
-  return tz < 2 ? 2 : (tz > 32 ? 32 : tz);
+  const long long wave = 3LL * nsm;
+  int best = 2;
+  double best_cost = 1e300;
+  for (int tz = 2; tz <= 32; ++tz) {
+    const long long nb = tiles * ((g.n[2] + tz - 1) / tz);
+    const double cost = (double)((nb + wave - 1) / wave) * (tz + 1.5);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = tz;
+    }
+  }
+  return best;
 }
 
 int launch_sweep(int D, const SweepArgs& a, cudaStream_t s) {

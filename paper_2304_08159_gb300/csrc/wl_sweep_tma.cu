@@ -28,9 +28,15 @@ namespace {
 constexpr int TX = SWEEP_TX, TY = SWEEP_TY;  // tile
 constexpr int BX = TX + 8, BY = TY + 4;  // box: x from i0-4 (aligned), y from j0-2
 constexpr int BOX = BX * BY;          // floats per field per plane
-constexpr int XR = 5;                 // iterate slots (planes k-1 .. k+3)
-constexpr int CR = 4;                 // coefficient slots (planes k .. k+3), 4 fields each: z, L0, L1, L2
-constexpr int NB = 5;                 // mbarriers (one per staged plane, reused every NB planes)
+// sweep: coefficient boxes of CROWS rows from j0-1 (z, L0, L2) and L1ROWS (L1, whose
+// upper face of row 8 is row 9); slots padded to 128-byte multiples
+constexpr int CROWS = SWEEP_CROWS, L1ROWS = SWEEP_CROWS + 1;
+constexpr int CSLOT = (BX * CROWS + 31) / 32 * 32, L1SLOT = (BX * L1ROWS + 31) / 32 * 32;
+constexpr int XR = 6;   // iterate slots (planes k-1 .. k+3, and k+4 in flight)
+constexpr int L2R = 5;  // L2 slots (planes k .. k+3, and k+4 in flight)
+constexpr int CR = 4;   // z, L0, L1 slots (planes k .. k+2, and k+3 in flight)
+constexpr int SW_NT = 320;  // sweep threads: 10 warps
+static_assert(BOX * 4 % 128 == 0, "iterate slots keep 128-byte alignment");
 constexpr unsigned kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -77,66 +83,73 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
 }  // namespace
 
 template <int D>
-__global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
+__global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
   extern __shared__ unsigned char smem_raw[];
-  // 128-byte aligned slot buffers (iterate ring, coefficient ring), then the mbarriers
+  // 128-byte aligned slot rings (iterate, L2, z, L0, L1), then the mbarriers
   float* xbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float* cbase = xbase + (size_t)XR * BOX;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(cbase + (size_t)CR * 4 * BOX);
+  float* l2base = xbase + (size_t)XR * BOX;
+  float* zbase = l2base + (size_t)L2R * CSLOT;
+  float* l0base = zbase + (size_t)CR * CSLOT;
+  float* l1base = l0base + (size_t)CR * CSLOT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(l1base + (size_t)CR * L1SLOT);
   const Grid& g = a.g;
-  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
   if (sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
-  const int p_first = (D == 3) ? k0 - 2 : 0;   // first plane whose iterate is staged
-  const int pc_first = (D == 3) ? k0 - 1 : 0;  // first plane whose coefficients are staged
-  const int p_last = (D == 3) ? k1 + 1 : 0;    // last plane needed
-  auto X = [&](int p) -> float* { return xbase + (size_t)((p - p_first) % XR) * BOX; };
-  // coefficient field f (0: rhs z, 1: L0, 2: L1, 3: L2) of plane p
-  auto C = [&](int p, int f) -> float* { return cbase + ((size_t)((p - pc_first) % CR) * 4 + f) * BOX; };
-  auto bar = [&](int p) { return smem_addr(&bars[(p - p_first) % NB]); };
-  auto phase = [&](int p) { return (uint32_t)(((p - p_first) / NB) & 1); };
-  const CUtensorMap* cmaps[4] = {&m.z, &m.L0, &m.L1, &m.L2};
-  const int ncf = (D == 3) ? 4 : 3;  // 2-D has no L2
+  // ring slots: iterate planes from k0-2, coefficient planes from k0-1
+  auto X = [&](int p) -> float* { return xbase + (size_t)((p - k0 + 2) % XR) * BOX; };
+  auto CL2 = [&](int p) -> float* { return l2base + (size_t)((p - k0 + 1) % L2R) * CSLOT; };
+  auto CZ = [&](int p) -> float* { return zbase + (size_t)((p - k0 + 1) & (CR - 1)) * CSLOT; };
+  auto CL0 = [&](int p) -> float* { return l0base + (size_t)((p - k0 + 1) & (CR - 1)) * CSLOT; };
+  auto CL1 = [&](int p) -> float* { return l1base + (size_t)((p - k0 + 1) & (CR - 1)) * L1SLOT; };
+  // barrier 0: the prologue's planes; barriers 1, 2: bundle b (alternating)
+  auto bbar = [&](int b) { return smem_addr(&bars[1 + ((b - k0) & 1)]); };
+  auto bphase = [&](int b) { return (uint32_t)(((b - k0) >> 1) & 1); };
 
   if (tid == 0) {
-    for (int s = 0; s < NB; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    for (int s = 0; s < 3; ++s) mbar_init(smem_addr(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  int p_issued = p_first - 1;  // (thread 0) last plane staged
-  auto issue = [&](int p) {     // thread 0: stage plane p (iterate, and coefficients from pc_first on)
-    if (p > p_last) return;
-    p_issued = p;
-    const bool coef = p >= pc_first;
-    const uint32_t bytes = (uint32_t)(((a.has_x ? 1 : 0) + (coef ? ncf : 0)) * BOX * sizeof(float));
-    mbar_expect_tx(bar(p), bytes);
-    if (a.has_x) tma_load(smem_addr(X(p)), &m.x, i0 - 4, j0 - 2, p, bar(p), D);
-    if (coef)
-      for (int f = 0; f < ncf; ++f) tma_load(smem_addr(C(p, f)), cmaps[f], i0 - 4, j0 - 2, p, bar(p), D);
+
+  // thread 0 staging.  Coefficient boxes start one row above the tile (j0-1), the
+  // iterate's two rows above (j0-2); all start 4 columns left of the tile.
+  auto ld_x = [&](int p, uint32_t bar) { tma_load(smem_addr(X(p)), &m.x, i0 - 4, j0 - 2, p, bar, D); };
+  auto ld_c = [&](int p, uint32_t bar, bool l2) {
+    tma_load(smem_addr(CZ(p)), &m.z, i0 - 4, j0 - 1, p, bar, D);
+    tma_load(smem_addr(CL0(p)), &m.L0, i0 - 4, j0 - 1, p, bar, D);
+    tma_load(smem_addr(CL1(p)), &m.L1, i0 - 4, j0 - 1, p, bar, D);
+    if (l2) tma_load(smem_addr(CL2(p)), &m.L2, i0 - 4, j0 - 1, p, bar, D);
   };
-  // wait for plane p; iterate := (staged iterate or 0) + prolonged coarse correction.
-  // Returns false (block-uniform) if a copy did not arrive in time.
-  auto ready = [&](int p) -> bool {
-    const bool ok = mbar_wait(bar(p), phase(p));
-    if (__syncthreads_or(!ok)) return false;
-    if (!a.has_x || a.xc) {
-      float* Xp = X(p);
-      for (int e = tid; e < BOX; e += 256) {
-        const int row = e / BX, col = e - row * BX;
-        const int gi = i0 - 4 + col, gj = j0 - 2 + row;
-        float v = a.has_x ? Xp[e] : 0.f;
-        if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && p >= 0 && p < g.n[2])
-          v += __ldg(a.xc + (long long)(gi >> 1) +
-                     (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
-        Xp[e] = v;
-      }
-      __syncthreads();
+  constexpr uint32_t kXB = BOX * 4, kCB = BX * CROWS * 4, kL1B = BX * L1ROWS * 4;
+  int b_issued = k0 - 1;  // (thread 0) last bundle staged
+  // bundle b (waited at the start of iteration b): iterate and L2 of plane b+3,
+  // z, L0, L1 of plane b+2
+  auto issue_bundle = [&](int b) {
+    b_issued = b;
+    mbar_expect_tx(bbar(b), (a.has_x ? kXB : 0u) + 3 * kCB + kL1B);
+    if (a.has_x) ld_x(b + 3, bbar(b));
+    tma_load(smem_addr(CL2(b + 3)), &m.L2, i0 - 4, j0 - 1, b + 3, bbar(b), D);
+    ld_c(b + 2, bbar(b), false);
+  };
+  // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p
+  auto fix_x = [&](int p) {
+    float* Xp = X(p);
+    for (int e = tid; e < BOX; e += SW_NT) {
+      const int row = e / BX, col = e - row * BX;
+      const int gi = i0 - 4 + col, gj = j0 - 2 + row;
+      float v = a.has_x ? Xp[e] : 0.f;
+      if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && p >= 0 && p < g.n[2])
+        v += __ldg(a.xc + (long long)(gi >> 1) +
+                   (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
+      Xp[e] = v;
     }
-    return true;
   };
-  // operand planes of a relaxation at plane p, looked up once per phase
+  const bool fix = !a.has_x || a.xc;
+  // operand planes of a relaxation at plane p (coefficient pointers shifted one row
+  // so that one shared index e addresses the iterate box and the coefficient boxes)
   struct Planes {
     const float *xm, *xp, *z, *l0, *l1, *l2, *l2u;
     float* x0;
@@ -146,11 +159,11 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
     P.x0 = X(p);
     P.xm = (D == 3) ? X(p - 1) : P.x0;
     P.xp = (D == 3) ? X(p + 1) : P.x0;
-    P.z = C(p, 0);
-    P.l0 = C(p, 1);
-    P.l1 = C(p, 2);
-    P.l2 = (D == 3) ? C(p, 3) : P.l0;
-    P.l2u = (D == 3) ? C(p + 1, 3) : P.l0;
+    P.z = CZ(p) - BX;
+    P.l0 = CL0(p) - BX;
+    P.l1 = CL1(p) - BX;
+    P.l2 = (D == 3) ? CL2(p) - BX : P.l0;
+    P.l2u = (D == 3) ? CL2(p + 1) - BX : P.l0;
     return P;
   };
   // Gauss-Seidel value of the cell at shared index e (all operands staged;
@@ -171,89 +184,164 @@ __global__ void __launch_bounds__(256) k_sweep_tma(const __grid_constant__ Sweep
     }
     return (dg > 0.f) ? __fdividef(sum - P.z[e], dg) : 0.f;
   };
-  // red cells of plane p on the tile plus a 1-cell halo (rows -1..8, columns -1..64):
-  // ten 32-cell tasks (two adjacent rows x half the tile's columns) and the ten
-  // edge-column cells
+  // Red cells of plane p cover the tile plus a 1-cell halo (rows -1..8, columns
+  // -1..64): task t < 10 is 32 of them (two adjacent rows x half the tile's
+  // columns); the ten edge-column cells go to warp 8.  Black cells of plane k: task
+  // t < 8 (rows 0..7).  Index into the iterate box.
+  auto red_e = [&](int t, int p) {
+    const int jj = 2 * (t >> 1) + (lane >> 4) - 1;
+    const int ii = 32 * (t & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + p) & 1);
+    return (jj + 2) * BX + (ii + 4);
+  };
+  auto red_edge_e = [&](int p) {
+    const int jj = lane - 1;
+    const int ii = ((i0 + j0 + jj + p) & 1) ? -1 : 64;
+    return (jj + 2) * BX + (ii + 4);
+  };
+  auto black_e = [&](int t, int k) {
+    const int jj = 2 * (t >> 1) + (lane >> 4);
+    const int ii = 32 * (t & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + k + 1) & 1);
+    return (jj + 2) * BX + (ii + 4);
+  };
   auto red_plane = [&](int p) {
     const Planes P = planes(p);
-    for (int t = warp; t < 10; t += 8) {
-      const int jj = 2 * (t >> 1) + (lane >> 4) - 1;
-      const int ii = 32 * (t & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + p) & 1);
-      const int e = (jj + 2) * BX + (ii + 4);
-      P.x0[e] = relax(P, e);
-    }
-    if (warp == 2 && lane < 10) {
-      const int jj = lane - 1;
-      const int ii = ((i0 + j0 + jj + p) & 1) ? -1 : 64;
-      const int e = (jj + 2) * BX + (ii + 4);
-      P.x0[e] = relax(P, e);
+    const int e = red_e(warp, p);
+    P.x0[e] = relax(P, e);
+    if (warp == 8 && lane < 10) {
+      const int ee = red_edge_e(p);
+      P.x0[ee] = relax(P, ee);
     }
   };
-  // a copy timed out at plane p_fail: flag it, wait (bounded) for the planes still in
-  // flight so none lands after the block has left, then leave
-  auto bail = [&](int p_fail) {
+  // write the tile's plane k: thread (tx, ty) of the first 8 warps takes columns
+  // 2tx, 2tx+1 of row ty (n0 % 4 == 0, so both columns exist when the first does)
+  const int stx = tid & 31, sty = tid >> 5;
+  const int gi = i0 + 2 * stx, gj = j0 + sty;
+  const bool st_own = tid < 256 && gi < g.n[0] && gj < g.n[1];
+  auto gidx = [&](int k) -> long long {
+    return (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * (D == 3 ? k : 0));
+  };
+  float2 hph = make_float2(0.f, 0.f), hpl = make_float2(0.f, 0.f);  // ph, pl of the next plane to store
+  auto prefetch = [&](int k) {
+    if (a.ph && st_own && k < k1) {
+      const long long q = gidx(k);
+      hph = *reinterpret_cast<const float2*>(a.ph + q);
+      hpl = *reinterpret_cast<const float2*>(a.pl + q);
+    }
+  };
+  auto store = [&](int k) {
+    if (!st_own) return;
+    const float2 v = *reinterpret_cast<const float2*>(X(k) + (sty + 2) * BX + 2 * stx + 4);
+    const long long q = gidx(k);
+    if (a.ph) {
+      const float vv[2] = {v.x, v.y}, oh[2] = {hph.x, hph.y}, ol[2] = {hpl.x, hpl.y};
+      float nh[2], nl[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        float sh, sl;
+        two_sum(oh[t], vv[t], sh, sl);
+        sl += ol[t];
+        fast_two_sum(sh, sl, nh[t], nl[t]);
+      }
+      *reinterpret_cast<float2*>(a.ph + q) = make_float2(nh[0], nh[1]);
+      *reinterpret_cast<float2*>(a.pl + q) = make_float2(nl[0], nl[1]);
+    } else {
+      *reinterpret_cast<float2*>(a.x_out + q) = v;
+    }
+  };
+  // a copy timed out: flag it, wait (bounded) for the copies still in flight so none
+  // lands after the block has left, then leave
+  auto bail = [&](bool prologue_pending, int b_fail) {
     if (tid == 0) {
       atomicOr(&a.st->status, 4);
-      for (int p = p_fail; p <= p_issued; ++p) mbar_wait(bar(p), phase(p));
+      if (prologue_pending) mbar_wait(smem_addr(&bars[0]), 0);
+      for (int b = b_fail; b <= b_issued; ++b) mbar_wait(bbar(b), bphase(b));
     }
     __syncthreads();
   };
 
-  // ---- prologue: stage planes k0-2 .. k0+2, relax red cells of k0-1 and k0
-  if (tid == 0)
-    for (int p = p_first; p <= min(p_first + NB - 1, p_last); ++p) issue(p);
-  if (D == 3) {
-    for (int p = k0 - 2; p <= k0 + 1; ++p)
-      if (!ready(p)) return bail(p);
-    red_plane(k0 - 1);
-    red_plane(k0);
+  // ---- prologue: iterate planes k0-2..k0+2, coefficients k0-1..k0+1 (L2 to k0+2)
+  const int plo = (D == 3) ? k0 - 2 : 0, phi = (D == 3) ? k0 + 2 : 0;
+  if (tid == 0) {
+    const int ncp = (D == 3) ? 3 : 1, nl2 = (D == 3) ? 4 : 0;
+    mbar_expect_tx(smem_addr(&bars[0]), (a.has_x ? (uint32_t)(phi - plo + 1) * kXB : 0u) +
+                                            (uint32_t)ncp * (2 * kCB + kL1B) + (uint32_t)nl2 * kCB);
+    if (a.has_x)
+      for (int p = plo; p <= phi; ++p) ld_x(p, smem_addr(&bars[0]));
+    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 + 1 : 0); ++p) ld_c(p, smem_addr(&bars[0]), false);
+    if (D == 3)
+      for (int p = k0 - 1; p <= k0 + 2; ++p)
+        tma_load(smem_addr(CL2(p)), &m.L2, i0 - 4, j0 - 1, p, smem_addr(&bars[0]), D);
+    if (D == 3 && k0 <= k1 - 2) issue_bundle(k0);
+  }
+  {
+    const bool ok = mbar_wait(smem_addr(&bars[0]), 0);
+    if (__syncthreads_or(!ok)) return bail(true, k0);
+  }
+  if (fix) {
+    for (int p = plo; p <= phi; ++p) fix_x(p);
     __syncthreads();
   }
-  for (int k = k0; k < k1; ++k) {
-    const int pn = (D == 3) ? k + 2 : 0;
-    if (!ready(pn)) return bail(pn);
-    // every thread is past the last use of plane k-2's iterate and plane k-1's
-    // coefficients (both in the previous iteration or the prologue): stage plane k+3
-    if (D == 3 && tid == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(k + 3);
-    }
-    red_plane(D == 3 ? k + 1 : 0);
+  if (D == 2) {
+    red_plane(0);
     __syncthreads();
-    // black cells of plane k: eight 32-cell tasks (two adjacent rows x half the columns)
-    {
-      const Planes P = planes(k);
-      const int jj = 2 * (warp >> 1) + (lane >> 4);
-      const int ii = 32 * (warp & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + k + 1) & 1);
-      const int e = (jj + 2) * BX + (ii + 4);
+    if (warp < 8) {
+      const Planes P = planes(0);
+      const int e = black_e(warp, 0);
       P.x0[e] = relax(P, e);
     }
     __syncthreads();
-    // write the tile's plane k: thread (tx, ty) takes columns 2tx, 2tx+1 of row ty
-    const float2 v = *reinterpret_cast<const float2*>(X(k) + (ty + 2) * BX + 2 * tx + 4);
-    const int gi = i0 + 2 * tx, gj = j0 + ty;
-    if (gi < g.n[0] && gj < g.n[1]) {
-      const long long q = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * (D == 3 ? k : 0));
-      const bool two = gi + 1 < g.n[0];
-      if (a.ph) {
-        const float vv[2] = {v.x, v.y};
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          if (t == 1 && !two) continue;
-          float sh, sl, nh, nl;
-          two_sum(a.ph[q + t], vv[t], sh, sl);
-          sl += a.pl[q + t];
-          fast_two_sum(sh, sl, nh, nl);
-          a.ph[q + t] = nh;
-          a.pl[q + t] = nl;
-        }
-      } else if (two) {
-        reinterpret_cast<float2*>(a.x_out + q)[0] = v;
-      } else {
-        a.x_out[q] = v.x;
+    store(0);
+    return;
+  }
+  // red cells of planes k0-1, k0, k0+1 (independent of one another)
+  red_plane(k0 - 1);
+  red_plane(k0);
+  red_plane(k0 + 1);
+  prefetch(k0);
+
+  // ---- iteration k: red cells of plane k+2 and black cells of plane k (disjoint
+  // cells; neither reads a value the other writes), and the store of plane k-1
+  for (int k = k0; k < k1; ++k) {
+    if (k <= k1 - 2) {
+      const bool ok = mbar_wait(bbar(k), bphase(k));
+      if (__syncthreads_or(!ok)) return bail(false, k);
+      if (fix) {
+        fix_x(k + 3);
+        __syncthreads();
       }
+    } else {
+      __syncthreads();
+    }
+    // every thread is past iteration k-1, the last use of iterate plane k-2 and of
+    // coefficient plane k-1: stage bundle k+1 into their slots
+    if (tid == 0 && k + 1 <= k1 - 2) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue_bundle(k + 1);
+    }
+    if (k > k0) {
+      store(k - 1);
+      prefetch(k);
+    }
+    const bool do_red = k + 2 <= k1;
+    if (warp < 8) {
+      const Planes Pb = planes(k);
+      const int eb = black_e(warp, k);
+      if (do_red) {
+        const Planes Pr = planes(k + 2);
+        const int er = red_e(warp, k + 2);
+        const float vr = relax(Pr, er);
+        const float vb = relax(Pb, eb);
+        Pr.x0[er] = vr;
+        Pb.x0[eb] = vb;
+      } else {
+        Pb.x0[eb] = relax(Pb, eb);
+      }
+    } else if (do_red) {
+      red_plane(k + 2);
     }
   }
+  __syncthreads();
+  store(k1 - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -465,7 +553,8 @@ int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s) 
 }
 
 size_t sweep_tma_smem() {
-  return ((size_t)XR + 4 * (size_t)CR) * BOX * sizeof(float) + NB * sizeof(uint64_t) + 128;
+  return ((size_t)XR * BOX + (size_t)L2R * CSLOT + (size_t)CR * (2 * CSLOT + L1SLOT)) * sizeof(float) +
+         3 * sizeof(uint64_t) + 128;
 }
 
 int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s) {
@@ -477,10 +566,10 @@ int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStrea
     cudaFuncSetAttribute(k_sweep_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (D == 3) {
     dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-    k_sweep_tma<3><<<grd, 256, smem, s>>>(m, a);
+    k_sweep_tma<3><<<grd, SW_NT, smem, s>>>(m, a);
   } else {
     dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, 1);
-    k_sweep_tma<2><<<grd, 256, smem, s>>>(m, a);
+    k_sweep_tma<2><<<grd, SW_NT, smem, s>>>(m, a);
   }
   return 0;
 }
