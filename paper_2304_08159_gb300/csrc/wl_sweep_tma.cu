@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
     __syncthreads();
   }
   if (D == 2) {
+    prefetch(0);
     red_plane(0);
     __syncthreads();
     if (warp < 8) {
