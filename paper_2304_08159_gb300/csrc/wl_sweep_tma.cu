@@ -32,10 +32,13 @@ constexpr int BOX = BX * BY;          // floats per field per plane
 // upper face of row 8 is row 9); slots padded to 128-byte multiples
 constexpr int CROWS = SWEEP_CROWS, L1ROWS = SWEEP_CROWS + 1;
 constexpr int CSLOT = (BX * CROWS + 31) / 32 * 32, L1SLOT = (BX * L1ROWS + 31) / 32 * 32;
-constexpr int XR = 6;   // iterate slots (planes k-1 .. k+3, and k+4 in flight)
-constexpr int L2R = 5;  // L2 slots (planes k .. k+3, and k+4 in flight)
-constexpr int CR = 4;   // z, L0, L1 slots (planes k .. k+2, and k+3 in flight)
-constexpr int SW_NT = 320;  // sweep threads: 10 warps
+constexpr int LEAD = 3;         // bundles staged ahead of the iteration that waits for them
+constexpr int XR = LEAD + 5;    // iterate slots (planes k-1 .. k+3, and LEAD more in flight)
+constexpr int L2R = LEAD + 4;   // L2 slots (planes k .. k+3, and LEAD more in flight)
+constexpr int CR = LEAD + 3;    // z, L0, L1 slots (planes k .. k+2, and LEAD more in flight)
+constexpr int NBB = 4;          // bundle mbarriers (a power of two, > LEAD)
+constexpr int SW_NT = 320;      // sweep threads: 10 warps
+static_assert(NBB > LEAD && (NBB & (NBB - 1)) == 0, "bundle barriers");
 static_assert(BOX * 4 % 128 == 0, "iterate slots keep 128-byte alignment");
 constexpr unsigned kWaitLimit = 1u << 22;
 
@@ -83,7 +86,8 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
 }  // namespace
 
 template <int D>
-__global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
+__global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
+    k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
   extern __shared__ unsigned char smem_raw[];
   // 128-byte aligned slot rings (iterate, L2, z, L0, L1), then the mbarriers
   float* xbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -98,30 +102,35 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
   const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
   if (sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
-  // ring slots: iterate planes from k0-2, coefficient planes from k0-1
-  auto X = [&](int p) -> float* { return xbase + (size_t)((p - k0 + 2) % XR) * BOX; };
-  auto CL2 = [&](int p) -> float* { return l2base + (size_t)((p - k0 + 1) % L2R) * CSLOT; };
-  auto CZ = [&](int p) -> float* { return zbase + (size_t)((p - k0 + 1) & (CR - 1)) * CSLOT; };
-  auto CL0 = [&](int p) -> float* { return l0base + (size_t)((p - k0 + 1) & (CR - 1)) * CSLOT; };
-  auto CL1 = [&](int p) -> float* { return l1base + (size_t)((p - k0 + 1) & (CR - 1)) * L1SLOT; };
-  // barrier 0: the prologue's planes; barriers 1, 2: bundle b (alternating)
-  auto bbar = [&](int b) { return smem_addr(&bars[1 + ((b - k0) & 1)]); };
-  auto bphase = [&](int b) { return (uint32_t)(((b - k0) >> 1) & 1); };
+  // Ring slots: iterate plane p lives in slot (p - k0 + 2) mod XR, coefficient plane
+  // p in slot (p - k0 + 1) mod L2R (L2) or mod CR (z, L0, L1).
+  auto Xs = [&](int s) -> float* { return xbase + s * BOX; };
+  auto L2s = [&](int s) -> float* { return l2base + s * CSLOT; };
+  auto Zs = [&](int s) -> float* { return zbase + s * CSLOT; };
+  auto L0s = [&](int s) -> float* { return l0base + s * CSLOT; };
+  auto L1s = [&](int s) -> float* { return l1base + s * L1SLOT; };
+  auto xslot = [&](int p) { return (p - k0 + 2) % XR; };
+  auto l2slot = [&](int p) { return (p - k0 + 1) % L2R; };
+  auto cslot = [&](int p) { return (p - k0 + 1) % CR; };
+  // barrier 0: the prologue's planes; barriers 1..NBB: bundle b, round robin
+  auto bbar = [&](int b) { return smem_addr(&bars[1 + ((b - k0) & (NBB - 1))]); };
+  auto bphase = [&](int b) { return (uint32_t)(((b - k0) / NBB) & 1); };
 
   if (tid == 0) {
-    for (int s = 0; s < 3; ++s) mbar_init(smem_addr(&bars[s]), 1);
+    for (int s = 0; s <= NBB; ++s) mbar_init(smem_addr(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
   // thread 0 staging.  Coefficient boxes start one row above the tile (j0-1), the
   // iterate's two rows above (j0-2); all start 4 columns left of the tile.
-  auto ld_x = [&](int p, uint32_t bar) { tma_load(smem_addr(X(p)), &m.x, i0 - 4, j0 - 2, p, bar, D); };
-  auto ld_c = [&](int p, uint32_t bar, bool l2) {
-    tma_load(smem_addr(CZ(p)), &m.z, i0 - 4, j0 - 1, p, bar, D);
-    tma_load(smem_addr(CL0(p)), &m.L0, i0 - 4, j0 - 1, p, bar, D);
-    tma_load(smem_addr(CL1(p)), &m.L1, i0 - 4, j0 - 1, p, bar, D);
-    if (l2) tma_load(smem_addr(CL2(p)), &m.L2, i0 - 4, j0 - 1, p, bar, D);
+  auto ld_x = [&](int p, uint32_t bar) { tma_load(smem_addr(Xs(xslot(p))), &m.x, i0 - 4, j0 - 2, p, bar, D); };
+  auto ld_l2 = [&](int p, uint32_t bar) { tma_load(smem_addr(L2s(l2slot(p))), &m.L2, i0 - 4, j0 - 1, p, bar, D); };
+  auto ld_c = [&](int p, uint32_t bar) {
+    const int c = cslot(p);
+    tma_load(smem_addr(Zs(c)), &m.z, i0 - 4, j0 - 1, p, bar, D);
+    tma_load(smem_addr(L0s(c)), &m.L0, i0 - 4, j0 - 1, p, bar, D);
+    tma_load(smem_addr(L1s(c)), &m.L1, i0 - 4, j0 - 1, p, bar, D);
   };
   constexpr uint32_t kXB = BOX * 4, kCB = BX * CROWS * 4, kL1B = BX * L1ROWS * 4;
   int b_issued = k0 - 1;  // (thread 0) last bundle staged
@@ -131,12 +140,12 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
     b_issued = b;
     mbar_expect_tx(bbar(b), (a.has_x ? kXB : 0u) + 3 * kCB + kL1B);
     if (a.has_x) ld_x(b + 3, bbar(b));
-    tma_load(smem_addr(CL2(b + 3)), &m.L2, i0 - 4, j0 - 1, b + 3, bbar(b), D);
-    ld_c(b + 2, bbar(b), false);
+    ld_l2(b + 3, bbar(b));
+    ld_c(b + 2, bbar(b));
   };
   // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p
   auto fix_x = [&](int p) {
-    float* Xp = X(p);
+    float* Xp = Xs(xslot(p));
     for (int e = tid; e < BOX; e += SW_NT) {
       const int row = e / BX, col = e - row * BX;
       const int gi = i0 - 4 + col, gj = j0 - 2 + row;
@@ -148,33 +157,37 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
     }
   };
   const bool fix = !a.has_x || a.xc;
-  // operand planes of a relaxation at plane p (coefficient pointers shifted one row
-  // so that one shared index e addresses the iterate box and the coefficient boxes)
+  // Operand planes of a relaxation: iterate planes below / at / above, and the
+  // coefficient planes (pointers shifted one row so that one shared index e
+  // addresses the iterate box and the coefficient boxes).
   struct Planes {
     const float *xm, *xp, *z, *l0, *l1, *l2, *l2u;
     float* x0;
   };
-  auto planes = [&](int p) -> Planes {
+  // sxm: slot of the iterate plane below; sl: L2 slot of the plane; sc: z/L0/L1 slot
+  auto planes = [&](int sxm, int sl, int sc) -> Planes {
     Planes P;
-    P.x0 = X(p);
-    P.xm = (D == 3) ? X(p - 1) : P.x0;
-    P.xp = (D == 3) ? X(p + 1) : P.x0;
-    P.z = CZ(p) - BX;
-    P.l0 = CL0(p) - BX;
-    P.l1 = CL1(p) - BX;
-    P.l2 = (D == 3) ? CL2(p) - BX : P.l0;
-    P.l2u = (D == 3) ? CL2(p + 1) - BX : P.l0;
+    P.xm = Xs(sxm);
+    P.x0 = Xs(sxm + 1 < XR ? sxm + 1 : sxm + 1 - XR);
+    P.xp = Xs(sxm + 2 < XR ? sxm + 2 : sxm + 2 - XR);
+    P.z = Zs(sc) - BX;
+    P.l0 = L0s(sc) - BX;
+    P.l1 = L1s(sc) - BX;
+    P.l2 = L2s(sl) - BX;
+    P.l2u = L2s(sl + 1 < L2R ? sl + 1 : 0) - BX;
     return P;
   };
+  auto planes_of = [&](int p) { return planes(D == 3 ? xslot(p - 1) : xslot(p), l2slot(p), cslot(p)); };
   // Gauss-Seidel value of the cell at shared index e (all operands staged;
   // out-of-range faces carry 0, so cells outside the grid come out as 0).
   // Same operation order as k_sweep (upper then lower face; x, y, z), same bits.
   auto relax = [&](const Planes& P, int e) -> float {
-    float sum = fmaf(P.l0[e + 1], P.x0[e + 1], 0.f);
-    sum = fmaf(P.l0[e], P.x0[e - 1], sum);
+    const float* x0 = P.x0;
+    float sum = fmaf(P.l0[e + 1], x0[e + 1], 0.f);
+    sum = fmaf(P.l0[e], x0[e - 1], sum);
     float dg = P.l0[e + 1] + P.l0[e];
-    sum = fmaf(P.l1[e + BX], P.x0[e + BX], sum);
-    sum = fmaf(P.l1[e], P.x0[e - BX], sum);
+    sum = fmaf(P.l1[e + BX], x0[e + BX], sum);
+    sum = fmaf(P.l1[e], x0[e - BX], sum);
     dg += P.l1[e + BX] + P.l1[e];
     if (D == 3) {
       const float lu = P.l2u[e], ll = P.l2[e];
@@ -185,31 +198,27 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
     return (dg > 0.f) ? __fdividef(sum - P.z[e], dg) : 0.f;
   };
   // Red cells of plane p cover the tile plus a 1-cell halo (rows -1..8, columns
-  // -1..64): task t < 10 is 32 of them (two adjacent rows x half the tile's
-  // columns); the ten edge-column cells go to warp 8.  Black cells of plane k: task
-  // t < 8 (rows 0..7).  Index into the iterate box.
-  auto red_e = [&](int t, int p) {
-    const int jj = 2 * (t >> 1) + (lane >> 4) - 1;
-    const int ii = 32 * (t & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + p) & 1);
-    return (jj + 2) * BX + (ii + 4);
-  };
-  auto red_edge_e = [&](int p) {
-    const int jj = lane - 1;
-    const int ii = ((i0 + j0 + jj + p) & 1) ? -1 : 64;
-    return (jj + 2) * BX + (ii + 4);
-  };
-  auto black_e = [&](int t, int k) {
-    const int jj = 2 * (t >> 1) + (lane >> 4);
-    const int ii = 32 * (t & 1) + 2 * (lane & 15) + ((i0 + j0 + jj + k + 1) & 1);
-    return (jj + 2) * BX + (ii + 4);
-  };
-  auto red_plane = [&](int p) {
-    const Planes P = planes(p);
-    const int e = red_e(warp, p);
+  // -1..64): warp t < 10 takes 32 of them (two adjacent rows x half the tile's
+  // columns); the ten edge-column cells go to lanes 0..9 of warp 8.  Black cells of
+  // plane k: warp t < 8 (rows 0..7).  Indices into the iterate box, for even and
+  // odd planes.
+  int er0, er1, eb0, eb1, ee0, ee1;
+  {
+    const int jr = 2 * (warp >> 1) + (lane >> 4) - 1, jb = jr + 1, je = lane - 1;
+    const int ib = 32 * (warp & 1) + 2 * (lane & 15);
+    er0 = (jr + 2) * BX + ib + ((i0 + j0 + jr) & 1) + 4;
+    er1 = (jr + 2) * BX + ib + ((i0 + j0 + jr + 1) & 1) + 4;
+    eb0 = (jb + 2) * BX + ib + ((i0 + j0 + jb + 1) & 1) + 4;
+    eb1 = (jb + 2) * BX + ib + ((i0 + j0 + jb) & 1) + 4;
+    ee0 = (je + 2) * BX + (((i0 + j0 + je) & 1) ? -1 : 64) + 4;
+    ee1 = (je + 2) * BX + (((i0 + j0 + je + 1) & 1) ? -1 : 64) + 4;
+  }
+  auto red_plane = [&](const Planes& P, int par) {
+    const int e = par ? er1 : er0;
     P.x0[e] = relax(P, e);
     if (warp == 8 && lane < 10) {
-      const int ee = red_edge_e(p);
-      P.x0[ee] = relax(P, ee);
+      const int f = par ? ee1 : ee0;
+      P.x0[f] = relax(P, f);
     }
   };
   // write the tile's plane k: thread (tx, ty) of the first 8 warps takes columns
@@ -217,21 +226,20 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
   const int stx = tid & 31, sty = tid >> 5;
   const int gi = i0 + 2 * stx, gj = j0 + sty;
   const bool st_own = tid < 256 && gi < g.n[0] && gj < g.n[1];
-  auto gidx = [&](int k) -> long long {
-    return (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * (D == 3 ? k : 0));
-  };
+  const long long q0 = (long long)gi + (long long)g.n[0] * gj, qk = (long long)g.n[0] * g.n[1];
+  const int est = (sty + 2) * BX + 2 * stx + 4;
   float2 hph = make_float2(0.f, 0.f), hpl = make_float2(0.f, 0.f);  // ph, pl of the next plane to store
   auto prefetch = [&](int k) {
     if (a.ph && st_own && k < k1) {
-      const long long q = gidx(k);
+      const long long q = q0 + (D == 3 ? qk * k : 0);
       hph = *reinterpret_cast<const float2*>(a.ph + q);
       hpl = *reinterpret_cast<const float2*>(a.pl + q);
     }
   };
-  auto store = [&](int k) {
+  auto store = [&](const float* Xk, int k) {
     if (!st_own) return;
-    const float2 v = *reinterpret_cast<const float2*>(X(k) + (sty + 2) * BX + 2 * stx + 4);
-    const long long q = gidx(k);
+    const float2 v = *reinterpret_cast<const float2*>(Xk + est);
+    const long long q = q0 + (D == 3 ? qk * k : 0);
     if (a.ph) {
       const float vv[2] = {v.x, v.y}, oh[2] = {hph.x, hph.y}, ol[2] = {hpl.x, hpl.y};
       float nh[2], nl[2];
@@ -259,19 +267,21 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
     __syncthreads();
   };
 
-  // ---- prologue: iterate planes k0-2..k0+2, coefficients k0-1..k0+1 (L2 to k0+2)
+  // ---- prologue: iterate planes k0-2..k0+2, coefficients k0-1..k0+1 (L2 to k0+2),
+  // and the first LEAD bundles
   const int plo = (D == 3) ? k0 - 2 : 0, phi = (D == 3) ? k0 + 2 : 0;
   if (tid == 0) {
     const int ncp = (D == 3) ? 3 : 1, nl2 = (D == 3) ? 4 : 0;
-    mbar_expect_tx(smem_addr(&bars[0]), (a.has_x ? (uint32_t)(phi - plo + 1) * kXB : 0u) +
-                                            (uint32_t)ncp * (2 * kCB + kL1B) + (uint32_t)nl2 * kCB);
+    const uint32_t b0 = smem_addr(&bars[0]);
+    mbar_expect_tx(b0, (a.has_x ? (uint32_t)(phi - plo + 1) * kXB : 0u) + (uint32_t)ncp * (2 * kCB + kL1B) +
+                           (uint32_t)nl2 * kCB);
     if (a.has_x)
-      for (int p = plo; p <= phi; ++p) ld_x(p, smem_addr(&bars[0]));
-    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 + 1 : 0); ++p) ld_c(p, smem_addr(&bars[0]), false);
+      for (int p = plo; p <= phi; ++p) ld_x(p, b0);
+    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 + 1 : 0); ++p) ld_c(p, b0);
     if (D == 3)
-      for (int p = k0 - 1; p <= k0 + 2; ++p)
-        tma_load(smem_addr(CL2(p)), &m.L2, i0 - 4, j0 - 1, p, smem_addr(&bars[0]), D);
-    if (D == 3 && k0 <= k1 - 2) issue_bundle(k0);
+      for (int p = k0 - 1; p <= k0 + 2; ++p) ld_l2(p, b0);
+    if (D == 3)
+      for (int b = k0; b < k0 + LEAD && b <= k1 - 2; ++b) issue_bundle(b);
   }
   {
     const bool ok = mbar_wait(smem_addr(&bars[0]), 0);
@@ -281,27 +291,23 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
     for (int p = plo; p <= phi; ++p) fix_x(p);
     __syncthreads();
   }
-  if (D == 2) {
+  if constexpr (D == 2) {
     prefetch(0);
-    red_plane(0);
+    const Planes P = planes_of(0);
+    red_plane(P, 0);
     __syncthreads();
-    if (warp < 8) {
-      const Planes P = planes(0);
-      const int e = black_e(warp, 0);
-      P.x0[e] = relax(P, e);
-    }
+    if (warp < 8) P.x0[eb0] = relax(P, eb0);
     __syncthreads();
-    store(0);
+    store(P.x0, 0);
     return;
-  }
+  } else {
   // red cells of planes k0-1, k0, k0+1 (independent of one another)
-  red_plane(k0 - 1);
-  red_plane(k0);
-  red_plane(k0 + 1);
+  for (int p = k0 - 1; p <= k0 + 1; ++p) red_plane(planes_of(p), p & 1);
   prefetch(k0);
 
   // ---- iteration k: red cells of plane k+2 and black cells of plane k (disjoint
   // cells; neither reads a value the other writes), and the store of plane k-1
+  int sx = xslot(k0 - 1), sl = l2slot(k0), sc = cslot(k0);  // rolling slots of planes k-1 / k / k
   for (int k = k0; k < k1; ++k) {
     if (k <= k1 - 2) {
       const bool ok = mbar_wait(bbar(k), bphase(k));
@@ -314,35 +320,41 @@ __global__ void __launch_bounds__(SW_NT) k_sweep_tma(const __grid_constant__ Swe
       __syncthreads();
     }
     // every thread is past iteration k-1, the last use of iterate plane k-2 and of
-    // coefficient plane k-1: stage bundle k+1 into their slots
-    if (tid == 0 && k + 1 <= k1 - 2) {
+    // coefficient plane k-1, the slots bundle k+LEAD fills
+    if (tid == 0 && k + LEAD <= k1 - 2) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_bundle(k + 1);
+      issue_bundle(k + LEAD);
     }
     if (k > k0) {
-      store(k - 1);
+      store(Xs(sx), k - 1);
       prefetch(k);
     }
+    const int par = k & 1, erk = par ? er1 : er0, ebk = par ? eb1 : eb0;
     const bool do_red = k + 2 <= k1;
+    const int sx2 = sx + 2 < XR ? sx + 2 : sx + 2 - XR;
+    const int sl2 = sl + 2 < L2R ? sl + 2 : sl + 2 - L2R;
+    const int sc2 = sc + 2 < CR ? sc + 2 : sc + 2 - CR;
     if (warp < 8) {
-      const Planes Pb = planes(k);
-      const int eb = black_e(warp, k);
+      const Planes Pb = planes(sx, sl, sc);
       if (do_red) {
-        const Planes Pr = planes(k + 2);
-        const int er = red_e(warp, k + 2);
-        const float vr = relax(Pr, er);
-        const float vb = relax(Pb, eb);
-        Pr.x0[er] = vr;
-        Pb.x0[eb] = vb;
+        const Planes Pr = planes(sx2, sl2, sc2);
+        const float vr = relax(Pr, erk);
+        const float vb = relax(Pb, ebk);
+        Pr.x0[erk] = vr;
+        Pb.x0[ebk] = vb;
       } else {
-        Pb.x0[eb] = relax(Pb, eb);
+        Pb.x0[ebk] = relax(Pb, ebk);
       }
     } else if (do_red) {
-      red_plane(k + 2);
+      red_plane(planes(sx2, sl2, sc2), par);
     }
+    sx = sx + 1 < XR ? sx + 1 : 0;
+    sl = sl + 1 < L2R ? sl + 1 : 0;
+    sc = sc + 1 < CR ? sc + 1 : 0;
   }
   __syncthreads();
-  store(k1 - 1);
+  store(Xs(sx), k1 - 1);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -555,7 +567,7 @@ int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s) 
 
 size_t sweep_tma_smem() {
   return ((size_t)XR * BOX + (size_t)L2R * CSLOT + (size_t)CR * (2 * CSLOT + L1SLOT)) * sizeof(float) +
-         3 * sizeof(uint64_t) + 128;
+         (1 + NBB) * sizeof(uint64_t) + 128;
 }
 
 int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s) {
