@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
     P.l2u = L2s(sl + 1 < L2R ? sl + 1 : 0) - BX;
     return P;
   };
-  auto planes_of = [&](int p) { return planes(D == 3 ? xslot(p - 1) : xslot(p), l2slot(p), cslot(p)); };
+  auto planes_of = [&](int p) { return planes(xslot(p - 1), l2slot(p), cslot(p)); };
   // Gauss-Seidel value of the cell at shared index e (all operands staged;
   // out-of-range faces carry 0, so cells outside the grid come out as 0).
   // Same operation order as k_sweep (upper then lower face; x, y, z), same bits.
