@@ -32,15 +32,17 @@ constexpr int BOX = BX * BY;          // floats per field per plane
 // upper face of row 8 is row 9); slots padded to 128-byte multiples
 constexpr int CROWS = SWEEP_CROWS, L1ROWS = SWEEP_CROWS + 1;
 constexpr int CSLOT = (BX * CROWS + 31) / 32 * 32, L1SLOT = (BX * L1ROWS + 31) / 32 * 32;
-constexpr int LEAD = 3;         // bundles staged ahead of the iteration that waits for them
+constexpr int LEAD = 1;         // bundles staged ahead of the iteration that waits for them
 constexpr int XR = LEAD + 5;    // iterate slots (planes k-1 .. k+3, and LEAD more in flight)
 constexpr int L2R = LEAD + 4;   // L2 slots (planes k .. k+3, and LEAD more in flight)
 constexpr int CR = LEAD + 3;    // z, L0, L1 slots (planes k .. k+2, and LEAD more in flight)
-constexpr int NBB = 4;          // bundle mbarriers (a power of two, > LEAD)
-constexpr int SW_NT = 320;      // sweep threads: 10 warps
+constexpr int NBB = 2;          // bundle mbarriers (a power of two, > LEAD)
+constexpr int SW_NT = 160;      // sweep threads: 5 warps
 static_assert(NBB > LEAD && (NBB & (NBB - 1)) == 0, "bundle barriers");
 static_assert(BOX * 4 % 128 == 0, "iterate slots keep 128-byte alignment");
-constexpr unsigned kWaitLimit = 1u << 22;
+constexpr unsigned kWaitLimit = 1u << 21;      // wait attempts
+constexpr unsigned kSuspendNs = 10000;         // longest sleep of one attempt
+constexpr uint64_t kWaitNs = 2000000000ull;    // longest wait (2 s)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -50,21 +52,33 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// One wait attempt: the thread may sleep until the phase completes, for at most
+// kSuspendNs, so waiting warps leave the issue slots to the warps with work.
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "n"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
-// bounded wait: false if the phase did not complete within the limit
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// bounded wait: false if the phase did not complete within kWaitNs of wall time
+// (or kWaitLimit attempts)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (unsigned it = 0; it < kWaitLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
   return false;
 }
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar,
@@ -83,19 +97,32 @@ __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// shared loads / stores at a 32-bit shared-window byte address (+ immediate offset)
+__device__ __forceinline__ float lds(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ float lds(uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+  return v;
+}
+__device__ __forceinline__ void sts(uint32_t a, float v) { asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v)); }
+
 }  // namespace
 
 template <int D>
 __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
     k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
-  extern __shared__ unsigned char smem_raw[];
-  // 128-byte aligned slot rings (iterate, L2, z, L0, L1), then the mbarriers
-  float* xbase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float* l2base = xbase + (size_t)XR * BOX;
-  float* zbase = l2base + (size_t)L2R * CSLOT;
-  float* l0base = zbase + (size_t)CR * CSLOT;
-  float* l1base = l0base + (size_t)CR * CSLOT;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(l1base + (size_t)CR * L1SLOT);
+  extern __shared__ float smf[];
+  // 128-byte aligned slot rings (iterate, L2, z, L0, L1), then the mbarriers, all
+  // addressed by 32-bit float offsets into smf
+  const int ox = (int)(((128u - (smem_addr(smf) & 127u)) & 127u) >> 2);
+  constexpr int O_L2 = XR * BOX, O_Z = O_L2 + L2R * CSLOT, O_L0 = O_Z + CR * CSLOT, O_L1 = O_L0 + CR * CSLOT,
+                O_BAR = O_L1 + CR * L1SLOT;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smf + ox + O_BAR);
   const Grid& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -104,11 +131,12 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   if (sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
   // Ring slots: iterate plane p lives in slot (p - k0 + 2) mod XR, coefficient plane
   // p in slot (p - k0 + 1) mod L2R (L2) or mod CR (z, L0, L1).
-  auto Xs = [&](int s) -> float* { return xbase + s * BOX; };
-  auto L2s = [&](int s) -> float* { return l2base + s * CSLOT; };
-  auto Zs = [&](int s) -> float* { return zbase + s * CSLOT; };
-  auto L0s = [&](int s) -> float* { return l0base + s * CSLOT; };
-  auto L1s = [&](int s) -> float* { return l1base + s * L1SLOT; };
+  auto Xs = [&](int s) { return ox + s * BOX; };
+  auto L2s = [&](int s) { return ox + O_L2 + s * CSLOT; };
+  auto Zs = [&](int s) { return ox + O_Z + s * CSLOT; };
+  auto L0s = [&](int s) { return ox + O_L0 + s * CSLOT; };
+  auto L1s = [&](int s) { return ox + O_L1 + s * L1SLOT; };
+  auto sa = [&](int o) { return smem_addr(smf + o); };
   auto xslot = [&](int p) { return (p - k0 + 2) % XR; };
   auto l2slot = [&](int p) { return (p - k0 + 1) % L2R; };
   auto cslot = [&](int p) { return (p - k0 + 1) % CR; };
@@ -124,13 +152,13 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
 
   // thread 0 staging.  Coefficient boxes start one row above the tile (j0-1), the
   // iterate's two rows above (j0-2); all start 4 columns left of the tile.
-  auto ld_x = [&](int p, uint32_t bar) { tma_load(smem_addr(Xs(xslot(p))), &m.x, i0 - 4, j0 - 2, p, bar, D); };
-  auto ld_l2 = [&](int p, uint32_t bar) { tma_load(smem_addr(L2s(l2slot(p))), &m.L2, i0 - 4, j0 - 1, p, bar, D); };
+  auto ld_x = [&](int p, uint32_t bar) { tma_load(sa(Xs(xslot(p))), &m.x, i0 - 4, j0 - 2, p, bar, D); };
+  auto ld_l2 = [&](int p, uint32_t bar) { tma_load(sa(L2s(l2slot(p))), &m.L2, i0 - 4, j0 - 1, p, bar, D); };
   auto ld_c = [&](int p, uint32_t bar) {
     const int c = cslot(p);
-    tma_load(smem_addr(Zs(c)), &m.z, i0 - 4, j0 - 1, p, bar, D);
-    tma_load(smem_addr(L0s(c)), &m.L0, i0 - 4, j0 - 1, p, bar, D);
-    tma_load(smem_addr(L1s(c)), &m.L1, i0 - 4, j0 - 1, p, bar, D);
+    tma_load(sa(Zs(c)), &m.z, i0 - 4, j0 - 1, p, bar, D);
+    tma_load(sa(L0s(c)), &m.L0, i0 - 4, j0 - 1, p, bar, D);
+    tma_load(sa(L1s(c)), &m.L1, i0 - 4, j0 - 1, p, bar, D);
   };
   constexpr uint32_t kXB = BOX * 4, kCB = BX * CROWS * 4, kL1B = BX * L1ROWS * 4;
   int b_issued = k0 - 1;  // (thread 0) last bundle staged
@@ -145,115 +173,156 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   };
   // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p
   auto fix_x = [&](int p) {
-    float* Xp = Xs(xslot(p));
+    const int Xp = Xs(xslot(p));
     for (int e = tid; e < BOX; e += SW_NT) {
       const int row = e / BX, col = e - row * BX;
       const int gi = i0 - 4 + col, gj = j0 - 2 + row;
-      float v = a.has_x ? Xp[e] : 0.f;
+      float v = a.has_x ? smf[Xp + e] : 0.f;
       if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && p >= 0 && p < g.n[2])
         v += __ldg(a.xc + (long long)(gi >> 1) +
                    (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
-      Xp[e] = v;
+      smf[Xp + e] = v;
     }
   };
   const bool fix = !a.has_x || a.xc;
-  // Operand planes of a relaxation: iterate planes below / at / above, and the
-  // coefficient planes (pointers shifted one row so that one shared index e
-  // addresses the iterate box and the coefficient boxes).
+  // Operand planes of a relaxation (shared byte addresses): iterate planes below /
+  // at / above, and the coefficient planes (shifted one row so that one shared
+  // offset e addresses the iterate box and the coefficient boxes).
   struct Planes {
-    const float *xm, *xp, *z, *l0, *l1, *l2, *l2u;
-    float* x0;
+    uint32_t xm, x0, xp, z, l0, l1, l2, l2u;
   };
+  const uint32_t sb = smem_addr(smf);
   // sxm: slot of the iterate plane below; sl: L2 slot of the plane; sc: z/L0/L1 slot
   auto planes = [&](int sxm, int sl, int sc) -> Planes {
     Planes P;
-    P.xm = Xs(sxm);
-    P.x0 = Xs(sxm + 1 < XR ? sxm + 1 : sxm + 1 - XR);
-    P.xp = Xs(sxm + 2 < XR ? sxm + 2 : sxm + 2 - XR);
-    P.z = Zs(sc) - BX;
-    P.l0 = L0s(sc) - BX;
-    P.l1 = L1s(sc) - BX;
-    P.l2 = L2s(sl) - BX;
-    P.l2u = L2s(sl + 1 < L2R ? sl + 1 : 0) - BX;
+    P.xm = sb + 4u * Xs(sxm);
+    P.x0 = sb + 4u * Xs(sxm + 1 < XR ? sxm + 1 : sxm + 1 - XR);
+    P.xp = sb + 4u * Xs(sxm + 2 < XR ? sxm + 2 : sxm + 2 - XR);
+    P.z = sb + 4u * (Zs(sc) - BX);
+    P.l0 = sb + 4u * (L0s(sc) - BX);
+    P.l1 = sb + 4u * (L1s(sc) - BX);
+    P.l2 = sb + 4u * (L2s(sl) - BX);
+    P.l2u = sb + 4u * (L2s(sl + 1 < L2R ? sl + 1 : 0) - BX);
     return P;
   };
   auto planes_of = [&](int p) { return planes(xslot(p - 1), l2slot(p), cslot(p)); };
-  // Gauss-Seidel value of the cell at shared index e (all operands staged;
+  // Gauss-Seidel value of the cell at shared byte offset e (all operands staged;
   // out-of-range faces carry 0, so cells outside the grid come out as 0).
   // Same operation order as k_sweep (upper then lower face; x, y, z), same bits.
-  auto relax = [&](const Planes& P, int e) -> float {
-    const float* x0 = P.x0;
-    float sum = fmaf(P.l0[e + 1], x0[e + 1], 0.f);
-    sum = fmaf(P.l0[e], x0[e - 1], sum);
-    float dg = P.l0[e + 1] + P.l0[e];
-    sum = fmaf(P.l1[e + BX], x0[e + BX], sum);
-    sum = fmaf(P.l1[e], x0[e - BX], sum);
-    dg += P.l1[e + BX] + P.l1[e];
+  auto relax = [&](const Planes& P, uint32_t e) -> float {
+    const uint32_t x0 = P.x0 + e, l0 = P.l0 + e, l1 = P.l1 + e;
+    const float l0u = lds<4>(l0), l0d = lds(l0), l1u = lds<4 * BX>(l1), l1d = lds(l1);
+    float sum = fmaf(l0u, lds<4>(x0), 0.f);
+    sum = fmaf(l0d, lds<-4>(x0), sum);
+    float dg = l0u + l0d;
+    sum = fmaf(l1u, lds<4 * BX>(x0), sum);
+    sum = fmaf(l1d, lds<-4 * BX>(x0), sum);
+    dg += l1u + l1d;
     if (D == 3) {
-      const float lu = P.l2u[e], ll = P.l2[e];
-      sum = fmaf(lu, P.xp[e], sum);
-      sum = fmaf(ll, P.xm[e], sum);
+      const float lu = lds(P.l2u + e), ll = lds(P.l2 + e);
+      sum = fmaf(lu, lds(P.xp + e), sum);
+      sum = fmaf(ll, lds(P.xm + e), sum);
       dg += lu + ll;
     }
-    return (dg > 0.f) ? __fdividef(sum - P.z[e], dg) : 0.f;
+    return (dg > 0.f) ? __fdividef(sum - lds(P.z + e), dg) : 0.f;
   };
   // Red cells of plane p cover the tile plus a 1-cell halo (rows -1..8, columns
-  // -1..64): warp t < 10 takes 32 of them (two adjacent rows x half the tile's
-  // columns); the ten edge-column cells go to lanes 0..9 of warp 8.  Black cells of
-  // plane k: warp t < 8 (rows 0..7).  Indices into the iterate box, for even and
-  // odd planes.
-  int er0, er1, eb0, eb1, ee0, ee1;
+  // -1..64): ten tasks of 32 (two adjacent rows x half the tile's columns), tasks w
+  // and w+5 for warp w, and ten edge-column cells, rows -1..3 on lanes 0..4 of warp
+  // 3 and rows 4..8 on lanes 0..4 of warp 4.  Black cells of plane k (rows 0..7):
+  // eight tasks, w and (w < 3) w+5.  Shared byte offsets into the iterate box, for
+  // even and odd planes.
+  uint32_t er[2][2], eb[2][2], ee[2];
   {
-    const int jr = 2 * (warp >> 1) + (lane >> 4) - 1, jb = jr + 1, je = lane - 1;
-    const int ib = 32 * (warp & 1) + 2 * (lane & 15);
-    er0 = (jr + 2) * BX + ib + ((i0 + j0 + jr) & 1) + 4;
-    er1 = (jr + 2) * BX + ib + ((i0 + j0 + jr + 1) & 1) + 4;
-    eb0 = (jb + 2) * BX + ib + ((i0 + j0 + jb + 1) & 1) + 4;
-    eb1 = (jb + 2) * BX + ib + ((i0 + j0 + jb) & 1) + 4;
-    ee0 = (je + 2) * BX + (((i0 + j0 + je) & 1) ? -1 : 64) + 4;
-    ee1 = (je + 2) * BX + (((i0 + j0 + je + 1) & 1) ? -1 : 64) + 4;
-  }
-  auto red_plane = [&](const Planes& P, int par) {
-    const int e = par ? er1 : er0;
-    P.x0[e] = relax(P, e);
-    if (warp == 8 && lane < 10) {
-      const int f = par ? ee1 : ee0;
-      P.x0[f] = relax(P, f);
-    }
-  };
-  // write the tile's plane k: thread (tx, ty) of the first 8 warps takes columns
-  // 2tx, 2tx+1 of row ty (n0 % 4 == 0, so both columns exist when the first does)
-  const int stx = tid & 31, sty = tid >> 5;
-  const int gi = i0 + 2 * stx, gj = j0 + sty;
-  const bool st_own = tid < 256 && gi < g.n[0] && gj < g.n[1];
-  const long long q0 = (long long)gi + (long long)g.n[0] * gj, qk = (long long)g.n[0] * g.n[1];
-  const int est = (sty + 2) * BX + 2 * stx + 4;
-  float2 hph = make_float2(0.f, 0.f), hpl = make_float2(0.f, 0.f);  // ph, pl of the next plane to store
-  auto prefetch = [&](int k) {
-    if (a.ph && st_own && k < k1) {
-      const long long q = q0 + (D == 3 ? qk * k : 0);
-      hph = *reinterpret_cast<const float2*>(a.ph + q);
-      hpl = *reinterpret_cast<const float2*>(a.pl + q);
-    }
-  };
-  auto store = [&](const float* Xk, int k) {
-    if (!st_own) return;
-    const float2 v = *reinterpret_cast<const float2*>(Xk + est);
-    const long long q = q0 + (D == 3 ? qk * k : 0);
-    if (a.ph) {
-      const float vv[2] = {v.x, v.y}, oh[2] = {hph.x, hph.y}, ol[2] = {hpl.x, hpl.y};
-      float nh[2], nl[2];
+    const int ib0 = 2 * (lane & 15);
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        float sh, sl;
-        two_sum(oh[t], vv[t], sh, sl);
-        sl += ol[t];
-        fast_two_sum(sh, sl, nh[t], nl[t]);
+    for (int h = 0; h < 2; ++h) {
+      const int t = warp + 5 * h;
+      const int jr = 2 * (t >> 1) + (lane >> 4) - 1, jb = jr + 1;
+      const int ib = 32 * (t & 1) + ib0;
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        er[h][par] = 4u * ((jr + 2) * BX + ib + ((i0 + j0 + jr + par) & 1) + 4);
+        eb[h][par] = 4u * ((jb + 2) * BX + ib + ((i0 + j0 + jb + par + 1) & 1) + 4);
       }
-      *reinterpret_cast<float2*>(a.ph + q) = make_float2(nh[0], nh[1]);
-      *reinterpret_cast<float2*>(a.pl + q) = make_float2(nl[0], nl[1]);
+    }
+    const int je = (warp == 3) ? lane - 1 : lane + 4;
+#pragma unroll
+    for (int par = 0; par < 2; ++par) ee[par] = 4u * ((je + 2) * BX + (((i0 + j0 + je + par) & 1) ? -1 : 64) + 4);
+  }
+  const bool has_edge = warp >= 3 && lane < 5, two_black = warp < 3;
+  // red cells of the plane whose operands are P (parity par)
+  auto red_plane = [&](const Planes& P, int par) {
+    const uint32_t e0 = par ? er[0][1] : er[0][0], e1 = par ? er[1][1] : er[1][0];
+    const float v0 = relax(P, e0), v1 = relax(P, e1);
+    sts(P.x0 + e0, v0);
+    sts(P.x0 + e1, v1);
+    if (has_edge) {
+      const uint32_t f = par ? ee[1] : ee[0];
+      sts(P.x0 + f, relax(P, f));
+    }
+  };
+  // black cells of the plane whose operands are P (parity par)
+  auto black_plane = [&](const Planes& P, int par) {
+    const uint32_t e0 = par ? eb[0][1] : eb[0][0];
+    if (two_black) {
+      const uint32_t e1 = par ? eb[1][1] : eb[1][0];
+      const float v0 = relax(P, e0), v1 = relax(P, e1);
+      sts(P.x0 + e0, v0);
+      sts(P.x0 + e1, v1);
     } else {
-      *reinterpret_cast<float2*>(a.x_out + q) = v;
+      sts(P.x0 + e0, relax(P, e0));
+    }
+  };
+  // Write the tile's plane k: 256 column pairs, pair t and t + 160 for thread t;
+  // pair (tx, ty) is columns 2tx, 2tx+1 of row ty (n0 % 4 == 0, so both columns
+  // exist when the first does).
+  bool st_own[2];
+  long long q0[2];
+  int est[2];
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int pos = tid + SW_NT * r, stx = pos & 31, sty = pos >> 5;
+    const int gi = i0 + 2 * stx, gj = j0 + sty;
+    st_own[r] = pos < 256 && gi < g.n[0] && gj < g.n[1];
+    q0[r] = (long long)gi + (long long)g.n[0] * gj;
+    est[r] = (sty + 2) * BX + 2 * stx + 4;
+  }
+  const long long qk = (long long)g.n[0] * g.n[1];
+  float2 hph[2], hpl[2];  // ph, pl of the next plane to store
+#pragma unroll
+  for (int r = 0; r < 2; ++r) hph[r] = hpl[r] = make_float2(0.f, 0.f);
+  auto prefetch = [&](int k) {
+    if (!a.ph || k >= k1) return;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      if (st_own[r]) {
+        const long long q = q0[r] + (D == 3 ? qk * k : 0);
+        hph[r] = *reinterpret_cast<const float2*>(a.ph + q);
+        hpl[r] = *reinterpret_cast<const float2*>(a.pl + q);
+      }
+  };
+  auto store = [&](int Xk, int k) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (!st_own[r]) continue;
+      const float2 v = *reinterpret_cast<const float2*>(smf + Xk + est[r]);
+      const long long q = q0[r] + (D == 3 ? qk * k : 0);
+      if (a.ph) {
+        const float vv[2] = {v.x, v.y}, oh[2] = {hph[r].x, hph[r].y}, ol[2] = {hpl[r].x, hpl[r].y};
+        float nh[2], nl[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          float sh, sl;
+          two_sum(oh[t], vv[t], sh, sl);
+          sl += ol[t];
+          fast_two_sum(sh, sl, nh[t], nl[t]);
+        }
+        *reinterpret_cast<float2*>(a.ph + q) = make_float2(nh[0], nh[1]);
+        *reinterpret_cast<float2*>(a.pl + q) = make_float2(nl[0], nl[1]);
+      } else {
+        *reinterpret_cast<float2*>(a.x_out + q) = v;
+      }
     }
   };
   // a copy timed out: flag it, wait (bounded) for the copies still in flight so none
@@ -296,9 +365,9 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
     const Planes P = planes_of(0);
     red_plane(P, 0);
     __syncthreads();
-    if (warp < 8) P.x0[eb0] = relax(P, eb0);
+    black_plane(P, 0);
     __syncthreads();
-    store(P.x0, 0);
+    store(Xs(xslot(0)), 0);
     return;
   } else {
   // red cells of planes k0-1, k0, k0+1 (independent of one another)
@@ -329,25 +398,12 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
       store(Xs(sx), k - 1);
       prefetch(k);
     }
-    const int par = k & 1, erk = par ? er1 : er0, ebk = par ? eb1 : eb0;
-    const bool do_red = k + 2 <= k1;
+    const int par = k & 1;
     const int sx2 = sx + 2 < XR ? sx + 2 : sx + 2 - XR;
     const int sl2 = sl + 2 < L2R ? sl + 2 : sl + 2 - L2R;
     const int sc2 = sc + 2 < CR ? sc + 2 : sc + 2 - CR;
-    if (warp < 8) {
-      const Planes Pb = planes(sx, sl, sc);
-      if (do_red) {
-        const Planes Pr = planes(sx2, sl2, sc2);
-        const float vr = relax(Pr, erk);
-        const float vb = relax(Pb, ebk);
-        Pr.x0[erk] = vr;
-        Pb.x0[ebk] = vb;
-      } else {
-        Pb.x0[ebk] = relax(Pb, ebk);
-      }
-    } else if (do_red) {
-      red_plane(planes(sx2, sl2, sc2), par);
-    }
+    if (k + 2 <= k1) red_plane(planes(sx2, sl2, sc2), par);
+    black_plane(planes(sx, sl, sc), par);
     sx = sx + 1 < XR ? sx + 1 : 0;
     sl = sl + 1 < L2R ? sl + 1 : 0;
     sc = sc + 1 < CR ? sc + 1 : 0;
