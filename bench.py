@@ -74,9 +74,9 @@ def algo_bytes(cls, D, n_div=0, n_res=0):
     raise KeyError(cls)
 
 
-KERNEL_NAMES = {"sweep_fine": "k_sweep<3> (fine level)", "resid_fine": "k_residual<3> (fine level)",
-                "stage": "k_stage<3>", "correct": "k_correct<3>"}
-KERNEL_SRC = {"sweep_fine": "wl_poisson.cu", "resid_fine": "wl_poisson.cu", "stage": "wl_momentum.cu",
+KERNEL_NAMES = {"sweep_fine": "k_sweep_tma<3> (fine level)", "resid_fine": "k_resid_tma (fine level)",
+                "stage": "k_stage<3>", "correct": "k_correct3"}
+KERNEL_SRC = {"sweep_fine": "wl_sweep_tma.cu", "resid_fine": "wl_sweep_tma.cu", "stage": "wl_momentum.cu",
               "correct": "wl_poisson.cu"}
 
 
