@@ -18,12 +18,13 @@ constexpr int ST_TX = 32, ST_TY = 8, ST_TZ = 32;
 constexpr int ST_HX = ST_TX + 4, ST_HY = ST_TY + 4;
 
 // Tile of ST_TX x ST_TY columns marching upward through ST_TZ planes.  The velocity
-// of planes k-1..k+2 (with a 2-cell in-plane halo) sits in a 4-plane shared ring.
+// of planes k-1..k+2 (with a 2-cell in-plane halo) sits in a 4-plane shared ring;
+// plane k+3 is loaded into registers while plane k is computed.
 // Each thread computes the lower x-, y- and z-face fluxes of its cell; the upper x/y
 // fluxes come from the neighbour through shared memory, the upper z flux is carried
 // in registers to the next plane, so every face flux is evaluated once.
 template <int D>
-__global__ void __launch_bounds__(256) k_stage(StageArgs a) {
+__global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
   constexpr int NP = (D == 3) ? 4 : 1;
   __shared__ float s_u[D][NP][ST_HY][ST_HX];
   __shared__ float s_fx[D][ST_TY][ST_TX + 1];
@@ -47,23 +48,40 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
   constexpr int HX = ST_HX;
   int k_cur = k0;  // plane whose x- and y-face fluxes are being formed
 
-  auto load_plane = [&](int kk) {
-    const int sl = slot(kk);
+  // A plane of the velocity (2-cell in-plane halo) moves in two steps: fetch() loads
+  // this thread's elements (at most two per component) into registers, commit()
+  // stores them into the plane's ring slot, so the loads of plane k+3 are in flight
+  // while the fluxes of plane k are formed.
+  constexpr int NE = ST_HY * ST_HX;
+  float rv[2][D];
+  auto fetch = [&](int kk) {
     const bool inner = (i0 >= 2) && (i0 + ST_TX + 2 <= g.n[0]) && (j0 >= 2) && (j0 + ST_TY + 2 <= g.n[1]) &&
                        (D == 2 || (kk >= 0 && kk < g.n[2]));
-    for (int e = tid; e < ST_HY * ST_HX; e += 256) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + 256 * h;
+      if (e >= NE) break;
       const int row = e / ST_HX, col = e - row * ST_HX;
       const int gi = i0 - 2 + col, gj = j0 - 2 + row;
 #pragma unroll
-      for (int c = 0; c < D; ++c) {
-        float v;
-        if (inner)
-          v = __ldg(a.u[c] + cell_index(g, gi, gj, D == 3 ? kk : 0));
-        else
-          v = load_u_bc<D>(a.u[c], c, g, gi, gj, kk);
-        s_u[c][sl][row][col] = v;
-      }
+      for (int c = 0; c < D; ++c)
+        rv[h][c] = inner ? __ldg(a.u[c] + cell_index(g, gi, gj, D == 3 ? kk : 0)) : load_u_bc<D>(a.u[c], c, g, gi, gj, kk);
     }
+  };
+  auto commit = [&](int kk) {
+    const int sl = slot(kk);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + 256 * h;
+      if (e >= NE) break;
+      const int row = e / ST_HX, col = e - row * ST_HX;
+#pragma unroll
+      for (int c = 0; c < D; ++c) s_u[c][sl][row][col] = rv[h][c];
+    }
+  };
+  auto load_plane = [&](int kk) {
+    fetch(kk);
+    commit(kk);
   };
 
   // Lower x-face flux of the u_c control volume at flat position pos of plane k
@@ -101,6 +119,7 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
     load_plane(k0 - 1);
     load_plane(k0);
     load_plane(k0 + 1);
+    fetch(k0 + 2);
     __syncthreads();
     int q[4][3];
     zoffs(k0, q);
@@ -110,8 +129,22 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
   }
 
   for (int k = k0; k < k1; ++k) {
-    load_plane(D == 3 ? k + 2 : 0);
+    // plane k+2 into the slot of plane k-2 (last read by the z fluxes of face k)
+    if (D == 3)
+      commit(k + 2);
+    else
+      load_plane(0);
     __syncthreads();
+    // in flight while the fluxes are formed: plane k+3 (the last plane used is k1+1),
+    // and this cell's mu0 and stage-1 velocity
+    if (D == 3 && k + 3 <= k1 + 1) fetch(k + 3);
+    const long long qg = cell_index(g, own_cell ? i : 0, own_cell ? j : 0, k);
+    float m0[D], u0v[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      m0[c] = own_cell ? __ldg(a.mu0[c] + qg) : 0.f;
+      u0v[c] = (own_cell && a.stage != 1) ? __ldg(a.u0[c] + qg) : 0.f;
+    }
     k_cur = k;
     int o[3], om2 = 0;
 #pragma unroll
@@ -137,7 +170,6 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
     }
     __syncthreads();
     if (own_cell) {
-      const long long qg = cell_index(g, i, j, k);
       const int I[3] = {i, j, k};
 #pragma unroll
       for (int c = 0; c < D; ++c) {
@@ -149,9 +181,9 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
           ov = g.U[c];
         } else {
           const float uc = sf[o[c] + own];
-          const float u0 = (a.stage == 1) ? uc : __ldg(a.u0[c] + qg);
+          const float u0 = (a.stage == 1) ? uc : u0v[c];
           const float f = fmaf(dt, r, u0);
-          const float m = __ldg(a.mu0[c] + qg);
+          const float m = m0[c];
           ov = (a.stage == 1) ? m * f : 0.5f * (uc + m * f);
         }
         a.out[c][qg] = ov;
