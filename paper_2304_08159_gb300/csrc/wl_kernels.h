@@ -139,7 +139,7 @@ constexpr int SWEEP_TX = 64, SWEEP_TY = 8;
 // rows of the sweep's coefficient boxes (z, L0, L2; L1 takes one more), from j0-1
 constexpr int SWEEP_CROWS = SWEEP_TY + 2;
 // resident blocks per SM of the staged sweep (shared memory bound)
-constexpr int SWEEP_BLOCKS_PER_SM = 3;
+constexpr int SWEEP_BLOCKS_PER_SM = 4;
 __host__ __device__ inline bool sweep_tile_wraps(const Grid& g, int D, int i0, int j0, int k0, int k1) {
   if ((g.per & 1u) && (i0 - 4 < 0 || i0 + SWEEP_TX + 4 > g.n[0])) return true;
   if ((g.per & 2u) && (j0 - 2 < 0 || j0 + SWEEP_TY + 2 > g.n[1])) return true;

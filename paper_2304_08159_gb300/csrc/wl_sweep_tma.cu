@@ -33,9 +33,9 @@ constexpr int BOX = BX * BY;          // floats per field per plane
 constexpr int CROWS = SWEEP_CROWS, L1ROWS = SWEEP_CROWS + 1;
 constexpr int CSLOT = (BX * CROWS + 31) / 32 * 32, L1SLOT = (BX * L1ROWS + 31) / 32 * 32;
 constexpr int LEAD = 1;         // bundles staged ahead of the iteration that waits for them
-constexpr int XR = LEAD + 5;    // iterate slots (planes k-1 .. k+3, and LEAD more in flight)
-constexpr int L2R = LEAD + 4;   // L2 slots (planes k .. k+3, and LEAD more in flight)
-constexpr int CR = LEAD + 3;    // z, L0, L1 slots (planes k .. k+2, and LEAD more in flight)
+constexpr int XR = LEAD + 4;    // iterate slots (planes k-1 .. k+2, and LEAD more in flight)
+constexpr int L2R = LEAD + 3;   // L2 slots (planes k .. k+2, and LEAD more in flight)
+constexpr int CR = LEAD + 2;    // z, L0, L1 slots (planes k, k+1, and LEAD more in flight)
 constexpr int NBB = 2;          // bundle mbarriers (a power of two, > LEAD)
 constexpr int SW_NT = 160;      // sweep threads: 5 warps
 static_assert(NBB > LEAD && (NBB & (NBB - 1)) == 0, "bundle barriers");
@@ -162,14 +162,14 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   };
   constexpr uint32_t kXB = BOX * 4, kCB = BX * CROWS * 4, kL1B = BX * L1ROWS * 4;
   int b_issued = k0 - 1;  // (thread 0) last bundle staged
-  // bundle b (waited at the start of iteration b): iterate and L2 of plane b+3,
-  // z, L0, L1 of plane b+2
+  // bundle b (waited at the start of iteration b): iterate and L2 of plane b+2,
+  // z, L0, L1 of plane b+1
   auto issue_bundle = [&](int b) {
     b_issued = b;
     mbar_expect_tx(bbar(b), (a.has_x ? kXB : 0u) + 3 * kCB + kL1B);
-    if (a.has_x) ld_x(b + 3, bbar(b));
-    ld_l2(b + 3, bbar(b));
-    ld_c(b + 2, bbar(b));
+    if (a.has_x) ld_x(b + 2, bbar(b));
+    ld_l2(b + 2, bbar(b));
+    ld_c(b + 1, bbar(b));
   };
   // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p
   auto fix_x = [&](int p) {
@@ -336,21 +336,21 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
     __syncthreads();
   };
 
-  // ---- prologue: iterate planes k0-2..k0+2, coefficients k0-1..k0+1 (L2 to k0+2),
+  // ---- prologue: iterate planes k0-2..k0+1, coefficients k0-1..k0 (L2 to k0+1),
   // and the first LEAD bundles
-  const int plo = (D == 3) ? k0 - 2 : 0, phi = (D == 3) ? k0 + 2 : 0;
+  const int plo = (D == 3) ? k0 - 2 : 0, phi = (D == 3) ? k0 + 1 : 0;
   if (tid == 0) {
-    const int ncp = (D == 3) ? 3 : 1, nl2 = (D == 3) ? 4 : 0;
+    const int ncp = (D == 3) ? 2 : 1, nl2 = (D == 3) ? 3 : 0;
     const uint32_t b0 = smem_addr(&bars[0]);
     mbar_expect_tx(b0, (a.has_x ? (uint32_t)(phi - plo + 1) * kXB : 0u) + (uint32_t)ncp * (2 * kCB + kL1B) +
                            (uint32_t)nl2 * kCB);
     if (a.has_x)
       for (int p = plo; p <= phi; ++p) ld_x(p, b0);
-    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 + 1 : 0); ++p) ld_c(p, b0);
+    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 : 0); ++p) ld_c(p, b0);
     if (D == 3)
-      for (int p = k0 - 1; p <= k0 + 2; ++p) ld_l2(p, b0);
+      for (int p = k0 - 1; p <= k0 + 1; ++p) ld_l2(p, b0);
     if (D == 3)
-      for (int b = k0; b < k0 + LEAD && b <= k1 - 2; ++b) issue_bundle(b);
+      for (int b = k0; b < k0 + LEAD && b <= k1 - 1; ++b) issue_bundle(b);
   }
   {
     const bool ok = mbar_wait(smem_addr(&bars[0]), 0);
@@ -370,27 +370,25 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
     store(Xs(xslot(0)), 0);
     return;
   } else {
-  // red cells of planes k0-1, k0, k0+1 (independent of one another)
-  for (int p = k0 - 1; p <= k0 + 1; ++p) red_plane(planes_of(p), p & 1);
+  // red cells of planes k0-1 and k0 (independent of each other)
+  for (int p = k0 - 1; p <= k0; ++p) red_plane(planes_of(p), p & 1);
   prefetch(k0);
 
-  // ---- iteration k: red cells of plane k+2 and black cells of plane k (disjoint
-  // cells; neither reads a value the other writes), and the store of plane k-1
+  // ---- iteration k: red cells of plane k+1, then black cells of plane k, and the
+  // store of plane k-1
   int sx = xslot(k0 - 1), sl = l2slot(k0), sc = cslot(k0);  // rolling slots of planes k-1 / k / k
   for (int k = k0; k < k1; ++k) {
-    if (k <= k1 - 2) {
+    {
       const bool ok = mbar_wait(bbar(k), bphase(k));
       if (__syncthreads_or(!ok)) return bail(false, k);
       if (fix) {
-        fix_x(k + 3);
+        fix_x(k + 2);
         __syncthreads();
       }
-    } else {
-      __syncthreads();
     }
     // every thread is past iteration k-1, the last use of iterate plane k-2 and of
     // coefficient plane k-1, the slots bundle k+LEAD fills
-    if (tid == 0 && k + LEAD <= k1 - 2) {
+    if (tid == 0 && k + LEAD <= k1 - 1) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue_bundle(k + LEAD);
     }
@@ -399,14 +397,15 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
       prefetch(k);
     }
     const int par = k & 1;
-    const int sx2 = sx + 2 < XR ? sx + 2 : sx + 2 - XR;
-    const int sl2 = sl + 2 < L2R ? sl + 2 : sl + 2 - L2R;
-    const int sc2 = sc + 2 < CR ? sc + 2 : sc + 2 - CR;
-    if (k + 2 <= k1) red_plane(planes(sx2, sl2, sc2), par);
+    const int sx1 = sx + 1 < XR ? sx + 1 : 0;
+    const int sl1 = sl + 1 < L2R ? sl + 1 : 0;
+    const int sc1 = sc + 1 < CR ? sc + 1 : 0;
+    red_plane(planes(sx1, sl1, sc1), par ^ 1);
+    __syncthreads();
     black_plane(planes(sx, sl, sc), par);
-    sx = sx + 1 < XR ? sx + 1 : 0;
-    sl = sl + 1 < L2R ? sl + 1 : 0;
-    sc = sc + 1 < CR ? sc + 1 : 0;
+    sx = sx1;
+    sl = sl1;
+    sc = sc1;
   }
   __syncthreads();
   store(Xs(sx), k1 - 1);
