@@ -66,7 +66,7 @@ struct wl_sim {
   double* fout = nullptr;
   float* ph = nullptr;        // precision 1: fine-level pressure as the double-float ph + pl
   float* pl = nullptr;
-  CUtensorMap mrf{}, srf{};   // TMA descriptors of rf (residual box, sweep box)
+  CUtensorMap srf{};          // TMA descriptor of rf (sweep box)
   CUtensorMap mph{}, mpl{};   // TMA descriptors of the fine pressure (ph: hi part or FP32 pressure)
   CUtensorMap mu[3][3]{};     // TMA descriptors of the velocity buffers A, B, C (components)
   bool resid_tma = false;     // the fine residual uses the TMA-staged kernel
@@ -653,23 +653,26 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   if (!rc && !std::getenv("WL_NO_TMA")) {  // tensor maps for the staged sweep
     for (int l = 0; l < s->nlev; ++l) {
       LevelBuf& L = s->lev[l];
+      // sweep boxes: iterate 12 rows, coefficients 10 (L1: 11); residual boxes: 8 rows
+      // (faces of y: 9)
       bool ok = make_field_map(&L.mx, L.x, L.g, ndim) && make_field_map(&L.mx2, L.x2, L.g, ndim) &&
-                make_field_map(&L.mz, L.z, L.g, ndim) && make_field_map(&L.sz, L.z, L.g, ndim, SWEEP_CROWS);
+                make_field_map(&L.mz, L.z, L.g, ndim, SWEEP_TY) && make_field_map(&L.sz, L.z, L.g, ndim, SWEEP_CROWS);
       for (int c = 0; c < ndim; ++c)
-        ok = ok && make_field_map(&L.mL[c], L.L[c], L.g, ndim) &&
+        ok = ok && make_field_map(&L.mL[c], L.L[c], L.g, ndim, SWEEP_TY + (c == 1 ? 1 : 0)) &&
              make_field_map(&L.sL[c], L.L[c], L.g, ndim, SWEEP_CROWS + (c == 1 ? 1 : 0));
-      if (l == 0 && s->rf)
-        ok = ok && make_field_map(&s->mrf, s->rf, L.g, ndim) && make_field_map(&s->srf, s->rf, L.g, ndim, SWEEP_CROWS);
+      if (l == 0 && s->rf) ok = ok && make_field_map(&s->srf, s->rf, L.g, ndim, SWEEP_CROWS);
       L.tma = ok;
     }
     // fine residual: 3-D, no periodic side
     LevelBuf& L0 = s->lev[0];
     bool ok = L0.tma && ndim == 3 && s->g.per == 0;
-    if (ok) ok = make_field_map(&s->mph, s->ph ? s->ph : L0.x, L0.g, ndim);
-    if (ok && s->pl) ok = make_field_map(&s->mpl, s->pl, L0.g, ndim);
+    // pressure boxes with a 1-row halo: 10 rows from j0-1
+    if (ok) ok = make_field_map(&s->mph, s->ph ? s->ph : L0.x, L0.g, ndim, SWEEP_TY + 2);
+    if (ok && s->pl) ok = make_field_map(&s->mpl, s->pl, L0.g, ndim, SWEEP_TY + 2);
     float** bufs[3] = {s->ua, s->ub, s->uc};
     for (int b = 0; b < 3 && ok; ++b)
-      for (int c = 0; c < ndim && ok; ++c) ok = make_field_map(&s->mu[b][c], bufs[b][c], L0.g, ndim);
+      for (int c = 0; c < ndim && ok; ++c)
+        ok = make_field_map(&s->mu[b][c], bufs[b][c], L0.g, ndim, SWEEP_TY + (c == 1 ? 1 : 0));
     s->resid_tma = ok;
   }
   if (!rc) {

@@ -417,20 +417,34 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
 // fields go to two rings: "column" fields needed at planes k-1..k+1 (pressure hi/lo,
 // z-face coefficients, and in divergence mode the z-velocity) in 4 slots, "plane"
 // fields needed only at plane k (right-hand side or x/y velocities, x/y face
-// coefficients) in 3 slots; plane k+2 is staged while plane k is computed.  Each
-// thread computes cells (lane, row) and (lane + 32, row) of the 64 x 8 tile, so the
-// restriction pairs x neighbours by a shuffle, y neighbours through shared memory
-// and z neighbours in registers.  Zero fill supplies L = 0 across the walls; the
-// velocity on an upper wall face is the boundary value, patched explicitly.
+// coefficients) in 3 slots; plane k+2 is staged while plane k is computed.  Boxes are
+// as tall as each field needs: the pressure with a 1-row halo (rows -1..8), the upper
+// faces of y (rows 0..8), everything else the tile's rows 0..7; all 72 wide from
+// i0-4.  Each thread computes cells (lane, row) and (lane + 32, row) of the 64 x 8
+// tile, so the restriction pairs x neighbours by a shuffle, y neighbours through
+// shared memory and z neighbours in registers.  Zero fill supplies L = 0 across the
+// walls; the velocity on an upper wall face is the boundary value, patched explicitly.
+constexpr int RS_P = 736, RS_8 = 576, RS_9 = 672;  // slot floats: 72 x 10, 72 x 8, 72 x 9 (128-byte multiples)
+constexpr int RS_PROWS = TY + 2, RS_8ROWS = TY, RS_9ROWS = TY + 1;
+template <bool DIV, bool DF>
+struct ResidLayout {
+  // column slot: ph, [pl], L2, [u2]; plane slot: DIV: u0, u1, L0, L1; else z, L0, L1
+  static constexpr int oPL = RS_P, oL2 = RS_P * (DF ? 2 : 1), oU2 = oL2 + RS_8;
+  static constexpr int ASZ = oU2 + (DIV ? RS_8 : 0);
+  static constexpr int oU0 = 0, oU1 = RS_8, oL0 = DIV ? RS_8 + RS_9 : RS_8, oL1 = oL0 + RS_8, oZ = 0;
+  static constexpr int BSZ = oL1 + RS_9;
+  static constexpr int SA = 4, SB = 3, NBAR = 4;
+  static constexpr size_t bytes = ((size_t)SA * ASZ + (size_t)SB * BSZ) * sizeof(float);
+};
+
 template <bool DIV, bool DF>
 __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ ResidMaps m, ResidTmaArgs a) {
-  constexpr int NA = (DF ? 2 : 1) + 1 + (DIV ? 1 : 0);  // column fields: ph, [pl], L2, [u2]
-  constexpr int NBF = DIV ? 4 : 3;                        // plane fields: (z | u0, u1), L0, L1
-  constexpr int SA = 4, SB = 3, NBAR = 4;
+  using LY = ResidLayout<DIV, DF>;
+  constexpr int SA = LY::SA, SB = LY::SB, NBAR = LY::NBAR;
   extern __shared__ unsigned char smem_raw[];
   float* abase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  float* bbase = abase + (size_t)SA * NA * BOX;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(bbase + (size_t)SB * NBF * BOX);
+  float* bbase = abase + (size_t)SA * LY::ASZ;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bbase + (size_t)SB * LY::BSZ);
   __shared__ float s_r[8][64];
   __shared__ unsigned s_m[8];
   const Grid& g = a.g;
@@ -438,14 +452,12 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int kb = blockIdx.z * a.tz, ke = min(kb + a.tz, g.n[2]);
   const int pa_first = kb - 1, pb_first = kb, p_last = ke;
-  // column field f of plane p: 0 ph, 1 pl (DF), then L2, then u2 (DIV)
-  auto A = [&](int p, int f) -> float* { return abase + ((size_t)((p - pa_first) % SA) * NA + f) * BOX; };
-  // plane field f of plane p: DIV: 0 u0, 1 u1, 2 L0, 3 L1; else 0 z, 1 L0, 2 L1
-  auto B = [&](int p, int f) -> float* { return bbase + ((size_t)((p - pb_first) % SB) * NBF + f) * BOX; };
+  // column slot / plane slot of plane p (fields at the LY offsets)
+  auto A = [&](int p) -> float* { return abase + (size_t)((p - pa_first) % SA) * LY::ASZ; };
+  auto B = [&](int p) -> float* { return bbase + (size_t)((p - pb_first) % SB) * LY::BSZ; };
   auto bar = [&](int p) { return smem_addr(&bars[(p - pa_first) % NBAR]); };
   auto phase = [&](int p) { return (uint32_t)(((p - pa_first) / NBAR) & 1); };
-  constexpr int fL2 = DF ? 2 : 1, fU2 = fL2 + 1;
-  constexpr int fL0 = DIV ? 2 : 1, fL1 = fL0 + 1;
+  constexpr uint32_t kPB = BX * RS_PROWS * 4, k8B = BX * RS_8ROWS * 4, k9B = BX * RS_9ROWS * 4;
 
   if (tid == 0) {
     for (int b = 0; b < NBAR; ++b) mbar_init(smem_addr(&bars[b]), 1);
@@ -457,23 +469,26 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
     if (p > p_last) return;
     p_issued = p;
     const bool plane = p >= pb_first && p < ke;
-    const uint32_t bytes = (uint32_t)((NA + (plane ? NBF : 0)) * BOX * sizeof(float));
+    const uint32_t col = (DF ? 2 : 1) * kPB + k8B + (DIV ? k8B : 0);
+    const uint32_t pln = DIV ? (k8B + k9B + k8B + k9B) : (k8B + k8B + k9B);
     const uint32_t br = bar(p);
-    mbar_expect_tx(br, bytes);
-    const int x = i0 - 4, y = j0 - 2;
-    tma_load(smem_addr(A(p, 0)), &m.ph, x, y, p, br, 3);
-    if (DF) tma_load(smem_addr(A(p, 1)), &m.pl, x, y, p, br, 3);
-    tma_load(smem_addr(A(p, fL2)), &m.L2, x, y, p, br, 3);
-    if (DIV) tma_load(smem_addr(A(p, fU2)), &m.u2, x, y, p, br, 3);
+    mbar_expect_tx(br, col + (plane ? pln : 0u));
+    const int x = i0 - 4;
+    float* Ap = A(p);
+    tma_load(smem_addr(Ap), &m.ph, x, j0 - 1, p, br, 3);
+    if (DF) tma_load(smem_addr(Ap + LY::oPL), &m.pl, x, j0 - 1, p, br, 3);
+    tma_load(smem_addr(Ap + LY::oL2), &m.L2, x, j0, p, br, 3);
+    if (DIV) tma_load(smem_addr(Ap + LY::oU2), &m.u2, x, j0, p, br, 3);
     if (plane) {
+      float* Bp = B(p);
       if (DIV) {
-        tma_load(smem_addr(B(p, 0)), &m.u0, x, y, p, br, 3);
-        tma_load(smem_addr(B(p, 1)), &m.u1, x, y, p, br, 3);
+        tma_load(smem_addr(Bp + LY::oU0), &m.u0, x, j0, p, br, 3);
+        tma_load(smem_addr(Bp + LY::oU1), &m.u1, x, j0, p, br, 3);
       } else {
-        tma_load(smem_addr(B(p, 0)), &m.z, x, y, p, br, 3);
+        tma_load(smem_addr(Bp + LY::oZ), &m.z, x, j0, p, br, 3);
       }
-      tma_load(smem_addr(B(p, fL0)), &m.L0, x, y, p, br, 3);
-      tma_load(smem_addr(B(p, fL1)), &m.L1, x, y, p, br, 3);
+      tma_load(smem_addr(Bp + LY::oL0), &m.L0, x, j0, p, br, 3);
+      tma_load(smem_addr(Bp + LY::oL1), &m.L1, x, j0, p, br, 3);
     }
   };
   auto bail = [&](int p_fail) {
@@ -502,38 +517,43 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       issue(k + 2);
     }
-    const float* ph0 = A(k, 0);
-    const float* pl0 = DF ? A(k, 1) : nullptr;
-    const float* phm = A(k - 1, 0);
-    const float* plm = DF ? A(k - 1, 1) : nullptr;
-    const float* php = A(k + 1, 0);
-    const float* plp = DF ? A(k + 1, 1) : nullptr;
-    const float* L0 = B(k, fL0);
-    const float* L1 = B(k, fL1);
-    const float* L2 = A(k, fL2);
-    const float* L2u = A(k + 1, fL2);
+    const float* A0 = A(k);
+    const float* Am = A(k - 1);
+    const float* Ap = A(k + 1);
+    const float* B0 = B(k);
+    const float* ph0 = A0;
+    const float* pl0 = A0 + LY::oPL;
+    const float* phm = Am;
+    const float* plm = Am + LY::oPL;
+    const float* php = Ap;
+    const float* plp = Ap + LY::oPL;
+    const float* L0 = B0 + LY::oL0;
+    const float* L1 = B0 + LY::oL1;
+    const float* L2 = A0 + LY::oL2;
+    const float* L2u = Ap + LY::oL2;
     const int gj = j0 + ty;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int ii = lane + 32 * h;
       const int gi = i0 + ii;
-      const int e = (ty + 2) * BX + ii + 4;
+      const int e = (ty + 1) * BX + ii + 4;  // pressure boxes (from row -1)
+      const int c = ty * BX + ii + 4;        // the other boxes (from row 0)
       const bool in = gi < g.n[0] && gj < g.n[1];
       float z;
       if (DIV) {
-        const float* U0 = B(k, 0);
-        const float* U1 = B(k, 1);
-        const float uxp = (gi + 1 < g.n[0]) ? U0[e + 1] : g.U[0];
-        const float uyp = (gj + 1 < g.n[1]) ? U1[e + BX] : g.U[1];
-        const float uzp = (k + 1 < g.n[2]) ? A(k + 1, fU2)[e] : g.U[2];
+        const float* U0 = B0 + LY::oU0;
+        const float* U1 = B0 + LY::oU1;
+        const float uxp = (gi + 1 < g.n[0]) ? U0[c + 1] : g.U[0];
+        const float uyp = (gj + 1 < g.n[1]) ? U1[c + BX] : g.U[1];
+        const float uzp = (k + 1 < g.n[2]) ? (Ap + LY::oU2)[c] : g.U[2];
         float div = 0.f;
-        div += uxp - U0[e];
-        div += uyp - U1[e];
-        div += uzp - A(k, fU2)[e];
+        div += uxp - U0[c];
+        div += uyp - U1[c];
+        div += uzp - (A0 + LY::oU2)[c];
         z = div * inv;
         if (in) a.z[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = z;
       } else {
-        z = B(k, 0)[e];
+        z = (B0 + LY::oZ)[c];
       }
       float r;
       if (DF) {
@@ -550,21 +570,21 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
           al += sl + tl;
         };
         // a missing neighbour across a wall reads 0 with a 0 coefficient: adds exactly 0
-        face(L0[e + 1], ph0[e + 1], pl0[e + 1]);
-        face(L0[e], ph0[e - 1], pl0[e - 1]);
-        face(L1[e + BX], ph0[e + BX], pl0[e + BX]);
-        face(L1[e], ph0[e - BX], pl0[e - BX]);
-        face(L2u[e], php[e], plp[e]);
-        face(L2[e], phm[e], plm[e]);
+        face(L0[c + 1], ph0[e + 1], pl0[e + 1]);
+        face(L0[c], ph0[e - 1], pl0[e - 1]);
+        face(L1[c + BX], ph0[e + BX], pl0[e + BX]);
+        face(L1[c], ph0[e - BX], pl0[e - BX]);
+        face(L2u[c], php[e], plp[e]);
+        face(L2[c], phm[e], plm[e]);
         float rh, rl;
         two_sum(z, -ah, rh, rl);
         r = rh + (rl - al);
       } else {
         const float x0 = ph0[e];
         float acc = 0.f;
-        acc += L0[e + 1] * (ph0[e + 1] - x0) + L0[e] * (ph0[e - 1] - x0);
-        acc += L1[e + BX] * (ph0[e + BX] - x0) + L1[e] * (ph0[e - BX] - x0);
-        acc += L2u[e] * (php[e] - x0) + L2[e] * (phm[e] - x0);
+        acc += L0[c + 1] * (ph0[e + 1] - x0) + L0[c] * (ph0[e - 1] - x0);
+        acc += L1[c + BX] * (ph0[e + BX] - x0) + L1[c] * (ph0[e - BX] - x0);
+        acc += L2u[c] * (php[e] - x0) + L2[c] * (phm[e] - x0);
         r = z - acc;
       }
       if (in) {
@@ -595,8 +615,9 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
 }
 
 size_t resid_tma_smem(bool div, bool df) {
-  const int na = (df ? 2 : 1) + 1 + (div ? 1 : 0), nb = div ? 4 : 3;
-  return ((size_t)4 * na + (size_t)3 * nb) * BOX * sizeof(float) + 4 * sizeof(uint64_t) + 128;
+  const size_t b = div ? (df ? ResidLayout<true, true>::bytes : ResidLayout<true, false>::bytes)
+                       : (df ? ResidLayout<false, true>::bytes : ResidLayout<false, false>::bytes);
+  return b + ResidLayout<false, false>::NBAR * sizeof(uint64_t) + 128;
 }
 
 int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s) {
