@@ -323,6 +323,14 @@ def run_ours(args, w, dist, rank, ws, lrank):
                "sample": f"1 full time step of the {args.workload} workload by the FP64 oracle (multigrid "
                          f"V(0,4) projections to tol 1e-6) after its setup, {tcpu:.1f} s"}
 
+    # whole-step roofline: algorithmic bytes per cell per step of the model (3-D: 196 B
+    # fixed + 142 B per V-cycle; 2-D: 136 B + 187 B), with the V-cycles actually run
+    nv = vcycles / args.steps
+    bstep = (196.0 + 142.0 * nv) if D == 3 else (136.0 + 187.0 * nv)
+    at_peak = peak * 1e9 / bstep
+    step_roof = {"bytes_per_cell_step": bstep, "vcycles_per_step": nv, "cells_steps_per_s_at_peak": at_peak,
+                 "frac": value / ws / at_peak, "peak": peak, "peak_kind": peak_kind}
+
     if rank == 0:
         line = {"metric": "cells*steps/s", "value": value, "unit": "cell*step/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
@@ -333,7 +341,8 @@ def run_ours(args, w, dist, rank, ws, lrank):
                            "l2": "inputs larger than L2 (working set %.1f GB)" % (sim.workspace.numel() / 1e9)},
                 "vcycles_per_s": vtot / tmax, "vcycles_per_step": vcycles / args.steps,
                 "converged": rc == 0, "worst_residual": worst,
-                "roofline": roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
+                "roofline": roof, "step_roofline": step_roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": ck,
                 "gpu_launches": int(ws * launches)}
         print(json.dumps(line), flush=True)
     sim.close()
