@@ -211,6 +211,19 @@ int wl_profile_step(wl_handle h, int nsteps, double* ms, long long* launches);
 int wl_forces_noalloc(const int* dims, int ndim, unsigned periodic_mask, const wl_body* body, double eps,
                       const float* p, const float* L, double* F, void* stream);
 
+/* Self-test of the bounded device waits.  Every kernel that waits on the device (the
+ * TMA-staged sweep and residual wait for their copies on mbarriers) gives up after a
+ * wall-clock limit (2 s), records the timeout in the sim's status and returns, so that
+ * a wait that cannot end becomes WL_ETIMEOUT instead of a hung GPU.  This call runs
+ * the same wait on an mbarrier that nothing arrives at, with the limit `seconds`
+ * (0 < seconds <= 10):
+ *   returns WL_ETIMEOUT when the wait gave up (the expected result), WL_OK if it
+ *   completed (it cannot), WL_EINVAL for a bad limit, WL_ECUDA/WL_ENOMEM on a CUDA
+ *   failure; *elapsed_ms (may be NULL) receives the kernel's duration.
+ * Synchronous; allocates 4 bytes of device memory for the flag.  No counterpart in the
+ * paper. */
+int wl_wait_probe(double seconds, double* elapsed_ms);
+
 /* Levels of the multigrid hierarchy and the dims of level l (dims[3]). */
 int wl_levels(wl_handle h, int* nlevels);
 int wl_level_dims(wl_handle h, int l, int* dims);

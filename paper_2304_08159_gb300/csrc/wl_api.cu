@@ -955,6 +955,36 @@ int wl_profile_step(wl_handle s, int nsteps, double* ms, long long* launches) {
   return rc;
 }
 
+int wl_wait_probe(double seconds, double* elapsed_ms) {
+  if (!(seconds > 0.0) || seconds > 10.0) return WL_EINVAL;
+  int* flag = nullptr;
+  if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return WL_ENOMEM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int rc = WL_OK, gave_up = 0;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WL_ECUDA;
+  if (!rc) {
+    cudaMemset(flag, 0, sizeof(int));
+    cudaEventRecord(e0, 0);
+    launch_wait_probe((uint64_t)(seconds * 1e9), flag, 0);
+    cudaEventRecord(e1, 0);
+    if (cudaMemcpy(&gave_up, flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) rc = WL_ECUDA;
+  }
+  if (!rc && elapsed_ms) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *elapsed_ms = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(flag);
+  if (cudaGetLastError() != cudaSuccess && !rc) rc = WL_ECUDA;
+  if (rc) return rc;
+  return gave_up ? WL_ETIMEOUT : WL_OK;
+}
+
 int wl_levels(wl_handle s, int* nlevels) {
   if (!s || !nlevels) return WL_EINVAL;
   *nlevels = s->nlev;

@@ -129,6 +129,7 @@ struct ResidTmaArgs {
   DevState* st;        // dt, residual maximum, timeout flag
 };
 int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s);
+int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s);
 int sweep_planes_per_block(const Grid& g);
 
 // Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.

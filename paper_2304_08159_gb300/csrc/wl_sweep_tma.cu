@@ -70,14 +70,14 @@ __device__ __forceinline__ uint64_t global_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// bounded wait: false if the phase did not complete within kWaitNs of wall time
+// bounded wait: false if the phase did not complete within limit_ns of wall time
 // (or kWaitLimit attempts)
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (unsigned it = 0; it < kWaitLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
   return false;
 }
@@ -612,6 +612,22 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
   }
   const unsigned mb = block_max_bits<256>(mbits, s_m);
   if (tid == 0 && mb) atomicMax(&a.st->norm_bits, mb);
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at, so the wait has to give up after limit_ns; *gave_up records it.
+__global__ void k_wait_probe(uint64_t limit_ns, int* gave_up) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_addr(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *gave_up = mbar_wait(smem_addr(&bar), 0, limit_ns) ? 0 : 1;
+  }
+}
+
+int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(limit_ns, gave_up);
+  return 0;
 }
 
 size_t resid_tma_smem(bool div, bool df) {
