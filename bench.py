@@ -40,6 +40,15 @@ WORKLOADS = {
     "tgv128": dict(dims=(128, 128, 128), nu=(128.0 / (2 * 3.141592653589793)) / 1600.0, U=(0.0, 0.0, 0.0),
                    body=None, periodic=7, ic=1,
                    desc="3-D Taylor-Green vortex, 128^3 periodic, Re=1600, tol 1e-6"),
+    # the paper's donut: a torus (axis along the flow) in an N = (2^(p+1), 2^p, 2^p) box,
+    # Re = 1000 on the ring diameter; ring radius 2^p/8 and tube radius 2^p/32 centred a
+    # quarter of the way down the box (the paper shows the shape, not its dimensions)
+    "donut256": dict(dims=(256, 128, 128), nu=32.0 / 1000.0, U=(1.0, 0.0, 0.0),
+                     body=dict(kind=2, center=(64.0, 64.0, 64.0), radius=16.0, radius2=4.0), periodic=0, ic=0,
+                     desc="3-D flow past a torus R=16 r=4 (axis along the flow), Re=1000, 256x128x128 cells, tol 1e-6"),
+    "donut512": dict(dims=(512, 256, 256), nu=64.0 / 1000.0, U=(1.0, 0.0, 0.0),
+                     body=dict(kind=2, center=(128.0, 128.0, 128.0), radius=32.0, radius2=8.0), periodic=0, ic=0,
+                     desc="3-D flow past a torus R=32 r=8 (axis along the flow), Re=1000, 512x256x256 cells, tol 1e-6"),
     "cyl128x64": dict(dims=(128, 64), nu=0.064, U=(1.0, 0.0), body=dict(kind=1, center=(32.0, 32.0), radius=8.0),
                       periodic=0, ic=0, desc="2-D flow past a circle R=8, Re=250, 128x64 cells, tol 1e-6"),
 }

@@ -20,6 +20,8 @@ CASES_3D = [
          body=dict(kind=1, center=(20.0, 16.0, 16.0), radius=6.0)),
     dict(id="ragged35x21x19", dims=(35, 21, 19), nu=0.015, U=(0.6, 0.2, -0.1), periodic=2,
          body=dict(kind=1, center=(12.7, 10.1, 9.4), radius=3.6)),
+    dict(id="torus48x32x32", dims=(48, 32, 32), nu=0.02, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=2, center=(14.0, 16.3, 15.8), radius=8.0, radius2=3.0)),
 ]
 
 

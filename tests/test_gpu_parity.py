@@ -111,8 +111,25 @@ def test_vcycle_parity(case):
         # oracle returns the zero-mean solution, the GPU adds a zero-mean correction)
         xg = (xg - xg[act].mean()) * act
         xo = (xo - xo[act].mean()) * act
+    # Rows whose faces are almost blocked by the body (diagonal below 1e-2) divide
+    # near-cancelling sums by that small diagonal and so amplify FP32 rounding; what the
+    # projection uses there is the face flux L (x_I - x_{I-e}), which is small with L.
+    # So: cell values on the other rows, face fluxes everywhere.
     scale = np.abs(xo).max()
-    assert np.abs(xg - xo).max() <= 1e-5 * scale, (np.abs(xg - xo).max(), scale)
+    well = ref.poisson_diag() >= 1e-2
+    assert np.abs(xg - xo)[well].max() <= 1e-5 * scale, (np.abs(xg - xo)[well].max(), scale)
+    Ls = ref.level_L(0)
+    D = len(case["dims"])
+    for d in range(D):
+        ax = D - 1 - d  # x fastest: direction d is array axis D-1-d
+        hi = [slice(None)] * D
+        lo = [slice(None)] * D
+        hi[ax], lo[ax] = slice(1, None), slice(0, -1)
+        hi, lo = tuple(hi), tuple(lo)
+        Lf = np.asarray(Ls[d])[hi]
+        fg = Lf * (xg[hi] - xg[lo])
+        fo = Lf * (xo[hi] - xo[lo])
+        assert np.abs(fg - fo).max() <= 1e-5 * max(np.abs(fo).max(), 1e-300), (d, np.abs(fg - fo).max())
     if ref.nlevels() > 1:
         assert abs(r_gpu - r_or) <= 1e-3 * abs(r_or) + 1e-5 * np.abs(z).max()
 
@@ -205,6 +222,28 @@ def test_pressure_parity_tight():
     assert rel_l2(pg, po) <= 1e-5, rel_l2(pg, po)
 
 
+def test_donut_steps_parity():
+    """The paper's donut workload in small: a torus (ring radius 8, tube radius 3, axis
+    along the flow) in a 64x32x32 box, U = 1, 10 adaptive steps at Poisson tol 1e-8:
+    velocity, pressure and the drag force against the oracle."""
+    case = dict(id="donut64", dims=(64, 32, 32), nu=16.0 / 1000.0, U=(1.0, 0.0, 0.0), periodic=0,
+                body=dict(kind=2, center=(16.0, 16.0, 16.0), radius=8.0, radius2=3.0))
+    sim, ref = make_pair(case, tol=1e-8)
+    sim.step(10)
+    ref.step(10, tol=1e-12)
+    rc, last, tot, worst = sim.status()
+    assert rc == 0, (rc, last, tot, worst)
+    assert rel_l2(sim.get(0).astype(np.float64), ref.get_u()) <= 1e-5
+    act = active_mask(ref)
+    pg, po = sim.get(1).astype(np.float64), ref.get_p()
+    pg = (pg - pg[act].mean()) * act
+    po = (po - po[act].mean()) * act
+    assert rel_l2(pg, po) <= 1e-5, rel_l2(pg, po)
+    Fg, Fo = sim.forces(), ref.forces()
+    assert abs(Fg[0] - Fo[0]) <= 1e-4 * abs(Fo[0]), (Fg, Fo)
+    assert abs(sim.dt - ref.dt) <= 1e-5 * ref.dt
+
+
 def test_tgv3d_steps_parity():
     N = 32
     L = N / (2 * np.pi)
@@ -269,7 +308,7 @@ def test_impulsive_start_meets_tol_with_fp64_pressure():
         assert rc == 0 and worst <= 1e-6 and max(last) < 32, (rc, last, tot, worst)
 
 
-@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[2], CASES_2D[0], CASES_2D[3]], ids=lambda c: c["id"])
+@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[2], CASES_3D[4], CASES_2D[0], CASES_2D[3]], ids=lambda c: c["id"])
 def test_tma_sweep_matches_table_sweep(case, monkeypatch):
     """The TMA-staged sweep and the index-table sweep are the same arithmetic: three
     steps give identical bits."""

@@ -68,6 +68,23 @@ def test_body_volume_sphere():
         assert abs((1 - m[c]).sum() / V - 1) < 0.5 / R**2
 
 
+def test_body_volume_torus():
+    """Sum of (1 - mu0) over the faces is the torus volume 2 pi^2 R r^2 up to the
+    kernel's O(eps^2 / r^2) smearing: for a symmetric kernel the excess is eps^2 times
+    the integrated mean curvature (4 pi^2 R for a torus) up to a constant, so the
+    relative error times r^2 is the same constant for every tube radius."""
+    scaled = []
+    for R, r, n in ((12, 4, 64), (10, 5, 64), (16, 6, 80)):
+        o = O.Oracle((n, n, n), 0.01, U=(1, 0, 0), body=dict(kind=2, center=(n / 2, n / 2, n / 2), radius=R, radius2=r))
+        m = o.mu0()
+        V = 2.0 * math.pi**2 * R * r**2
+        for c in range(3):
+            err = (1 - m[c]).sum() / V - 1
+            assert abs(err) < 0.5 / r**2
+            scaled.append(err * r**2)
+    assert max(scaled) - min(scaled) < 0.1 * max(abs(x) for x in scaled)
+
+
 def test_mu1_direction_and_band():
     """mu1 is eps*K1(d/eps) times the outward normal; zero outside |d| < eps."""
     o = O.Oracle((48, 40), 0.05, U=(1, 0), body=dict(kind=1, center=(20.3, 19.7), radius=6.5))
@@ -467,6 +484,18 @@ def test_buoyancy_sphere():
     o.set_p(X)
     F = o.forces()
     assert abs(F[0] / (-4.0 / 3.0 * math.pi * R**3) - 1) < 0.5 / R**2
+    assert abs(F[1]) < 1e-9 and abs(F[2]) < 1e-9
+
+
+def test_buoyancy_torus():
+    """p = x on a torus whose axis is x: F = -V e_x with V = 2 pi^2 R r^2, no side force."""
+    R, r = 12, 4
+    o = O.Oracle((64, 64, 64), 0.01, U=(1, 0, 0), body=dict(kind=2, center=(32, 32, 32), radius=R, radius2=r))
+    nz, ny, nx = o.shape
+    Z, Y, X = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    o.set_p(X)
+    F = o.forces()
+    assert abs(F[0] / (-2.0 * math.pi**2 * R * r**2) - 1) < 0.5 / r**2
     assert abs(F[1]) < 1e-9 and abs(F[2]) < 1e-9
 
 
