@@ -332,6 +332,13 @@ def run_ours(args, w, dist, rank, ws, lrank):
                "sample": f"1 full time step of the {args.workload} workload by the FP64 oracle (multigrid "
                          f"V(0,4) projections to tol 1e-6) after its setup, {tcpu:.1f} s"}
 
+    serving = None
+    if rank == 0 and ws == 1 and not args.no_serve:
+        try:
+            serving = serving_bench(args.serve_requests, args.tol)
+        except Exception as e:  # reported, not fatal: the main measurement stands
+            serving = {"error": f"{type(e).__name__}: {e}"}
+
     # whole-step roofline: algorithmic bytes per cell per step of the model (3-D: 196 B
     # fixed + 142 B per V-cycle; 2-D: 136 B + 187 B), with the V-cycles actually run
     nv = vcycles / args.steps
@@ -351,11 +358,41 @@ def run_ours(args, w, dist, rank, ws, lrank):
                 "vcycles_per_s": vtot / tmax, "vcycles_per_step": vcycles / args.steps,
                 "converged": rc == 0, "worst_residual": worst,
                 "roofline": roof, "step_roofline": step_roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": ck,
+                "serving": serving, "clocks": ck,
                 "gpu_launches": int(ws * launches)}
         print(json.dumps(line), flush=True)
     sim.close()
     return 0
+
+
+def serving_bench(n_req, tol):
+    """The serving mix (seeded Poisson stream of 2-D cylinder and 3-D sphere cases of
+    different sizes) served batched (continuous batching, one wl_step_batch per round)
+    and one request at a time on the same GPU; wall time includes admission and
+    simulation setup in both."""
+    import numpy as np
+    from paper_2304_08159_gb300 import serve
+
+    reqs = serve.request_stream(n_req)
+    warm = serve.request_stream(2, seed=1)
+    serve.serve_gpu(warm, tol=tol)
+    serve.sequential_gpu(warm, tol=tol)
+    stats, lat = serve.serve_gpu(reqs, tol=tol)
+    t_seq, cs_seq, lat_seq = serve.sequential_gpu(reqs, tol=tol)
+    occ = [n for n, _, _ in stats["rounds"]]
+    b = stats["cells_steps"] / stats["wall_s"]
+    q = cs_seq / t_seq
+    return {"requests": n_req, "mix": "seeded Poisson stream (seed 20230417, 2 per round): 2-D cylinder N^2 "
+                                      "N 64-512, 3-D sphere N^3 N 32-192, R 4-24, Re 100-1000, 20-200 steps",
+            "batched": {"value": b, "unit": "cell*step/s", "wall_s": stats["wall_s"],
+                        "step_latency_ms_p50": float(np.percentile(lat, 50)),
+                        "step_latency_ms_p99": float(np.percentile(lat, 99)),
+                        "rounds": len(lat), "mean_resident": float(np.mean(occ)), "max_resident": int(max(occ)),
+                        "peak_workspace_gb": stats["peak_bytes"] / 1e9},
+            "sequential": {"value": q, "unit": "cell*step/s", "wall_s": t_seq,
+                           "step_latency_ms_p50": float(np.percentile(lat_seq, 50)),
+                           "step_latency_ms_p99": float(np.percentile(lat_seq, 99))},
+            "batched_over_sequential": b / q, "poisson_tol": tol}
 
 
 def main():
@@ -371,6 +408,8 @@ def main():
     ap.add_argument("--ref-steps", type=int, default=2)
     ap.add_argument("--ref-warmup", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -125,6 +125,16 @@ int wl_set_ic(wl_handle h, int kind, double amp, const float* src, int src_is_de
  * the device; wl_status() reads them. */
 int wl_step(wl_handle h, int nsteps);
 
+/* Advance n resident simulations together: every sim hs[i] advances nsteps time steps
+ * on its own stream, the sims' work overlaps on the device, and the whole batch is
+ * ordered after the work already queued on `stream` and before the work queued on it
+ * next (fork and join through events), so a caller can time one batch round with two
+ * events on `stream`.  Give each sim its own stream (wl_opts.stream) for the overlap.
+ * Asynchronous.  Returns the first error (the other sims are still launched); a
+ * poisoned sim is skipped with WL_ENONFINITE.  Serving many simulations of different
+ * sizes on one device; no counterpart in the paper. */
+int wl_step_batch(const wl_handle* hs, int n, int nsteps, void* stream);
+
 /* One Heun stage of convdiff! + BDIM! + BC! (Table 2) with the current dt, written
  * to the stage buffer (WL_FIELD_USTAGE): stage 1 maps u0 = WL_FIELD_U to
  * mu0 f + mu1.grad f with f = u0 + dt r(u0); stage 2 maps (u0 = WL_FIELD_U,

@@ -77,6 +77,7 @@ struct wl_sim {
   bool own_ws = false;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaEvent_t join = nullptr;  // wl_step_batch: end of this sim's part of a batch round
   cudaGraphConditionalHandle hc[2]{};
   bool poisoned = false;
   std::string err;
@@ -715,6 +716,7 @@ void wl_destroy(wl_handle s) {
   else cudaDeviceSynchronize();
   if (s->exec) cudaGraphExecDestroy(s->exec);
   if (s->graph) cudaGraphDestroy(s->graph);
+  if (s->join) cudaEventDestroy(s->join);
   if (s->cs) cudaStreamDestroy(s->cs);
   if (s->hs) cudaFreeHost(s->hs);
   if (s->own_ws && s->ws) cudaFree(s->ws);
@@ -758,6 +760,38 @@ int wl_step(wl_handle s, int nsteps) {
   }
   for (int n = 0; n < nsteps; ++n) WL_CUDA(s, cudaGraphLaunch(s->exec, s->st));
   return WL_OK;
+}
+
+int wl_step_batch(const wl_handle* hs, int n, int nsteps, void* stream) {
+  if ((!hs && n > 0) || n < 0 || nsteps < 0) return WL_EINVAL;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaEvent_t fork = nullptr;
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventRecord(fork, cs) != cudaSuccess) {
+    cudaGetLastError();
+    if (fork) cudaEventDestroy(fork);
+    return WL_ECUDA;
+  }
+  int first = WL_OK;
+  for (int i = 0; i < n; ++i) {
+    wl_handle s = hs[i];
+    int rc = WL_OK;
+    if (!s) {
+      rc = WL_EINVAL;
+    } else if (s->poisoned) {
+      rc = fail(s, WL_ENONFINITE, "sim is poisoned by a non-finite value");
+    } else {
+      const bool own = s->st != cs;
+      if (own && !s->join) rc = cuda_check(s, cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming), "join event");
+      if (!rc && own) rc = cuda_check(s, cudaStreamWaitEvent(s->st, fork, 0), "fork");
+      if (!rc) rc = wl_step(s, nsteps);
+      if (!rc && own) rc = cuda_check(s, cudaEventRecord(s->join, s->st), "join record");
+      if (!rc && own) rc = cuda_check(s, cudaStreamWaitEvent(cs, s->join, 0), "join");
+    }
+    if (rc && !first) first = rc;
+  }
+  cudaEventDestroy(fork);
+  return first;
 }
 
 int wl_stage(wl_handle s, int stage) {

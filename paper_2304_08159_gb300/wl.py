@@ -41,7 +41,7 @@ EXPORTS = (
     "wl_default_opts", "wl_workspace_bytes", "wl_create", "wl_set_ic", "wl_step", "wl_stage",
     "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_get_field", "wl_set_field", "wl_get_dt",
     "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_levels", "wl_level_dims",
-    "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe",
+    "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
 )
 KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coarse", "coarsest", "correct",
             "control")
@@ -103,6 +103,7 @@ def load(path: str = LIB_PATH):
         "wl_last_error": (ctypes.c_char_p, [H]),
         "wl_forces_noalloc": (I, [IP, I, ctypes.c_uint, ctypes.POINTER(WlBody), D, P, P, P, P]),
         "wl_wait_probe": (I, [D, DP]),
+        "wl_step_batch": (I, [ctypes.POINTER(H), I, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -225,6 +226,12 @@ def wl_forces_noalloc(dims, periodic, body: WlBody, eps, p_ptr, L_ptr, F_ptr, st
     d = (ctypes.c_int * 3)(*(list(dims) + [1] * (3 - len(dims))))
     return load().wl_forces_noalloc(d, len(dims), int(periodic), ctypes.byref(body), float(eps), p_ptr, L_ptr,
                                     F_ptr, stream)
+
+
+def wl_step_batch(handles, nsteps, stream=None):
+    """Advance the sims `handles` (wl_handle values) by nsteps each, together (see include/wl.h)."""
+    arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    return load().wl_step_batch(arr, len(handles), int(nsteps), stream)
 
 
 def wl_wait_probe(seconds):
