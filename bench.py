@@ -332,6 +332,14 @@ def run_ours(args, w, dist, rank, ws, lrank):
                "sample": f"1 full time step of the {args.workload} workload by the FP64 oracle (multigrid "
                          f"V(0,4) projections to tol 1e-6) after its setup, {tcpu:.1f} s"}
 
+    mixed = None
+    if rank == 0 and ws == 1 and not args.no_mixed:
+        sim.close()
+        try:
+            mixed = mixed_bench(w, args)
+        except Exception as e:  # reported, not fatal: the main measurement stands
+            mixed = {"error": f"{type(e).__name__}: {e}"}
+
     serving = None
     if rank == 0 and ws == 1 and not args.no_serve:
         try:
@@ -358,11 +366,58 @@ def run_ours(args, w, dist, rank, ws, lrank):
                 "vcycles_per_s": vtot / tmax, "vcycles_per_step": vcycles / args.steps,
                 "converged": rc == 0, "worst_residual": worst,
                 "roofline": roof, "step_roofline": step_roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
-                "serving": serving, "clocks": ck,
+                "mixed_precision": mixed, "serving": serving, "clocks": ck,
                 "gpu_launches": int(ws * launches)}
         print(json.dumps(line), flush=True)
     sim.close()
     return 0
+
+
+def mixed_bench(w, args):
+    """The same workload with the multigrid levels between the fine and the coarsest
+    one stored in BF16 and in FP16 (FP32 arithmetic; fine residual, pressure and FP64
+    coarsest solve unchanged), timed like the main line over up to 100 steps, and its
+    velocity and pressure after warm-up + those steps against an FP32 run of the same
+    steps (relative L2; the pressure with its mean removed)."""
+    import numpy as np
+    import torch
+
+    from paper_2304_08159_gb300 import Sim
+
+    steps = max(1, min(args.steps, 100))
+    stream = torch.cuda.current_stream()
+
+    def run(cp):
+        sim = Sim(w["dims"], w["nu"], w["U"], body=w["body"], periodic=w["periodic"], tol=args.tol,
+                  coarse_precision=cp)
+        if w["ic"]:
+            sim.set_ic(w["ic"], 1.0)
+        sim.step(args.warmup)
+        sim.status()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        rc, last, vc, worst = sim.status()
+        u, p = sim.get(0, device=True).double(), sim.get(1, device=True).double()
+        sim.close()
+        return t, vc, rc, worst, u, p - p.mean()
+
+    ncell = int(np.prod(w["dims"]))
+    t32, vc32, _, _, u32, p32 = run("fp32")
+    out = {"steps": steps, "poisson_tol": args.tol,
+           "fp32": {"value": ncell * steps / t32, "unit": "cell*step/s", "vcycles_per_step": vc32 / steps}}
+    for cp in ("bf16", "fp16"):
+        t, vc, rc, worst, u, p = run(cp)
+        out[cp] = {"value": ncell * steps / t, "unit": "cell*step/s", "vcycles_per_step": vc / steps,
+                   "converged": rc == 0, "worst_residual": worst, "speedup_vs_fp32": t32 / t,
+                   "rel_l2_u_vs_fp32": float(torch.linalg.norm(u - u32) / torch.linalg.norm(u32)),
+                   "rel_l2_p_vs_fp32": float(torch.linalg.norm(p - p32) / torch.linalg.norm(p32))}
+        del u, p
+    return out
 
 
 def serving_bench(n_req, tol):
@@ -410,6 +465,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -95,13 +95,26 @@ typedef struct {
   void* stream;          /* cudaStream_t for all work (default NULL) */
   void* workspace;       /* optional caller-owned device buffer of wl_workspace_bytes() */
   size_t workspace_bytes;
+  int coarse_precision;  /* storage of the multigrid levels between the fine and the coarsest one:
+                            WL_COARSE_FP32 (default), WL_COARSE_BF16 or WL_COARSE_FP16.  A 16-bit
+                            level keeps its face coefficients, right-hand side and iterate in 16 bits
+                            and does every operation in FP32; its right-hand side is stored as the
+                            mean, not the sum, of its fine cells' residuals (an exact power-of-two
+                            scale), so its values stay within the fine residual's range (FP16 holds
+                            magnitudes up to 65504).  The fine-level residual, the pressure and the
+                            FP64 coarsest solve are unchanged, so the V-cycles converge to the same
+                            tolerance (iterative refinement); only their count may change. */
 } wl_opts;
+
+#define WL_COARSE_FP32 0
+#define WL_COARSE_BF16 1
+#define WL_COARSE_FP16 2
 
 /* Fill *o with the defaults listed above. */
 void wl_default_opts(wl_opts* o);
 
 /* Bytes of device workspace one sim of these dimensions needs (ndim 2 or 3;
- * dims[d] >= 2).  Returns 0 on bad arguments. */
+ * dims[d] >= 2) with these options (NULL = defaults).  Returns 0 on bad arguments. */
 size_t wl_workspace_bytes(const int* dims, int ndim, const wl_opts* opts);
 
 /* Create a sim (measure step of the method: evaluates the body's signed distance

@@ -32,10 +32,15 @@ namespace {
 
 struct LevelBuf {
   Grid g;
-  float* L[3];
-  float* z;
-  float* x;
+  float* L[3];                    // face coefficients in FP32 (hierarchy construction, coarsest solve)
+  float* Lk[3];                   // the coefficients the level's kernels read (storage type st)
+  float* z;                       // right-hand side, iterate, ping-pong iterate (storage type st;
+  float* x;                       //   a 16-bit level's pointers are reinterpreted by the kernels)
   float* x2;
+  int st;                         // storage type ST_* of Lk, z, x, x2
+  float zs;                       // z is stored scaled: stored = zs * value (a power of two)
+  float* z32;                     // a 16-bit level 1: the restricted fine residual in FP32, converted
+                                  // (with the scale DevState::cs_used) by level 1's restriction pass
   bool tma;                       // tensor maps below are valid (n_0 % 4 == 0)
   CUtensorMap mx, mx2, mz, mL[3];  // TMA descriptors of this level's fields
   CUtensorMap sz, sL[3];           // the sweep's shorter coefficient boxes
@@ -180,7 +185,13 @@ struct Carver {
 };
 
 // Walks the workspace layout; with base == nullptr only measures it.
-size_t layout(wl_sim* s, int D, const int* dims, int precision, char* base) {
+// Storage type of level l: the coarse levels between the fine and the coarsest one
+// take wl_opts.coarse_precision (FP32 arithmetic on 16-bit values); the fine and the
+// coarsest level stay FP32.
+int level_storage(int l, int nlev, int cprec) { return (l >= 1 && l + 1 < nlev) ? cprec : ST_F32; }
+size_t esize(int st) { return st == ST_F32 ? sizeof(float) : 2; }
+
+size_t layout(wl_sim* s, int D, const int* dims, int precision, int cprec, char* base) {
   int ld[kMaxLevels][3];
   const int nlev = plan_levels(dims, D, ld);
   Carver cv{base};
@@ -193,17 +204,27 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, char* base) {
     }
   for (int l = 0; l < nlev; ++l) {
     const long long n = (long long)ld[l][0] * ld[l][1] * ld[l][2];
+    const int st = level_storage(l, nlev, cprec);
     for (int c = 0; c < D; ++c) {
       void* p = cv.take(sizeof(float) * n);
-      if (s) s->lev[l].L[c] = (float*)p;
+      void* pk = st == ST_F32 ? p : cv.take(esize(st) * n);
+      if (s) {
+        s->lev[l].L[c] = (float*)p;
+        s->lev[l].Lk[c] = (float*)pk;
+      }
     }
-    void* z = cv.take(sizeof(float) * n);
-    void* x = cv.take(sizeof(float) * n);
-    void* x2 = cv.take(sizeof(float) * n);
+    void* z = cv.take(esize(st) * n);
+    void* x = cv.take(esize(st) * n);
+    void* x2 = cv.take(esize(st) * n);
+    void* z32 = (l == 1 && st != ST_F32) ? cv.take(sizeof(float) * n) : nullptr;
     if (s) {
+      s->lev[l].z32 = (float*)z32;
       s->lev[l].z = (float*)z;
       s->lev[l].x = (float*)x;
       s->lev[l].x2 = (float*)x2;
+      s->lev[l].st = st;
+      // a 16-bit level holds the mean rather than the sum of its 2^(D l) fine cells
+      s->lev[l].zs = st == ST_F32 ? 1.f : ldexpf(1.f, -D * l);
     }
   }
   void* ds = cv.take(sizeof(DevState));
@@ -234,7 +255,10 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, char* base) {
     for (int b = 0; b < 3; ++b)
       for (int c = D; c < 3; ++c) bufs[b][c] = bufs[b][D - 1];  // 2-D: unused slot aliases a valid pointer
     for (int l = 0; l < nlev; ++l)
-      for (int c = D; c < 3; ++c) s->lev[l].L[c] = s->lev[l].L[D - 1];
+      for (int c = D; c < 3; ++c) {
+        s->lev[l].L[c] = s->lev[l].L[D - 1];
+        s->lev[l].Lk[c] = s->lev[l].Lk[D - 1];
+      }
   }
   return cv.off;
 }
@@ -265,13 +289,34 @@ void enq_stage(wl_sim* s, int stage, cudaStream_t st) {
 ResArgs res_args(wl_sim* s, int l, int mode) {
   ResArgs a{};
   const LevelBuf& L = s->lev[l];
-  for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
+  for (int c = 0; c < 3; ++c) a.L[c] = L.Lk[c];
   a.x = L.x;
   a.z = L.z;
   a.zc = (l + 1 < s->nlev) ? s->lev[l + 1].z : nullptr;
   a.g = L.g;
-  if (l + 1 < s->nlev)
+  a.ztype = L.st;
+  a.zctype = ST_F32;
+  a.zcmul = 1.f;
+  if (l + 1 < s->nlev) {
     for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
+    if (l == 0 && s->lev[1].z32) {
+      a.zc = s->lev[1].z32;  // the fine level restricts into level 1's FP32 staging field
+    } else {
+      a.zctype = s->lev[l + 1].st;
+      a.zcmul = s->lev[l + 1].zs / L.zs;
+    }
+  }
+  if (L.z32) {
+    // level 1's pass reads the FP32 restricted residual, stores its 16-bit copy and
+    // restricts further, both with the scale 2^cs_used chosen from the fine residual
+    a.z = L.z32;
+    a.ztype = ST_F32;
+    a.zconv = L.z;
+    a.zconvtype = L.st;
+    a.zconvmul = L.zs;
+    a.zcmul = (l + 1 < s->nlev) ? s->lev[l + 1].zs : 1.f;
+    a.apply_cs = 1;
+  }
   a.inv_w = 1.f;
   a.st = s->ds;
   a.mode = mode;
@@ -302,8 +347,12 @@ void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) 
     t.rout = s->rf;
     t.zc = (s->nlev > 1) ? s->lev[1].z : nullptr;
     t.g = L.g;
-    if (s->nlev > 1)
+    t.zctype = ST_F32;
+    t.zcmul = 1.f;
+    if (s->nlev > 1) {
       for (int d = 0; d < 3; ++d) t.cn[d] = s->lev[1].g.n[d];
+      if (s->lev[1].z32) t.zc = s->lev[1].z32;  // FP32 staging of a 16-bit level 1
+    }
     const int tz = sweep_planes_per_block(L.g);
     t.tz = tz + (tz & 1);
     t.inv_w = 1.f / w;
@@ -338,10 +387,15 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   const int P = s->o.post;
   const bool refine = (l == 0 && s->ph);
   SweepArgs a{};
-  for (int c = 0; c < 3; ++c) a.L[c] = L.L[c];
+  for (int c = 0; c < 3; ++c) a.L[c] = L.Lk[c];
   a.z = refine ? s->rf : L.z;
   a.g = L.g;
   for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
+  a.stype = L.st;
+  a.xctype = s->lev[l + 1].st;
+  a.zmul = 1.f / L.zs;
+  // the coarse levels' values carry the factor 2^cs_used; the fine level removes it
+  if (l == 0 && s->lev[1].z32) a.cs = s->ds;
   a.tz = sweep_planes_per_block(L.g);
   float* bufs[2] = {L.x, L.x2};
   const CUtensorMap* bmaps[2] = {&L.mx, &L.mx2};
@@ -365,6 +419,8 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       SweepTmaArgs t{};
       t.has_x = in >= 0;
       t.xc = a.xc;
+      t.xctype = a.xctype;
+      t.xc_cs = a.cs != nullptr;
       t.x_out = a.x_out;
       t.ph = a.ph;
       t.pl = a.pl;
@@ -382,7 +438,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
     in = out;
     out ^= 1;
   }
-  if (!refine && in != 0) cudaMemcpyAsync(L.x, bufs[in], sizeof(float) * L.g.nc, cudaMemcpyDeviceToDevice, st);
+  if (!refine && in != 0) cudaMemcpyAsync(L.x, bufs[in], esize(L.st) * L.g.nc, cudaMemcpyDeviceToDevice, st);
 }
 
 // coarsest solve of level l: x = A^+ z (dense FP64 pseudo-inverse when small, FP64 CG otherwise)
@@ -582,13 +638,18 @@ void wl_default_opts(wl_opts* o) {
   o->stream = nullptr;
   o->workspace = nullptr;
   o->workspace_bytes = 0;
+  o->coarse_precision = 0;
 }
 
 size_t wl_workspace_bytes(const int* dims, int ndim, const wl_opts* opts) {
   if (!dims || (ndim != 2 && ndim != 3)) return 0;
   for (int d = 0; d < ndim; ++d)
     if (dims[d] < 2) return 0;
-  return layout(nullptr, ndim, dims, opts ? opts->precision : 0, nullptr);
+  wl_opts o;
+  wl_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.coarse_precision < 0 || o.coarse_precision > 2) return 0;
+  return layout(nullptr, ndim, dims, o.precision, o.coarse_precision, nullptr);
 }
 
 int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_body* body, const wl_opts* opts,
@@ -605,7 +666,7 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   wl_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_vcycles < 0 || o.post < 1 || !(o.eps > 0.0) || !(o.dt_cap > 0.0) ||
-      o.precision < 0 || o.precision > 1)
+      o.precision < 0 || o.precision > 1 || o.coarse_precision < 0 || o.coarse_precision > 2)
     return WL_EINVAL;
   if (body && (body->kind < 0 || body->kind > 2 || (body->kind == 2 && ndim != 3))) return WL_EINVAL;
   wl_sim* s = new wl_sim();
@@ -628,7 +689,7 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   s->body.r1 = body ? body->radius : 0.0;
   s->body.r2 = body ? body->radius2 : 0.0;
   s->body.eps = o.eps;
-  const size_t need = layout(nullptr, ndim, dims, o.precision, nullptr);
+  const size_t need = layout(nullptr, ndim, dims, o.precision, o.coarse_precision, nullptr);
   if (o.workspace) {
     if (o.workspace_bytes < need || ((uintptr_t)o.workspace & 255u)) {
       delete s;
@@ -647,13 +708,17 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
     s->own_ws = true;
   }
   s->ws_bytes = need;
-  layout(s, ndim, dims, o.precision, s->ws);
+  layout(s, ndim, dims, o.precision, o.coarse_precision, s->ws);
   int rc = WL_OK;
   if (cudaMallocHost(&s->hs, sizeof(DevState)) != cudaSuccess) rc = fail(s, WL_ENOMEM, "pinned host state");
   if (!rc) rc = cuda_check(s, cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking), "capture stream");
   if (!rc && !std::getenv("WL_NO_TMA")) {  // tensor maps for the staged sweep
     for (int l = 0; l < s->nlev; ++l) {
       LevelBuf& L = s->lev[l];
+      if (L.st != ST_F32) {  // 16-bit levels use the table sweep
+        L.tma = false;
+        continue;
+      }
       // sweep boxes: iterate 12 rows, coefficients 10 (L1: 11); residual boxes: 8 rows
       // (faces of y: 9)
       bool ok = make_field_map(&L.mx, L.x, L.g, ndim) && make_field_map(&L.mx2, L.x2, L.g, ndim) &&
@@ -683,8 +748,12 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       launch_coarsen(ndim, s->lev[l - 1].g, Lf, s->lev[l].g, s->lev[l].L, s->st);
     }
     for (int l = 0; l < s->nlev; ++l) {
-      cudaMemsetAsync(s->lev[l].x, 0, sizeof(float) * s->lev[l].g.nc, s->st);
-      cudaMemsetAsync(s->lev[l].z, 0, sizeof(float) * s->lev[l].g.nc, s->st);
+      const LevelBuf& L = s->lev[l];
+      if (L.st != ST_F32)
+        for (int c = 0; c < ndim; ++c) launch_to_storage(L.L[c], L.Lk[c], L.st, L.g.nc, s->st);
+      cudaMemsetAsync(L.x, 0, esize(L.st) * L.g.nc, s->st);
+      cudaMemsetAsync(L.z, 0, esize(L.st) * L.g.nc, s->st);
+      if (L.z32) cudaMemsetAsync(L.z32, 0, sizeof(float) * L.g.nc, s->st);
     }
     if (s->rf) cudaMemsetAsync(s->rf, 0, sizeof(float) * s->g.nc, s->st);
     if (s->G) {

@@ -1,11 +1,14 @@
 // Device-side building blocks shared by the kernels of libwl.so.
 //
-// Storage: every field is float32, interior cells only, x fastest.  There are no
+// Storage: every field is float32 (the coarse multigrid levels optionally 16-bit),
+// interior cells only, x fastest.  There are no
 // ghost cells in memory: the domain boundary conditions (BC!, Table 2) are applied
 // on the fly by mapping an out-of-range index to the value the BC defines
 // ("virtual ghosts").  This removes the separate BC kernel and its traffic.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace wl {
@@ -18,6 +21,46 @@ struct Grid {
 };
 
 __device__ __forceinline__ bool is_per(const Grid& g, int d) { return (g.per >> d) & 1u; }
+
+// Storage types of the coarse multigrid levels' fields (wl_opts.coarse_precision):
+// values are stored in 16 bits and every operation on them runs in FP32.
+enum { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };
+
+__device__ __forceinline__ float ldf(const float* p, long long i) { return __ldg(p + i); }
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p, long long i) { return __bfloat162float(__ldg(p + i)); }
+__device__ __forceinline__ float ldf(const __half* p, long long i) { return __half2float(__ldg(p + i)); }
+template <typename T>
+__device__ __forceinline__ T from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+// Two adjacent values (index i even, so the pair is 4/8-byte aligned) stored at once.
+__device__ __forceinline__ void st_pair(float* p, long long i, float a, float b) {
+  *reinterpret_cast<float2*>(p + i) = make_float2(a, b);
+}
+__device__ __forceinline__ void st_pair(__nv_bfloat16* p, long long i, float a, float b) {
+  *reinterpret_cast<__nv_bfloat162*>(p + i) = __floats2bfloat162_rn(a, b);
+}
+__device__ __forceinline__ void st_pair(__half* p, long long i, float a, float b) {
+  *reinterpret_cast<__half2*>(p + i) = __floats2half2_rn(a, b);
+}
+// Load / store by a run-time storage type (ST_*), for fields touched once per cell.
+__device__ __forceinline__ float ld_st(const void* p, int type, long long i) {
+  if (type == ST_BF16) return ldf(static_cast<const __nv_bfloat16*>(p), i);
+  if (type == ST_F16) return ldf(static_cast<const __half*>(p), i);
+  return ldf(static_cast<const float*>(p), i);
+}
+__device__ __forceinline__ void st_st(void* p, int type, long long i, float v) {
+  if (type == ST_BF16)
+    static_cast<__nv_bfloat16*>(p)[i] = __float2bfloat16_rn(v);
+  else if (type == ST_F16)
+    static_cast<__half*>(p)[i] = __float2half_rn(v);
+  else
+    static_cast<float*>(p)[i] = v;
+}
 
 __device__ __forceinline__ long long cell_index(const Grid& g, int i, int j, int k) {
   return (long long)i + (long long)g.n[0] * ((long long)j + (long long)g.n[1] * k);
@@ -148,6 +191,9 @@ struct DevState {
   float worst_res;
   int status;             // bit 0: non-finite seen; bit 1: max_vcycles hit
   int proj_index;         // 0 / 1: which projection of the step is running
+  int cs_used;            // 16-bit coarse levels: their values carry the factor 2^cs_used, set
+                          // from the max-norm of the residual they correct (so that FP16's range
+                          // holds the correction whatever the residual's size)
 };
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned* addr, float v) {

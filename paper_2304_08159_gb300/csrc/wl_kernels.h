@@ -36,17 +36,31 @@ struct ResArgs {
   float* zc;           // restricted residual for the next level (may be null)
   Grid g;
   int cn[3];           // next level's dims
+  int ztype;           // storage type (ST_*) of z in RES_RESTRICT mode (else ST_F32)
+  int zctype;          // storage type of zc
+  float zcmul;         // zc = zcmul * (sum of the 2^D children): the levels' scale ratio
+  float* zconv;        // RES_RESTRICT: if set, also store zconvmul * z here (type zconvtype)
+  int zconvtype;
+  float zconvmul;
+  int apply_cs;        // multiply zc and zconv by 2^(st->cs_used) as well
   float inv_w;         // divergence modes: z = div u * inv_w / dt
   DevState* st;        // dt and the running max |residual|
   int mode;
 };
 
+// A 16-bit level (stype != ST_F32) keeps x_in, z, L and x_out in that type (the
+// pointers are then reinterpreted) and stores its right-hand side scaled: the value
+// used is zmul * z.
 struct SweepArgs {
   const float* x_in;   // current iterate, or null for zero
   const float* xc;     // coarse correction added by piecewise-constant prolongation, or null
   const float* z;
   const float* L[3];
   float* x_out;
+  int stype;           // storage type (ST_*) of x_in, z, L, x_out
+  int xctype;          // storage type of xc
+  float zmul;
+  const DevState* cs;  // if set, xc carries the factor 2^(cs->cs_used), removed on reading
   float* ph;           // if set: add the swept values into the double-float field ph + pl
   float* pl;           //   instead of writing x_out
   Grid g;
@@ -63,6 +77,8 @@ struct SweepMaps {
 struct SweepTmaArgs {
   int has_x;           // stage the iterate (else it starts from zero)
   const float* xc;     // coarse correction to prolong into it, or null
+  int xctype;          // storage type (ST_*) of xc
+  int xc_cs;           // xc carries the factor 2^(st->cs_used), removed on reading
   float* x_out;
   float* ph;           // if set: fold the result into ph + pl instead of writing x_out
   float* pl;
@@ -122,6 +138,8 @@ struct ResidTmaArgs {
   float* z;            // divergence mode: right-hand side out
   float* rout;         // residual out (or null)
   float* zc;           // restricted residual (or null)
+  int zctype;          // storage type (ST_*) of zc
+  float zcmul;         // zc = zcmul * (sum of the 2^D children)
   Grid g;
   int cn[3];
   int tz;              // planes per block (even)
@@ -165,6 +183,8 @@ int launch_apply_pinv(const DenseArgs& a, cudaStream_t s);
 int launch_df_round(const float* ph, const float* pl, float* out, long long n, cudaStream_t s);
 // (ph, pl) += e (double-float accumulate)
 int launch_df_add(float* ph, float* pl, const float* e, long long n, cudaStream_t s);
+// FP32 -> storage type (ST_*) copy of n values (coarse-level face coefficients)
+int launch_to_storage(const float* in, void* out, int type, long long n, cudaStream_t s);
 int launch_sync_dt(DevState* st, cudaStream_t s);
 
 }  // namespace wl

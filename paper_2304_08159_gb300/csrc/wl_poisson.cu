@@ -14,6 +14,8 @@
 // FP64 conjugate gradients, piecewise-constant prolongation fused into the first
 // smoothing sweep, red-black Gauss-Seidel sweeps (red: i+j+k even, first).  Cells
 // whose row is zero (all faces blocked by the body) carry x = 0.
+#include <type_traits>
+
 #include "wl_dev.cuh"
 #include "wl_kernels.h"
 
@@ -59,7 +61,7 @@ __device__ __forceinline__ long long nb_dn(const Grid& g, int c, int Ic, long lo
 constexpr int RS_ZP = 2;
 
 template <int D>
-__device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, int k, unsigned& mbits) {
+__device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, int k, unsigned& mbits, float zvm) {
   const Grid& g = a.g;
   const long long q = cell_index(g, i, j, k);
   const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
@@ -78,9 +80,12 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
     a.z[q] = z;
     if (a.mode == RES_DIV_ONLY) return 0.f;
   } else {
-    z = a.z[q];
+    z = ld_st(a.z, a.ztype, q);
   }
-  if (a.mode == RES_RESTRICT) return z;
+  if (a.mode == RES_RESTRICT) {
+    if (a.zconv) st_st(a.zconv, a.zconvtype, q, z * zvm);
+    return z;
+  }
   float r;
   if (a.ph) {
     // r = z - sum_f L_f (p_nb - p_0) with p = ph + pl in double-float arithmetic
@@ -131,6 +136,9 @@ template <int D>
 __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   __shared__ float s_r[8][32];
   __shared__ unsigned s_m[8];
+  // the coarse levels' scale folded into the restriction's multipliers
+  const float S = a.apply_cs ? ldexpf(1.f, a.st->cs_used) : 1.f;
+  const float zcm = a.zcmul * S, zvm = a.zconvmul * S;
   const Grid& g = a.g;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int i = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + ty;
@@ -141,8 +149,8 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   for (int k = kb; k < ke; k += (D == 3 ? 2 : 1)) {
     float v = 0.f;
     if (inxy) {
-      v = residual_cell<D>(a, i, j, k, mbits);
-      if (D == 3 && k + 1 < ke) v += residual_cell<D>(a, i, j, k + 1, mbits);
+      v = residual_cell<D>(a, i, j, k, mbits, zvm);
+      if (D == 3 && k + 1 < ke) v += residual_cell<D>(a, i, j, k + 1, mbits, zvm);
     }
     if (a.zc) {
       v += __shfl_xor_sync(0xffffffffu, v, 1);
@@ -153,7 +161,8 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
         const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
         const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 4 + cy, K = (D == 3) ? (k >> 1) : 0;
         if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
-          a.zc[(long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K)] = sum;
+          st_st(a.zc, a.zctype, (long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K),
+                sum * zcm);
       }
       __syncthreads();
     }
@@ -201,8 +210,14 @@ struct RelaxIn {
 // Offsets of the tile footprint's columns / rows / planes after the boundary mapping
 // (periodic wrap; -1 outside a non-periodic side), so that every load of the march
 // is a table read and two adds whether or not the tile touches the boundary.
-template <int D>
+template <int D, typename T>
 __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+  const T* __restrict__ xin = reinterpret_cast<const T*>(a.x_in);
+  const T* __restrict__ zf = reinterpret_cast<const T*>(a.z);
+  const T* __restrict__ Lf[3] = {reinterpret_cast<const T*>(a.L[0]), reinterpret_cast<const T*>(a.L[1]),
+                                 reinterpret_cast<const T*>(a.L[2])};
+  T* xout = reinterpret_cast<T*>(a.x_out);
+  const float xcm = a.cs ? ldexpf(1.f, -a.cs->cs_used) : 1.f;  // removes the coarse levels' scale
   constexpr int NP = (D == 3) ? 4 : 1;
   __shared__ float s_x[NP][SW_HY][SW_HX];
   __shared__ int s_xo[SW_HX], s_yo[SW_HY], s_cxo[SW_HX], s_cyo[SW_HY];
@@ -249,8 +264,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     const int xo = s_xo[col], yo = s_yo[row];
     float v = 0.f;
     if (xo >= 0 && yo >= 0 && zo >= 0) {
-      if (a.x_in) v = __ldg(a.x_in + (xo + yo + zo));
-      if (a.xc) v += __ldg(a.xc + (s_cxo[col] + s_cyo[row] + czo));
+      if (xin) v = ldf(xin, xo + yo + zo);
+      if (a.xc) v += xcm * ld_st(a.xc, a.xctype, s_cxo[col] + s_cyo[row] + czo);
     }
     return v;
   };
@@ -261,15 +276,16 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     c.ok = xo >= 0 && yo >= 0 && zo >= 0;
     if (!c.ok) return;
     const int q = xo + yo + zo;
-    c.z = __ldg(a.z + q);
+    c.z = ldf(zf, q);
+    if constexpr (!std::is_same<T, float>::value) c.z *= a.zmul;
     const int xu = s_xo[col + 1], yu = s_yo[row + 1];
-    c.Ll[0] = __ldg(a.L[0] + q);
-    c.Lu[0] = xu >= 0 ? __ldg(a.L[0] + (xu + yo + zo)) : 0.f;
-    c.Ll[1] = __ldg(a.L[1] + q);
-    c.Lu[1] = yu >= 0 ? __ldg(a.L[1] + (xo + yu + zo)) : 0.f;
+    c.Ll[0] = ldf(Lf[0], q);
+    c.Lu[0] = xu >= 0 ? ldf(Lf[0], xu + yo + zo) : 0.f;
+    c.Ll[1] = ldf(Lf[1], q);
+    c.Lu[1] = yu >= 0 ? ldf(Lf[1], xo + yu + zo) : 0.f;
     if (D == 3) {
-      c.Ll[2] = __ldg(a.L[2] + q);
-      c.Lu[2] = zou >= 0 ? __ldg(a.L[2] + (xo + yo + zou)) : 0.f;
+      c.Ll[2] = ldf(Lf[2], q);
+      c.Lu[2] = zou >= 0 ? ldf(Lf[2], xo + yo + zou) : 0.f;
     }
   };
   // Gauss-Seidel value from the shared neighbours (0 for a cell with no equation)
@@ -386,7 +402,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
       const int q = gi + n0 * gj + zk;
       const float v0 = P ? vb : vr, v1 = P ? vr : vb;
       const bool two = gi + 1 < g.n[0];
-      if (a.ph) {
+      if (std::is_same<T, float>::value && a.ph) {
         // last sweep of a correction cycle: fold the correction into ph + pl
         const float vv[2] = {v0, v1};
 #pragma unroll
@@ -400,10 +416,10 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
           a.pl[q + t] = nl;
         }
       } else if (two && (n0 & 1) == 0) {
-        reinterpret_cast<float2*>(a.x_out + q)[0] = make_float2(v0, v1);
+        st_pair(xout, q, v0, v1);
       } else {
-        a.x_out[q] = v0;
-        if (two) a.x_out[q + 1] = v1;
+        xout[q] = from_f<T>(v0);
+        if (two) xout[q + 1] = from_f<T>(v1);
       }
     }
     __syncthreads();
@@ -439,14 +455,24 @@ int sweep_planes_per_block(const Grid& g) {
   return best;
 }
 
+template <int D>
+void launch_sweep_d(const SweepArgs& a, dim3 grd, cudaStream_t s) {
+  if (a.stype == ST_BF16)
+    k_sweep<D, __nv_bfloat16><<<grd, 256, 0, s>>>(a);
+  else if (a.stype == ST_F16)
+    k_sweep<D, __half><<<grd, 256, 0, s>>>(a);
+  else
+    k_sweep<D, float><<<grd, 256, 0, s>>>(a);
+}
+
 int launch_sweep(int D, const SweepArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
   if (D == 3) {
     dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, (g.n[2] + a.tz - 1) / a.tz);
-    k_sweep<3><<<grd, 256, 0, s>>>(a);
+    launch_sweep_d<3>(a, grd, s);
   } else {
     dim3 grd((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, 1);
-    k_sweep<2><<<grd, 256, 0, s>>>(a);
+    launch_sweep_d<2>(a, grd, s);
   }
   return 0;
 }
@@ -816,6 +842,10 @@ __global__ void k_decide(DevState* st, cudaGraphConditionalHandle h, int use_han
                          double tol, int maxit) {
   const float nrm = __uint_as_float(st->norm_bits);
   st->norm_bits = 0u;
+  // scale of the 16-bit coarse levels for the cycle that corrects this residual: its
+  // max-norm maps to [2^-6, 2^-5), which leaves FP16 room for the corrections (a smooth
+  // error is at most ~(n/pi)^2 times its residual) and keeps the residual normal
+  if (nrm > 0.f && isfinite(nrm)) st->cs_used = min(max(-ilogbf(nrm) - 6, -100), 100);
   const float res = (float)((double)nrm * (double)w * st->dt);
   if (first) {
     st->iter = 0;
@@ -1309,6 +1339,16 @@ __global__ void k_df_add(float* ph, float* pl, const float* e, long long n) {
 
 int launch_df_add(float* ph, float* pl, const float* e, long long n, cudaStream_t s) {
   k_df_add<<<(int)((n + 255) / 256), 256, 0, s>>>(ph, pl, e, n);
+  return 0;
+}
+
+__global__ void k_to_storage(const float* in, void* out, int type, long long n) {
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q < n) st_st(out, type, q, in[q]);
+}
+
+int launch_to_storage(const float* in, void* out, int type, long long n, cudaStream_t s) {
+  k_to_storage<<<(int)((n + 255) / 256), 256, 0, s>>>(in, out, type, n);
   return 0;
 }
 

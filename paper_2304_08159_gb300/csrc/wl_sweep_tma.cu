@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
     ld_c(b + 1, bbar(b));
   };
   // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p
+  const float xcm = a.xc_cs ? ldexpf(1.f, -a.st->cs_used) : 1.f;  // removes the coarse levels' scale
   auto fix_x = [&](int p) {
     const int Xp = Xs(xslot(p));
     for (int e = tid; e < BOX; e += SW_NT) {
@@ -179,8 +180,9 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
       const int gi = i0 - 4 + col, gj = j0 - 2 + row;
       float v = a.has_x ? smf[Xp + e] : 0.f;
       if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && p >= 0 && p < g.n[2])
-        v += __ldg(a.xc + (long long)(gi >> 1) +
-                   (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
+        v += xcm * ld_st(a.xc, a.xctype,
+                         (long long)(gi >> 1) +
+                             (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
       smf[Xp + e] = v;
     }
   };
@@ -605,7 +607,8 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
         const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
         const int I = (i0 >> 1) + cx, J = (j0 >> 1) + cy, K = k >> 1;
         if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
-          a.zc[(long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K)] = sum;
+          st_st(a.zc, a.zctype, (long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K),
+                sum * a.zcmul);
       }
     }
     __syncthreads();

@@ -36,6 +36,12 @@ WL_BODY_NONE = 0
 WL_BODY_SPHERE = 1
 WL_BODY_TORUS = 2
 
+WL_COARSE_FP32 = 0
+WL_COARSE_BF16 = 1
+WL_COARSE_FP16 = 2
+# storage of the multigrid levels between the fine and the coarsest one, by name
+COARSE_PRECISION = {"fp32": WL_COARSE_FP32, "bf16": WL_COARSE_BF16, "fp16": WL_COARSE_FP16}
+
 # every symbol include/wl.h declares
 EXPORTS = (
     "wl_default_opts", "wl_workspace_bytes", "wl_create", "wl_set_ic", "wl_step", "wl_stage",
@@ -57,7 +63,7 @@ class WlOpts(ctypes.Structure):
                 ("eps", ctypes.c_double), ("dt_cap", ctypes.c_double), ("dt_fixed", ctypes.c_double),
                 ("periodic_mask", ctypes.c_uint), ("advect", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("coarse_precision", ctypes.c_int)]
 
 
 class WLError(RuntimeError):
@@ -264,7 +270,8 @@ class Sim:
     Every method is a direct call of the C entry point of the same name."""
 
     def __init__(self, dims, nu, U, body=None, periodic=0, tol=1e-6, max_vcycles=32, post=4, eps=1.0,
-                 dt_cap=10.0, dt_fixed=0.0, advect=True, precision=1, use_graph=True, device=None):
+                 dt_cap=10.0, dt_fixed=0.0, advect=True, precision=1, use_graph=True, device=None,
+                 coarse_precision=0):
         import torch
 
         self.torch = torch
@@ -277,6 +284,7 @@ class Sim:
         o.tol, o.max_vcycles, o.post, o.eps = float(tol), int(max_vcycles), int(post), float(eps)
         o.dt_cap, o.dt_fixed, o.periodic_mask = float(dt_cap), float(dt_fixed), int(periodic)
         o.advect, o.precision, o.use_graph = int(bool(advect)), int(precision), int(bool(use_graph))
+        o.coarse_precision = COARSE_PRECISION.get(coarse_precision, coarse_precision)
         with torch.cuda.device(self.device):
             o.stream = torch.cuda.current_stream().cuda_stream
             nbytes = wl_workspace_bytes(self.dims, o)

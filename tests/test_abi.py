@@ -44,11 +44,23 @@ def test_workspace_bytes_host_only(lib):
     from paper_2304_08159_gb300 import wl
 
     small = wl.wl_workspace_bytes((128, 64))
-    big = wl.wl_workspace_bytes((512, 256, 256))
+    o = wl.wl_default_opts()
+    o.precision = 0
+    big = wl.wl_workspace_bytes((512, 256, 256), o)
     assert small > 0 and big > 0
     # 3 velocity buffers + (3 coefficients + z, x, x2) on the fine level, + about 1/7 for coarse levels
     nc = 512 * 256 * 256
     assert 4 * nc * (9 + 6) <= big <= 4 * nc * (9 + 6 * 8 / 7) + (1 << 20)
+    # NULL options mean the defaults: the double-float pressure adds ph, pl and the residual
+    assert wl.wl_workspace_bytes((512, 256, 256)) == wl.wl_workspace_bytes((512, 256, 256), wl.wl_default_opts())
+    assert wl.wl_workspace_bytes((512, 256, 256)) - big == 3 * 4 * nc
+    # 16-bit coarse levels add 16-bit copies of their D coefficient fields and hold z, x, x2
+    # in 2 bytes instead of 4 (in 3-D the two cancel exactly); level 1 adds an FP32 staging
+    # field for the restricted fine residual
+    o.coarse_precision = wl.WL_COARSE_BF16
+    assert wl.wl_workspace_bytes((512, 256, 256), o) == big + 4 * nc // 8
+    o.coarse_precision = 3
+    assert wl.wl_workspace_bytes((512, 256, 256), o) == 0
     assert wl.wl_workspace_bytes((1, 64)) == 0
     assert wl.wl_workspace_bytes((8,)) == 0
 
