@@ -89,6 +89,12 @@ def _load():
             "or_face_value": (_D, [_D, _D, _D]),
             "or_psi": (_D, [_D]),
             "or_sdf": (_D, [_P, _DP, _DP]),
+            "or_convdiff_adjoint": (None, [_P, _DP, _DP, _DP]),
+            "or_stage_adjoint": (None, [_P, _I, _D, _DP, _DP, _DP, _DP, _DP, _DP, _DP]),
+            "or_project_adjoint": (None, [_P, _DP, _D, _D, _D, _DP, _DP, _DP, _DP]),
+            "or_force_adjoint": (None, [_P, _DP, _DP, _DP, _DP, _DP]),
+            "or_moments_adjoint": (None, [_P, _DP, _DP, _DP, _DP]),
+            "or_rollout_grad": (_I, [_P, _I, _D, _D, _DP, _DP, _DP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -317,3 +323,62 @@ class Oracle:
 
     def kinetic_energy(self) -> float:
         return self.lib.or_kinetic_energy(self.h)
+
+    # ---- reverse-mode derivative (adjoint) of the step at fixed dt; theta = (R, c_0, ..)
+    def _vec(self, a, blocks):
+        a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+        assert a.size == blocks * self.ncell
+        return a
+
+    def convdiff_adjoint(self, u, rbar):
+        """(d convdiff/du at u)^T rbar."""
+        out = np.zeros(self.D * self.ncell)
+        self.lib.or_convdiff_adjoint(self.h, _dp(self._vec(u, self.D)), _dp(self._vec(rbar, self.D)), _dp(out))
+        return out.reshape((self.D,) + self.shape)
+
+    def stage_adjoint(self, stage, dt, u0, u1, outbar):
+        """Transpose of bdim_stage: returns (u0bar, u1bar, mu0bar, mu1bar[D*D])."""
+        D, n = self.D, self.ncell
+        u0b, u1b, m0b, m1b = (np.zeros(D * n), np.zeros(D * n), np.zeros(D * n), np.zeros(D * D * n))
+        u1p = _dp(self._vec(u1, D)) if u1 is not None else None
+        self.lib.or_stage_adjoint(self.h, int(stage), float(dt), _dp(self._vec(u0, D)), u1p,
+                                  _dp(self._vec(outbar, D)), _dp(u0b), _dp(u1b), _dp(m0b), _dp(m1b))
+        sh = (D,) + self.shape
+        return u0b.reshape(sh), u1b.reshape(sh), m0b.reshape(sh), m1b.reshape((D * D,) + self.shape)
+
+    def project_adjoint(self, v, w, dt, ubar, pbar, tol=1e-12):
+        """Transpose of project! of v (weight w) for cotangents of u and p: (vbar, Lbar)."""
+        D, n = self.D, self.ncell
+        vb, Lb = np.zeros(D * n), np.zeros(D * n)
+        self.lib.or_project_adjoint(self.h, _dp(self._vec(v, D)), float(w), float(dt), float(tol),
+                                    _dp(self._vec(ubar, D)), _dp(self._vec(pbar, 1)), _dp(vb), _dp(Lb))
+        sh = (D,) + self.shape
+        return vb.reshape(sh), Lb.reshape(sh)
+
+    def force_adjoint(self, p, Fbar):
+        """Force of p and its adjoint: (F, pbar, theta-cotangent of the force weights)."""
+        F, pb, tb = np.zeros(3), np.zeros(self.ncell), np.zeros(4)
+        fb = np.zeros(3)
+        fb[: self.D] = Fbar
+        self.lib.or_force_adjoint(self.h, _dp(self._vec(p, 1)), _dp(fb), _dp(F), _dp(pb), _dp(tb))
+        return F[: self.D], pb.reshape(self.shape), tb[: self.D + 1]
+
+    def moments_adjoint(self, mu0bar, Lbar, mu1bar):
+        tb = np.zeros(4)
+        D = self.D
+        self.lib.or_moments_adjoint(self.h, _dp(self._vec(mu0bar, D)), _dp(self._vec(Lbar, D)),
+                                    _dp(self._vec(mu1bar, D * D)), _dp(tb))
+        return tb[: D + 1]
+
+    def rollout_grad(self, nsteps, dt, gF, tol=1e-12):
+        """nsteps steps at fixed dt from the current state (which advances); returns the
+        forces after each step (nsteps x D) and dJ/dtheta for J = sum_n gF[n] . F_n,
+        theta = (R, c_0, .., c_{D-1}) of the circle/sphere."""
+        D = self.D
+        g = np.ascontiguousarray(gF, dtype=np.float64).reshape(-1)
+        assert g.size == nsteps * D
+        F, tb = np.zeros(nsteps * D), np.zeros(4)
+        rc = self.lib.or_rollout_grad(self.h, int(nsteps), float(dt), float(tol), _dp(g), _dp(F), _dp(tb))
+        if rc != 0:
+            raise ValueError("rollout_grad needs a circle/sphere body, nsteps >= 1 and dt > 0")
+        return F.reshape(nsteps, D), tb[: D + 1]

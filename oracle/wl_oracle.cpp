@@ -706,6 +706,404 @@ double cfl(const OSim& s) {
   return std::min(s.dt_cap, 1.0 / (m + 2.0 * s.D * s.nu));
 }
 
+// ===========================================================================
+// Reverse-mode derivative (adjoint) of the time step at a fixed dt with respect to the
+// circle/sphere parameters theta = (R, c_0, .., c_{D-1}) (the differentiable-solver
+// use of the method, Section 1).  Every routine is the transpose of the forward routine
+// it names, written out from that routine's arithmetic.  Where the forward is not
+// differentiable (the limiter's switch points, the upwind switch at a = 0) the
+// derivative of the branch the forward takes is used.  A projection is differentiated as
+// the exact projection (A x = div u solved exactly); the forward solves it to a tight
+// tolerance.  dt is held fixed: the CFL rule is a maximum over the field and is not
+// differentiated.
+
+// Derivative of face_value(uu, cc, dd) with respect to (uu, cc, dd).
+void face_value_grad(double uu, double cc, double dd, double* g) {
+  g[0] = 0.0;  // phi = cc unless the limiter is active
+  g[1] = 1.0;
+  g[2] = 0.0;
+  if (dd == cc) return;
+  const double r = (cc - uu) / (dd - cc);
+  const double a = 2.0 * r, b = (2.0 + r) / 3.0;
+  const double m = std::min(std::min(a, b), 2.0);
+  if (m <= 0.0) return;  // psi = 0
+  if (m == a) {          // psi = 2r: phi = 2 cc - uu
+    g[0] = -1.0;
+    g[1] = 2.0;
+  } else if (m == b) {   // psi = (2 + r)/3: phi = (5 cc + 2 dd - uu)/6
+    g[0] = -1.0 / 6.0;
+    g[1] = 5.0 / 6.0;
+    g[2] = 2.0 / 6.0;
+  } else {               // psi = 2: phi = dd
+    g[1] = 0.0;
+    g[2] = 1.0;
+  }
+}
+
+// Transpose of flux(): ubar (padded) += Fbar * dF/du at the faces flux() reads.
+void flux_adjoint(const OSim& s, const vec* u, int c, int j, const int* I, double Fbar, vec* ubar) {
+  auto pos = [&](int dj, int dc) {
+    int J[3] = {I[0], I[1], I[2]};
+    J[j] += dj;
+    J[c] += dc;
+    return pidx(s, J);
+  };
+  ubar[c][pos(0, 0)] -= s.nu * Fbar;
+  ubar[c][pos(-1, 0)] += s.nu * Fbar;
+  if (!s.advect) return;
+  const double a = 0.5 * (u[j][pos(0, 0)] + u[j][pos(0, -1)]);
+  long q[3];
+  if (a > 0.0) {
+    q[0] = pos(-2, 0);
+    q[1] = pos(-1, 0);
+    q[2] = pos(0, 0);
+  } else {
+    q[0] = pos(1, 0);
+    q[1] = pos(0, 0);
+    q[2] = pos(-1, 0);
+  }
+  const double phi = face_value(u[c][q[0]], u[c][q[1]], u[c][q[2]]);
+  double gr[3];
+  face_value_grad(u[c][q[0]], u[c][q[1]], u[c][q[2]], gr);
+  ubar[j][pos(0, 0)] += 0.5 * phi * Fbar;
+  ubar[j][pos(0, -1)] += 0.5 * phi * Fbar;
+  for (int t = 0; t < 3; ++t) ubar[c][q[t]] += a * gr[t] * Fbar;
+}
+
+// Transpose of apply_bc(): the cotangent of every ghost or boundary face moves to the
+// face it was copied from (periodic wrap, tangential zero gradient) or is dropped (a
+// prescribed normal velocity), direction by direction in the reverse order.
+void apply_bc_adjoint(const OSim& s, vec* f) {
+  for (int d = s.D - 1; d >= 0; --d) {
+    const int lo[3] = {-s.g[0], -s.g[1], -s.g[2]};
+    const int hi[3] = {s.n[0] + s.g[0], s.n[1] + s.g[1], s.n[2] + s.g[2]};
+    for (int c = 0; c < s.D; ++c) {
+      vec& a = f[c];
+      for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+          for (int i = lo[0]; i < hi[0]; ++i) {
+            int I[3] = {i, j, k};
+            int q = I[d];
+            bool ghost = (q < 0 || q >= s.n[d]);
+            bool bface = (!is_per(s, d) && c == d && q == 0);
+            if (!ghost && !bface) continue;
+            const long qi = pidx(s, I);
+            const double v = a[qi];
+            a[qi] = 0.0;
+            int J[3] = {I[0], I[1], I[2]};
+            if (is_per(s, d)) {
+              J[d] = ((q % s.n[d]) + s.n[d]) % s.n[d];
+              a[pidx(s, J)] += v;
+            } else if (c != d) {
+              J[d] = std::max(0, std::min(s.n[d] - 1, q));
+              a[pidx(s, J)] += v;
+            }
+          }
+    }
+  }
+}
+
+// Transpose of convdiff() at u (padded, BC applied): ubar (padded) += (dr/du)^T rbar
+// with rbar on interior cells; only interior entries of ubar change.
+void convdiff_adjoint(const OSim& s, const vec* u, const vec* rbar, vec* ubar) {
+  vec ub[3];
+  for (int c = 0; c < s.D; ++c) ub[c].assign(s.npad, 0.0);
+  for (int c = 0; c < s.D; ++c)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (!updated(s, c, I)) continue;
+          const double rb = rbar[c][cidx(s, i, j, k)];
+          if (rb == 0.0) continue;
+          for (int d = 0; d < s.D; ++d) {  // r_c[I] = sum_d F_cd[I] - F_cd[I + e_d]
+            int Ip[3] = {i, j, k};
+            Ip[d] += 1;
+            flux_adjoint(s, u, c, d, I, rb, ub);
+            flux_adjoint(s, u, c, d, Ip, -rb, ub);
+          }
+        }
+  apply_bc_adjoint(s, ub);
+  for (int c = 0; c < s.D; ++c)
+    for (long q = 0; q < s.npad; ++q) ubar[c][q] += ub[c][q];
+}
+
+// Transpose of bdim_stage() at (u0, u1) (padded, BC applied): given outbar (interior
+// cells), accumulate the cotangents of u0 and u1 (padded arrays, interior entries) and
+// of the BDIM moments mu0bar[c][cell], mu1bar[c][j][cell].
+void bdim_stage_adjoint(const OSim& s, int stage, double dt, const vec* u0, const vec* u1, const vec* outbar,
+                        vec* u0bar, vec* u1bar, vec* mu0bar, vec (*mu1bar)[3]) {
+  const vec* uin = (stage == 1) ? u0 : u1;
+  vec r[3], f[3], fb[3], rb[3];
+  convdiff(s, uin, r);  // recompute f as the forward does
+  for (int c = 0; c < s.D; ++c) {
+    f[c] = u0[c];
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (updated(s, c, I)) f[c][pidx(s, I)] = u0[c][pidx(s, I)] + dt * r[c][cidx(s, i, j, k)];
+        }
+  }
+  apply_bc(s, f);
+  for (int c = 0; c < s.D; ++c) fb[c].assign(s.npad, 0.0);
+  for (int c = 0; c < s.D; ++c)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (!updated(s, c, I)) continue;  // boundary faces carry the BC value
+          const long ci = cidx(s, i, j, k), pi = pidx(s, I);
+          const double ob = outbar[c][ci];
+          const double vb = (stage == 1) ? ob : 0.5 * ob;
+          if (stage == 2) u1bar[c][pi] += 0.5 * ob;
+          fb[c][pi] += s.mu0[c][ci] * vb;
+          mu0bar[c][ci] += vb * f[c][pi];
+          for (int d = 0; d < s.D; ++d) {
+            int Ip[3] = {i, j, k}, Im[3] = {i, j, k};
+            Ip[d] += 1;
+            Im[d] -= 1;
+            fb[c][pidx(s, Ip)] += 0.5 * s.mu1[c][d][ci] * vb;
+            fb[c][pidx(s, Im)] -= 0.5 * s.mu1[c][d][ci] * vb;
+            mu1bar[c][d][ci] += vb * 0.5 * (f[c][pidx(s, Ip)] - f[c][pidx(s, Im)]);
+          }
+        }
+  apply_bc_adjoint(s, fb);
+  for (int c = 0; c < s.D; ++c) {
+    rb[c].assign(s.ncell, 0.0);
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          const long pi = pidx(s, I);
+          u0bar[c][pi] += fb[c][pi];  // f = u0 + dt r
+          if (updated(s, c, I)) rb[c][cidx(s, i, j, k)] = dt * fb[c][pi];
+        }
+  }
+  convdiff_adjoint(s, uin, rb, (stage == 1) ? u0bar : u1bar);
+}
+
+// Transpose of project() at its converged solution x (x units, mean removed over the
+// active cells): given the interior cotangent ubar_out of the corrected velocity and a
+// cotangent xbar_in of x, set vbar (padded; interior entries) to the cotangent of the
+// velocity before the projection and accumulate the cotangent of the Poisson face
+// coefficients into Lbar.  With y = A^+ (xbar_in + D(L ubar)):
+//   vbar = ubar - G y,   Lbar_c[I] -= (x[I] - x[I-e_c]) (vbar_c[I]).
+void project_adjoint(const OSim& s, const vec& x, const vec* ubar_out, const vec& xbar_in, double rtol, vec* vbar,
+                     vec* Lbar) {
+  Op A = make_op(s, s.lev[0]);
+  vec dg;
+  A.diagonal(dg);
+  vec ub[3];
+  for (int c = 0; c < s.D; ++c) {
+    ub[c] = ubar_out[c];
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          if (!updated(s, c, I)) ub[c][cidx(s, i, j, k)] = 0.0;  // boundary faces: BC values
+        }
+  }
+  vec xb = xbar_in;
+  for (int c = 0; c < s.D; ++c)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          const long qm = A.nb(I, c, -1), q = cidx(s, i, j, k);
+          if (qm < 0) continue;
+          const double v = A.Llower(I, c) * ub[c][q];  // u_c[I] -= L (x[I] - x[I-e_c])
+          xb[q] -= v;
+          xb[qm] += v;
+        }
+  vec y(s.ncell, 0.0);
+  double res = 0.0;
+  pcg(A, y, xb, rtol * std::max(norm_inf(xb), 1e-300), 1000000, &res);
+  remove_mean_active(y, dg);
+  for (int c = 0; c < s.D; ++c) {
+    vbar[c].assign(s.npad, 0.0);
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) vbar[c][pidx(s, i, j, k)] = ub[c][cidx(s, i, j, k)];
+  }
+  for (int k = 0; k < s.n[2]; ++k)  // D^T y: z[I] = sum_c u_c[I + e_c] - u_c[I]
+    for (int j = 0; j < s.n[1]; ++j)
+      for (int i = 0; i < s.n[0]; ++i) {
+        const double yv = y[cidx(s, i, j, k)];
+        for (int c = 0; c < s.D; ++c) {
+          int I[3] = {i, j, k}, Ip[3] = {i, j, k};
+          Ip[c] += 1;
+          vbar[c][pidx(s, Ip)] += yv;
+          vbar[c][pidx(s, I)] -= yv;
+        }
+      }
+  apply_bc_adjoint(s, vbar);
+  for (int c = 0; c < s.D; ++c)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          int I[3] = {i, j, k};
+          const long qm = A.nb(I, c, -1), q = cidx(s, i, j, k);
+          if (qm < 0) continue;
+          Lbar[c][q] -= (x[q] - x[qm]) * vbar[c][pidx(s, I)];
+        }
+}
+
+// Derivatives of the circle/sphere distance d = |x - c| - R and normal n = (x - c)/|x - c|
+// at x with respect to theta = (R, c_0, .., c_{D-1}): dd[t], dn[j][t].
+void sdf_theta_grad(const OSim& s, const double* x, double* dd, double dn[3][4]) {
+  double rho2 = 0.0, n[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < s.D; ++d) rho2 += (x[d] - s.center[d]) * (x[d] - s.center[d]);
+  const double rho = std::sqrt(rho2);
+  for (int d = 0; d < s.D; ++d) n[d] = rho > 0.0 ? (x[d] - s.center[d]) / rho : 0.0;
+  dd[0] = -1.0;
+  for (int j = 0; j < 3; ++j) dn[j][0] = 0.0;
+  for (int k = 0; k < s.D; ++k) {
+    dd[1 + k] = -n[k];
+    for (int j = 0; j < s.D; ++j) dn[j][1 + k] = rho > 0.0 ? -((j == k ? 1.0 : 0.0) - n[j] * n[k]) / rho : 0.0;
+  }
+}
+
+// Pressure force of p (forces() of the C interface) and its adjoint: for a cotangent
+// Fbar, pbar (cells) and the theta-cotangent of the force weights n K_eps(d), added to tb.
+void force_adjoint(const OSim& s, const vec& p, const double* Fbar, double* F, vec& pbar, double* tb) {
+  Op A = make_op(s, s.lev[0]);
+  vec dg;
+  A.diagonal(dg);
+  double sum = 0.0;
+  long cnt = 0;
+  for (long q = 0; q < s.ncell; ++q)
+    if (dg[q] > 0.0) {
+      sum += p[q];
+      ++cnt;
+    }
+  const double pm = cnt ? sum / cnt : 0.0;
+  for (int d = 0; d < 3; ++d) F[d] = 0.0;
+  pbar.assign(s.ncell, 0.0);
+  double wg = 0.0;  // sum over band cells of Fbar . n K
+  for (int k = 0; k < s.n[2]; ++k)
+    for (int j = 0; j < s.n[1]; ++j)
+      for (int i = 0; i < s.n[0]; ++i) {
+        double x[3] = {i + 0.5, j + 0.5, k + 0.5}, nrm[3];
+        const double d = sdf(s, x, nrm);
+        if (std::fabs(d) >= s.eps) continue;
+        const long q = cidx(s, i, j, k);
+        const double K = (1.0 + std::cos(M_PI * d / s.eps)) / (2.0 * s.eps);
+        const double Kp = -M_PI * std::sin(M_PI * d / s.eps) / (2.0 * s.eps * s.eps);
+        const double pp = p[q] - pm;
+        double gw = 0.0;
+        for (int dd = 0; dd < s.D; ++dd) {
+          F[dd] -= pp * nrm[dd] * K;
+          gw += Fbar[dd] * nrm[dd] * K;
+        }
+        pbar[q] -= gw;
+        wg += gw;
+        double ddt[4], dn[3][4];
+        sdf_theta_grad(s, x, ddt, dn);
+        for (int t = 0; t <= s.D; ++t)
+          for (int dd = 0; dd < s.D; ++dd)
+            tb[t] -= Fbar[dd] * pp * (dn[dd][t] * K + nrm[dd] * Kp * ddt[t]);
+      }
+  for (long q = 0; q < s.ncell; ++q)  // the mean pm over active cells
+    if (dg[q] > 0.0) pbar[q] += wg / cnt;
+}
+
+// theta-cotangent of the BDIM moments and the Poisson coefficients (measure()):
+// mu0 = K0(d/eps), L = mu0 except on non-periodic boundary faces (fixed 0),
+// mu1_j = eps K1(d/eps) n_j; K0' = K, K1'(s) = -s K(s).
+void moments_adjoint(const OSim& s, const vec* mu0bar, const vec* Lbar, const vec (*mu1bar)[3], double* tb) {
+  for (int c = 0; c < s.D; ++c)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) {
+          double x[3] = {i + 0.5, j + 0.5, k + 0.5}, nrm[3];
+          x[c] -= 0.5;
+          const double d = sdf(s, x, nrm), sc = d / s.eps;
+          if (std::fabs(sc) >= 1.0) continue;
+          int I[3] = {i, j, k};
+          const long q = cidx(s, i, j, k);
+          const double K = 0.5 * (1.0 + std::cos(M_PI * sc));
+          const bool bnd = !is_per(s, c) && I[c] == 0;
+          const double g0 = mu0bar[c][q] + (bnd ? 0.0 : Lbar[c][q]);
+          double ddt[4], dn[3][4];
+          sdf_theta_grad(s, x, ddt, dn);
+          const double k1 = s.eps * K1(sc), k1p = -sc * K;
+          for (int t = 0; t <= s.D; ++t) {
+            tb[t] += g0 * K / s.eps * ddt[t];
+            for (int jj = 0; jj < s.D; ++jj) tb[t] += mu1bar[c][jj][q] * (k1p * nrm[jj] * ddt[t] + k1 * dn[jj][t]);
+          }
+        }
+}
+
+// nsteps full steps at fixed dt from the current state, then the gradient of
+// J = sum_n gF[n] . F_n (F_n the pressure force after step n) with respect to theta.
+// F receives nsteps * D forces, tb D + 1 values.  The state advances.
+void rollout_grad(OSim& s, int nsteps, double dt, double tol, const double* gF, double* F, double* tb) {
+  const int D = s.D;
+  std::vector<std::vector<vec>> U0(nsteps), UP(nsteps);
+  std::vector<vec> X1(nsteps), X2(nsteps), P2(nsteps);
+  for (int n = 0; n < nsteps; ++n) {
+    vec u0[3], u1[3];
+    for (int c = 0; c < D; ++c) u0[c] = s.u[c];
+    bdim_stage(s, 1, dt, u0, u0, u1);
+    project(s, u1, 1.0, dt, tol, 1000000, 0);
+    X1[n] = s.p;
+    for (auto& v : X1[n]) v *= dt;
+    UP[n].assign(u1, u1 + D);
+    bdim_stage(s, 2, dt, u0, u1, s.u);
+    project(s, s.u, 0.5, dt, tol, 1000000, 0);
+    X2[n] = s.p;
+    for (auto& v : X2[n]) v *= 0.5 * dt;
+    P2[n] = s.p;
+    U0[n].assign(u0, u0 + D);
+    s.t += dt;
+    s.nsteps += 1;
+  }
+  s.dt = dt;
+  for (int t = 0; t <= D; ++t) tb[t] = 0.0;
+  vec mu0bar[3], Lbar[3], mu1bar[3][3], ub[3];
+  for (int c = 0; c < D; ++c) {
+    mu0bar[c].assign(s.ncell, 0.0);
+    Lbar[c].assign(s.ncell, 0.0);
+    for (int j = 0; j < 3; ++j) mu1bar[c][j].assign(s.ncell, 0.0);
+    ub[c].assign(s.ncell, 0.0);
+  }
+  const double rtol = 1e-13;
+  for (int n = nsteps - 1; n >= 0; --n) {
+    double Fn[3];
+    vec pb;
+    force_adjoint(s, P2[n], gF + (long)n * D, Fn, pb, tb);
+    for (int d = 0; d < D; ++d) F[(long)n * D + d] = Fn[d];
+    for (auto& v : pb) v /= 0.5 * dt;  // p = x / (w dt)
+    vec v2b[3], v1b[3], u0b[3], upb[3], ubi[3];
+    project_adjoint(s, X2[n], ub, pb, rtol, v2b, Lbar);
+    for (int c = 0; c < D; ++c) {
+      u0b[c].assign(s.npad, 0.0);
+      upb[c].assign(s.npad, 0.0);
+      ubi[c].assign(s.ncell, 0.0);
+      for (int k = 0; k < s.n[2]; ++k)
+        for (int j = 0; j < s.n[1]; ++j)
+          for (int i = 0; i < s.n[0]; ++i) ubi[c][cidx(s, i, j, k)] = v2b[c][pidx(s, i, j, k)];
+    }
+    bdim_stage_adjoint(s, 2, dt, U0[n].data(), UP[n].data(), ubi, u0b, upb, mu0bar, mu1bar);
+    for (int c = 0; c < D; ++c)
+      for (int k = 0; k < s.n[2]; ++k)
+        for (int j = 0; j < s.n[1]; ++j)
+          for (int i = 0; i < s.n[0]; ++i) ubi[c][cidx(s, i, j, k)] = upb[c][pidx(s, i, j, k)];
+    project_adjoint(s, X1[n], ubi, vec(s.ncell, 0.0), rtol, v1b, Lbar);
+    for (int c = 0; c < D; ++c)
+      for (int k = 0; k < s.n[2]; ++k)
+        for (int j = 0; j < s.n[1]; ++j)
+          for (int i = 0; i < s.n[0]; ++i) ubi[c][cidx(s, i, j, k)] = v1b[c][pidx(s, i, j, k)];
+    bdim_stage_adjoint(s, 1, dt, U0[n].data(), U0[n].data(), ubi, u0b, u0b, mu0bar, mu1bar);
+    for (int c = 0; c < D; ++c)
+      for (int k = 0; k < s.n[2]; ++k)
+        for (int j = 0; j < s.n[1]; ++j)
+          for (int i = 0; i < s.n[0]; ++i) ub[c][cidx(s, i, j, k)] = u0b[c][pidx(s, i, j, k)];
+  }
+  moments_adjoint(s, mu0bar, Lbar, mu1bar, tb);
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1006,5 +1404,120 @@ double or_K1(double x) { return K1(x); }
 double or_face_value(double uu, double cc, double dd) { return face_value(uu, cc, dd); }
 double or_psi(double r) { return std::max(0.0, std::min(std::min(2.0 * r, (2.0 + r) / 3.0), 2.0)); }
 double or_sdf(void* h, const double* x, double* nrm) { return sdf(*(OSim*)h, x, nrm); }
+
+// ---- adjoint (reverse-mode derivative) entry points; see rollout_grad and the
+// transposes above.  Interior arrays as for the forward routines.
+namespace {
+void to_padded(const OSim& s, const double* in, vec* u) {
+  for (int c = 0; c < s.D; ++c) {
+    u[c].assign(s.npad, 0.0);
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) u[c][pidx(s, i, j, k)] = in[c * s.ncell + cidx(s, i, j, k)];
+  }
+  apply_bc(s, u);
+}
+void from_padded(const OSim& s, const vec* u, double* out) {
+  for (int c = 0; c < s.D; ++c)
+    for (int k = 0; k < s.n[2]; ++k)
+      for (int j = 0; j < s.n[1]; ++j)
+        for (int i = 0; i < s.n[0]; ++i) out[c * s.ncell + cidx(s, i, j, k)] = u[c][pidx(s, i, j, k)];
+}
+}  // namespace
+
+// ubar = (d convdiff / du)^T rbar at u.
+void or_convdiff_adjoint(void* h, const double* uin, const double* rbar, double* ubar) {
+  OSim* s = (OSim*)h;
+  vec u[3], rb[3], ub[3];
+  to_padded(*s, uin, u);
+  for (int c = 0; c < s->D; ++c) {
+    rb[c].assign(rbar + c * s->ncell, rbar + (c + 1) * s->ncell);
+    ub[c].assign(s->npad, 0.0);
+  }
+  convdiff_adjoint(*s, u, rb, ub);
+  from_padded(*s, ub, ubar);
+}
+
+// Transpose of one BDIM stage at (u0, u1): outbar -> u0bar, u1bar (D blocks each),
+// mu0bar (D blocks), mu1bar (D*D blocks, block c*D + j).
+void or_stage_adjoint(void* h, int stage, double dt, const double* u0in, const double* u1in, const double* outbar,
+                      double* u0bar, double* u1bar, double* mu0bar, double* mu1bar) {
+  OSim* s = (OSim*)h;
+  vec u0[3], u1[3], ob[3], u0b[3], u1b[3], m0b[3], m1b[3][3];
+  to_padded(*s, u0in, u0);
+  to_padded(*s, u1in ? u1in : u0in, u1);
+  for (int c = 0; c < s->D; ++c) {
+    ob[c].assign(outbar + c * s->ncell, outbar + (c + 1) * s->ncell);
+    u0b[c].assign(s->npad, 0.0);
+    u1b[c].assign(s->npad, 0.0);
+    m0b[c].assign(s->ncell, 0.0);
+    for (int j = 0; j < 3; ++j) m1b[c][j].assign(s->ncell, 0.0);
+  }
+  bdim_stage_adjoint(*s, stage, dt, u0, u1, ob, u0b, u1b, m0b, m1b);
+  from_padded(*s, u0b, u0bar);
+  from_padded(*s, u1b, u1bar);
+  for (int c = 0; c < s->D; ++c) {
+    std::memcpy(mu0bar + c * s->ncell, m0b[c].data(), s->ncell * sizeof(double));
+    for (int j = 0; j < s->D; ++j) std::memcpy(mu1bar + (c * s->D + j) * s->ncell, m1b[c][j].data(), s->ncell * sizeof(double));
+  }
+}
+
+// Transpose of project! of the velocity v (interior) with weight w: the forward solve
+// (PCG to tol) gives x; then ubar (D blocks) and pbar (cells, cotangent of p) give
+// vbar (D blocks) and Lbar (D blocks).  The state is not changed.
+void or_project_adjoint(void* h, const double* vin, double w, double dt, double tol, const double* ubar,
+                        const double* pbar, double* vbar, double* Lbar) {
+  OSim* s = (OSim*)h;
+  OSim t = *s;  // work on a copy of the state
+  vec v[3], ub[3], vb[3], Lb[3];
+  to_padded(t, vin, v);
+  std::fill(t.p.begin(), t.p.end(), 0.0);
+  project(t, v, w, dt, tol, 1000000, 0);
+  vec x = t.p;
+  for (auto& q : x) q *= w * dt;
+  vec xb(pbar, pbar + s->ncell);
+  for (auto& q : xb) q /= w * dt;
+  for (int c = 0; c < s->D; ++c) {
+    ub[c].assign(ubar + c * s->ncell, ubar + (c + 1) * s->ncell);
+    Lb[c].assign(s->ncell, 0.0);
+  }
+  project_adjoint(t, x, ub, xb, 1e-13, vb, Lb);
+  from_padded(t, vb, vbar);
+  for (int c = 0; c < s->D; ++c) std::memcpy(Lbar + c * s->ncell, Lb[c].data(), s->ncell * sizeof(double));
+}
+
+// Force of the pressure p (cells) and its adjoint for Fbar: pbar (cells) and the
+// theta-cotangent of the force weights (D + 1 values, circle/sphere only).
+void or_force_adjoint(void* h, const double* p, const double* Fbar, double* F, double* pbar, double* tb) {
+  OSim* s = (OSim*)h;
+  vec pp(p, p + s->ncell), pb;
+  for (int t = 0; t <= s->D; ++t) tb[t] = 0.0;
+  force_adjoint(*s, pp, Fbar, F, pb, tb);
+  std::memcpy(pbar, pb.data(), s->ncell * sizeof(double));
+}
+
+// theta-cotangent of field cotangents of the moments and coefficients (moments_adjoint).
+void or_moments_adjoint(void* h, const double* mu0bar, const double* Lbar, const double* mu1bar, double* tb) {
+  OSim* s = (OSim*)h;
+  vec m0[3], Lb[3], m1[3][3];
+  for (int c = 0; c < s->D; ++c) {
+    m0[c].assign(mu0bar + c * s->ncell, mu0bar + (c + 1) * s->ncell);
+    Lb[c].assign(Lbar + c * s->ncell, Lbar + (c + 1) * s->ncell);
+    for (int j = 0; j < 3; ++j)
+      m1[c][j] = (j < s->D) ? vec(mu1bar + (c * s->D + j) * s->ncell, mu1bar + (c * s->D + j + 1) * s->ncell)
+                            : vec(s->ncell, 0.0);
+  }
+  for (int t = 0; t <= s->D; ++t) tb[t] = 0.0;
+  moments_adjoint(*s, m0, Lb, m1, tb);
+}
+
+// Differentiated rollout (rollout_grad): returns 0, or -1 unless the body is a circle/sphere.
+int or_rollout_grad(void* h, int nsteps, double dt, double tol, const double* gF, double* F, double* tb) {
+  OSim* s = (OSim*)h;
+  if (s->body_kind != 1 || nsteps < 1 || !(dt > 0.0)) return -1;
+  rollout_grad(*s, nsteps, dt, tol, gF, F, tb);
+  return 0;
+}
+
 
 }  // extern "C"
