@@ -247,6 +247,43 @@ int wl_forces_noalloc(const int* dims, int ndim, unsigned periodic_mask, const w
  * paper. */
 int wl_wait_probe(double seconds, double* elapsed_ms);
 
+/* ---- Gradients of the pressure force with respect to the body (the differentiable
+ * use of the solver, Section 1; the body enters through its signed-distance function,
+ * Section 2).  theta = (R, c_0, .., c_{D-1}): the radius and centre of a circle/sphere
+ * body (WL_BODY_SPHERE).  The derivative is taken with dt held fixed (wl_opts.dt_fixed
+ * > 0 is required: the CFL rule is a maximum over the field and is not differentiated),
+ * each projection differentiated as the exact projection, and, where the convection
+ * scheme is not differentiable (the limiter's switch points, the upwind switch), the
+ * derivative of the branch the step takes.
+ *
+ * Memory: (nsteps/every + 1) checkpoints of the velocity and pressure, the recorded
+ * intermediates of `every` steps (2D + 2 fields each) and 6D + 1 adjoint fields, in a
+ * gradient workspace of wl_grad_workspace_bytes() bytes (256-byte aligned), supplied by
+ * the caller or (workspace = NULL) allocated by the library and freed by the next
+ * wl_grad_forward or wl_destroy.  Long horizons fit in memory by recomputing each
+ * segment of `every` steps from its checkpoint during the backward pass. */
+
+/* Bytes of the gradient workspace for nsteps steps with a checkpoint every `every`
+ * steps; 0 on bad arguments. */
+size_t wl_grad_workspace_bytes(wl_handle h, int nsteps, int every);
+
+/* Advance nsteps time steps from the current state (host-driven, the same kernels as
+ * wl_step), record the pressure force after each step into F (host, nsteps*D doubles,
+ * F_d = -sum (p - pbar) n_d K_eps(d) as wl_forces) and keep the checkpoints for
+ * wl_grad_backward.  Returns WL_EINVAL unless the body is a circle/sphere and dt is
+ * fixed; WL_WNOTCONV / WL_ENONFINITE as wl_step; WL_ENOMEM if the supplied workspace
+ * is too small or unaligned.  Synchronises. */
+int wl_grad_forward(wl_handle h, int nsteps, int every, void* workspace, size_t workspace_bytes, double* F);
+
+/* Gradient of J = sum_n gF[n] . F_n (gF: host, nsteps*D doubles, the cotangents of the
+ * forces wl_grad_forward recorded) with respect to theta into theta_bar (host, D + 1
+ * doubles: dJ/dR, dJ/dc_0, ..).  Recomputes every segment from its checkpoint and runs
+ * the adjoint of each step backwards (adjoint Poisson solves by the same multigrid to
+ * 1e-7 relative); the sim's state is the one after the forward rollout again on
+ * return.  Returns WL_WNOTCONV (theta_bar still written) if an adjoint solve hit
+ * max_vcycles.  Synchronises. */
+int wl_grad_backward(wl_handle h, const double* gF, double* theta_bar);
+
 /* Levels of the multigrid hierarchy and the dims of level l (dims[3]). */
 int wl_levels(wl_handle h, int* nlevels);
 int wl_level_dims(wl_handle h, int l, int* dims);

@@ -88,6 +88,22 @@ struct wl_sim {
   std::string err;
   // per-launch event pairs while wl_profile_step runs (class, start, stop)
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>>* prof = nullptr;
+  // differentiated rollout (wl_grad_forward / wl_grad_backward)
+  struct Grad {
+    int nsteps = 0, every = 0, nseg = 0;
+    char* mem = nullptr;
+    bool own = false;
+    float* ck = nullptr;       // checkpoints 0..nseg: D velocity fields + 2 pressure fields each
+    DevState* ckst = nullptr;  // the device state of each checkpoint
+    float* seg = nullptr;      // per step of a segment: u^n (D), u' (D), p after each projection (2)
+    float* adj = nullptr;      // u' of the state (D), of u^n (D), of the predictor (D), v', f', mbar (D each), y
+    double* rec = nullptr;     // force after each step (nsteps x D)
+    double* gF = nullptr;      // cotangents of those forces (nsteps x D)
+    AdjState* as = nullptr;
+    double* part = nullptr;    // reduction partials (4 x kForceParts)
+    bool ready = false;        // a forward rollout is recorded
+    bool notconv = false;      // an adjoint solve hit max_vcycles
+  } gr;
 };
 
 namespace {
@@ -525,14 +541,35 @@ int host_projection(wl_sim* s, int ubuf, float w, int proj) {
   return WL_OK;
 }
 
-int host_step(wl_sim* s) {
+// FP32 copy of the fine-level pressure into dst
+void copy_pressure(wl_sim* s, float* dst, cudaStream_t st) {
+  if (s->ph)
+    launch_df_round(s->ph, s->pl, dst, s->g.nc, st);
+  else
+    cudaMemcpyAsync(dst, s->lev[0].x, sizeof(float) * s->g.nc, cudaMemcpyDeviceToDevice, st);
+}
+
+// One step through the host-driven sequence.  rec (optional): where to keep u^n (D
+// fields), u' (D fields) and the pressure after each projection (2 fields), for the
+// adjoint of this step.
+int host_step(wl_sim* s, float* rec = nullptr) {
+  const long long n = s->g.nc;
+  const int D = s->D;
+  if (rec)
+    for (int c = 0; c < D; ++c)
+      cudaMemcpyAsync(rec + c * n, s->ua[c], sizeof(float) * n, cudaMemcpyDeviceToDevice, s->st);
   enq_stage(s, 1, s->st);
   int rc = host_projection(s, 1, 1.f, 0);
   if (rc) return rc;
+  if (rec) copy_pressure(s, rec + 2 * D * n, s->st);
   enq_correct(s, s->ub, s->uc, 1.f, 0, s->st);
+  if (rec)
+    for (int c = 0; c < D; ++c)
+      cudaMemcpyAsync(rec + (D + c) * n, s->uc[c], sizeof(float) * n, cudaMemcpyDeviceToDevice, s->st);
   enq_stage(s, 2, s->st);
   rc = host_projection(s, 1, 0.5f, 1);
   if (rc) return rc;
+  if (rec) copy_pressure(s, rec + (2 * D + 1) * n, s->st);
   enq_correct(s, s->ub, s->ua, 0.5f, 1, s->st);
   PROF(s, s->st, WL_KCLASS_CONTROL, launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->st));
   return cuda_check(s, cudaGetLastError(), "step launch");
@@ -789,6 +826,7 @@ void wl_destroy(wl_handle s) {
   if (s->cs) cudaStreamDestroy(s->cs);
   if (s->hs) cudaFreeHost(s->hs);
   if (s->own_ws && s->ws) cudaFree(s->ws);
+  if (s->gr.own && s->gr.mem) cudaFree(s->gr.mem);
   delete s;
 }
 
@@ -1101,3 +1139,266 @@ int wl_level_dims(wl_handle s, int l, int* dims) {
 }
 
 }  // extern "C"
+
+// --------------------------------------------------------------- differentiated rollout
+namespace {
+
+size_t grad_layout(wl_sim* s, int nsteps, int every, char* base) {
+  const int D = s->D;
+  const size_t n = (size_t)s->g.nc;
+  const int nseg = (nsteps + every - 1) / every;
+  Carver cv{base};
+  void* ck = cv.take(sizeof(float) * n * (D + 2) * (size_t)(nseg + 1));
+  void* ckst = cv.take(sizeof(DevState) * (size_t)(nseg + 1));
+  void* seg = cv.take(sizeof(float) * n * (2 * D + 2) * (size_t)every);
+  void* adj = cv.take(sizeof(float) * n * (6 * D + 1));
+  void* rec = cv.take(sizeof(double) * (size_t)nsteps * D);
+  void* gF = cv.take(sizeof(double) * (size_t)nsteps * D);
+  void* as = cv.take(sizeof(AdjState));
+  void* part = cv.take(sizeof(double) * 4 * kForceParts);
+  if (base) {
+    wl_sim::Grad& G = s->gr;
+    G.nsteps = nsteps;
+    G.every = every;
+    G.nseg = nseg;
+    G.ck = (float*)ck;
+    G.ckst = (DevState*)ckst;
+    G.seg = (float*)seg;
+    G.adj = (float*)adj;
+    G.rec = (double*)rec;
+    G.gF = (double*)gF;
+    G.as = (AdjState*)as;
+    G.part = (double*)part;
+  }
+  return cv.off;
+}
+
+float* ck_field(wl_sim* s, int k, int f) { return s->gr.ck + ((size_t)k * (s->D + 2) + f) * (size_t)s->g.nc; }
+
+// checkpoint k: the velocity, the fine-level pressure and the device state
+void save_ck(wl_sim* s, int k) {
+  const size_t nb = sizeof(float) * (size_t)s->g.nc;
+  for (int c = 0; c < s->D; ++c) cudaMemcpyAsync(ck_field(s, k, c), s->ua[c], nb, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemcpyAsync(ck_field(s, k, s->D), s->ph ? s->ph : s->lev[0].x, nb, cudaMemcpyDeviceToDevice, s->st);
+  if (s->pl) cudaMemcpyAsync(ck_field(s, k, s->D + 1), s->pl, nb, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemcpyAsync(s->gr.ckst + k, s->ds, sizeof(DevState), cudaMemcpyDeviceToDevice, s->st);
+}
+void restore_ck(wl_sim* s, int k) {
+  const size_t nb = sizeof(float) * (size_t)s->g.nc;
+  for (int c = 0; c < s->D; ++c) cudaMemcpyAsync(s->ua[c], ck_field(s, k, c), nb, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemcpyAsync(s->ph ? s->ph : s->lev[0].x, ck_field(s, k, s->D), nb, cudaMemcpyDeviceToDevice, s->st);
+  if (s->pl) cudaMemcpyAsync(s->pl, ck_field(s, k, s->D + 1), nb, cudaMemcpyDeviceToDevice, s->st);
+  cudaMemcpyAsync(s->ds, s->gr.ckst + k, sizeof(DevState), cudaMemcpyDeviceToDevice, s->st);
+}
+
+// adjoint fields: [0,D) cotangent of the state, [D,2D) of u^n, [2D,3D) of the
+// predictor u', [3D,4D) v', [4D,5D) f', [5D,6D) the coefficient cotangent, 6D: y
+struct AdjFields {
+  float* f[7][3];
+};
+AdjFields adj_fields(wl_sim* s) {
+  AdjFields a{};
+  const int D = s->D;
+  for (int b = 0; b < 6; ++b)
+    for (int c = 0; c < 3; ++c) a.f[b][c] = s->gr.adj + (size_t)(b * D + (c < D ? c : D - 1)) * s->g.nc;
+  for (int c = 0; c < 3; ++c) a.f[6][c] = s->gr.adj + (size_t)(6 * D) * s->g.nc;
+  return a;
+}
+
+// Solve A y = b (b in the fine right-hand side, mean-free over the active cells) with the
+// forward multigrid to ||b - A y||_inf <= rtol ||b||_inf; y (FP32) into dst.
+int adj_solve(wl_sim* s, double rtol, float* dst) {
+  const size_t nb = sizeof(float) * (size_t)s->g.nc;
+  if (s->ph) {
+    cudaMemsetAsync(s->ph, 0, nb, s->st);
+    cudaMemsetAsync(s->pl, 0, nb, s->st);
+  } else {
+    cudaMemsetAsync(s->lev[0].x, 0, nb, s->st);
+  }
+  double bnorm = 0.0;
+  for (int it = 0;; ++it) {
+    WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
+    enq_fine_residual(s, RES_RESIDUAL, 0, 1.f, s->st);
+    int rc = sync_state(s);
+    if (rc) return rc;
+    const double r = reinterpret_cast<const float&>(s->hs->norm_bits);
+    if (!std::isfinite(r)) {
+      s->poisoned = true;
+      return fail(s, WL_ENONFINITE, "non-finite adjoint residual");
+    }
+    if (it == 0) bnorm = r;
+    if (r <= rtol * bnorm || r == 0.0) break;
+    if (it >= s->o.max_vcycles) {  // a warning: the gradient is returned, less accurate
+      s->gr.notconv = true;
+      fail(s, WL_WNOTCONV, "adjoint solve hit max_vcycles");
+      break;
+    }
+    enq_vcycle_core(s, s->st);
+  }
+  WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
+  copy_pressure(s, dst, s->st);
+  return WL_OK;
+}
+
+constexpr double kAdjRtol = 1e-7;
+
+// Adjoint of step n (its recorded slot m): the cotangent of u^{n+1} in field block 0 and
+// of the force after the step in gF[n] give the cotangent of u^n in block 0 and add to
+// theta and to the coefficient cotangent.
+int adj_step(wl_sim* s, int m, int n) {
+  const int D = s->D;
+  const size_t nc = (size_t)s->g.nc;
+  float* rec = s->gr.seg + (size_t)m * (2 * D + 2) * nc;
+  float* un[3];
+  float* up[3];
+  for (int c = 0; c < 3; ++c) {
+    un[c] = rec + (size_t)(c < D ? c : D - 1) * nc;
+    up[c] = rec + (size_t)(D + (c < D ? c : D - 1)) * nc;
+  }
+  float* p1 = rec + (size_t)(2 * D) * nc;
+  float* p2 = rec + (size_t)(2 * D + 1) * nc;
+  AdjFields A = adj_fields(s);
+  float* const* ub = A.f[0];
+  float* const* ub0 = A.f[1];
+  float* const* ubp = A.f[2];
+  float* const* vb = A.f[3];
+  float* const* fb = A.f[4];
+  float* const* mb = A.f[5];
+  float* y = A.f[6][0];
+  const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
+  const double dt = s->o.dt_fixed;
+  const double* g = s->gr.gF + (size_t)n * D;
+  cudaStream_t st = s->st;
+  // force after the step: F = -sum (p - pbar) n K_eps(d), p = x2 / (dt/2)
+  launch_forces(D, s->g, s->body, p2, nullptr, L, s->fpart, kForceParts, s->fout, st);
+  launch_adj_force_theta(D, s->g, s->body, p2, s->fout + 3, g, s->gr.as, st);
+  // projection 2 (w = 1/2)
+  launch_adj_proj_rhs(D, s->g, s->body, ub, L, g, 1.0 / (0.5 * dt), s->gr.as, s->lev[0].z, s->gr.part, kForceParts, st);
+  int rc = adj_solve(s, kAdjRtol, y);
+  if (rc) return rc;
+  launch_adj_proj_out(D, s->g, ub, y, p2, (float)(0.5 * dt), vb, mb, st);
+  // stage 2: out = (u' + mu0 f + mu1 . grad f)/2, f = u^n + dt r(u')
+  launch_adj_stage_local(D, s->g, vb, L, 0.5f, fb, ubp, st);
+  StageArgs a = stage_args(s, 2);
+  for (int c = 0; c < 3; ++c) {
+    a.u[c] = up[c];
+    a.u0[c] = un[c];
+  }
+  launch_adj_band(D, a, s->body, vb, 0.5f, fb, mb, s->gr.as, st);
+  for (int c = 0; c < D; ++c) cudaMemsetAsync(ub0[c], 0, sizeof(float) * nc, st);
+  launch_adj_convdiff(D, s->g, up, fb, &s->ds->dtf, (float)s->nu, s->o.advect, ub0, ubp, st);
+  // projection 1 (w = 1)
+  launch_adj_proj_rhs(D, s->g, s->body, ubp, L, nullptr, 0.0, s->gr.as, s->lev[0].z, s->gr.part, kForceParts, st);
+  rc = adj_solve(s, kAdjRtol, y);
+  if (rc) return rc;
+  launch_adj_proj_out(D, s->g, ubp, y, p1, (float)dt, vb, mb, st);
+  // stage 1: out = mu0 f + mu1 . grad f, f = u^n + dt r(u^n)
+  launch_adj_stage_local(D, s->g, vb, L, 1.f, fb, nullptr, st);
+  a = stage_args(s, 1);
+  for (int c = 0; c < 3; ++c) a.u[c] = a.u0[c] = un[c];
+  launch_adj_band(D, a, s->body, vb, 1.f, fb, mb, s->gr.as, st);
+  launch_adj_convdiff(D, s->g, un, fb, &s->ds->dtf, (float)s->nu, s->o.advect, ub0, ub0, st);
+  for (int c = 0; c < D; ++c) cudaMemcpyAsync(ub[c], ub0[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
+  return cuda_check(s, cudaGetLastError(), "adjoint step");
+}
+
+int grad_check(wl_sim* s) {
+  if (s->body.kind != 1) return fail(s, WL_EINVAL, "gradients need a circle/sphere body");
+  if (!(s->o.dt_fixed > 0.0)) return fail(s, WL_EINVAL, "gradients need a fixed dt (wl_opts.dt_fixed > 0)");
+  if (s->poisoned) return fail(s, WL_ENONFINITE, "sim is poisoned");
+  return WL_OK;
+}
+
+}  // namespace
+
+size_t wl_grad_workspace_bytes(wl_handle s, int nsteps, int every) {
+  if (!s || nsteps < 1 || every < 1) return 0;
+  return grad_layout(s, nsteps, std::min(every, nsteps), nullptr);
+}
+
+int wl_grad_forward(wl_handle s, int nsteps, int every, void* workspace, size_t workspace_bytes, double* F) {
+  if (!s || nsteps < 1 || every < 1 || !F) return WL_EINVAL;
+  int rc = grad_check(s);
+  if (rc) return rc;
+  every = std::min(every, nsteps);
+  const size_t need = grad_layout(s, nsteps, every, nullptr);
+  wl_sim::Grad& G = s->gr;
+  if (G.own && G.mem) {
+    cudaStreamSynchronize(s->st);
+    cudaFree(G.mem);
+  }
+  G = wl_sim::Grad{};
+  if (workspace) {
+    if (workspace_bytes < need || ((uintptr_t)workspace & 255u)) return fail(s, WL_ENOMEM, "gradient workspace too small");
+    G.mem = (char*)workspace;
+  } else {
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(s, WL_ENOMEM, "gradient workspace");
+    }
+    G.mem = (char*)p;
+    G.own = true;
+  }
+  grad_layout(s, nsteps, every, G.mem);
+  WL_CUDA(s, cudaMemsetAsync(&s->ds->status, 0, sizeof(int), s->st));
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % every == 0) save_ck(s, n / every);
+    rc = host_step(s);
+    if (rc) return rc;
+    const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
+    launch_forces(s->D, s->g, s->body, s->ph ? s->ph : s->lev[0].x, s->pl, L, s->fpart, kForceParts, s->fout, s->st);
+    WL_CUDA(s, cudaMemcpyAsync(G.rec + (size_t)n * s->D, s->fout, sizeof(double) * s->D, cudaMemcpyDeviceToDevice,
+                               s->st));
+  }
+  save_ck(s, G.nseg);
+  WL_CUDA(s, cudaMemcpyAsync(F, G.rec, sizeof(double) * nsteps * s->D, cudaMemcpyDeviceToHost, s->st));
+  rc = sync_state(s);
+  if (rc) return rc;
+  if (s->hs->status & 1) {
+    s->poisoned = true;
+    return fail(s, WL_ENONFINITE, "non-finite value in the rollout");
+  }
+  G.ready = true;
+  return (s->hs->status & 2) ? WL_WNOTCONV : WL_OK;
+}
+
+int wl_grad_backward(wl_handle s, const double* gF, double* theta_bar) {
+  if (!s || !gF || !theta_bar) return WL_EINVAL;
+  int rc = grad_check(s);
+  if (rc) return rc;
+  wl_sim::Grad& G = s->gr;
+  if (!G.ready) return fail(s, WL_EINVAL, "wl_grad_backward needs a wl_grad_forward first");
+  const int D = s->D;
+  const size_t nc = (size_t)s->g.nc;
+  WL_CUDA(s, cudaMemcpyAsync(G.gF, gF, sizeof(double) * G.nsteps * D, cudaMemcpyHostToDevice, s->st));
+  const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
+  launch_adj_setup(D, s->g, s->body, L, G.as, G.part, kForceParts, s->st);
+  AdjFields A = adj_fields(s);
+  for (int c = 0; c < D; ++c) {
+    cudaMemsetAsync(A.f[0][c], 0, sizeof(float) * nc, s->st);  // J has no term in the final state
+    cudaMemsetAsync(A.f[5][c], 0, sizeof(float) * nc, s->st);
+  }
+  const size_t slot = (size_t)(2 * D + 2) * nc;
+  G.notconv = false;
+  for (int k = G.nseg - 1; k >= 0; --k) {
+    const int n0 = k * G.every, n1 = std::min(n0 + G.every, G.nsteps);
+    restore_ck(s, k);
+    for (int n = n0; n < n1; ++n) {  // recompute the segment, keeping what the adjoint needs
+      rc = host_step(s, G.seg + (size_t)(n - n0) * slot);
+      if (rc) return rc;
+    }
+    for (int n = n1 - 1; n >= n0; --n) {
+      rc = adj_step(s, n - n0, n);
+      if (rc) return rc;
+    }
+  }
+  launch_adj_moments(D, s->g, s->body, A.f[5], G.as, s->st);
+  restore_ck(s, G.nseg);
+  double th[4];
+  WL_CUDA(s, cudaMemcpyAsync(th, G.as->theta, sizeof(th), cudaMemcpyDeviceToHost, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  for (int t = 0; t <= D; ++t) theta_bar[t] = th[t];
+  rc = cuda_check(s, cudaGetLastError(), "wl_grad_backward");
+  return rc ? rc : (G.notconv ? WL_WNOTCONV : WL_OK);
+}

@@ -190,6 +190,34 @@ int launch_sync_dt(DevState* st, cudaStream_t s);
 }  // namespace wl
 
 namespace wl {
+
+// ---- reverse-mode derivative of the time step (wl_adjoint.cu)
+struct AdjState {
+  double theta[4];  // dJ/d(R, c_0, .., c_{D-1}), accumulated
+  double W[3];      // sum over band cells of the force weights n K_eps(d)
+  double Na;        // active cells (nonzero Poisson row)
+  double mean;      // mean over active cells of the last adjoint right-hand side
+};
+int launch_adj_setup(int D, const Grid& g, const Body& b, const float* const* L, AdjState* as, double* part,
+                     int npart, cudaStream_t s);
+int launch_adj_force_theta(int D, const Grid& g, const Body& b, const float* p, const double* pmean,
+                           const double* gF, AdjState* as, cudaStream_t s);
+int launch_adj_proj_rhs(int D, const Grid& g, const Body& b, const float* const* ub, const float* const* L,
+                        const double* gF, double fmul, AdjState* as, float* rhs, double* part, int npart,
+                        cudaStream_t s);
+int launch_adj_proj_out(int D, const Grid& g, const float* const* ub, const float* y, const float* p, float xmul,
+                        float* const* vb, float* const* mbar, cudaStream_t s);
+int launch_adj_stage_local(int D, const Grid& g, const float* const* vb, const float* const* mu0, float sfac,
+                           float* const* fb, float* const* up, cudaStream_t s);
+int launch_adj_band(int D, const StageArgs& a, const Body& b, const float* const* vb, float sfac, float* const* fb,
+                    float* const* mbar, AdjState* as, cudaStream_t s);
+int launch_adj_convdiff(int D, const Grid& g, const float* const* u, const float* const* fb, const float* dt, float nu,
+                        int advect, float* const* ub0, float* const* ubin, cudaStream_t s);
+int launch_adj_moments(int D, const Grid& g, const Body& b, const float* const* mbar, AdjState* as, cudaStream_t s);
+
+}  // namespace wl
+
+namespace wl {
 int launch_set_dt_from_cfl(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s);
 int launch_fix_bfaces(int D, const Grid& g, float* const* u, cudaStream_t s);
 }  // namespace wl

@@ -48,6 +48,7 @@ EXPORTS = (
     "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_get_field", "wl_set_field", "wl_get_dt",
     "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_levels", "wl_level_dims",
     "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
+    "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward",
 )
 KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coarse", "coarsest", "correct",
             "control")
@@ -110,6 +111,9 @@ def load(path: str = LIB_PATH):
         "wl_forces_noalloc": (I, [IP, I, ctypes.c_uint, ctypes.POINTER(WlBody), D, P, P, P, P]),
         "wl_wait_probe": (I, [D, DP]),
         "wl_step_batch": (I, [ctypes.POINTER(H), I, I, P]),
+        "wl_grad_workspace_bytes": (ctypes.c_size_t, [H, I, I]),
+        "wl_grad_forward": (I, [H, I, I, P, ctypes.c_size_t, DP]),
+        "wl_grad_backward": (I, [H, DP, DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -403,6 +407,36 @@ class Sim:
         rc, d = wl_profile_step(self.h, nsteps)
         self._check(rc, "wl_profile_step")
         return d
+
+    def grad_forward(self, nsteps, every):
+        """wl_grad_forward: nsteps steps recording the force after each (returned as an
+        (nsteps, D) float64 array) and the checkpoints for grad_backward; the gradient
+        workspace is a torch tensor kept by this object."""
+        nb = load().wl_grad_workspace_bytes(self.h, int(nsteps), int(every))
+        if nb == 0:
+            raise WLError(WL_EINVAL, "bad gradient rollout arguments")
+        self.grad_workspace = self.torch.empty(nb + 256, dtype=self.torch.uint8, device=self.device)
+        base = self.grad_workspace.data_ptr()
+        ptr = (base + 255) // 256 * 256
+        F = np.zeros(int(nsteps) * self.D)
+        rc = load().wl_grad_forward(self.h, int(nsteps), int(every), ctypes.c_void_p(ptr), nb,
+                                    F.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self._check(rc, "wl_grad_forward")
+        self.grad_steps = int(nsteps)
+        return F.reshape(int(nsteps), self.D)
+
+    def grad_backward(self, gF, return_status=False):
+        """wl_grad_backward: dJ/d(R, c_0, ..) for J = sum_n gF[n] . F_n (and the status,
+        WL_OK or WL_WNOTCONV, with return_status)."""
+        g = np.ascontiguousarray(gF, dtype=np.float64).reshape(-1)
+        n = getattr(self, "grad_steps", 0)
+        if n and g.size != n * self.D:
+            raise WLError(WL_EINVAL, f"gF must hold {n} x {self.D} values")
+        tb = np.zeros(self.D + 1)
+        rc = load().wl_grad_backward(self.h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     tb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        self._check(rc, "wl_grad_backward")
+        return (tb, rc) if return_status else tb
 
     def levels(self):
         rc, n = wl_levels(self.h)
