@@ -340,6 +340,13 @@ def run_ours(args, w, dist, rank, ws, lrank):
         except Exception as e:  # reported, not fatal: the main measurement stands
             mixed = {"error": f"{type(e).__name__}: {e}"}
 
+    adjoint = None
+    if rank == 0 and ws == 1 and not args.no_adjoint:
+        try:
+            adjoint = adjoint_bench(args.tol)
+        except Exception as e:  # reported, not fatal: the main measurement stands
+            adjoint = {"error": f"{type(e).__name__}: {e}"}
+
     serving = None
     if rank == 0 and ws == 1 and not args.no_serve:
         try:
@@ -366,7 +373,7 @@ def run_ours(args, w, dist, rank, ws, lrank):
                 "vcycles_per_s": vtot / tmax, "vcycles_per_step": vcycles / args.steps,
                 "converged": rc == 0, "worst_residual": worst,
                 "roofline": roof, "step_roofline": step_roof, "kernels": kern, "cpu_baseline": cpu, "e2e": e2e,
-                "mixed_precision": mixed, "serving": serving, "clocks": ck,
+                "mixed_precision": mixed, "adjoint": adjoint, "serving": serving, "clocks": ck,
                 "gpu_launches": int(ws * launches)}
         print(json.dumps(line), flush=True)
     sim.close()
@@ -420,6 +427,44 @@ def mixed_bench(w, args):
     return out
 
 
+def adjoint_bench(tol):
+    """The adjoint configuration: 2-D cylinder 256x128, R = 12 at (64, 64), Re = 200 on the
+    diameter, U = 1, fixed dt 0.1, mean drag coefficient over 50 steps differentiated with
+    respect to (R, cx, cy) by the hand-written adjoint with checkpoints every 10 steps.
+    Wall time of the recorded forward rollout and of the backward pass (segment
+    recomputation + adjoint), both host-driven and synchronising."""
+    import numpy as np
+
+    from paper_2304_08159_gb300 import Sim
+
+    nsteps, every, R = 50, 10, 12.0
+
+    def run():
+        sim = Sim((256, 128), 24.0 / 200.0, (1.0, 0.0), body=dict(kind=1, center=(64.0, 64.0), radius=R), tol=tol,
+                  dt_fixed=0.1)
+        t0 = time.perf_counter()
+        F = sim.grad_forward(nsteps, every)
+        t1 = time.perf_counter()
+        g = np.zeros_like(F)
+        g[:, 0] = 1.0 / (nsteps * R)
+        tb = sim.grad_backward(g)
+        t2 = time.perf_counter()
+        ws = sim.grad_workspace.numel()
+        sim.close()
+        J = F[:, 0].mean() / R
+        tb[0] -= J / R
+        return t1 - t0, t2 - t1, J, tb, ws
+
+    run()  # warm-up (module load, first kernel launches)
+    tf, tbk, J, tb, ws = run()
+    ncell = 256 * 128
+    return {"workload": "2-D cylinder 256x128, R=12, Re=200, 50 steps at dt=0.1, checkpoints every 10",
+            "forward_ms": 1e3 * tf, "backward_ms": 1e3 * tbk, "backward_over_forward": tbk / tf,
+            "forward_cells_steps_per_s": ncell * nsteps / tf,
+            "mean_drag_coefficient": J, "dCD_dtheta": [float(v) for v in tb], "theta": ["R", "cx", "cy"],
+            "gradient_workspace_mb": ws / 1e6, "poisson_tol": tol}
+
+
 def serving_bench(n_req, tol):
     """The serving mix (seeded Poisson stream of 2-D cylinder and 3-D sphere cases of
     different sizes) served batched (continuous batching, one wl_step_batch per round)
@@ -466,6 +511,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
