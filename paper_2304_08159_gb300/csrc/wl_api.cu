@@ -47,6 +47,7 @@ struct LevelBuf {
 };
 
 constexpr int kMaxLevels = 16;
+constexpr long long kTailCells = 4096;  // largest hierarchy tail (cells) run by k_vcycle_tail
 constexpr int kForceParts = 1024;
 
 }  // namespace
@@ -75,6 +76,7 @@ struct wl_sim {
   CUtensorMap mph{}, mpl{};   // TMA descriptors of the fine pressure (ph: hi part or FP32 pressure)
   CUtensorMap mu[3][3]{};     // TMA descriptors of the velocity buffers A, B, C (components)
   bool resid_tma = false;     // the fine residual uses the TMA-staged kernel
+  int tail_lf = 0;            // > 0: levels tail_lf .. nlev-1 run as one block (k_vcycle_tail)
   float* rf = nullptr;        // precision 1: FP32 residual, right-hand side of each correction cycle
   double* G = nullptr;        // dense pseudo-inverse of the coarsest operator (small coarsest levels)
   char* ws = nullptr;
@@ -293,6 +295,19 @@ StageArgs stage_args(wl_sim* s, int stage) {
   a.nu = (float)s->nu;
   a.stage = stage;
   a.advect = s->o.advect;
+  // f of the body's band box goes to the fine level's ping-pong iterate, which is free
+  // until the projection's sweeps
+  int lo[3], hi[3];
+  if (stage_band_box(s->D, s->g, s->body, lo, hi)) {
+    const long long vol = (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    if (vol * s->D <= s->g.nc) {
+      a.fbox = s->lev[0].x2;
+      for (int d = 0; d < 3; ++d) {
+        a.blo[d] = lo[d];
+        a.bn[d] = hi[d] - lo[d];
+      }
+    }
+  }
   return a;
 }
 
@@ -492,6 +507,27 @@ void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
     } else {
       enq_coarsest(s, 0, s->lev[0].z, s->lev[0].x, st);
     }
+    return;
+  }
+  if (s->tail_lf > 0) {  // the small levels in one block
+    const int lf = s->tail_lf;
+    for (int l = 1; l < lf; ++l) PROF(s, st, WL_KCLASS_RESTRICT, launch_residual(s->D, res_args(s, l, RES_RESTRICT), st));
+    TailArgs t{};
+    t.nl = Lv - lf;
+    for (int l = 0; l < t.nl; ++l) {
+      const LevelBuf& L = s->lev[lf + l];
+      for (int d = 0; d < 3; ++d) t.n[l][d] = L.g.n[d];
+      for (int c = 0; c < 3; ++c) t.L[l][c] = L.Lk[c];
+      t.st[l] = L.st;
+    }
+    t.z = s->lev[lf].z;
+    t.zmul = 1.f / s->lev[lf].zs;
+    t.x = s->lev[lf].x;
+    t.G = s->G;
+    t.post = s->o.post;
+    t.per = s->g.per;
+    PROF(s, st, WL_KCLASS_SWEEP_COARSE, launch_vcycle_tail(s->D, t, st));
+    for (int l = lf - 1; l >= 0; --l) enq_smooth(s, l, st);
     return;
   }
   for (int l = 1; l + 1 < Lv; ++l) PROF(s, st, WL_KCLASS_RESTRICT, launch_residual(s->D, res_args(s, l, RES_RESTRICT), st));
@@ -746,6 +782,25 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   }
   s->ws_bytes = need;
   layout(s, ndim, dims, o.precision, o.coarse_precision, s->ws);
+  // The coarse end of the V-cycle runs in one block from the largest level whose
+  // hierarchy below holds at most kTailCells cells (the coarsest solved densely; a
+  // 16-bit level 1 keeps its staged conversion, so the tail starts at level 2 or below).
+  // Measured in a CUDA graph: a per-level launch costs ~2.5 us, the block ~4 us plus its
+  // sweeps on one SM, so the tail pays for small levels only (with 9K cells it lost).
+  if (s->G && s->nlev >= 3 && !std::getenv("WL_NO_TAIL")) {
+    int n[kMaxLevels][3];
+    long long cells = 0;
+    for (int l = 0; l < s->nlev; ++l)
+      for (int d = 0; d < 3; ++d) n[l][d] = s->lev[l].g.n[d];
+    const int lmin = s->lev[1].z32 ? 2 : 1;
+    for (int lf = s->nlev - 1; lf >= lmin; --lf) {  // grow the tail upwards while it stays small
+      cells += s->lev[lf].g.nc;
+      if (cells > kTailCells || s->nlev - lf > kTailMaxLevels ||
+          vcycle_tail_smem(ndim, n + lf, s->nlev - lf) > kTailSmemMax)
+        break;
+      if (lf + 2 <= s->nlev) s->tail_lf = lf;
+    }
+  }
   int rc = WL_OK;
   if (cudaMallocHost(&s->hs, sizeof(DevState)) != cudaSuccess) rc = fail(s, WL_ENOMEM, "pinned host state");
   if (!rc) rc = cuda_check(s, cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking), "capture stream");

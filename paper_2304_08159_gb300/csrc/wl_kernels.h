@@ -16,7 +16,12 @@ struct StageArgs {
   float nu;
   int stage;            // 1 or 2
   int advect;
+  float* fbox;          // if set: f = u0 + dt r(u) of every face in the body's band box (D blocks of
+  int blo[3], bn[3];    //   bn[0]*bn[1]*bn[2] values, box origin blo), kept for the mu1 term
 };
+// Faces whose f the mu1 term of BDIM reads: the body's band (|d| < eps) and one face
+// beyond, boxed ([lo, hi) per direction, clamped to the grid); false if the box is empty.
+bool stage_band_box(int D, const Grid& g, const Body& b, int* lo, int* hi);
 
 // residual / divergence / restriction modes of k_residual
 enum { RES_RESIDUAL = 0, RES_DIVERGENCE = 1, RES_RESTRICT = 2, RES_DIV_ONLY = 3 };
@@ -98,6 +103,27 @@ struct DenseArgs {
   const float* z;
   float* x;
 };
+
+// The coarse end of a V-cycle in one block (k_vcycle_tail): levels lf .. lf + nl - 1
+// (the last one the coarsest, solved by its dense pseudo-inverse), all held in shared
+// memory.  Reads level lf's right-hand side, writes level lf's smoothed correction.
+constexpr int kTailMaxLevels = 8;
+constexpr int kTailThreads = 1024;
+constexpr size_t kTailSmemMax = 200 * 1024;  // bytes of shared memory the tail may use
+struct TailArgs {
+  int nl;
+  int n[kTailMaxLevels][3];
+  const float* L[kTailMaxLevels][3];  // each level's coefficients (storage type st[l])
+  int st[kTailMaxLevels];
+  const float* z;                      // level lf's right-hand side (type st[0]), value = zmul * stored
+  float zmul;
+  float* x;                            // level lf's correction out (type st[0])
+  const double* G;                     // coarsest pseudo-inverse, column-major
+  int post;
+  unsigned per;
+};
+int launch_vcycle_tail(int D, const TailArgs& a, cudaStream_t s);
+size_t vcycle_tail_smem(int D, const int (*n)[3], int nl);
 
 struct CoarseArgs {
   const float* z;

@@ -40,6 +40,9 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
   const float dt = *a.dt;
   const bool adv = a.advect != 0;
   const float nu = a.nu;
+  // this tile overlaps the body's band box: its faces there keep f for the mu1 term
+  const bool box_tile = a.fbox && i0 < a.blo[0] + a.bn[0] && i0 + ST_TX > a.blo[0] && j0 < a.blo[1] + a.bn[1] &&
+                        j0 + ST_TY > a.blo[1] && k0 < a.blo[2] + a.bn[2] && k1 > a.blo[2];
 
   auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
   // flat shared-memory view: component c of plane kk starts at off(c, kk); a tile
@@ -177,17 +180,22 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
         float r = (s_fx[c][ty][tx] - s_fx[c][ty][tx + 1]) + (s_fy[c][ty][tx] - s_fy[c][ty + 1][tx]);
         if (D == 3) r += fzl[c] - fzu[c];
         const bool upd = is_per(g, c) || I[c] >= 1;
-        float ov;
+        float ov, f = g.U[c];
         if (!upd) {
           ov = g.U[c];
         } else {
           const float uc = sf[o[c] + own];
           const float u0 = (a.stage == 1) ? uc : u0v[c];
-          const float f = fmaf(dt, r, u0);
+          f = fmaf(dt, r, u0);
           const float m = m0[c];
           ov = (a.stage == 1) ? m * f : 0.5f * (uc + m * f);
         }
         a.out[c][qg] = ov;
+        if (box_tile) {  // keep f inside the body's band box for the mu1 term
+          const unsigned bi = (unsigned)(i - a.blo[0]), bj = (unsigned)(j - a.blo[1]), bk = (unsigned)(k - a.blo[2]);
+          if (bi < (unsigned)a.bn[0] && bj < (unsigned)a.bn[1] && bk < (unsigned)a.bn[2])
+            a.fbox[(long long)c * a.bn[0] * a.bn[1] * a.bn[2] + bi + (long long)a.bn[0] * (bj + (long long)a.bn[1] * bk)] = f;
+        }
       }
     }
 #pragma unroll
@@ -220,14 +228,25 @@ __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0,
   if (!(fabs(d) < b.eps)) return;
   const double k1 = b.eps * kernel_K1(d / b.eps);
   const float dt = *a.dt;
+  // f at a face: from the stage kernel's box when the face is inside it (in range),
+  // else evaluated here with the BC mapping
+  auto fget = [&](const int* F) -> float {
+    if (a.fbox) {
+      const unsigned bi = (unsigned)(F[0] - a.blo[0]), bj = (unsigned)(F[1] - a.blo[1]),
+                     bk = (unsigned)(F[2] - a.blo[2]);
+      if (bi < (unsigned)a.bn[0] && bj < (unsigned)a.bn[1] && bk < (unsigned)a.bn[2])
+        return a.fbox[(long long)c * a.bn[0] * a.bn[1] * a.bn[2] + bi + (long long)a.bn[0] * (bj + (long long)a.bn[1] * bk)];
+    }
+    return f_at<D>(a, c, F[0], F[1], F[2], dt);
+  };
   float acc = 0.f;
 #pragma unroll
   for (int jd = 0; jd < D; ++jd) {
     int P[3] = {i, j, k}, M[3] = {i, j, k};
     P[jd] += 1;
     M[jd] -= 1;
-    const float fp = f_at<D>(a, c, P[0], P[1], P[2], dt);
-    const float fm = f_at<D>(a, c, M[0], M[1], M[2], dt);
+    const float fp = fget(P);
+    const float fm = fget(M);
     acc += (float)(k1 * nrm[jd]) * 0.5f * (fp - fm);
   }
   const long long q = cell_index(g, i, j, k);
@@ -248,24 +267,29 @@ int launch_stage(int D, const StageArgs& a, cudaStream_t s) {
   return 0;
 }
 
+bool stage_band_box(int D, const Grid& g, const Body& b, int* lo, int* hi) {
+  if (b.kind == 0) return false;
+  double ext = b.r1 + b.eps + 2.0;
+  if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 2.0;
+  for (int d = 0; d < 3; ++d) {
+    if (d >= D) {
+      lo[d] = 0;
+      hi[d] = 1;
+      continue;
+    }
+    lo[d] = (int)fmax(0.0, floor(b.c[d] - ext));
+    hi[d] = (int)fmin((double)g.n[d], ceil(b.c[d] + ext) + 1.0);
+    if (hi[d] <= lo[d]) return false;  // body outside the grid: no band
+  }
+  return true;
+}
+
 int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s) {
   const Grid& g = a.g;
   if (b.kind != 0) {
     // bounding box of the faces within eps of the surface
-    double ext = b.r1 + b.eps + 2.0;
-    if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 2.0;
     int lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) {
-      if (d >= D) {
-        lo[d] = 0;
-        hi[d] = 1;
-        continue;
-      }
-      double l = b.c[d] - ext, h = b.c[d] + ext;
-      lo[d] = (int)fmax(0.0, floor(l));
-      hi[d] = (int)fmin((double)g.n[d], ceil(h) + 1.0);
-      if (hi[d] <= lo[d]) return 0;  // body outside the grid: no band
-    }
+    if (!stage_band_box(D, g, b, lo, hi)) return 0;
     const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
     const long long n = (long long)bx * by * bz * D;
     const int nb = (int)((n + 255) / 256);

@@ -1314,6 +1314,158 @@ int launch_apply_pinv(const DenseArgs& a, cudaStream_t s) {
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// k_vcycle_tail: the small levels of a V-cycle in one block of shared memory.  The same
+// arithmetic, in the same order, as the per-level kernels it replaces (restriction of
+// RES_RESTRICT: z pairs, then x pairs, then y pairs; k_apply_pinv; k_sweep's
+// prolongation and relaxation), without a launch per level and sweep.  Values in shared
+// memory carry no per-level storage scale.
+size_t vcycle_tail_smem(int D, const int (*n)[3], int nl) {
+  size_t b = 0;
+  for (int l = 0; l < nl; ++l) b += sizeof(float) * (size_t)(D + 2) * n[l][0] * n[l][1] * n[l][2];
+  return b;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs a) {
+  extern __shared__ float tsm[];
+  // shared-memory layout: per level, D coefficient fields, z, x (all levels < 2^31 cells)
+  auto level_base = [&](int l) {
+    int off = 0;
+    for (int m = 0; m < l; ++m) off += (D + 2) * a.n[m][0] * a.n[m][1] * a.n[m][2];
+    return tsm + off;
+  };
+  auto ncells = [&](int l) { return a.n[l][0] * a.n[l][1] * a.n[l][2]; };
+  const int tid = threadIdx.x;
+  for (int l = 0; l < a.nl; ++l) {
+    float* b = level_base(l);
+    const int nc = ncells(l);
+    for (int c = 0; c < D; ++c)
+      for (int q = tid; q < nc; q += kTailThreads) b[c * nc + q] = ld_st(a.L[l][c], a.st[l], q);
+  }
+  {
+    const int nc = ncells(0);
+    float* z0 = level_base(0) + D * nc;
+    for (int q = tid; q < nc; q += kTailThreads) z0[q] = a.zmul * ld_st(a.z, a.st[0], q);
+  }
+  __syncthreads();
+  // restriction down to the coarsest level (the iterate of every tail level starts at 0)
+  for (int l = 0; l + 1 < a.nl; ++l) {
+    const int f0 = a.n[l][0], f1 = a.n[l][1];
+    const int c0 = a.n[l + 1][0], c1 = a.n[l + 1][1];
+    const float* zf = level_base(l) + D * ncells(l);
+    float* zc = level_base(l + 1) + D * ncells(l + 1);
+    const int ncc = ncells(l + 1);
+    for (int q = tid; q < ncc; q += kTailThreads) {
+      const int I = q % c0, t = q / c0;
+      const int J = t % c1, K = t / c1;
+      const int b0 = 2 * I + f0 * (2 * J + f1 * 2 * K);  // child (2I, 2J, 2K)
+      float sum;
+      if (D == 3) {
+        const int sz = f0 * f1;
+        const float a00 = zf[b0] + zf[b0 + sz];
+        const float a10 = zf[b0 + 1] + zf[b0 + 1 + sz];
+        const float a01 = zf[b0 + f0] + zf[b0 + f0 + sz];
+        const float a11 = zf[b0 + f0 + 1] + zf[b0 + f0 + 1 + sz];
+        sum = (a00 + a10) + (a01 + a11);
+      } else {
+        sum = (zf[b0] + zf[b0 + 1]) + (zf[b0 + f0] + zf[b0 + f0 + 1]);
+      }
+      zc[q] = sum;
+    }
+    __syncthreads();
+  }
+  // coarsest level: x = G z in FP64
+  {
+    const int lc = a.nl - 1;
+    const int nc = ncells(lc);
+    float* zc = level_base(lc) + D * nc;
+    float* xc = zc + nc;
+    for (int i = tid; i < nc; i += kTailThreads) {
+      double acc = 0.0;
+      for (int jj = 0; jj < nc; ++jj) acc += __ldg(a.G + (long long)jj * nc + i) * (double)zc[jj];
+      xc[i] = (float)acc;
+    }
+    __syncthreads();
+  }
+  // up: prolong (piecewise constant) and smooth each level
+  for (int l = a.nl - 2; l >= 0; --l) {
+    const int n0 = a.n[l][0], n1 = a.n[l][1], n2 = a.n[l][2];
+    const int nc = n0 * n1 * n2;
+    const int c0 = a.n[l + 1][0], c1 = a.n[l + 1][1];
+    float* b = level_base(l);
+    const float* Lc[3] = {b, b + (D > 1 ? nc : 0), b + (D > 2 ? 2 * nc : nc)};
+    const float* zl = b + D * nc;
+    float* xl = b + (D + 1) * nc;
+    const float* xcoarse = level_base(l + 1) + (D + 1) * ncells(l + 1);
+    for (int q = tid; q < nc; q += kTailThreads) {
+      const int i = q % n0, t = q / n0;
+      const int j = t % n1, k = t / n1;
+      xl[q] = 0.f + xcoarse[(i >> 1) + c0 * ((j >> 1) + c1 * (k >> 1))];
+    }
+    __syncthreads();
+    const int st[3] = {1, n0, n0 * n1};
+    const int nd[3] = {n0, n1, n2};
+    const int h0 = n0 >> 1;  // cells of one colour per row (n0 is even on every level above the coarsest)
+    const int nhalf = nc >> 1;
+    for (int sw = 0; sw < a.post; ++sw) {
+      for (int color = 0; color < 2; ++color) {
+        for (int m = tid; m < nhalf; m += kTailThreads) {
+          const int row = m / h0;
+          const int j = row % n1, k = row / n1;
+          const int i = 2 * (m - row * h0) + ((j + k + color) & 1);
+          const int q = i + n0 * row;
+          const int I[3] = {i, j, k};
+          float sum = 0.f, dg = 0.f;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            float Lu = 0.f, xu = 0.f, xd = 0.f;
+            if (I[d] + 1 < nd[d]) {
+              Lu = Lc[d][q + st[d]];
+              xu = xl[q + st[d]];
+            } else if ((a.per >> d) & 1u) {
+              Lu = Lc[d][q - (nd[d] - 1) * st[d]];
+              xu = xl[q - (nd[d] - 1) * st[d]];
+            }
+            const float Ll = Lc[d][q];
+            if (I[d] > 0)
+              xd = xl[q - st[d]];
+            else if ((a.per >> d) & 1u)
+              xd = xl[q + (nd[d] - 1) * st[d]];
+            sum = fmaf(Lu, xu, sum);
+            sum = fmaf(Ll, xd, sum);
+            dg += Lu + Ll;
+          }
+          xl[q] = (dg > 0.f) ? __fdividef(sum - zl[q], dg) : 0.f;
+        }
+        __syncthreads();
+      }
+    }
+  }
+  {
+    const int nc = ncells(0);
+    const float* x0 = level_base(0) + (D + 1) * nc;
+    for (int q = tid; q < nc; q += kTailThreads) st_st(a.x, a.st[0], q, x0[q]);
+  }
+}
+
+int launch_vcycle_tail(int D, const TailArgs& a, cudaStream_t s) {
+  const size_t smem = vcycle_tail_smem(D, a.n, a.nl);
+  static bool attr[2] = {false, false};
+  if (!attr[D - 2]) {
+    if (D == 3)
+      cudaFuncSetAttribute(k_vcycle_tail<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    else
+      cudaFuncSetAttribute(k_vcycle_tail<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    attr[D - 2] = true;
+  }
+  if (D == 3)
+    k_vcycle_tail<3><<<1, kTailThreads, smem, s>>>(a);
+  else
+    k_vcycle_tail<2><<<1, kTailThreads, smem, s>>>(a);
+  return 0;
+}
+
 // ph + pl rounded to FP32
 __global__ void k_df_round(const float* ph, const float* pl, float* out, long long n) {
   const long long q = (long long)blockIdx.x * 256 + threadIdx.x;

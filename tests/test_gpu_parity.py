@@ -320,3 +320,19 @@ def test_tma_sweep_matches_table_sweep(case, monkeypatch):
     b.step(3)
     assert np.array_equal(a.get(0), b.get(0))
     assert np.array_equal(a.get(1), b.get(1))
+
+
+@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[1], CASES_3D[2], CASES_3D[3], CASES_3D[4], CASES_2D[0],
+                                  CASES_2D[2], CASES_2D[3]], ids=lambda c: c["id"])
+def test_vcycle_tail_matches_per_level_kernels(case, monkeypatch):
+    """The small levels run in one block (k_vcycle_tail) with the same arithmetic, in the
+    same order, as the per-level restriction, dense coarsest solve and sweep kernels:
+    three steps give identical bits either way."""
+    a, _ = make_pair(case, oracle=False)
+    monkeypatch.setenv("WL_NO_TAIL", "1")
+    b, _ = make_pair(case, oracle=False)
+    monkeypatch.delenv("WL_NO_TAIL")
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.get(0), b.get(0))
+    assert np.array_equal(a.get(1), b.get(1))
