@@ -39,6 +39,8 @@ struct LevelBuf {
   float* x2;
   int st;                         // storage type ST_* of Lk, z, x, x2
   float zs;                       // z is stored scaled: stored = zs * value (a power of two)
+  BandBox band;                   // region whose coefficients may differ from uval (staged kernels)
+  float uval;                     // the level's coefficient away from the body: 2^(l (D-2))
   float* z32;                     // a 16-bit level 1: the restricted fine residual in FP32, converted
                                   // (with the scale DevState::cs_used) by level 1's restriction pass
   bool tma;                       // tensor maps below are valid (n_0 % 4 == 0)
@@ -60,6 +62,7 @@ struct wl_sim {
   wl_opts o{};
   cudaStream_t st = nullptr;  // caller's stream
   cudaStream_t cs = nullptr;  // private stream used only for graph capture
+  SideStream side{};          // second stream for the band tiles' launches (beside the uniform tiles)
   int nlev = 0;
   LevelBuf lev[kMaxLevels]{};
   float* ua[3]{};
@@ -282,6 +285,8 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, int cprec, char*
 }
 
 // ------------------------------------------------------------------- enqueue helpers
+const SideStream* side_of(wl_sim* s) { return s->side.aux ? &s->side : nullptr; }
+
 StageArgs stage_args(wl_sim* s, int stage) {
   StageArgs a{};
   for (int c = 0; c < 3; ++c) {
@@ -384,11 +389,12 @@ void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) 
       for (int d = 0; d < 3; ++d) t.cn[d] = s->lev[1].g.n[d];
       if (s->lev[1].z32) t.zc = s->lev[1].z32;  // FP32 staging of a 16-bit level 1
     }
-    const int tz = sweep_planes_per_block(L.g);
+    const int tz = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
     t.tz = tz + (tz & 1);
     t.inv_w = 1.f / w;
     t.st = s->ds;
-    PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st));
+    t.band = L.band;
+    PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st, side_of(s)));
     return;
   }
   ResArgs a = res_args(s, 0, mode);
@@ -427,7 +433,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   a.zmul = 1.f / L.zs;
   // the coarse levels' values carry the factor 2^cs_used; the fine level removes it
   if (l == 0 && s->lev[1].z32) a.cs = s->ds;
-  a.tz = sweep_planes_per_block(L.g);
+  a.tz = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
   float* bufs[2] = {L.x, L.x2};
   const CUtensorMap* bmaps[2] = {&L.mx, &L.mx2};
   const bool from_x = (l == 0 && !refine);  // precision 0: the fine iterate is the pressure itself
@@ -452,6 +458,8 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       t.xc = a.xc;
       t.xctype = a.xctype;
       t.xc_cs = a.cs != nullptr;
+      t.band = L.band;
+      t.uval = L.uval;
       t.x_out = a.x_out;
       t.ph = a.ph;
       t.pl = a.pl;
@@ -459,7 +467,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       for (int d = 0; d < 3; ++d) t.cn[d] = a.cn[d];
       t.tz = a.tz;
       t.st = s->ds;
-      PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st));
+      PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st, side_of(s)));
       a.only_wrapping = 1;  // tiles crossing a periodic side
       if (L.g.per) PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
     } else {
@@ -782,6 +790,34 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   }
   s->ws_bytes = need;
   layout(s, ndim, dims, o.precision, o.coarse_precision, s->ws);
+  // Staged kernels: tiles away from the body take the variant that forms the face
+  // coefficients (the level's free-stream value 2^(l (D-2)), 0 on walls) instead of
+  // loading them.  The band box (faces with mu0 < 1 lie inside it) scaled to each level,
+  // one cell wider; without a body every tile is uniform.  The band tiles then run as a
+  // second launch beside the uniform one; measured, that pays only where they are a small
+  // part of the level (<= 5 % of its tiles: the fine level of large grids), so other
+  // levels load every coefficient.
+  {
+    int lo[3], hi[3];
+    const bool body = stage_band_box(ndim, s->g, s->body, lo, hi);
+    const bool split = !std::getenv("WL_NO_UNIFORM");
+    const double frac_max = std::getenv("WL_UNIFORM_ALL") ? 2.0 : 0.05;  // WL_UNIFORM_ALL: split every level
+    for (int l = 0; l < s->nlev; ++l) {
+      LevelBuf& L = s->lev[l];
+      L.uval = ldexpf(1.f, l * (ndim - 2));
+      for (int d = 0; d < 3; ++d) {
+        if (body) {
+          L.band.lo[d] = (lo[d] >> l) - 1;
+          L.band.hi[d] = ((hi[d] + (1 << l) - 1) >> l) + 1;
+        } else {  // empty box
+          L.band.lo[d] = 1 << 30;
+          L.band.hi[d] = -(1 << 30);
+        }
+      }
+      const int tz = sweep_planes_per_block(L.g, SWEEP_UNI_BLOCKS_PER_SM);
+      L.band.on = (split && band_tile_fraction(ndim, L.g, tz, L.band) <= frac_max) ? 1 : 0;
+    }
+  }
   // The coarse end of the V-cycle runs in one block from the largest level whose
   // hierarchy below holds at most kTailCells cells (the coarsest solved densely; a
   // 16-bit level 1 keeps its staged conversion, so the tail starts at level 2 or below).
@@ -804,6 +840,9 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   int rc = WL_OK;
   if (cudaMallocHost(&s->hs, sizeof(DevState)) != cudaSuccess) rc = fail(s, WL_ENOMEM, "pinned host state");
   if (!rc) rc = cuda_check(s, cudaStreamCreateWithFlags(&s->cs, cudaStreamNonBlocking), "capture stream");
+  if (!rc) rc = cuda_check(s, cudaStreamCreateWithFlags(&s->side.aux, cudaStreamNonBlocking), "side stream");
+  if (!rc) rc = cuda_check(s, cudaEventCreateWithFlags(&s->side.fork, cudaEventDisableTiming), "side event");
+  if (!rc) rc = cuda_check(s, cudaEventCreateWithFlags(&s->side.join, cudaEventDisableTiming), "side event");
   if (!rc && !std::getenv("WL_NO_TMA")) {  // tensor maps for the staged sweep
     for (int l = 0; l < s->nlev; ++l) {
       LevelBuf& L = s->lev[l];
@@ -879,6 +918,9 @@ void wl_destroy(wl_handle s) {
   if (s->graph) cudaGraphDestroy(s->graph);
   if (s->join) cudaEventDestroy(s->join);
   if (s->cs) cudaStreamDestroy(s->cs);
+  if (s->side.aux) cudaStreamDestroy(s->side.aux);
+  if (s->side.fork) cudaEventDestroy(s->side.fork);
+  if (s->side.join) cudaEventDestroy(s->side.join);
   if (s->hs) cudaFreeHost(s->hs);
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->gr.own && s->gr.mem) cudaFree(s->gr.mem);

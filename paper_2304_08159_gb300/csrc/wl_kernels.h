@@ -74,6 +74,16 @@ struct SweepArgs {
   int only_wrapping;   // 1: sweep only the tiles whose footprint crosses a periodic side
 };
 
+// Region of a level (level cell coordinates, [lo, hi) per direction) whose face
+// coefficients may differ from the level's free-stream value: the body's band box
+// scaled to the level.  Tiles whose footprint misses it take the staged kernels'
+// uniform variants, which compute the coefficients (free-stream value, 0 on walls)
+// instead of loading them.  on = 0: no split, every tile loads its coefficients.
+struct BandBox {
+  int on;
+  int lo[3], hi[3];
+};
+
 // TMA-staged sweep (wl_sweep_tma.cu): tensor maps of the fields of one level
 // (box 72 x 12 [x 1], x start 16-byte aligned, zero fill out of range).
 struct SweepMaps {
@@ -91,6 +101,9 @@ struct SweepTmaArgs {
   int cn[3];
   int tz;
   DevState* st;        // status bit 2 set if a staged copy never arrived
+  BandBox band;        // tiles outside it: coefficients = uval (0 on walls), not loaded
+  float uval;
+  int t0[3];           // first tile of the launch (the band tiles' launch starts inside the grid)
 };
 
 // Dense pseudo-inverse of the coarsest operator (column-major, FP64), used when the
@@ -152,7 +165,15 @@ int launch_stage(int D, const StageArgs& a, cudaStream_t s);
 int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s);
 int launch_residual(int D, const ResArgs& a, cudaStream_t s);
 int launch_sweep(int D, const SweepArgs& a, cudaStream_t s);
-int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s);
+// A second stream on which the loading (band) tiles' launch runs beside the uniform
+// tiles' launch (fork / join by events; captured as parallel graph branches).
+struct SideStream {
+  cudaStream_t aux;
+  cudaEvent_t fork, join;
+};
+int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s, const SideStream* side);
+// fraction of a level's sweep tiles (tz planes per block) that meet the band box
+double band_tile_fraction(int D, const Grid& g, int tz, const BandBox& b);
 
 // TMA-staged fine residual / divergence (3-D, levels with no periodic side)
 struct ResidMaps {
@@ -171,10 +192,13 @@ struct ResidTmaArgs {
   int tz;              // planes per block (even)
   float inv_w;
   DevState* st;        // dt, residual maximum, timeout flag
+  BandBox band;        // tiles outside it: coefficients 1 (0 on walls), not loaded
+  int t0[3];           // first tile of the launch
 };
-int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s);
+int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s, const SideStream* side);
 int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s);
-int sweep_planes_per_block(const Grid& g);
+// planes per block of the sweep kernels for blocks_per_sm resident blocks
+int sweep_planes_per_block(const Grid& g, int blocks_per_sm);
 
 // Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.
 // A tile "wraps" when its TMA footprint (x i0-4..i0+67, y j0-2..j0+9, planes
@@ -183,8 +207,19 @@ int sweep_planes_per_block(const Grid& g);
 constexpr int SWEEP_TX = 64, SWEEP_TY = 8;
 // rows of the sweep's coefficient boxes (z, L0, L2; L1 takes one more), from j0-1
 constexpr int SWEEP_CROWS = SWEEP_TY + 2;
-// resident blocks per SM of the staged sweep (shared memory bound)
+// resident blocks per SM of the staged sweep (shared memory bound) and of its uniform
+// variant (register bound)
 constexpr int SWEEP_BLOCKS_PER_SM = 4;
+constexpr int SWEEP_UNI_BLOCKS_PER_SM = 6;
+// The tile's staged footprint (x i0-4..i0+67, y j0-2..j0+9, planes k0-2..k1+1)
+// meets the band box (always true without a split).
+__host__ __device__ inline bool tile_in_band(const BandBox& b, int D, int i0, int j0, int k0, int k1) {
+  if (!b.on) return true;
+  if (i0 - 4 >= b.hi[0] || i0 + SWEEP_TX + 4 <= b.lo[0]) return false;
+  if (j0 - 2 >= b.hi[1] || j0 + SWEEP_TY + 2 <= b.lo[1]) return false;
+  if (D == 3 && (k0 - 2 >= b.hi[2] || k1 + 2 <= b.lo[2])) return false;
+  return true;
+}
 __host__ __device__ inline bool sweep_tile_wraps(const Grid& g, int D, int i0, int j0, int k0, int k1) {
   if ((g.per & 1u) && (i0 - 4 < 0 || i0 + SWEEP_TX + 4 > g.n[0])) return true;
   if ((g.per & 2u) && (j0 - 2 < 0 || j0 + SWEEP_TY + 2 > g.n[1])) return true;

@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 // Planes per block of both sweep kernels: the z-blocking that minimises the modelled
 // time, whole waves of blocks (SWEEP_BLOCKS_PER_SM resident per SM) times the planes a block
 // marches through plus about 1.5 planes of prologue and epilogue work.
-int sweep_planes_per_block(const Grid& g) {
+int sweep_planes_per_block(const Grid& g, int blocks_per_sm) {
   static int nsm = 0;
   if (nsm <= 0) {
     int dev = 0;
@@ -441,7 +441,7 @@ int sweep_planes_per_block(const Grid& g) {
     }
   }
   const long long tiles = (long long)((g.n[0] + SW_TX - 1) / SW_TX) * ((g.n[1] + SW_TY - 1) / SW_TY);
-  const long long wave = (long long)SWEEP_BLOCKS_PER_SM * nsm;
+  const long long wave = (long long)blocks_per_sm * nsm;
   int best = 2;
   double best_cost = 1e300;
   for (int tz = 2; tz <= 32; ++tz) {

@@ -18,6 +18,8 @@
 // left to k_sweep.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "wl_dev.cuh"
 #include "wl_kernels.h"
 
@@ -113,22 +115,29 @@ __device__ __forceinline__ void sts(uint32_t a, float v) { asm volatile("st.shar
 
 }  // namespace
 
-template <int D>
-__global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
+// UNI: the variant for tiles outside the level's band box, whose face coefficients are
+// the level's free-stream value uval (0 on the walls): only the iterate and the
+// right-hand side are staged, the coefficients are formed from the cell's position
+// (same values, same operation order, same bits), and the smaller rings fit more
+// blocks per SM.
+template <int D, bool UNI>
+__global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM)
     k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
   extern __shared__ float smf[];
   // 128-byte aligned slot rings (iterate, L2, z, L0, L1), then the mbarriers, all
   // addressed by 32-bit float offsets into smf
   const int ox = (int)(((128u - (smem_addr(smf) & 127u)) & 127u) >> 2);
-  constexpr int O_L2 = XR * BOX, O_Z = O_L2 + L2R * CSLOT, O_L0 = O_Z + CR * CSLOT, O_L1 = O_L0 + CR * CSLOT,
-                O_BAR = O_L1 + CR * L1SLOT;
+  constexpr int O_L2 = XR * BOX, O_Z = O_L2 + (UNI ? 0 : L2R * CSLOT), O_L0 = O_Z + CR * CSLOT,
+                O_L1 = O_L0 + (UNI ? 0 : CR * CSLOT), O_BAR = O_L1 + (UNI ? 0 : CR * L1SLOT);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smf + ox + O_BAR);
   const Grid& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
+  const int i0 = (blockIdx.x + a.t0[0]) * TX, j0 = (blockIdx.y + a.t0[1]) * TY;
+  const int k0 = (D == 3) ? (blockIdx.z + a.t0[2]) * a.tz : 0;
+  if (i0 >= g.n[0] || j0 >= g.n[1] || k0 >= g.n[2]) return;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
   if (sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
+  if (tile_in_band(a.band, D, i0, j0, k0, k1) == UNI) return;  // the other variant's tile
   // Ring slots: iterate plane p lives in slot (p - k0 + 2) mod XR, coefficient plane
   // p in slot (p - k0 + 1) mod L2R (L2) or mod CR (z, L0, L1).
   auto Xs = [&](int s) { return ox + s * BOX; };
@@ -163,9 +172,15 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   constexpr uint32_t kXB = BOX * 4, kCB = BX * CROWS * 4, kL1B = BX * L1ROWS * 4;
   int b_issued = k0 - 1;  // (thread 0) last bundle staged
   // bundle b (waited at the start of iteration b): iterate and L2 of plane b+2,
-  // z, L0, L1 of plane b+1
+  // z, L0, L1 of plane b+1 (UNI: iterate and z)
   auto issue_bundle = [&](int b) {
     b_issued = b;
+    if (UNI) {
+      mbar_expect_tx(bbar(b), (a.has_x ? kXB : 0u) + kCB);
+      if (a.has_x) ld_x(b + 2, bbar(b));
+      tma_load(sa(Zs(cslot(b + 1))), &m.z, i0 - 4, j0 - 1, b + 1, bbar(b), D);
+      return;
+    }
     mbar_expect_tx(bbar(b), (a.has_x ? kXB : 0u) + 3 * kCB + kL1B);
     if (a.has_x) ld_x(b + 2, bbar(b));
     ld_l2(b + 2, bbar(b));
@@ -211,6 +226,47 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   // Gauss-Seidel value of the cell at shared byte offset e (all operands staged;
   // out-of-range faces carry 0, so cells outside the grid come out as 0).
   // Same operation order as k_sweep (upper then lower face; x, y, z), same bits.
+  // UNI: coefficients from the cell's position.  mxy: bit 0/1 lower/upper x face
+  // present, 2/3 lower/upper y face, 4 cell inside the grid in x and y; zlo/zhi: lower /
+  // upper z face present, kin: plane inside the grid.
+  const float uv = a.uval;
+  auto relax_uni = [&](const Planes& P, uint32_t e, uint32_t mxy, bool zlo, bool zhi, bool kin) -> float {
+    if (!(mxy & 16u) || !kin) return 0.f;  // outside the grid: every face reads 0 -> 0
+    const uint32_t x0 = P.x0 + e;
+    const float l0u = (mxy & 2u) ? uv : 0.f, l0d = (mxy & 1u) ? uv : 0.f;
+    const float l1u = (mxy & 8u) ? uv : 0.f, l1d = (mxy & 4u) ? uv : 0.f;
+    float sum = fmaf(l0u, lds<4>(x0), 0.f);
+    sum = fmaf(l0d, lds<-4>(x0), sum);
+    float dg = l0u + l0d;
+    sum = fmaf(l1u, lds<4 * BX>(x0), sum);
+    sum = fmaf(l1d, lds<-4 * BX>(x0), sum);
+    dg += l1u + l1d;
+    if (D == 3) {
+      const float lu = zhi ? uv : 0.f, ll = zlo ? uv : 0.f;
+      sum = fmaf(lu, lds(P.xp + e), sum);
+      sum = fmaf(ll, lds(P.xm + e), sum);
+      dg += lu + ll;
+    }
+    return (dg > 0.f) ? __fdividef(sum - lds(P.z + e), dg) : 0.f;
+  };
+  // UNI tile that touches no wall (every cell it relaxes, halo included, has all its
+  // faces): each coefficient is uv, so the relaxation is the same FMA chain with uv
+  // and the diagonal the constant 2D uv (the same bits as relax_uni)
+  const bool interior = UNI && i0 >= 4 && i0 + TX + 4 <= g.n[0] && j0 >= 2 && j0 + TY + 2 <= g.n[1] &&
+                        (D == 2 || (k0 >= 2 && k1 + 2 <= g.n[2]));
+  const float dg_int = D == 3 ? (uv + uv) + (uv + uv) + (uv + uv) : (uv + uv) + (uv + uv);
+  auto relax_fast = [&](const Planes& P, uint32_t e) -> float {
+    const uint32_t x0 = P.x0 + e;
+    float sum = fmaf(uv, lds<4>(x0), 0.f);
+    sum = fmaf(uv, lds<-4>(x0), sum);
+    sum = fmaf(uv, lds<4 * BX>(x0), sum);
+    sum = fmaf(uv, lds<-4 * BX>(x0), sum);
+    if (D == 3) {
+      sum = fmaf(uv, lds(P.xp + e), sum);
+      sum = fmaf(uv, lds(P.xm + e), sum);
+    }
+    return __fdividef(sum - lds(P.z + e), dg_int);
+  };
   auto relax = [&](const Planes& P, uint32_t e) -> float {
     const uint32_t x0 = P.x0 + e, l0 = P.l0 + e, l1 = P.l1 + e;
     const float l0u = lds<4>(l0), l0d = lds(l0), l1u = lds<4 * BX>(l1), l1d = lds(l1);
@@ -235,6 +291,13 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   // eight tasks, w and (w < 3) w+5.  Shared byte offsets into the iterate box, for
   // even and odd planes.
   uint32_t er[2][2], eb[2][2], ee[2];
+  uint32_t mr[2][2], mb[2][2], me[2];  // UNI: face masks of each task's cell (relax_uni)
+  auto xymask = [&](int col, int row) -> uint32_t {
+    const int gi = i0 + col, gj = j0 + row;
+    const bool px = is_per(g, 0), py = is_per(g, 1);
+    return (gi > 0 || px ? 1u : 0u) | (gi + 1 < g.n[0] || px ? 2u : 0u) | (gj > 0 || py ? 4u : 0u) |
+           (gj + 1 < g.n[1] || py ? 8u : 0u) | (gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] ? 16u : 0u);
+  };
   {
     const int ib0 = 2 * (lane & 15);
 #pragma unroll
@@ -244,18 +307,57 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
       const int ib = 32 * (t & 1) + ib0;
 #pragma unroll
       for (int par = 0; par < 2; ++par) {
-        er[h][par] = 4u * ((jr + 2) * BX + ib + ((i0 + j0 + jr + par) & 1) + 4);
-        eb[h][par] = 4u * ((jb + 2) * BX + ib + ((i0 + j0 + jb + par + 1) & 1) + 4);
+        const int cr = ib + ((i0 + j0 + jr + par) & 1), cb = ib + ((i0 + j0 + jb + par + 1) & 1);
+        er[h][par] = 4u * ((jr + 2) * BX + cr + 4);
+        eb[h][par] = 4u * ((jb + 2) * BX + cb + 4);
+        if (UNI) {
+          mr[h][par] = xymask(cr, jr);
+          mb[h][par] = xymask(cb, jb);
+        }
       }
     }
     const int je = (warp == 3) ? lane - 1 : lane + 4;
 #pragma unroll
-    for (int par = 0; par < 2; ++par) ee[par] = 4u * ((je + 2) * BX + (((i0 + j0 + je + par) & 1) ? -1 : 64) + 4);
+    for (int par = 0; par < 2; ++par) {
+      const int ce = ((i0 + j0 + je + par) & 1) ? -1 : 64;
+      ee[par] = 4u * ((je + 2) * BX + ce + 4);
+      if (UNI) me[par] = xymask(ce, je);
+    }
   }
+  // UNI: z faces and range of plane kk
+  auto zmask = [&](int kk, bool& zlo, bool& zhi, bool& kin) {
+    const bool pz = D == 3 && is_per(g, 2);
+    zlo = kk > 0 || pz;
+    zhi = kk + 1 < g.n[2] || pz;
+    kin = kk >= 0 && kk < g.n[2];
+  };
   const bool has_edge = warp >= 3 && lane < 5, two_black = warp < 3;
-  // red cells of the plane whose operands are P (parity par)
-  auto red_plane = [&](const Planes& P, int par) {
+  // red cells of plane kk (parity par) whose operands are P
+  auto red_plane = [&](const Planes& P, int par, int kk) {
     const uint32_t e0 = par ? er[0][1] : er[0][0], e1 = par ? er[1][1] : er[1][0];
+    if (UNI && interior) {
+      const float v0 = relax_fast(P, e0), v1 = relax_fast(P, e1);
+      sts(P.x0 + e0, v0);
+      sts(P.x0 + e1, v1);
+      if (has_edge) {
+        const uint32_t f = par ? ee[1] : ee[0];
+        sts(P.x0 + f, relax_fast(P, f));
+      }
+      return;
+    }
+    if (UNI) {
+      bool zlo, zhi, kin;
+      zmask(kk, zlo, zhi, kin);
+      const float v0 = relax_uni(P, e0, par ? mr[0][1] : mr[0][0], zlo, zhi, kin);
+      const float v1 = relax_uni(P, e1, par ? mr[1][1] : mr[1][0], zlo, zhi, kin);
+      sts(P.x0 + e0, v0);
+      sts(P.x0 + e1, v1);
+      if (has_edge) {
+        const uint32_t f = par ? ee[1] : ee[0];
+        sts(P.x0 + f, relax_uni(P, f, par ? me[1] : me[0], zlo, zhi, kin));
+      }
+      return;
+    }
     const float v0 = relax(P, e0), v1 = relax(P, e1);
     sts(P.x0 + e0, v0);
     sts(P.x0 + e1, v1);
@@ -264,9 +366,35 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
       sts(P.x0 + f, relax(P, f));
     }
   };
-  // black cells of the plane whose operands are P (parity par)
-  auto black_plane = [&](const Planes& P, int par) {
+  // black cells of plane kk (parity par) whose operands are P
+  auto black_plane = [&](const Planes& P, int par, int kk) {
     const uint32_t e0 = par ? eb[0][1] : eb[0][0];
+    if (UNI && interior) {
+      if (two_black) {
+        const uint32_t e1 = par ? eb[1][1] : eb[1][0];
+        const float v0 = relax_fast(P, e0), v1 = relax_fast(P, e1);
+        sts(P.x0 + e0, v0);
+        sts(P.x0 + e1, v1);
+      } else {
+        sts(P.x0 + e0, relax_fast(P, e0));
+      }
+      return;
+    }
+    if (UNI) {
+      bool zlo, zhi, kin;
+      zmask(kk, zlo, zhi, kin);
+      const uint32_t m0 = par ? mb[0][1] : mb[0][0];
+      if (two_black) {
+        const uint32_t e1 = par ? eb[1][1] : eb[1][0];
+        const float v0 = relax_uni(P, e0, m0, zlo, zhi, kin);
+        const float v1 = relax_uni(P, e1, par ? mb[1][1] : mb[1][0], zlo, zhi, kin);
+        sts(P.x0 + e0, v0);
+        sts(P.x0 + e1, v1);
+      } else {
+        sts(P.x0 + e0, relax_uni(P, e0, m0, zlo, zhi, kin));
+      }
+      return;
+    }
     if (two_black) {
       const uint32_t e1 = par ? eb[1][1] : eb[1][0];
       const float v0 = relax(P, e0), v1 = relax(P, e1);
@@ -344,12 +472,20 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   if (tid == 0) {
     const int ncp = (D == 3) ? 2 : 1, nl2 = (D == 3) ? 3 : 0;
     const uint32_t b0 = smem_addr(&bars[0]);
-    mbar_expect_tx(b0, (a.has_x ? (uint32_t)(phi - plo + 1) * kXB : 0u) + (uint32_t)ncp * (2 * kCB + kL1B) +
-                           (uint32_t)nl2 * kCB);
+    if (UNI)
+      mbar_expect_tx(b0, (a.has_x ? (uint32_t)(phi - plo + 1) * kXB : 0u) + (uint32_t)ncp * kCB);
+    else
+      mbar_expect_tx(b0, (a.has_x ? (uint32_t)(phi - plo + 1) * kXB : 0u) + (uint32_t)ncp * (2 * kCB + kL1B) +
+                             (uint32_t)nl2 * kCB);
     if (a.has_x)
       for (int p = plo; p <= phi; ++p) ld_x(p, b0);
-    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 : 0); ++p) ld_c(p, b0);
-    if (D == 3)
+    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 : 0); ++p) {
+      if (UNI)
+        tma_load(sa(Zs(cslot(p))), &m.z, i0 - 4, j0 - 1, p, b0, D);
+      else
+        ld_c(p, b0);
+    }
+    if (D == 3 && !UNI)
       for (int p = k0 - 1; p <= k0 + 1; ++p) ld_l2(p, b0);
     if (D == 3)
       for (int b = k0; b < k0 + LEAD && b <= k1 - 1; ++b) issue_bundle(b);
@@ -365,15 +501,15 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
   if constexpr (D == 2) {
     prefetch(0);
     const Planes P = planes_of(0);
-    red_plane(P, 0);
+    red_plane(P, 0, 0);
     __syncthreads();
-    black_plane(P, 0);
+    black_plane(P, 0, 0);
     __syncthreads();
     store(Xs(xslot(0)), 0);
     return;
   } else {
   // red cells of planes k0-1 and k0 (independent of each other)
-  for (int p = k0 - 1; p <= k0; ++p) red_plane(planes_of(p), p & 1);
+  for (int p = k0 - 1; p <= k0; ++p) red_plane(planes_of(p), p & 1, p);
   prefetch(k0);
 
   // ---- iteration k: red cells of plane k+1, then black cells of plane k, and the
@@ -402,9 +538,9 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
     const int sx1 = sx + 1 < XR ? sx + 1 : 0;
     const int sl1 = sl + 1 < L2R ? sl + 1 : 0;
     const int sc1 = sc + 1 < CR ? sc + 1 : 0;
-    red_plane(planes(sx1, sl1, sc1), par ^ 1);
+    red_plane(planes(sx1, sl1, sc1), par ^ 1, k + 1);
     __syncthreads();
-    black_plane(planes(sx, sl, sc), par);
+    black_plane(planes(sx, sl, sc), par, k);
     sx = sx1;
     sl = sl1;
     sc = sc1;
@@ -428,20 +564,22 @@ __global__ void __launch_bounds__(SW_NT, SWEEP_BLOCKS_PER_SM)
 // walls; the velocity on an upper wall face is the boundary value, patched explicitly.
 constexpr int RS_P = 736, RS_8 = 576, RS_9 = 672;  // slot floats: 72 x 10, 72 x 8, 72 x 9 (128-byte multiples)
 constexpr int RS_PROWS = TY + 2, RS_8ROWS = TY, RS_9ROWS = TY + 1;
-template <bool DIV, bool DF>
+// UNI: tiles outside the band box, whose coefficients are 1 (0 on the walls): the
+// coefficient fields are neither staged nor kept.
+template <bool DIV, bool DF, bool UNI>
 struct ResidLayout {
   // column slot: ph, [pl], L2, [u2]; plane slot: DIV: u0, u1, L0, L1; else z, L0, L1
-  static constexpr int oPL = RS_P, oL2 = RS_P * (DF ? 2 : 1), oU2 = oL2 + RS_8;
+  static constexpr int oPL = RS_P, oL2 = RS_P * (DF ? 2 : 1), oU2 = oL2 + (UNI ? 0 : RS_8);
   static constexpr int ASZ = oU2 + (DIV ? RS_8 : 0);
   static constexpr int oU0 = 0, oU1 = RS_8, oL0 = DIV ? RS_8 + RS_9 : RS_8, oL1 = oL0 + RS_8, oZ = 0;
-  static constexpr int BSZ = oL1 + RS_9;
+  static constexpr int BSZ = UNI ? oL0 : oL1 + RS_9;
   static constexpr int SA = 4, SB = 3, NBAR = 4;
   static constexpr size_t bytes = ((size_t)SA * ASZ + (size_t)SB * BSZ) * sizeof(float);
 };
 
-template <bool DIV, bool DF>
-__global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ ResidMaps m, ResidTmaArgs a) {
-  using LY = ResidLayout<DIV, DF>;
+template <bool DIV, bool DF, bool UNI>
+__global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_constant__ ResidMaps m, ResidTmaArgs a) {
+  using LY = ResidLayout<DIV, DF, UNI>;
   constexpr int SA = LY::SA, SB = LY::SB, NBAR = LY::NBAR;
   extern __shared__ unsigned char smem_raw[];
   float* abase = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -451,8 +589,11 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
   __shared__ unsigned s_m[8];
   const Grid& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int kb = blockIdx.z * a.tz, ke = min(kb + a.tz, g.n[2]);
+  const int i0 = (blockIdx.x + a.t0[0]) * TX, j0 = (blockIdx.y + a.t0[1]) * TY;
+  const int kb = (blockIdx.z + a.t0[2]) * a.tz;
+  if (i0 >= g.n[0] || j0 >= g.n[1] || kb >= g.n[2]) return;
+  const int ke = min(kb + a.tz, g.n[2]);
+  if (tile_in_band(a.band, 3, i0, j0, kb, ke) == UNI) return;  // the other variant's tile
   const int pa_first = kb - 1, pb_first = kb, p_last = ke;
   // column slot / plane slot of plane p (fields at the LY offsets)
   auto A = [&](int p) -> float* { return abase + (size_t)((p - pa_first) % SA) * LY::ASZ; };
@@ -471,15 +612,15 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
     if (p > p_last) return;
     p_issued = p;
     const bool plane = p >= pb_first && p < ke;
-    const uint32_t col = (DF ? 2 : 1) * kPB + k8B + (DIV ? k8B : 0);
-    const uint32_t pln = DIV ? (k8B + k9B + k8B + k9B) : (k8B + k8B + k9B);
+    const uint32_t col = (DF ? 2 : 1) * kPB + (UNI ? 0u : k8B) + (DIV ? k8B : 0);
+    const uint32_t pln = (DIV ? k8B + k9B : k8B) + (UNI ? 0u : k8B + k9B);
     const uint32_t br = bar(p);
     mbar_expect_tx(br, col + (plane ? pln : 0u));
     const int x = i0 - 4;
     float* Ap = A(p);
     tma_load(smem_addr(Ap), &m.ph, x, j0 - 1, p, br, 3);
     if (DF) tma_load(smem_addr(Ap + LY::oPL), &m.pl, x, j0 - 1, p, br, 3);
-    tma_load(smem_addr(Ap + LY::oL2), &m.L2, x, j0, p, br, 3);
+    if (!UNI) tma_load(smem_addr(Ap + LY::oL2), &m.L2, x, j0, p, br, 3);
     if (DIV) tma_load(smem_addr(Ap + LY::oU2), &m.u2, x, j0, p, br, 3);
     if (plane) {
       float* Bp = B(p);
@@ -489,8 +630,10 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
       } else {
         tma_load(smem_addr(Bp + LY::oZ), &m.z, x, j0, p, br, 3);
       }
-      tma_load(smem_addr(Bp + LY::oL0), &m.L0, x, j0, p, br, 3);
-      tma_load(smem_addr(Bp + LY::oL1), &m.L1, x, j0, p, br, 3);
+      if (!UNI) {
+        tma_load(smem_addr(Bp + LY::oL0), &m.L0, x, j0, p, br, 3);
+        tma_load(smem_addr(Bp + LY::oL1), &m.L1, x, j0, p, br, 3);
+      }
     }
   };
   auto bail = [&](int p_fail) {
@@ -557,6 +700,23 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
       } else {
         z = (B0 + LY::oZ)[c];
       }
+      // face coefficients: staged, or (UNI) 1 inside the grid and 0 across a wall
+      float cxu, cxd, cyu, cyd, czu, czd;
+      if (UNI) {
+        cxu = gi + 1 < g.n[0] ? 1.f : 0.f;
+        cxd = gi > 0 ? 1.f : 0.f;
+        cyu = gj + 1 < g.n[1] ? 1.f : 0.f;
+        cyd = gj > 0 ? 1.f : 0.f;
+        czu = k + 1 < g.n[2] ? 1.f : 0.f;
+        czd = k > 0 ? 1.f : 0.f;
+      } else {
+        cxu = L0[c + 1];
+        cxd = L0[c];
+        cyu = L1[c + BX];
+        cyd = L1[c];
+        czu = L2u[c];
+        czd = L2[c];
+      }
       float r;
       if (DF) {
         const float h0 = ph0[e], l0 = pl0[e];
@@ -572,21 +732,21 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ Resid
           al += sl + tl;
         };
         // a missing neighbour across a wall reads 0 with a 0 coefficient: adds exactly 0
-        face(L0[c + 1], ph0[e + 1], pl0[e + 1]);
-        face(L0[c], ph0[e - 1], pl0[e - 1]);
-        face(L1[c + BX], ph0[e + BX], pl0[e + BX]);
-        face(L1[c], ph0[e - BX], pl0[e - BX]);
-        face(L2u[c], php[e], plp[e]);
-        face(L2[c], phm[e], plm[e]);
+        face(cxu, ph0[e + 1], pl0[e + 1]);
+        face(cxd, ph0[e - 1], pl0[e - 1]);
+        face(cyu, ph0[e + BX], pl0[e + BX]);
+        face(cyd, ph0[e - BX], pl0[e - BX]);
+        face(czu, php[e], plp[e]);
+        face(czd, phm[e], plm[e]);
         float rh, rl;
         two_sum(z, -ah, rh, rl);
         r = rh + (rl - al);
       } else {
         const float x0 = ph0[e];
         float acc = 0.f;
-        acc += L0[c + 1] * (ph0[e + 1] - x0) + L0[c] * (ph0[e - 1] - x0);
-        acc += L1[c + BX] * (ph0[e + BX] - x0) + L1[c] * (ph0[e - BX] - x0);
-        acc += L2u[c] * (php[e] - x0) + L2[c] * (phm[e] - x0);
+        acc += cxu * (ph0[e + 1] - x0) + cxd * (ph0[e - 1] - x0);
+        acc += cyu * (ph0[e + BX] - x0) + cyd * (ph0[e - BX] - x0);
+        acc += czu * (php[e] - x0) + czd * (phm[e] - x0);
         r = z - acc;
       }
       if (in) {
@@ -633,51 +793,168 @@ int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s) {
   return 0;
 }
 
-size_t resid_tma_smem(bool div, bool df) {
-  const size_t b = div ? (df ? ResidLayout<true, true>::bytes : ResidLayout<true, false>::bytes)
-                       : (df ? ResidLayout<false, true>::bytes : ResidLayout<false, false>::bytes);
-  return b + ResidLayout<false, false>::NBAR * sizeof(uint64_t) + 128;
+// tiles [lo, hi) along one direction whose footprint [t*w - pad_lo, t*w + w + pad_hi)
+// (clamped by n for the z march) meets the band box [blo, bhi)
+static void band_tiles(int n, int w, int pad, int blo, int bhi, int& lo, int& hi) {
+  const int nt = (n + w - 1) / w;
+  lo = nt;
+  hi = 0;
+  for (int t = 0; t < nt; ++t) {
+    const int a0 = t * w, a1 = std::min(a0 + w, n);
+    if (a0 - pad < bhi && a1 + pad > blo) {
+      lo = std::min(lo, t);
+      hi = t + 1;
+    }
+  }
 }
 
-int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s) {
-  const Grid& g = a.g;
-  const bool div = a.div != 0, df = a.df != 0;
-  const size_t smem = resid_tma_smem(div, df);
-  dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-  if (div && df) {
-    cudaFuncSetAttribute(k_resid_tma<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_resid_tma<true, true><<<grd, 256, smem, s>>>(m, a);
-  } else if (div) {
-    cudaFuncSetAttribute(k_resid_tma<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_resid_tma<true, false><<<grd, 256, smem, s>>>(m, a);
-  } else if (df) {
-    cudaFuncSetAttribute(k_resid_tma<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_resid_tma<false, true><<<grd, 256, smem, s>>>(m, a);
+double band_tile_fraction(int D, const Grid& g, int tz, const BandBox& b) {
+  int lo[3], hi[3];
+  band_tiles(g.n[0], TX, 4, b.lo[0], b.hi[0], lo[0], hi[0]);
+  band_tiles(g.n[1], TY, 2, b.lo[1], b.hi[1], lo[1], hi[1]);
+  if (D == 3)
+    band_tiles(g.n[2], tz, 2, b.lo[2], b.hi[2], lo[2], hi[2]);
+  else {
+    lo[2] = 0;
+    hi[2] = 1;
+  }
+  const double all = (double)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) *
+                     (D == 3 ? (g.n[2] + tz - 1) / tz : 1);
+  double band = 1.0;
+  for (int d = 0; d < 3; ++d) band *= std::max(0, hi[d] - lo[d]);
+  return band / all;
+}
+
+template <bool DIV, bool DF, bool UNI>
+void launch_resid_tma_v(const ResidMaps& m, const ResidTmaArgs& a, dim3 grd, cudaStream_t s) {
+  const size_t smem = ResidLayout<DIV, DF, UNI>::bytes + ResidLayout<DIV, DF, UNI>::NBAR * sizeof(uint64_t) + 128;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_resid_tma<DIV, DF, UNI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_resid_tma<DIV, DF, UNI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    attr = true;
+  }
+  k_resid_tma<DIV, DF, UNI><<<grd, 256, smem, s>>>(m, a);
+}
+template <bool UNI>
+void launch_resid_tma_u(const ResidMaps& m, const ResidTmaArgs& a, dim3 grd, cudaStream_t s) {
+  if (a.div && a.df)
+    launch_resid_tma_v<true, true, UNI>(m, a, grd, s);
+  else if (a.div)
+    launch_resid_tma_v<true, false, UNI>(m, a, grd, s);
+  else if (a.df)
+    launch_resid_tma_v<false, true, UNI>(m, a, grd, s);
+  else
+    launch_resid_tma_v<false, false, UNI>(m, a, grd, s);
+}
+
+int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a0, cudaStream_t s, const SideStream* side) {
+  const Grid& g = a0.g;
+  ResidTmaArgs a = a0;
+  a.t0[0] = a.t0[1] = a.t0[2] = 0;
+  const dim3 full((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
+  if (!a.band.on) {
+    launch_resid_tma_u<false>(m, a, full, s);
+    return 0;
+  }
+  int lo[3], hi[3];
+  band_tiles(g.n[0], TX, 4, a.band.lo[0], a.band.hi[0], lo[0], hi[0]);
+  band_tiles(g.n[1], TY, 2, a.band.lo[1], a.band.hi[1], lo[1], hi[1]);
+  band_tiles(g.n[2], a.tz, 2, a.band.lo[2], a.band.hi[2], lo[2], hi[2]);
+  if (hi[0] <= lo[0] || hi[1] <= lo[1] || hi[2] <= lo[2]) {
+    launch_resid_tma_u<true>(m, a, full, s);
+    return 0;
+  }
+  ResidTmaArgs b = a;
+  for (int d = 0; d < 3; ++d) b.t0[d] = lo[d];
+  const dim3 grd(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]);
+  if (side) {  // the band tiles beside the uniform ones
+    cudaEventRecord(side->fork, s);
+    cudaStreamWaitEvent(side->aux, side->fork, 0);
+    launch_resid_tma_u<false>(m, b, grd, side->aux);
+    launch_resid_tma_u<true>(m, a, full, s);
+    cudaEventRecord(side->join, side->aux);
+    cudaStreamWaitEvent(s, side->join, 0);
   } else {
-    cudaFuncSetAttribute(k_resid_tma<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_resid_tma<false, false><<<grd, 256, smem, s>>>(m, a);
+    launch_resid_tma_u<false>(m, b, grd, s);
+    launch_resid_tma_u<true>(m, a, full, s);
   }
   return 0;
 }
 
-size_t sweep_tma_smem() {
-  return ((size_t)XR * BOX + (size_t)L2R * CSLOT + (size_t)CR * (2 * CSLOT + L1SLOT)) * sizeof(float) +
-         (1 + NBB) * sizeof(uint64_t) + 128;
+size_t sweep_tma_smem(bool uni) {
+  const size_t rings = uni ? (size_t)XR * BOX + (size_t)CR * CSLOT
+                           : (size_t)XR * BOX + (size_t)L2R * CSLOT + (size_t)CR * (2 * CSLOT + L1SLOT);
+  return rings * sizeof(float) + (1 + NBB) * sizeof(uint64_t) + 128;
 }
 
-int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s) {
-  const Grid& g = a.g;
-  const size_t smem = sweep_tma_smem();
+template <int D, bool UNI>
+void launch_sweep_tma_v(const SweepMaps& m, const SweepTmaArgs& a, dim3 grd, cudaStream_t s) {
+  const size_t smem = sweep_tma_smem(UNI);
+  static bool attr = false;
+  if (!attr) {  // all of the unified L1/shared storage as shared memory: the blocks per SM are smem-bound
+    cudaFuncSetAttribute(k_sweep_tma<D, UNI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sweep_tma<D, UNI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    attr = true;
+  }
+  k_sweep_tma<D, UNI><<<grd, SW_NT, smem, s>>>(m, a);
+}
+
+// Tiles meeting the level's band box run the loading kernel, the others the uniform
+// one; without a split every tile loads its coefficients.
+int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStream_t s, const SideStream* side) {
+  const Grid& g = a0.g;
+  const int tz = D == 3 ? a0.tz : 1;
+  const dim3 full((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, D == 3 ? (g.n[2] + tz - 1) / tz : 1);
+  SweepTmaArgs a = a0;
+  a.t0[0] = a.t0[1] = a.t0[2] = 0;
+  if (!a.band.on) {
+    if (D == 3)
+      launch_sweep_tma_v<3, false>(m, a, full, s);
+    else
+      launch_sweep_tma_v<2, false>(m, a, full, s);
+    return 0;
+  }
+  auto uni = [&](cudaStream_t st) {
+    if (D == 3)
+      launch_sweep_tma_v<3, true>(m, a, full, st);
+    else
+      launch_sweep_tma_v<2, true>(m, a, full, st);
+  };
+  int lo[3], hi[3];
+  band_tiles(g.n[0], TX, 4, a.band.lo[0], a.band.hi[0], lo[0], hi[0]);
+  band_tiles(g.n[1], TY, 2, a.band.lo[1], a.band.hi[1], lo[1], hi[1]);
   if (D == 3)
-    cudaFuncSetAttribute(k_sweep_tma<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else
-    cudaFuncSetAttribute(k_sweep_tma<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (D == 3) {
-    dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + a.tz - 1) / a.tz);
-    k_sweep_tma<3><<<grd, SW_NT, smem, s>>>(m, a);
+    band_tiles(g.n[2], tz, 2, a.band.lo[2], a.band.hi[2], lo[2], hi[2]);
+  else {
+    lo[2] = 0;
+    hi[2] = 1;
+  }
+  if (hi[0] <= lo[0] || hi[1] <= lo[1] || hi[2] <= lo[2]) {
+    uni(s);
+    return 0;
+  }
+  SweepTmaArgs b = a;
+  for (int d = 0; d < 3; ++d) b.t0[d] = lo[d];
+  const dim3 grd(hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2]);
+  auto band = [&](cudaStream_t st) {
+    if (D == 3)
+      launch_sweep_tma_v<3, false>(m, b, grd, st);
+    else
+      launch_sweep_tma_v<2, false>(m, b, grd, st);
+  };
+  if (side) {  // the band tiles beside the uniform ones
+    cudaEventRecord(side->fork, s);
+    cudaStreamWaitEvent(side->aux, side->fork, 0);
+    band(side->aux);
+    uni(s);
+    cudaEventRecord(side->join, side->aux);
+    cudaStreamWaitEvent(s, side->join, 0);
   } else {
-    dim3 grd((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, 1);
-    k_sweep_tma<2><<<grd, SW_NT, smem, s>>>(m, a);
+    band(s);
+    uni(s);
   }
   return 0;
 }

@@ -336,3 +336,49 @@ def test_vcycle_tail_matches_per_level_kernels(case, monkeypatch):
     b.step(3)
     assert np.array_equal(a.get(0), b.get(0))
     assert np.array_equal(a.get(1), b.get(1))
+
+
+@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[2], CASES_3D[4], CASES_2D[0], CASES_2D[3]],
+                         ids=lambda c: c["id"])
+def test_uniform_tiles_match_loading_kernels(case, monkeypatch):
+    """Tiles away from the body form their face coefficients (the level's free-stream
+    value, 0 on walls) instead of loading them: identical bits to the kernels that load
+    every coefficient (the split forced on every level, whatever its band fraction)."""
+    monkeypatch.setenv("WL_UNIFORM_ALL", "1")
+    a, _ = make_pair(case, oracle=False)
+    monkeypatch.delenv("WL_UNIFORM_ALL")
+    monkeypatch.setenv("WL_NO_UNIFORM", "1")
+    b, _ = make_pair(case, oracle=False)
+    monkeypatch.delenv("WL_NO_UNIFORM")
+    a.step(3)
+    b.step(3)
+    assert np.array_equal(a.get(0), b.get(0))
+    assert np.array_equal(a.get(1), b.get(1))
+
+
+@pytest.mark.parametrize("case", [
+    dict(id="s192", dims=(192, 96, 96), nu=0.01, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=1, center=(60.3, 47.2, 49.7), radius=9.0)),
+    dict(id="channel128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.2, 0.0), periodic=0, body=None),
+    dict(id="yper128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.0, 0.0), periodic=2,
+         body=dict(kind=1, center=(40.0, 30.0, 24.0), radius=6.0)),
+], ids=lambda c: c["id"])
+def test_uniform_tiles_large_sphere_bitwise(case, monkeypatch):
+    """Grids large enough for many uniform tiles on several levels (a band of loading
+    tiles around the sphere; a body-free channel whose uniform tiles meet every wall; a
+    periodic side): identical bits either way."""
+    monkeypatch.setenv("WL_UNIFORM_ALL", "1")
+    a, _ = make_pair(case, oracle=False)
+    monkeypatch.delenv("WL_UNIFORM_ALL")
+    monkeypatch.setenv("WL_NO_UNIFORM", "1")
+    b, _ = make_pair(case, oracle=False)
+    monkeypatch.delenv("WL_NO_UNIFORM")
+    # a seeded disturbance, so that every projection has work to do
+    rng = np.random.default_rng(106)
+    u = _rand_u(a, rng, case["U"], 0.2).astype(np.float32)
+    for sim in (a, b):
+        sim.set(0, u)
+    a.step(4)
+    b.step(4)
+    assert np.array_equal(a.get(0), b.get(0))
+    assert np.array_equal(a.get(1), b.get(1))
