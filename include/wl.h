@@ -288,6 +288,14 @@ int wl_grad_backward(wl_handle h, const double* gF, double* theta_bar);
 int wl_levels(wl_handle h, int* nlevels);
 int wl_level_dims(wl_handle h, int l, int* dims);
 
+/* Whether level l's staged (TMA) sweeps and residual split their tiles: tiles away from
+ * the body form their face coefficients (the level's free-stream value, 0 on walls)
+ * instead of loading them, the rest (the body's band) load them.  *split (may be NULL)
+ * receives 1 or 0, *band_fraction (may be NULL) the fraction of the level's tiles that
+ * load their coefficients (1 without a split).  For measurement: the bytes a sweep moves
+ * depend on it.  No counterpart in the paper. */
+int wl_level_split(wl_handle h, int l, int* split, double* band_fraction);
+
 void wl_destroy(wl_handle h);
 const char* wl_last_error(wl_handle h);
 

@@ -1499,3 +1499,14 @@ int wl_grad_backward(wl_handle s, const double* gF, double* theta_bar) {
   rc = cuda_check(s, cudaGetLastError(), "wl_grad_backward");
   return rc ? rc : (G.notconv ? WL_WNOTCONV : WL_OK);
 }
+
+int wl_level_split(wl_handle s, int l, int* split, double* band_fraction) {
+  if (!s || l < 0 || l >= s->nlev) return WL_EINVAL;
+  const LevelBuf& L = s->lev[l];
+  const bool on = L.tma && L.band.on;
+  if (split) *split = on ? 1 : 0;
+  if (band_fraction)
+    *band_fraction = on ? band_tile_fraction(s->D, L.g, sweep_planes_per_block(L.g, SWEEP_UNI_BLOCKS_PER_SM), L.band)
+                        : 1.0;
+  return WL_OK;
+}

@@ -48,7 +48,7 @@ EXPORTS = (
     "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_get_field", "wl_set_field", "wl_get_dt",
     "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_levels", "wl_level_dims",
     "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
-    "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward",
+    "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split",
 )
 KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coarse", "coarsest", "correct",
             "control")
@@ -114,6 +114,7 @@ def load(path: str = LIB_PATH):
         "wl_grad_workspace_bytes": (ctypes.c_size_t, [H, I, I]),
         "wl_grad_forward": (I, [H, I, I, P, ctypes.c_size_t, DP]),
         "wl_grad_backward": (I, [H, DP, DP]),
+        "wl_level_split": (I, [H, I, IP, DP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -437,6 +438,12 @@ class Sim:
                                      tb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         self._check(rc, "wl_grad_backward")
         return (tb, rc) if return_status else tb
+
+    def level_split(self, l=0):
+        """(split, band_fraction) of level l's staged kernels (wl_level_split)."""
+        sp, fr = ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(load().wl_level_split(self.h, int(l), ctypes.byref(sp), ctypes.byref(fr)), "wl_level_split")
+        return bool(sp.value), fr.value
 
     def levels(self):
         rc, n = wl_levels(self.h)
