@@ -95,6 +95,9 @@ def _load():
             "or_force_adjoint": (None, [_P, _DP, _DP, _DP, _DP, _DP]),
             "or_moments_adjoint": (None, [_P, _DP, _DP, _DP, _DP]),
             "or_rollout_grad": (_I, [_P, _I, _D, _D, _DP, _DP, _DP]),
+            "or_set_exit": (_I, [_P, _I]),
+            "or_get_exit": (None, [_P, _DP]),
+            "or_set_exit_plane": (None, [_P, _DP]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -323,6 +326,23 @@ class Oracle:
 
     def kinetic_energy(self) -> float:
         return self.lib.or_kinetic_energy(self.h)
+
+    def set_exit(self, on=True):
+        """Convective exit on the upper x face (the exit face starts at U_x)."""
+        if self.lib.or_set_exit(self.h, int(bool(on))) != 0:
+            raise ValueError("a convective exit needs a non-periodic x direction")
+
+    def set_exit_plane(self, e):
+        a = np.ascontiguousarray(e, dtype=np.float64).reshape(-1)
+        self.lib.or_set_exit_plane(self.h, _dp(a))
+
+    def get_exit(self):
+        """Normal velocity on the exit face, shape (n_2, n_1) (2-D: (n_1,))."""
+        n1 = self.dims[1]
+        n2 = self.dims[2] if self.D == 3 else 1
+        out = np.zeros(n1 * n2)
+        self.lib.or_get_exit(self.h, _dp(out))
+        return out.reshape((n2, n1) if self.D == 3 else (n1,))
 
     # ---- reverse-mode derivative (adjoint) of the step at fixed dt; theta = (R, c_0, ..)
     def _vec(self, a, blocks):

@@ -57,6 +57,7 @@ struct OSim {
   int body_kind;      // 0 none, 1 circle/sphere, 2 torus
   double center[3], radius, radius2, eps;
   int advect;         // 1: full convection-diffusion; 0: diffusion only (Stokes checks)
+  int exit_bc = 0;    // 1: convective exit on the upper x face (see exit_stage)
   double dt, dt_cap, t;
   long nsteps;
   vec u[3];           // padded velocity, BC applied
@@ -147,6 +148,13 @@ void apply_bc(const OSim& s, vec* f) {
             if (is_per(s, d)) {
               J[d] = ((q % s.n[d]) + s.n[d]) % s.n[d];
               a[pidx(s, I)] = a[pidx(s, J)];
+            } else if (c == d && d == 0 && s.exit_bc && q >= s.n[0]) {
+              // convective exit: the exit face (q = n_0) keeps the value exit_stage gave it,
+              // the faces beyond copy it (zero gradient)
+              if (q > s.n[0]) {
+                J[0] = s.n[0];
+                a[pidx(s, I)] = a[pidx(s, J)];
+              }
             } else if (c == d) {
               a[pidx(s, I)] = s.U[c];
             } else {
@@ -215,6 +223,45 @@ void convdiff(const OSim& s, const vec* u, vec* r) {
   }
 }
 
+// Convective exit (reading: the paper's BC! names the boundary conditions only).  On the
+// upper x face the normal velocity e is carried out of the domain at the free-stream
+// speed U = U_x: de/dt = -U (e - u_x[n_0 - 1]) (first-order upwind difference across
+// the last cell), integrated by the same Heun stages as the interior: f_e = e0 - dt U
+// (e_in - u_in[n_0 - 1]) from the stage's input velocity, out_e = f_e (stage 1) or
+// (e' + f_e)/2 (stage 2).  Then the exit plane is shifted uniformly so that it carries
+// out exactly the flux that enters (the mean of out_e equals U: the net flux through the
+// other boundaries is zero), which the projection's Neumann problem needs.  The
+// tangential components keep zero gradient.
+void exit_f(const OSim& s, double dt, const vec* u0, const vec* uin, vec* f) {
+  const int n0 = s.n[0];
+  for (int k = 0; k < s.n[2]; ++k)
+    for (int j = 0; j < s.n[1]; ++j) {
+      const long qe = pidx(s, n0, j, k), ql = pidx(s, n0 - 1, j, k);
+      f[0][qe] = u0[0][qe] - dt * s.U[0] * (uin[0][qe] - uin[0][ql]);
+    }
+}
+// The state's exit plane into the x component of a padded velocity (interior arrays given
+// through the C interface carry no exit face).
+void copy_exit(const OSim& s, vec* u) {
+  if (!s.exit_bc) return;
+  for (int k = 0; k < s.n[2]; ++k)
+    for (int j = 0; j < s.n[1]; ++j) u[0][pidx(s, s.n[0], j, k)] = s.u[0][pidx(s, s.n[0], j, k)];
+}
+void exit_out(const OSim& s, int stage, const vec* u1, const vec* f, vec* out) {
+  const int n0 = s.n[0];
+  double sum = 0.0;
+  for (int k = 0; k < s.n[2]; ++k)
+    for (int j = 0; j < s.n[1]; ++j) {
+      const long qe = pidx(s, n0, j, k);
+      const double v = (stage == 1) ? f[0][qe] : 0.5 * (u1[0][qe] + f[0][qe]);
+      out[0][qe] = v;
+      sum += v;
+    }
+  const double shift = s.U[0] - sum / ((double)s.n[1] * s.n[2]);
+  for (int k = 0; k < s.n[2]; ++k)
+    for (int j = 0; j < s.n[1]; ++j) out[0][pidx(s, n0, j, k)] += shift;
+}
+
 // BDIM! (Table 2, Weymouth & Yue 2011) for one Heun stage.
 //   stage 1: f = u0 + dt r(u0);  out = mu0 f + sum_j mu1_j (f[I+e_j] - f[I-e_j])/2
 //   stage 2: f = u0 + dt r(u1);  out = (u1 + mu0 f + mu1 . grad f) / 2
@@ -236,6 +283,7 @@ void bdim_stage(const OSim& s, int stage, double dt, const vec* u0, const vec* u
           f[c][pidx(s, I)] = u0[c][pidx(s, I)] + dt * r[c][cidx(s, i, j, k)];
         }
   }
+  if (s.exit_bc) exit_f(s, dt, u0, uin, f);
   apply_bc(s, f);
   for (int c = 0; c < s.D; ++c) {
     out[c] = uin[c];
@@ -256,6 +304,7 @@ void bdim_stage(const OSim& s, int stage, double dt, const vec* u0, const vec* u
           out[c][pidx(s, I)] = (stage == 1) ? v : 0.5 * (u1[c][pidx(s, I)] + v);
         }
   }
+  if (s.exit_bc) exit_out(s, stage, u1, f, out);
   apply_bc(s, out);
 }
 
@@ -1147,6 +1196,32 @@ void* or_create(int D, const int* dims, double nu, const double* U, unsigned per
 
 void or_destroy(void* h) { delete (OSim*)h; }
 
+// Convective exit on the upper x face (exit_f / exit_out); x must not be periodic.  The
+// exit face starts at U_x.  Returns 0, or -1 if x is periodic.
+int or_set_exit(void* h, int on) {
+  OSim* s = (OSim*)h;
+  if (on && is_per(*s, 0)) return -1;
+  s->exit_bc = on ? 1 : 0;
+  if (on)
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j) s->u[0][pidx(*s, s->n[0], j, k)] = s->U[0];
+  apply_bc(*s, s->u);
+  return 0;
+}
+// Set the exit plane's normal velocity (n_1 * n_2 values, y fastest).
+void or_set_exit_plane(void* h, const double* in) {
+  OSim* s = (OSim*)h;
+  for (int k = 0; k < s->n[2]; ++k)
+    for (int j = 0; j < s->n[1]; ++j) s->u[0][pidx(*s, s->n[0], j, k)] = in[j + (long)s->n[1] * k];
+  apply_bc(*s, s->u);
+}
+// The exit plane's normal velocity (n_1 * n_2 values, y fastest).
+void or_get_exit(void* h, double* out) {
+  OSim* s = (OSim*)h;
+  for (int k = 0; k < s->n[2]; ++k)
+    for (int j = 0; j < s->n[1]; ++j) out[j + (long)s->n[1] * k] = s->u[0][pidx(*s, s->n[0], j, k)];
+}
+
 int or_nlevels(void* h) { return (int)((OSim*)h)->lev.size(); }
 void or_level_dims(void* h, int l, int* dims) {
   OSim* s = (OSim*)h;
@@ -1226,6 +1301,9 @@ void or_set_ic(void* h, int kind, double amp) {
           }
           s->u[c][pidx(*s, i, j, k)] = v;
         }
+  if (s->exit_bc)  // the exit face starts at the free stream
+    for (int k = 0; k < s->n[2]; ++k)
+      for (int j = 0; j < s->n[1]; ++j) s->u[0][pidx(*s, s->n[0], j, k)] = s->U[0];
   apply_bc(*s, s->u);
   std::fill(s->p.begin(), s->p.end(), 0.0);
   s->dt = cfl(*s);
@@ -1243,6 +1321,7 @@ void or_convdiff(void* h, const double* uin, double* rout) {
       for (int j = 0; j < s->n[1]; ++j)
         for (int i = 0; i < s->n[0]; ++i) u[c][pidx(*s, i, j, k)] = uin[c * s->ncell + cidx(*s, i, j, k)];
   }
+  copy_exit(*s, u);
   apply_bc(*s, u);
   convdiff(*s, u, r);
   for (int c = 0; c < s->D; ++c) std::memcpy(rout + c * s->ncell, r[c].data(), s->ncell * sizeof(double));
@@ -1263,6 +1342,8 @@ void or_bdim_stage(void* h, int stage, double dt, const double* u0in, const doub
           if (u1in) u1[c][pidx(*s, i, j, k)] = u1in[q];
         }
   }
+  copy_exit(*s, u0);
+  copy_exit(*s, u1);
   apply_bc(*s, u0);
   apply_bc(*s, u1);
   bdim_stage(*s, stage, dt, u0, u1, o);
@@ -1415,6 +1496,7 @@ void to_padded(const OSim& s, const double* in, vec* u) {
       for (int j = 0; j < s.n[1]; ++j)
         for (int i = 0; i < s.n[0]; ++i) u[c][pidx(s, i, j, k)] = in[c * s.ncell + cidx(s, i, j, k)];
   }
+  copy_exit(s, u);
   apply_bc(s, u);
 }
 void from_padded(const OSim& s, const vec* u, double* out) {
@@ -1514,7 +1596,7 @@ void or_moments_adjoint(void* h, const double* mu0bar, const double* Lbar, const
 // Differentiated rollout (rollout_grad): returns 0, or -1 unless the body is a circle/sphere.
 int or_rollout_grad(void* h, int nsteps, double dt, double tol, const double* gF, double* F, double* tb) {
   OSim* s = (OSim*)h;
-  if (s->body_kind != 1 || nsteps < 1 || !(dt > 0.0)) return -1;
+  if (s->body_kind != 1 || nsteps < 1 || !(dt > 0.0) || s->exit_bc) return -1;
   rollout_grad(*s, nsteps, dt, tol, gF, F, tb);
   return 0;
 }
