@@ -61,6 +61,8 @@ extern "C" {
 #define WL_FIELD_Z 4    /* right-hand side of the fine multigrid system (read/write) */
 #define WL_FIELD_UPRED 5 /* projected predictor velocity u' that stage 2 reads, D blocks (read/write) */
 #define WL_FIELD_USTAGE 6 /* output of the last wl_stage call, D blocks (read) */
+#define WL_FIELD_EXIT 7  /* convective exit (wl_opts.exit_bc): normal velocity on the upper x face,
+                            n_1 [x n_2] values, y fastest (read/write) */
 
 /* body kinds */
 #define WL_BODY_NONE 0
@@ -95,6 +97,11 @@ typedef struct {
   void* stream;          /* cudaStream_t for all work (default NULL) */
   void* workspace;       /* optional caller-owned device buffer of wl_workspace_bytes() */
   size_t workspace_bytes;
+  int exit_bc;           /* 1: convective exit on the upper x face instead of the Dirichlet value U_x: the
+                            normal velocity e there is carried out at U_x, de/dt = -U_x (e - u_x[n_0-1]),
+                            by the same Heun stages, then shifted so that the flux out equals the flux in;
+                            tangential components keep zero gradient.  Needs x non-periodic and
+                            U_x > 0; not differentiated (wl_grad_* refuse it).  Default 0. */
   int coarse_precision;  /* storage of the multigrid levels between the fine and the coarsest one:
                             WL_COARSE_FP32 (default), WL_COARSE_BF16 or WL_COARSE_FP16.  A 16-bit
                             level keeps its face coefficients, right-hand side and iterate in 16 bits

@@ -212,15 +212,16 @@ struct Carver {
 int level_storage(int l, int nlev, int cprec) { return (l >= 1 && l + 1 < nlev) ? cprec : ST_F32; }
 size_t esize(int st) { return st == ST_F32 ? sizeof(float) : 2; }
 
-size_t layout(wl_sim* s, int D, const int* dims, int precision, int cprec, char* base) {
+size_t layout(wl_sim* s, int D, const int* dims, int precision, int cprec, int exit_bc, char* base) {
   int ld[kMaxLevels][3];
   const int nlev = plan_levels(dims, D, ld);
   Carver cv{base};
   const long long nc = (long long)ld[0][0] * ld[0][1] * ld[0][2];
+  const long long ne = exit_bc ? (long long)ld[0][1] * ld[0][2] : 0;  // exit plane after u_x
   float** bufs[3] = {s ? s->ua : nullptr, s ? s->ub : nullptr, s ? s->uc : nullptr};
   for (int b = 0; b < 3; ++b)
     for (int c = 0; c < D; ++c) {
-      void* p = cv.take(sizeof(float) * nc);
+      void* p = cv.take(sizeof(float) * (nc + (c == 0 ? ne : 0)));
       if (s) bufs[b][c] = (float*)p;
     }
   for (int l = 0; l < nlev; ++l) {
@@ -319,6 +320,7 @@ StageArgs stage_args(wl_sim* s, int stage) {
 void enq_stage(wl_sim* s, int stage, cudaStream_t st) {
   const StageArgs a = stage_args(s, stage);
   PROF(s, st, WL_KCLASS_STAGE, launch_stage(s->D, a, st));
+  if (s->g.exit) PROF(s, st, WL_KCLASS_STAGE, launch_exit_stage(s->D, s->g, s->ua[0], a.u[0], s->ub[0], a.dt, stage, st));
   if (s->body.kind != 0) PROF(s, st, WL_KCLASS_BAND, launch_band(s->D, a, s->body, st));
 }
 
@@ -394,6 +396,10 @@ void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) 
     t.inv_w = 1.f / w;
     t.st = s->ds;
     t.band = L.band;
+    if (s->g.exit && mode == RES_DIVERGENCE) {
+      float* const* ub[3] = {s->ua, s->ub, s->uc};
+      t.uxe = ub[ubuf][0] + s->g.nc;
+    }
     PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st, side_of(s)));
     return;
   }
@@ -564,6 +570,9 @@ void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int 
   a.cfl = cfl;
   a.st = s->ds;
   PROF(s, st, WL_KCLASS_CORRECT, launch_correct(s->D, a, st));
+  if (s->g.exit && uout[0] != uin[0])  // the exit plane is not corrected: carry it over
+    cudaMemcpyAsync(uout[0] + s->g.nc, uin[0] + s->g.nc, sizeof(float) * (size_t)s->g.n[1] * s->g.n[2],
+                    cudaMemcpyDeviceToDevice, st);
 }
 
 int sync_state(wl_sim* s) {
@@ -696,7 +705,16 @@ int reset_state(wl_sim* s) {
   return WL_OK;
 }
 
-bool valid_field(int which) { return which >= WL_FIELD_U && which <= WL_FIELD_USTAGE; }
+bool valid_field(int which) { return which >= WL_FIELD_U && which <= WL_FIELD_EXIT; }
+
+// the three velocity buffers' exit planes start at the free stream
+void init_exit(wl_sim* s) {
+  if (!s->g.exit) return;
+  const long long ne = (long long)s->g.n[1] * s->g.n[2];
+  launch_fill(s->ua[0] + s->g.nc, ne, s->g.U[0], s->st);
+  launch_fill(s->ub[0] + s->g.nc, ne, s->g.U[0], s->st);
+  launch_fill(s->uc[0] + s->g.nc, ne, s->g.U[0], s->st);
+}
 
 }  // namespace
 
@@ -730,7 +748,7 @@ size_t wl_workspace_bytes(const int* dims, int ndim, const wl_opts* opts) {
   wl_default_opts(&o);
   if (opts) o = *opts;
   if (o.coarse_precision < 0 || o.coarse_precision > 2) return 0;
-  return layout(nullptr, ndim, dims, o.precision, o.coarse_precision, nullptr);
+  return layout(nullptr, ndim, dims, o.precision, o.coarse_precision, o.exit_bc ? 1 : 0, nullptr);
 }
 
 int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_body* body, const wl_opts* opts,
@@ -747,8 +765,10 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   wl_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_vcycles < 0 || o.post < 1 || !(o.eps > 0.0) || !(o.dt_cap > 0.0) ||
-      o.precision < 0 || o.precision > 1 || o.coarse_precision < 0 || o.coarse_precision > 2)
+      o.precision < 0 || o.precision > 1 || o.coarse_precision < 0 || o.coarse_precision > 2 || o.exit_bc < 0 ||
+      o.exit_bc > 1)
     return WL_EINVAL;
+  if (o.exit_bc && ((o.periodic_mask & 1u) || !(U[0] > 0.0))) return WL_EINVAL;  // exit: x walls, outflow
   if (body && (body->kind < 0 || body->kind > 2 || (body->kind == 2 && ndim != 3))) return WL_EINVAL;
   wl_sim* s = new wl_sim();
   s->D = ndim;
@@ -765,12 +785,13 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   }
   s->g.per = o.periodic_mask & ((1u << ndim) - 1u);
   s->g.nc = nc;
+  s->g.exit = o.exit_bc ? 1 : 0;
   s->body.kind = body ? body->kind : 0;
   for (int d = 0; d < 3; ++d) s->body.c[d] = body ? body->center[d] : 0.0;
   s->body.r1 = body ? body->radius : 0.0;
   s->body.r2 = body ? body->radius2 : 0.0;
   s->body.eps = o.eps;
-  const size_t need = layout(nullptr, ndim, dims, o.precision, o.coarse_precision, nullptr);
+  const size_t need = layout(nullptr, ndim, dims, o.precision, o.coarse_precision, o.exit_bc ? 1 : 0, nullptr);
   if (o.workspace) {
     if (o.workspace_bytes < need || ((uintptr_t)o.workspace & 255u)) {
       delete s;
@@ -789,7 +810,7 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
     s->own_ws = true;
   }
   s->ws_bytes = need;
-  layout(s, ndim, dims, o.precision, o.coarse_precision, s->ws);
+  layout(s, ndim, dims, o.precision, o.coarse_precision, o.exit_bc ? 1 : 0, s->ws);
   // Staged kernels: tiles away from the body take the variant that forms the face
   // coefficients (the level's free-stream value 2^(l (D-2)), 0 on walls) instead of
   // loading them.  The band box (faces with mu0 < 1 lie inside it) scaled to each level,
@@ -899,6 +920,7 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   }
   if (!rc) {
     launch_set_ic(ndim, s->g, 0, 0.0, s->ua, s->st);
+    init_exit(s);
     rc = set_dt_from_ic(s);
   }
   if (!rc) rc = cuda_check(s, cudaStreamSynchronize(s->st), "create");
@@ -940,6 +962,7 @@ int wl_set_ic(wl_handle s, int kind, double amp, const float* src, int src_is_de
   } else {
     launch_set_ic(s->D, s->g, kind, amp, s->ua, s->st);
   }
+  init_exit(s);
   int rc = reset_state(s);
   if (rc) return rc;
   rc = set_dt_from_ic(s);
@@ -1081,6 +1104,10 @@ int wl_get_field(wl_handle s, int which, void* dst, int dst_is_device) {
     case WL_FIELD_USTAGE:
       for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(d + c * nb, s->ub[c], nb, kind, s->st));
       break;
+    case WL_FIELD_EXIT:
+      if (!s->g.exit) return fail(s, WL_EINVAL, "no convective exit");
+      WL_CUDA(s, cudaMemcpyAsync(d, s->ua[0] + s->g.nc, sizeof(float) * (size_t)s->g.n[1] * s->g.n[2], kind, s->st));
+      break;
     default:
       return WL_EINVAL;
   }
@@ -1108,6 +1135,10 @@ int wl_set_field(wl_handle s, int which, const void* src, int src_is_device) {
     case WL_FIELD_UPRED:
       for (int c = 0; c < s->D; ++c) WL_CUDA(s, cudaMemcpyAsync(s->uc[c], p + c * nb, nb, kind, s->st));
       launch_fix_bfaces(s->D, s->g, s->uc, s->st);
+      break;
+    case WL_FIELD_EXIT:
+      if (!s->g.exit) return fail(s, WL_EINVAL, "no convective exit");
+      WL_CUDA(s, cudaMemcpyAsync(s->ua[0] + s->g.nc, p, sizeof(float) * (size_t)s->g.n[1] * s->g.n[2], kind, s->st));
       break;
     default:
       return fail(s, WL_EINVAL, "field is read-only");
@@ -1401,6 +1432,7 @@ int adj_step(wl_sim* s, int m, int n) {
 
 int grad_check(wl_sim* s) {
   if (s->body.kind != 1) return fail(s, WL_EINVAL, "gradients need a circle/sphere body");
+  if (s->g.exit) return fail(s, WL_EINVAL, "the convective exit is not differentiated");
   if (!(s->o.dt_fixed > 0.0)) return fail(s, WL_EINVAL, "gradients need a fixed dt (wl_opts.dt_fixed > 0)");
   if (s->poisoned) return fail(s, WL_ENONFINITE, "sim is poisoned");
   return WL_OK;

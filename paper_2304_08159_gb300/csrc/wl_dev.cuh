@@ -18,7 +18,14 @@ struct Grid {
   unsigned per;    // bit d: direction d periodic
   float U[3];      // boundary velocity (normal component on non-periodic sides)
   long long nc;    // cells
+  int exit;        // 1: convective exit on the upper x face; its normal velocity is stored
+                   //    after the n_c values of every velocity's x component (n_1 n_2 values)
 };
+
+// Index of the exit-plane value of row (j, k) after the x component's cells.
+__host__ __device__ inline long long exit_index(const Grid& g, int j, int k) {
+  return g.nc + (long long)j + (long long)g.n[1] * k;
+}
 
 __device__ __forceinline__ bool is_per(const Grid& g, int d) { return (g.per >> d) & 1u; }
 
@@ -74,6 +81,22 @@ __device__ __forceinline__ long long cell_index(const Grid& g, int i, int j, int
 template <int D>
 __device__ __forceinline__ float load_u_bc(const float* __restrict__ uc, int c, const Grid& g, int i, int j,
                                            int k) {
+  if (c == 0 && g.exit && i >= g.n[0]) {
+    // convective exit: the exit face and the faces beyond it (zero gradient) read the
+    // stored exit plane at the row (y clamped / wrapped like a tangential component)
+    int J = j, K = D == 3 ? k : 0;
+    if (is_per(g, 1))
+      J = J < 0 ? J + g.n[1] : (J >= g.n[1] ? J - g.n[1] : J);
+    else
+      J = J < 0 ? 0 : (J >= g.n[1] ? g.n[1] - 1 : J);
+    if (D == 3) {
+      if (is_per(g, 2))
+        K = K < 0 ? K + g.n[2] : (K >= g.n[2] ? K - g.n[2] : K);
+      else
+        K = K < 0 ? 0 : (K >= g.n[2] ? g.n[2] - 1 : K);
+    }
+    return __ldg(uc + exit_index(g, J, K));
+  }
   int I[3] = {i, j, k};
 #pragma unroll
   for (int d = 0; d < D; ++d) {

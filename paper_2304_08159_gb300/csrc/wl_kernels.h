@@ -163,6 +163,12 @@ struct CorrArgs {
 
 int launch_stage(int D, const StageArgs& a, cudaStream_t s);
 int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s);
+// Convective exit of one stage: the exit plane of outx from those of u0x and uinx (and
+// u_in's last x faces), shifted so that its mean is U_x.  One block.
+int launch_exit_stage(int D, const Grid& g, const float* u0x, const float* uinx, float* outx, const float* dt, int stage,
+                      cudaStream_t s);
+// fill n floats with v
+int launch_fill(float* p, long long n, float v, cudaStream_t s);
 int launch_residual(int D, const ResArgs& a, cudaStream_t s);
 int launch_sweep(int D, const SweepArgs& a, cudaStream_t s);
 // A second stream on which the loading (band) tiles' launch runs beside the uniform
@@ -194,6 +200,7 @@ struct ResidTmaArgs {
   DevState* st;        // dt, residual maximum, timeout flag
   BandBox band;        // tiles outside it: coefficients 1 (0 on walls), not loaded
   int t0[3];           // first tile of the launch
+  const float* uxe;    // divergence mode with a convective exit: the velocity's exit plane
 };
 int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s, const SideStream* side);
 int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s);

@@ -267,6 +267,58 @@ int launch_stage(int D, const StageArgs& a, cudaStream_t s) {
   return 0;
 }
 
+// Convective exit (reading: BC! of the paper names the boundary conditions only): the
+// normal velocity e on the upper x face is carried out at the free-stream speed U,
+// de/dt = -U (e - u[n_0 - 1]), by the same Heun stages as the interior:
+// f_e = e0 - dt U (e_in - u_in[n_0 - 1]), out_e = f_e (stage 1) or (e_in + f_e)/2
+// (stage 2); then the plane is shifted so that its mean is U: the flux out equals the
+// flux in (the other boundaries' net flux is zero), as the projection's Neumann problem
+// needs.  One block, the sum in FP64 in a fixed order.
+template <int D>
+__global__ void __launch_bounds__(1024) k_exit_stage(Grid g, const float* u0x, const float* uinx, float* outx,
+                                                     const float* dtp, int stage) {
+  __shared__ double sh[32];
+  const int n0 = g.n[0], n1 = g.n[1], n2 = D == 3 ? g.n[2] : 1;
+  const long long ne = (long long)n1 * n2;
+  const float dt = *dtp, U = g.U[0];
+  double sum = 0.0;
+  for (long long q = threadIdx.x; q < ne; q += 1024) {
+    const int j = (int)(q % n1), k = (int)(q / n1);
+    const float e0 = u0x[g.nc + q], ei = uinx[g.nc + q];
+    const float ul = uinx[(long long)(n0 - 1) + (long long)n0 * ((long long)j + (long long)n1 * k)];
+    const float f = fmaf(-dt * U, ei - ul, e0);
+    const float v = stage == 1 ? f : 0.5f * (ei + f);
+    outx[g.nc + q] = v;
+    sum += v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  double tot = 0.0;
+  for (int w = 0; w < 32; ++w) tot += sh[w];
+  const float shift = (float)((double)U - tot / (double)ne);
+  for (long long q = threadIdx.x; q < ne; q += 1024) outx[g.nc + q] += shift;
+}
+
+int launch_exit_stage(int D, const Grid& g, const float* u0x, const float* uinx, float* outx, const float* dt, int stage,
+                      cudaStream_t s) {
+  if (D == 3)
+    k_exit_stage<3><<<1, 1024, 0, s>>>(g, u0x, uinx, outx, dt, stage);
+  else
+    k_exit_stage<2><<<1, 1024, 0, s>>>(g, u0x, uinx, outx, dt, stage);
+  return 0;
+}
+
+__global__ void k_fill(float* p, long long n, float v) {
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q < n) p[q] = v;
+}
+int launch_fill(float* p, long long n, float v, cudaStream_t s) {
+  if (n > 0) k_fill<<<(int)((n + 255) / 256), 256, 0, s>>>(p, n, v);
+  return 0;
+}
+
 bool stage_band_box(int D, const Grid& g, const Body& b, int* lo, int* hi) {
   if (b.kind == 0) return false;
   double ext = b.r1 + b.eps + 2.0;

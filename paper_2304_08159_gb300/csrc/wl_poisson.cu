@@ -73,7 +73,8 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
     for (int c = 0; c < D; ++c) {
       bool has;
       const long long qu = nb_up(g, c, I[c], q, st[c], has);
-      const float up = has ? __ldg(a.u[c] + qu) : g.U[c];
+      const float up =
+          has ? __ldg(a.u[c] + qu) : ((c == 0 && g.exit) ? __ldg(a.u[0] + exit_index(g, I[1], I[2])) : g.U[c]);
       div += up - __ldg(a.u[c] + q);
     }
     z = (a.mode == RES_DIV_ONLY) ? div : div * a.inv_w * a.st->inv_dtf;
@@ -655,7 +656,8 @@ __global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
       if (a.cfl) {
         bool has;
         const long long qu = nb_up(g, c, I[c], q, st[c], has);
-        const float uup = has ? __ldg(a.u_in[c] + qu) - s * __ldg(a.L[c] + qu) * dp(qu, q) : g.U[c];
+        const float uup = has ? __ldg(a.u_in[c] + qu) - s * __ldg(a.L[c] + qu) * dp(qu, q)
+                              : ((c == 0 && g.exit) ? __ldg(a.u_in[0] + exit_index(g, I[1], I[2])) : g.U[c]);
         mc += fmaxf(0.f, uup) + fmaxf(0.f, -ulo);
       }
     }
@@ -740,7 +742,8 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
         xph = __ldg(P + ok + cxp);
         xpl = DF ? __ldg(a.pl + ok + cxp) : 0.f;
       }
-      const float up0 = hxp ? uxp - s * Lxp * dp(xph, xpl, wh[1], wl[1]) : g.U[0];
+      const float up0 = hxp ? uxp - s * Lxp * dp(xph, xpl, wh[1], wl[1])
+                            : (g.exit ? __ldg(a.u_in[0] + exit_index(g, jc, k)) : g.U[0]);
       float up1 = g.U[1];
       if (hyp) {
         const float yph = __ldg(P + ok + cyp), ypl = DF ? __ldg(a.pl + ok + cyp) : 0.f;
@@ -817,7 +820,7 @@ __global__ void __launch_bounds__(256) k_cfl_only(Grid g, const float* u0, const
     for (int c = 0; c < D; ++c) {
       bool has;
       const long long qu = nb_up(g, c, I[c], q, stv[c], has);
-      const float uup = has ? u[c][qu] : g.U[c];
+      const float uup = has ? u[c][qu] : ((c == 0 && g.exit) ? u[0][exit_index(g, I[1], I[2])] : g.U[c]);
       m += fmaxf(0.f, uup) + fmaxf(0.f, -u[c][q]);
     }
   }

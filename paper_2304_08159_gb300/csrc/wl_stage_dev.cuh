@@ -39,6 +39,14 @@ __device__ float conv_residual(const float* const* u, int c, const Grid& g, int 
 template <int D>
 __device__ float f_at(const StageArgs& a, int c, int i, int j, int k, float dt) {
   const Grid& g = a.g;
+  if (c == 0 && g.exit && i >= g.n[0]) {
+    // convective exit: f_e = e0 - dt U (e_in - u_in[n_0 - 1]) at the row (the exit update
+    // before its flux correction)
+    const float e0 = load_u_bc<D>(a.u0[0], 0, g, g.n[0], j, k);
+    const float ei = load_u_bc<D>(a.u[0], 0, g, g.n[0], j, k);
+    const float ul = load_u_bc<D>(a.u[0], 0, g, g.n[0] - 1, j, k);
+    return fmaf(-dt * g.U[0], ei - ul, e0);
+  }
   int I[3] = {i, j, k};
 #pragma unroll
   for (int d = 0; d < D; ++d) {

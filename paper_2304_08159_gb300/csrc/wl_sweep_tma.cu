@@ -688,7 +688,8 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
       if (DIV) {
         const float* U0 = B0 + LY::oU0;
         const float* U1 = B0 + LY::oU1;
-        const float uxp = (gi + 1 < g.n[0]) ? U0[c + 1] : g.U[0];
+        const float uxp = (gi + 1 < g.n[0]) ? U0[c + 1]
+                                            : ((a.uxe && in) ? __ldg(a.uxe + gj + (long long)g.n[1] * k) : g.U[0]);
         const float uyp = (gj + 1 < g.n[1]) ? U1[c + BX] : g.U[1];
         const float uzp = (k + 1 < g.n[2]) ? (Ap + LY::oU2)[c] : g.U[2];
         float div = 0.f;

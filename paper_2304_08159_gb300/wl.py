@@ -31,6 +31,7 @@ WL_FIELD_MU0 = 3
 WL_FIELD_Z = 4
 WL_FIELD_UPRED = 5
 WL_FIELD_USTAGE = 6
+WL_FIELD_EXIT = 7
 
 WL_BODY_NONE = 0
 WL_BODY_SPHERE = 1
@@ -64,7 +65,7 @@ class WlOpts(ctypes.Structure):
                 ("eps", ctypes.c_double), ("dt_cap", ctypes.c_double), ("dt_fixed", ctypes.c_double),
                 ("periodic_mask", ctypes.c_uint), ("advect", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("coarse_precision", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("exit_bc", ctypes.c_int), ("coarse_precision", ctypes.c_int)]
 
 
 class WLError(RuntimeError):
@@ -276,7 +277,7 @@ class Sim:
 
     def __init__(self, dims, nu, U, body=None, periodic=0, tol=1e-6, max_vcycles=32, post=4, eps=1.0,
                  dt_cap=10.0, dt_fixed=0.0, advect=True, precision=1, use_graph=True, device=None,
-                 coarse_precision=0):
+                 coarse_precision=0, exit_bc=False):
         import torch
 
         self.torch = torch
@@ -290,6 +291,7 @@ class Sim:
         o.dt_cap, o.dt_fixed, o.periodic_mask = float(dt_cap), float(dt_fixed), int(periodic)
         o.advect, o.precision, o.use_graph = int(bool(advect)), int(precision), int(bool(use_graph))
         o.coarse_precision = COARSE_PRECISION.get(coarse_precision, coarse_precision)
+        o.exit_bc = int(bool(exit_bc))
         with torch.cuda.device(self.device):
             o.stream = torch.cuda.current_stream().cuda_stream
             nbytes = wl_workspace_bytes(self.dims, o)
@@ -333,10 +335,15 @@ class Sim:
     def _nblocks(self, which):
         return self.D if which in (WL_FIELD_U, WL_FIELD_MU0, WL_FIELD_UPRED, WL_FIELD_USTAGE) else 1
 
+    def _field_shape(self, which):
+        if which == WL_FIELD_EXIT:  # the exit plane: n_1 [x n_2] values, y fastest
+            return tuple(reversed(self.dims[1:]))
+        nb = self._nblocks(which)
+        return ((nb,) if nb > 1 else ()) + self.shape
+
     def get(self, which, device=False):
         """Field as a float32 tensor on the GPU (device=True) or a numpy array."""
-        nb = self._nblocks(which)
-        shape = ((nb,) if nb > 1 else ()) + self.shape
+        shape = self._field_shape(which)
         if device:
             t = self.torch.empty(shape, dtype=self.torch.float32, device=self.device)
             self._check(wl_get_field(self.h, which, t.data_ptr(), 1), "wl_get_field")
@@ -346,13 +353,14 @@ class Sim:
         return a
 
     def set(self, which, value):
+        n = int(np.prod(self._field_shape(which)))
         if isinstance(value, np.ndarray):
             a = np.ascontiguousarray(value, dtype=np.float32)
-            assert a.size == self._nblocks(which) * self.ncell
+            assert a.size == n
             self._check(wl_set_field(self.h, which, a.ctypes.data, 0), "wl_set_field")
         else:
             t = value.to(device=self.device, dtype=self.torch.float32).contiguous()
-            assert t.numel() == self._nblocks(which) * self.ncell
+            assert t.numel() == n
             self._check(wl_set_field(self.h, which, t.data_ptr(), 1), "wl_set_field")
 
     # routines
