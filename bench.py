@@ -51,6 +51,12 @@ WORKLOADS = {
                      desc="3-D flow past a torus R=32 r=8 (axis along the flow), Re=1000, 512x256x256 cells, tol 1e-6"),
     "cyl128x64": dict(dims=(128, 64), nu=0.064, U=(1.0, 0.0), body=dict(kind=1, center=(32.0, 32.0), radius=8.0),
                       periodic=0, ic=0, desc="2-D flow past a circle R=8, Re=250, 128x64 cells, tol 1e-6"),
+    # the paper's own benchmark shape: Taylor-Green vortex at Re = 1e5 on N^3 (N = 2^p,
+    # 2^21 and 2^24 cells), length scale N/(2 pi)
+    "tgv128re1e5": dict(dims=(128, 128, 128), nu=(128.0 / (2 * 3.141592653589793)) / 1e5, U=(0.0, 0.0, 0.0),
+                        body=None, periodic=7, ic=1, desc="3-D Taylor-Green vortex, 128^3 periodic, Re=1e5, tol 1e-6"),
+    "tgv256re1e5": dict(dims=(256, 256, 256), nu=(256.0 / (2 * 3.141592653589793)) / 1e5, U=(0.0, 0.0, 0.0),
+                        body=None, periodic=7, ic=1, desc="3-D Taylor-Green vortex, 256^3 periodic, Re=1e5, tol 1e-6"),
 }
 
 # Algorithmic bytes per fine-level cell of one launch of each kernel class (D
