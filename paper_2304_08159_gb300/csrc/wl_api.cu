@@ -847,7 +847,8 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
         for (int tj = 0; tj < (L.g.n[1] + SWEEP_TY - 1) / SWEEP_TY; ++tj)
           for (int ti = 0; ti < (L.g.n[0] + SWEEP_TX - 1) / SWEEP_TX; ++ti) {
             const int k0 = ndim == 3 ? tk * tzs : 0, k1 = ndim == 3 ? std::min(k0 + tzs, L.g.n[2]) : 1;
-            if (sweep_tile_wraps(L.g, ndim, ti * SWEEP_TX, tj * SWEEP_TY, k0, k1))
+            (void)k1;
+            if (sweep_tile_wraps_xy(L.g, ti * SWEEP_TX, tj * SWEEP_TY))
               ++L.wrap_tiles;
             else
               ++L.tma_tiles;

@@ -208,9 +208,9 @@ int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s);
 int sweep_planes_per_block(const Grid& g, int blocks_per_sm);
 
 // Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.
-// A tile "wraps" when its TMA footprint (x i0-4..i0+67, y j0-2..j0+9, planes
-// k0-2..k1+1) crosses a periodic side: those tiles are swept by k_sweep, the others
-// by k_sweep_tma.
+// A tile whose TMA footprint (x i0-4..i0+67, y j0-2..j0+9) crosses a periodic x or y
+// side is swept by k_sweep; the others by k_sweep_tma, which stages planes past a
+// periodic z side from their wrapped planes.
 constexpr int SWEEP_TX = 64, SWEEP_TY = 8;
 // rows of the sweep's coefficient boxes (z, L0, L2; L1 takes one more), from j0-1
 constexpr int SWEEP_CROWS = SWEEP_TY + 2;
@@ -226,6 +226,13 @@ __host__ __device__ inline bool tile_in_band(const BandBox& b, int D, int i0, in
   if (j0 - 2 >= b.hi[1] || j0 + SWEEP_TY + 2 <= b.lo[1]) return false;
   if (D == 3 && (k0 - 2 >= b.hi[2] || k1 + 2 <= b.lo[2])) return false;
   return true;
+}
+// The tile's footprint crosses a periodic x or y side (the staged sweep stages planes
+// past a periodic z side from their wrapped planes; x and y wraps go to k_sweep).
+__host__ __device__ inline bool sweep_tile_wraps_xy(const Grid& g, int i0, int j0) {
+  if ((g.per & 1u) && (i0 - 4 < 0 || i0 + SWEEP_TX + 4 > g.n[0])) return true;
+  if ((g.per & 2u) && (j0 - 2 < 0 || j0 + SWEEP_TY + 2 > g.n[1])) return true;
+  return false;
 }
 __host__ __device__ inline bool sweep_tile_wraps(const Grid& g, int D, int i0, int j0, int k0, int k1) {
   if ((g.per & 1u) && (i0 - 4 < 0 || i0 + SWEEP_TX + 4 > g.n[0])) return true;

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   const int i0 = blockIdx.x * SW_TX, j0 = blockIdx.y * SW_TY;
   const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
-  if (a.only_wrapping && !sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
+  if (a.only_wrapping && !sweep_tile_wraps_xy(g, i0, j0)) return;
   const int n0 = g.n[0], nn = g.n[0] * g.n[1];
   const int cn0 = a.cn[0], cnn = a.cn[0] * a.cn[1];
   auto wrap = [&](int q, int d) -> int {  // mapped index along d, or -1

@@ -136,8 +136,11 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
   const int k0 = (D == 3) ? (blockIdx.z + a.t0[2]) * a.tz : 0;
   if (i0 >= g.n[0] || j0 >= g.n[1] || k0 >= g.n[2]) return;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
-  if (sweep_tile_wraps(g, D, i0, j0, k0, k1)) return;
+  if (sweep_tile_wraps_xy(g, i0, j0)) return;  // the table kernel's tile
   if (tile_in_band(a.band, D, i0, j0, k0, k1) == UNI) return;  // the other variant's tile
+  // a plane past a periodic z side is staged from its wrapped plane
+  const bool pz = D == 3 && is_per(g, 2);
+  auto wz = [&](int p) { return pz ? (p < 0 ? p + g.n[2] : (p >= g.n[2] ? p - g.n[2] : p)) : p; };
   // Ring slots: iterate plane p lives in slot (p - k0 + 2) mod XR, coefficient plane
   // p in slot (p - k0 + 1) mod L2R (L2) or mod CR (z, L0, L1).
   auto Xs = [&](int s) { return ox + s * BOX; };
@@ -161,13 +164,14 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
 
   // thread 0 staging.  Coefficient boxes start one row above the tile (j0-1), the
   // iterate's two rows above (j0-2); all start 4 columns left of the tile.
-  auto ld_x = [&](int p, uint32_t bar) { tma_load(sa(Xs(xslot(p))), &m.x, i0 - 4, j0 - 2, p, bar, D); };
-  auto ld_l2 = [&](int p, uint32_t bar) { tma_load(sa(L2s(l2slot(p))), &m.L2, i0 - 4, j0 - 1, p, bar, D); };
+  auto ld_x = [&](int p, uint32_t bar) { tma_load(sa(Xs(xslot(p))), &m.x, i0 - 4, j0 - 2, wz(p), bar, D); };
+  auto ld_l2 = [&](int p, uint32_t bar) { tma_load(sa(L2s(l2slot(p))), &m.L2, i0 - 4, j0 - 1, wz(p), bar, D); };
+  auto ld_z = [&](int p, uint32_t bar) { tma_load(sa(Zs(cslot(p))), &m.z, i0 - 4, j0 - 1, wz(p), bar, D); };
   auto ld_c = [&](int p, uint32_t bar) {
     const int c = cslot(p);
-    tma_load(sa(Zs(c)), &m.z, i0 - 4, j0 - 1, p, bar, D);
-    tma_load(sa(L0s(c)), &m.L0, i0 - 4, j0 - 1, p, bar, D);
-    tma_load(sa(L1s(c)), &m.L1, i0 - 4, j0 - 1, p, bar, D);
+    ld_z(p, bar);
+    tma_load(sa(L0s(c)), &m.L0, i0 - 4, j0 - 1, wz(p), bar, D);
+    tma_load(sa(L1s(c)), &m.L1, i0 - 4, j0 - 1, wz(p), bar, D);
   };
   constexpr uint32_t kXB = BOX * 4, kCB = BX * CROWS * 4, kL1B = BX * L1ROWS * 4;
   int b_issued = k0 - 1;  // (thread 0) last bundle staged
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
     if (UNI) {
       mbar_expect_tx(bbar(b), (a.has_x ? kXB : 0u) + kCB);
       if (a.has_x) ld_x(b + 2, bbar(b));
-      tma_load(sa(Zs(cslot(b + 1))), &m.z, i0 - 4, j0 - 1, b + 1, bbar(b), D);
+      ld_z(b + 1, bbar(b));
       return;
     }
     mbar_expect_tx(bbar(b), (a.has_x ? kXB : 0u) + 3 * kCB + kL1B);
@@ -194,10 +198,11 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       const int row = e / BX, col = e - row * BX;
       const int gi = i0 - 4 + col, gj = j0 - 2 + row;
       float v = a.has_x ? smf[Xp + e] : 0.f;
-      if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && p >= 0 && p < g.n[2])
+      const int wp = D == 3 ? wz(p) : p;  // the coarse correction of a wrapped plane
+      if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && wp >= 0 && wp < g.n[2])
         v += xcm * ld_st(a.xc, a.xctype,
                          (long long)(gi >> 1) +
-                             (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (p >> 1)));
+                             (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (wp >> 1)));
       smf[Xp + e] = v;
     }
   };
@@ -326,10 +331,9 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
   }
   // UNI: z faces and range of plane kk
   auto zmask = [&](int kk, bool& zlo, bool& zhi, bool& kin) {
-    const bool pz = D == 3 && is_per(g, 2);
     zlo = kk > 0 || pz;
     zhi = kk + 1 < g.n[2] || pz;
-    kin = kk >= 0 && kk < g.n[2];
+    kin = pz || (kk >= 0 && kk < g.n[2]);
   };
   const bool has_edge = warp >= 3 && lane < 5, two_black = warp < 3;
   // red cells of plane kk (parity par) whose operands are P
@@ -481,7 +485,7 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       for (int p = plo; p <= phi; ++p) ld_x(p, b0);
     for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 : 0); ++p) {
       if (UNI)
-        tma_load(sa(Zs(cslot(p))), &m.z, i0 - 4, j0 - 1, p, b0, D);
+        ld_z(p, b0);
       else
         ld_c(p, b0);
     }
