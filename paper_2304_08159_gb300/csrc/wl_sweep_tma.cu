@@ -190,23 +190,53 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
     ld_l2(b + 2, bbar(b));
     ld_c(b + 1, bbar(b));
   };
-  // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p
+  // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p.  The
+  // box starts at an even cell, so it covers 36 x 6 coarse cells; each thread owns up to
+  // two of them and adds each one's value to its 2 x 2 fine cells.  Two fine planes share
+  // a coarse plane: a thread keeps the values of the last coarse plane it loaded, and
+  // the loop loads the next plane's one iteration ahead of their use.
   const float xcm = a.xc_cs ? ldexpf(1.f, -a.st->cs_used) : 1.f;  // removes the coarse levels' scale
-  auto fix_x = [&](int p) {
-    const int Xp = Xs(xslot(p));
-    for (int e = tid; e < BOX; e += SW_NT) {
-      const int row = e / BX, col = e - row * BX;
-      const int gi = i0 - 4 + col, gj = j0 - 2 + row;
-      float v = a.has_x ? smf[Xp + e] : 0.f;
-      const int wp = D == 3 ? wz(p) : p;  // the coarse correction of a wrapped plane
-      if (a.xc && gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] && wp >= 0 && wp < g.n[2])
-        v += xcm * ld_st(a.xc, a.xctype,
-                         (long long)(gi >> 1) +
-                             (long long)a.cn[0] * ((long long)(gj >> 1) + (long long)a.cn[1] * (wp >> 1)));
-      smf[Xp + e] = v;
+  const bool fix = !a.has_x || a.xc;
+  constexpr int CBX = BX / 2, CBOX = CBX * (BY / 2);
+  static_assert(BX % 2 == 0 && BY % 2 == 0 && CBOX <= 2 * SW_NT, "coarse box");
+  int cxy[2], ceo[2];  // coarse in-plane index (-1: outside the grid), fine box offset (-1: none)
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int t = tid + SW_NT * r, cr = t / CBX, cc = t - cr * CBX;
+    const int ci = (i0 >> 1) - 2 + cc, cj = (j0 >> 1) - 1 + cr;
+    ceo[r] = t < CBOX ? 2 * cr * BX + 2 * cc : -1;
+    cxy[r] = (t < CBOX && a.xc && ci >= 0 && ci < a.cn[0] && cj >= 0 && cj < a.cn[1]) ? ci + a.cn[0] * cj : -1;
+  }
+  float cv[2] = {0.f, 0.f};
+  int ckey = -2;  // coarse plane whose values cv holds (-1: outside the grid)
+  auto load_c = [&](int p) {
+    const int wp = D == 3 ? wz(p) : p;  // the coarse correction of a wrapped plane
+    const int kz = (wp >= 0 && wp < g.n[2]) ? (wp >> 1) : -1;
+    if (kz == ckey) return;
+    ckey = kz;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+      cv[r] = (kz >= 0 && cxy[r] >= 0)
+                  ? xcm * ld_st(a.xc, a.xctype, (long long)cxy[r] + (long long)a.cn[0] * a.cn[1] * kz)
+                  : 0.f;
+  };
+  auto apply_c = [&](int p) {
+    float* X = smf + Xs(xslot(p));
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+      if (ceo[r] < 0) continue;
+      float2* q0 = reinterpret_cast<float2*>(X + ceo[r]);
+      float2* q1 = reinterpret_cast<float2*>(X + ceo[r] + BX);
+      const float2 z = make_float2(0.f, 0.f);
+      const float2 v0 = a.has_x ? *q0 : z, v1 = a.has_x ? *q1 : z;
+      *q0 = make_float2(v0.x + cv[r], v0.y + cv[r]);
+      *q1 = make_float2(v1.x + cv[r], v1.y + cv[r]);
     }
   };
-  const bool fix = !a.has_x || a.xc;
+  auto fix_x = [&](int p) {
+    load_c(p);
+    apply_c(p);
+  };
   // Operand planes of a relaxation (shared byte addresses): iterate planes below /
   // at / above, and the coefficient planes (shifted one row so that one shared
   // offset e addresses the iterate box and the coefficient boxes).
@@ -329,6 +359,22 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       if (UNI) me[par] = xymask(ce, je);
     }
   }
+  // UNI, tiles that touch a wall: bit t of fast_m is set when every lane's cell of task t
+  // (red 2h+par, black 4+2h+par, edge 8+par) is inside the grid with all four x/y faces,
+  // so that on a plane with both z faces the task takes relax_fast (same bits)
+  uint32_t fast_m = 0u;
+  if (UNI && !interior) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int par = 0; par < 2; ++par) {
+        if (__all_sync(0xffffffffu, mr[h][par] == 31u)) fast_m |= 1u << (2 * h + par);
+        if (__all_sync(0xffffffffu, mb[h][par] == 31u)) fast_m |= 1u << (4 + 2 * h + par);
+      }
+#pragma unroll
+    for (int par = 0; par < 2; ++par)
+      if (__all_sync(0xffffffffu, !(warp >= 3 && lane < 5) || me[par] == 31u)) fast_m |= 1u << (8 + par);
+  }
   // UNI: z faces and range of plane kk
   auto zmask = [&](int kk, bool& zlo, bool& zhi, bool& kin) {
     zlo = kk > 0 || pz;
@@ -352,13 +398,14 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
     if (UNI) {
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
-      const float v0 = relax_uni(P, e0, par ? mr[0][1] : mr[0][0], zlo, zhi, kin);
-      const float v1 = relax_uni(P, e1, par ? mr[1][1] : mr[1][0], zlo, zhi, kin);
+      const uint32_t fm = (zlo && zhi && kin) ? fast_m >> par : 0u;
+      const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, par ? mr[0][1] : mr[0][0], zlo, zhi, kin);
+      const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mr[1][1] : mr[1][0], zlo, zhi, kin);
       sts(P.x0 + e0, v0);
       sts(P.x0 + e1, v1);
       if (has_edge) {
         const uint32_t f = par ? ee[1] : ee[0];
-        sts(P.x0 + f, relax_uni(P, f, par ? me[1] : me[0], zlo, zhi, kin));
+        sts(P.x0 + f, (fm & 256u) ? relax_fast(P, f) : relax_uni(P, f, par ? me[1] : me[0], zlo, zhi, kin));
       }
       return;
     }
@@ -388,14 +435,15 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
       const uint32_t m0 = par ? mb[0][1] : mb[0][0];
+      const uint32_t fm = (zlo && zhi && kin) ? fast_m >> (4 + par) : 0u;
+      const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, m0, zlo, zhi, kin);
       if (two_black) {
         const uint32_t e1 = par ? eb[1][1] : eb[1][0];
-        const float v0 = relax_uni(P, e0, m0, zlo, zhi, kin);
-        const float v1 = relax_uni(P, e1, par ? mb[1][1] : mb[1][0], zlo, zhi, kin);
+        const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mb[1][1] : mb[1][0], zlo, zhi, kin);
         sts(P.x0 + e0, v0);
         sts(P.x0 + e1, v1);
       } else {
-        sts(P.x0 + e0, relax_uni(P, e0, m0, zlo, zhi, kin));
+        sts(P.x0 + e0, v0);
       }
       return;
     }
@@ -501,6 +549,7 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
   if (fix) {
     for (int p = plo; p <= phi; ++p) fix_x(p);
     __syncthreads();
+    if (D == 3 && k0 + 2 <= k1 + 1) load_c(k0 + 2);
   }
   if constexpr (D == 2) {
     prefetch(0);
@@ -524,8 +573,9 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       const bool ok = mbar_wait(bbar(k), bphase(k));
       if (__syncthreads_or(!ok)) return bail(false, k);
       if (fix) {
-        fix_x(k + 2);
+        apply_c(k + 2);
         __syncthreads();
+        if (k + 3 <= k1 + 1) load_c(k + 3);  // used by the next iteration
       }
     }
     // every thread is past iteration k-1, the last use of iterate plane k-2 and of
