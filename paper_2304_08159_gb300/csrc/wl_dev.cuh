@@ -258,4 +258,21 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
   e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
+// Packed FP32 pairs (two lanes per instruction, sm_100 and later).  Each lane rounds
+// exactly as the scalar operation does, so a packed path gives the scalar path's bits.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+__device__ __forceinline__ void two_prod2(float2 a, float2 b, float2& p, float2& e) {
+  p = mul2(a, b);
+  e = fma2(a, b, neg2(p));
+}
+
 }  // namespace wl

@@ -9,6 +9,8 @@
 // body velocity is zero.  k_stage computes everything but the mu1 term, which is
 // non-zero only in the thin band |d| < eps around the body and is added by
 // k_bdim_band over the body's bounding box.
+#include <type_traits>
+
 #include "wl_dev.cuh"
 #include "wl_kernels.h"
 #include "wl_stage_dev.cuh"
@@ -17,21 +19,26 @@ namespace wl {
 
 constexpr int ST_TX = 32, ST_TY = 8, ST_TZ = 32;
 constexpr int ST_HX = ST_TX + 4, ST_HY = ST_TY + 4;
+template <int N>
+using IC = std::integral_constant<int, N>;
 
 // Tile of ST_TX x ST_TY columns marching upward through ST_TZ planes.  The velocity
 // of planes k-1..k+2 (with a 2-cell in-plane halo) sits in a 4-plane shared ring;
 // plane k+3 is loaded into registers while plane k is computed.
 // Each thread computes the lower x-, y- and z-face fluxes of its cell; the upper x/y
 // fluxes come from the neighbour through shared memory, the upper z flux is carried
-// in registers to the next plane, so every face flux is evaluated once.
+// in registers to the next plane, so every face flux is evaluated once.  The plane loop
+// is unrolled by the ring's length, so every ring slot, and with it every shared
+// operand offset, is a compile-time constant.
 template <int D>
 __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
   constexpr int NP = (D == 3) ? 4 : 1;
-  __shared__ float s_u[D][NP][ST_HY][ST_HX];
+  constexpr int HX = ST_HX, PL = ST_HY * ST_HX, NE = PL;
+  __shared__ float s_u[D * NP * PL];
   __shared__ float s_fx[D][ST_TY][ST_TX + 1];
   __shared__ float s_fy[D][ST_TY + 1][ST_TX];
   const Grid& g = a.g;
-  const int tid = threadIdx.x, tx = tid % ST_TX, ty = tid / ST_TX;
+  const int tid = threadIdx.x, tx = tid % ST_TX, ty = tid / ST_TX, warp = tid >> 5, lane = tid & 31;
   const int i0 = blockIdx.x * ST_TX, j0 = blockIdx.y * ST_TY;
   const int k0 = (D == 3) ? blockIdx.z * ST_TZ : 0;
   const int k1 = (D == 3) ? min(k0 + ST_TZ, g.n[2]) : 1;
@@ -43,134 +50,149 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
   // this tile overlaps the body's band box: its faces there keep f for the mu1 term
   const bool box_tile = a.fbox && i0 < a.blo[0] + a.bn[0] && i0 + ST_TX > a.blo[0] && j0 < a.blo[1] + a.bn[1] &&
                         j0 + ST_TY > a.blo[1] && k0 < a.blo[2] + a.bn[2] && k1 > a.blo[2];
-
-  auto slot = [&](int kk) { return (D == 3) ? ((kk - k0 + 2) & 3) : 0; };
-  // flat shared-memory view: component c of plane kk starts at off(c, kk); a tile
-  // position (ii, jj) adds (jj + 2) * ST_HX + ii + 2
-  const float* sf = &s_u[0][0][0][0];
-  auto off = [&](int c, int kk) -> int { return (c * NP + slot(kk)) * (ST_HY * ST_HX); };
-  constexpr int HX = ST_HX;
-  int k_cur = k0;  // plane whose x- and y-face fluxes are being formed
+  // component c of ring slot sl starts at soff(c, sl); a tile position (ii, jj) adds
+  // (jj + 2) * HX + ii + 2.  Plane kk lives in slot (kk - k0 + 2) mod NP.
+  auto soff = [](int c, int sl) { return (c * NP + sl) * PL; };
 
   // A plane of the velocity (2-cell in-plane halo) moves in two steps: fetch() loads
-  // this thread's elements (at most two per component) into registers, commit()
-  // stores them into the plane's ring slot, so the loads of plane k+3 are in flight
-  // while the fluxes of plane k are formed.
-  constexpr int NE = ST_HY * ST_HX;
+  // this thread's elements e = tid, tid + 256 (at most two per component) into
+  // registers, commit() stores them into the plane's ring slot, so the loads of plane
+  // k+3 are in flight while the fluxes of plane k are formed.
+  const bool xy_inner = (i0 >= 2) && (i0 + ST_TX + 2 <= g.n[0]) && (j0 >= 2) && (j0 + ST_TY + 2 <= g.n[1]);
+  const long long nxy = (long long)g.n[0] * g.n[1];
+  const long long fbase = (long long)(i0 - 2) + (long long)g.n[0] * (j0 - 2);  // halo origin (inner tiles)
+  int foff[2];  // element offsets from it
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + 256 * h, row = e / HX;
+    foff[h] = (e - row * HX) + g.n[0] * row;
+  }
   float rv[2][D];
   auto fetch = [&](int kk) {
-    const bool inner = (i0 >= 2) && (i0 + ST_TX + 2 <= g.n[0]) && (j0 >= 2) && (j0 + ST_TY + 2 <= g.n[1]) &&
-                       (D == 2 || (kk >= 0 && kk < g.n[2]));
+    const bool inner = xy_inner && (D == 2 || (kk >= 0 && kk < g.n[2]));
+    const long long qk = fbase + ((D == 3) ? nxy * kk : 0);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int e = tid + 256 * h;
       if (e >= NE) break;
-      const int row = e / ST_HX, col = e - row * ST_HX;
-      const int gi = i0 - 2 + col, gj = j0 - 2 + row;
+      if (inner) {
 #pragma unroll
-      for (int c = 0; c < D; ++c)
-        rv[h][c] = inner ? __ldg(a.u[c] + cell_index(g, gi, gj, D == 3 ? kk : 0)) : load_u_bc<D>(a.u[c], c, g, gi, gj, kk);
+        for (int c = 0; c < D; ++c) rv[h][c] = __ldg(a.u[c] + qk + foff[h]);
+      } else {
+        const int row = e / HX, col = e - row * HX;
+#pragma unroll
+        for (int c = 0; c < D; ++c) rv[h][c] = load_u_bc<D>(a.u[c], c, g, i0 - 2 + col, j0 - 2 + row, kk);
+      }
     }
   };
-  auto commit = [&](int kk) {
-    const int sl = slot(kk);
+  auto commit = [&](int sl) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int e = tid + 256 * h;
       if (e >= NE) break;
-      const int row = e / ST_HX, col = e - row * ST_HX;
 #pragma unroll
-      for (int c = 0; c < D; ++c) s_u[c][sl][row][col] = rv[h][c];
+      for (int c = 0; c < D; ++c) s_u[soff(c, sl) + e] = rv[h][c];
     }
-  };
-  auto load_plane = [&](int kk) {
-    fetch(kk);
-    commit(kk);
   };
 
-  // Lower x-face flux of the u_c control volume at flat position pos of plane k
-  // (o: component offsets of plane k; om2: offset of component z in plane k-1, for
-  // the advecting velocity of c = z).
-  auto flux_x = [&](int c, const int* o, int om2, int pos) -> float {
-    const float* U = sf + off(c, k_cur) + pos;
-    const float* A = sf + o[0] + pos;
-    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : sf[om2 - o[2] + o[0] + pos]));
+  // Lower-face fluxes of the u_c control volume at tile position pos, with plane k in
+  // slot S (and k-1 in SM, whose u_x / u_y advect u_z across the x / y faces).
+  auto flux_x = [&](auto C, auto S, auto SM, int pos) -> float {
+    constexpr int c = decltype(C)::value, s = decltype(S)::value, sm = decltype(SM)::value;
+    const float* U = s_u + soff(c, s) + pos;
+    const float* A = s_u + soff(0, s) + pos;
+    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : s_u[soff(0, sm) + pos]));
     return mom_flux(U[-2], U[-1], U[0], U[1], a2, nu, adv);
   };
-  auto flux_y = [&](int c, const int* o, int om2, int pos) -> float {
-    const float* U = sf + off(c, k_cur) + pos;
-    const float* A = sf + o[1] + pos;
-    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : sf[om2 - o[2] + o[1] + pos]));
+  auto flux_y = [&](auto C, auto S, auto SM, int pos) -> float {
+    constexpr int c = decltype(C)::value, s = decltype(S)::value, sm = decltype(SM)::value;
+    const float* U = s_u + soff(c, s) + pos;
+    const float* A = s_u + soff(1, s) + pos;
+    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : s_u[soff(1, sm) + pos]));
     return mom_flux(U[-2 * HX], U[-HX], U[0], U[HX], a2, nu, adv);
   };
-  // lower z-face flux at plane kf: q[t][c] = offsets of planes kf-2+t
-  auto flux_z = [&](int c, const int (*q)[3], int pos) -> float {
-    const float* A = sf + q[2][2] + pos;  // u_z at plane kf
-    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : sf[q[1][2] + pos]));
-    return mom_flux(sf[q[0][c] + pos], sf[q[1][c] + pos], sf[q[2][c] + pos], sf[q[3][c] + pos], a2, nu, adv);
-  };
-  // offsets of the four planes kk-2 .. kk+1 (flux_z of face kk)
-  auto zoffs = [&](int kk, int (*q)[3]) {
-    for (int t = 0; t < 4; ++t)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) q[t][c] = (c < D) ? off(c, kk - 2 + t) : 0;
+  // lower z-face flux at plane kf, planes kf-2 .. kf+1 in slots Q0 .. Q3
+  auto flux_z = [&](auto C, auto Q0, auto Q1, auto Q2, auto Q3, int pos) -> float {
+    constexpr int c = decltype(C)::value, q0 = decltype(Q0)::value, q1 = decltype(Q1)::value,
+                  q2 = decltype(Q2)::value, q3 = decltype(Q3)::value;
+    const float* A = s_u + soff(2, q2) + pos;  // u_z at plane kf
+    const float a2 = A[0] + (c == 0 ? A[-1] : (c == 1 ? A[-HX] : s_u[soff(2, q1) + pos]));
+    return mom_flux(s_u[soff(c, q0) + pos], s_u[soff(c, q1) + pos], s_u[soff(c, q2) + pos], s_u[soff(c, q3) + pos],
+                    a2, nu, adv);
   };
   const int own = (ty + 2) * HX + (tx + 2);
+  const long long qij = own_cell ? (long long)i + (long long)g.n[0] * j : 0;
 
   float fzl[3] = {0.f, 0.f, 0.f};
-  if (D == 3) {
-    load_plane(k0 - 2);
-    load_plane(k0 - 1);
-    load_plane(k0);
-    load_plane(k0 + 1);
+  if constexpr (D == 3) {
+    // planes k0-2 .. k0+1 in slots 0 .. 3
+    for (int t = 0; t < 4; ++t) {
+      fetch(k0 - 2 + t);
+      commit(t);
+    }
     fetch(k0 + 2);
     __syncthreads();
-    int q[4][3];
-    zoffs(k0, q);
-#pragma unroll
-    for (int c = 0; c < D; ++c) fzl[c] = flux_z(c, q, own);
+    fzl[0] = flux_z(IC<0>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{}, own);
+    fzl[1] = flux_z(IC<1>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{}, own);
+    fzl[2] = flux_z(IC<2>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{}, own);
     __syncthreads();
   }
 
-  for (int k = k0; k < k1; ++k) {
+  // plane k, with k - k0 = PH (mod NP): plane k+t sits in slot (PH + t + 2) mod NP
+  auto step = [&](auto PHc, int k) {
+    constexpr int PH = decltype(PHc)::value;
+    constexpr int S0 = (PH + 2) % NP, SM1 = (PH + 1) % NP;
+    [[maybe_unused]] constexpr int SP1 = (PH + 3) % NP, SP2 = PH % NP;
+    using I0 = IC<S0>;
+    using Im = IC<SM1>;
     // plane k+2 into the slot of plane k-2 (last read by the z fluxes of face k)
-    if (D == 3)
-      commit(k + 2);
-    else
-      load_plane(0);
+    if constexpr (D == 3) {
+      commit(SP2);
+    } else {
+      fetch(0);
+      commit(0);
+    }
     __syncthreads();
     // in flight while the fluxes are formed: plane k+3 (the last plane used is k1+1),
     // and this cell's mu0 and stage-1 velocity
     if (D == 3 && k + 3 <= k1 + 1) fetch(k + 3);
-    const long long qg = cell_index(g, own_cell ? i : 0, own_cell ? j : 0, k);
+    const long long qg = qij + (D == 3 ? nxy * k : 0);
     float m0[D], u0v[D];
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       m0[c] = own_cell ? __ldg(a.mu0[c] + qg) : 0.f;
       u0v[c] = (own_cell && a.stage != 1) ? __ldg(a.u0[c] + qg) : 0.f;
     }
-    k_cur = k;
-    int o[3], om2 = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) o[c] = (c < D) ? off(c, k) : 0;
-    if (D == 3) om2 = off(2 % D, k - 1);
     float fzu[3] = {0.f, 0.f, 0.f};
-    int q[4][3];
-    if (D == 3) zoffs(k + 1, q);
-#pragma unroll
-    for (int c = 0; c < D; ++c) {
-      s_fx[c][ty][tx] = flux_x(c, o, om2, own);
-      s_fy[c][ty][tx] = flux_y(c, o, om2, own);
-      if (D == 3) fzu[c] = flux_z(c, q, own);
+    s_fx[0][ty][tx] = flux_x(IC<0>{}, I0{}, Im{}, own);
+    s_fy[0][ty][tx] = flux_y(IC<0>{}, I0{}, Im{}, own);
+    s_fx[1][ty][tx] = flux_x(IC<1>{}, I0{}, Im{}, own);
+    s_fy[1][ty][tx] = flux_y(IC<1>{}, I0{}, Im{}, own);
+    if constexpr (D == 3) {
+      s_fx[2][ty][tx] = flux_x(IC<2>{}, I0{}, Im{}, own);
+      s_fy[2][ty][tx] = flux_y(IC<2>{}, I0{}, Im{}, own);
+      // face k+1: planes k-1 .. k+2
+      fzu[0] = flux_z(IC<0>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{}, own);
+      fzu[1] = flux_z(IC<1>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{}, own);
+      fzu[2] = flux_z(IC<2>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{}, own);
     }
-    // fluxes through the upper edge faces of the tile
-    if (tid < D * ST_TY) {
-      const int c = tid / ST_TY, row = tid - c * ST_TY;
-      s_fx[c][row][ST_TX] = flux_x(c, o, om2, (row + 2) * HX + ST_TX + 2);
-    } else if (tid < D * ST_TY + D * ST_TX) {
-      const int t = tid - D * ST_TY;
-      const int c = t / ST_TX, col = t - c * ST_TX;
-      s_fy[c][ST_TY][col] = flux_y(c, o, om2, (ST_TY + 2) * HX + col + 2);
+    // fluxes through the upper edge faces of the tile: the x edge (D x ST_TY faces) on
+    // warp 0, the y edge of component c (ST_TX faces) on warp c + 1
+    if (warp == 0) {
+      if (lane < D * ST_TY) {
+        const int c = lane / ST_TY, row = lane - c * ST_TY, pos = (row + 2) * HX + ST_TX + 2;
+        const float f = c == 0 ? flux_x(IC<0>{}, I0{}, Im{}, pos)
+                               : (c == 1 ? flux_x(IC<1>{}, I0{}, Im{}, pos) : flux_x(IC<D - 1>{}, I0{}, Im{}, pos));
+        s_fx[c][row][ST_TX] = f;
+      }
+    } else if (warp <= D) {
+      const int pos = (ST_TY + 2) * HX + lane + 2;
+      if (warp == 1)
+        s_fy[0][ST_TY][lane] = flux_y(IC<0>{}, I0{}, Im{}, pos);
+      else if (warp == 2)
+        s_fy[1][ST_TY][lane] = flux_y(IC<1>{}, I0{}, Im{}, pos);
+      else
+        s_fy[D - 1][ST_TY][lane] = flux_y(IC<D - 1>{}, I0{}, Im{}, pos);
     }
     __syncthreads();
     if (own_cell) {
@@ -184,7 +206,7 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
         if (!upd) {
           ov = g.U[c];
         } else {
-          const float uc = sf[o[c] + own];
+          const float uc = s_u[soff(c, S0) + own];
           const float u0 = (a.stage == 1) ? uc : u0v[c];
           f = fmaf(dt, r, u0);
           const float m = m0[c];
@@ -200,6 +222,16 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
     }
 #pragma unroll
     for (int c = 0; c < D; ++c) fzl[c] = fzu[c];
+  };
+  if constexpr (D == 3) {
+    for (int kb = k0; kb < k1; kb += NP) {
+      step(IC<0>{}, kb);
+      if (kb + 1 < k1) step(IC<1>{}, kb + 1);
+      if (kb + 2 < k1) step(IC<2>{}, kb + 2);
+      if (kb + 3 < k1) step(IC<3>{}, kb + 3);
+    }
+  } else {
+    step(IC<0>{}, 0);
   }
 }
 

@@ -302,6 +302,21 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
     }
     return __fdividef(sum - lds(P.z + e), dg_int);
   };
+  // two cells at once in packed FP32 pairs (each lane rounds as relax_fast does)
+  auto relax_fast2 = [&](const Planes& P, uint32_t e0, uint32_t e1) -> float2 {
+    const uint32_t a0 = P.x0 + e0, a1 = P.x0 + e1;
+    const float2 u2 = make_float2(uv, uv);
+    float2 sum = fma2(u2, make_float2(lds<4>(a0), lds<4>(a1)), make_float2(0.f, 0.f));
+    sum = fma2(u2, make_float2(lds<-4>(a0), lds<-4>(a1)), sum);
+    sum = fma2(u2, make_float2(lds<4 * BX>(a0), lds<4 * BX>(a1)), sum);
+    sum = fma2(u2, make_float2(lds<-4 * BX>(a0), lds<-4 * BX>(a1)), sum);
+    if (D == 3) {
+      sum = fma2(u2, make_float2(lds(P.xp + e0), lds(P.xp + e1)), sum);
+      sum = fma2(u2, make_float2(lds(P.xm + e0), lds(P.xm + e1)), sum);
+    }
+    const float2 d = sub2(sum, make_float2(lds(P.z + e0), lds(P.z + e1)));
+    return make_float2(__fdividef(d.x, dg_int), __fdividef(d.y, dg_int));
+  };
   auto relax = [&](const Planes& P, uint32_t e) -> float {
     const uint32_t x0 = P.x0 + e, l0 = P.l0 + e, l1 = P.l1 + e;
     const float l0u = lds<4>(l0), l0d = lds(l0), l1u = lds<4 * BX>(l1), l1d = lds(l1);
@@ -386,9 +401,9 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
   auto red_plane = [&](const Planes& P, int par, int kk) {
     const uint32_t e0 = par ? er[0][1] : er[0][0], e1 = par ? er[1][1] : er[1][0];
     if (UNI && interior) {
-      const float v0 = relax_fast(P, e0), v1 = relax_fast(P, e1);
-      sts(P.x0 + e0, v0);
-      sts(P.x0 + e1, v1);
+      const float2 v = relax_fast2(P, e0, e1);
+      sts(P.x0 + e0, v.x);
+      sts(P.x0 + e1, v.y);
       if (has_edge) {
         const uint32_t f = par ? ee[1] : ee[0];
         sts(P.x0 + f, relax_fast(P, f));
@@ -399,10 +414,16 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
       const uint32_t fm = (zlo && zhi && kin) ? fast_m >> par : 0u;
-      const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, par ? mr[0][1] : mr[0][0], zlo, zhi, kin);
-      const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mr[1][1] : mr[1][0], zlo, zhi, kin);
-      sts(P.x0 + e0, v0);
-      sts(P.x0 + e1, v1);
+      if ((fm & 5u) == 5u) {
+        const float2 v = relax_fast2(P, e0, e1);
+        sts(P.x0 + e0, v.x);
+        sts(P.x0 + e1, v.y);
+      } else {
+        const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, par ? mr[0][1] : mr[0][0], zlo, zhi, kin);
+        const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mr[1][1] : mr[1][0], zlo, zhi, kin);
+        sts(P.x0 + e0, v0);
+        sts(P.x0 + e1, v1);
+      }
       if (has_edge) {
         const uint32_t f = par ? ee[1] : ee[0];
         sts(P.x0 + f, (fm & 256u) ? relax_fast(P, f) : relax_uni(P, f, par ? me[1] : me[0], zlo, zhi, kin));
@@ -423,9 +444,9 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
     if (UNI && interior) {
       if (two_black) {
         const uint32_t e1 = par ? eb[1][1] : eb[1][0];
-        const float v0 = relax_fast(P, e0), v1 = relax_fast(P, e1);
-        sts(P.x0 + e0, v0);
-        sts(P.x0 + e1, v1);
+        const float2 v = relax_fast2(P, e0, e1);
+        sts(P.x0 + e0, v.x);
+        sts(P.x0 + e1, v.y);
       } else {
         sts(P.x0 + e0, relax_fast(P, e0));
       }
@@ -436,6 +457,13 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       zmask(kk, zlo, zhi, kin);
       const uint32_t m0 = par ? mb[0][1] : mb[0][0];
       const uint32_t fm = (zlo && zhi && kin) ? fast_m >> (4 + par) : 0u;
+      if (two_black && (fm & 5u) == 5u) {
+        const uint32_t e1 = par ? eb[1][1] : eb[1][0];
+        const float2 v = relax_fast2(P, e0, e1);
+        sts(P.x0 + e0, v.x);
+        sts(P.x0 + e1, v.y);
+        return;
+      }
       const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, m0, zlo, zhi, kin);
       if (two_black) {
         const uint32_t e1 = par ? eb[1][1] : eb[1][0];
@@ -731,14 +759,17 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
     const float* L2 = A0 + LY::oL2;
     const float* L2u = Ap + LY::oL2;
     const int gj = j0 + ty;
+    // this thread's cells (lane, ty) and (lane + 32, ty): right-hand side, face
+    // coefficients (x up/down, y up/down, z up/down) and whether the cell exists
+    float zv[2], cf[2][6];
+    bool inb[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int ii = lane + 32 * h;
       const int gi = i0 + ii;
-      const int e = (ty + 1) * BX + ii + 4;  // pressure boxes (from row -1)
-      const int c = ty * BX + ii + 4;        // the other boxes (from row 0)
+      const int c = ty * BX + ii + 4;  // the boxes other than the pressure (from row 0)
       const bool in = gi < g.n[0] && gj < g.n[1];
-      float z;
+      inb[h] = in;
       if (DIV) {
         const float* U0 = B0 + LY::oU0;
         const float* U1 = B0 + LY::oU1;
@@ -750,61 +781,76 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
         div += uxp - U0[c];
         div += uyp - U1[c];
         div += uzp - (A0 + LY::oU2)[c];
-        z = div * inv;
-        if (in) a.z[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = z;
+        zv[h] = div * inv;
+        if (in) a.z[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = zv[h];
       } else {
-        z = (B0 + LY::oZ)[c];
+        zv[h] = (B0 + LY::oZ)[c];
       }
       // face coefficients: staged, or (UNI) 1 inside the grid and 0 across a wall
-      float cxu, cxd, cyu, cyd, czu, czd;
       if (UNI) {
-        cxu = gi + 1 < g.n[0] ? 1.f : 0.f;
-        cxd = gi > 0 ? 1.f : 0.f;
-        cyu = gj + 1 < g.n[1] ? 1.f : 0.f;
-        cyd = gj > 0 ? 1.f : 0.f;
-        czu = k + 1 < g.n[2] ? 1.f : 0.f;
-        czd = k > 0 ? 1.f : 0.f;
+        cf[h][0] = gi + 1 < g.n[0] ? 1.f : 0.f;
+        cf[h][1] = gi > 0 ? 1.f : 0.f;
+        cf[h][2] = gj + 1 < g.n[1] ? 1.f : 0.f;
+        cf[h][3] = gj > 0 ? 1.f : 0.f;
+        cf[h][4] = k + 1 < g.n[2] ? 1.f : 0.f;
+        cf[h][5] = k > 0 ? 1.f : 0.f;
       } else {
-        cxu = L0[c + 1];
-        cxd = L0[c];
-        cyu = L1[c + BX];
-        cyd = L1[c];
-        czu = L2u[c];
-        czd = L2[c];
+        cf[h][0] = L0[c + 1];
+        cf[h][1] = L0[c];
+        cf[h][2] = L1[c + BX];
+        cf[h][3] = L1[c];
+        cf[h][4] = L2u[c];
+        cf[h][5] = L2[c];
       }
-      float r;
-      if (DF) {
-        const float h0 = ph0[e], l0 = pl0[e];
-        float ah = 0.f, al = 0.f;
-        auto face = [&](float L, float hn, float ln) {
-          float dh, dl, th, tl, sh, sl;
-          two_sum(hn, -h0, dh, dl);
-          dl += ln - l0;
-          two_prod(L, dh, th, tl);
-          tl = fmaf(L, dl, tl);
-          two_sum(ah, th, sh, sl);
-          ah = sh;
-          al += sl + tl;
-        };
-        // a missing neighbour across a wall reads 0 with a 0 coefficient: adds exactly 0
-        face(cxu, ph0[e + 1], pl0[e + 1]);
-        face(cxd, ph0[e - 1], pl0[e - 1]);
-        face(cyu, ph0[e + BX], pl0[e + BX]);
-        face(cyd, ph0[e - BX], pl0[e - BX]);
-        face(czu, php[e], plp[e]);
-        face(czd, phm[e], plm[e]);
-        float rh, rl;
-        two_sum(z, -ah, rh, rl);
-        r = rh + (rl - al);
-      } else {
+    }
+    const int e0 = (ty + 1) * BX + lane + 4;  // pressure boxes (from row -1); the second cell is 32 further
+    float rr[2];
+    if (DF) {
+      // both cells at once in packed FP32 pairs (each lane rounds as the scalar
+      // operation would: the same error-free transformations, the same bits)
+      auto P2 = [&](const float* f, int o) { return make_float2(f[e0 + o], f[e0 + 32 + o]); };
+      auto C2 = [&](int t) { return make_float2(cf[0][t], cf[1][t]); };
+      const float2 h0 = P2(ph0, 0), l0 = P2(pl0, 0);
+      float2 ah = make_float2(0.f, 0.f), al = make_float2(0.f, 0.f);
+      auto face = [&](float2 L, float2 hn, float2 ln) {
+        float2 dh, dl, th, tl, sh, sl;
+        two_sum2(hn, neg2(h0), dh, dl);
+        dl = add2(dl, sub2(ln, l0));
+        two_prod2(L, dh, th, tl);
+        tl = fma2(L, dl, tl);
+        two_sum2(ah, th, sh, sl);
+        ah = sh;
+        al = add2(al, add2(sl, tl));
+      };
+      // a missing neighbour across a wall reads 0 with a 0 coefficient: adds exactly 0
+      face(C2(0), P2(ph0, 1), P2(pl0, 1));
+      face(C2(1), P2(ph0, -1), P2(pl0, -1));
+      face(C2(2), P2(ph0, BX), P2(pl0, BX));
+      face(C2(3), P2(ph0, -BX), P2(pl0, -BX));
+      face(C2(4), P2(php, 0), P2(plp, 0));
+      face(C2(5), P2(phm, 0), P2(plm, 0));
+      float2 rh, rl;
+      two_sum2(make_float2(zv[0], zv[1]), neg2(ah), rh, rl);
+      const float2 r2 = add2(rh, sub2(rl, al));
+      rr[0] = r2.x;
+      rr[1] = r2.y;
+    } else {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = e0 + 32 * h;
         const float x0 = ph0[e];
         float acc = 0.f;
-        acc += cxu * (ph0[e + 1] - x0) + cxd * (ph0[e - 1] - x0);
-        acc += cyu * (ph0[e + BX] - x0) + cyd * (ph0[e - BX] - x0);
-        acc += czu * (php[e] - x0) + czd * (phm[e] - x0);
-        r = z - acc;
+        acc += cf[h][0] * (ph0[e + 1] - x0) + cf[h][1] * (ph0[e - 1] - x0);
+        acc += cf[h][2] * (ph0[e + BX] - x0) + cf[h][3] * (ph0[e - BX] - x0);
+        acc += cf[h][4] * (php[e] - x0) + cf[h][5] * (phm[e] - x0);
+        rr[h] = zv[h] - acc;
       }
-      if (in) {
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int gi = i0 + lane + 32 * h;
+      float r = rr[h];
+      if (inb[h]) {
         if (a.rout) a.rout[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = r;
         mbits = max(mbits, __float_as_uint(fabsf(r)));
       } else {
