@@ -712,21 +712,46 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
       wl[t] = DF ? __ldg(a.pl + o[t] + c0) : 0.f;
     }
   }
+  // per-plane operands, loaded one plane ahead of their use: y neighbour's pressure,
+  // face coefficients and velocity of the cell, and (CFL) the upper y face's operands
+  struct PlaneVals {
+    float ymh, yml, L0, L1, L2, u0, u1, u2, yph, ypl, uyp, Lyp;
+  };
+  auto load_plane = [&](int k, PlaneVals& v) {
+    const long long ok = zoff(k), q = ok + c0;
+    v.ymh = __ldg(P + ok + cym);
+    v.yml = DF ? __ldg(a.pl + ok + cym) : 0.f;
+    v.L0 = __ldg(a.L[0] + q);
+    v.L1 = __ldg(a.L[1] + q);
+    v.L2 = __ldg(a.L[2] + q);
+    v.u0 = __ldg(a.u_in[0] + q);
+    v.u1 = __ldg(a.u_in[1] + q);
+    v.u2 = __ldg(a.u_in[2] + q);
+    if (CFL && hyp) {
+      v.yph = __ldg(P + ok + cyp);
+      v.ypl = DF ? __ldg(a.pl + ok + cyp) : 0.f;
+      v.uyp = __ldg(a.u_in[1] + ok + cyp);
+      v.Lyp = __ldg(a.L[1] + ok + cyp);
+    }
+  };
+  PlaneVals cur;
+  load_plane(kb, cur);
   float m = 0.f;
   for (int k = kb; k < ke; ++k) {
     const long long ok = zoff(k);
     const long long q = ok + c0;
+    // plane k+1 (for k + 1 = ke an in-range plane whose values go unused, except the
+    // z-velocity and coefficient of the upper z face)
+    PlaneVals nxt;
+    load_plane(k + 1, nxt);
     float xmh = __shfl_up_sync(0xffffffffu, wh[1], 1), xml = __shfl_up_sync(0xffffffffu, wl[1], 1);
     if (edge_xm) {
       xmh = __ldg(P + ok + cxm);
       xml = DF ? __ldg(a.pl + ok + cxm) : 0.f;
     }
-    const float ymh = __ldg(P + ok + cym), yml = DF ? __ldg(a.pl + ok + cym) : 0.f;
-    const float L0 = __ldg(a.L[0] + q), L1 = __ldg(a.L[1] + q), L2 = __ldg(a.L[2] + q);
-    const float u0 = __ldg(a.u_in[0] + q), u1 = __ldg(a.u_in[1] + q), u2 = __ldg(a.u_in[2] + q);
-    const float lo0 = u0 - s * L0 * dp(wh[1], wl[1], xmh, xml);
-    const float lo1 = u1 - s * L1 * dp(wh[1], wl[1], ymh, yml);
-    const float lo2 = u2 - s * L2 * dp(wh[1], wl[1], wh[0], wl[0]);
+    const float lo0 = cur.u0 - s * cur.L0 * dp(wh[1], wl[1], xmh, xml);
+    const float lo1 = cur.u1 - s * cur.L1 * dp(wh[1], wl[1], cur.ymh, cur.yml);
+    const float lo2 = cur.u2 - s * cur.L2 * dp(wh[1], wl[1], wh[0], wl[0]);
     if (inxy) {
       a.u_out[0][q] = lo0;
       a.u_out[1][q] = lo1;
@@ -734,7 +759,7 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
     }
     if (CFL) {
       // corrected upper faces: x from the next lane, y loaded, z from the window
-      float uxp = __shfl_down_sync(0xffffffffu, u0, 1), Lxp = __shfl_down_sync(0xffffffffu, L0, 1);
+      float uxp = __shfl_down_sync(0xffffffffu, cur.u0, 1), Lxp = __shfl_down_sync(0xffffffffu, cur.L0, 1);
       float xph = __shfl_down_sync(0xffffffffu, wh[1], 1), xpl = __shfl_down_sync(0xffffffffu, wl[1], 1);
       if (edge_xp) {
         uxp = __ldg(a.u_in[0] + ok + cxp);
@@ -744,16 +769,8 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
       }
       const float up0 = hxp ? uxp - s * Lxp * dp(xph, xpl, wh[1], wl[1])
                             : (g.exit ? __ldg(a.u_in[0] + exit_index(g, jc, k)) : g.U[0]);
-      float up1 = g.U[1];
-      if (hyp) {
-        const float yph = __ldg(P + ok + cyp), ypl = DF ? __ldg(a.pl + ok + cyp) : 0.f;
-        up1 = __ldg(a.u_in[1] + ok + cyp) - s * __ldg(a.L[1] + ok + cyp) * dp(yph, ypl, wh[1], wl[1]);
-      }
-      float up2 = g.U[2];
-      if (k + 1 < n2 || per2) {
-        const long long qz = zoff(k + 1) + c0;
-        up2 = __ldg(a.u_in[2] + qz) - s * __ldg(a.L[2] + qz) * dp(wh[2], wl[2], wh[1], wl[1]);
-      }
+      const float up1 = hyp ? cur.uyp - s * cur.Lyp * dp(cur.yph, cur.ypl, wh[1], wl[1]) : g.U[1];
+      const float up2 = (k + 1 < n2 || per2) ? nxt.u2 - s * nxt.L2 * dp(wh[2], wl[2], wh[1], wl[1]) : g.U[2];
       float mc = 0.f;
       mc += fmaxf(0.f, up0) + fmaxf(0.f, -lo0);
       mc += fmaxf(0.f, up1) + fmaxf(0.f, -lo1);
@@ -769,6 +786,7 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
       wh[2] = __ldg(P + o2 + c0);
       wl[2] = DF ? __ldg(a.pl + o2 + c0) : 0.f;
     }
+    cur = nxt;
   }
   if (CFL) {
     const unsigned mb = block_max_bits<256>(__float_as_uint(fabsf(m)), s_m);
