@@ -329,6 +329,9 @@ ResArgs res_args(wl_sim* s, int l, int mode) {
   ResArgs a{};
   const LevelBuf& L = s->lev[l];
   for (int c = 0; c < 3; ++c) a.L[c] = L.Lk[c];
+  // no body: the band box is empty and every coefficient is the level's free-stream value
+  a.uni = (L.band.on && L.band.lo[0] >= L.band.hi[0]) ? 1 : 0;
+  a.uval = L.uval;
   a.x = L.x;
   a.z = L.z;
   a.zc = (l + 1 < s->nlev) ? s->lev[l + 1].z : nullptr;
@@ -441,6 +444,9 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   // the coarse levels' values carry the factor 2^cs_used; the fine level removes it
   if (l == 0 && s->lev[1].z32) a.cs = s->ds;
   a.tz = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
+  // no body: the band box is empty and every coefficient is the level's free-stream value
+  a.uni = (L.band.on && L.band.lo[0] >= L.band.hi[0]) ? 1 : 0;
+  a.uval = L.uval;
   float* bufs[2] = {L.x, L.x2};
   const CUtensorMap* bmaps[2] = {&L.mx, &L.mx2};
   const bool from_x = (l == 0 && !refine);  // precision 0: the fine iterate is the pressure itself

@@ -51,6 +51,8 @@ struct ResArgs {
   float inv_w;         // divergence modes: z = div u * inv_w / dt
   DevState* st;        // dt and the running max |residual|
   int mode;
+  int uni;             // 1: no body on the level, so every face coefficient is uval (0 across
+  float uval;          //   a non-periodic wall) and is formed instead of loaded
 };
 
 // A 16-bit level (stype != ST_F32) keeps x_in, z, L and x_out in that type (the
@@ -72,6 +74,8 @@ struct SweepArgs {
   int cn[3];
   int tz;              // planes per block (3-D)
   int only_wrapping;   // 1: sweep only the tiles whose footprint crosses a periodic side
+  int uni;             // 1: no body on the level, so every face coefficient is uval (0 across
+  float uval;          //   a non-periodic wall) and is formed instead of loaded
 };
 
 // Region of a level (level cell coordinates, [lo, hi) per direction) whose face

@@ -97,7 +97,8 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
       bool has;
       const long long qu = nb_up(g, c, I[c], q, st[c], has);
       const long long qm = nb_dn(g, c, I[c], q, st[c]);
-      const float Lf[2] = {has ? __ldg(a.L[c] + qu) : 0.f, __ldg(a.L[c] + q)};
+      const float Lf[2] = {has ? (a.uni ? a.uval : __ldg(a.L[c] + qu)) : 0.f,
+                           a.uni ? ((I[c] > 0 || is_per(g, c)) ? a.uval : 0.f) : __ldg(a.L[c] + q)};
       const long long qn[2] = {qu, qm};
 #pragma unroll
       for (int sd = 0; sd < 2; ++sd) {
@@ -122,8 +123,8 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
       bool has;
       const long long qu = nb_up(g, c, I[c], q, st[c], has);
       const long long qm = nb_dn(g, c, I[c], q, st[c]);
-      const float Lu = has ? __ldg(a.L[c] + qu) : 0.f;
-      const float Ll = __ldg(a.L[c] + q);
+      const float Lu = has ? (a.uni ? a.uval : __ldg(a.L[c] + qu)) : 0.f;
+      const float Ll = a.uni ? ((I[c] > 0 || is_per(g, c)) ? a.uval : 0.f) : __ldg(a.L[c] + q);
       acc += Lu * (__ldg(a.x + qu) - x0) + Ll * (__ldg(a.x + qm) - x0);
     }
     r = z - acc;
@@ -270,7 +271,12 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     }
     return v;
   };
-  // right-hand side and face coefficients of the cell at tile position (ii, jj)
+  // right-hand side and face coefficients of the cell at tile position (ii, jj); on a
+  // level without a body (uni) the coefficients are formed: uval on every face, 0 on a
+  // non-periodic wall face (the values stored there, so the same bits)
+  const bool uni = a.uni != 0;
+  const float uv = a.uval;
+  const bool px = is_per(g, 0), py = is_per(g, 1), pz = is_per(g, 2);
   auto fetch = [&](int ii, int jj, int zo, int zou, RelaxIn& c) {
     const int col = ii + 2, row = jj + 2;
     const int xo = s_xo[col], yo = s_yo[row];
@@ -280,6 +286,17 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     c.z = ldf(zf, q);
     if constexpr (!std::is_same<T, float>::value) c.z *= a.zmul;
     const int xu = s_xo[col + 1], yu = s_yo[row + 1];
+    if (uni) {
+      c.Ll[0] = (xo > 0 || px) ? uv : 0.f;
+      c.Lu[0] = xu >= 0 ? uv : 0.f;
+      c.Ll[1] = (yo > 0 || py) ? uv : 0.f;
+      c.Lu[1] = yu >= 0 ? uv : 0.f;
+      if (D == 3) {
+        c.Ll[2] = (zo > 0 || pz) ? uv : 0.f;
+        c.Lu[2] = zou >= 0 ? uv : 0.f;
+      }
+      return;
+    }
     c.Ll[0] = ldf(Lf[0], q);
     c.Lu[0] = xu >= 0 ? ldf(Lf[0], xu + yo + zo) : 0.f;
     c.Ll[1] = ldf(Lf[1], q);
@@ -347,11 +364,14 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     __syncthreads();
   }
   const int P0 = (i0 + j0 + ty) & 1;  // parity of column 2*tx in plane 0
-  for (int k = k0; k < k1; ++k) {
-    // ---- issue every global load of this iteration
+  // The global loads of iteration k are issued one phase of iteration k-1 ahead of
+  // their use, each into registers that phase has just freed: the new iterate plane
+  // (k+2) after the previous one is committed, the red cells' operands (plane k+1)
+  // after the red phase, the black cell's (plane k) after the black phase.
+  float xv[SW_LOADS];
+  auto load_x = [&](int k) {
     const int kn = (D == 3) ? k + 2 : 0;
     const int zn = zoff(kn), czn = czoff(kn);
-    float xv[SW_LOADS];
 #pragma unroll
     for (int m = 0; m < SW_LOADS; ++m) {
       const int e = tid + 256 * m;
@@ -361,10 +381,12 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         xv[m] = xeff(col, row, zn, czn);
       }
     }
+  };
+  RelaxIn rc[2];
+  int rii[2], rjj[2];
+  auto load_red = [&](int k) {
     const int kr = (D == 3) ? k + 1 : 0;
     const int zr = zoff(kr), zru = zoff(kr + 1);
-    RelaxIn rc[2];
-    int rii[2], rjj[2];
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
       const int e = tid + 256 * m;
@@ -374,13 +396,23 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         fetch(rii[m], rjj[m], zr, zru, rc[m]);
       }
     }
-    const int P = (P0 + k) & 1;
-    const int ib = 2 * tx + (P ^ 1), ir = 2 * tx + P;
-    const int zk = zoff(k);
-    RelaxIn bc;
+  };
+  RelaxIn bc;
+  int P = 0, ib = 0, ir = 0;
+  auto load_black = [&](int k) {
+    P = (P0 + k) & 1;
+    ib = 2 * tx + (P ^ 1);
+    ir = 2 * tx + P;
     bc.ok = false;
-    if (i0 + ib < g.n[0] && j0 + ty < g.n[1]) fetch(ib, ty, zk, zoff(k + 1), bc);
+    if (i0 + ib < g.n[0] && j0 + ty < g.n[1]) fetch(ib, ty, zoff(k), zoff(k + 1), bc);
+  };
+  load_x(k0);
+  load_red(k0);
+  load_black(k0);
+  for (int k = k0; k < k1; ++k) {
+    const bool more = k + 1 < k1;
     // ---- new plane into the ring (2-D: the only plane)
+    const int kn = (D == 3) ? k + 2 : 0;
 #pragma unroll
     for (int m = 0; m < SW_LOADS; ++m) {
       const int e = tid + 256 * m;
@@ -389,18 +421,21 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         s_x[slot(kn)][row][col] = xv[m];
       }
     }
+    if (more) load_x(k + 1);
     __syncthreads();
     // ---- red cells of plane kr on the tile plus halo
+    const int kr = (D == 3) ? k + 1 : 0;
 #pragma unroll
     for (int m = 0; m < 2; ++m)
       if (rc[m].ok) s_x[slot(kr)][rjj[m] + 2][rii[m] + 2] = relax(rc[m], rii[m], rjj[m], kr);
+    if (more) load_red(k + 1);
     __syncthreads();
     // ---- black cells of plane k on the tile, one per thread; write plane k
     const float vb = bc.ok ? relax(bc, ib, ty, k) : 0.f;
     const float vr = s_x[slot(k)][ty + 2][ir + 2];
     const int gi = i0 + 2 * tx, gj = j0 + ty;
     if (gj < g.n[1] && gi < g.n[0]) {
-      const int q = gi + n0 * gj + zk;
+      const int q = gi + n0 * gj + zoff(k);
       const float v0 = P ? vb : vr, v1 = P ? vr : vb;
       const bool two = gi + 1 < g.n[0];
       if (std::is_same<T, float>::value && a.ph) {
@@ -423,6 +458,7 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
         if (two) xout[q + 1] = from_f<T>(v1);
       }
     }
+    if (more) load_black(k + 1);
     __syncthreads();
   }
 }

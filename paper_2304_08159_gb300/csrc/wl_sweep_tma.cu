@@ -519,17 +519,13 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
       const float2 v = *reinterpret_cast<const float2*>(smf + Xk + est[r]);
       const long long q = q0[r] + (D == 3 ? qk * k : 0);
       if (a.ph) {
-        const float vv[2] = {v.x, v.y}, oh[2] = {hph[r].x, hph[r].y}, ol[2] = {hpl[r].x, hpl[r].y};
-        float nh[2], nl[2];
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          float sh, sl;
-          two_sum(oh[t], vv[t], sh, sl);
-          sl += ol[t];
-          fast_two_sum(sh, sl, nh[t], nl[t]);
-        }
-        *reinterpret_cast<float2*>(a.ph + q) = make_float2(nh[0], nh[1]);
-        *reinterpret_cast<float2*>(a.pl + q) = make_float2(nl[0], nl[1]);
+        // (ph, pl) += v for both columns at once in packed pairs (the scalar bits)
+        float2 sh, sl;
+        two_sum2(hph[r], v, sh, sl);
+        sl = add2(sl, hpl[r]);
+        const float2 nh = add2(sh, sl);
+        *reinterpret_cast<float2*>(a.ph + q) = nh;
+        *reinterpret_cast<float2*>(a.pl + q) = sub2(sl, sub2(nh, sh));
       } else {
         *reinterpret_cast<float2*>(a.x_out + q) = v;
       }

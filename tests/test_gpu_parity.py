@@ -338,8 +338,8 @@ def test_vcycle_tail_matches_per_level_kernels(case, monkeypatch):
     assert np.array_equal(a.get(1), b.get(1))
 
 
-@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[2], CASES_3D[4], CASES_2D[0], CASES_2D[3]],
-                         ids=lambda c: c["id"])
+@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[1], CASES_3D[2], CASES_3D[4], CASES_2D[0], CASES_2D[2],
+                                  CASES_2D[3]], ids=lambda c: c["id"])
 def test_uniform_tiles_match_loading_kernels(case, monkeypatch):
     """Tiles away from the body form their face coefficients (the level's free-stream
     value, 0 on walls) instead of loading them: identical bits to the kernels that load
@@ -362,11 +362,14 @@ def test_uniform_tiles_match_loading_kernels(case, monkeypatch):
     dict(id="channel128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.2, 0.0), periodic=0, body=None),
     dict(id="yper128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.0, 0.0), periodic=2,
          body=dict(kind=1, center=(40.0, 30.0, 24.0), radius=6.0)),
+    dict(id="tgv64", dims=(64, 64, 64), nu=0.01, U=(0.0, 0.0, 0.0), periodic=7, body=None),
+    dict(id="xchannel128", dims=(128, 32, 32), nu=0.01, U=(1.0, 0.0, 0.0), periodic=1, body=None),
 ], ids=lambda c: c["id"])
 def test_uniform_tiles_large_sphere_bitwise(case, monkeypatch):
     """Grids large enough for many uniform tiles on several levels (a band of loading
     tiles around the sphere; a body-free channel whose uniform tiles meet every wall; a
-    periodic side): identical bits either way."""
+    periodic side; body-free periodic grids, whose tiles across a periodic side form
+    their coefficients in the table kernel): identical bits either way."""
     monkeypatch.setenv("WL_UNIFORM_ALL", "1")
     a, _ = make_pair(case, oracle=False)
     monkeypatch.delenv("WL_UNIFORM_ALL")
