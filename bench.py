@@ -96,6 +96,19 @@ def algo_bytes(cls, D, n_div=0, n_res=0, band_fraction=1.0):
 
 KERNEL_NAMES = {"sweep_fine": "k_sweep_tma<3> (fine level)", "resid_fine": "k_resid_tma (fine level)",
                 "stage": "k_stage<3>", "correct": "k_correct3"}
+
+
+def kernel_name(cls, D, periodic):
+    """The kernels behind a class on this grid: tiles across a periodic x or y side sweep
+    in the table kernel k_sweep, and the fine residual of a periodic grid is k_residual."""
+    name = KERNEL_NAMES[cls].replace("<3>", f"<{D}>")
+    if cls == "sweep_fine" and periodic & 3:
+        name = f"k_sweep_tma<{D}> + k_sweep<{D}> (fine level; k_sweep: tiles across a periodic side)"
+    if cls == "resid_fine" and (periodic or D == 2):
+        name = f"k_residual<{D}> (fine level)"
+    if cls == "correct" and D == 2:
+        name = "k_correct<2>"
+    return name
 KERNEL_SRC = {"sweep_fine": "wl_sweep_tma.cu", "resid_fine": "wl_sweep_tma.cu", "stage": "wl_momentum.cu",
               "correct": "wl_poisson.cu"}
 
@@ -313,7 +326,7 @@ def run_ours(args, w, dist, rank, ws, lrank):
     bytes_launch = algo_bytes(cls, D, nd, n - nd, band_fraction) * ncell
     avg_s = ms_tot / n / 1e3
     achieved = bytes_launch / avg_s / 1e9
-    roof = {"bound": "hbm", "kernel": KERNEL_NAMES[cls], "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roof = {"bound": "hbm", "kernel": kernel_name(cls, D, w["periodic"]), "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "peak_kind": peak_kind, "traffic": _traffic(cls, ncell),
             "algorithmic_bytes_per_launch": bytes_launch, "avg_launch_ms": avg_s * 1e3,
             "coefficients_read_by_fraction_of_tiles": band_fraction,
