@@ -443,7 +443,10 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   a.zmul = 1.f / L.zs;
   // the coarse levels' values carry the factor 2^cs_used; the fine level removes it
   if (l == 0 && s->lev[1].z32) a.cs = s->ds;
-  a.tz = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
+  // z-blocking for each kernel's own residency: the table kernel (tiles across a periodic
+  // side, 16-bit levels) and the staged one (uniform or loading variant)
+  a.tz = sweep_planes_per_block(L.g, sweep_table_blocks_per_sm(s->D, L.st));
+  const int tz_staged = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
   // no body: the band box is empty and every coefficient is the level's free-stream value
   a.uni = (L.band.on && L.band.lo[0] >= L.band.hi[0]) ? 1 : 0;
   a.uval = L.uval;
@@ -478,7 +481,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       t.pl = a.pl;
       t.g = a.g;
       for (int d = 0; d < 3; ++d) t.cn[d] = a.cn[d];
-      t.tz = a.tz;
+      t.tz = tz_staged;
       t.st = s->ds;
       PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st, side_of(s)));
       a.only_wrapping = 1;  // tiles crossing a periodic side

@@ -210,6 +210,7 @@ int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s, 
 int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s);
 // planes per block of the sweep kernels for blocks_per_sm resident blocks
 int sweep_planes_per_block(const Grid& g, int blocks_per_sm);
+int sweep_table_blocks_per_sm(int D, int stype);
 
 // Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.
 // A tile whose TMA footprint (x i0-4..i0+67, y j0-2..j0+9) crosses a periodic x or y

@@ -463,10 +463,10 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   }
 }
 
-// planes per block: enough blocks to fill the GPU, at most 32 planes per march
-// Planes per block of both sweep kernels: the z-blocking that minimises the modelled
-// time, whole waves of blocks (SWEEP_BLOCKS_PER_SM resident per SM) times the planes a block
-// marches through plus about 1.5 planes of prologue and epilogue work.
+// Planes per block of the sweep kernels (at most 32 per march): the z-blocking that
+// minimises the modelled time, whole waves of blocks (blocks_per_sm resident per SM, the
+// kernel's own residency) times the planes a block marches through plus about 1.5 planes
+// of prologue and epilogue work.
 int sweep_planes_per_block(const Grid& g, int blocks_per_sm) {
   static int nsm = 0;
   if (nsm <= 0) {
@@ -490,6 +490,30 @@ int sweep_planes_per_block(const Grid& g, int blocks_per_sm) {
     }
   }
   return best;
+}
+
+// resident blocks per SM of the table kernel for a level's storage type (from the
+// occupancy calculator once per variant; its register count decides it)
+int sweep_table_blocks_per_sm(int D, int stype) {
+  static int cache[2][3] = {};
+  if (D < 2 || D > 3 || stype < 0 || stype > 2) return SWEEP_BLOCKS_PER_SM;
+  int& c = cache[D - 2][stype];
+  if (c > 0) return c;
+  int n = 0;
+  cudaError_t e;
+  if (D == 3)
+    e = stype == ST_BF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<3, __nv_bfloat16>, 256, 0)
+        : stype == ST_F16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<3, __half>, 256, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<3, float>, 256, 0);
+  else
+    e = stype == ST_BF16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, __nv_bfloat16>, 256, 0)
+        : stype == ST_F16 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, __half>, 256, 0)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep<2, float>, 256, 0);
+  if (e != cudaSuccess || n <= 0) {
+    cudaGetLastError();
+    n = SWEEP_BLOCKS_PER_SM;
+  }
+  return c = n;
 }
 
 template <int D>
@@ -1358,6 +1382,8 @@ __global__ void __launch_bounds__(1024) k_apply_pinv(DenseArgs a) {
   __syncthreads();
   for (int i = threadIdx.x; i < nc; i += blockDim.x) {
     double acc = 0.0;
+    // unrolled so that many rows of G are in flight; the sum keeps its order
+#pragma unroll 16
     for (int jj = 0; jj < nc; ++jj) acc += __ldg(a.G + (long long)jj * nc + i) * zs[jj];
     a.x[i] = (float)acc;
   }
@@ -1440,6 +1466,8 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs a) {
     float* xc = zc + nc;
     for (int i = tid; i < nc; i += kTailThreads) {
       double acc = 0.0;
+      // unrolled so that many rows of G are in flight; the sum keeps its order
+#pragma unroll 16
       for (int jj = 0; jj < nc; ++jj) acc += __ldg(a.G + (long long)jj * nc + i) * (double)zc[jj];
       xc[i] = (float)acc;
     }
