@@ -385,3 +385,84 @@ def test_uniform_tiles_large_sphere_bitwise(case, monkeypatch):
     b.step(4)
     assert np.array_equal(a.get(0), b.get(0))
     assert np.array_equal(a.get(1), b.get(1))
+
+
+# --------------------------------------------------------------------------- full size
+def _bench_pair(name):
+    """The bench's workload `name` at its full size, created as bench.py creates it (CUDA-
+    graph steps, default options, Poisson tol 1e-6), and the FP64 oracle on the same
+    grid from the same initial condition."""
+    from bench import WORKLOADS
+    from paper_2304_08159_gb300 import Sim
+
+    w = WORKLOADS[name]
+    sim = Sim(w["dims"], w["nu"], w["U"], body=w["body"], periodic=w["periodic"], tol=1e-6)
+    ref = O.Oracle(w["dims"], w["nu"], U=w["U"], periodic=w["periodic"], body=w["body"])
+    if w["ic"]:
+        sim.set_ic(w["ic"], 1.0)
+    ref.set_ic(w["ic"], 1.0)
+    return w, sim, ref
+
+
+def _check_step_parity(w, sim, ref, nsteps, p_bar=2e-4):
+    rc, last, tot, worst = sim.status()
+    assert rc == 0 and worst <= 1e-6, (rc, last, tot, worst)
+    ug, uo = sim.get(0).astype(np.float64), ref.get_u()
+    act = active_mask(ref)
+    pg, po = sim.get(1).astype(np.float64), ref.get_p()
+    pg = (pg - pg[act].mean()) * act
+    po = (po - po[act].mean()) * act
+    print(f"{w['desc']}: {nsteps} step(s), u rel L2 {rel_l2(ug, uo):.2e}, p rel L2 {rel_l2(pg, po):.2e}, "
+          f"dt {sim.dt:.6g} vs {ref.dt:.6g}")
+    assert rel_l2(ug, uo) <= 1e-5, rel_l2(ug, uo)
+    assert rel_l2(pg, po) <= p_bar, rel_l2(pg, po)
+    t, n = sim.time()
+    assert n == nsteps and abs(t - ref.time) <= 1e-5 * ref.time
+    assert abs(sim.dt - ref.dt) <= 1e-5 * ref.dt
+    return ug, uo
+
+
+@pytest.mark.parametrize("name", ["sphere256", "sphere512"])
+def test_bench_sphere_first_step_full_size(name):
+    """The sphere workloads at full size (4.2 M and 33.5 M cells; the larger one is what
+    bench.py times): the first step from the uniform start, launched as the bench launches
+    it, against the oracle's step with multigrid projections to 1e-10.  Velocity and
+    pressure over every cell, dt, and the drag coefficient within its 1e-4 bar; the flow
+    keeps the sphere's mirror symmetry in y and z up to the solver tolerance."""
+    w, sim, ref = _bench_pair(name)
+    sim.step(1)
+    ref.step(1, tol=1e-10, maxit=200, solver=1)
+    ug, uo = _check_step_parity(w, sim, ref, 1)
+    R = w["body"]["radius"]
+    Fg, Fo = sim.forces(), ref.forces()
+    CDg, CDo = Fg[0] / (0.5 * np.pi * R * R), Fo[0] / (0.5 * np.pi * R * R)
+    print(f"C_D {CDg:.6f} vs {CDo:.6f}")
+    assert abs(CDg - CDo) <= 1e-4 * abs(CDo), (CDg, CDo)
+    # mirror symmetry about the sphere's centre planes (y = n1/2, z = n2/2): u and w are
+    # even in y, v odd (v sits on lower y faces, so its mirror is shifted by one face)
+    u = ug[0]
+    assert np.abs(u - u[:, ::-1, :]).max() <= 1e-4 * np.abs(u).max()
+    assert np.abs(u - u[::-1, :, :]).max() <= 1e-4 * np.abs(u).max()
+    v = ug[1]
+    assert np.abs(v[:, 1:, :] + v[:, :0:-1, :]).max() <= 1e-4 * np.abs(u).max()
+
+
+def test_bench_tgv_full_size_steps():
+    """The 128^3 Taylor-Green vortex at Re 1600 (the bench's periodic workload) at full
+    size: 10 steps against the oracle's (velocity, pressure, dt), kinetic energy
+    non-increasing every step, zero net momentum and a divergence-free field."""
+    w, sim, ref = _bench_pair("tgv128")
+    assert abs(sim.dt - ref.dt) <= 1e-6 * ref.dt
+    E = ref.kinetic_energy()
+    for s in range(10):
+        sim.step(1)
+        ref.step(1, tol=1e-10, maxit=200, solver=1)
+        E2 = ref.kinetic_energy()
+        assert E2 <= E
+        E = E2
+    ug, uo = _check_step_parity(w, sim, ref, 10, p_bar=1e-3)
+    Eg = 0.5 * (ug**2).sum() / ug[0].size
+    assert abs(Eg - E) <= 1e-5 * E
+    for c in range(3):
+        assert abs(ug[c].mean()) <= 1e-6
+    assert np.abs(sim.get(2)).max() <= 1e-5
