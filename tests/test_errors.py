@@ -20,6 +20,8 @@ def create(dims, nu=0.01, U=(1.0, 0.0, 0.0), body=None, opts=None):
 
 def test_bad_grids(lib):
     assert create((1, 8)) == wl.WL_EINVAL          # a side shorter than 2
+    assert create((0, 8)) == wl.WL_EINVAL          # an empty grid
+    assert create((8, -4)) == wl.WL_EINVAL
     for ndim in (1, 4):  # 1-D and 4-D, straight through the C ABI
         d = (ctypes.c_int * 4)(8, 8, 8, 8)
         u = (ctypes.c_double * 4)(1.0, 0.0, 0.0, 0.0)
