@@ -89,32 +89,63 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
   }
   float r;
   if (a.ph) {
-    // r = z - sum_f L_f (p_nb - p_0) with p = ph + pl in double-float arithmetic
+    // r = z - sum_f L_f (p_nb - p_0) with p = ph + pl in double-float arithmetic; faces
+    // in the order x up, x down, y up, y down (, z up, z down)
     const float h0 = __ldg(a.ph + q), l0 = __ldg(a.pl + q);
-    float ah = 0.f, al = 0.f;
+    float Lf[2 * D], hn[2 * D], ln[2 * D];
+    bool unit = true;
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       bool has;
       const long long qu = nb_up(g, c, I[c], q, st[c], has);
       const long long qm = nb_dn(g, c, I[c], q, st[c]);
-      const float Lf[2] = {has ? (a.uni ? a.uval : __ldg(a.L[c] + qu)) : 0.f,
-                           a.uni ? ((I[c] > 0 || is_per(g, c)) ? a.uval : 0.f) : __ldg(a.L[c] + q)};
-      const long long qn[2] = {qu, qm};
+      Lf[2 * c] = has ? (a.uni ? a.uval : __ldg(a.L[c] + qu)) : 0.f;
+      Lf[2 * c + 1] = a.uni ? ((I[c] > 0 || is_per(g, c)) ? a.uval : 0.f) : __ldg(a.L[c] + q);
+      hn[2 * c] = __ldg(a.ph + qu);
+      ln[2 * c] = __ldg(a.pl + qu);
+      hn[2 * c + 1] = __ldg(a.ph + qm);
+      ln[2 * c + 1] = __ldg(a.pl + qm);
+    }
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
+    for (int f = 0; f < 2 * D; ++f) unit = unit && (Lf[f] == 0.f || Lf[f] == 1.f);
+    float rh, rl;
+    if (unit) {
+      // every coefficient 1 or 0: the present neighbours' pressures summed in
+      // double-float, minus nf p0 (nf faces, a small integer: nf h0 exact by TwoProd)
+      float S = __fmul_rn(Lf[0], hn[0]), Se = 0.f, Sl = __fmul_rn(Lf[0], ln[0]), nf = Lf[0];
+#pragma unroll
+      for (int f = 1; f < 2 * D; ++f) {
+        float e;
+        two_sum(S, __fmul_rn(Lf[f], hn[f]), S, e);
+        Se = __fadd_rn(Se, e);
+        Sl = fmaf(Lf[f], ln[f], Sl);
+        nf = __fadd_rn(nf, Lf[f]);
+      }
+      float T, Te, Dh, Dl;
+      two_prod(nf, h0, T, Te);
+      Te = fmaf(nf, l0, Te);
+      two_sum(S, -T, Dh, Dl);
+      Dl = __fadd_rn(Dl, __fsub_rn(__fadd_rn(Se, Sl), Te));
+      two_sum(z, -Dh, rh, rl);
+      r = __fadd_rn(rh, __fsub_rn(rl, Dl));
+    } else {
+      // face by face: the exact difference to the neighbour times its coefficient
+      // (TwoSum, TwoProd), accumulated in double-float
+      float ah = 0.f, al = 0.f;
+#pragma unroll
+      for (int f = 0; f < 2 * D; ++f) {
         float dh, dl, th, tl, sh, sl;
-        two_sum(__ldg(a.ph + qn[sd]), -h0, dh, dl);
-        dl += __ldg(a.pl + qn[sd]) - l0;
-        two_prod(Lf[sd], dh, th, tl);
-        tl = fmaf(Lf[sd], dl, tl);
+        two_sum(hn[f], -h0, dh, dl);
+        dl += ln[f] - l0;
+        two_prod(Lf[f], dh, th, tl);
+        tl = fmaf(Lf[f], dl, tl);
         two_sum(ah, th, sh, sl);
         ah = sh;
         al += sl + tl;
       }
+      two_sum(z, -ah, rh, rl);
+      r = rh + (rl - al);
     }
-    float rh, rl;
-    two_sum(z, -ah, rh, rl);
-    r = rh + (rl - al);
   } else {
     const float x0 = __ldg(a.x + q);
     float acc = 0.f;

@@ -807,29 +807,63 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
       auto P2 = [&](const float* f, int o) { return make_float2(f[e0 + o], f[e0 + 32 + o]); };
       auto C2 = [&](int t) { return make_float2(cf[0][t], cf[1][t]); };
       const float2 h0 = P2(ph0, 0), l0 = P2(pl0, 0);
-      float2 ah = make_float2(0.f, 0.f), al = make_float2(0.f, 0.f);
-      auto face = [&](float2 L, float2 hn, float2 ln) {
-        float2 dh, dl, th, tl, sh, sl;
-        two_sum2(hn, neg2(h0), dh, dl);
-        dl = add2(dl, sub2(ln, l0));
-        two_prod2(L, dh, th, tl);
-        tl = fma2(L, dl, tl);
-        two_sum2(ah, th, sh, sl);
-        ah = sh;
-        al = add2(al, add2(sl, tl));
+      const float2 Lc[6] = {C2(0), C2(1), C2(2), C2(3), C2(4), C2(5)};
+      const float2 hn[6] = {P2(ph0, 1), P2(ph0, -1), P2(ph0, BX), P2(ph0, -BX), P2(php, 0), P2(phm, 0)};
+      const float2 ln[6] = {P2(pl0, 1), P2(pl0, -1), P2(pl0, BX), P2(pl0, -BX), P2(plp, 0), P2(plm, 0)};
+      // a cell whose face coefficients are all 1 or 0 (every uniform-tile cell, and most of
+      // a band tile's) takes the short form; the choice is the cell's own, so every kernel
+      // gives a cell the same bits (a missing neighbour across a wall reads 0 with a 0
+      // coefficient: adds exactly 0)
+      auto unit = [&](int h) {
+        bool ok = true;
+#pragma unroll
+        for (int t = 0; t < 6; ++t) ok = ok && (cf[h][t] == 0.f || cf[h][t] == 1.f);
+        return ok;
       };
-      // a missing neighbour across a wall reads 0 with a 0 coefficient: adds exactly 0
-      face(C2(0), P2(ph0, 1), P2(pl0, 1));
-      face(C2(1), P2(ph0, -1), P2(pl0, -1));
-      face(C2(2), P2(ph0, BX), P2(pl0, BX));
-      face(C2(3), P2(ph0, -BX), P2(pl0, -BX));
-      face(C2(4), P2(php, 0), P2(plp, 0));
-      face(C2(5), P2(phm, 0), P2(plm, 0));
-      float2 rh, rl;
-      two_sum2(make_float2(zv[0], zv[1]), neg2(ah), rh, rl);
-      const float2 r2 = add2(rh, sub2(rl, al));
-      rr[0] = r2.x;
-      rr[1] = r2.y;
+      const bool q0 = UNI || unit(0), q1 = UNI || unit(1);
+      float2 rf = make_float2(0.f, 0.f), rg = make_float2(0.f, 0.f);
+      if (q0 || q1) {
+        // short form: the present neighbours' pressures summed in double-float, minus
+        // nf p0 (nf faces, a small integer: nf h0 exact by TwoProd)
+        float2 S = mul2(Lc[0], hn[0]), Se = make_float2(0.f, 0.f), Sl = mul2(Lc[0], ln[0]);
+        float2 nf = Lc[0];
+#pragma unroll
+        for (int f = 1; f < 6; ++f) {
+          float2 e;
+          two_sum2(S, mul2(Lc[f], hn[f]), S, e);
+          Se = add2(Se, e);
+          Sl = fma2(Lc[f], ln[f], Sl);
+          nf = add2(nf, Lc[f]);
+        }
+        float2 T, Te, Dh, Dl, rh, rl;
+        two_prod2(nf, h0, T, Te);
+        Te = fma2(nf, l0, Te);
+        two_sum2(S, neg2(T), Dh, Dl);
+        Dl = add2(Dl, sub2(add2(Se, Sl), Te));
+        two_sum2(make_float2(zv[0], zv[1]), neg2(Dh), rh, rl);
+        rf = add2(rh, sub2(rl, Dl));
+      }
+      if (!UNI && !(q0 && q1)) {
+        // general form, face by face: the exact difference to the neighbour times its
+        // coefficient (TwoSum, TwoProd), accumulated in double-float
+        float2 ah = make_float2(0.f, 0.f), al = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          float2 dh, dl, th, tl, sh, sl;
+          two_sum2(hn[f], neg2(h0), dh, dl);
+          dl = add2(dl, sub2(ln[f], l0));
+          two_prod2(Lc[f], dh, th, tl);
+          tl = fma2(Lc[f], dl, tl);
+          two_sum2(ah, th, sh, sl);
+          ah = sh;
+          al = add2(al, add2(sl, tl));
+        }
+        float2 rh, rl;
+        two_sum2(make_float2(zv[0], zv[1]), neg2(ah), rh, rl);
+        rg = add2(rh, sub2(rl, al));
+      }
+      rr[0] = q0 ? rf.x : rg.x;
+      rr[1] = q1 ? rf.y : rg.y;
     } else {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
