@@ -803,7 +803,7 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
       wl[t] = DF ? __ldg(a.pl + o[t] + c0) : 0.f;
     }
   }
-  // per-plane operands, loaded one plane ahead of their use: y neighbour's pressure,
+  // per-plane operands, loaded two planes ahead of their use: y neighbour's pressure,
   // face coefficients and velocity of the cell, and (CFL) the upper y face's operands
   struct PlaneVals {
     float ymh, yml, L0, L1, L2, u0, u1, u2, yph, ypl, uyp, Lyp;
@@ -825,16 +825,18 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
       v.Lyp = __ldg(a.L[1] + ok + cyp);
     }
   };
-  PlaneVals cur;
+  PlaneVals cur, nxt;
   load_plane(kb, cur);
+  load_plane(kb + 1, nxt);
   float m = 0.f;
   for (int k = kb; k < ke; ++k) {
     const long long ok = zoff(k);
     const long long q = ok + c0;
-    // plane k+1 (for k + 1 = ke an in-range plane whose values go unused, except the
-    // z-velocity and coefficient of the upper z face)
-    PlaneVals nxt;
-    load_plane(k + 1, nxt);
+    // plane k+2 in flight (past the column's end an in-range plane whose values go
+    // unused; the upper z face of plane k reads the next plane's own velocity and
+    // coefficient)
+    PlaneVals nx2;
+    load_plane(k + 2, nx2);
     float xmh = __shfl_up_sync(0xffffffffu, wh[1], 1), xml = __shfl_up_sync(0xffffffffu, wl[1], 1);
     if (edge_xm) {
       xmh = __ldg(P + ok + cxm);
@@ -878,6 +880,7 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
       wl[2] = DF ? __ldg(a.pl + o2 + c0) : 0.f;
     }
     cur = nxt;
+    nxt = nx2;
   }
   if (CFL) {
     const unsigned mb = block_max_bits<256>(__float_as_uint(fabsf(m)), s_m);
