@@ -206,8 +206,72 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   }
 }
 
+// RES_RESTRICT alone (coarse levels): one thread per coarse cell loads its 2^D children
+// at once (x pairs as float2 when the field is FP32) and sums them in the fused pass's
+// order (z pairs, then x pairs, then y pairs: the same bits), storing the 16-bit copy
+// of z on the way when the level keeps one.  Every restricting level has even sides.
+template <int D>
+__global__ void __launch_bounds__(256) k_restrict(ResArgs a) {
+  const float S = a.apply_cs ? ldexpf(1.f, a.st->cs_used) : 1.f;
+  const float zcm = a.zcmul * S, zvm = a.zconvmul * S;
+  const Grid& g = a.g;
+  const int c0 = a.cn[0], c1 = a.cn[1];
+  const long long ncc = (long long)c0 * c1 * (D == 3 ? a.cn[2] : 1);
+  const long long n0 = g.n[0], nn = (long long)g.n[0] * g.n[1];
+  const bool plain = a.ztype == ST_F32 && !a.zconv;
+  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < ncc; t += (long long)gridDim.x * 256) {
+    const int I = (int)(t % c0);
+    const long long r = t / c0;
+    const int J = (int)(r % c1), K = (int)(r / c1);
+    const long long b = 2LL * I + n0 * (2LL * J) + (D == 3 ? nn * (2LL * K) : 0);
+    // children (dx, dy, dz) at b + dx + n0 dy + nn dz
+    float v[2][2][2];
+    if (plain) {
+      const float* z = a.z;
+#pragma unroll
+      for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy) {
+          const float2 p = __ldg(reinterpret_cast<const float2*>(z + b + n0 * dy + nn * dz));
+          v[dz][dy][0] = p.x;
+          v[dz][dy][1] = p.y;
+        }
+    } else {
+#pragma unroll
+      for (int dz = 0; dz < (D == 3 ? 2 : 1); ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) {
+            const long long q = b + dx + n0 * dy + nn * dz;
+            const float zq = ld_st(a.z, a.ztype, q);
+            if (a.zconv) st_st(a.zconv, a.zconvtype, q, zq * zvm);
+            v[dz][dy][dx] = zq;
+          }
+    }
+    float sum;
+    if (D == 3) {
+      const float a00 = v[0][0][0] + v[1][0][0], a10 = v[0][0][1] + v[1][0][1];
+      const float a01 = v[0][1][0] + v[1][1][0], a11 = v[0][1][1] + v[1][1][1];
+      sum = (a00 + a10) + (a01 + a11);
+    } else {
+      sum = (v[0][0][0] + v[0][0][1]) + (v[0][1][0] + v[0][1][1]);
+    }
+    st_st(a.zc, a.zctype, t, sum * zcm);
+  }
+}
+
 int launch_residual(int D, const ResArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
+  if (a.mode == RES_RESTRICT && a.zc) {
+    const long long ncc = (long long)a.cn[0] * a.cn[1] * (D == 3 ? a.cn[2] : 1);
+    const int blocks = (int)std::min<long long>((ncc + 255) / 256, 152LL * 8 * 4);
+    if (D == 3)
+      k_restrict<3><<<blocks, 256, 0, s>>>(a);
+    else
+      k_restrict<2><<<blocks, 256, 0, s>>>(a);
+    return 0;
+  }
   if (D == 3) {
     dim3 grd((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + 2 * RS_ZP - 1) / (2 * RS_ZP));
     k_residual<3><<<grd, 256, 0, s>>>(a);
