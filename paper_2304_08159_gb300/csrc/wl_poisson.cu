@@ -1504,7 +1504,8 @@ int launch_apply_pinv(const DenseArgs& a, cudaStream_t s) {
 size_t vcycle_tail_smem(int D, const int (*n)[3], int nl) {
   size_t b = 0;
   for (int l = 0; l < nl; ++l) b += sizeof(float) * (size_t)(D + 2) * n[l][0] * n[l][1] * n[l][2];
-  return b;
+  b = (b + 7) & ~size_t(7);  // the coarsest right-hand side in FP64 follows
+  return b + sizeof(double) * (size_t)n[nl - 1][0] * n[nl - 1][1] * n[nl - 1][2];
 }
 
 template <int D>
@@ -1562,11 +1563,16 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs a) {
     const int nc = ncells(lc);
     float* zc = level_base(lc) + D * nc;
     float* xc = zc + nc;
+    // z in FP64 once (the FP64 pipe is the bound here), after the levels' data
+    const int nf = (int)(level_base(a.nl) - tsm);
+    double* zd = reinterpret_cast<double*>(tsm + ((nf + 1) & ~1));
+    for (int i = tid; i < nc; i += kTailThreads) zd[i] = (double)zc[i];
+    __syncthreads();
     for (int i = tid; i < nc; i += kTailThreads) {
       double acc = 0.0;
       // unrolled so that many rows of G are in flight; the sum keeps its order
 #pragma unroll 16
-      for (int jj = 0; jj < nc; ++jj) acc += __ldg(a.G + (long long)jj * nc + i) * (double)zc[jj];
+      for (int jj = 0; jj < nc; ++jj) acc += __ldg(a.G + (long long)jj * nc + i) * zd[jj];
       xc[i] = (float)acc;
     }
     __syncthreads();
