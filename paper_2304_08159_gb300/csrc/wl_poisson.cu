@@ -1320,28 +1320,31 @@ int launch_forces(int D, const Grid& g, const Body& b, const float* p, const flo
 namespace wl {
 
 // Boundary faces of non-periodic directions always carry U_c (used after a caller
-// overwrites the velocity).
+// overwrites the velocity): only the lower boundary plane of each component c is
+// touched (blockIdx.y = c), one thread per face of that plane.
 template <int D>
 __global__ void k_fix_bfaces(Grid g, float* u0, float* u1, float* u2) {
-  float* u[3] = {u0, u1, u2};
-  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
-  if (q >= g.nc) return;
-  int I[3];
-  I[0] = (int)(q % g.n[0]);
-  long long t = q / g.n[0];
-  I[1] = (int)(t % g.n[1]);
-  I[2] = (int)(t / g.n[1]);
-#pragma unroll
-  for (int c = 0; c < D; ++c)
-    if (!is_per(g, c) && I[c] == 0) u[c][q] = g.U[c];
+  const int c = blockIdx.y;
+  if (c >= D || is_per(g, c)) return;
+  float* u = c == 0 ? u0 : (c == 1 ? u1 : u2);
+  const int da = c == 0 ? 1 : 0, db = c == 2 ? 1 : 2;  // the plane's two directions
+  const long long na = g.n[da], np = na * g.n[db];  // n[2] = 1 in 2-D
+  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < np; t += (long long)gridDim.x * 256) {
+    int I[3] = {0, 0, 0};
+    I[da] = (int)(t % na);
+    I[db] = (int)(t / na);
+    u[cell_index(g, I[0], I[1], I[2])] = g.U[c];
+  }
 }
 
 int launch_fix_bfaces(int D, const Grid& g, float* const* u, cudaStream_t s) {
-  const int nb = (int)((g.nc + 255) / 256);
+  long long np = 0;  // largest boundary plane
+  for (int c = 0; c < D; ++c) np = std::max(np, g.nc / g.n[c]);
+  const dim3 grd((unsigned)std::min<long long>((np + 255) / 256, 152LL * 16), (unsigned)D);
   if (D == 3)
-    k_fix_bfaces<3><<<nb, 256, 0, s>>>(g, u[0], u[1], u[2]);
+    k_fix_bfaces<3><<<grd, 256, 0, s>>>(g, u[0], u[1], u[2]);
   else
-    k_fix_bfaces<2><<<nb, 256, 0, s>>>(g, u[0], u[1], u[1]);
+    k_fix_bfaces<2><<<grd, 256, 0, s>>>(g, u[0], u[1], u[1]);
   return 0;
 }
 
