@@ -83,6 +83,7 @@ def _load():
             "or_step": (None, [_P, _I, _D, _I, _D, _I]),
             "or_cfl": (_D, [_P]),
             "or_forces": (None, [_P, _DP]),
+            "or_viscous_force": (None, [_P, _DP]),
             "or_kinetic_energy": (_D, [_P]),
             "or_K0": (_D, [_D]),
             "or_K1": (_D, [_D]),
@@ -322,6 +323,12 @@ class Oracle:
     def forces(self):
         F = np.zeros(3)
         self.lib.or_forces(self.h, _dp(F))
+        return F[: self.D]
+
+    def viscous_force(self):
+        """Viscous force on the body: sum over band cells of 2 nu S n K_eps(d)."""
+        F = np.zeros(3)
+        self.lib.or_viscous_force(self.h, _dp(F))
         return F[: self.D]
 
     def kinetic_energy(self) -> float:

@@ -1466,6 +1466,48 @@ void or_forces(void* h, double* F) {
       }
 }
 
+// Viscous force on the body (reading: the paper states no force; this is the viscous
+// part of the surface integral, kernel-weighted like the pressure force):
+// F_i = sum_cells 2 nu S_ij n_j K_eps(d) over cells with |d| < eps, with the strain rate
+// S = (grad u + grad u^T)/2 at the cell centre: du_c/dx_c from the cell's two c-faces,
+// du_c/dx_e (e != c) by the central difference of the cell-centred u_c (the mean of its
+// two faces) over the neighbours at -e and +e.  Ghosts carry the BC.
+void or_viscous_force(void* h, double* F) {
+  OSim* s = (OSim*)h;
+  for (int d = 0; d < 3; ++d) F[d] = 0.0;
+  if (s->body_kind == 0) return;
+  auto uc = [&](int c, const int* I) {  // u_c at the centre of cell I
+    int J[3] = {I[0], I[1], I[2]};
+    J[c] += 1;
+    return 0.5 * (s->u[c][pidx(*s, I)] + s->u[c][pidx(*s, J)]);
+  };
+  for (int k = 0; k < s->n[2]; ++k)
+    for (int j = 0; j < s->n[1]; ++j)
+      for (int i = 0; i < s->n[0]; ++i) {
+        double x[3] = {i + 0.5, j + 0.5, k + 0.5}, nrm[3];
+        double d = sdf(*s, x, nrm);
+        if (std::fabs(d) >= s->eps) continue;
+        double K = (1.0 + std::cos(M_PI * d / s->eps)) / (2.0 * s->eps);
+        const int I[3] = {i, j, k};
+        double G[3][3] = {{0.0}};  // G[c][e] = du_c/dx_e
+        for (int c = 0; c < s->D; ++c)
+          for (int e = 0; e < s->D; ++e) {
+            if (c == e) {
+              int J[3] = {i, j, k};
+              J[c] += 1;
+              G[c][e] = s->u[c][pidx(*s, J)] - s->u[c][pidx(*s, I)];
+            } else {
+              int Jp[3] = {i, j, k}, Jm[3] = {i, j, k};
+              Jp[e] += 1;
+              Jm[e] -= 1;
+              G[c][e] = 0.5 * (uc(c, Jp) - uc(c, Jm));
+            }
+          }
+        for (int a = 0; a < s->D; ++a)
+          for (int b = 0; b < s->D; ++b) F[a] += 2.0 * s->nu * 0.5 * (G[a][b] + G[b][a]) * nrm[b] * K;
+      }
+}
+
 // Kinetic energy E = 1/2 sum_faces sum_c u_c^2 / ncell (stored lower faces).
 double or_kinetic_energy(void* h) {
   OSim* s = (OSim*)h;

@@ -505,6 +505,61 @@ def test_force_ignores_constant_pressure():
     assert np.abs(o.forces()).max() < 1e-12
 
 
+def _shear_y2(o, D):
+    """u_x = y^2 sampled at the x-faces (y = j + 1/2), other components 0."""
+    y = np.arange(o.shape[-2]) + 0.5
+    u = np.zeros((D,) + o.shape)
+    u[0] = (y**2)[:, None] if D == 2 else (y**2)[None, :, None]
+    return u
+
+
+@pytest.mark.parametrize("D,body,volume,bar", [
+    (2, dict(kind=1, radius=9.0), math.pi * 81.0, 0.01),
+    (3, dict(kind=1, radius=7.0), 4.0 / 3.0 * math.pi * 343.0, 0.02),
+    (3, dict(kind=2, radius=8.0, radius2=3.0), 2.0 * math.pi**2 * 8.0 * 9.0, 0.03),
+], ids=["circle", "sphere", "torus"])
+def test_viscous_force_closed_form(D, body, volume, bar):
+    """For u = (y^2, 0, 0) the strain rate has S_xy = S_yx = y, so by the divergence
+    theorem the viscous surface force is 2 nu (div S) V = (2 nu V, 0, 0) with V the body's
+    volume; the kernel-weighted cell sum matches it up to O(eps^2/r^2) (mean over seeded
+    sub-cell offsets of the body)."""
+    nu = 0.04
+    n = 48 if D == 2 else 32
+    rng = np.random.default_rng(5)
+    Fs = []
+    for _ in range(6 if D == 2 else 3):
+        b = dict(body)
+        b["center"] = tuple(n / 2 + rng.random() for _ in range(D))
+        o = O.Oracle((n,) * D, nu, U=(0.0,) * D, body=b)
+        o.set_ic(0)
+        o.set_u(_shear_y2(o, D))
+        Fs.append(o.viscous_force())
+    F = np.mean(Fs, axis=0)
+    ref = 2 * nu * volume
+    assert abs(F[0] / ref - 1) < bar, (F, ref)
+    assert np.abs(F[1:]).max() < 0.01 * ref, F
+
+
+@pytest.mark.parametrize("D", [2, 3])
+def test_viscous_force_vanishes_for_rigid_motion(D):
+    """A uniform translation and a rigid rotation have zero strain rate; the centred
+    differences are exact for linear fields, so the force is zero to rounding."""
+    n = 24
+    b = dict(kind=1, center=(12.3,) * D if D == 2 else (12.3, 11.8, 12.1), radius=5.0)
+    o = O.Oracle((n,) * D, 0.05, U=(0.0,) * D, body=b)
+    o.set_ic(0)
+    # u_x on x-faces (x = i, y = j + 1/2), u_y on y-faces (x = i + 1/2, y = j): rotation about z
+    idx = np.indices(o.shape).astype(float)  # (k,) j, i
+    i, j = idx[-1], idx[-2]
+    u = np.zeros((D,) + o.shape)
+    u[0] = 0.3 - 0.7 * (j + 0.5 - 12.0)
+    u[1] = -0.2 + 0.7 * (i + 0.5 - 12.0)
+    if D == 3:
+        u[2] = 0.1
+    o.set_u(u)
+    assert np.abs(o.viscous_force()).max() < 1e-10
+
+
 def test_bdim_blend_linear_field():
     """With dt = 0 the stage reduces to the blend u' = mu0 u0 + mu1 . grad u0; for a
     linear field the central difference is the exact gradient, so the blend is
