@@ -184,6 +184,16 @@ int wl_gmg_vcycle(wl_handle h, double* resid_inf_out);
  * F receives D values.  Synchronises. */
 int wl_forces(wl_handle h, double* F);
 
+/* Viscous force on the body of the current velocity, F_i = sum_cells 2 nu S_ij n_j
+ * K_eps(d) over |d| < eps (the viscous part of the surface integral, kernel-weighted like
+ * wl_forces; the paper states no force, so this form is this library's reading), with
+ * the strain rate S = (grad u + grad u^T)/2 at cell centres: du_c/dx_c from the cell's
+ * two c-faces, du_c/dx_e (e != c) by the central difference of the cell-centred u_c;
+ * neighbours outside the grid follow the boundary conditions.  Accumulated in FP64 in a
+ * fixed order.  F receives D values (zeros without a body).  Synchronises.
+ * WL_EINVAL for a null handle or F. */
+int wl_viscous_force(wl_handle h, double* F);
+
 /* Copy a field (WL_FIELD_*) to dst (host or device).  Synchronises when dst is on
  * the host. */
 int wl_get_field(wl_handle h, int which, void* dst, int dst_is_device);

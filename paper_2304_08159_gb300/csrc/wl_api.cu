@@ -1095,6 +1095,17 @@ int wl_forces(wl_handle s, double* F) {
   return WL_OK;
 }
 
+int wl_viscous_force(wl_handle s, double* F) {
+  if (!s || !F) return WL_EINVAL;
+  const float* u[3] = {s->ua[0], s->ua[1], s->ua[2]};
+  launch_viscous_force(s->D, s->g, s->body, u, s->nu, s->fout, s->st);
+  double h[3];
+  WL_CUDA(s, cudaMemcpyAsync(h, s->fout, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  for (int d = 0; d < s->D; ++d) F[d] = h[d];
+  return WL_OK;
+}
+
 int wl_get_field(wl_handle s, int which, void* dst, int dst_is_device) {
   if (!s || !dst || !valid_field(which)) return WL_EINVAL;
   const cudaMemcpyKind kind = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;

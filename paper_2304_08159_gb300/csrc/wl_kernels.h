@@ -255,6 +255,8 @@ int launch_coarsen(int D, const Grid& fine, const float* const* Lf, const Grid& 
                    cudaStream_t s);
 int launch_set_ic(int D, const Grid& g, int kind, double amp, float* const* u, cudaStream_t s);
 int launch_cfl_only(int D, const Grid& g, const float* const* u, DevState* st, cudaStream_t s);
+int launch_viscous_force(int D, const Grid& g, const Body& b, const float* const* u, double nu, double* out,
+                         cudaStream_t s);
 int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* pl, const float* const* L,
                   double* partials, int npart, double* out, cudaStream_t s);
 int launch_build_pinv(int D, const DenseArgs& a, cudaStream_t s);

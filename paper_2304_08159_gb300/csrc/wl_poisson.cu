@@ -1289,15 +1289,68 @@ __global__ void __launch_bounds__(256) k_force_final(Grid g, Body b, const float
   if (threadIdx.x == 0) out[3] = pbar;
 }
 
-int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* pl, const float* const* L,
-                  double* partials, int npart, double* out, cudaStream_t s) {
-  if (D == 3)
-    k_force_partials<3><<<npart, 256, 0, s>>>(g, p, pl, L[0], L[1], L[2], partials);
-  else
-    k_force_partials<2><<<npart, 256, 0, s>>>(g, p, pl, L[0], L[1], L[1], partials);
+// viscous force: F_i = sum over cells with |d| < eps of 2 nu S_ij n_j K_eps(d), with the
+// strain rate S = (grad u + grad u^T)/2 at the cell centre: du_c/dx_c from the cell's two
+// c-faces, du_c/dx_e (e != c) by the central difference of the cell-centred u_c (the mean
+// of its two faces); neighbours outside the grid through the BC mapping.  One block, FP64
+// accumulation in a fixed order (deterministic).
+template <int D>
+__global__ void __launch_bounds__(256) k_viscous_force(Grid g, Body b, const float* u0, const float* u1,
+                                                        const float* u2, double nu, int lo0, int lo1, int lo2,
+                                                        int bx, int by, int bz, double* out) {
+  __shared__ double sh[9];
+  const float* u[3] = {u0, u1, u2};
+  auto U = [&](int c, const int* J) { return (double)load_u_bc<D>(u[c], c, g, J[0], J[1], J[2]); };
+  double F[3] = {0.0, 0.0, 0.0};
+  const long long nbox = (long long)bx * by * bz;
+  for (long long t = threadIdx.x; t < nbox; t += 256) {
+    const int i = lo0 + (int)(t % bx);
+    const long long r = t / bx;
+    const int j = lo1 + (int)(r % by);
+    const int k = lo2 + (int)(r / by);
+    double x[3] = {i + 0.5, j + 0.5, k + 0.5}, n[3];
+    const double d = body_sdf<D>(b, x, n);
+    if (!(fabs(d) < b.eps)) continue;
+    const double K = (1.0 + cospi(d / b.eps)) / (2.0 * b.eps);
+    const int I[3] = {i, j, k};
+    double G[3][3] = {{0.0}};  // G[c][e] = du_c/dx_e
+#pragma unroll
+    for (int c = 0; c < D; ++c)
+#pragma unroll
+      for (int e = 0; e < D; ++e) {
+        if (c == e) {
+          int J[3] = {i, j, k};
+          J[c] += 1;
+          G[c][e] = U(c, J) - U(c, I);
+        } else {
+          int P0[3] = {i, j, k}, M0[3] = {i, j, k};
+          P0[e] += 1;
+          M0[e] -= 1;
+          int P1[3] = {P0[0], P0[1], P0[2]}, M1[3] = {M0[0], M0[1], M0[2]};
+          P1[c] += 1;
+          M1[c] += 1;
+          G[c][e] = 0.5 * (0.5 * (U(c, P0) + U(c, P1)) - 0.5 * (U(c, M0) + U(c, M1)));
+        }
+      }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int e = 0; e < D; ++e) F[a] += 2.0 * nu * 0.5 * (G[a][e] + G[e][a]) * n[e] * K;
+  }
+  for (int dd = 0; dd < D; ++dd) {
+    const double v = block_sum_d(F[dd], sh);
+    if (threadIdx.x == 0) out[dd] = v;
+  }
+}
+
+// cells around the body that can hold band cells: the body's bounding box grown by eps + 1
+void force_box(int D, const Grid& g, const Body& b, int* lo, int* hi) {
   double ext = b.r1 + b.eps + 1.0;
   if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 1.0;
-  int lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = 0;
+    hi[d] = 1;
+  }
   if (b.kind != 0) {
     for (int d = 0; d < D; ++d) {
       lo[d] = (int)fmax(0.0, floor(b.c[d] - ext));
@@ -1307,6 +1360,28 @@ int launch_forces(int D, const Grid& g, const Body& b, const float* p, const flo
   } else {
     hi[0] = lo[0];
   }
+}
+
+int launch_viscous_force(int D, const Grid& g, const Body& b, const float* const* u, double nu, double* out,
+                         cudaStream_t s) {
+  int lo[3], hi[3];
+  force_box(D, g, b, lo, hi);
+  const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
+  if (D == 3)
+    k_viscous_force<3><<<1, 256, 0, s>>>(g, b, u[0], u[1], u[2], nu, lo[0], lo[1], lo[2], bx, by, bz, out);
+  else
+    k_viscous_force<2><<<1, 256, 0, s>>>(g, b, u[0], u[1], u[1], nu, lo[0], lo[1], lo[2], bx, by, bz, out);
+  return 0;
+}
+
+int launch_forces(int D, const Grid& g, const Body& b, const float* p, const float* pl, const float* const* L,
+                  double* partials, int npart, double* out, cudaStream_t s) {
+  if (D == 3)
+    k_force_partials<3><<<npart, 256, 0, s>>>(g, p, pl, L[0], L[1], L[2], partials);
+  else
+    k_force_partials<2><<<npart, 256, 0, s>>>(g, p, pl, L[0], L[1], L[1], partials);
+  int lo[3], hi[3];
+  force_box(D, g, b, lo, hi);
   const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
   if (D == 3)
     k_force_final<3><<<1, 256, 0, s>>>(g, b, p, pl, partials, npart, lo[0], lo[1], lo[2], bx, by, bz, out);

@@ -46,7 +46,7 @@ COARSE_PRECISION = {"fp32": WL_COARSE_FP32, "bf16": WL_COARSE_BF16, "fp16": WL_C
 # every symbol include/wl.h declares
 EXPORTS = (
     "wl_default_opts", "wl_workspace_bytes", "wl_create", "wl_set_ic", "wl_step", "wl_stage",
-    "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_get_field", "wl_set_field", "wl_get_dt",
+    "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_viscous_force", "wl_get_field", "wl_set_field", "wl_get_dt",
     "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_levels", "wl_level_dims",
     "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
     "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split",
@@ -98,6 +98,7 @@ def load(path: str = LIB_PATH):
         "wl_project": (I, [H, D, IP, DP]),
         "wl_gmg_vcycle": (I, [H, DP]),
         "wl_forces": (I, [H, DP]),
+        "wl_viscous_force": (I, [H, DP]),
         "wl_get_field": (I, [H, I, P, I]),
         "wl_set_field": (I, [H, I, P, I]),
         "wl_get_dt": (I, [H, DP]),
@@ -174,6 +175,12 @@ def wl_gmg_vcycle(h):
 def wl_forces(h, D):
     F = (ctypes.c_double * 3)()
     rc = load().wl_forces(h, F)
+    return rc, [F[i] for i in range(D)]
+
+
+def wl_viscous_force(h, D):
+    F = (ctypes.c_double * 3)()
+    rc = load().wl_viscous_force(h, F)
     return rc, [F[i] for i in range(D)]
 
 
@@ -389,6 +396,12 @@ class Sim:
     def forces(self):
         rc, F = wl_forces(self.h, self.D)
         self._check(rc, "wl_forces")
+        return np.array(F)
+
+    def viscous_force(self):
+        """wl_viscous_force: the viscous force on the body of the current velocity."""
+        rc, F = wl_viscous_force(self.h, self.D)
+        self._check(rc, "wl_viscous_force")
         return np.array(F)
 
     @property
