@@ -83,6 +83,7 @@ def _load():
             "or_step": (None, [_P, _I, _D, _I, _D, _I]),
             "or_cfl": (_D, [_P]),
             "or_forces": (None, [_P, _DP]),
+            "or_set_body_nodes": (None, [_P, _DP]),
             "or_viscous_force": (None, [_P, _DP]),
             "or_kinetic_energy": (_D, [_P]),
             "or_K0": (_D, [_D]),
@@ -147,17 +148,27 @@ class Oracle:
         U = list(U) if U is not None else [0.0] * self.D
         U = (U + [0.0] * 3)[:3]
         kind, center, r1, r2 = 0, [0.0, 0.0, 0.0], 0.0, 0.0
+        nodes = None
         if body is not None:
             kind = int(body.get("kind", 1))
-            center = (list(body["center"]) + [0.0] * 3)[:3]
-            r1 = float(body.get("radius", 0.0))
-            r2 = float(body.get("radius2", 0.0))
+            if kind == 3:  # signed distance sampled at the nodes, shape reversed(dims + 1)
+                nodes = np.ascontiguousarray(body["nodes"], dtype=np.float64).reshape(-1)
+                kind = 0
+            else:
+                center = (list(body["center"]) + [0.0] * 3)[:3]
+                r1 = float(body.get("radius", 0.0))
+                r2 = float(body.get("radius2", 0.0))
         d3 = (ctypes.c_int * 3)(*(list(self.dims) + [1] * (3 - self.D)))
         self.h = self.lib.or_create(self.D, d3, float(nu), (ctypes.c_double * 3)(*U),
                                     int(periodic), kind, (ctypes.c_double * 3)(*center),
                                     r1, r2, float(eps), int(bool(advect)), float(dt_cap))
         if not self.h:
             raise ValueError("oracle: bad arguments")
+        if nodes is not None:
+            want = int(np.prod([d + 1 for d in self.dims]))
+            if nodes.size != want:
+                raise ValueError(f"oracle: {want} node values expected, got {nodes.size}")
+            self.lib.or_set_body_nodes(self.h, _dp(nodes))
         self.ncell = int(np.prod(self.dims))
         self.shape = tuple(reversed(self.dims))
 

@@ -54,7 +54,9 @@ struct OSim {
   unsigned periodic;  // bit d set: direction d is periodic
   double nu;
   double U[3];
-  int body_kind;      // 0 none, 1 circle/sphere, 2 torus
+  int body_kind;      // 0 none, 1 circle/sphere, 2 torus, 3 sampled distance (nodes)
+  vec nodes;          // body_kind 3: signed distance at the grid's nodes (positions (i, j, k),
+                      // (n0+1)(n1+1)(n2+1) values in 3-D, (n0+1)(n1+1) in 2-D, x fastest)
   double center[3], radius, radius2, eps;
   int advect;         // 1: full convection-diffusion; 0: diffusion only (Stokes checks)
   int exit_bc = 0;    // 1: convective exit on the upper x face (see exit_stage)
@@ -119,6 +121,37 @@ double sdf(const OSim& s, const double* x, double* nrm) {
       nrm[2] = q1 / dq * e2;
     }
     return dq - s.radius2;
+  }
+  if (s.body_kind == 3) {  // sampled: multilinear between the nodes of the cell holding x
+    const int D = s.D;
+    int c0[3] = {0, 0, 0};
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < D; ++d) {
+      c0[d] = std::max(0, std::min(s.n[d] - 1, (int)std::floor(x[d])));
+      f[d] = x[d] - c0[d];
+    }
+    const long s0 = 1, s1 = s.n[0] + 1, s2 = (long)(s.n[0] + 1) * (s.n[1] + 1);
+    const long base = c0[0] * s0 + c0[1] * s1 + (D == 3 ? c0[2] * s2 : 0);
+    // corner values v[a][b][c] at node offsets (a, b, c)
+    double v[2][2][2];
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < 2; ++c) v[a][b][c] = s.nodes[base + a * s0 + b * s1 + (D == 3 ? c * s2 : 0)];
+    const double w0[2] = {1.0 - f[0], f[0]}, w1[2] = {1.0 - f[1], f[1]};
+    const double w2[2] = {D == 3 ? 1.0 - f[2] : 1.0, D == 3 ? f[2] : 0.0};
+    double d = 0.0, g[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < 2; ++a)
+      for (int b = 0; b < 2; ++b)
+        for (int c = 0; c < (D == 3 ? 2 : 1); ++c) {
+          d += w0[a] * w1[b] * w2[c] * v[a][b][c];
+          g[0] += (a ? 1.0 : -1.0) * w1[b] * w2[c] * v[a][b][c];
+          g[1] += (b ? 1.0 : -1.0) * w0[a] * w2[c] * v[a][b][c];
+          if (D == 3) g[2] += (c ? 1.0 : -1.0) * w0[a] * w1[b] * v[a][b][c];
+        }
+    const double gn = std::sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (gn > 0.0)
+      for (int dd = 0; dd < D; ++dd) nrm[dd] = g[dd] / gn;
+    return d;
   }
   return 1e30;  // no body: everything is fluid
 }
@@ -1192,6 +1225,16 @@ void* or_create(int D, const int* dims, double nu, const double* U, unsigned per
   measure(*s);
   s->dt = 0.0;
   return s;
+}
+
+// A body given by its signed distance sampled at the grid's nodes (body_kind 3): the
+// field replaces the closed-form distance, and the moments and levels are rebuilt.
+void or_set_body_nodes(void* h, const double* nodes) {
+  OSim* s = (OSim*)h;
+  const long nn = (long)(s->n[0] + 1) * (s->n[1] + 1) * (s->D == 3 ? s->n[2] + 1 : 1);
+  s->nodes.assign(nodes, nodes + nn);
+  s->body_kind = 3;
+  measure(*s);
 }
 
 void or_destroy(void* h) { delete (OSim*)h; }

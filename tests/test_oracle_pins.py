@@ -505,6 +505,60 @@ def test_force_ignores_constant_pressure():
     assert np.abs(o.forces()).max() < 1e-12
 
 
+# --------------------------------------------------------------------------- sampled SDF body
+def _node_grid(dims):
+    """Node coordinates (i, j[, k]) of a grid of cells `dims`, arrays shaped reversed(dims + 1)."""
+    idx = np.indices(tuple(d + 1 for d in reversed(dims))).astype(float)
+    return list(reversed(list(idx)))  # x, y[, z]
+
+
+def _K0(s):
+    s = np.clip(s, -1.0, 1.0)
+    return 0.5 + 0.5 * s + np.sin(np.pi * s) / (2 * np.pi)
+
+
+@pytest.mark.parametrize("dims,a,b", [
+    ((24, 16), (0.8, -0.6), 9.3),
+    ((20, 16, 12), (0.6, 0.48, 0.64), 9.1),
+], ids=["2d", "3d"])
+def test_sampled_sdf_planar_is_exact(dims, a, b):
+    """A body given by its signed distance at the nodes: multilinear interpolation
+    reproduces a linear distance exactly, so for a tilted half-space every face's mu0 is
+    K0(d(x_f)/eps) and mu1 is eps K1(d/eps) times the plane's normal, to rounding."""
+    a = np.array(a) / np.linalg.norm(a)
+    X = _node_grid(dims)
+    nodes = sum(a[d] * X[d] for d in range(len(dims))) - b
+    o = O.Oracle(dims, 0.05, U=(1.0,) + (0.0,) * (len(dims) - 1), body=dict(kind=3, nodes=nodes))
+    mu0, mu1 = o.mu0(), o.mu1()
+    centres = list(reversed(list(np.indices(o.shape).astype(float))))
+    for c in range(len(dims)):
+        x = [centres[d] + 0.5 for d in range(len(dims))]
+        x[c] = x[c] - 0.5
+        d = sum(a[e] * x[e] for e in range(len(dims))) - b
+        assert np.abs(mu0[c] - _K0(d)).max() < 1e-13
+        k1 = np.vectorize(O.K1)(d)
+        for e in range(len(dims)):
+            assert np.abs(mu1[c, e] - k1 * a[e]).max() < 1e-13
+
+
+def test_sampled_sdf_sphere_volume_and_buoyancy():
+    """A sphere's distance sampled at the nodes: the solid volume sum (1 - mu0) and the
+    buoyancy of p = x match (4/3) pi R^3 within the interpolation's O(h^2/R) error."""
+    R, c, dims = 6.0, (10.3, 8.1, 6.2), (20, 16, 12)
+    X = _node_grid(dims)
+    nodes = np.sqrt(sum((X[d] - c[d]) ** 2 for d in range(3))) - R
+    o = O.Oracle(dims, 0.05, U=(1.0, 0.0, 0.0), body=dict(kind=3, nodes=nodes))
+    V = 4.0 / 3.0 * math.pi * R**3
+    for comp in range(3):
+        assert abs((1 - o.mu0()[comp]).sum() / V - 1) < 0.02
+    nz, ny, nx = o.shape
+    Z, Y, Xc = np.meshgrid(np.arange(nz) + 0.5, np.arange(ny) + 0.5, np.arange(nx) + 0.5, indexing="ij")
+    o.set_p(Xc)
+    F = o.forces()
+    assert abs(F[0] / (-V) - 1) < 0.03, F
+    assert np.abs(F[1:]).max() < 0.03 * V
+
+
 def _shear_y2(o, D):
     """u_x = y^2 sampled at the x-faces (y = j + 1/2), other components 0."""
     y = np.arange(o.shape[-2]) + 0.5
