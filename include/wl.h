@@ -68,6 +68,7 @@ extern "C" {
 #define WL_BODY_NONE 0
 #define WL_BODY_SPHERE 1 /* circle in 2-D, sphere in 3-D: centre, radius */
 #define WL_BODY_TORUS 2  /* 3-D: ring of radius `radius` in the y-z plane about the x axis, tube radius `radius2` */
+#define WL_BODY_FIELD 3  /* any shape: its signed distance sampled at the grid's nodes (`sdf_nodes`) */
 
 typedef struct wl_sim* wl_handle;
 
@@ -79,6 +80,12 @@ typedef struct {
   double center[3];
   double radius;
   double radius2;
+  /* WL_BODY_FIELD: host array of the signed distance (in cells, negative inside) at the
+   * grid's nodes, positions (i, j, k) for 0 <= i <= n0 etc.: (n0+1)(n1+1)(n2+1) values in
+   * 3-D, (n0+1)(n1+1) in 2-D, x fastest; copied by wl_create.  Between nodes the distance
+   * is multilinear and the normal is the normalised gradient of that interpolant (exact
+   * for planes; O(h^2) for smooth shapes).  Unused (may be NULL) for the other kinds. */
+  const float* sdf_nodes;
 } wl_body;
 
 typedef struct {

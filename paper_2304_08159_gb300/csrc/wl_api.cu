@@ -80,6 +80,7 @@ struct wl_sim {
   CUtensorMap mph{}, mpl{};   // TMA descriptors of the fine pressure (ph: hi part or FP32 pressure)
   CUtensorMap mu[3][3]{};     // TMA descriptors of the velocity buffers A, B, C (components)
   bool resid_tma = false;     // the fine residual uses the TMA-staged kernel
+  float* body_nodes = nullptr;  // WL_BODY_FIELD: device copy of the sampled distance
   int tail_lf = 0;            // > 0: levels tail_lf .. nlev-1 run as one block (k_vcycle_tail)
   float* rf = nullptr;        // precision 1: FP32 residual, right-hand side of each correction cycle
   double* G = nullptr;        // dense pseudo-inverse of the coarsest operator (small coarsest levels)
@@ -779,7 +780,9 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       o.exit_bc > 1)
     return WL_EINVAL;
   if (o.exit_bc && ((o.periodic_mask & 1u) || !(U[0] > 0.0))) return WL_EINVAL;  // exit: x walls, outflow
-  if (body && (body->kind < 0 || body->kind > 2 || (body->kind == 2 && ndim != 3))) return WL_EINVAL;
+  if (body && (body->kind < 0 || body->kind > 3 || (body->kind == 2 && ndim != 3) ||
+               (body->kind == 3 && !body->sdf_nodes)))
+    return WL_EINVAL;
   wl_sim* s = new wl_sim();
   s->D = ndim;
   s->o = o;
@@ -801,6 +804,57 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   s->body.r1 = body ? body->radius : 0.0;
   s->body.r2 = body ? body->radius2 : 0.0;
   s->body.eps = o.eps;
+  s->body.nodes = nullptr;
+  if (s->body.kind == 3) {
+    // the sampled distance: a device copy, and the cells whose corner values bracket
+    // |d| < eps (a multilinear value lies between its corners' values)
+    long long nn = 1;
+    for (int d = 0; d < 3; ++d) {
+      s->body.nn[d] = d < ndim ? dims[d] + 1 : 1;
+      nn *= s->body.nn[d];
+    }
+    const float* v = body->sdf_nodes;
+    for (long long q = 0; q < nn; ++q)
+      if (!std::isfinite(v[q])) {
+        delete s;
+        return WL_EINVAL;
+      }
+    for (int d = 0; d < 3; ++d) {
+      s->body.blo[d] = d < ndim ? dims[d] : 0;
+      s->body.bhi[d] = d < ndim ? 0 : 1;
+    }
+    const int n0 = s->g.n[0], n1 = s->g.n[1], n2 = ndim == 3 ? s->g.n[2] : 1;
+    const long long s1 = s->body.nn[0], s2 = s1 * s->body.nn[1];
+    for (int k = 0; k < n2; ++k)
+      for (int j = 0; j < n1; ++j)
+        for (int i = 0; i < n0; ++i) {
+          float lo = 1e30f, hi = -1e30f;
+          for (int c = 0; c < (ndim == 3 ? 8 : 4); ++c) {
+            const float w = v[(i + (c & 1)) + s1 * (j + ((c >> 1) & 1)) + s2 * (k + ((c >> 2) & 1))];
+            lo = std::min(lo, w);
+            hi = std::max(hi, w);
+          }
+          if (lo < o.eps && hi > -o.eps) {
+            const int I[3] = {i, j, k};
+            for (int d = 0; d < ndim; ++d) {
+              s->body.blo[d] = std::min(s->body.blo[d], I[d]);
+              s->body.bhi[d] = std::max(s->body.bhi[d], I[d] + 1);
+            }
+          }
+        }
+    if (cudaMalloc(&s->body_nodes, sizeof(float) * nn) != cudaSuccess) {
+      cudaGetLastError();
+      delete s;
+      return WL_ENOMEM;
+    }
+    if (cudaMemcpy(s->body_nodes, v, sizeof(float) * nn, cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(s->body_nodes);
+      delete s;
+      return WL_ECUDA;
+    }
+    s->body.nodes = s->body_nodes;
+  }
   const size_t need = layout(nullptr, ndim, dims, o.precision, o.coarse_precision, o.exit_bc ? 1 : 0, nullptr);
   if (o.workspace) {
     if (o.workspace_bytes < need || ((uintptr_t)o.workspace & 255u)) {
@@ -971,6 +1025,7 @@ void wl_destroy(wl_handle s) {
   if (s->hs) cudaFreeHost(s->hs);
   if (s->own_ws && s->ws) cudaFree(s->ws);
   if (s->gr.own && s->gr.mem) cudaFree(s->gr.mem);
+  if (s->body_nodes) cudaFree(s->body_nodes);
   delete s;
 }
 

@@ -142,10 +142,13 @@ __device__ __forceinline__ float mom_flux(float m2, float m1, float p0, float p1
 // Immersed body: analytic signed distance and outward unit normal (Section 2: the
 // geometry is a signed-distance function; normals are its gradient).
 struct Body {
-  int kind;          // 0 none, 1 circle/sphere, 2 torus (3-D)
+  int kind;          // 0 none, 1 circle/sphere, 2 torus (3-D), 3 sampled distance
   double c[3];
   double r1, r2;     // radius; torus tube radius
   double eps;        // BDIM kernel half-width
+  const float* nodes;  // kind 3: signed distance at the grid's nodes (device), x fastest
+  int nn[3];           //   node counts (n_d + 1; 1 for the unused z of 2-D)
+  int blo[3], bhi[3];  //   cells whose corners bracket |d| < eps ([lo, hi), computed on the host)
 };
 
 template <int D>
@@ -174,6 +177,40 @@ __device__ __forceinline__ double body_sdf(const Body& b, const double* x, doubl
       n[2] = q1 / dq * e2;
     }
     return dq - b.r2;
+  }
+  if (b.kind == 3) {
+    // sampled: multilinear between the nodes of the cell holding x; the normal is the
+    // normalised gradient of that interpolant
+    int c0[3] = {0, 0, 0};
+    double f[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      c0[d] = max(0, min(b.nn[d] - 2, (int)floor(x[d])));
+      f[d] = x[d] - c0[d];
+    }
+    const long long s1 = b.nn[0], s2 = (long long)b.nn[0] * b.nn[1];
+    const long long base = c0[0] + s1 * c0[1] + (D == 3 ? s2 * c0[2] : 0);
+    const double w0[2] = {1.0 - f[0], f[0]}, w1[2] = {1.0 - f[1], f[1]};
+    const double w2[2] = {D == 3 ? 1.0 - f[2] : 1.0, D == 3 ? f[2] : 0.0};
+    double dist = 0.0, g[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+        for (int c = 0; c < (D == 3 ? 2 : 1); ++c) {
+          const double v = (double)b.nodes[base + a + s1 * bb + (D == 3 ? s2 * c : 0)];
+          dist += w0[a] * w1[bb] * w2[c] * v;
+          g[0] += (a ? 1.0 : -1.0) * w1[bb] * w2[c] * v;
+          g[1] += (bb ? 1.0 : -1.0) * w0[a] * w2[c] * v;
+          if (D == 3) g[2] += (c ? 1.0 : -1.0) * w0[a] * w1[bb] * v;
+        }
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    if (gn > 0.0) {
+#pragma unroll
+      for (int d = 0; d < D; ++d) n[d] = g[d] / gn;
+    }
+    return dist;
   }
   return 1e30;
 }

@@ -9,6 +9,7 @@
 // body velocity is zero.  k_stage computes everything but the mu1 term, which is
 // non-zero only in the thin band |d| < eps around the body and is added by
 // k_bdim_band over the body's bounding box.
+#include <algorithm>
 #include <type_traits>
 
 #include "wl_dev.cuh"
@@ -353,6 +354,19 @@ int launch_fill(float* p, long long n, float v, cudaStream_t s) {
 
 bool stage_band_box(int D, const Grid& g, const Body& b, int* lo, int* hi) {
   if (b.kind == 0) return false;
+  if (b.kind == 3) {  // the cells bracketing the band, two cells wider
+    for (int d = 0; d < 3; ++d) {
+      if (d >= D) {
+        lo[d] = 0;
+        hi[d] = 1;
+        continue;
+      }
+      if (b.bhi[d] <= b.blo[d]) return false;  // no band cell
+      lo[d] = std::max(0, b.blo[d] - 2);
+      hi[d] = std::min(g.n[d], b.bhi[d] + 2);
+    }
+    return true;
+  }
   double ext = b.r1 + b.eps + 2.0;
   if (b.kind == 2) ext = b.r1 + b.r2 + b.eps + 2.0;
   for (int d = 0; d < 3; ++d) {

@@ -1351,7 +1351,13 @@ void force_box(int D, const Grid& g, const Body& b, int* lo, int* hi) {
     lo[d] = 0;
     hi[d] = 1;
   }
-  if (b.kind != 0) {
+  if (b.kind == 3) {  // the cells bracketing the band, one cell wider
+    for (int d = 0; d < D; ++d) {
+      lo[d] = std::max(0, b.blo[d] - 1);
+      hi[d] = std::min(g.n[d], std::max(b.bhi[d] + 1, lo[d]));
+      if (b.bhi[d] <= b.blo[d]) hi[d] = lo[d];
+    }
+  } else if (b.kind != 0) {
     for (int d = 0; d < D; ++d) {
       lo[d] = (int)fmax(0.0, floor(b.c[d] - ext));
       hi[d] = (int)fmin((double)g.n[d], ceil(b.c[d] + ext) + 1.0);

@@ -36,6 +36,7 @@ WL_FIELD_EXIT = 7
 WL_BODY_NONE = 0
 WL_BODY_SPHERE = 1
 WL_BODY_TORUS = 2
+WL_BODY_FIELD = 3
 
 WL_COARSE_FP32 = 0
 WL_COARSE_BF16 = 1
@@ -57,7 +58,8 @@ KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coar
 
 class WlBody(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("center", ctypes.c_double * 3),
-                ("radius", ctypes.c_double), ("radius2", ctypes.c_double)]
+                ("radius", ctypes.c_double), ("radius2", ctypes.c_double),
+                ("sdf_nodes", ctypes.POINTER(ctypes.c_float))]
 
 
 class WlOpts(ctypes.Structure):
@@ -261,13 +263,20 @@ def wl_wait_probe(seconds):
 
 
 def make_body(body) -> WlBody:
+    """A wl_body from a dict: kind (WL_BODY_*), center, radius, radius2, or for
+    WL_BODY_FIELD the node-sampled distance `nodes` (shape reversed(dims + 1)).  The
+    returned struct keeps the node array alive (attribute `_nodes`) until wl_create."""
     b = WlBody()
     b.kind = int(body.get("kind", WL_BODY_SPHERE))
-    c = list(body["center"]) + [0.0] * 3
+    c = list(body.get("center", (0.0, 0.0, 0.0))) + [0.0] * 3
     for i in range(3):
         b.center[i] = float(c[i])
     b.radius = float(body.get("radius", 0.0))
     b.radius2 = float(body.get("radius2", 0.0))
+    if b.kind == WL_BODY_FIELD:
+        nodes = np.ascontiguousarray(body["nodes"], dtype=np.float32).reshape(-1)
+        b._nodes = nodes
+        b.sdf_nodes = nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
     return b
 
 
@@ -309,13 +318,9 @@ class Sim:
             o.workspace_bytes = nbytes
             b = None
             if body is not None:
-                b = WlBody()
-                b.kind = int(body.get("kind", WL_BODY_SPHERE))
-                c = list(body["center"]) + [0.0] * 3
-                for i in range(3):
-                    b.center[i] = float(c[i])
-                b.radius = float(body.get("radius", 0.0))
-                b.radius2 = float(body.get("radius2", 0.0))
+                b = make_body(body)
+                if b.kind == WL_BODY_FIELD and b._nodes.size != int(np.prod([d + 1 for d in self.dims])):
+                    raise WLError(WL_EINVAL, "sdf nodes: (n0+1)(n1+1)[(n2+1)] values expected")
             rc, h = wl_create(self.dims, nu, U, b, o)
         if rc != WL_OK:
             raise WLError(rc, "wl_create failed")

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from tests.gpu_cases import CASES_2D, CASES_3D, make_pair, rel_l2, active_mask
+from tests.gpu_cases import CASES_2D, CASES_3D, make_pair, rel_l2, active_mask, rounded_box, sampled_nodes
 
 pytestmark = pytest.mark.gpu
 
@@ -338,8 +338,8 @@ def test_vcycle_tail_matches_per_level_kernels(case, monkeypatch):
     assert np.array_equal(a.get(1), b.get(1))
 
 
-@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[1], CASES_3D[2], CASES_3D[4], CASES_2D[0], CASES_2D[2],
-                                  CASES_2D[3]], ids=lambda c: c["id"])
+@pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[1], CASES_3D[2], CASES_3D[4], CASES_3D[5], CASES_2D[0],
+                                  CASES_2D[2], CASES_2D[3], CASES_2D[4]], ids=lambda c: c["id"])
 def test_uniform_tiles_match_loading_kernels(case, monkeypatch):
     """Tiles away from the body form their face coefficients (the level's free-stream
     value, 0 on walls) instead of loading them: identical bits to the kernels that load
@@ -363,6 +363,8 @@ def test_uniform_tiles_match_loading_kernels(case, monkeypatch):
     dict(id="yper128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.0, 0.0), periodic=2,
          body=dict(kind=1, center=(40.0, 30.0, 24.0), radius=6.0)),
     dict(id="tgv64", dims=(64, 64, 64), nu=0.01, U=(0.0, 0.0, 0.0), periodic=7, body=None),
+    dict(id="sdfbox160", dims=(160, 80, 64), nu=0.01, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=3, nodes=sampled_nodes((160, 80, 64), rounded_box((50.3, 40.2, 31.7), (8.0, 6.0, 5.0), 2.0)))),
     dict(id="xchannel128", dims=(128, 32, 32), nu=0.01, U=(1.0, 0.0, 0.0), periodic=1, body=None),
 ], ids=lambda c: c["id"])
 def test_uniform_tiles_large_sphere_bitwise(case, monkeypatch):
