@@ -292,7 +292,7 @@ def run_ours(args, w, dist, rank, ws, lrank):
             dist.barrier()
 
     sim.step(args.warmup)
-    sim.status()
+    _, _, vc_warm, _ = sim.status()  # the V-cycle total is cumulative since creation
     barrier()
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(lrank).uuid)
@@ -308,11 +308,15 @@ def run_ours(args, w, dist, rank, ws, lrank):
     barrier()
     ck = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
-    rc, last, vcycles, worst = sim.status()
+    rc, last, vc_end, worst = sim.status()
+    vcycles = vc_end - vc_warm  # the timed steps' V-cycles
     tmax, vtot = reduce_replicas(dist, t, vcycles, "cuda")
     value = job_value(ws, ncell, args.steps, tmax)
     nlev = len(sim.levels())
-    fixed, per_cycle = _launches_per_step(nlev, 4, w["body"] is not None)
+    try:  # the captured step graph's own kernel nodes (per step, per V-cycle)
+        fixed, per_cycle = sim.graph_kernels()
+    except Exception:
+        fixed, per_cycle = _launches_per_step(nlev, 4, w["body"] is not None)
     launches = args.steps * fixed + vcycles * per_cycle
 
     # ---- per-kernel device time (host-driven steps with events around each launch)
@@ -426,7 +430,7 @@ def mixed_bench(w, args):
         if w["ic"]:
             sim.set_ic(w["ic"], 1.0)
         sim.step(args.warmup)
-        sim.status()
+        _, _, vc0, _ = sim.status()  # cumulative since creation
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -434,7 +438,8 @@ def mixed_bench(w, args):
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
-        rc, last, vc, worst = sim.status()
+        rc, last, vc1, worst = sim.status()
+        vc = vc1 - vc0
         u, p = sim.get(0, device=True).double(), sim.get(1, device=True).double()
         sim.close()
         return t, vc, rc, worst, u, p - p.mean()

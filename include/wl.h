@@ -213,9 +213,10 @@ int wl_get_dt(wl_handle h, double* dt);
 int wl_set_dt(wl_handle h, double dt);
 int wl_get_time(wl_handle h, double* t, long long* steps);
 
-/* Device-recorded status of the steps since the last call: V-cycles used by the
- * two projections of the last step, total V-cycles, and the worst final residual
- * (x units).  Returns WL_ENONFINITE / WL_WNOTCONV if any step saw that.
+/* Device-recorded status: V-cycles used by the two projections of the last step, the
+ * total V-cycles since wl_create (cumulative: difference two calls to count an
+ * interval), and the worst final residual (x units) of the steps since the last call.
+ * Returns WL_ENONFINITE / WL_WNOTCONV if any step since the last call saw that.
  * Synchronises. */
 int wl_status(wl_handle h, int* last_vcycles /*[2]*/, long long* total_vcycles, double* worst_resid);
 
@@ -237,6 +238,13 @@ int wl_status(wl_handle h, int* last_vcycles /*[2]*/, long long* total_vcycles, 
  * launch count in launches[] (arrays of WL_KCLASS_COUNT).  For measurement;
  * synchronises. */
 int wl_profile_step(wl_handle h, int nsteps, double* ms, long long* launches);
+
+/* Kernel launches of the step graph: *per_step = kernel nodes outside the V-cycle loops
+ * (stages, divergences, corrections, controls), *per_vcycle = kernel nodes of one V-cycle
+ * (counted in the graph as captured, so side-stream launches are included).  A graph step
+ * with n V-cycles launches per_step + n per_vcycle kernels.  WL_EINVAL without a step graph
+ * (use_graph = 0, or before the first wl_step). */
+int wl_graph_kernels(wl_handle h, int* per_step, int* per_vcycle);
 
 /* Allocation-free pressure force, for callers that cannot allocate device memory
  * (for example while capturing a CUDA graph, where cudaMalloc is not allowed, or under

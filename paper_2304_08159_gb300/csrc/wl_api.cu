@@ -88,6 +88,7 @@ struct wl_sim {
   size_t ws_bytes = 0;
   bool own_ws = false;
   cudaGraph_t graph = nullptr;
+  cudaGraph_t vbody = nullptr;   // the first projection's V-cycle body (owned by graph)
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t join = nullptr;  // wl_step_batch: end of this sim's part of a batch round
   cudaGraphConditionalHandle hc[2]{};
@@ -657,6 +658,7 @@ int add_while(wl_sim* s, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps
   cp.conditional.size = 1;
   WL_CUDA(s, cudaGraphAddNode(node, g, deps.data(), nullptr, deps.size(), &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
+  if (proj == 0) s->vbody = body;
   WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   enq_vcycle(s, w, proj, s->cs, 1);
   cudaGraph_t out = nullptr;
@@ -1286,6 +1288,29 @@ int wl_status(wl_handle s, int* last_vcycles, long long* total_vcycles, double* 
   }
   if (h.status & 4) return fail(s, WL_ETIMEOUT, "a staged copy of the sweep did not arrive in time");
   if (h.status & 2) return WL_WNOTCONV;
+  return WL_OK;
+}
+
+// kernel nodes of a graph (not descending into conditional nodes' bodies)
+static int graph_kernels(cudaGraph_t g) {
+  size_t n = 0;
+  if (!g || cudaGraphGetNodes(g, nullptr, &n) != cudaSuccess) return -1;
+  std::vector<cudaGraphNode_t> v(n);
+  if (n && cudaGraphGetNodes(g, v.data(), &n) != cudaSuccess) return -1;
+  int k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(v[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
+
+int wl_graph_kernels(wl_handle s, int* per_step, int* per_vcycle) {
+  if (!s || !per_step || !per_vcycle) return WL_EINVAL;
+  if (!s->graph || !s->vbody) return fail(s, WL_EINVAL, "no step graph (use_graph = 0 or no step yet)");
+  *per_step = graph_kernels(s->graph);
+  *per_vcycle = graph_kernels(s->vbody);
+  if (*per_step < 0 || *per_vcycle < 0) return cuda_check(s, cudaGetLastError(), "graph nodes");
   return WL_OK;
 }
 

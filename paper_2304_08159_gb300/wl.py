@@ -48,7 +48,7 @@ COARSE_PRECISION = {"fp32": WL_COARSE_FP32, "bf16": WL_COARSE_BF16, "fp16": WL_C
 EXPORTS = (
     "wl_default_opts", "wl_workspace_bytes", "wl_create", "wl_set_ic", "wl_step", "wl_stage",
     "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_viscous_force", "wl_get_field", "wl_set_field", "wl_get_dt",
-    "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_levels", "wl_level_dims",
+    "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_graph_kernels", "wl_levels", "wl_level_dims",
     "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
     "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split",
 )
@@ -108,6 +108,7 @@ def load(path: str = LIB_PATH):
         "wl_get_time": (I, [H, DP, ctypes.POINTER(ctypes.c_longlong)]),
         "wl_status": (I, [H, IP, ctypes.POINTER(ctypes.c_longlong), DP]),
         "wl_profile_step": (I, [H, I, DP, ctypes.POINTER(ctypes.c_longlong)]),
+        "wl_graph_kernels": (I, [H, IP, IP]),
         "wl_levels": (I, [H, IP]),
         "wl_level_dims": (I, [H, I, IP]),
         "wl_destroy": (None, [H]),
@@ -224,6 +225,12 @@ def wl_profile_step(h, nsteps):
     n = (ctypes.c_longlong * len(KCLASSES))()
     rc = load().wl_profile_step(h, int(nsteps), ms, n)
     return rc, {k: (ms[i], n[i]) for i, k in enumerate(KCLASSES)}
+
+
+def wl_graph_kernels(h):
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    rc = load().wl_graph_kernels(h, ctypes.byref(a), ctypes.byref(b))
+    return rc, a.value, b.value
 
 
 def wl_levels(h):
@@ -428,6 +435,12 @@ class Sim:
         rc, last, tot, worst = wl_status(self.h)
         self._check(rc, "wl_status")
         return rc, last, tot, worst
+
+    def graph_kernels(self):
+        """wl_graph_kernels: (kernels per step outside the V-cycles, kernels per V-cycle)."""
+        rc, a, b = wl_graph_kernels(self.h)
+        self._check(rc, "wl_graph_kernels")
+        return a, b
 
     def profile_step(self, nsteps=1):
         """{kernel class: (total ms, launches)} over nsteps host-driven steps."""
