@@ -40,6 +40,7 @@ struct LevelBuf {
   int st;                         // storage type ST_* of Lk, z, x, x2
   float zs;                       // z is stored scaled: stored = zs * value (a power of two)
   int tma_tiles, wrap_tiles;      // sweep tiles for the staged kernel / across a periodic side (table kernel)
+  int wrap_tma_tiles;             // tiles across a periodic side for the staged kernel's wrapping variant
   BandBox band;                   // region whose coefficients may differ from uval (staged kernels)
   float uval;                     // the level's coefficient away from the body: 2^(l (D-2))
   float* z32;                     // a 16-bit level 1: the restricted fine residual in FP32, converted
@@ -464,7 +465,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
     a.x_out = bufs[out];
     a.ph = (refine && it == P - 1) ? s->ph : nullptr;
     a.pl = (refine && it == P - 1) ? s->pl : nullptr;
-    if (L.tma && L.tma_tiles > 0) {
+    if (L.tma && (L.tma_tiles > 0 || L.wrap_tma_tiles > 0)) {
       SweepMaps m;
       m.x = in >= 0 ? *bmaps[in] : L.mx;
       m.z = refine ? s->srf : L.sz;
@@ -485,6 +486,10 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       for (int d = 0; d < 3; ++d) t.cn[d] = a.cn[d];
       t.tz = tz_staged;
       t.st = s->ds;
+      t.plain = L.tma_tiles > 0;
+      t.wrap = L.wrap_tma_tiles > 0;
+      t.xsrc = a.x_in;
+      t.zsrc = refine ? s->rf : L.z;
       PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st, side_of(s)));
       a.only_wrapping = 1;  // tiles crossing a periodic side
       if (L.wrap_tiles > 0) PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
@@ -904,20 +909,27 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       const int tz = sweep_planes_per_block(L.g, SWEEP_UNI_BLOCKS_PER_SM);
       L.band.on = (split && band_tile_fraction(ndim, L.g, tz, L.band) <= frac_max) ? 1 : 0;
       // tiles the staged sweep takes and tiles across a periodic side (launches with
-      // no tile of their kind are skipped)
+      // no tile of their kind are skipped).  The staged kernel takes the latter too when
+      // the periodic sides are whole tiles and all of those tiles are uniform.
       const int tzs = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
-      L.tma_tiles = L.wrap_tiles = 0;
+      L.tma_tiles = L.wrap_tiles = L.wrap_tma_tiles = 0;
+      bool wrap_uni = L.band.on && sweep_wrap_shape_ok(L.g);
       const int nz = ndim == 3 ? (L.g.n[2] + tzs - 1) / tzs : 1;
       for (int tk = 0; tk < nz; ++tk)
         for (int tj = 0; tj < (L.g.n[1] + SWEEP_TY - 1) / SWEEP_TY; ++tj)
           for (int ti = 0; ti < (L.g.n[0] + SWEEP_TX - 1) / SWEEP_TX; ++ti) {
             const int k0 = ndim == 3 ? tk * tzs : 0, k1 = ndim == 3 ? std::min(k0 + tzs, L.g.n[2]) : 1;
-            (void)k1;
-            if (sweep_tile_wraps_xy(L.g, ti * SWEEP_TX, tj * SWEEP_TY))
+            if (sweep_tile_wraps_xy(L.g, ti * SWEEP_TX, tj * SWEEP_TY)) {
               ++L.wrap_tiles;
-            else
+              if (tile_in_band(L.band, ndim, ti * SWEEP_TX, tj * SWEEP_TY, k0, k1)) wrap_uni = false;
+            } else {
               ++L.tma_tiles;
+            }
           }
+      if (wrap_uni) {
+        L.wrap_tma_tiles = L.wrap_tiles;
+        L.wrap_tiles = 0;
+      }
     }
   }
   // The coarse end of the V-cycle runs in one block from the largest level whose

@@ -108,6 +108,11 @@ struct SweepTmaArgs {
   BandBox band;        // tiles outside it: coefficients = uval (0 on walls), not loaded
   float uval;
   int t0[3];           // first tile of the launch (the band tiles' launch starts inside the grid)
+  int plain;           // sweep the tiles that cross no periodic x / y side
+  int wrap;            // also sweep (uniform variant) the tiles that cross one; their halo
+                       // elements past the side are read from the wrapped cells of:
+  const float* xsrc;   //   the staged iterate (has_x)
+  const float* zsrc;   //   the staged right-hand side
 };
 
 // Dense pseudo-inverse of the coarsest operator (column-major, FP64), used when the
@@ -213,9 +218,10 @@ int sweep_planes_per_block(const Grid& g, int blocks_per_sm);
 int sweep_table_blocks_per_sm(int D, int stype);
 
 // Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.
-// A tile whose TMA footprint (x i0-4..i0+67, y j0-2..j0+9) crosses a periodic x or y
-// side is swept by k_sweep; the others by k_sweep_tma, which stages planes past a
-// periodic z side from their wrapped planes.
+// k_sweep_tma stages planes past a periodic z side from their wrapped planes.  A tile
+// whose TMA footprint (x i0-4..i0+67, y j0-2..j0+9) crosses a periodic x or y side is
+// swept by k_sweep_tma's wrapping variant when the level's periodic sides are whole
+// tiles (sweep_wrap_shape_ok) and every such tile is uniform, else by k_sweep.
 constexpr int SWEEP_TX = 64, SWEEP_TY = 8;
 // rows of the sweep's coefficient boxes (z, L0, L2; L1 takes one more), from j0-1
 constexpr int SWEEP_CROWS = SWEEP_TY + 2;
@@ -223,6 +229,7 @@ constexpr int SWEEP_CROWS = SWEEP_TY + 2;
 // variant (register bound)
 constexpr int SWEEP_BLOCKS_PER_SM = 4;
 constexpr int SWEEP_UNI_BLOCKS_PER_SM = 6;
+constexpr int SWEEP_WRAP_BLOCKS_PER_SM = 4;  // the wrapping variant (register bound)
 // The tile's staged footprint (x i0-4..i0+67, y j0-2..j0+9, planes k0-2..k1+1)
 // meets the band box (always true without a split).
 __host__ __device__ inline bool tile_in_band(const BandBox& b, int D, int i0, int j0, int k0, int k1) {
@@ -238,6 +245,13 @@ __host__ __device__ inline bool sweep_tile_wraps_xy(const Grid& g, int i0, int j
   if ((g.per & 1u) && (i0 - 4 < 0 || i0 + SWEEP_TX + 4 > g.n[0])) return true;
   if ((g.per & 2u) && (j0 - 2 < 0 || j0 + SWEEP_TY + 2 > g.n[1])) return true;
   return false;
+}
+// The level's periodic x / y sides are whole tiles (n_0 % 64 == 0, n_1 % 8 == 0), so every
+// halo element of a tile past such a side is a cell of the wrapped tile column / row,
+// and a plane's cells have a 32-bit index.
+__host__ __device__ inline bool sweep_wrap_shape_ok(const Grid& g) {
+  return (!(g.per & 1u) || g.n[0] % SWEEP_TX == 0) && (!(g.per & 2u) || g.n[1] % SWEEP_TY == 0) &&
+         (long long)g.n[0] * g.n[1] < (1ll << 31);
 }
 __host__ __device__ inline bool sweep_tile_wraps(const Grid& g, int D, int i0, int j0, int k0, int k1) {
   if ((g.per & 1u) && (i0 - 4 < 0 || i0 + SWEEP_TX + 4 > g.n[0])) return true;

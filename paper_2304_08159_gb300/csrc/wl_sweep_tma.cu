@@ -14,8 +14,9 @@
 // disjoint banks and no shared access conflicts.  Out-of-range elements are
 // zero-filled by the copy engine, which is exactly the value a non-periodic wall
 // needs (face coefficient 0 across it), so the relaxation itself carries no
-// boundary logic.  Tiles whose footprint would wrap across a periodic side are
-// left to k_sweep.
+// boundary logic.  A tile whose footprint crosses a periodic x or y side takes the
+// wrapping variant (uniform tiles only), which overwrites the zero-filled halo elements
+// past the side with the wrapped cells' values, read from global memory one plane ahead.
 #include <cuda.h>
 
 #include <algorithm>
@@ -119,10 +120,14 @@ __device__ __forceinline__ void sts(uint32_t a, float v) { asm volatile("st.shar
 // the level's free-stream value uval (0 on the walls): only the iterate and the
 // right-hand side are staged, the coefficients are formed from the cell's position
 // (same values, same operation order, same bits), and the smaller rings fit more
-// blocks per SM.
-template <int D, bool UNI>
-__global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM)
+// blocks per SM.  WRAP (uniform only): the tiles whose footprint crosses a periodic x
+// or y side, the others' the tiles that cross none.
+template <int D, bool UNI, bool WRAP>
+__global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
+                                         : UNI ? SWEEP_UNI_BLOCKS_PER_SM
+                                               : SWEEP_BLOCKS_PER_SM)
     k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
+  static_assert(UNI || !WRAP, "wrapping tiles are uniform");
   extern __shared__ float smf[];
   // 128-byte aligned slot rings (iterate, L2, z, L0, L1), then the mbarriers, all
   // addressed by 32-bit float offsets into smf
@@ -136,7 +141,7 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
   const int k0 = (D == 3) ? (blockIdx.z + a.t0[2]) * a.tz : 0;
   if (i0 >= g.n[0] || j0 >= g.n[1] || k0 >= g.n[2]) return;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
-  if (sweep_tile_wraps_xy(g, i0, j0)) return;  // the table kernel's tile
+  if (sweep_tile_wraps_xy(g, i0, j0) != WRAP) return;  // the other launch's tile
   if (tile_in_band(a.band, D, i0, j0, k0, k1) == UNI) return;  // the other variant's tile
   // a plane past a periodic z side is staged from its wrapped plane
   const bool pz = D == 3 && is_per(g, 2);
@@ -203,7 +208,9 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
 #pragma unroll
   for (int r = 0; r < 2; ++r) {
     const int t = tid + SW_NT * r, cr = t / CBX, cc = t - cr * CBX;
-    const int ci = (i0 >> 1) - 2 + cc, cj = (j0 >> 1) - 1 + cr;
+    int ci = (i0 >> 1) - 2 + cc, cj = (j0 >> 1) - 1 + cr;
+    if (is_per(g, 0)) ci = ci < 0 ? ci + a.cn[0] : (ci >= a.cn[0] ? ci - a.cn[0] : ci);  // a wrapping tile
+    if (is_per(g, 1)) cj = cj < 0 ? cj + a.cn[1] : (cj >= a.cn[1] ? cj - a.cn[1] : cj);
     ceo[r] = t < CBOX ? 2 * cr * BX + 2 * cc : -1;
     cxy[r] = (t < CBOX && a.xc && ci >= 0 && ci < a.cn[0] && cj >= 0 && cj < a.cn[1]) ? ci + a.cn[0] * cj : -1;
   }
@@ -236,6 +243,79 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
   auto fix_x = [&](int p) {
     load_c(p);
     apply_c(p);
+  };
+  // WRAP: the halo elements past a periodic x / y side, which the copy engine zero-fills,
+  // hold the wrapped cells' values: in the iterate box rows 0-1 / 10-11 (y j0-2, j0-1 /
+  // j0+8, j0+9) and columns 0-3 / 68-71, in the right-hand side box row 0 / 9 (y j0-1 /
+  // j0+8) and the same columns.  The entries form one list per box, full-width row
+  // strips first, then the column strips over the remaining rows; thread t takes
+  // entries t, t + 160, ...  Each entry keeps its box offset (-1: none, or a cell past
+  // a wall) and the wrapped cell's index in its plane.
+  constexpr int NWX = 3, NWZ = 2;  // list lengths <= 352 and <= 208
+  int wxo[NWX], wzo[NWZ];
+  unsigned wxq[NWX], wzq[NWZ];
+  float wxv[NWX], wzv[NWZ];  // values of the next planes to patch
+  if constexpr (WRAP) {
+    const bool px = is_per(g, 0), py = is_per(g, 1);
+    const bool wl = px && i0 == 0, wr = px && i0 + TX == g.n[0];
+    const bool wt = py && j0 == 0, wb = py && j0 + TY == g.n[1];
+    // rows: box height, ry: rows of one wrapped strip, y0: the box's first y
+    auto entry = [&](int t, int rows, int ry, int y0, int& off, unsigned& q) {
+      const int rt = wt ? ry : 0, rb = wb ? ry : 0, hr = rows - rt - rb;
+      const int nrow = (rt + rb) * BX, ncol = ((wl ? 1 : 0) + (wr ? 1 : 0)) * 4 * hr;
+      int row, col;
+      if (t < nrow) {
+        const int r = t / BX;
+        row = r < rt ? r : rows - rb + (r - rt);
+        col = t - r * BX;
+      } else if (t < nrow + ncol) {
+        const int u = t - nrow, sd = u / (4 * hr), v = u - sd * 4 * hr;
+        row = rt + (v >> 2);
+        col = (wl && sd == 0) ? (v & 3) : BX - 4 + (v & 3);
+      } else {
+        off = -1;
+        q = 0u;
+        return;
+      }
+      int gi = i0 - 4 + col, gj = y0 + row;
+      if (px) gi = gi < 0 ? gi + g.n[0] : (gi >= g.n[0] ? gi - g.n[0] : gi);
+      if (py) gj = gj < 0 ? gj + g.n[1] : (gj >= g.n[1] ? gj - g.n[1] : gj);
+      const bool in = gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1];
+      off = in ? row * BX + col : -1;
+      q = in ? (unsigned)gi + (unsigned)g.n[0] * (unsigned)gj : 0u;
+    };
+#pragma unroll
+    for (int r = 0; r < NWX; ++r) entry(tid + SW_NT * r, BY, 2, j0 - 2, wxo[r], wxq[r]);
+#pragma unroll
+    for (int r = 0; r < NWZ; ++r) entry(tid + SW_NT * r, CROWS, 1, j0 - 1, wzo[r], wzq[r]);
+  }
+  // in-plane offset of plane p's wrapped plane, or -1 past a wall in z
+  auto wplane = [&](int p) -> long long {
+    if (D == 2) return 0;
+    const int w = wz(p);
+    return (w >= 0 && w < g.n[2]) ? (long long)g.n[0] * g.n[1] * w : -1;
+  };
+  auto wload_x = [&](int p, float* v) {
+    const long long o = wplane(p);
+#pragma unroll
+    for (int r = 0; r < NWX; ++r) v[r] = (o >= 0 && wxo[r] >= 0) ? a.xsrc[o + wxq[r]] : 0.f;
+  };
+  auto wload_z = [&](int p, float* v) {
+    const long long o = wplane(p);
+#pragma unroll
+    for (int r = 0; r < NWZ; ++r) v[r] = (o >= 0 && wzo[r] >= 0) ? a.zsrc[o + wzq[r]] : 0.f;
+  };
+  auto wstore_x = [&](int p, const float* v) {
+    float* X = smf + Xs(xslot(p));
+#pragma unroll
+    for (int r = 0; r < NWX; ++r)
+      if (wxo[r] >= 0) X[wxo[r]] = v[r];
+  };
+  auto wstore_z = [&](int p, const float* v) {
+    float* Z = smf + Zs(cslot(p));
+#pragma unroll
+    for (int r = 0; r < NWZ; ++r)
+      if (wzo[r] >= 0) Z[wzo[r]] = v[r];
   };
   // Operand planes of a relaxation (shared byte addresses): iterate planes below /
   // at / above, and the coefficient planes (shifted one row so that one shared
@@ -345,8 +425,10 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
   auto xymask = [&](int col, int row) -> uint32_t {
     const int gi = i0 + col, gj = j0 + row;
     const bool px = is_per(g, 0), py = is_per(g, 1);
+    // past a periodic side (a wrapping tile's halo) the cell is the wrapped one
+    const bool in = ((gi >= 0 && gi < g.n[0]) || px) && ((gj >= 0 && gj < g.n[1]) || py);
     return (gi > 0 || px ? 1u : 0u) | (gi + 1 < g.n[0] || px ? 2u : 0u) | (gj > 0 || py ? 4u : 0u) |
-           (gj + 1 < g.n[1] || py ? 8u : 0u) | (gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1] ? 16u : 0u);
+           (gj + 1 < g.n[1] || py ? 8u : 0u) | (in ? 16u : 0u);
   };
   {
     const int ib0 = 2 * (lane & 15);
@@ -566,9 +648,26 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
     if (D == 3)
       for (int b = k0; b < k0 + LEAD && b <= k1 - 1; ++b) issue_bundle(b);
   }
+  // WRAP: the prologue's patch values, read while the copies are in flight
+  float wpx[4][NWX], wpz[2][NWZ];
+  if constexpr (WRAP) {
+    if (a.has_x)
+      for (int p = plo; p <= phi; ++p) wload_x(p, wpx[p - plo]);
+    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 : 0); ++p) wload_z(p, wpz[p - (D == 3 ? k0 - 1 : 0)]);
+  }
   {
     const bool ok = mbar_wait(smem_addr(&bars[0]), 0);
     if (__syncthreads_or(!ok)) return bail(true, k0);
+  }
+  if constexpr (WRAP) {
+    if (a.has_x)
+      for (int p = plo; p <= phi; ++p) wstore_x(p, wpx[p - plo]);
+    for (int p = (D == 3 ? k0 - 1 : 0); p <= (D == 3 ? k0 : 0); ++p) wstore_z(p, wpz[p - (D == 3 ? k0 - 1 : 0)]);
+    __syncthreads();
+    if (D == 3) {  // bundle k0's planes
+      if (a.has_x) wload_x(k0 + 2, wxv);
+      wload_z(k0 + 1, wzv);
+    }
   }
   if (fix) {
     for (int p = plo; p <= phi; ++p) fix_x(p);
@@ -596,6 +695,15 @@ __global__ void __launch_bounds__(SW_NT, UNI ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_B
     {
       const bool ok = mbar_wait(bbar(k), bphase(k));
       if (__syncthreads_or(!ok)) return bail(false, k);
+      if constexpr (WRAP) {  // bundle k: iterate plane k+2, right-hand side plane k+1
+        if (a.has_x) wstore_x(k + 2, wxv);
+        wstore_z(k + 1, wzv);
+        __syncthreads();
+        if (k + 1 <= k1 - 1) {  // bundle k+1's, used by the next iteration
+          if (a.has_x) wload_x(k + 3, wxv);
+          wload_z(k + 2, wzv);
+        }
+      }
       if (fix) {
         apply_c(k + 2);
         __syncthreads();
@@ -1020,22 +1128,25 @@ size_t sweep_tma_smem(bool uni) {
   return rings * sizeof(float) + (1 + NBB) * sizeof(uint64_t) + 128;
 }
 
-template <int D, bool UNI>
+template <int D, bool UNI, bool WRAP = false>
 void launch_sweep_tma_v(const SweepMaps& m, const SweepTmaArgs& a, dim3 grd, cudaStream_t s) {
   const size_t smem = sweep_tma_smem(UNI);
   static bool attr = false;
   if (!attr) {  // all of the unified L1/shared storage as shared memory: the blocks per SM are smem-bound
-    cudaFuncSetAttribute(k_sweep_tma<D, UNI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_sweep_tma<D, UNI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_sweep_tma<D, UNI, WRAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sweep_tma<D, UNI, WRAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     attr = true;
   }
-  k_sweep_tma<D, UNI><<<grd, SW_NT, smem, s>>>(m, a);
+  k_sweep_tma<D, UNI, WRAP><<<grd, SW_NT, smem, s>>>(m, a);
 }
 
-// Tiles meeting the level's band box run the loading kernel, the others the uniform
-// one; without a split every tile loads its coefficients.
-int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStream_t s, const SideStream* side) {
+namespace {
+
+// The tiles that cross no periodic side: those meeting the level's band box run the
+// loading kernel, the others the uniform one; without a split every tile loads its
+// coefficients.
+void launch_plain(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStream_t s, const SideStream* side) {
   const Grid& g = a0.g;
   const int tz = D == 3 ? a0.tz : 1;
   const dim3 full((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, D == 3 ? (g.n[2] + tz - 1) / tz : 1);
@@ -1046,7 +1157,7 @@ int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStre
       launch_sweep_tma_v<3, false>(m, a, full, s);
     else
       launch_sweep_tma_v<2, false>(m, a, full, s);
-    return 0;
+    return;
   }
   auto uni = [&](cudaStream_t st) {
     if (D == 3)
@@ -1065,7 +1176,7 @@ int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStre
   }
   if (hi[0] <= lo[0] || hi[1] <= lo[1] || hi[2] <= lo[2]) {
     uni(s);
-    return 0;
+    return;
   }
   SweepTmaArgs b = a;
   for (int d = 0; d < 3; ++d) b.t0[d] = lo[d];
@@ -1086,6 +1197,23 @@ int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStre
   } else {
     band(s);
     uni(s);
+  }
+}
+
+}  // namespace
+
+int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStream_t s, const SideStream* side) {
+  if (a0.plain) launch_plain(D, m, a0, s, side);
+  if (a0.wrap) {  // the tiles across a periodic x / y side (all uniform), after the others
+    const Grid& g = a0.g;
+    const int tz = D == 3 ? a0.tz : 1;
+    const dim3 full((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, D == 3 ? (g.n[2] + tz - 1) / tz : 1);
+    SweepTmaArgs a = a0;
+    a.t0[0] = a.t0[1] = a.t0[2] = 0;
+    if (D == 3)
+      launch_sweep_tma_v<3, true, true>(m, a, full, s);
+    else
+      launch_sweep_tma_v<2, true, true>(m, a, full, s);
   }
   return 0;
 }
