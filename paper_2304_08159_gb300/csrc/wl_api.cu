@@ -41,6 +41,7 @@ struct LevelBuf {
   float zs;                       // z is stored scaled: stored = zs * value (a power of two)
   int tma_tiles, wrap_tiles;      // sweep tiles for the staged kernel / across a periodic side (table kernel)
   int wrap_tma_tiles;             // tiles across a periodic side for the staged kernel's wrapping variant
+  int tzw;                        // planes per block of its launch
   BandBox band;                   // region whose coefficients may differ from uval (staged kernels)
   float uval;                     // the level's coefficient away from the body: 2^(l (D-2))
   float* z32;                     // a 16-bit level 1: the restricted fine residual in FP32, converted
@@ -490,6 +491,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       t.wrap = L.wrap_tma_tiles > 0;
       t.xsrc = a.x_in;
       t.zsrc = refine ? s->rf : L.z;
+      t.tzw = L.tzw;
       PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st, side_of(s)));
       a.only_wrapping = 1;  // tiles crossing a periodic side
       if (L.wrap_tiles > 0) PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
@@ -911,21 +913,28 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       // tiles the staged sweep takes and tiles across a periodic side (launches with
       // no tile of their kind are skipped).  The staged kernel takes the latter too when
       // the periodic sides are whole tiles and all of those tiles are uniform.
-      const int tzs = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
+      // Tile columns (x, y) of each kind; the wrapping launch blocks z for its own tile
+      // columns and residency, and the band test uses its tiles.
       L.tma_tiles = L.wrap_tiles = L.wrap_tma_tiles = 0;
+      const int ntx = (L.g.n[0] + SWEEP_TX - 1) / SWEEP_TX, nty = (L.g.n[1] + SWEEP_TY - 1) / SWEEP_TY;
+      for (int tj = 0; tj < nty; ++tj)
+        for (int ti = 0; ti < ntx; ++ti) {
+          if (sweep_tile_wraps_xy(L.g, ti * SWEEP_TX, tj * SWEEP_TY))
+            ++L.wrap_tiles;
+          else
+            ++L.tma_tiles;
+        }
+      L.tzw = sweep_planes_for_columns(L.g.n[2], std::max(L.wrap_tiles, 1), SWEEP_WRAP_BLOCKS_PER_SM);
       bool wrap_uni = L.band.on && sweep_wrap_shape_ok(L.g);
-      const int nz = ndim == 3 ? (L.g.n[2] + tzs - 1) / tzs : 1;
-      for (int tk = 0; tk < nz; ++tk)
-        for (int tj = 0; tj < (L.g.n[1] + SWEEP_TY - 1) / SWEEP_TY; ++tj)
-          for (int ti = 0; ti < (L.g.n[0] + SWEEP_TX - 1) / SWEEP_TX; ++ti) {
-            const int k0 = ndim == 3 ? tk * tzs : 0, k1 = ndim == 3 ? std::min(k0 + tzs, L.g.n[2]) : 1;
-            if (sweep_tile_wraps_xy(L.g, ti * SWEEP_TX, tj * SWEEP_TY)) {
-              ++L.wrap_tiles;
-              if (tile_in_band(L.band, ndim, ti * SWEEP_TX, tj * SWEEP_TY, k0, k1)) wrap_uni = false;
-            } else {
-              ++L.tma_tiles;
-            }
+      const int nz = ndim == 3 ? (L.g.n[2] + L.tzw - 1) / L.tzw : 1;
+      for (int tj = 0; tj < nty && wrap_uni; ++tj)
+        for (int ti = 0; ti < ntx; ++ti) {
+          if (!sweep_tile_wraps_xy(L.g, ti * SWEEP_TX, tj * SWEEP_TY)) continue;
+          for (int tk = 0; tk < nz; ++tk) {
+            const int k0 = ndim == 3 ? tk * L.tzw : 0, k1 = ndim == 3 ? std::min(k0 + L.tzw, L.g.n[2]) : 1;
+            if (tile_in_band(L.band, ndim, ti * SWEEP_TX, tj * SWEEP_TY, k0, k1)) wrap_uni = false;
           }
+        }
       if (wrap_uni) {
         L.wrap_tma_tiles = L.wrap_tiles;
         L.wrap_tiles = 0;

@@ -109,10 +109,12 @@ struct SweepTmaArgs {
   float uval;
   int t0[3];           // first tile of the launch (the band tiles' launch starts inside the grid)
   int plain;           // sweep the tiles that cross no periodic x / y side
-  int wrap;            // also sweep (uniform variant) the tiles that cross one; their halo
+  int wrap;            // also sweep (uniform variant, tzw planes per block) the tiles that
+                       // cross one; their halo
                        // elements past the side are read from the wrapped cells of:
   const float* xsrc;   //   the staged iterate (has_x)
   const float* zsrc;   //   the staged right-hand side
+  int tzw;             // planes per block of the wrapping tiles' launch (its own residency)
 };
 
 // Dense pseudo-inverse of the coarsest operator (column-major, FP64), used when the
@@ -215,6 +217,7 @@ int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s, 
 int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s);
 // planes per block of the sweep kernels for blocks_per_sm resident blocks
 int sweep_planes_per_block(const Grid& g, int blocks_per_sm);
+int sweep_planes_for_columns(int n2, long long tiles, int blocks_per_sm);
 int sweep_table_blocks_per_sm(int D, int stype);
 
 // Both sweep kernels cut a level into the same tiles of 64 x 8 cells and `tz` planes.

@@ -563,6 +563,12 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
 // kernel's own residency) times the planes a block marches through plus about 1.5 planes
 // of prologue and epilogue work.
 int sweep_planes_per_block(const Grid& g, int blocks_per_sm) {
+  const long long tiles = (long long)((g.n[0] + SW_TX - 1) / SW_TX) * ((g.n[1] + SW_TY - 1) / SW_TY);
+  return sweep_planes_for_columns(g.n[2], tiles, blocks_per_sm);
+}
+
+// The same for a launch over `tiles` tile columns of n2 planes.
+int sweep_planes_for_columns(int n2, long long tiles, int blocks_per_sm) {
   static int nsm = 0;
   if (nsm <= 0) {
     int dev = 0;
@@ -572,12 +578,11 @@ int sweep_planes_per_block(const Grid& g, int blocks_per_sm) {
       nsm = 152;
     }
   }
-  const long long tiles = (long long)((g.n[0] + SW_TX - 1) / SW_TX) * ((g.n[1] + SW_TY - 1) / SW_TY);
   const long long wave = (long long)blocks_per_sm * nsm;
   int best = 2;
   double best_cost = 1e300;
   for (int tz = 2; tz <= 32; ++tz) {
-    const long long nb = tiles * ((g.n[2] + tz - 1) / tz);
+    const long long nb = tiles * ((n2 + tz - 1) / tz);
     const double cost = (double)((nb + wave - 1) / wave) * (tz + 1.5);
     if (cost < best_cost) {
       best_cost = cost;

@@ -1206,9 +1206,10 @@ int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStre
   if (a0.plain) launch_plain(D, m, a0, s, side);
   if (a0.wrap) {  // the tiles across a periodic x / y side (all uniform), after the others
     const Grid& g = a0.g;
-    const int tz = D == 3 ? a0.tz : 1;
+    const int tz = D == 3 ? a0.tzw : 1;
     const dim3 full((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, D == 3 ? (g.n[2] + tz - 1) / tz : 1);
     SweepTmaArgs a = a0;
+    a.tz = tz;
     a.t0[0] = a.t0[1] = a.t0[2] = 0;
     if (D == 3)
       launch_sweep_tma_v<3, true, true>(m, a, full, s);
