@@ -252,7 +252,12 @@ int wl_graph_kernels(wl_handle h, int* per_step, int* per_vcycle);
  * wl_forces' computation (F_d = -sum (p - pbar) n_d K_eps(d), FP64) on fields the caller
  * already holds:
  *   dims/ndim/periodic_mask: the grid; body, eps: the immersed body and BDIM half-width;
- *   p: device pointer, n cells of FP32 pressure (x fastest);
+ *   p: device pointer, n cells of FP32 pressure (x fastest).  A sim at the default
+ *      precision (1) keeps its fine pressure as a double-float pair ph + pl and wl_forces
+ *      sums that pair; this entry point sees only the FP32 pressure it is given (for a
+ *      sim's own state, WL_FIELD_P: the pair rounded to FP32), so its result differs from
+ *      wl_forces by that rounding (the low word is left out).  At precision 0 both read
+ *      the same FP32 field;
  *   L: device pointer, ndim blocks of n FP32 face coefficients (WL_FIELD_MU0 layout),
  *      used to find the cells with a nonzero Poisson row for pbar;
  *   F: device pointer receiving ndim doubles; stream: cudaStream_t (NULL = default).

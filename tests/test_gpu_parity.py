@@ -117,6 +117,10 @@ def test_vcycle_parity(case):
     # So: cell values on the other rows, face fluxes everywhere.
     scale = np.abs(xo).max()
     well = ref.poisson_diag() >= 1e-2
+    if (~well).any():
+        print(f"{case['id']}: low-diagonal rows {int((~well).sum())}, worst cell error "
+              f"{np.abs(xg - xo)[~well].max() / scale:.2e} of max|x| (well-conditioned rows "
+              f"{np.abs(xg - xo)[well].max() / scale:.2e})")
     assert np.abs(xg - xo)[well].max() <= 1e-5 * scale, (np.abs(xg - xo)[well].max(), scale)
     Ls = ref.level_L(0)
     D = len(case["dims"])
@@ -399,12 +403,21 @@ def test_uniform_tiles_large_sphere_bitwise(case, monkeypatch):
     dict(id="yper128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.0, 0.0), periodic=2,
          body=dict(kind=1, center=(40.0, 30.0, 24.0), radius=6.0)),
     dict(id="xyper64x16x24", dims=(64, 16, 24), nu=0.01, U=(0.0, 0.0, 0.0), periodic=3, body=None),
+    # fallbacks to the table sweep: the body's band meets a tile across the periodic x
+    # side (so no tile across it is uniform), and periodic sides that are not whole tiles
+    dict(id="xper256x64cyl_at_side", dims=(256, 64), nu=0.02, U=(1.0, 0.0), periodic=1,
+         body=dict(kind=1, center=(8.0, 31.6), radius=6.0)),
+    dict(id="xper200x48", dims=(200, 48), nu=0.02, U=(0.0, 0.0), periodic=3, body=None),
+    dict(id="yper96x36x32", dims=(96, 36, 32), nu=0.01, U=(1.0, 0.0, 0.0), periodic=2,
+         body=dict(kind=1, center=(30.0, 18.0, 16.0), radius=5.0)),
 ], ids=lambda c: c["id"])
 def test_wrapping_tiles_match_table_sweep(case, monkeypatch):
     """Tiles across a periodic x / y side whose sides are whole tiles (n_0 % 64, n_1 % 8)
     take the staged sweep's wrapping variant, which reads the halo past the side from the
     wrapped cells: identical bits to the index-table sweep on every level (uniform split
-    forced on every level in both runs, so only the sweep kernel differs)."""
+    forced on every level in both runs, so only the sweep kernel differs).  Where a tile
+    across a periodic side meets the body's band, or a periodic side is not whole tiles,
+    those tiles go to the table sweep: the same bits again."""
     monkeypatch.setenv("WL_UNIFORM_ALL", "1")
     a, _ = make_pair(case, oracle=False)
     monkeypatch.setenv("WL_NO_TMA", "1")
@@ -482,6 +495,42 @@ def test_bench_sphere_first_step_full_size(name):
     assert np.abs(u - u[::-1, :, :]).max() <= 1e-4 * np.abs(u).max()
     v = ug[1]
     assert np.abs(v[:, 1:, :] + v[:, :0:-1, :]).max() <= 1e-4 * np.abs(u).max()
+
+
+@pytest.mark.parametrize("name,nsteps", [("sphere256", 10), ("donut256", 3)])
+def test_bench_body_full_size_steps(name, nsteps):
+    """Body workloads at full size over several adaptive steps: the 256x128x128 sphere
+    (Re 3700) for 10 steps, the stated bar's horizon, and the 256x128x128 donut (Re 1000)
+    for 3, against the oracle's steps with multigrid projections to 1e-10.  After the
+    impulsive start the wake forms, the pressure grows and the band faces carry nonzero
+    mu1 gradients, so this covers what a first step does not.
+    Two GPU runs from the same start: as bench.py launches it (CUDA-graph steps, Poisson
+    tol 1e-6), where every cell's velocity (1e-5), dt, time and the drag coefficient (1e-4)
+    are checked, and the pressure within the tolerance gap (a residual of 1e-6 in x = p w
+    dt units leaves an absolute pressure error of order 1e-6/(w dt), 2e-4 of this flow's
+    small pressure after 10 steps); and the same steps at tol 1e-8, where the pressure
+    meets the stated 1e-5 bar as well."""
+    from bench import WORKLOADS
+    from paper_2304_08159_gb300 import Sim
+
+    w, sim, ref = _bench_pair(name)
+    tight = Sim(w["dims"], w["nu"], w["U"], body=w["body"], periodic=w["periodic"], tol=1e-8)
+    for _ in range(nsteps):
+        sim.step(1)
+        tight.step(1)
+        ref.step(1, tol=1e-10, maxit=200, solver=1)
+    _check_step_parity(w, sim, ref, nsteps, p_bar=1e-3)
+    _check_step_parity(w, tight, ref, nsteps, p_bar=1e-5)
+    b = w["body"]
+    area = np.pi * b["radius"] ** 2 if b["kind"] == 1 else 4.0 * np.pi * b["radius"] * b["radius2"]
+    Fo = ref.forces()
+    CDo = Fo[0] / (0.5 * area)
+    for s, tol in ((sim, 1e-6), (tight, 1e-8)):
+        CDg = s.forces()[0] / (0.5 * area)
+        print(f"{name}: C_D {CDg:.6f} vs {CDo:.6f} after {nsteps} steps (tol {tol:g})")
+        assert abs(CDg - CDo) <= 1e-4 * abs(CDo), (CDg, CDo)
+    sim.close()
+    tight.close()
 
 
 def test_bench_tgv_full_size_steps():
