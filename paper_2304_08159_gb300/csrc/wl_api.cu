@@ -399,7 +399,7 @@ void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) 
       for (int d = 0; d < 3; ++d) t.cn[d] = s->lev[1].g.n[d];
       if (s->lev[1].z32) t.zc = s->lev[1].z32;  // FP32 staging of a 16-bit level 1
     }
-    const int tz = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
+    const int tz = sweep_planes_per_block(L.g, L.band.on ? RESID_UNI_WAVE_BLOCKS : SWEEP_BLOCKS_PER_SM);
     t.tz = tz + (tz & 1);
     t.inv_w = 1.f / w;
     t.st = s->ds;

@@ -231,8 +231,10 @@ constexpr int SWEEP_CROWS = SWEEP_TY + 2;
 // resident blocks per SM of the staged sweep (shared memory bound) and of its uniform
 // variant (register bound)
 constexpr int SWEEP_BLOCKS_PER_SM = 4;
-constexpr int SWEEP_UNI_BLOCKS_PER_SM = 6;
-constexpr int SWEEP_WRAP_BLOCKS_PER_SM = 4;  // the wrapping variant (register bound)
+constexpr int SWEEP_UNI_BLOCKS_PER_SM = 8;
+constexpr int SWEEP_WRAP_BLOCKS_PER_SM = 5;  // the wrapping variant (register bound)
+// blocks per SM the fine residual's z-blocking assumes for its split launches
+constexpr int RESID_UNI_WAVE_BLOCKS = 6;
 // The tile's staged footprint (x i0-4..i0+67, y j0-2..j0+9, planes k0-2..k1+1)
 // meets the band box (always true without a split).
 __host__ __device__ inline bool tile_in_band(const BandBox& b, int D, int i0, int j0, int k0, int k1) {

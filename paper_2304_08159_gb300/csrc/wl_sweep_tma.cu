@@ -40,7 +40,7 @@ constexpr int XR = LEAD + 4;    // iterate slots (planes k-1 .. k+2, and LEAD mo
 constexpr int L2R = LEAD + 3;   // L2 slots (planes k .. k+2, and LEAD more in flight)
 constexpr int CR = LEAD + 2;    // z, L0, L1 slots (planes k, k+1, and LEAD more in flight)
 constexpr int NBB = 2;          // bundle mbarriers (a power of two, > LEAD)
-constexpr int SW_NT = 160;      // sweep threads: 5 warps
+constexpr int SW_NT = 128;      // sweep threads: 4 warps
 static_assert(NBB > LEAD && (NBB & (NBB - 1)) == 0, "bundle barriers");
 static_assert(BOX * 4 % 128 == 0, "iterate slots keep 128-byte alignment");
 constexpr unsigned kWaitLimit = 1u << 21;      // wait attempts
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   // j0+8, j0+9) and columns 0-3 / 68-71, in the right-hand side box row 0 / 9 (y j0-1 /
   // j0+8) and the same columns.  The entries form one list per box, full-width row
   // strips first, then the column strips over the remaining rows; thread t takes
-  // entries t, t + 160, ...  Each entry keeps its box offset (-1: none, or a cell past
+  // entries t, t + 128, ...  Each entry keeps its box offset (-1: none, or a cell past
   // a wall) and the wrapped cell's index in its plane.
   constexpr int NWX = 3, NWZ = 2;  // list lengths <= 352 and <= 208
   int wxo[NWX], wzo[NWZ];
@@ -415,13 +415,14 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     return (dg > 0.f) ? __fdividef(sum - lds(P.z + e), dg) : 0.f;
   };
   // Red cells of plane p cover the tile plus a 1-cell halo (rows -1..8, columns
-  // -1..64): ten tasks of 32 (two adjacent rows x half the tile's columns), tasks w
-  // and w+5 for warp w, and ten edge-column cells, rows -1..3 on lanes 0..4 of warp
-  // 3 and rows 4..8 on lanes 0..4 of warp 4.  Black cells of plane k (rows 0..7):
-  // eight tasks, w and (w < 3) w+5.  Shared byte offsets into the iterate box, for
-  // even and odd planes.
-  uint32_t er[2][2], eb[2][2], ee[2];
-  uint32_t mr[2][2], mb[2][2], me[2];  // UNI: face masks of each task's cell (relax_uni)
+  // -1..64): ten tasks of 32 (two adjacent rows x half the tile's columns) and ten
+  // edge-column cells.  Warp w takes red tasks w and w+4 as a pair, and a third red
+  // task: w+8 for warps 0-1, or five edge cells (rows -1..3 on warp 2, rows 4..8 on
+  // warp 3; lanes 0..4).  Black cells of plane k (rows 0..7): eight tasks, w and w+4
+  // as a pair.  So every warp relaxes one red pair, one red single and one black pair
+  // per plane.  Shared byte offsets into the iterate box, for even and odd planes.
+  uint32_t er[3][2], eb[2][2];
+  uint32_t mr[3][2], mb[2][2];  // UNI: face masks of each task's cell (relax_uni)
   auto xymask = [&](int col, int row) -> uint32_t {
     const int gi = i0 + col, gj = j0 + row;
     const bool px = is_per(g, 0), py = is_per(g, 1);
@@ -430,47 +431,46 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     return (gi > 0 || px ? 1u : 0u) | (gi + 1 < g.n[0] || px ? 2u : 0u) | (gj > 0 || py ? 4u : 0u) |
            (gj + 1 < g.n[1] || py ? 8u : 0u) | (in ? 16u : 0u);
   };
+  const bool third = warp < 2 || lane < 5;  // this lane has a third red cell
   {
     const int ib0 = 2 * (lane & 15);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int t = warp + 5 * h;
+    for (int h = 0; h < 3; ++h) {
+      const int t = warp + 4 * h;
       const int jr = 2 * (t >> 1) + (lane >> 4) - 1, jb = jr + 1;
       const int ib = 32 * (t & 1) + ib0;
+      const int je = (warp == 2) ? lane - 1 : lane + 4;  // edge rows (third cell of warps 2, 3)
 #pragma unroll
       for (int par = 0; par < 2; ++par) {
-        const int cr = ib + ((i0 + j0 + jr + par) & 1), cb = ib + ((i0 + j0 + jb + par + 1) & 1);
-        er[h][par] = 4u * ((jr + 2) * BX + cr + 4);
-        eb[h][par] = 4u * ((jb + 2) * BX + cb + 4);
-        if (UNI) {
-          mr[h][par] = xymask(cr, jr);
-          mb[h][par] = xymask(cb, jb);
+        int cr = ib + ((i0 + j0 + jr + par) & 1), rr = jr;
+        if (h == 2 && warp >= 2) {
+          cr = ((i0 + j0 + je + par) & 1) ? -1 : 64;
+          rr = je;
+        }
+        er[h][par] = 4u * ((rr + 2) * BX + cr + 4);
+        if (UNI) mr[h][par] = xymask(cr, rr);
+        if (h < 2) {
+          const int cb = ib + ((i0 + j0 + jb + par + 1) & 1);
+          eb[h][par] = 4u * ((jb + 2) * BX + cb + 4);
+          if (UNI) mb[h][par] = xymask(cb, jb);
         }
       }
     }
-    const int je = (warp == 3) ? lane - 1 : lane + 4;
-#pragma unroll
-    for (int par = 0; par < 2; ++par) {
-      const int ce = ((i0 + j0 + je + par) & 1) ? -1 : 64;
-      ee[par] = 4u * ((je + 2) * BX + ce + 4);
-      if (UNI) me[par] = xymask(ce, je);
-    }
   }
   // UNI, tiles that touch a wall: bit t of fast_m is set when every lane's cell of task t
-  // (red 2h+par, black 4+2h+par, edge 8+par) is inside the grid with all four x/y faces,
-  // so that on a plane with both z faces the task takes relax_fast (same bits)
+  // (red 2h+par, black 6+2h+par) is inside the grid with all four x/y faces, so that on
+  // a plane with both z faces the task takes relax_fast (same bits)
   uint32_t fast_m = 0u;
   if (UNI && !interior) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
+    for (int par = 0; par < 2; ++par) {
 #pragma unroll
-      for (int par = 0; par < 2; ++par) {
+      for (int h = 0; h < 2; ++h) {
         if (__all_sync(0xffffffffu, mr[h][par] == 31u)) fast_m |= 1u << (2 * h + par);
-        if (__all_sync(0xffffffffu, mb[h][par] == 31u)) fast_m |= 1u << (4 + 2 * h + par);
+        if (__all_sync(0xffffffffu, mb[h][par] == 31u)) fast_m |= 1u << (6 + 2 * h + par);
       }
-#pragma unroll
-    for (int par = 0; par < 2; ++par)
-      if (__all_sync(0xffffffffu, !(warp >= 3 && lane < 5) || me[par] == 31u)) fast_m |= 1u << (8 + par);
+      if (__all_sync(0xffffffffu, !third || mr[2][par] == 31u)) fast_m |= 1u << (4 + par);
+    }
   }
   // UNI: z faces and range of plane kk
   auto zmask = [&](int kk, bool& zlo, bool& zhi, bool& kin) {
@@ -478,18 +478,15 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     zhi = kk + 1 < g.n[2] || pz;
     kin = pz || (kk >= 0 && kk < g.n[2]);
   };
-  const bool has_edge = warp >= 3 && lane < 5, two_black = warp < 3;
   // red cells of plane kk (parity par) whose operands are P
   auto red_plane = [&](const Planes& P, int par, int kk) {
     const uint32_t e0 = par ? er[0][1] : er[0][0], e1 = par ? er[1][1] : er[1][0];
+    const uint32_t e2 = par ? er[2][1] : er[2][0];
     if (UNI && interior) {
       const float2 v = relax_fast2(P, e0, e1);
       sts(P.x0 + e0, v.x);
       sts(P.x0 + e1, v.y);
-      if (has_edge) {
-        const uint32_t f = par ? ee[1] : ee[0];
-        sts(P.x0 + f, relax_fast(P, f));
-      }
+      if (third) sts(P.x0 + e2, relax_fast(P, e2));
       return;
     }
     if (UNI) {
@@ -506,67 +503,45 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
         sts(P.x0 + e0, v0);
         sts(P.x0 + e1, v1);
       }
-      if (has_edge) {
-        const uint32_t f = par ? ee[1] : ee[0];
-        sts(P.x0 + f, (fm & 256u) ? relax_fast(P, f) : relax_uni(P, f, par ? me[1] : me[0], zlo, zhi, kin));
-      }
+      if (third)
+        sts(P.x0 + e2, (fm & 16u) ? relax_fast(P, e2) : relax_uni(P, e2, par ? mr[2][1] : mr[2][0], zlo, zhi, kin));
       return;
     }
     const float v0 = relax(P, e0), v1 = relax(P, e1);
     sts(P.x0 + e0, v0);
     sts(P.x0 + e1, v1);
-    if (has_edge) {
-      const uint32_t f = par ? ee[1] : ee[0];
-      sts(P.x0 + f, relax(P, f));
-    }
+    if (third) sts(P.x0 + e2, relax(P, e2));
   };
   // black cells of plane kk (parity par) whose operands are P
   auto black_plane = [&](const Planes& P, int par, int kk) {
-    const uint32_t e0 = par ? eb[0][1] : eb[0][0];
+    const uint32_t e0 = par ? eb[0][1] : eb[0][0], e1 = par ? eb[1][1] : eb[1][0];
     if (UNI && interior) {
-      if (two_black) {
-        const uint32_t e1 = par ? eb[1][1] : eb[1][0];
-        const float2 v = relax_fast2(P, e0, e1);
-        sts(P.x0 + e0, v.x);
-        sts(P.x0 + e1, v.y);
-      } else {
-        sts(P.x0 + e0, relax_fast(P, e0));
-      }
+      const float2 v = relax_fast2(P, e0, e1);
+      sts(P.x0 + e0, v.x);
+      sts(P.x0 + e1, v.y);
       return;
     }
     if (UNI) {
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
-      const uint32_t m0 = par ? mb[0][1] : mb[0][0];
-      const uint32_t fm = (zlo && zhi && kin) ? fast_m >> (4 + par) : 0u;
-      if (two_black && (fm & 5u) == 5u) {
-        const uint32_t e1 = par ? eb[1][1] : eb[1][0];
+      const uint32_t fm = (zlo && zhi && kin) ? fast_m >> (6 + par) : 0u;
+      if ((fm & 5u) == 5u) {
         const float2 v = relax_fast2(P, e0, e1);
         sts(P.x0 + e0, v.x);
         sts(P.x0 + e1, v.y);
         return;
       }
-      const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, m0, zlo, zhi, kin);
-      if (two_black) {
-        const uint32_t e1 = par ? eb[1][1] : eb[1][0];
-        const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mb[1][1] : mb[1][0], zlo, zhi, kin);
-        sts(P.x0 + e0, v0);
-        sts(P.x0 + e1, v1);
-      } else {
-        sts(P.x0 + e0, v0);
-      }
-      return;
-    }
-    if (two_black) {
-      const uint32_t e1 = par ? eb[1][1] : eb[1][0];
-      const float v0 = relax(P, e0), v1 = relax(P, e1);
+      const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, par ? mb[0][1] : mb[0][0], zlo, zhi, kin);
+      const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mb[1][1] : mb[1][0], zlo, zhi, kin);
       sts(P.x0 + e0, v0);
       sts(P.x0 + e1, v1);
-    } else {
-      sts(P.x0 + e0, relax(P, e0));
+      return;
     }
+    const float v0 = relax(P, e0), v1 = relax(P, e1);
+    sts(P.x0 + e0, v0);
+    sts(P.x0 + e1, v1);
   };
-  // Write the tile's plane k: 256 column pairs, pair t and t + 160 for thread t;
+  // Write the tile's plane k: 256 column pairs, pair t and t + 128 for thread t;
   // pair (tx, ty) is columns 2tx, 2tx+1 of row ty (n0 % 4 == 0, so both columns
   // exist when the first does).
   bool st_own[2];
