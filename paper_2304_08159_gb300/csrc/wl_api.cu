@@ -1679,3 +1679,127 @@ int wl_level_split(wl_handle s, int l, int* split, double* band_fraction) {
                         : 1.0;
   return WL_OK;
 }
+
+// --------------------------------------------------------------- checkpoint / resume
+namespace {
+
+// Header of a saved state; the payload follows it: the velocity (D fields of nc values,
+// then the exit plane when the sim has one), the fine pressure (ph and pl at precision 1,
+// the FP32 pressure otherwise) and the device state.
+struct SaveHeader {
+  char magic[8];
+  int version;
+  int D;
+  int n[3];
+  unsigned per;
+  int precision;
+  int exit;
+  int state_bytes;  // sizeof(DevState)
+  int pad;
+  long long nc;
+  long long bytes;  // header + payload
+  double nu;
+  double U[3];
+};
+constexpr char kSaveMagic[8] = {'W', 'L', 'S', 'T', 'A', 'T', 'E', '1'};
+
+long long exit_values(const wl_sim* s) { return s->g.exit ? (long long)s->g.n[1] * s->g.n[2] : 0; }
+int npressure(const wl_sim* s) { return s->ph ? 2 : 1; }
+
+size_t state_bytes(const wl_sim* s) {
+  return sizeof(SaveHeader) + sizeof(float) * ((size_t)s->D * s->g.nc + exit_values(s) + npressure(s) * s->g.nc) +
+         sizeof(DevState);
+}
+
+SaveHeader make_header(const wl_sim* s) {
+  SaveHeader h{};
+  std::memcpy(h.magic, kSaveMagic, sizeof(kSaveMagic));
+  h.version = 1;
+  h.D = s->D;
+  for (int d = 0; d < 3; ++d) h.n[d] = s->g.n[d];
+  h.per = s->g.per;
+  h.precision = s->ph ? 1 : 0;
+  h.exit = s->g.exit;
+  h.state_bytes = (int)sizeof(DevState);
+  h.nc = s->g.nc;
+  h.bytes = (long long)state_bytes(s);
+  h.nu = s->nu;
+  for (int d = 0; d < 3; ++d) h.U[d] = s->g.U[d];
+  return h;
+}
+
+}  // namespace
+
+extern "C" size_t wl_state_bytes(wl_handle s) { return s ? state_bytes(s) : 0; }
+
+extern "C" int wl_save(wl_handle s, void* dst, size_t dst_bytes, int dst_is_device) {
+  if (!s || !dst) return WL_EINVAL;
+  if (dst_bytes < state_bytes(s)) return fail(s, WL_EINVAL, "wl_save: destination smaller than wl_state_bytes");
+  const SaveHeader h = make_header(s);
+  const cudaMemcpyKind d2x = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  char* p = static_cast<char*>(dst);
+  if (dst_is_device)
+    WL_CUDA(s, cudaMemcpyAsync(p, &h, sizeof(h), cudaMemcpyHostToDevice, s->st));
+  else
+    std::memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  const size_t nb = sizeof(float) * (size_t)s->g.nc;
+  for (int c = 0; c < s->D; ++c, p += nb) WL_CUDA(s, cudaMemcpyAsync(p, s->ua[c], nb, d2x, s->st));
+  if (s->g.exit) {
+    const size_t eb = sizeof(float) * (size_t)exit_values(s);
+    WL_CUDA(s, cudaMemcpyAsync(p, s->ua[0] + s->g.nc, eb, d2x, s->st));
+    p += eb;
+  }
+  if (s->ph) {
+    WL_CUDA(s, cudaMemcpyAsync(p, s->ph, nb, d2x, s->st));
+    WL_CUDA(s, cudaMemcpyAsync(p + nb, s->pl, nb, d2x, s->st));
+    p += 2 * nb;
+  } else {
+    WL_CUDA(s, cudaMemcpyAsync(p, s->lev[0].x, nb, d2x, s->st));
+    p += nb;
+  }
+  WL_CUDA(s, cudaMemcpyAsync(p, s->ds, sizeof(DevState), d2x, s->st));
+  // a host destination (and the header's staging copy) must be complete on return
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  return WL_OK;
+}
+
+extern "C" int wl_load(wl_handle s, const void* src, size_t src_bytes, int src_is_device) {
+  if (!s || !src) return WL_EINVAL;
+  if (src_bytes < sizeof(SaveHeader)) return fail(s, WL_EINVAL, "wl_load: source smaller than a state header");
+  SaveHeader h{};
+  if (src_is_device) {
+    WL_CUDA(s, cudaMemcpyAsync(&h, src, sizeof(h), cudaMemcpyDeviceToHost, s->st));
+    WL_CUDA(s, cudaStreamSynchronize(s->st));
+  } else {
+    std::memcpy(&h, src, sizeof(h));
+  }
+  const SaveHeader want = make_header(s);
+  bool same = std::memcmp(h.magic, kSaveMagic, sizeof(kSaveMagic)) == 0 && h.version == want.version &&
+              h.D == want.D && h.per == want.per && h.precision == want.precision && h.exit == want.exit &&
+              h.state_bytes == want.state_bytes && h.nc == want.nc && h.bytes == want.bytes && h.nu == want.nu;
+  for (int d = 0; d < 3; ++d) same = same && h.n[d] == want.n[d] && h.U[d] == want.U[d];
+  if (!same) return fail(s, WL_EINVAL, "wl_load: the saved state belongs to a different simulation setup");
+  if (src_bytes < (size_t)h.bytes) return fail(s, WL_EINVAL, "wl_load: source shorter than the saved state");
+  const cudaMemcpyKind x2d = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  const char* p = static_cast<const char*>(src) + sizeof(h);
+  const size_t nb = sizeof(float) * (size_t)s->g.nc;
+  for (int c = 0; c < s->D; ++c, p += nb) WL_CUDA(s, cudaMemcpyAsync(s->ua[c], p, nb, x2d, s->st));
+  if (s->g.exit) {
+    const size_t eb = sizeof(float) * (size_t)exit_values(s);
+    WL_CUDA(s, cudaMemcpyAsync(s->ua[0] + s->g.nc, p, eb, x2d, s->st));
+    p += eb;
+  }
+  if (s->ph) {
+    WL_CUDA(s, cudaMemcpyAsync(s->ph, p, nb, x2d, s->st));
+    WL_CUDA(s, cudaMemcpyAsync(s->pl, p + nb, nb, x2d, s->st));
+    p += 2 * nb;
+  } else {
+    WL_CUDA(s, cudaMemcpyAsync(s->lev[0].x, p, nb, x2d, s->st));
+    p += nb;
+  }
+  WL_CUDA(s, cudaMemcpyAsync(s->ds, p, sizeof(DevState), x2d, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  s->poisoned = false;
+  return WL_OK;
+}

@@ -10,6 +10,7 @@
 // non-zero only in the thin band |d| < eps around the body and is added by
 // k_bdim_band over the body's bounding box.
 #include <algorithm>
+#include <cstdlib>
 #include <type_traits>
 
 #include "wl_dev.cuh"
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
           const float u0 = (a.stage == 1) ? uc : u0v[c];
           f = fmaf(dt, r, u0);
           const float m = m0[c];
-          ov = (a.stage == 1) ? m * f : 0.5f * (uc + m * f);
+          ov = (a.stage == 1) ? m * f : 0.5f * fmaf(m, f, uc);
         }
         a.out[c][qg] = ov;
         if (box_tile) {  // keep f inside the body's band box for the mu1 term
@@ -233,6 +234,281 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
     }
   } else {
     step(IC<0>{}, 0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3-D stage kernel with two x-adjacent cells per thread.  The same fluxes and blend as
+// k_stage, in the same operation order: mom_flux2 is mom_flux lane by lane (the packed
+// FP32 operations round each lane as the scalar operation does), so both kernels give
+// the same bits.  A tile of 64 x 8 cells marches up 32 planes; thread (l, w) owns cells
+// (2l, w) and (2l+1, w).  The velocity of planes k-1..k+2 (box x i0-2..i0+65, y
+// j0-2..j0+9) sits in a 4-plane shared ring, read as aligned pairs; plane k+3 is loaded
+// into registers while plane k is computed.  A thread forms the lower x-, y- and z-face
+// fluxes of its two cells: the upper x flux of cell 2l is its own lower flux of 2l+1,
+// that of 2l+1 comes from lane l+1 by a shuffle; upper y fluxes come from the next row
+// through shared memory; the upper z flux is carried to the next plane in registers.
+// The fluxes through the tile's upper x edge (column 64; 3 components x 8 rows) are
+// formed by lanes 0..23 of warp 0, those through its upper y edge (row 8) by warps
+// 1..3, one component each.  ADV: convection on (the viscous flux alone otherwise).
+constexpr int S3_TX = 64, S3_TY = 8, S3_TZ = 32;
+constexpr int S3_HX = S3_TX + 4, S3_HY = S3_TY + 4, S3_PL = S3_HX * S3_HY;
+constexpr int S3_NP = 4;
+constexpr int S3_NPAIR = S3_PL / 2;  // float pairs per component per plane
+
+// mom_flux on two lanes at once (each lane: the same operations as mom_flux)
+template <bool ADV>
+__device__ __forceinline__ float2 mom_flux2(float2 m2, float2 m1, float2 p0, float2 p1, float2 a2, float nu) {
+  const float2 diff = mul2(make_float2(nu, nu), sub2(p0, m1));
+  if (!ADV) return neg2(diff);
+  const bool px = a2.x > 0.f, py = a2.y > 0.f;
+  const float2 uu = make_float2(px ? m2.x : p1.x, py ? m2.y : p1.y);
+  const float2 cc = make_float2(px ? m1.x : p0.x, py ? m1.y : p0.y);
+  const float2 dd = make_float2(px ? p0.x : m1.x, py ? p0.y : m1.y);
+  const float2 dD = sub2(dd, cc), dU = sub2(cc, uu);
+  const float2 ad = make_float2(fabsf(dD.x), fabsf(dD.y)), au = make_float2(fabsf(dU.x), fabsf(dU.y));
+  const float2 two = make_float2(2.f, 2.f);
+  const float2 t2u = mul2(two, au), t2d = mul2(two, ad);
+  const float2 mid = mul2(fma2(two, ad, au), make_float2(1.f / 3.f, 1.f / 3.f));
+  const float tx = fminf(fminf(t2u.x, mid.x), t2d.x), ty = fminf(fminf(t2u.y, mid.y), t2d.y);
+  const float2 pr = mul2(dU, dD);
+  const float2 lim = make_float2(pr.x > 0.f ? copysignf(tx, dD.x) : 0.f, pr.y > 0.f ? copysignf(ty, dD.y) : 0.f);
+  const float2 half = make_float2(0.5f, 0.5f);
+  const float2 phi = fma2(half, lim, cc);
+  return fma2(mul2(half, a2), phi, neg2(diff));
+}
+
+template <bool ADV>
+__global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
+  constexpr int HX = S3_HX, PL = S3_PL, NP = S3_NP;
+  __shared__ __align__(16) float s_u[3 * NP * PL];
+  __shared__ __align__(16) float s_fy[3][S3_TY + 1][S3_TX];
+  __shared__ float s_fxe[3][S3_TY];
+  const Grid& g = a.g;
+  const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
+  const int i0 = blockIdx.x * S3_TX, j0 = blockIdx.y * S3_TY;
+  const int k0 = blockIdx.z * S3_TZ;
+  const int k1 = min(k0 + S3_TZ, g.n[2]);
+  const int i = i0 + 2 * lane, j = j0 + ty;
+  const bool own_cell = (i < g.n[0]) && (j < g.n[1]);  // n_0 even: both cells or neither
+  const float dt = *a.dt;
+  const float nu = a.nu;
+  const bool box_tile = a.fbox && i0 < a.blo[0] + a.bn[0] && i0 + S3_TX > a.blo[0] && j0 < a.blo[1] + a.bn[1] &&
+                        j0 + S3_TY > a.blo[1] && k0 < a.blo[2] + a.bn[2] && k1 > a.blo[2];
+  auto soff = [](int c, int sl) { return (c * NP + sl) * PL; };
+  auto ld2 = [&](int o) { return *reinterpret_cast<const float2*>(s_u + o); };
+
+  // plane fetch: pair e = tid, tid + 256 of each component's 34 x 12 pairs
+  const bool xy_inner = (i0 >= 2) && (i0 + S3_TX + 2 <= g.n[0]) && (j0 >= 2) && (j0 + S3_TY + 2 <= g.n[1]);
+  const long long nxy = (long long)g.n[0] * g.n[1];
+  const long long fbase = (long long)(i0 - 2) + (long long)g.n[0] * (j0 - 2);
+  int foff[2], fsh[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + 256 * h, row = e / (HX / 2), cp = e - row * (HX / 2);
+    foff[h] = 2 * cp + g.n[0] * row;
+    fsh[h] = row * HX + 2 * cp;
+  }
+  float2 rv[2][3];
+  auto fetch = [&](int kk) {
+    const bool inner = xy_inner && kk >= 0 && kk < g.n[2];
+    const long long qk = fbase + nxy * kk;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + 256 * h;
+      if (e >= S3_NPAIR) break;
+      if (inner) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rv[h][c] = __ldg(reinterpret_cast<const float2*>(a.u[c] + qk + foff[h]));
+      } else {
+        const int row = e / (HX / 2), col = 2 * (e - row * (HX / 2));
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          rv[h][c] = make_float2(load_u_bc<3>(a.u[c], c, g, i0 - 2 + col, j0 - 2 + row, kk),
+                                 load_u_bc<3>(a.u[c], c, g, i0 - 1 + col, j0 - 2 + row, kk));
+      }
+    }
+  };
+  auto commit = [&](int sl) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + 256 * h;
+      if (e >= S3_NPAIR) break;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) *reinterpret_cast<float2*>(s_u + soff(c, sl) + fsh[h]) = rv[h][c];
+    }
+  };
+  const int own = (ty + 2) * HX + 2 * lane + 2;  // box position of cell 2l
+  // the pair (U[p-1], U[p]) from the aligned pairs A = (U[p-2], U[p-1]), B = (U[p], U[p+1])
+  auto mid2 = [](float2 A, float2 B) { return make_float2(A.y, B.x); };
+
+  // lower x-face fluxes of the two cells, component C, plane slot S (plane k), SM (k-1)
+  auto flux_x = [&](auto C, auto S, auto SM) -> float2 {
+    constexpr int c = decltype(C)::value, sl = decltype(S)::value, sm = decltype(SM)::value;
+    const int o = soff(c, sl) + own;
+    const float2 A = ld2(o - 2), B = ld2(o), Cn = ld2(o + 2);
+    float2 a2;
+    if (c == 0) {
+      a2 = add2(B, mid2(A, B));
+    } else {
+      const int ox = soff(0, sl) + own;
+      a2 = add2(ld2(ox), c == 1 ? ld2(ox - HX) : ld2(soff(0, sm) + own));
+    }
+    return mom_flux2<ADV>(A, mid2(A, B), B, mid2(B, Cn), a2, nu);
+  };
+  auto flux_y = [&](auto C, auto S, auto SM) -> float2 {
+    constexpr int c = decltype(C)::value, sl = decltype(S)::value, sm = decltype(SM)::value;
+    const int o = soff(c, sl) + own;
+    const int oy = soff(1, sl) + own;
+    const float2 Y0 = ld2(oy);
+    float2 a2;
+    if (c == 0)
+      a2 = add2(Y0, mid2(ld2(oy - 2), Y0));
+    else if (c == 1)
+      a2 = add2(Y0, ld2(oy - HX));
+    else
+      a2 = add2(Y0, ld2(soff(1, sm) + own));
+    return mom_flux2<ADV>(ld2(o - 2 * HX), ld2(o - HX), ld2(o), ld2(o + HX), a2, nu);
+  };
+  // lower z-face flux at plane kf, planes kf-2 .. kf+1 in slots Q0 .. Q3
+  auto flux_z = [&](auto C, auto Q0, auto Q1, auto Q2, auto Q3) -> float2 {
+    constexpr int c = decltype(C)::value, q0 = decltype(Q0)::value, q1 = decltype(Q1)::value,
+                  q2 = decltype(Q2)::value, q3 = decltype(Q3)::value;
+    const int oz = soff(2, q2) + own;
+    const float2 Z0 = ld2(oz);
+    float2 a2;
+    if (c == 0)
+      a2 = add2(Z0, mid2(ld2(oz - 2), Z0));
+    else if (c == 1)
+      a2 = add2(Z0, ld2(oz - HX));
+    else
+      a2 = add2(Z0, ld2(soff(2, q1) + own));
+    return mom_flux2<ADV>(ld2(soff(c, q0) + own), ld2(soff(c, q1) + own), ld2(soff(c, q2) + own),
+                          ld2(soff(c, q3) + own), a2, nu);
+  };
+  // warp 0, lanes 0..23: the flux through the upper x edge (face i0+64) of row lane%8,
+  // component lane/8 (scalar mom_flux, operand addresses chosen per lane)
+  auto edge_x = [&](int sl, int sm) {
+    const int c = lane >> 3, row = lane & 7;
+    const int pe = (row + 2) * HX + S3_TX + 2;  // box position of cell 64
+    const float* U = s_u + soff(c, sl) + pe;
+    const float* A = s_u + soff(0, sl) + pe;
+    const float other = c == 0 ? A[-1] : (c == 1 ? A[-HX] : s_u[soff(0, sm) + pe]);
+    s_fxe[c][row] = mom_flux(U[-2], U[-1], U[0], U[1], A[0] + other, nu, ADV);
+  };
+  // warps 1..3: the fluxes through the upper y edge (row 8) of component warp-1
+  auto edge_y = [&](auto C, auto S, auto SM) {
+    constexpr int c = decltype(C)::value, sl = decltype(S)::value, sm = decltype(SM)::value;
+    const int p8 = (S3_TY + 2) * HX + 2 * lane + 2;
+    const int o = soff(c, sl) + p8, oy = soff(1, sl) + p8;
+    const float2 Y0 = ld2(oy);
+    float2 a2;
+    if (c == 0)
+      a2 = add2(Y0, mid2(ld2(oy - 2), Y0));
+    else if (c == 1)
+      a2 = add2(Y0, ld2(oy - HX));
+    else
+      a2 = add2(Y0, ld2(soff(1, sm) + p8));
+    const float2 f = mom_flux2<ADV>(ld2(o - 2 * HX), ld2(o - HX), ld2(o), ld2(o + HX), a2, nu);
+    *reinterpret_cast<float2*>(&s_fy[c][S3_TY][2 * lane]) = f;
+  };
+  const long long qij = own_cell ? (long long)i + (long long)g.n[0] * j : 0;
+
+  float2 fzl[3];
+  // planes k0-2 .. k0+1 in slots 0 .. 3
+  for (int t = 0; t < 4; ++t) {
+    fetch(k0 - 2 + t);
+    commit(t);
+  }
+  fetch(k0 + 2);
+  __syncthreads();
+  fzl[0] = flux_z(IC<0>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{});
+  fzl[1] = flux_z(IC<1>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{});
+  fzl[2] = flux_z(IC<2>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{});
+  __syncthreads();
+
+  // plane k, with k - k0 = PH (mod NP): plane k+t sits in slot (PH + t + 2) mod NP
+  auto step = [&](auto PHc, int k) {
+    constexpr int PH = decltype(PHc)::value;
+    constexpr int S0 = (PH + 2) % NP, SM1 = (PH + 1) % NP, SP1 = (PH + 3) % NP, SP2 = PH % NP;
+    using I0 = IC<S0>;
+    using Im = IC<SM1>;
+    commit(SP2);  // plane k+2 into the slot of plane k-2
+    __syncthreads();
+    if (k + 3 <= k1 + 1) fetch(k + 3);
+    const long long qg = qij + nxy * k;
+    float2 m0[3], u0v[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      m0[c] = own_cell ? __ldg(reinterpret_cast<const float2*>(a.mu0[c] + qg)) : make_float2(0.f, 0.f);
+      u0v[c] = (own_cell && a.stage != 1) ? __ldg(reinterpret_cast<const float2*>(a.u0[c] + qg))
+                                          : make_float2(0.f, 0.f);
+    }
+    float2 fx[3], fzu[3];
+    fx[0] = flux_x(IC<0>{}, I0{}, Im{});
+    fx[1] = flux_x(IC<1>{}, I0{}, Im{});
+    fx[2] = flux_x(IC<2>{}, I0{}, Im{});
+    *reinterpret_cast<float2*>(&s_fy[0][ty][2 * lane]) = flux_y(IC<0>{}, I0{}, Im{});
+    *reinterpret_cast<float2*>(&s_fy[1][ty][2 * lane]) = flux_y(IC<1>{}, I0{}, Im{});
+    *reinterpret_cast<float2*>(&s_fy[2][ty][2 * lane]) = flux_y(IC<2>{}, I0{}, Im{});
+    // face k+1: planes k-1 .. k+2
+    fzu[0] = flux_z(IC<0>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{});
+    fzu[1] = flux_z(IC<1>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{});
+    fzu[2] = flux_z(IC<2>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{});
+    if (ty == 0) {
+      if (lane < 24) edge_x(S0, SM1);
+    } else if (ty == 1) {
+      edge_y(IC<0>{}, I0{}, Im{});
+    } else if (ty == 2) {
+      edge_y(IC<1>{}, I0{}, Im{});
+    } else if (ty == 3) {
+      edge_y(IC<2>{}, I0{}, Im{});
+    }
+    __syncthreads();
+    float nxt[3];  // lower x flux of lane l+1's first cell (every lane takes part)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) nxt[c] = __shfl_down_sync(0xffffffffu, fx[c].x, 1);
+    if (own_cell) {
+      const int I[3] = {i, j, k};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        // upper x faces: (lower flux of 2l+1, lower flux of 2l+2 from lane l+1 or the edge)
+        const float2 fxu = make_float2(fx[c].y, lane == 31 ? s_fxe[c][ty] : nxt[c]);
+        const float2 fyu = *reinterpret_cast<const float2*>(&s_fy[c][ty + 1][2 * lane]);
+        const float2 fyl = *reinterpret_cast<const float2*>(&s_fy[c][ty][2 * lane]);
+        const float2 r = add2(add2(sub2(fx[c], fxu), sub2(fyl, fyu)), sub2(fzl[c], fzu[c]));
+        const float2 uc = ld2(soff(c, S0) + own);
+        const float2 u0 = (a.stage == 1) ? uc : u0v[c];
+        const float2 f = fma2(make_float2(dt, dt), r, u0);
+        const float2 mf = mul2(m0[c], f);
+        float2 ov = (a.stage == 1) ? mf : mul2(make_float2(0.5f, 0.5f), fma2(m0[c], f, uc));
+        float2 fo = f;
+        // boundary faces of a non-periodic direction keep U_c (only i = 0 can be the pair's first cell)
+        const bool upd0 = is_per(g, c) || I[c] >= 1;
+        const bool upd1 = is_per(g, c) || (c == 0 ? i + 1 : I[c]) >= 1;
+        if (!upd0) ov.x = fo.x = g.U[c];
+        if (!upd1) ov.y = fo.y = g.U[c];
+        *reinterpret_cast<float2*>(a.out[c] + qg) = ov;
+        if (box_tile) {  // keep f inside the body's band box for the mu1 term
+          const unsigned bj = (unsigned)(j - a.blo[1]), bk = (unsigned)(k - a.blo[2]);
+          if (bj < (unsigned)a.bn[1] && bk < (unsigned)a.bn[2]) {
+            const long long base =
+                (long long)c * a.bn[0] * a.bn[1] * a.bn[2] + (long long)a.bn[0] * (bj + (long long)a.bn[1] * bk);
+            const unsigned b0 = (unsigned)(i - a.blo[0]), b1 = (unsigned)(i + 1 - a.blo[0]);
+            if (b0 < (unsigned)a.bn[0]) a.fbox[base + b0] = fo.x;
+            if (b1 < (unsigned)a.bn[0]) a.fbox[base + b1] = fo.y;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) fzl[c] = fzu[c];
+  };
+  for (int kb = k0; kb < k1; kb += NP) {
+    step(IC<0>{}, kb);
+    if (kb + 1 < k1) step(IC<1>{}, kb + 1);
+    if (kb + 2 < k1) step(IC<2>{}, kb + 2);
+    if (kb + 3 < k1) step(IC<3>{}, kb + 3);
   }
 }
 
@@ -290,7 +566,14 @@ __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0,
 int launch_stage(int D, const StageArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
   dim3 blk(256);
-  if (D == 3) {
+  const bool v1 = std::getenv("WL_STAGE_V1") != nullptr;  // the one-cell-per-thread kernel
+  if (D == 3 && g.n[0] % 2 == 0 && !v1) {
+    dim3 grd((g.n[0] + S3_TX - 1) / S3_TX, (g.n[1] + S3_TY - 1) / S3_TY, (g.n[2] + S3_TZ - 1) / S3_TZ);
+    if (a.advect)
+      k_stage3<true><<<grd, blk, 0, s>>>(a);
+    else
+      k_stage3<false><<<grd, blk, 0, s>>>(a);
+  } else if (D == 3) {
     dim3 grd((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_TY - 1) / ST_TY, (g.n[2] + ST_TZ - 1) / ST_TZ);
     k_stage<3><<<grd, blk, 0, s>>>(a);
   } else {

@@ -343,6 +343,49 @@ def test_vcycle_tail_matches_per_level_kernels(case, monkeypatch):
     assert np.array_equal(a.get(1), b.get(1))
 
 
+STAGE3_CASES = [c for c in CASES_3D if c["dims"][0] % 2 == 0] + [
+    dict(id="s130x70x40", dims=(130, 70, 40), nu=0.01, U=(1.0, 0.1, -0.05), periodic=0,
+         body=dict(kind=1, center=(60.3, 33.2, 19.7), radius=7.0)),
+    dict(id="xyper128x48x24", dims=(128, 48, 24), nu=0.02, U=(0.3, 0.0, 0.0), periodic=3, body=None),
+    dict(id="exit96x40x32", dims=(96, 40, 32), nu=0.02, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=1, center=(30.0, 20.3, 15.8), radius=5.0), kw=dict(exit_bc=True)),
+]
+
+
+@pytest.mark.parametrize("case", STAGE3_CASES, ids=lambda c: c["id"])
+@pytest.mark.parametrize("advect", [True, False], ids=["advect", "diffuse"])
+def test_stage_pairs_match_single_cell_kernel(case, advect, monkeypatch):
+    """The 3-D stage kernel with two cells per thread (packed FP32 pairs, shuffled x
+    fluxes) against the one-cell-per-thread kernel: identical bits for both stages on a
+    seeded velocity, and over three full steps (the band box of f included)."""
+    from paper_2304_08159_gb300 import wl
+
+    a, _ = make_pair(case, oracle=False, advect=advect, **case.get("kw", {}))
+    b, _ = make_pair(case, oracle=False, advect=advect, **case.get("kw", {}))
+    rng = np.random.default_rng(109)
+    u0 = _rand_u(a, rng, case["U"]).astype(np.float32)
+    u1 = _rand_u(a, rng, case["U"]).astype(np.float32)
+    for st in (1, 2):
+        for sim, v1 in ((a, False), (b, True)):
+            sim.set(wl.WL_FIELD_U, u0)
+            sim.set(wl.WL_FIELD_UPRED, u1)
+            sim.dt = 0.31
+            if v1:
+                monkeypatch.setenv("WL_STAGE_V1", "1")
+            sim.stage(st)
+            monkeypatch.delenv("WL_STAGE_V1", raising=False)
+        assert np.array_equal(a.get(wl.WL_FIELD_USTAGE), b.get(wl.WL_FIELD_USTAGE)), st
+    uic = (0.3 * u0 + 0.7 * np.asarray(case["U"]).reshape(3, 1, 1, 1)).astype(np.float32)
+    for sim in (a, b):
+        sim.set_ic(2, 1.0, u=uic)
+    a.step(3)
+    monkeypatch.setenv("WL_STAGE_V1", "1")
+    b.step(3)  # the step graph is captured here, with the one-cell kernel
+    monkeypatch.delenv("WL_STAGE_V1")
+    assert np.array_equal(a.get(0), b.get(0))
+    assert np.array_equal(a.get(1), b.get(1))
+
+
 @pytest.mark.parametrize("case", [CASES_3D[0], CASES_3D[1], CASES_3D[2], CASES_3D[4], CASES_3D[5], CASES_2D[0],
                                   CASES_2D[2], CASES_2D[3], CASES_2D[4]], ids=lambda c: c["id"])
 def test_uniform_tiles_match_loading_kernels(case, monkeypatch):
