@@ -118,6 +118,9 @@ typedef struct {
                             magnitudes up to 65504).  The fine-level residual, the pressure and the
                             FP64 coarsest solve are unchanged, so the V-cycles converge to the same
                             tolerance (iterative refinement); only their count may change. */
+  int metrics;           /* 1: every step also records the kinetic energy and max |div u| of the velocity at
+                            its end and the pressure force (three reductions added to the step; see
+                            wl_get_metrics); 0 (default): only the scalars every step records anyway */
 } wl_opts;
 
 #define WL_COARSE_FP32 0
@@ -212,6 +215,58 @@ int wl_set_field(wl_handle h, int which, const void* src, int src_is_device);
 int wl_get_dt(wl_handle h, double* dt);
 int wl_set_dt(wl_handle h, double dt);
 int wl_get_time(wl_handle h, double* t, long long* steps);
+
+/* ---- Checkpoint / resume.  Long runs (and the segment recomputation of a differentiated
+ * rollout, Section 1) need to stop and continue a simulation exactly; the paper has no
+ * counterpart.  A saved state holds everything a step reads from the steps before it: the
+ * velocity (with the exit plane of a convective exit), the fine pressure (both words of
+ * the double-float pair at precision 1, which is the next projection's initial guess), dt,
+ * the clock, the step count and the V-cycle bookkeeping.  Layout: a header (magic
+ * "WLSTATE1", format version, grid, periodic mask, precision, exit option, nu, U, sizes)
+ * followed by those fields, in host or device memory as the caller chooses; the caller
+ * owns the buffer.  Loading it into a sim created with the same dims, nu, U, body,
+ * periodic mask, precision and exit option makes every later step bit-identical to the
+ * run that saved it (the body and the multigrid options are not recorded: they must
+ * match too).  Both calls synchronise the sim's stream. */
+
+/* Bytes of a saved state of this sim (0 for a null handle). */
+size_t wl_state_bytes(wl_handle h);
+/* Write the state into dst (dst_bytes >= wl_state_bytes; host or device per
+ * dst_is_device).  WL_EINVAL for a null pointer or a short buffer. */
+int wl_save(wl_handle h, void* dst, size_t dst_bytes, int dst_is_device);
+/* Restore a state written by wl_save.  WL_EINVAL (and nothing changed) when the header
+ * is not a saved state, belongs to a different setup (grid, periodic mask, precision,
+ * exit option, nu, U) or src_bytes is short.  Clears a poisoned flag. */
+int wl_load(wl_handle h, const void* src, size_t src_bytes, int src_is_device);
+
+/* ---- Per-step metrics.  Every step appends one record of WL_METRIC_FIELDS doubles to a
+ * device ring of the last WL_METRIC_RING steps, written on the device at the step's end
+ * (no host round trip, inside the step graph): the step number, the time after it and
+ * the dt it used, the V-cycles and final residual (||div u - A x||_inf, x = p w dt units)
+ * of both projections (Section 2: project!), the CFL out-flux maximum of its end velocity
+ * (the dt rule's numerator, Table 2: CFL!); with wl_opts.metrics also the kinetic energy
+ * 0.5 sum_c sum_I u_c[I]^2 / n_cells, max |div u| and the pressure force F_d of wl_forces
+ * (D values), each summed in FP64 in a fixed order; fields not measured are NaN.  The
+ * paper times only these routines; it has no counterpart for the record itself. */
+#define WL_METRIC_RING 1024
+#define WL_METRIC_FIELDS 13
+#define WL_METRIC_STEP 0
+#define WL_METRIC_TIME 1
+#define WL_METRIC_DT 2
+#define WL_METRIC_VCYCLES1 3
+#define WL_METRIC_VCYCLES2 4
+#define WL_METRIC_RESID1 5
+#define WL_METRIC_RESID2 6
+#define WL_METRIC_CFL 7
+#define WL_METRIC_KE 8
+#define WL_METRIC_MAXDIV 9
+#define WL_METRIC_FORCE 10 /* 10, 11, 12: F_0, F_1, F_2 */
+
+/* Copy the last min(max_records, steps recorded, WL_METRIC_RING) records, oldest first,
+ * into out (host, max_records x WL_METRIC_FIELDS doubles); *n_out (may be NULL) receives
+ * their number.  Synchronises.  WL_EINVAL for a null handle, a negative count or a null
+ * out with max_records > 0. */
+int wl_get_metrics(wl_handle h, double* out, int max_records, int* n_out);
 
 /* Device-recorded status: V-cycles used by the two projections of the last step, the
  * total V-cycles since wl_create (cumulative: difference two calls to count an

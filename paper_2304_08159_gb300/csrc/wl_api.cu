@@ -54,6 +54,7 @@ struct LevelBuf {
 constexpr int kMaxLevels = 16;
 constexpr long long kTailCells = 4096;  // largest hierarchy tail (cells) run by k_vcycle_tail
 constexpr int kForceParts = 1024;
+constexpr int kMetricRing = WL_METRIC_RING;
 
 }  // namespace
 
@@ -76,6 +77,8 @@ struct wl_sim {
   double* cg_work = nullptr;
   double* fpart = nullptr;
   double* fout = nullptr;
+  double* mring = nullptr;    // per-step metric records (kMetricRing x NMETRIC doubles)
+  double* mforce = nullptr;   // the pressure force of the step's metrics
   float* ph = nullptr;        // precision 1: fine-level pressure as the double-float ph + pl
   float* pl = nullptr;
   CUtensorMap srf{};          // TMA descriptor of rf (sweep box)
@@ -259,6 +262,8 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, int cprec, int e
   void* cg = cv.take(sizeof(double) * 5 * ncoarse);
   void* fp = cv.take(sizeof(double) * 2 * kForceParts);
   void* fo = cv.take(sizeof(double) * 4);
+  void* mr = cv.take(sizeof(double) * NMETRIC * kMetricRing);
+  void* mf = cv.take(sizeof(double) * 4);
   void* ph = precision == 1 ? cv.take(sizeof(float) * nc) : nullptr;
   void* pl = precision == 1 ? cv.take(sizeof(float) * nc) : nullptr;
   void* rf = precision == 1 ? cv.take(sizeof(float) * nc) : nullptr;
@@ -268,6 +273,8 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, int cprec, int e
     s->cg_work = (double*)cg;
     s->fpart = (double*)fp;
     s->fout = (double*)fo;
+    s->mring = (double*)mr;
+    s->mforce = (double*)mf;
     s->ph = (float*)ph;
     s->pl = (float*)pl;
     s->rf = (float*)rf;
@@ -594,6 +601,25 @@ void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int 
                     cudaMemcpyDeviceToDevice, st);
 }
 
+// End of a step: with wl_opts.metrics the end-of-step velocity's kinetic energy and
+// max |div u| and the pressure force go into the step's metric record; then the clock,
+// the record and the next dt.
+void enq_step_end(wl_sim* s, cudaStream_t st) {
+  if (s->o.metrics) {
+    const float* u[3] = {s->ua[0], s->ua[1], s->ua[2]};
+    PROF(s, st, WL_KCLASS_CONTROL, launch_metrics_u(s->D, s->g, u, s->ds, s->fpart, kForceParts, st));
+    if (s->body.kind != 0) {
+      const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
+      PROF(s, st, WL_KCLASS_CONTROL,
+           launch_forces(s->D, s->g, s->body, s->ph ? s->ph : s->lev[0].x, s->pl, L, s->fpart, kForceParts,
+                         s->mforce, st));
+    }
+  }
+  PROF(s, st, WL_KCLASS_CONTROL,
+       launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->mring, kMetricRing,
+                       s->o.metrics ? s->mforce : nullptr, st));
+}
+
 int sync_state(wl_sim* s) {
   WL_CUDA(s, cudaMemcpyAsync(s->hs, s->ds, sizeof(DevState), cudaMemcpyDeviceToHost, s->st));
   WL_CUDA(s, cudaStreamSynchronize(s->st));
@@ -643,7 +669,7 @@ int host_step(wl_sim* s, float* rec = nullptr) {
   if (rc) return rc;
   if (rec) copy_pressure(s, rec + (2 * D + 1) * n, s->st);
   enq_correct(s, s->ub, s->ua, 0.5f, 1, s->st);
-  PROF(s, s->st, WL_KCLASS_CONTROL, launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->st));
+  enq_step_end(s, s->st);
   return cuda_check(s, cudaGetLastError(), "step launch");
 }
 
@@ -703,7 +729,7 @@ int build_step_graph(wl_sim* s) {
   // segment 3: correction with the CFL maximum, step end
   WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w2, nullptr, 1, cudaStreamCaptureModeThreadLocal));
   enq_correct(s, s->ub, s->ua, 0.5f, 1, s->cs);
-  launch_step_end(s->ds, s->D, s->nu, s->o.dt_cap, s->o.dt_fixed, s->cs);
+  enq_step_end(s, s->cs);
   WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
   WL_CUDA(s, cudaGraphInstantiate(&s->exec, g, 0));
   s->graph = g;
@@ -786,7 +812,7 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   if (opts) o = *opts;
   if (!(o.tol > 0.0) || o.max_vcycles < 0 || o.post < 1 || !(o.eps > 0.0) || !(o.dt_cap > 0.0) ||
       o.precision < 0 || o.precision > 1 || o.coarse_precision < 0 || o.coarse_precision > 2 || o.exit_bc < 0 ||
-      o.exit_bc > 1)
+      o.exit_bc > 1 || o.metrics < 0 || o.metrics > 1)
     return WL_EINVAL;
   if (o.exit_bc && ((o.periodic_mask & 1u) || !(U[0] > 0.0))) return WL_EINVAL;  // exit: x walls, outflow
   if (body && (body->kind < 0 || body->kind > 3 || (body->kind == 2 && ndim != 3) ||
@@ -1801,5 +1827,25 @@ extern "C" int wl_load(wl_handle s, const void* src, size_t src_bytes, int src_i
   WL_CUDA(s, cudaMemcpyAsync(s->ds, p, sizeof(DevState), x2d, s->st));
   WL_CUDA(s, cudaStreamSynchronize(s->st));
   s->poisoned = false;
+  return WL_OK;
+}
+
+// --------------------------------------------------------------- per-step metrics
+extern "C" int wl_get_metrics(wl_handle s, double* out, int max_records, int* n_out) {
+  if (!s || (!out && max_records > 0) || max_records < 0) return WL_EINVAL;
+  int rc = sync_state(s);
+  if (rc) return rc;
+  const long long total = s->hs->mcount;
+  const long long have = total < kMetricRing ? total : kMetricRing;
+  const long long n = have < max_records ? have : max_records;
+  std::vector<double> ring((size_t)NMETRIC * kMetricRing);
+  WL_CUDA(s, cudaMemcpyAsync(ring.data(), s->mring, sizeof(double) * ring.size(), cudaMemcpyDeviceToHost, s->st));
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  // the last n records, oldest first: ring slots (total - n) .. (total - 1) mod kMetricRing
+  for (long long r = 0; r < n; ++r) {
+    const long long slot = (total - n + r) % kMetricRing;
+    std::memcpy(out + r * NMETRIC, ring.data() + slot * NMETRIC, sizeof(double) * NMETRIC);
+  }
+  if (n_out) *n_out = (int)n;
   return WL_OK;
 }

@@ -254,6 +254,10 @@ struct DevState {
   int cs_used;            // 16-bit coarse levels: their values carry the factor 2^cs_used, set
                           // from the max-norm of the residual they correct (so that FP16's range
                           // holds the correction whatever the residual's size)
+  long long mcount;       // per-step metric records written (the ring holds the last WL_METRIC_RING)
+  double ke;              // metrics of the velocity at the end of the step (wl_opts.metrics = 1):
+  unsigned maxdiv_bits;   //   kinetic energy, max |div u| (float bits)
+  int pad_;
 };
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned* addr, float v) {

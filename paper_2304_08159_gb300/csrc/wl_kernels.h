@@ -268,7 +268,16 @@ int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s);
 int launch_correct(int D, const CorrArgs& a, cudaStream_t s);
 int launch_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, int first, int proj, float w,
                   double tol, int maxit, cudaStream_t s);
-int launch_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s);
+// End of a step: advance the clock, record the step's metrics in the ring (NMETRIC doubles
+// per record, `cap` records; F: the metric force, or null when metrics are off), set the
+// next dt from the CFL maximum.
+constexpr int NMETRIC = 13;
+int launch_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, double* ring, int cap,
+                    const double* F, cudaStream_t s);
+// Kinetic energy 0.5 sum_c sum_I u_c[I]^2 / n and max |div u| of velocity u into st->ke and
+// st->maxdiv_bits: per-block FP64 partials (npart blocks) summed in a fixed order.
+int launch_metrics_u(int D, const Grid& g, const float* const* u, DevState* st, double* partials, int npart,
+                     cudaStream_t s);
 int launch_measure(int D, const Grid& g, const Body& b, float* const* L, cudaStream_t s);
 int launch_coarsen(int D, const Grid& fine, const float* const* Lf, const Grid& coarse, float* const* Lc,
                    cudaStream_t s);

@@ -295,7 +295,8 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
   const float nu = a.nu;
   const bool box_tile = a.fbox && i0 < a.blo[0] + a.bn[0] && i0 + S3_TX > a.blo[0] && j0 < a.blo[1] + a.bn[1] &&
                         j0 + S3_TY > a.blo[1] && k0 < a.blo[2] + a.bn[2] && k1 > a.blo[2];
-  auto soff = [](int c, int sl) { return (c * NP + sl) * PL; };
+  // ring slot sl holds one plane of the three components: component c at (3 sl + c) PL
+  auto soff = [](int c, int sl) { return (3 * sl + c) * PL; };
   auto ld2 = [&](int o) { return *reinterpret_cast<const float2*>(s_u + o); };
 
   // plane fetch: pair e = tid, tid + 256 of each component's 34 x 12 pairs
@@ -343,8 +344,8 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
   auto mid2 = [](float2 A, float2 B) { return make_float2(A.y, B.x); };
 
   // lower x-face fluxes of the two cells, component C, plane slot S (plane k), SM (k-1)
-  auto flux_x = [&](auto C, auto S, auto SM) -> float2 {
-    constexpr int c = decltype(C)::value, sl = decltype(S)::value, sm = decltype(SM)::value;
+  auto flux_x = [&](auto C, int sl, int sm) -> float2 {
+    constexpr int c = decltype(C)::value;
     const int o = soff(c, sl) + own;
     const float2 A = ld2(o - 2), B = ld2(o), Cn = ld2(o + 2);
     float2 a2;
@@ -356,8 +357,8 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
     }
     return mom_flux2<ADV>(A, mid2(A, B), B, mid2(B, Cn), a2, nu);
   };
-  auto flux_y = [&](auto C, auto S, auto SM) -> float2 {
-    constexpr int c = decltype(C)::value, sl = decltype(S)::value, sm = decltype(SM)::value;
+  auto flux_y = [&](auto C, int sl, int sm) -> float2 {
+    constexpr int c = decltype(C)::value;
     const int o = soff(c, sl) + own;
     const int oy = soff(1, sl) + own;
     const float2 Y0 = ld2(oy);
@@ -371,9 +372,8 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
     return mom_flux2<ADV>(ld2(o - 2 * HX), ld2(o - HX), ld2(o), ld2(o + HX), a2, nu);
   };
   // lower z-face flux at plane kf, planes kf-2 .. kf+1 in slots Q0 .. Q3
-  auto flux_z = [&](auto C, auto Q0, auto Q1, auto Q2, auto Q3) -> float2 {
-    constexpr int c = decltype(C)::value, q0 = decltype(Q0)::value, q1 = decltype(Q1)::value,
-                  q2 = decltype(Q2)::value, q3 = decltype(Q3)::value;
+  auto flux_z = [&](auto C, int q0, int q1, int q2, int q3) -> float2 {
+    constexpr int c = decltype(C)::value;
     const int oz = soff(2, q2) + own;
     const float2 Z0 = ld2(oz);
     float2 a2;
@@ -397,8 +397,8 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
     s_fxe[c][row] = mom_flux(U[-2], U[-1], U[0], U[1], A[0] + other, nu, ADV);
   };
   // warps 1..3: the fluxes through the upper y edge (row 8) of component warp-1
-  auto edge_y = [&](auto C, auto S, auto SM) {
-    constexpr int c = decltype(C)::value, sl = decltype(S)::value, sm = decltype(SM)::value;
+  auto edge_y = [&](auto C, int sl, int sm) {
+    constexpr int c = decltype(C)::value;
     const int p8 = (S3_TY + 2) * HX + 2 * lane + 2;
     const int o = soff(c, sl) + p8, oy = soff(1, sl) + p8;
     const float2 Y0 = ld2(oy);
@@ -422,17 +422,17 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
   }
   fetch(k0 + 2);
   __syncthreads();
-  fzl[0] = flux_z(IC<0>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{});
-  fzl[1] = flux_z(IC<1>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{});
-  fzl[2] = flux_z(IC<2>{}, IC<0>{}, IC<1>{}, IC<2>{}, IC<3>{});
+  fzl[0] = flux_z(IC<0>{}, 0, 1, 2, 3);
+  fzl[1] = flux_z(IC<1>{}, 0, 1, 2, 3);
+  fzl[2] = flux_z(IC<2>{}, 0, 1, 2, 3);
   __syncthreads();
 
-  // plane k, with k - k0 = PH (mod NP): plane k+t sits in slot (PH + t + 2) mod NP
-  auto step = [&](auto PHc, int k) {
-    constexpr int PH = decltype(PHc)::value;
-    constexpr int S0 = (PH + 2) % NP, SM1 = (PH + 1) % NP, SP1 = (PH + 3) % NP, SP2 = PH % NP;
-    using I0 = IC<S0>;
-    using Im = IC<SM1>;
+  // plane k: plane k+t sits in slot (k - k0 + t + 2) mod NP (run-time slots keep the
+  // loop body a single copy: unrolled by the ring length it overflowed the instruction
+  // cache)
+  auto step = [&](int k) {
+    const int PH = (k - k0) & (NP - 1);
+    const int S0 = (PH + 2) & (NP - 1), SM1 = (PH + 1) & (NP - 1), SP1 = (PH + 3) & (NP - 1), SP2 = PH;
     commit(SP2);  // plane k+2 into the slot of plane k-2
     __syncthreads();
     if (k + 3 <= k1 + 1) fetch(k + 3);
@@ -445,24 +445,24 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
                                           : make_float2(0.f, 0.f);
     }
     float2 fx[3], fzu[3];
-    fx[0] = flux_x(IC<0>{}, I0{}, Im{});
-    fx[1] = flux_x(IC<1>{}, I0{}, Im{});
-    fx[2] = flux_x(IC<2>{}, I0{}, Im{});
-    *reinterpret_cast<float2*>(&s_fy[0][ty][2 * lane]) = flux_y(IC<0>{}, I0{}, Im{});
-    *reinterpret_cast<float2*>(&s_fy[1][ty][2 * lane]) = flux_y(IC<1>{}, I0{}, Im{});
-    *reinterpret_cast<float2*>(&s_fy[2][ty][2 * lane]) = flux_y(IC<2>{}, I0{}, Im{});
+    fx[0] = flux_x(IC<0>{}, S0, SM1);
+    fx[1] = flux_x(IC<1>{}, S0, SM1);
+    fx[2] = flux_x(IC<2>{}, S0, SM1);
+    *reinterpret_cast<float2*>(&s_fy[0][ty][2 * lane]) = flux_y(IC<0>{}, S0, SM1);
+    *reinterpret_cast<float2*>(&s_fy[1][ty][2 * lane]) = flux_y(IC<1>{}, S0, SM1);
+    *reinterpret_cast<float2*>(&s_fy[2][ty][2 * lane]) = flux_y(IC<2>{}, S0, SM1);
     // face k+1: planes k-1 .. k+2
-    fzu[0] = flux_z(IC<0>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{});
-    fzu[1] = flux_z(IC<1>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{});
-    fzu[2] = flux_z(IC<2>{}, Im{}, I0{}, IC<SP1>{}, IC<SP2>{});
+    fzu[0] = flux_z(IC<0>{}, SM1, S0, SP1, SP2);
+    fzu[1] = flux_z(IC<1>{}, SM1, S0, SP1, SP2);
+    fzu[2] = flux_z(IC<2>{}, SM1, S0, SP1, SP2);
     if (ty == 0) {
       if (lane < 24) edge_x(S0, SM1);
     } else if (ty == 1) {
-      edge_y(IC<0>{}, I0{}, Im{});
+      edge_y(IC<0>{}, S0, SM1);
     } else if (ty == 2) {
-      edge_y(IC<1>{}, I0{}, Im{});
+      edge_y(IC<1>{}, S0, SM1);
     } else if (ty == 3) {
-      edge_y(IC<2>{}, I0{}, Im{});
+      edge_y(IC<2>{}, S0, SM1);
     }
     __syncthreads();
     float nxt[3];  // lower x flux of lane l+1's first cell (every lane takes part)
@@ -504,12 +504,7 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) fzl[c] = fzu[c];
   };
-  for (int kb = k0; kb < k1; kb += NP) {
-    step(IC<0>{}, kb);
-    if (kb + 1 < k1) step(IC<1>{}, kb + 1);
-    if (kb + 2 < k1) step(IC<2>{}, kb + 2);
-    if (kb + 3 < k1) step(IC<3>{}, kb + 3);
-  }
+  for (int k = k0; k < k1; ++k) step(k);
 }
 
 // mu1 term of BDIM over the body's bounding box: out_c[I] += s * sum_j mu1_j (f[I+e_j]

@@ -1060,11 +1060,30 @@ int launch_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, in
 // End of a step: advance the clock and take the next dt from the CFL maximum
 // (dt = min(dt_cap, 1/(max out-flux + 2 D nu)), CFL! of Table 2), or keep dt fixed.
 // advance = 0: only set dt (initial condition).
-__global__ void k_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, int advance) {
+__global__ void k_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, int advance,
+                           double* ring, int cap, const double* F) {
   const double used = st->dt;
   if (advance) {
     st->time += used;
     st->steps += 1;
+    if (ring && cap > 0) {
+      // the step's record: step, time, dt, V-cycles and final residuals of both
+      // projections, CFL out-flux maximum, then (metrics on) KE, max |div u|, force
+      double* r = ring + (size_t)(st->mcount % cap) * NMETRIC;
+      const double nan = __longlong_as_double(0x7ff8000000000000ll);
+      r[0] = (double)st->steps;
+      r[1] = st->time;
+      r[2] = used;
+      r[3] = st->last_iters[0];
+      r[4] = st->last_iters[1];
+      r[5] = st->last_res[0];
+      r[6] = st->last_res[1];
+      r[7] = (double)__uint_as_float(st->cfl_bits);
+      r[8] = F ? st->ke : nan;
+      r[9] = F ? (double)__uint_as_float(st->maxdiv_bits) : nan;
+      for (int d = 0; d < 3; ++d) r[10 + d] = (F && d < D) ? F[d] : nan;
+      st->mcount += 1;
+    }
   }
   double dn;
   if (dt_fixed > 0.0) {
@@ -1094,13 +1113,100 @@ int launch_sync_dt(DevState* st, cudaStream_t s) {
   return 0;
 }
 
-int launch_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s) {
-  k_step_end<<<1, 1, 0, s>>>(st, D, nu, dt_cap, dt_fixed, 1);
+int launch_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, double* ring, int cap,
+                    const double* F, cudaStream_t s) {
+  k_step_end<<<1, 1, 0, s>>>(st, D, nu, dt_cap, dt_fixed, 1, ring, cap, F);
   return 0;
 }
 
 int launch_set_dt_from_cfl(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s) {
-  k_step_end<<<1, 1, 0, s>>>(st, D, nu, dt_cap, dt_fixed, 0);
+  k_step_end<<<1, 1, 0, s>>>(st, D, nu, dt_cap, dt_fixed, 0, nullptr, 0, nullptr);
+  return 0;
+}
+
+// Metrics of a velocity: per block the FP64 sum of u_c^2 over its cells (grid-stride, a
+// fixed pattern, then a fixed-order block sum) and the running max |div u| (atomic max of
+// float bits: order-free).  div u = sum_c u_c[I+e_c] - u_c[I], the upper face of a
+// non-periodic side being U_c (the stored exit plane for x with a convective exit).
+template <int D>
+__global__ void __launch_bounds__(256) k_metrics_u(Grid g, const float* u0, const float* u1, const float* u2,
+                                                    DevState* st, double* partials) {
+  __shared__ double sh[8];
+  __shared__ unsigned sm[8];
+  const float* u[3] = {u0, u1, u2};
+  const long long st2[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
+  double e = 0.0;
+  unsigned mx = 0u;
+  for (long long q = (long long)blockIdx.x * 256 + threadIdx.x; q < g.nc; q += (long long)gridDim.x * 256) {
+    int I[3];
+    I[0] = (int)(q % g.n[0]);
+    const long long t = q / g.n[0];
+    I[1] = (int)(t % g.n[1]);
+    I[2] = (int)(t / g.n[1]);
+    float div = 0.f;
+#pragma unroll
+    for (int c = 0; c < D; ++c) {
+      const float v = u[c][q];
+      e += (double)v * (double)v;
+      float up;
+      if (I[c] + 1 < g.n[c])
+        up = u[c][q + st2[c]];
+      else if (is_per(g, c))
+        up = u[c][q - (long long)(g.n[c] - 1) * st2[c]];
+      else if (c == 0 && g.exit)
+        up = u[0][exit_index(g, I[1], I[2])];
+      else
+        up = g.U[c];
+      div += up - v;
+    }
+    mx = max(mx, __float_as_uint(fabsf(div)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    sh[threadIdx.x >> 5] = e;
+    sm[threadIdx.x >> 5] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    unsigned m = 0u;
+    for (int w = 0; w < 8; ++w) {
+      a += sh[w];
+      m = max(m, sm[w]);
+    }
+    partials[blockIdx.x] = a;
+    atomicMax(&st->maxdiv_bits, m);
+  }
+}
+
+// sum of the npart partials in a fixed order (strided per thread, then a fixed tree)
+__global__ void __launch_bounds__(256) k_metrics_final(DevState* st, const double* partials, int npart, double inv_n) {
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < npart; b += 256) a += partials[b];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) st->ke = 0.5 * sh[0] * inv_n;
+}
+
+__global__ void k_clear_maxdiv(DevState* st) { st->maxdiv_bits = 0u; }
+
+int launch_metrics_u(int D, const Grid& g, const float* const* u, DevState* st, double* partials, int npart,
+                     cudaStream_t s) {
+  k_clear_maxdiv<<<1, 1, 0, s>>>(st);
+  if (D == 3)
+    k_metrics_u<3><<<npart, 256, 0, s>>>(g, u[0], u[1], u[2], st, partials);
+  else
+    k_metrics_u<2><<<npart, 256, 0, s>>>(g, u[0], u[1], u[1], st, partials);
+  k_metrics_final<<<1, 256, 0, s>>>(st, partials, npart, 1.0 / (double)g.nc);
   return 0;
 }
 

@@ -51,7 +51,10 @@ EXPORTS = (
     "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_graph_kernels", "wl_levels", "wl_level_dims",
     "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
     "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split",
+    "wl_state_bytes", "wl_save", "wl_load", "wl_get_metrics",
 )
+METRIC_RING, METRIC_FIELDS = 1024, 13
+METRICS = ("step", "time", "dt", "vcycles1", "vcycles2", "resid1", "resid2", "cfl", "ke", "maxdiv", "F0", "F1", "F2")
 KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coarse", "coarsest", "correct",
             "control")
 
@@ -67,7 +70,8 @@ class WlOpts(ctypes.Structure):
                 ("eps", ctypes.c_double), ("dt_cap", ctypes.c_double), ("dt_fixed", ctypes.c_double),
                 ("periodic_mask", ctypes.c_uint), ("advect", ctypes.c_int), ("precision", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("stream", ctypes.c_void_p), ("workspace", ctypes.c_void_p),
-                ("workspace_bytes", ctypes.c_size_t), ("exit_bc", ctypes.c_int), ("coarse_precision", ctypes.c_int)]
+                ("workspace_bytes", ctypes.c_size_t), ("exit_bc", ctypes.c_int), ("coarse_precision", ctypes.c_int),
+                ("metrics", ctypes.c_int)]
 
 
 class WLError(RuntimeError):
@@ -120,6 +124,10 @@ def load(path: str = LIB_PATH):
         "wl_grad_forward": (I, [H, I, I, P, ctypes.c_size_t, DP]),
         "wl_grad_backward": (I, [H, DP, DP]),
         "wl_level_split": (I, [H, I, IP, DP]),
+        "wl_state_bytes": (ctypes.c_size_t, [H]),
+        "wl_get_metrics": (I, [H, DP, I, IP]),
+        "wl_save": (I, [H, P, ctypes.c_size_t, I]),
+        "wl_load": (I, [H, P, ctypes.c_size_t, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -287,6 +295,26 @@ def make_body(body) -> WlBody:
     return b
 
 
+def wl_state_bytes(h) -> int:
+    return int(load().wl_state_bytes(h))
+
+
+def wl_save(h, dst_ptr, nbytes, dst_is_device):
+    return load().wl_save(h, dst_ptr, int(nbytes), int(dst_is_device))
+
+
+def wl_load(h, src_ptr, nbytes, src_is_device):
+    return load().wl_load(h, src_ptr, int(nbytes), int(src_is_device))
+
+
+def wl_get_metrics(h, max_records=METRIC_RING):
+    out = np.zeros((max(int(max_records), 0), METRIC_FIELDS))
+    n = ctypes.c_int(0)
+    rc = load().wl_get_metrics(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(max_records),
+                               ctypes.byref(n))
+    return rc, out[: n.value]
+
+
 def wl_last_error(h) -> str:
     s = load().wl_last_error(h)
     return s.decode() if s else ""
@@ -300,7 +328,7 @@ class Sim:
 
     def __init__(self, dims, nu, U, body=None, periodic=0, tol=1e-6, max_vcycles=32, post=4, eps=1.0,
                  dt_cap=10.0, dt_fixed=0.0, advect=True, precision=1, use_graph=True, device=None,
-                 coarse_precision=0, exit_bc=False):
+                 coarse_precision=0, exit_bc=False, metrics=False):
         import torch
 
         self.torch = torch
@@ -315,6 +343,7 @@ class Sim:
         o.advect, o.precision, o.use_graph = int(bool(advect)), int(precision), int(bool(use_graph))
         o.coarse_precision = COARSE_PRECISION.get(coarse_precision, coarse_precision)
         o.exit_bc = int(bool(exit_bc))
+        o.metrics = int(bool(metrics))
         with torch.cuda.device(self.device):
             o.stream = torch.cuda.current_stream().cuda_stream
             nbytes = wl_workspace_bytes(self.dims, o)
@@ -391,6 +420,32 @@ class Sim:
 
     def step(self, n=1):
         return self._check(wl_step(self.h, n), "wl_step")
+
+    def metrics(self, max_records=METRIC_RING):
+        """The last per-step metric records (wl_get_metrics), oldest first, as a dict of
+        numpy arrays keyed by METRICS."""
+        rc, rec = wl_get_metrics(self.h, max_records)
+        self._check(rc, "wl_get_metrics")
+        return {k: rec[:, i] for i, k in enumerate(METRICS)}
+
+    def save(self, device=False):
+        """The sim's state (wl_save) as a uint8 numpy array, or a uint8 tensor on its
+        device when device=True."""
+        n = wl_state_bytes(self.h)
+        if device:
+            buf = self.torch.empty(n, dtype=self.torch.uint8, device=self.device)
+            self._check(wl_save(self.h, buf.data_ptr(), n, 1), "wl_save")
+        else:
+            buf = np.empty(n, dtype=np.uint8)
+            self._check(wl_save(self.h, buf.ctypes.data, n, 0), "wl_save")
+        return buf
+
+    def load(self, buf):
+        """Restore a state saved by save() (host array or device tensor)."""
+        if isinstance(buf, np.ndarray):
+            a = np.ascontiguousarray(buf, dtype=np.uint8)
+            return self._check(wl_load(self.h, a.ctypes.data, a.nbytes, 0), "wl_load")
+        return self._check(wl_load(self.h, buf.data_ptr(), buf.numel() * buf.element_size(), 1), "wl_load")
 
     def stage(self, stage):
         return self._check(wl_stage(self.h, stage), "wl_stage")
