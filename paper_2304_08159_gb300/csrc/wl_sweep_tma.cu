@@ -364,11 +364,11 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     }
     return (dg > 0.f) ? __fdividef(sum - lds(P.z + e), dg) : 0.f;
   };
-  // UNI tile that touches no wall (every cell it relaxes, halo included, has all its
-  // faces): each coefficient is uv, so the relaxation is the same FMA chain with uv
-  // and the diagonal the constant 2D uv (the same bits as relax_uni)
-  const bool interior = UNI && i0 >= 4 && i0 + TX + 4 <= g.n[0] && j0 >= 2 && j0 + TY + 2 <= g.n[1] &&
-                        (D == 2 || (k0 >= 2 && k1 + 2 <= g.n[2]));
+  // UNI tile whose x/y footprint touches no wall: on a plane with both z faces
+  // (zfull) every cell it relaxes, halo included, has all its faces, each coefficient is
+  // uv, so the relaxation is the same FMA chain with uv and the diagonal the constant
+  // 2D uv (the same bits as relax_uni)
+  const bool interior = UNI && i0 >= 4 && i0 + TX + 4 <= g.n[0] && j0 >= 2 && j0 + TY + 2 <= g.n[1];
   const float dg_int = D == 3 ? (uv + uv) + (uv + uv) + (uv + uv) : (uv + uv) + (uv + uv);
   auto relax_fast = [&](const Planes& P, uint32_t e) -> float {
     const uint32_t x0 = P.x0 + e;
@@ -461,7 +461,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   // (red 2h+par, black 6+2h+par) is inside the grid with all four x/y faces, so that on
   // a plane with both z faces the task takes relax_fast (same bits)
   uint32_t fast_m = 0u;
-  if (UNI && !interior) {
+  if (UNI) {
 #pragma unroll
     for (int par = 0; par < 2; ++par) {
 #pragma unroll
@@ -478,11 +478,13 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     zhi = kk + 1 < g.n[2] || pz;
     kin = pz || (kk >= 0 && kk < g.n[2]);
   };
+  // plane kk is in the grid with both z faces
+  auto zfull = [&](int kk) { return D == 2 || pz || (kk > 0 && kk + 1 < g.n[2]); };
   // red cells of plane kk (parity par) whose operands are P
   auto red_plane = [&](const Planes& P, int par, int kk) {
     const uint32_t e0 = par ? er[0][1] : er[0][0], e1 = par ? er[1][1] : er[1][0];
     const uint32_t e2 = par ? er[2][1] : er[2][0];
-    if (UNI && interior) {
+    if (UNI && interior && zfull(kk)) {
       const float2 v = relax_fast2(P, e0, e1);
       sts(P.x0 + e0, v.x);
       sts(P.x0 + e1, v.y);
@@ -515,7 +517,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   // black cells of plane kk (parity par) whose operands are P
   auto black_plane = [&](const Planes& P, int par, int kk) {
     const uint32_t e0 = par ? eb[0][1] : eb[0][0], e1 = par ? eb[1][1] : eb[1][0];
-    if (UNI && interior) {
+    if (UNI && interior && zfull(kk)) {
       const float2 v = relax_fast2(P, e0, e1);
       sts(P.x0 + e0, v.x);
       sts(P.x0 + e1, v.y);
