@@ -512,23 +512,32 @@ def adjoint_bench(tol):
             "gradient_workspace_mb": ws / 1e6, "poisson_tol": tol}
 
 
-def serving_bench(n_req, tol):
+def serving_bench(n_req, tol, batch_cells=1 << 18):
     """The serving mix (seeded Poisson stream of 2-D cylinder and 3-D sphere cases of
-    different sizes) served batched (continuous batching, one wl_step_batch per round)
-    and one request at a time on the same GPU; wall time includes admission and
-    simulation setup in both."""
+    different sizes) served batched (continuous batching: one wl_step_batch per round, each
+    resident's own step graph; and one wl_batch_step per round, the residents of at most
+    batch_cells cells in one batched graph per dimension) and one request at a time on the
+    same GPU; wall time includes admission and simulation setup in all three."""
     import numpy as np
     from paper_2304_08159_gb300 import serve
 
     reqs = serve.request_stream(n_req)
     warm = serve.request_stream(2, seed=1)
     serve.serve_gpu(warm, tol=tol)
+    serve.serve_gpu(warm, tol=tol, batch_cells=batch_cells)
     serve.sequential_gpu(warm, tol=tol)
     stats, lat = serve.serve_gpu(reqs, tol=tol)
+    bstats, blat = serve.serve_gpu(reqs, tol=tol, batch_cells=batch_cells)
+    small, large = serve.class_latencies_ms(bstats)
     t_seq, cs_seq, lat_seq = serve.sequential_gpu(reqs, tol=tol)
     occ = [n for n, _, _ in stats["rounds"]]
     b = stats["cells_steps"] / stats["wall_s"]
+    bb = bstats["cells_steps"] / bstats["wall_s"]
     q = cs_seq / t_seq
+    nsmall = sum(1 for r in reqs if r.cells <= batch_cells)
+
+    def pct(v, p):
+        return float(np.percentile(v, p)) if v else None
     return {"requests": n_req, "mix": "seeded Poisson stream (seed 20230417, 2 per round): 2-D cylinder N^2 "
                                       "N 64-512, 3-D sphere N^3 N 32-192, R 4-24, Re 100-1000, 20-200 steps",
             "batched": {"value": b, "unit": "cell*step/s", "wall_s": stats["wall_s"],
@@ -536,6 +545,15 @@ def serving_bench(n_req, tol):
                         "step_latency_ms_p99": float(np.percentile(lat, 99)),
                         "rounds": len(lat), "mean_resident": float(np.mean(occ)), "max_resident": int(max(occ)),
                         "peak_workspace_gb": stats["peak_bytes"] / 1e9},
+            "small_batched": {"batch_cells": batch_cells, "small_requests": nsmall,
+                              "value": bb, "unit": "cell*step/s", "wall_s": bstats["wall_s"],
+                              "step_latency_ms_p50": pct(blat, 50), "step_latency_ms_p99": pct(blat, 99),
+                              "small_step_latency_ms_p50": pct(small, 50), "small_step_latency_ms_p99": pct(small, 99),
+                              "large_step_latency_ms_p50": pct(large, 50), "large_step_latency_ms_p99": pct(large, 99),
+                              "over_sequential": bb / q,
+                              "how": "requests of at most batch_cells cells step together in one batched graph per "
+                                     "dimension (wl_batch_step: every kernel of the step launched once for all of "
+                                     "them over a device descriptor table); the others with their own graphs"},
             "sequential": {"value": q, "unit": "cell*step/s", "wall_s": t_seq,
                            "step_latency_ms_p50": float(np.percentile(lat_seq, 50)),
                            "step_latency_ms_p99": float(np.percentile(lat_seq, 99))},

@@ -165,6 +165,43 @@ int wl_step(wl_handle h, int nsteps);
  * sizes on one device; no counterpart in the paper. */
 int wl_step_batch(const wl_handle* hs, int n, int nsteps, void* stream);
 
+/* ---- Batched steps of many small simulations (serving; no counterpart in the paper,
+ * whose GMG solve is linear in cells, Section 2, so many small grids are as cheap per cell
+ * as one large one once they share launches).  wl_step_batch above launches one step graph
+ * per simulation; for grids of a few thousand to ~10^5 cells each launch of such a graph is
+ * mostly launch latency.  A batch advances all its small simulations together: every kernel
+ * of the step is launched once for all of them, each block of a launch working on one
+ * simulation through a per-simulation descriptor table kept on the device (grid, field
+ * pointers, level sizes and every launch's arguments, built with the same argument
+ * builders as that simulation's own step), and the two projections' V-cycle loops run in
+ * conditional WHILE nodes until every simulation's projection has converged (a converged
+ * one skips the rest of the loop).  Each simulation computes exactly what its own step
+ * computes (the same kernels on the same inputs: the same bits alone and batched).
+ *
+ * A simulation is batched when it has at most max_cells cells and default-like options:
+ * precision 1, FP32 levels, convection on, no convective exit, metrics off, a multigrid
+ * hierarchy that ends in the small-level tail (at most 8 levels above it, at most 8 sweeps
+ * per level) and, in 3-D, an even n_0; up to 64 per dimension (2-D and 3-D batch
+ * separately).  Other simulations step with their own graphs on their own streams, as in
+ * wl_step_batch.  The batch owns its streams, graphs and a device table of 64 slots per
+ * dimension (about 1 MB); it rebuilds a graph when the set of its simulations changes. */
+typedef struct wl_batch_s* wl_batch;
+int wl_batch_create(long long max_cells, wl_batch* out);
+/* Advance the n simulations hs one time step each (the batched ones in one graph per
+ * dimension, the others on their own streams), ordered after the work already queued on
+ * `stream` and before the work queued on it next, and on each simulation's own stream
+ * after its earlier work and before its later work.  small_done (a cudaEvent_t, may be
+ * NULL) is recorded on `stream` once the batched simulations' steps are done, before the
+ * others are joined: it times the small simulations' step latency.  Asynchronous.
+ * Returns the first error; a poisoned simulation is skipped with WL_ENONFINITE. */
+int wl_batch_step(wl_batch b, const wl_handle* hs, int n, void* stream, void* small_done);
+void wl_batch_destroy(wl_batch b);
+const char* wl_batch_last_error(wl_batch b);
+/* Milliseconds between two recorded CUDA events (cudaEvent_t; e.g. a round's start and the
+ * small_done event wl_batch_step recorded), for callers whose event wrappers do not know
+ * the library recorded one of them.  WL_ECUDA if either is not complete. */
+int wl_event_elapsed(void* start, void* end, float* ms);
+
 /* One Heun stage of convdiff! + BDIM! + BC! (Table 2) with the current dt, written
  * to the stage buffer (WL_FIELD_USTAGE): stage 1 maps u0 = WL_FIELD_U to
  * mu0 f + mu1.grad f with f = u0 + dt r(u0); stage 2 maps (u0 = WL_FIELD_U,

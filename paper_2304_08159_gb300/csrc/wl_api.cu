@@ -17,6 +17,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -59,6 +60,7 @@ constexpr int kMetricRing = WL_METRIC_RING;
 }  // namespace
 
 struct wl_sim {
+  unsigned long long uid = 0;  // unique per sim of the process (a batch keys its graphs on it)
   int D = 0;
   Grid g{};
   double nu = 0.0;
@@ -376,6 +378,20 @@ ResArgs res_args(wl_sim* s, int l, int mode) {
   return a;
 }
 
+// arguments of the index-table kernel k_residual for the fine level (mode RES_RESIDUAL,
+// or RES_DIVERGENCE of velocity buffer `ubuf` 0/1/2 = A/B/C with weight w)
+ResArgs fine_res_args(wl_sim* s, int mode, int ubuf, float w) {
+  ResArgs a = res_args(s, 0, mode);
+  float* const* ub[3] = {s->ua, s->ub, s->uc};
+  if (mode == RES_DIVERGENCE)
+    for (int c = 0; c < 3; ++c) a.u[c] = ub[ubuf][c];
+  a.inv_w = 1.f / w;
+  a.ph = s->ph;
+  a.pl = s->pl;
+  a.rout = s->rf;
+  return a;
+}
+
 // fine-level residual (mode RES_RESIDUAL) or divergence + residual (RES_DIVERGENCE,
 // of velocity buffer `ubuf` 0/1/2 = A/B/C), with the restriction and the max-norm
 void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) {
@@ -418,21 +434,48 @@ void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) 
     PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st, side_of(s)));
     return;
   }
-  ResArgs a = res_args(s, 0, mode);
-  float* const* ub[3] = {s->ua, s->ub, s->uc};
-  if (mode == RES_DIVERGENCE)
-    for (int c = 0; c < 3; ++c) a.u[c] = ub[ubuf][c];
-  a.inv_w = 1.f / w;
-  a.ph = s->ph;
-  a.pl = s->pl;
-  a.rout = s->rf;
-  PROF(s, st, WL_KCLASS_RESID_FINE, launch_residual(s->D, a, st));
+  PROF(s, st, WL_KCLASS_RESID_FINE, launch_residual(s->D, fine_res_args(s, mode, ubuf, w), st));
 }
 
 // divergence of u (scaled by 1/(w dt)), first residual, restriction, first decision
 void enq_proj_head(wl_sim* s, int ubuf, float w, int proj, cudaStream_t st, int use_h) {
   enq_fine_residual(s, RES_DIVERGENCE, ubuf, w, st);
   PROF(s, st, WL_KCLASS_CONTROL, launch_decide(s->ds, s->hc[proj], use_h, 1, proj, w, s->o.tol, s->o.max_vcycles, st));
+}
+
+// the index-table kernel's arguments of sweep `it` of level l, as enq_smooth forms them
+// (the same buffers, coarse correction and double-float store)
+SweepArgs smooth_args(wl_sim* s, int l, int it) {
+  LevelBuf& L = s->lev[l];
+  const int P = s->o.post;
+  const bool refine = (l == 0 && s->ph);
+  SweepArgs a{};
+  for (int c = 0; c < 3; ++c) a.L[c] = L.Lk[c];
+  a.z = refine ? s->rf : L.z;
+  a.g = L.g;
+  for (int d = 0; d < 3; ++d) a.cn[d] = s->lev[l + 1].g.n[d];
+  a.stype = L.st;
+  a.xctype = s->lev[l + 1].st;
+  a.zmul = 1.f / L.zs;
+  if (l == 0 && s->lev[1].z32) a.cs = s->ds;
+  a.tz = sweep_planes_per_block(L.g, sweep_table_blocks_per_sm(s->D, L.st));
+  a.uni = (L.band.on && L.band.lo[0] >= L.band.hi[0]) ? 1 : 0;
+  a.uval = L.uval;
+  float* bufs[2] = {L.x, L.x2};
+  const bool from_x = (l == 0 && !refine);
+  int out = from_x ? 1 : ((P % 2 == 1) ? 0 : 1);
+  int in = from_x ? 0 : -1;
+  for (int k = 0; k < it; ++k) {
+    in = out;
+    out ^= 1;
+  }
+  a.x_in = in >= 0 ? bufs[in] : nullptr;
+  a.xc = (it == 0) ? s->lev[l + 1].x : nullptr;
+  a.x_out = bufs[out];
+  a.ph = (refine && it == P - 1) ? s->ph : nullptr;
+  a.pl = (refine && it == P - 1) ? s->pl : nullptr;
+  a.only_wrapping = 0;
+  return a;
 }
 
 // post sweeps on level l with the coarse correction of level l+1 prolonged into the
@@ -536,6 +579,26 @@ void enq_coarsest(wl_sim* s, int l, const float* z, float* x, cudaStream_t st) {
   PROF(s, st, WL_KCLASS_COARSEST, launch_coarse(s->D, a, st));
 }
 
+// the coarse end of a V-cycle (levels tail_lf .. nlev-1) in one block
+TailArgs tail_args(wl_sim* s) {
+  const int lf = s->tail_lf;
+  TailArgs t{};
+  t.nl = s->nlev - lf;
+  for (int l = 0; l < t.nl; ++l) {
+    const LevelBuf& L = s->lev[lf + l];
+    for (int d = 0; d < 3; ++d) t.n[l][d] = L.g.n[d];
+    for (int c = 0; c < 3; ++c) t.L[l][c] = L.Lk[c];
+    t.st[l] = L.st;
+  }
+  t.z = s->lev[lf].z;
+  t.zmul = 1.f / s->lev[lf].zs;
+  t.x = s->lev[lf].x;
+  t.G = s->G;
+  t.post = s->o.post;
+  t.per = s->g.per;
+  return t;
+}
+
 // restriction down the coarse levels, coarsest solve, prolongation + smoothing up to
 // the fine level (whose right-hand side and restricted residual are already set)
 void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
@@ -552,21 +615,7 @@ void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
   if (s->tail_lf > 0) {  // the small levels in one block
     const int lf = s->tail_lf;
     for (int l = 1; l < lf; ++l) PROF(s, st, WL_KCLASS_RESTRICT, launch_residual(s->D, res_args(s, l, RES_RESTRICT), st));
-    TailArgs t{};
-    t.nl = Lv - lf;
-    for (int l = 0; l < t.nl; ++l) {
-      const LevelBuf& L = s->lev[lf + l];
-      for (int d = 0; d < 3; ++d) t.n[l][d] = L.g.n[d];
-      for (int c = 0; c < 3; ++c) t.L[l][c] = L.Lk[c];
-      t.st[l] = L.st;
-    }
-    t.z = s->lev[lf].z;
-    t.zmul = 1.f / s->lev[lf].zs;
-    t.x = s->lev[lf].x;
-    t.G = s->G;
-    t.post = s->o.post;
-    t.per = s->g.per;
-    PROF(s, st, WL_KCLASS_SWEEP_COARSE, launch_vcycle_tail(s->D, t, st));
+    PROF(s, st, WL_KCLASS_SWEEP_COARSE, launch_vcycle_tail(s->D, tail_args(s), st));
     for (int l = lf - 1; l >= 0; --l) enq_smooth(s, l, st);
     return;
   }
@@ -581,7 +630,7 @@ void enq_vcycle(wl_sim* s, float w, int proj, cudaStream_t st, int use_h) {
   PROF(s, st, WL_KCLASS_CONTROL, launch_decide(s->ds, s->hc[proj], use_h, 0, proj, w, s->o.tol, s->o.max_vcycles, st));
 }
 
-void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int cfl, cudaStream_t st) {
+CorrArgs corr_args(wl_sim* s, float* const* uin, float* const* uout, float w, int cfl) {
   CorrArgs a{};
   for (int c = 0; c < 3; ++c) {
     a.u_in[c] = uin[c];
@@ -595,7 +644,11 @@ void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int 
   a.w = w;
   a.cfl = cfl;
   a.st = s->ds;
-  PROF(s, st, WL_KCLASS_CORRECT, launch_correct(s->D, a, st));
+  return a;
+}
+
+void enq_correct(wl_sim* s, float* const* uin, float* const* uout, float w, int cfl, cudaStream_t st) {
+  PROF(s, st, WL_KCLASS_CORRECT, launch_correct(s->D, corr_args(s, uin, uout, w, cfl), st));
   if (s->g.exit && uout[0] != uin[0])  // the exit plane is not corrected: carry it over
     cudaMemcpyAsync(uout[0] + s->g.nc, uin[0] + s->g.nc, sizeof(float) * (size_t)s->g.n[1] * s->g.n[2],
                     cudaMemcpyDeviceToDevice, st);
@@ -819,6 +872,8 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
                (body->kind == 3 && !body->sdf_nodes)))
     return WL_EINVAL;
   wl_sim* s = new wl_sim();
+  static std::atomic<unsigned long long> next_uid{1};
+  s->uid = next_uid.fetch_add(1);
   s->D = ndim;
   s->o = o;
   s->nu = nu;
@@ -1848,4 +1903,314 @@ extern "C" int wl_get_metrics(wl_handle s, double* out, int max_records, int* n_
   }
   if (n_out) *n_out = (int)n;
   return WL_OK;
+}
+
+// --------------------------------------------------------------- batched small simulations
+namespace {
+
+// A simulation goes into a batched launch when it is small and uses the options the
+// batched kernels cover: the double-float pressure, FP32 levels, convection on, no
+// convective exit, no per-step metric reductions, a small-level tail, at most
+// kBatchLevels levels above it and kBatchPost sweeps; 3-D needs an even n_0.
+bool batchable(const wl_sim* s, long long max_cells) {
+  return s && !s->poisoned && s->g.nc <= max_cells && (s->D == 2 || s->D == 3) && s->ph && !s->g.exit &&
+         s->o.coarse_precision == WL_COARSE_FP32 && s->o.advect && !s->o.metrics && s->tail_lf > 0 &&
+         s->tail_lf <= kBatchLevels && s->o.post >= 1 && s->o.post <= kBatchPost &&
+         (s->D == 2 || s->g.n[0] % 2 == 0);
+}
+
+BatchSlot batch_slot(wl_sim* s) {
+  BatchSlot b{};
+  b.ds = s->ds;
+  b.D = s->D;
+  b.stage[0] = stage_args(s, 1);
+  b.stage[1] = stage_args(s, 2);
+  b.body = s->body;
+  int lo[3], hi[3];
+  b.band = (s->body.kind != 0 && stage_band_box(s->D, s->g, s->body, lo, hi)) ? 1 : 0;
+  for (int d = 0; d < 3; ++d) {
+    b.blo[d] = b.band ? lo[d] : 0;
+    b.bn[d] = b.band ? hi[d] - lo[d] : 0;
+  }
+  b.div[0] = fine_res_args(s, RES_DIVERGENCE, 1, 1.f);
+  b.div[1] = fine_res_args(s, RES_DIVERGENCE, 1, 0.5f);
+  b.res = fine_res_args(s, RES_RESIDUAL, 0, 1.f);
+  const int lf = s->tail_lf;
+  b.nrestr = lf - 1;
+  for (int l = 1; l < lf; ++l) b.restr[l] = res_args(s, l, RES_RESTRICT);
+  b.nsmooth = lf;
+  b.post = s->o.post;
+  for (int l = 0; l < lf; ++l)
+    for (int it = 0; it < s->o.post; ++it) b.sweep[l][it] = smooth_args(s, l, it);
+  b.tail = tail_args(s);
+  b.corr[0] = corr_args(s, s->ub, s->uc, 1.f, 0);
+  b.corr[1] = corr_args(s, s->ub, s->ua, 0.5f, 1);
+  b.w[0] = 1.f;
+  b.w[1] = 0.5f;
+  b.tol = s->o.tol;
+  b.maxit = s->o.max_vcycles;
+  b.nu = s->nu;
+  b.dt_cap = s->o.dt_cap;
+  b.dt_fixed = s->o.dt_fixed;
+  b.ring = s->mring;
+  b.ring_cap = kMetricRing;
+  return b;
+}
+
+// a batched launch over the slots listed in `grid` (slot index, that slot's own grid)
+BatchGrid batch_grid(const std::vector<std::pair<int, dim3>>& grid) {
+  BatchGrid bg{};
+  bg.n = (int)grid.size();
+  int b = 0;
+  for (int i = 0; i < bg.n; ++i) {
+    bg.slot[i] = grid[i].first;
+    bg.start[i] = b;
+    bg.gx[i] = grid[i].second.x;
+    bg.gy[i] = grid[i].second.y;
+    b += (int)(grid[i].second.x * grid[i].second.y * grid[i].second.z);
+  }
+  bg.start[bg.n] = b;
+  return bg;
+}
+
+}  // namespace
+
+struct wl_batch_s {
+  long long max_cells = 0;
+  cudaStream_t cs = nullptr;  // capture stream
+  struct Group {
+    std::vector<unsigned long long> key;  // the slots (sim uids) of the current graph, in order
+    BatchSlot* dtab = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle hc[2]{};
+  } grp[2];  // 2-D and 3-D slots
+  std::string err;
+};
+
+namespace {
+
+int batch_fail(wl_batch_s* b, int code, const std::string& msg) {
+  b->err = msg;
+  return code;
+}
+#define WL_BCUDA(b, call)                                                         \
+  do {                                                                            \
+    cudaError_t _e = (call);                                                      \
+    if (_e != cudaSuccess) return batch_fail((b), WL_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// One step of every slot of group G as a graph: the single-simulation step's launch
+// sequence with each launch covering all slots, the two projections' V-cycle loops in
+// conditional WHILE nodes that run while any slot's projection continues (a slot whose
+// projection has converged skips the loop's launches).
+int build_group_graph(wl_batch_s* b, wl_batch_s::Group& G, int D, const std::vector<BatchSlot>& slots) {
+  const int n = (int)slots.size();
+  std::vector<std::pair<int, dim3>> gs, gband[2], gres, gtail, gcorr[2], gall;
+  int maxr = 0, maxs = 0, maxp = 0;
+  size_t tail_smem = 0;
+  for (int i = 0; i < n; ++i) {
+    const BatchSlot& sl = slots[i];
+    gs.push_back({i, stage_grid(D, sl.stage[0].g)});
+    if (sl.band)
+      for (int st = 0; st < 2; ++st) gband[st].push_back({i, band_grid(D, sl.bn)});
+    gres.push_back({i, residual_grid(D, sl.res.g)});
+    gtail.push_back({i, dim3(1, 1, 1)});
+    for (int w = 0; w < 2; ++w) gcorr[w].push_back({i, correct_grid(D, sl.corr[w])});
+    gall.push_back({i, dim3(1, 1, 1)});
+    maxr = std::max(maxr, sl.nrestr);
+    maxs = std::max(maxs, sl.nsmooth);
+    maxp = std::max(maxp, sl.post);
+    tail_smem = std::max(tail_smem, vcycle_tail_smem(D, sl.tail.n, sl.tail.nl));
+  }
+  std::vector<BatchGrid> grestr(maxr + 1), gsweep(maxs);
+  for (int l = 1; l <= maxr; ++l) {
+    std::vector<std::pair<int, dim3>> v;
+    for (int i = 0; i < n; ++i)
+      if (slots[i].nrestr >= l) v.push_back({i, restrict_grid(D, slots[i].restr[l])});
+    grestr[l] = batch_grid(v);
+  }
+  for (int l = 0; l < maxs; ++l) {
+    std::vector<std::pair<int, dim3>> v;
+    for (int i = 0; i < n; ++i)
+      if (slots[i].nsmooth > l) v.push_back({i, sweep_grid(D, slots[i].sweep[l][0])});
+    gsweep[l] = batch_grid(v);
+  }
+  const BatchGrid bs = batch_grid(gs), bres = batch_grid(gres), btail = batch_grid(gtail), ball = batch_grid(gall);
+  const BatchGrid bband[2] = {batch_grid(gband[0]), batch_grid(gband[1])};
+  const BatchGrid bcorr[2] = {batch_grid(gcorr[0]), batch_grid(gcorr[1])};
+  const BatchSlot* t = G.dtab;
+
+  cudaGraph_t g = nullptr;
+  WL_BCUDA(b, cudaGraphCreate(&g, 0));
+  for (int p = 0; p < 2; ++p) WL_BCUDA(b, cudaGraphConditionalHandleCreate(&G.hc[p], g, 0, 0));
+  auto vcycle = [&](int proj) {
+    for (int l = 1; l <= maxr; ++l) launch_batch_restrict(D, t, grestr[l], l, b->cs);
+    launch_batch_tail(D, t, btail, tail_smem, b->cs);
+    for (int l = maxs - 1; l >= 0; --l)
+      for (int it = 0; it < maxp; ++it) launch_batch_sweep(D, t, gsweep[l], l, it, b->cs);
+    launch_batch_residual(D, t, bres, 2, 1, b->cs);
+    launch_batch_decide(t, ball, G.hc[proj], 0, proj, b->cs);
+  };
+  std::vector<cudaGraphNode_t> leaf;
+  cudaGraph_t out = nullptr;
+  cudaGraphNode_t prev = nullptr;
+  for (int proj = 0; proj < 2; ++proj) {
+    WL_BCUDA(b, cudaStreamBeginCaptureToGraph(b->cs, g, prev ? &prev : nullptr, nullptr, prev ? 1 : 0,
+                                              cudaStreamCaptureModeThreadLocal));
+    if (proj == 1) launch_batch_correct(D, t, bcorr[0], 0, b->cs);
+    launch_batch_stage(D, t, bs, proj + 1, b->cs);
+    launch_batch_band(D, t, bband[proj], proj + 1, b->cs);
+    launch_batch_residual(D, t, bres, proj, 0, b->cs);
+    launch_batch_decide(t, ball, G.hc[proj], 1, proj, b->cs);
+    {
+      cudaStreamCaptureStatus cst;
+      const cudaGraphNode_t* deps = nullptr;
+      size_t nd = 0;
+      WL_BCUDA(b, cudaStreamGetCaptureInfo(b->cs, &cst, nullptr, nullptr, &deps, nullptr, &nd));
+      leaf.assign(deps, deps + nd);
+    }
+    WL_BCUDA(b, cudaStreamEndCapture(b->cs, &out));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = G.hc[proj];
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    WL_BCUDA(b, cudaGraphAddNode(&wnode, g, leaf.data(), nullptr, leaf.size(), &cp));
+    WL_BCUDA(b, cudaStreamBeginCaptureToGraph(b->cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+    vcycle(proj);
+    WL_BCUDA(b, cudaStreamEndCapture(b->cs, &out));
+    prev = wnode;
+  }
+  WL_BCUDA(b, cudaStreamBeginCaptureToGraph(b->cs, g, &prev, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  launch_batch_correct(D, t, bcorr[1], 1, b->cs);
+  launch_batch_step_end(t, ball, b->cs);
+  WL_BCUDA(b, cudaStreamEndCapture(b->cs, &out));
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  if (G.graph) cudaGraphDestroy(G.graph);
+  G.exec = nullptr;
+  G.graph = g;
+  WL_BCUDA(b, cudaGraphInstantiate(&G.exec, g, 0));
+  return WL_OK;
+}
+
+}  // namespace
+
+extern "C" int wl_batch_create(long long max_cells, wl_batch* out) {
+  if (!out || max_cells < 0) return WL_EINVAL;
+  *out = nullptr;
+  auto* b = new wl_batch_s();
+  b->max_cells = max_cells;
+  bool ok = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto& G : b->grp) {
+    ok = ok && cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaMalloc(&G.dtab, sizeof(BatchSlot) * kBatchMax) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    wl_batch_destroy(b);
+    return WL_ECUDA;
+  }
+  *out = b;
+  return WL_OK;
+}
+
+extern "C" void wl_batch_destroy(wl_batch b) {
+  if (!b) return;
+  for (auto& G : b->grp) {
+    if (G.st) cudaStreamSynchronize(G.st);
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    if (G.dtab) cudaFree(G.dtab);
+    if (G.done) cudaEventDestroy(G.done);
+    if (G.st) cudaStreamDestroy(G.st);
+  }
+  if (b->cs) cudaStreamDestroy(b->cs);
+  delete b;
+}
+
+extern "C" const char* wl_batch_last_error(wl_batch b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" int wl_batch_step(wl_batch b, const wl_handle* hs, int n, void* stream, void* small_done) {
+  if (!b || (!hs && n > 0) || n < 0) return WL_EINVAL;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaEvent_t fork = nullptr;
+  WL_BCUDA(b, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  WL_BCUDA(b, cudaEventRecord(fork, cs));
+  int first = WL_OK;
+  std::vector<wl_sim*> small[2], large;
+  for (int i = 0; i < n; ++i) {
+    wl_sim* s = hs[i];
+    if (!s) {
+      if (first == WL_OK) first = WL_EINVAL;
+      continue;
+    }
+    if (s->poisoned) {
+      if (first == WL_OK) first = WL_ENONFINITE;
+      continue;
+    }
+    const int gi = s->D - 2;
+    if (batchable(s, b->max_cells) && (int)small[gi].size() < kBatchMax)
+      small[gi].push_back(s);
+    else
+      large.push_back(s);
+  }
+  // the large simulations: each its own step graph on its own stream
+  for (wl_sim* s : large) {
+    int rc = WL_OK;
+    if (cudaStreamWaitEvent(s->st, fork, 0) != cudaSuccess) rc = WL_ECUDA;
+    if (rc == WL_OK && !s->exec) rc = build_step_graph(s);
+    if (rc == WL_OK && cudaGraphLaunch(s->exec, s->st) != cudaSuccess) rc = WL_ECUDA;
+    if (rc == WL_OK && !s->join && cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming) != cudaSuccess)
+      rc = WL_ECUDA;
+    if (rc == WL_OK && cudaEventRecord(s->join, s->st) != cudaSuccess) rc = WL_ECUDA;
+    if (rc != WL_OK) {
+      cudaGetLastError();
+      if (first == WL_OK) first = rc;
+    }
+  }
+  // the small ones: one batched graph per dimension
+  for (int gi = 0; gi < 2; ++gi) {
+    auto& G = b->grp[gi];
+    auto& v = small[gi];
+    if (v.empty()) continue;
+    std::vector<unsigned long long> key;
+    for (wl_sim* s : v) key.push_back(s->uid);
+    if (key != G.key) {
+      std::vector<BatchSlot> slots;
+      for (wl_sim* s : v) slots.push_back(batch_slot(s));
+      WL_BCUDA(b, cudaStreamSynchronize(G.st));  // the previous graph no longer reads the table
+      WL_BCUDA(b, cudaMemcpy(G.dtab, slots.data(), sizeof(BatchSlot) * slots.size(), cudaMemcpyHostToDevice));
+      G.key.clear();
+      int rc = build_group_graph(b, G, gi + 2, slots);
+      if (rc) return rc;
+      G.key = key;
+    }
+    WL_BCUDA(b, cudaStreamWaitEvent(G.st, fork, 0));
+    for (wl_sim* s : v) {  // after the work already queued on each slot's own stream
+      if (!s->join) WL_BCUDA(b, cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
+      WL_BCUDA(b, cudaEventRecord(s->join, s->st));
+      WL_BCUDA(b, cudaStreamWaitEvent(G.st, s->join, 0));
+    }
+    WL_BCUDA(b, cudaGraphLaunch(G.exec, G.st));
+    WL_BCUDA(b, cudaEventRecord(G.done, G.st));
+    for (wl_sim* s : v) WL_BCUDA(b, cudaStreamWaitEvent(s->st, G.done, 0));  // later work on the slot
+    WL_BCUDA(b, cudaStreamWaitEvent(cs, G.done, 0));
+  }
+  if (small_done) WL_BCUDA(b, cudaEventRecord((cudaEvent_t)small_done, cs));
+  for (wl_sim* s : large)
+    if (s->join) cudaStreamWaitEvent(cs, s->join, 0);
+  cudaEventDestroy(fork);
+  if (cudaGetLastError() != cudaSuccess && first == WL_OK) first = WL_ECUDA;
+  return first;
+}
+
+extern "C" int wl_event_elapsed(void* start, void* end, float* ms) {
+  if (!start || !end || !ms) return WL_EINVAL;
+  return cudaEventElapsedTime(ms, (cudaEvent_t)start, (cudaEvent_t)end) == cudaSuccess ? WL_OK : WL_ECUDA;
 }

@@ -331,3 +331,66 @@ namespace wl {
 int launch_set_dt_from_cfl(DevState* st, int D, double nu, double dt_cap, double dt_fixed, cudaStream_t s);
 int launch_fix_bfaces(int D, const Grid& g, float* const* u, cudaStream_t s);
 }  // namespace wl
+
+namespace wl {
+// ---- batched steps of many small simulations (serving): one launch of each kernel of
+// the step covers every simulation of a batch.  Each simulation ("slot") keeps its own
+// fields and device state; its arguments for every launch of its step sit in a device
+// table of BatchSlot, built on the host with the same argument builders as its own
+// step.  Block b of a batched launch belongs to slot bg.slot[s] for bg.start[s] <= b <
+// bg.start[s+1] and takes the block index it would have in that slot's own launch, so
+// every slot runs the same kernel bodies on the same inputs as alone (the same bits).
+constexpr int kBatchMax = 64;      // simulations in one batched launch
+constexpr int kBatchLevels = 8;    // multigrid levels above a slot's small-level tail
+constexpr int kBatchPost = 8;      // sweeps per level
+struct BatchSlot {
+  DevState* ds;
+  int D;
+  StageArgs stage[2];              // stage 1, stage 2
+  Body body;
+  int band;                        // the mu1 band term runs (a body with a band box)
+  int blo[3], bn[3];               // its box
+  ResArgs div[2];                  // divergence of the stage output (w = 1, 1/2)
+  ResArgs res;                     // fine residual of a V-cycle
+  int nrestr;                      // restrictions of levels 1 .. nrestr
+  ResArgs restr[kBatchLevels];
+  int nsmooth;                     // levels 0 .. nsmooth-1 smoothed above the tail
+  int post;                        // sweeps per level
+  SweepArgs sweep[kBatchLevels][kBatchPost];
+  TailArgs tail;
+  CorrArgs corr[2];
+  float w[2];
+  double tol;
+  int maxit;
+  double nu, dt_cap, dt_fixed;
+  double* ring;                    // metric ring (step end) of ring_cap records
+  int ring_cap;
+};
+struct BatchGrid {
+  int n;                           // slots in this launch
+  int slot[kBatchMax];             // their indices in the table
+  int start[kBatchMax + 1];        // first block of each (start[n] = total)
+  unsigned gx[kBatchMax], gy[kBatchMax];  // each slot's own grid in x and y
+};
+int launch_batch_stage(int D, const BatchSlot* t, const BatchGrid& bg, int stage, cudaStream_t s);
+int launch_batch_band(int D, const BatchSlot* t, const BatchGrid& bg, int stage, cudaStream_t s);
+// which: 0 / 1 divergence after stage 1 / 2, 2 the fine residual (vcycle: slots whose
+// projection has converged skip the launch)
+int launch_batch_residual(int D, const BatchSlot* t, const BatchGrid& bg, int which, int vcycle, cudaStream_t s);
+int launch_batch_restrict(int D, const BatchSlot* t, const BatchGrid& bg, int level, cudaStream_t s);
+int launch_batch_tail(int D, const BatchSlot* t, const BatchGrid& bg, size_t smem, cudaStream_t s);
+int launch_batch_sweep(int D, const BatchSlot* t, const BatchGrid& bg, int level, int it, cudaStream_t s);
+int launch_batch_correct(int D, const BatchSlot* t, const BatchGrid& bg, int which, cudaStream_t s);
+// V-cycle control of every slot (first: right after the divergence); sets h to whether
+// any slot's projection continues
+int launch_batch_decide(const BatchSlot* t, const BatchGrid& bg, cudaGraphConditionalHandle h, int first, int proj,
+                        cudaStream_t s);
+int launch_batch_step_end(const BatchSlot* t, const BatchGrid& bg, cudaStream_t s);
+// grids of the single-simulation launches, for the batched ones
+dim3 stage_grid(int D, const Grid& g);
+dim3 band_grid(int D, const int* bn);
+dim3 residual_grid(int D, const Grid& g);
+dim3 restrict_grid(int D, const ResArgs& a);
+dim3 sweep_grid(int D, const SweepArgs& a);
+dim3 correct_grid(int D, const CorrArgs& a);
+}  // namespace wl

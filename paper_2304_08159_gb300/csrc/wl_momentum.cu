@@ -33,7 +33,7 @@ using IC = std::integral_constant<int, N>;
 // is unrolled by the ring's length, so every ring slot, and with it every shared
 // operand offset, is a compile-time constant.
 template <int D>
-__global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
+__device__ __forceinline__ void stage_body(const StageArgs& a, const uint3 bid) {
   constexpr int NP = (D == 3) ? 4 : 1;
   constexpr int HX = ST_HX, PL = ST_HY * ST_HX, NE = PL;
   __shared__ float s_u[D * NP * PL];
@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
   __shared__ float s_fy[D][ST_TY + 1][ST_TX];
   const Grid& g = a.g;
   const int tid = threadIdx.x, tx = tid % ST_TX, ty = tid / ST_TX, warp = tid >> 5, lane = tid & 31;
-  const int i0 = blockIdx.x * ST_TX, j0 = blockIdx.y * ST_TY;
-  const int k0 = (D == 3) ? blockIdx.z * ST_TZ : 0;
+  const int i0 = bid.x * ST_TX, j0 = bid.y * ST_TY;
+  const int k0 = (D == 3) ? bid.z * ST_TZ : 0;
   const int k1 = (D == 3) ? min(k0 + ST_TZ, g.n[2]) : 1;
   const int i = i0 + tx, j = j0 + ty;
   const bool own_cell = (i < g.n[0]) && (j < g.n[1]);
@@ -236,6 +236,8 @@ __global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) {
     step(IC<0>{}, 0);
   }
 }
+template <int D>
+__global__ void __launch_bounds__(256, 4) k_stage(StageArgs a) { stage_body<D>(a, blockIdx); }
 
 // ---------------------------------------------------------------------------
 // 3-D stage kernel with two x-adjacent cells per thread.  The same fluxes and blend as
@@ -279,15 +281,15 @@ __device__ __forceinline__ float2 mom_flux2(float2 m2, float2 m1, float2 p0, flo
 }
 
 template <bool ADV>
-__global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
+__device__ __forceinline__ void stage3_body(const StageArgs& a, const uint3 bid) {
   constexpr int HX = S3_HX, PL = S3_PL, NP = S3_NP;
   __shared__ __align__(16) float s_u[3 * NP * PL];
   __shared__ __align__(16) float s_fy[3][S3_TY + 1][S3_TX];
   __shared__ float s_fxe[3][S3_TY];
   const Grid& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  const int i0 = blockIdx.x * S3_TX, j0 = blockIdx.y * S3_TY;
-  const int k0 = blockIdx.z * S3_TZ;
+  const int i0 = bid.x * S3_TX, j0 = bid.y * S3_TY;
+  const int k0 = bid.z * S3_TZ;
   const int k1 = min(k0 + S3_TZ, g.n[2]);
   const int i = i0 + 2 * lane, j = j0 + ty;
   const bool own_cell = (i < g.n[0]) && (j < g.n[1]);  // n_0 even: both cells or neither
@@ -506,15 +508,17 @@ __global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) {
   };
   for (int k = k0; k < k1; ++k) step(k);
 }
+template <bool ADV>
+__global__ void __launch_bounds__(256, 3) k_stage3(StageArgs a) { stage3_body<ADV>(a, blockIdx); }
 
 // mu1 term of BDIM over the body's bounding box: out_c[I] += s * sum_j mu1_j (f[I+e_j]
 // - f[I-e_j]) / 2 with mu1 = eps K1(d/eps) n at the face (s = 1 in stage 1, 1/2 in
 // stage 2).  mu1 vanishes for |d| >= eps, so only band faces do work.
 template <int D>
-__global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0, int lo1, int lo2, int bx,
-                                                    int by, int bz) {
+__device__ __forceinline__ void bdim_band_body(const StageArgs& a, const Body& b, int lo0, int lo1, int lo2, int bx,
+                                               int by, int bz, const uint3 bid) {
   const long long nbox = (long long)bx * by * bz;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long t = (long long)bid.x * blockDim.x + threadIdx.x;
   if (t >= nbox * D) return;
   const int c = (int)(t / nbox);
   long long rem = t - (long long)c * nbox;
@@ -555,6 +559,11 @@ __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0,
   }
   const long long q = cell_index(g, i, j, k);
   a.out[c][q] += (a.stage == 1 ? 1.f : 0.5f) * acc;
+}
+template <int D>
+__global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0, int lo1, int lo2, int bx,
+                                                    int by, int bz) {
+  bdim_band_body<D>(a, b, lo0, lo1, lo2, bx, by, bz, blockIdx);
 }
 
 // ---------------------------------------------------------------------------
@@ -674,6 +683,68 @@ int launch_band(int D, const StageArgs& a, const Body& b, cudaStream_t s) {
     else
       k_bdim_band<2><<<nb, 256, 0, s>>>(a, b, lo[0], lo[1], lo[2], bx, by, bz);
   }
+  return 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched launches (many small simulations, one launch; see BatchSlot).
+__device__ __forceinline__ int batch_block(const BatchGrid& bg, uint3& bid) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = bg.n;  // bg.start[lo] <= b < bg.start[hi]
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (bg.start[m] <= b) lo = m; else hi = m;
+  }
+  const unsigned local = (unsigned)(b - bg.start[lo]), gx = bg.gx[lo], gy = bg.gy[lo];
+  bid = make_uint3(local % gx, (local / gx) % gy, local / (gx * gy));
+  return bg.slot[lo];
+}
+
+dim3 stage_grid(int D, const Grid& g) {
+  if (D == 3 && g.n[0] % 2 == 0)
+    return dim3((g.n[0] + S3_TX - 1) / S3_TX, (g.n[1] + S3_TY - 1) / S3_TY, (g.n[2] + S3_TZ - 1) / S3_TZ);
+  if (D == 3) return dim3((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_TY - 1) / ST_TY, (g.n[2] + ST_TZ - 1) / ST_TZ);
+  return dim3((g.n[0] + ST_TX - 1) / ST_TX, (g.n[1] + ST_TY - 1) / ST_TY, 1);
+}
+dim3 band_grid(int D, const int* bn) {
+  const long long n = (long long)bn[0] * bn[1] * bn[2] * D;
+  return dim3((unsigned)((n + 255) / 256), 1, 1);
+}
+
+// a batch holds 3-D slots of even n_0 (the pair kernel) with convection on, or 2-D slots
+template <int D>
+__global__ void __launch_bounds__(256, 3) kb_stage(const BatchSlot* __restrict__ t, const __grid_constant__ BatchGrid bg,
+                                                   int stage) {
+  uint3 bid;
+  const int s = batch_block(bg, bid);
+  if constexpr (D == 3)
+    stage3_body<true>(t[s].stage[stage - 1], bid);
+  else
+    stage_body<2>(t[s].stage[stage - 1], bid);
+}
+template <int D>
+__global__ void __launch_bounds__(256) kb_band(const BatchSlot* __restrict__ t, const __grid_constant__ BatchGrid bg,
+                                               int stage) {
+  uint3 bid;
+  const BatchSlot& sl = t[batch_block(bg, bid)];
+  bdim_band_body<D>(sl.stage[stage - 1], sl.body, sl.blo[0], sl.blo[1], sl.blo[2], sl.bn[0], sl.bn[1], sl.bn[2], bid);
+}
+
+int launch_batch_stage(int D, const BatchSlot* t, const BatchGrid& bg, int stage, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  if (D == 3)
+    kb_stage<3><<<bg.start[bg.n], 256, 0, s>>>(t, bg, stage);
+  else
+    kb_stage<2><<<bg.start[bg.n], 256, 0, s>>>(t, bg, stage);
+  return 0;
+}
+int launch_batch_band(int D, const BatchSlot* t, const BatchGrid& bg, int stage, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  if (D == 3)
+    kb_band<3><<<bg.start[bg.n], 256, 0, s>>>(t, bg, stage);
+  else
+    kb_band<2><<<bg.start[bg.n], 256, 0, s>>>(t, bg, stage);
   return 0;
 }
 

@@ -166,7 +166,7 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
 }
 
 template <int D>
-__global__ void __launch_bounds__(256) k_residual(ResArgs a) {
+__device__ __forceinline__ void residual_body(const ResArgs& a, const uint3 bid) {
   __shared__ float s_r[8][32];
   __shared__ unsigned s_m[8];
   // the coarse levels' scale folded into the restriction's multipliers
@@ -174,9 +174,9 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
   const float zcm = a.zcmul * S, zvm = a.zconvmul * S;
   const Grid& g = a.g;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int i = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + ty;
+  const int i = bid.x * 32 + tx, j = bid.y * 8 + ty;
   const bool inxy = i < g.n[0] && j < g.n[1];
-  const int kb = (D == 3) ? blockIdx.z * 2 * RS_ZP : 0;
+  const int kb = (D == 3) ? bid.z * 2 * RS_ZP : 0;
   const int ke = (D == 3) ? min(kb + 2 * RS_ZP, g.n[2]) : 1;
   unsigned mbits = 0u;
   for (int k = kb; k < ke; k += (D == 3 ? 2 : 1)) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
       if (tid < 64) {
         const int cx = tid & 15, cy = tid >> 4;
         const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
-        const int I = blockIdx.x * 16 + cx, J = blockIdx.y * 4 + cy, K = (D == 3) ? (k >> 1) : 0;
+        const int I = bid.x * 16 + cx, J = bid.y * 4 + cy, K = (D == 3) ? (k >> 1) : 0;
         if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
           st_st(a.zc, a.zctype, (long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K),
                 sum * zcm);
@@ -205,13 +205,15 @@ __global__ void __launch_bounds__(256) k_residual(ResArgs a) {
     if (tid == 0 && m) atomicMax(&a.st->norm_bits, m);
   }
 }
+template <int D>
+__global__ void __launch_bounds__(256) k_residual(ResArgs a) { residual_body<D>(a, blockIdx); }
 
 // RES_RESTRICT alone (coarse levels): one thread per coarse cell loads its 2^D children
 // at once (x pairs as float2 when the field is FP32) and sums them in the fused pass's
 // order (z pairs, then x pairs, then y pairs: the same bits), storing the 16-bit copy
 // of z on the way when the level keeps one.  Every restricting level has even sides.
 template <int D>
-__global__ void __launch_bounds__(256) k_restrict(ResArgs a) {
+__device__ __forceinline__ void restrict_body(const ResArgs& a, const uint3 bid, const unsigned nbx) {
   const float S = a.apply_cs ? ldexpf(1.f, a.st->cs_used) : 1.f;
   const float zcm = a.zcmul * S, zvm = a.zconvmul * S;
   const Grid& g = a.g;
@@ -219,7 +221,7 @@ __global__ void __launch_bounds__(256) k_restrict(ResArgs a) {
   const long long ncc = (long long)c0 * c1 * (D == 3 ? a.cn[2] : 1);
   const long long n0 = g.n[0], nn = (long long)g.n[0] * g.n[1];
   const bool plain = a.ztype == ST_F32 && !a.zconv;
-  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < ncc; t += (long long)gridDim.x * 256) {
+  for (long long t = (long long)bid.x * 256 + threadIdx.x; t < ncc; t += (long long)nbx * 256) {
     const int I = (int)(t % c0);
     const long long r = t / c0;
     const int J = (int)(r % c1), K = (int)(r / c1);
@@ -260,6 +262,8 @@ __global__ void __launch_bounds__(256) k_restrict(ResArgs a) {
     st_st(a.zc, a.zctype, t, sum * zcm);
   }
 }
+template <int D>
+__global__ void __launch_bounds__(256) k_restrict(ResArgs a) { restrict_body<D>(a, blockIdx, gridDim.x); }
 
 int launch_residual(int D, const ResArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
@@ -308,7 +312,7 @@ struct RelaxIn {
 // (periodic wrap; -1 outside a non-periodic side), so that every load of the march
 // is a table read and two adds whether or not the tile touches the boundary.
 template <int D, typename T>
-__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
+__device__ __forceinline__ void sweep_body(const SweepArgs& a, const uint3 bid) {
   const T* __restrict__ xin = reinterpret_cast<const T*>(a.x_in);
   const T* __restrict__ zf = reinterpret_cast<const T*>(a.z);
   const T* __restrict__ Lf[3] = {reinterpret_cast<const T*>(a.L[0]), reinterpret_cast<const T*>(a.L[1]),
@@ -320,8 +324,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
   __shared__ int s_xo[SW_HX], s_yo[SW_HY], s_cxo[SW_HX], s_cyo[SW_HY];
   const Grid& g = a.g;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int i0 = blockIdx.x * SW_TX, j0 = blockIdx.y * SW_TY;
-  const int k0 = (D == 3) ? blockIdx.z * a.tz : 0;
+  const int i0 = bid.x * SW_TX, j0 = bid.y * SW_TY;
+  const int k0 = (D == 3) ? bid.z * a.tz : 0;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
   if (a.only_wrapping && !sweep_tile_wraps_xy(g, i0, j0)) return;
   const int n0 = g.n[0], nn = g.n[0] * g.n[1];
@@ -557,6 +561,8 @@ __global__ void __launch_bounds__(256) k_sweep(SweepArgs a) {
     __syncthreads();
   }
 }
+template <int D, typename T>
+__global__ void __launch_bounds__(256) k_sweep(SweepArgs a) { sweep_body<D, T>(a, blockIdx); }
 
 // Planes per block of the sweep kernels (at most 32 per march): the z-blocking that
 // minimises the modelled time, whole waves of blocks (blocks_per_sm resident per SM, the
@@ -786,13 +792,13 @@ int launch_coarse(int D, const CoarseArgs& a, cudaStream_t s) {
 constexpr int CR_Z = 4;
 
 template <int D>
-__global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
+__device__ __forceinline__ void correct_body(const CorrArgs& a, const uint3 bid) {
   __shared__ unsigned s_m[8];
   const Grid& g = a.g;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
-  const int i = blockIdx.x * 32 + tx, j = blockIdx.y * 8 + ty;
+  const int i = bid.x * 32 + tx, j = bid.y * 8 + ty;
   const bool inxy = i < g.n[0] && j < g.n[1];
-  const int kb = (D == 3) ? blockIdx.z * CR_Z : 0;
+  const int kb = (D == 3) ? bid.z * CR_Z : 0;
   const int ke = (D == 3) ? min(kb + CR_Z, g.n[2]) : 1;
   const float s = a.w * a.st->dtf;
   const long long st[3] = {1, (long long)g.n[0], (long long)g.n[0] * g.n[1]};
@@ -828,6 +834,8 @@ __global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
     if (tid == 0) atomicMax(&a.st->cfl_bits, mb);
   }
 }
+template <int D>
+__global__ void __launch_bounds__(256) k_correct(CorrArgs a) { correct_body<D>(a, blockIdx); }
 
 // 3-D correction (+ CFL) with one thread per cell column marching up C3_Z planes:
 // the column's pressure (hi, lo), z-velocity and z-face coefficients sit in a window
@@ -836,16 +844,16 @@ __global__ void __launch_bounds__(256) k_correct(CorrArgs a) {
 constexpr int C3_Z = 16;
 
 template <bool DF, bool CFL>
-__global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
+__device__ __forceinline__ void correct3_body(const CorrArgs& a, const uint3 bid) {
   __shared__ unsigned s_m[8];
   const Grid& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
-  const int i = blockIdx.x * 32 + lane, j = blockIdx.y * 8 + ty;
+  const int i = bid.x * 32 + lane, j = bid.y * 8 + ty;
   const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
   const bool inxy = i < n0 && j < n1;
   const bool per0 = is_per(g, 0), per1 = is_per(g, 1), per2 = is_per(g, 2);
   const long long nn = (long long)n0 * n1;
-  const int kb = blockIdx.z * C3_Z, ke = min(kb + C3_Z, n2);
+  const int kb = bid.z * C3_Z, ke = min(kb + C3_Z, n2);
   const int ic = min(i, n0 - 1), jc = min(j, n1 - 1);
   const long long c0 = ic + (long long)n0 * jc;
   const long long cxm = ((ic > 0) ? ic - 1 : (per0 ? n0 - 1 : ic)) + (long long)n0 * jc;
@@ -956,6 +964,8 @@ __global__ void __launch_bounds__(256) k_correct3(CorrArgs a) {
     if (tid == 0) atomicMax(&a.st->cfl_bits, mb);
   }
 }
+template <bool DF, bool CFL>
+__global__ void __launch_bounds__(256) k_correct3(CorrArgs a) { correct3_body<DF, CFL>(a, blockIdx); }
 
 int launch_correct(int D, const CorrArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
@@ -1022,8 +1032,7 @@ int launch_cfl_only(int D, const Grid& g, const float* const* u, DevState* st, c
 // Device-side control of the V-cycle loop: reads the residual maximum of the pass
 // just finished, converts it to x units (times w dt), counts V-cycles, records the
 // outcome and sets the graph's while-condition.  No host round trip.
-__global__ void k_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, int first, int proj, float w,
-                         double tol, int maxit) {
+__device__ __forceinline__ bool decide_state(DevState* st, int first, int proj, float w, double tol, int maxit) {
   const float nrm = __uint_as_float(st->norm_bits);
   st->norm_bits = 0u;
   // scale of the 16-bit coarse levels for the cycle that corrects this residual: its
@@ -1048,6 +1057,11 @@ __global__ void k_decide(DevState* st, cudaGraphConditionalHandle h, int use_han
   }
   st->res_x = res;
   st->cond = cont ? 1 : 0;
+  return cont;
+}
+__global__ void k_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, int first, int proj, float w,
+                         double tol, int maxit) {
+  const bool cont = decide_state(st, first, proj, w, tol, maxit);
   if (use_handle) cudaGraphSetConditional(h, cont ? 1u : 0u);
 }
 
@@ -1060,8 +1074,8 @@ int launch_decide(DevState* st, cudaGraphConditionalHandle h, int use_handle, in
 // End of a step: advance the clock and take the next dt from the CFL maximum
 // (dt = min(dt_cap, 1/(max out-flux + 2 D nu)), CFL! of Table 2), or keep dt fixed.
 // advance = 0: only set dt (initial condition).
-__global__ void k_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, int advance,
-                           double* ring, int cap, const double* F) {
+__device__ __forceinline__ void step_end_state(DevState* st, int D, double nu, double dt_cap, double dt_fixed,
+                                               int advance, double* ring, int cap, const double* F) {
   const double used = st->dt;
   if (advance) {
     st->time += used;
@@ -1100,6 +1114,10 @@ __global__ void k_step_end(DevState* st, int D, double nu, double dt_cap, double
   st->dtf = (float)dn;
   st->inv_dtf = (float)(1.0 / dn);
   st->cfl_bits = 0u;
+}
+__global__ void k_step_end(DevState* st, int D, double nu, double dt_cap, double dt_fixed, int advance,
+                           double* ring, int cap, const double* F) {
+  step_end_state(st, D, nu, dt_cap, dt_fixed, advance, ring, cap, F);
 }
 
 // refresh the FP32 copies after the host wrote dt
@@ -1704,7 +1722,7 @@ size_t vcycle_tail_smem(int D, const int (*n)[3], int nl) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs a) {
+__device__ __forceinline__ void vcycle_tail_body(const TailArgs& a, const uint3 bid) {
   extern __shared__ float tsm[];
   // shared-memory layout: per level, D coefficient fields, z, x (all levels < 2^31 cells)
   auto level_base = [&](int l) {
@@ -1832,6 +1850,8 @@ __global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs a) {
     for (int q = tid; q < nc; q += kTailThreads) st_st(a.x, a.st[0], q, x0[q]);
   }
 }
+template <int D>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_tail(TailArgs a) { vcycle_tail_body<D>(a, blockIdx); }
 
 int launch_vcycle_tail(int D, const TailArgs& a, cudaStream_t s) {
   const size_t smem = vcycle_tail_smem(D, a.n, a.nl);
@@ -1885,6 +1905,171 @@ __global__ void k_to_storage(const float* in, void* out, int type, long long n) 
 
 int launch_to_storage(const float* in, void* out, int type, long long n, cudaStream_t s) {
   k_to_storage<<<(int)((n + 255) / 256), 256, 0, s>>>(in, out, type, n);
+  return 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched launches (many small simulations, one launch; see BatchSlot).
+__device__ __forceinline__ int batch_block_p(const BatchGrid& bg, uint3& bid, unsigned& nb) {
+  const int b = (int)blockIdx.x;
+  int lo = 0, hi = bg.n;  // bg.start[lo] <= b < bg.start[hi]
+  while (hi - lo > 1) {
+    const int m = (lo + hi) >> 1;
+    if (bg.start[m] <= b) lo = m; else hi = m;
+  }
+  const unsigned local = (unsigned)(b - bg.start[lo]), gx = bg.gx[lo], gy = bg.gy[lo];
+  bid = make_uint3(local % gx, (local / gx) % gy, local / (gx * gy));
+  nb = (unsigned)(bg.start[lo + 1] - bg.start[lo]);
+  return bg.slot[lo];
+}
+
+dim3 residual_grid(int D, const Grid& g) {
+  if (D == 3) return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + 2 * RS_ZP - 1) / (2 * RS_ZP));
+  return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
+}
+dim3 restrict_grid(int D, const ResArgs& a) {
+  const long long ncc = (long long)a.cn[0] * a.cn[1] * (D == 3 ? a.cn[2] : 1);
+  return dim3((unsigned)std::min<long long>((ncc + 255) / 256, 152LL * 8 * 4), 1, 1);
+}
+dim3 sweep_grid(int D, const SweepArgs& a) {
+  const Grid& g = a.g;
+  return dim3((g.n[0] + SW_TX - 1) / SW_TX, (g.n[1] + SW_TY - 1) / SW_TY, D == 3 ? (g.n[2] + a.tz - 1) / a.tz : 1);
+}
+dim3 correct_grid(int D, const CorrArgs& a) {
+  const Grid& g = a.g;
+  if (D == 3 && a.u_in[0] != a.u_out[0]) return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + C3_Z - 1) / C3_Z);
+  if (D == 3) return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, (g.n[2] + CR_Z - 1) / CR_Z);
+  return dim3((g.n[0] + 31) / 32, (g.n[1] + 7) / 8, 1);
+}
+
+// the V-cycle launches skip slots whose projection has converged (cond 0)
+template <int D>
+__global__ void __launch_bounds__(256) kb_residual(const BatchSlot* __restrict__ t, const __grid_constant__ BatchGrid bg,
+                                                   int which, int vcycle) {
+  uint3 bid;
+  unsigned nb;
+  const BatchSlot& sl = t[batch_block_p(bg, bid, nb)];
+  if (vcycle && sl.ds->cond == 0) return;
+  residual_body<D>(which < 2 ? sl.div[which] : sl.res, bid);
+}
+template <int D>
+__global__ void __launch_bounds__(256) kb_restrict(const BatchSlot* __restrict__ t, const __grid_constant__ BatchGrid bg,
+                                                   int level) {
+  uint3 bid;
+  unsigned nb;
+  const BatchSlot& sl = t[batch_block_p(bg, bid, nb)];
+  if (sl.ds->cond == 0) return;
+  restrict_body<D>(sl.restr[level], bid, nb);
+}
+template <int D>
+__global__ void __launch_bounds__(kTailThreads) kb_tail(const BatchSlot* __restrict__ t,
+                                                        const __grid_constant__ BatchGrid bg) {
+  uint3 bid;
+  unsigned nb;
+  const BatchSlot& sl = t[batch_block_p(bg, bid, nb)];
+  if (sl.ds->cond == 0) return;
+  vcycle_tail_body<D>(sl.tail, bid);
+}
+template <int D>
+__global__ void __launch_bounds__(256) kb_sweep(const BatchSlot* __restrict__ t, const __grid_constant__ BatchGrid bg,
+                                                int level, int it) {
+  uint3 bid;
+  unsigned nb;
+  const BatchSlot& sl = t[batch_block_p(bg, bid, nb)];
+  if (sl.ds->cond == 0 || it >= sl.post) return;
+  sweep_body<D, float>(sl.sweep[level][it], bid);
+}
+// 3-D slots: the out-of-place corrector with the double-float pressure; 2-D: k_correct
+template <int D, bool CFL>
+__global__ void __launch_bounds__(256) kb_correct(const BatchSlot* __restrict__ t, const __grid_constant__ BatchGrid bg,
+                                                  int which) {
+  uint3 bid;
+  unsigned nb;
+  const BatchSlot& sl = t[batch_block_p(bg, bid, nb)];
+  if constexpr (D == 3)
+    correct3_body<true, CFL>(sl.corr[which], bid);
+  else
+    correct_body<2>(sl.corr[which], bid);
+}
+// one thread per slot: its V-cycle decision (as k_decide); the loop continues while any
+// slot's does
+__global__ void __launch_bounds__(kBatchMax) kb_decide(const BatchSlot* __restrict__ t,
+                                                       const __grid_constant__ BatchGrid bg,
+                                                       cudaGraphConditionalHandle h, int first, int proj) {
+  bool cont = false;
+  if ((int)threadIdx.x < bg.n) {
+    const BatchSlot& sl = t[bg.slot[threadIdx.x]];
+    if (first || sl.ds->cond) cont = decide_state(sl.ds, first, proj, sl.w[proj], sl.tol, sl.maxit);
+  }
+  const bool any = __syncthreads_or(cont);
+  if (threadIdx.x == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+__global__ void __launch_bounds__(kBatchMax) kb_step_end(const BatchSlot* __restrict__ t,
+                                                         const __grid_constant__ BatchGrid bg) {
+  if ((int)threadIdx.x >= bg.n) return;
+  const BatchSlot& sl = t[bg.slot[threadIdx.x]];
+  step_end_state(sl.ds, sl.D, sl.nu, sl.dt_cap, sl.dt_fixed, 1, sl.ring, sl.ring_cap, nullptr);
+}
+
+int launch_batch_residual(int D, const BatchSlot* t, const BatchGrid& bg, int which, int vcycle, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  if (D == 3)
+    kb_residual<3><<<bg.start[bg.n], 256, 0, s>>>(t, bg, which, vcycle);
+  else
+    kb_residual<2><<<bg.start[bg.n], 256, 0, s>>>(t, bg, which, vcycle);
+  return 0;
+}
+int launch_batch_restrict(int D, const BatchSlot* t, const BatchGrid& bg, int level, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  if (D == 3)
+    kb_restrict<3><<<bg.start[bg.n], 256, 0, s>>>(t, bg, level);
+  else
+    kb_restrict<2><<<bg.start[bg.n], 256, 0, s>>>(t, bg, level);
+  return 0;
+}
+int launch_batch_tail(int D, const BatchSlot* t, const BatchGrid& bg, size_t smem, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  static bool attr[2] = {false, false};
+  if (!attr[D - 2]) {
+    if (D == 3)
+      cudaFuncSetAttribute(kb_tail<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    else
+      cudaFuncSetAttribute(kb_tail<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+    attr[D - 2] = true;
+  }
+  if (D == 3)
+    kb_tail<3><<<bg.start[bg.n], kTailThreads, smem, s>>>(t, bg);
+  else
+    kb_tail<2><<<bg.start[bg.n], kTailThreads, smem, s>>>(t, bg);
+  return 0;
+}
+int launch_batch_sweep(int D, const BatchSlot* t, const BatchGrid& bg, int level, int it, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  if (D == 3)
+    kb_sweep<3><<<bg.start[bg.n], 256, 0, s>>>(t, bg, level, it);
+  else
+    kb_sweep<2><<<bg.start[bg.n], 256, 0, s>>>(t, bg, level, it);
+  return 0;
+}
+int launch_batch_correct(int D, const BatchSlot* t, const BatchGrid& bg, int which, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  if (D == 3 && which == 1)
+    kb_correct<3, true><<<bg.start[bg.n], 256, 0, s>>>(t, bg, which);
+  else if (D == 3)
+    kb_correct<3, false><<<bg.start[bg.n], 256, 0, s>>>(t, bg, which);
+  else
+    kb_correct<2, false><<<bg.start[bg.n], 256, 0, s>>>(t, bg, which);
+  return 0;
+}
+int launch_batch_decide(const BatchSlot* t, const BatchGrid& bg, cudaGraphConditionalHandle h, int first, int proj,
+                        cudaStream_t s) {
+  kb_decide<<<1, kBatchMax, 0, s>>>(t, bg, h, first, proj);
+  return 0;
+}
+int launch_batch_step_end(const BatchSlot* t, const BatchGrid& bg, cudaStream_t s) {
+  if (bg.n == 0) return 0;
+  kb_step_end<<<1, kBatchMax, 0, s>>>(t, bg);
   return 0;
 }
 

@@ -89,7 +89,7 @@ class Server:
     """
 
     def __init__(self, budget_bytes, max_slots=256, tol=1e-6, on_finish=None, make_sim=None, step_batch=None,
-                 timer=None):
+                 timer=None, batch_cells=0):
         self.budget = int(budget_bytes)
         self.max_slots = int(max_slots)
         self.tol = tol
@@ -98,6 +98,10 @@ class Server:
         self._step_batch = step_batch or self._gpu_step_batch
         self._timer = timer
         self.stream = None
+        # batch_cells > 0: simulations of at most that many cells step together in one
+        # batched graph per dimension (wl_batch_step), the others with their own graphs
+        self.batch_cells = int(batch_cells)
+        self.batch = None
 
     # ---- GPU hooks
     def _gpu_sim(self, req):
@@ -116,6 +120,15 @@ class Server:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(self.stream)
+        if self.batch_cells > 0:
+            if self.batch is None:
+                self.batch = wl.Batch(self.batch_cells)
+            es = torch.cuda.Event(enable_timing=True)
+            es.record(self.stream)  # creates the event; wl_batch_step records it again where the batch ends
+            self.batch.step([r.sim.h for r in residents], self.stream.cuda_stream, es.cuda_event)
+            e1.record(self.stream)
+            small = sum(1 for r in residents if r.req.cells <= self.batch_cells)
+            return (e0, e1, es, small, len(residents) - small)
         rc = wl.wl_step_batch([r.sim.h for r in residents], 1, self.stream.cuda_stream)
         e1.record(self.stream)
         if rc < 0:
@@ -193,16 +206,39 @@ def round_latencies_ms(stats):
     return [tok[0].elapsed_time(tok[1]) for _, _, tok in stats["rounds"]]
 
 
-def serve_gpu(requests, budget_bytes=None, max_slots=256, tol=1e-6, on_finish=None):
-    """Batched run on the current GPU; returns (stats, per-round latencies in ms)."""
+def class_latencies_ms(stats):
+    """Step latencies (ms) seen by the small (batched) and the large simulations of a run
+    with a batch: every resident request's step of a round counts once, a small one at the
+    batch's completion, a large one at the round's end.  Returns (small, large) lists."""
+    import torch
+
+    torch.cuda.synchronize()
+    small, large = [], []
+    for _, _, tok in stats["rounds"]:
+        if len(tok) < 5:
+            continue
+        e0, e1, es, ns, nl = tok
+        # es was recorded by the library (wl_batch_step), so its time comes through it
+        small += [wl.wl_event_elapsed(e0.cuda_event, es.cuda_event)] * ns
+        large += [e0.elapsed_time(e1)] * nl
+    return small, large
+
+
+def serve_gpu(requests, budget_bytes=None, max_slots=256, tol=1e-6, on_finish=None, batch_cells=0):
+    """Batched run on the current GPU; returns (stats, per-round latencies in ms).
+    batch_cells > 0: the simulations of at most that many cells step in batched graphs."""
     import torch
 
     if budget_bytes is None:
         free, _ = torch.cuda.mem_get_info()
         budget_bytes = int(0.5 * free)
-    srv = Server(budget_bytes, max_slots=max_slots, tol=tol, on_finish=on_finish, timer=torch.cuda.synchronize)
+    srv = Server(budget_bytes, max_slots=max_slots, tol=tol, on_finish=on_finish, timer=torch.cuda.synchronize,
+                 batch_cells=batch_cells)
     stats = srv.run(requests)
-    return stats, round_latencies_ms(stats)
+    lat = round_latencies_ms(stats)
+    if srv.batch is not None:
+        srv.batch.close()
+    return stats, lat
 
 
 def sequential_gpu(requests, tol=1e-6, on_finish=None):

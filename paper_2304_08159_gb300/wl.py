@@ -52,6 +52,7 @@ EXPORTS = (
     "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
     "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split",
     "wl_state_bytes", "wl_save", "wl_load", "wl_get_metrics",
+    "wl_batch_create", "wl_batch_step", "wl_batch_destroy", "wl_batch_last_error", "wl_event_elapsed",
 )
 METRIC_RING, METRIC_FIELDS = 1024, 13
 METRICS = ("step", "time", "dt", "vcycles1", "vcycles2", "resid1", "resid2", "cfl", "ke", "maxdiv", "F0", "F1", "F2")
@@ -126,6 +127,11 @@ def load(path: str = LIB_PATH):
         "wl_level_split": (I, [H, I, IP, DP]),
         "wl_state_bytes": (ctypes.c_size_t, [H]),
         "wl_get_metrics": (I, [H, DP, I, IP]),
+        "wl_batch_create": (I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_void_p)]),
+        "wl_batch_step": (I, [ctypes.c_void_p, ctypes.POINTER(H), I, P, P]),
+        "wl_batch_destroy": (None, [ctypes.c_void_p]),
+        "wl_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+        "wl_event_elapsed": (I, [P, P, ctypes.POINTER(ctypes.c_float)]),
         "wl_save": (I, [H, P, ctypes.c_size_t, I]),
         "wl_load": (I, [H, P, ctypes.c_size_t, I]),
     }
@@ -268,6 +274,47 @@ def wl_step_batch(handles, nsteps, stream=None):
     """Advance the sims `handles` (wl_handle values) by nsteps each, together (see include/wl.h)."""
     arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     return load().wl_step_batch(arr, len(handles), int(nsteps), stream)
+
+
+def wl_event_elapsed(start, end):
+    """ms between two recorded CUDA events (raw cudaEvent_t handles)."""
+    ms = ctypes.c_float(0.0)
+    rc = load().wl_event_elapsed(start, end, ctypes.byref(ms))
+    if rc != WL_OK:
+        raise WLError(rc, "wl_event_elapsed")
+    return ms.value
+
+
+class Batch:
+    """Batched steps of many small simulations (wl_batch_*): sims of at most max_cells
+    cells (and the options the batched kernels cover) step in one graph per dimension,
+    the others with their own graphs."""
+
+    def __init__(self, max_cells):
+        h = ctypes.c_void_p()
+        rc = load().wl_batch_create(int(max_cells), ctypes.byref(h))
+        if rc != WL_OK:
+            raise WLError(rc, "wl_batch_create")
+        self.h = h
+
+    def step(self, handles, stream=None, small_done=None):
+        arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+        rc = load().wl_batch_step(self.h, arr, len(handles), stream, small_done)
+        if rc < 0:
+            msg = load().wl_batch_last_error(self.h)
+            raise WLError(rc, "wl_batch_step: " + (msg.decode() if msg else ""))
+        return rc
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().wl_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def wl_wait_probe(seconds):

@@ -1,4 +1,5 @@
-"""Serving on the GPU: every request's result is the same alone and in the mix."""
+"""Serving on the GPU: every request's result is the same alone and in the mix, stepped
+with its own graph or in a batched graph, and matches the oracle."""
 import numpy as np
 import pytest
 
@@ -17,9 +18,10 @@ def small_requests():
     return reqs
 
 
-def test_results_same_alone_and_in_the_mix():
-    import torch
-
+@pytest.mark.parametrize("batch_cells", [0, 10000, 1 << 18], ids=["graphs", "batch2d", "batchall"])
+def test_results_same_alone_and_in_the_mix(batch_cells):
+    """batch_cells 0: every resident steps with its own graph; 10000: the 2-D grids step in
+    one batched graph, the 3-D ones with their own; 2^18: all of them batched."""
     reqs = small_requests()
     alone = {}
     for r in reqs:
@@ -34,17 +36,61 @@ def test_results_same_alone_and_in_the_mix():
 
     # a budget of three of the larger workspaces: requests queue, overlap and replace one another
     budget = 3 * max(serve.workspace_bytes(r) for r in reqs)
-    stats, lat = serve.serve_gpu(reqs, budget_bytes=budget, on_finish=on_finish)
+    stats, lat = serve.serve_gpu(reqs, budget_bytes=budget, on_finish=on_finish, batch_cells=batch_cells)
     assert sorted(mixed) == [r.rid for r in reqs] and not stats["rejected"]
     assert max(n for n, _, _ in stats["rounds"]) > 1
     for rid, (u, p, dt) in alone.items():
         um, pm, dtm = mixed[rid]
         assert np.array_equal(u, um) and np.array_equal(p, pm) and dt == dtm, rid
     assert len(lat) == len(stats["rounds"]) and min(lat) > 0
+    if batch_cells:
+        small, large = serve.class_latencies_ms(stats)
+        ns = sum(r.steps for r in reqs if r.cells <= batch_cells)
+        assert len(small) == ns and len(large) == sum(r.steps for r in reqs) - ns
+        assert min(small) > 0
+
+
+def test_batch_steps_through_the_c_abi():
+    """wl_batch_step directly: three small sims (2-D and 3-D, with and without a body)
+    advanced five rounds in one batch, and a large one beside them, give the bits each
+    gets from wl_step alone; the small-done event is recorded."""
+    import torch
+
+    cases = [((64, 32), dict(kind=wl.WL_BODY_SPHERE, center=(16.0, 16.0), radius=5.0)),
+             ((48, 48), None),
+             ((32, 16, 16), dict(kind=wl.WL_BODY_SPHERE, center=(10.0, 8.0, 8.0), radius=3.0)),
+             ((64, 32, 32), dict(kind=wl.WL_BODY_SPHERE, center=(20.0, 16.0, 16.0), radius=5.0))]
+
+    def make(dims, body):
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            sim = wl.Sim(dims, 0.02, (1.0,) + (0.0,) * (len(dims) - 1), body=body)
+        return sim, stream
+
+    ref = []
+    for dims, body in cases:
+        sim, _ = make(dims, body)
+        sim.step(5)
+        ref.append((sim.get(0), sim.get(1), sim.dt))
+        sim.close()
+    sims = [make(d, b) for d, b in cases]
+    batch = wl.Batch(20000)  # the 64 x 32 x 32 sim steps with its own graph
+    stream = torch.cuda.Stream()
+    for _ in range(5):
+        done = torch.cuda.Event(enable_timing=True)
+        done.record(stream)  # creates the event (wl_batch_step records it again)
+        assert batch.step([s.h for s, _ in sims], stream.cuda_stream, done.cuda_event) == wl.WL_OK
+    torch.cuda.synchronize()
+    for (sim, _), (u, p, dt) in zip(sims, ref):
+        assert np.array_equal(sim.get(0), u) and np.array_equal(sim.get(1), p) and sim.dt == dt
+        assert sim.time()[1] == 5
+    batch.close()
+    for sim, _ in sims:
+        sim.close()
 
 
 def test_mix_requests_match_oracle():
-    """Requests served in the mix against the FP64 oracle stepping the same flow alone
+    """Requests served in the mix (batched steps) against the FP64 oracle stepping the same flow alone
     (projections to 1e-10): a 2-D one (64 x 64 cylinder, 12 steps) and a 3-D one (32^3
     sphere, 7 steps).  Velocity within the stated 1e-5 relative L2, dt and time within
     1e-5, drag coefficient within 1e-4; the pressure (mean over active cells removed)
@@ -59,7 +105,7 @@ def test_mix_requests_match_oracle():
         mixed[req.rid] = (sim.get(wl.WL_FIELD_U), sim.get(wl.WL_FIELD_P), sim.dt, sim.time(), sim.forces())
 
     budget = 3 * max(serve.workspace_bytes(r) for r in reqs)
-    serve.serve_gpu(reqs, budget_bytes=budget, on_finish=on_finish)
+    serve.serve_gpu(reqs, budget_bytes=budget, on_finish=on_finish, batch_cells=1 << 18)
     for r in (reqs[0], reqs[1]):
         U = (1.0,) + (0.0,) * (len(r.dims) - 1)
         ref = O.Oracle(r.dims, r.nu, U=U, body=r.body)
