@@ -52,6 +52,7 @@ extern "C" {
 #define WL_ENONFINITE (-4) /* a non-finite dt or residual was produced */
 #define WL_ETIMEOUT (-5)   /* a device-side bounded wait gave up (a staged copy never arrived) */
 #define WL_WNOTCONV 1      /* multigrid hit max_vcycles before tol; state stays valid */
+#define WL_NODEBUG 2       /* wl_debug_bounds called on a library built without the bounds checks */
 
 /* field ids for wl_get_field / wl_set_field */
 #define WL_FIELD_U 0    /* velocity, D blocks (read/write) */
@@ -362,6 +363,20 @@ int wl_graph_kernels(wl_handle h, int* per_step, int* per_vcycle);
 #define WL_NOALLOC_MAX_CELLS (16384LL * 4096LL)
 int wl_forces_noalloc(const int* dims, int ndim, unsigned periodic_mask, const wl_body* body, double eps,
                       const float* p, const float* L, double* F, void* stream);
+
+/* Bounds-checked build (libwl_debug.so: the same sources compiled with WL_DEBUG_BOUNDS; a
+ * substitute for a memory checker, none being available to run on the GPU).  Its kernels
+ * test the index of every global store of the step and of the computed global loads
+ * against the array's size; an index outside sets a bit (WL_DBG_* in the kernels' sources:
+ * 1 stage, 2 band term, 4 sweep, 8 residual, 16 correction, 32 restriction, 64 a TMA copy
+ * whose inner coordinate is not 16-byte aligned, 128 coarse-correction load) and the
+ * access is skipped, never a trap.  Its workspace also leaves a 256-byte canary (bytes
+ * 0xA5) after every array.  This call reads and clears the kernels' flags (for every sim
+ * of the process) and checks this sim's canaries (bit 31: one was overwritten) into
+ * *flags; 0 means no bad index and intact canaries.  Synchronises.  In the release library
+ * the checks compile away: *flags = 0 and the call returns WL_NODEBUG.  No counterpart in
+ * the paper. */
+int wl_debug_bounds(wl_handle h, unsigned* flags);
 
 /* Self-test of the bounded device waits.  Every kernel that waits on the device (the
  * TMA-staged sweep and residual wait for their copies on mbarriers) gives up after a

@@ -16,6 +16,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwl.so")
+# the bounds-checked build: the same sources with WL_DEBUG_BOUNDS (index checks that flag
+# and skip, canaries between workspace arrays), for the tests
+DEBUG_BUILD = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(HERE, "libwl_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", os.path.join(ROOT, "include")]
 
@@ -38,8 +42,13 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, extra_flags=None) -> str:
-    """Compile and link libwl.so if any source or header changed; return its path."""
+def build(verbose: bool = False, extra_flags=None, debug: bool = False) -> str:
+    """Compile and link libwl.so (debug: the bounds-checked libwl_debug.so) if any source or
+    header changed; return its path."""
+    BUILD = DEBUG_BUILD if debug else globals()["BUILD"]
+    LIB = DEBUG_LIB if debug else globals()["LIB"]
+    if debug:
+        extra_flags = list(extra_flags or []) + ["-DWL_DEBUG_BOUNDS"]
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
@@ -71,5 +80,12 @@ def build(verbose: bool = False, extra_flags=None) -> str:
     return LIB
 
 
+def build_all(verbose: bool = False):
+    """Both libraries, compiled side by side."""
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        fs = [ex.submit(build, verbose), ex.submit(build, verbose, None, True)]
+        return [f.result() for f in fs]
+
+
 if __name__ == "__main__":
-    print(build(verbose="-v" in sys.argv))
+    print(build_all(verbose="-v" in sys.argv))

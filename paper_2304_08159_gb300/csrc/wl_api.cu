@@ -61,6 +61,7 @@ constexpr int kMetricRing = WL_METRIC_RING;
 
 struct wl_sim {
   unsigned long long uid = 0;  // unique per sim of the process (a batch keys its graphs on it)
+  std::vector<size_t> canaries;  // bounds-checked build: workspace offsets of the canary gaps
   int D = 0;
   Grid g{};
   double nu = 0.0;
@@ -204,13 +205,27 @@ bool make_field_map(CUtensorMap* m, const float* ptr, const Grid& g, int D, int 
   return r == CUDA_SUCCESS;
 }
 
+// Carves the workspace into 256-byte aligned arrays.  The bounds-checked build leaves a
+// 256-byte canary after every array (filled with 0xA5 at creation and checked by
+// wl_debug_bounds), so a write past an array's end shows up there.
+#ifdef WL_DEBUG_BOUNDS
+constexpr size_t kCanary = 256;
+#else
+constexpr size_t kCanary = 0;
+#endif
 struct Carver {
   char* base;
   size_t off = 0;
+  std::vector<size_t>* canaries = nullptr;
   void* take(size_t bytes) {
     off = (off + 255) & ~size_t(255);
     void* p = base ? base + off : nullptr;
     off += bytes;
+    if (kCanary) {
+      off = (off + 255) & ~size_t(255);
+      if (canaries) canaries->push_back(off);
+      off += kCanary;
+    }
     return p;
   }
 };
@@ -226,6 +241,10 @@ size_t layout(wl_sim* s, int D, const int* dims, int precision, int cprec, int e
   int ld[kMaxLevels][3];
   const int nlev = plan_levels(dims, D, ld);
   Carver cv{base};
+  if (s && base) {
+    s->canaries.clear();
+    cv.canaries = &s->canaries;
+  }
   const long long nc = (long long)ld[0][0] * ld[0][1] * ld[0][2];
   const long long ne = exit_bc ? (long long)ld[0][1] * ld[0][2] : 0;  // exit plane after u_x
   float** bufs[3] = {s ? s->ua : nullptr, s ? s->ub : nullptr, s ? s->uc : nullptr};
@@ -965,6 +984,7 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
   }
   s->ws_bytes = need;
   layout(s, ndim, dims, o.precision, o.coarse_precision, o.exit_bc ? 1 : 0, s->ws);
+  for (size_t off : s->canaries) cudaMemsetAsync(s->ws + off, 0xA5, kCanary, s->st);
   // Staged kernels: tiles away from the body take the variant that forms the face
   // coefficients (the level's free-stream value 2^(l (D-2)), 0 on walls) instead of
   // loading them.  The band box (faces with mu0 < 1 lie inside it) scaled to each level,
@@ -1494,6 +1514,10 @@ size_t grad_layout(wl_sim* s, int nsteps, int every, char* base) {
   const size_t n = (size_t)s->g.nc;
   const int nseg = (nsteps + every - 1) / every;
   Carver cv{base};
+  if (s && base) {
+    s->canaries.clear();
+    cv.canaries = &s->canaries;
+  }
   void* ck = cv.take(sizeof(float) * n * (D + 2) * (size_t)(nseg + 1));
   void* ckst = cv.take(sizeof(DevState) * (size_t)(nseg + 1));
   void* seg = cv.take(sizeof(float) * n * (2 * D + 2) * (size_t)every);
@@ -1981,12 +2005,14 @@ struct wl_batch_s {
   struct Group {
     std::vector<unsigned long long> key;  // the slots (sim uids) of the current graph, in order
     BatchSlot* dtab = nullptr;
-    cudaStream_t st = nullptr;
-    cudaEvent_t done = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaGraphConditionalHandle hc[2]{};
   } grp[2];  // 2-D and 3-D slots
+  // the batched graphs run on the caller's stream, in order with everything else queued
+  // there; events hand the slots' own streams over to it and back
+  std::vector<cudaEvent_t> ev_in;  // one per slot: its own stream's work before the round
+  cudaEvent_t ev_out = nullptr;    // the caller's stream after the batched graphs
   std::string err;
 };
 
@@ -2106,11 +2132,10 @@ extern "C" int wl_batch_create(long long max_cells, wl_batch* out) {
   auto* b = new wl_batch_s();
   b->max_cells = max_cells;
   bool ok = cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking) == cudaSuccess;
-  for (auto& G : b->grp) {
-    ok = ok && cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaMalloc(&G.dtab, sizeof(BatchSlot) * kBatchMax) == cudaSuccess;
-  }
+  ok = ok && cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  b->ev_in.assign(2 * kBatchMax, nullptr);
+  for (auto& e : b->ev_in) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  for (auto& G : b->grp) ok = ok && cudaMalloc(&G.dtab, sizeof(BatchSlot) * kBatchMax) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     wl_batch_destroy(b);
@@ -2122,14 +2147,15 @@ extern "C" int wl_batch_create(long long max_cells, wl_batch* out) {
 
 extern "C" void wl_batch_destroy(wl_batch b) {
   if (!b) return;
+  cudaDeviceSynchronize();  // no batched graph is still running
   for (auto& G : b->grp) {
-    if (G.st) cudaStreamSynchronize(G.st);
     if (G.exec) cudaGraphExecDestroy(G.exec);
     if (G.graph) cudaGraphDestroy(G.graph);
     if (G.dtab) cudaFree(G.dtab);
-    if (G.done) cudaEventDestroy(G.done);
-    if (G.st) cudaStreamDestroy(G.st);
   }
+  for (auto& e : b->ev_in)
+    if (e) cudaEventDestroy(e);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
   if (b->cs) cudaStreamDestroy(b->cs);
   delete b;
 }
@@ -2174,7 +2200,16 @@ extern "C" int wl_batch_step(wl_batch b, const wl_handle* hs, int n, void* strea
       if (first == WL_OK) first = rc;
     }
   }
-  // the small ones: one batched graph per dimension
+  // the small ones: one batched graph per dimension, on the caller's stream after the work
+  // already queued on each slot's own stream (every batched kernel, table upload and graph
+  // rebuild is then in order with the caller's stream)
+  int ne = 0;
+  for (int gi = 0; gi < 2; ++gi)
+    for (wl_sim* s : small[gi]) {
+      WL_BCUDA(b, cudaEventRecord(b->ev_in[ne], s->st));
+      WL_BCUDA(b, cudaStreamWaitEvent(cs, b->ev_in[ne], 0));
+      ++ne;
+    }
   for (int gi = 0; gi < 2; ++gi) {
     auto& G = b->grp[gi];
     auto& v = small[gi];
@@ -2184,23 +2219,21 @@ extern "C" int wl_batch_step(wl_batch b, const wl_handle* hs, int n, void* strea
     if (key != G.key) {
       std::vector<BatchSlot> slots;
       for (wl_sim* s : v) slots.push_back(batch_slot(s));
-      WL_BCUDA(b, cudaStreamSynchronize(G.st));  // the previous graph no longer reads the table
-      WL_BCUDA(b, cudaMemcpy(G.dtab, slots.data(), sizeof(BatchSlot) * slots.size(), cudaMemcpyHostToDevice));
+      // in stream order after the previous graph that read the table (a pageable source is
+      // staged before the call returns, so `slots` may go)
+      WL_BCUDA(b, cudaMemcpyAsync(G.dtab, slots.data(), sizeof(BatchSlot) * slots.size(), cudaMemcpyHostToDevice,
+                                  cs));
       G.key.clear();
       int rc = build_group_graph(b, G, gi + 2, slots);
       if (rc) return rc;
       G.key = key;
     }
-    WL_BCUDA(b, cudaStreamWaitEvent(G.st, fork, 0));
-    for (wl_sim* s : v) {  // after the work already queued on each slot's own stream
-      if (!s->join) WL_BCUDA(b, cudaEventCreateWithFlags(&s->join, cudaEventDisableTiming));
-      WL_BCUDA(b, cudaEventRecord(s->join, s->st));
-      WL_BCUDA(b, cudaStreamWaitEvent(G.st, s->join, 0));
-    }
-    WL_BCUDA(b, cudaGraphLaunch(G.exec, G.st));
-    WL_BCUDA(b, cudaEventRecord(G.done, G.st));
-    for (wl_sim* s : v) WL_BCUDA(b, cudaStreamWaitEvent(s->st, G.done, 0));  // later work on the slot
-    WL_BCUDA(b, cudaStreamWaitEvent(cs, G.done, 0));
+    WL_BCUDA(b, cudaGraphLaunch(G.exec, cs));
+  }
+  if (ne > 0) {
+    WL_BCUDA(b, cudaEventRecord(b->ev_out, cs));
+    for (int gi = 0; gi < 2; ++gi)
+      for (wl_sim* s : small[gi]) WL_BCUDA(b, cudaStreamWaitEvent(s->st, b->ev_out, 0));  // later work on the slot
   }
   if (small_done) WL_BCUDA(b, cudaEventRecord((cudaEvent_t)small_done, cs));
   for (wl_sim* s : large)
@@ -2213,4 +2246,23 @@ extern "C" int wl_batch_step(wl_batch b, const wl_handle* hs, int n, void* strea
 extern "C" int wl_event_elapsed(void* start, void* end, float* ms) {
   if (!start || !end || !ms) return WL_EINVAL;
   return cudaEventElapsedTime(ms, (cudaEvent_t)start, (cudaEvent_t)end) == cudaSuccess ? WL_OK : WL_ECUDA;
+}
+
+extern "C" int wl_debug_bounds(wl_handle s, unsigned* flags) {
+  if (!s || !flags) return WL_EINVAL;
+  *flags = 0u;
+#ifdef WL_DEBUG_BOUNDS
+  WL_CUDA(s, cudaStreamSynchronize(s->st));
+  unsigned f = dbg_take_momentum() | dbg_take_poisson() | dbg_take_sweep();
+  std::vector<unsigned char> buf(kCanary);
+  for (size_t off : s->canaries) {
+    WL_CUDA(s, cudaMemcpy(buf.data(), s->ws + off, kCanary, cudaMemcpyDeviceToHost));
+    for (unsigned char c : buf)
+      if (c != 0xA5) f |= 0x80000000u;
+  }
+  *flags = f;
+  return WL_OK;
+#else
+  return WL_NODEBUG;
+#endif
 }

@@ -29,6 +29,25 @@ __host__ __device__ inline long long exit_index(const Grid& g, int j, int k) {
 
 __device__ __forceinline__ bool is_per(const Grid& g, int d) { return (g.per >> d) & 1u; }
 
+// ---- Bounds-checked build (compiled with WL_DEBUG_BOUNDS into libwl_debug.so): an index
+// outside its array sets a bit of this translation unit's flag word and the access is
+// skipped, so a bad index is reported instead of corrupting memory or faulting (no trap).
+// The release build compiles every check to `true`.  Bits: WL_DBG_*.
+enum : unsigned {
+  WL_DBG_STAGE = 1u, WL_DBG_BAND = 2u, WL_DBG_SWEEP = 4u, WL_DBG_RESID = 8u, WL_DBG_CORRECT = 16u,
+  WL_DBG_RESTRICT = 32u, WL_DBG_TMA = 64u, WL_DBG_COARSE = 128u, WL_DBG_BATCH = 256u
+};
+#ifdef WL_DEBUG_BOUNDS
+static __device__ unsigned wl_dbg_bits;
+__device__ __forceinline__ bool wl_in(long long i, long long n, unsigned bit) {
+  if (i >= 0 && i < n) return true;
+  atomicOr(&wl_dbg_bits, bit);
+  return false;
+}
+#else
+__device__ __forceinline__ bool wl_in(long long, long long, unsigned) { return true; }
+#endif
+
 // Storage types of the coarse multigrid levels' fields (wl_opts.coarse_precision):
 // values are stored in 16 bits and every operation on them runs in FP32.
 enum { ST_F32 = 0, ST_BF16 = 1, ST_F16 = 2 };

@@ -394,3 +394,11 @@ dim3 restrict_grid(int D, const ResArgs& a);
 dim3 sweep_grid(int D, const SweepArgs& a);
 dim3 correct_grid(int D, const CorrArgs& a);
 }  // namespace wl
+
+namespace wl {
+// Bounds-checked build: take (read and clear) the index-check flag word of each
+// translation unit (0 in a release build).
+unsigned dbg_take_momentum();
+unsigned dbg_take_poisson();
+unsigned dbg_take_sweep();
+}  // namespace wl

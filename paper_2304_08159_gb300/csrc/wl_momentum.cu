@@ -79,7 +79,8 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const uint3 bid) 
       if (e >= NE) break;
       if (inner) {
 #pragma unroll
-        for (int c = 0; c < D; ++c) rv[h][c] = __ldg(a.u[c] + qk + foff[h]);
+        for (int c = 0; c < D; ++c)
+          rv[h][c] = wl_in(qk + foff[h], g.nc, WL_DBG_STAGE) ? __ldg(a.u[c] + qk + foff[h]) : 0.f;
       } else {
         const int row = e / HX, col = e - row * HX;
 #pragma unroll
@@ -214,11 +215,14 @@ __device__ __forceinline__ void stage_body(const StageArgs& a, const uint3 bid) 
           const float m = m0[c];
           ov = (a.stage == 1) ? m * f : 0.5f * fmaf(m, f, uc);
         }
-        a.out[c][qg] = ov;
+        if (wl_in(qg, g.nc, WL_DBG_STAGE)) a.out[c][qg] = ov;
         if (box_tile) {  // keep f inside the body's band box for the mu1 term
           const unsigned bi = (unsigned)(i - a.blo[0]), bj = (unsigned)(j - a.blo[1]), bk = (unsigned)(k - a.blo[2]);
           if (bi < (unsigned)a.bn[0] && bj < (unsigned)a.bn[1] && bk < (unsigned)a.bn[2])
-            a.fbox[(long long)c * a.bn[0] * a.bn[1] * a.bn[2] + bi + (long long)a.bn[0] * (bj + (long long)a.bn[1] * bk)] = f;
+          {
+            const long long fi = (long long)c * a.bn[0] * a.bn[1] * a.bn[2] + bi + (long long)a.bn[0] * (bj + (long long)a.bn[1] * bk);
+            if (wl_in(fi, g.nc, WL_DBG_BAND)) a.fbox[fi] = f;
+          }
         }
       }
     }
@@ -322,7 +326,10 @@ __device__ __forceinline__ void stage3_body(const StageArgs& a, const uint3 bid)
       if (e >= S3_NPAIR) break;
       if (inner) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) rv[h][c] = __ldg(reinterpret_cast<const float2*>(a.u[c] + qk + foff[h]));
+        for (int c = 0; c < 3; ++c)
+          rv[h][c] = wl_in(qk + foff[h] + 1, g.nc, WL_DBG_STAGE)
+                         ? __ldg(reinterpret_cast<const float2*>(a.u[c] + qk + foff[h]))
+                         : make_float2(0.f, 0.f);
       } else {
         const int row = e / (HX / 2), col = 2 * (e - row * (HX / 2));
 #pragma unroll
@@ -490,15 +497,15 @@ __device__ __forceinline__ void stage3_body(const StageArgs& a, const uint3 bid)
         const bool upd1 = is_per(g, c) || (c == 0 ? i + 1 : I[c]) >= 1;
         if (!upd0) ov.x = fo.x = g.U[c];
         if (!upd1) ov.y = fo.y = g.U[c];
-        *reinterpret_cast<float2*>(a.out[c] + qg) = ov;
+        if (wl_in(qg + 1, g.nc, WL_DBG_STAGE)) *reinterpret_cast<float2*>(a.out[c] + qg) = ov;
         if (box_tile) {  // keep f inside the body's band box for the mu1 term
           const unsigned bj = (unsigned)(j - a.blo[1]), bk = (unsigned)(k - a.blo[2]);
           if (bj < (unsigned)a.bn[1] && bk < (unsigned)a.bn[2]) {
             const long long base =
                 (long long)c * a.bn[0] * a.bn[1] * a.bn[2] + (long long)a.bn[0] * (bj + (long long)a.bn[1] * bk);
             const unsigned b0 = (unsigned)(i - a.blo[0]), b1 = (unsigned)(i + 1 - a.blo[0]);
-            if (b0 < (unsigned)a.bn[0]) a.fbox[base + b0] = fo.x;
-            if (b1 < (unsigned)a.bn[0]) a.fbox[base + b1] = fo.y;
+            if (b0 < (unsigned)a.bn[0] && wl_in(base + b0, g.nc, WL_DBG_BAND)) a.fbox[base + b0] = fo.x;
+            if (b1 < (unsigned)a.bn[0] && wl_in(base + b1, g.nc, WL_DBG_BAND)) a.fbox[base + b1] = fo.y;
           }
         }
       }
@@ -558,7 +565,7 @@ __device__ __forceinline__ void bdim_band_body(const StageArgs& a, const Body& b
     acc += (float)(k1 * nrm[jd]) * 0.5f * (fp - fm);
   }
   const long long q = cell_index(g, i, j, k);
-  a.out[c][q] += (a.stage == 1 ? 1.f : 0.5f) * acc;
+  if (wl_in(q, g.nc, WL_DBG_BAND)) a.out[c][q] += (a.stage == 1 ? 1.f : 0.5f) * acc;
 }
 template <int D>
 __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0, int lo1, int lo2, int bx,
@@ -698,6 +705,7 @@ __device__ __forceinline__ int batch_block(const BatchGrid& bg, uint3& bid) {
   }
   const unsigned local = (unsigned)(b - bg.start[lo]), gx = bg.gx[lo], gy = bg.gy[lo];
   bid = make_uint3(local % gx, (local / gx) % gy, local / (gx * gy));
+  wl_in(bid.z, (unsigned)(bg.start[lo + 1] - bg.start[lo]) / (gx * gy), WL_DBG_BATCH);
   return bg.slot[lo];
 }
 
@@ -748,4 +756,17 @@ int launch_batch_band(int D, const BatchSlot* t, const BatchGrid& bg, int stage,
   return 0;
 }
 
+}  // namespace wl
+
+namespace wl {
+unsigned dbg_take_momentum() {
+#ifdef WL_DEBUG_BOUNDS
+  unsigned v = 0, z = 0;
+  cudaMemcpyFromSymbol(&v, wl_dbg_bits, sizeof(v));
+  cudaMemcpyToSymbol(wl_dbg_bits, &z, sizeof(z));
+  return v;
+#else
+  return 0u;
+#endif
+}
 }  // namespace wl

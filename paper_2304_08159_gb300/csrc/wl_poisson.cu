@@ -78,7 +78,7 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
       div += up - __ldg(a.u[c] + q);
     }
     z = (a.mode == RES_DIV_ONLY) ? div : div * a.inv_w * a.st->inv_dtf;
-    a.z[q] = z;
+    if (wl_in(q, g.nc, WL_DBG_RESID)) a.z[q] = z;
     if (a.mode == RES_DIV_ONLY) return 0.f;
   } else {
     z = ld_st(a.z, a.ztype, q);
@@ -97,8 +97,10 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       bool has;
-      const long long qu = nb_up(g, c, I[c], q, st[c], has);
-      const long long qm = nb_dn(g, c, I[c], q, st[c]);
+      long long qu = nb_up(g, c, I[c], q, st[c], has);
+      long long qm = nb_dn(g, c, I[c], q, st[c]);
+      if (!wl_in(qu, g.nc, WL_DBG_RESID)) qu = q;
+      if (!wl_in(qm, g.nc, WL_DBG_RESID)) qm = q;
       Lf[2 * c] = has ? (a.uni ? a.uval : __ldg(a.L[c] + qu)) : 0.f;
       Lf[2 * c + 1] = a.uni ? ((I[c] > 0 || is_per(g, c)) ? a.uval : 0.f) : __ldg(a.L[c] + q);
       hn[2 * c] = __ldg(a.ph + qu);
@@ -152,15 +154,17 @@ __device__ __forceinline__ float residual_cell(const ResArgs& a, int i, int j, i
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       bool has;
-      const long long qu = nb_up(g, c, I[c], q, st[c], has);
-      const long long qm = nb_dn(g, c, I[c], q, st[c]);
+      long long qu = nb_up(g, c, I[c], q, st[c], has);
+      long long qm = nb_dn(g, c, I[c], q, st[c]);
+      if (!wl_in(qu, g.nc, WL_DBG_RESID)) qu = q;
+      if (!wl_in(qm, g.nc, WL_DBG_RESID)) qm = q;
       const float Lu = has ? (a.uni ? a.uval : __ldg(a.L[c] + qu)) : 0.f;
       const float Ll = a.uni ? ((I[c] > 0 || is_per(g, c)) ? a.uval : 0.f) : __ldg(a.L[c] + q);
       acc += Lu * (__ldg(a.x + qu) - x0) + Ll * (__ldg(a.x + qm) - x0);
     }
     r = z - acc;
   }
-  if (a.rout) a.rout[q] = r;
+  if (a.rout && wl_in(q, g.nc, WL_DBG_RESID)) a.rout[q] = r;
   mbits = max(mbits, __float_as_uint(fabsf(r)));
   return r;
 }
@@ -193,9 +197,10 @@ __device__ __forceinline__ void residual_body(const ResArgs& a, const uint3 bid)
         const int cx = tid & 15, cy = tid >> 4;
         const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
         const int I = bid.x * 16 + cx, J = bid.y * 4 + cy, K = (D == 3) ? (k >> 1) : 0;
-        if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
-          st_st(a.zc, a.zctype, (long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K),
-                sum * zcm);
+        if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2]) {
+          const long long qc = (long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K);
+          if (wl_in(qc, (long long)a.cn[0] * a.cn[1] * a.cn[2], WL_DBG_RESID)) st_st(a.zc, a.zctype, qc, sum * zcm);
+        }
       }
       __syncthreads();
     }
@@ -226,6 +231,7 @@ __device__ __forceinline__ void restrict_body(const ResArgs& a, const uint3 bid,
     const long long r = t / c0;
     const int J = (int)(r % c1), K = (int)(r / c1);
     const long long b = 2LL * I + n0 * (2LL * J) + (D == 3 ? nn * (2LL * K) : 0);
+    if (!wl_in(b + 1 + n0 + (D == 3 ? nn : 0), g.nc, WL_DBG_RESTRICT)) continue;  // the last child
     // children (dx, dy, dz) at b + dx + n0 dy + nn dz
     float v[2][2][2];
     if (plain) {
@@ -365,8 +371,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, const uint3 bid) 
     const int xo = s_xo[col], yo = s_yo[row];
     float v = 0.f;
     if (xo >= 0 && yo >= 0 && zo >= 0) {
-      if (xin) v = ldf(xin, xo + yo + zo);
-      if (a.xc) v += xcm * ld_st(a.xc, a.xctype, s_cxo[col] + s_cyo[row] + czo);
+      if (xin && wl_in(xo + yo + zo, g.nc, WL_DBG_SWEEP)) v = ldf(xin, xo + yo + zo);
+      if (a.xc && wl_in(s_cxo[col] + s_cyo[row] + czo, (long long)cn0 * a.cn[1] * a.cn[2], WL_DBG_COARSE))
+        v += xcm * ld_st(a.xc, a.xctype, s_cxo[col] + s_cyo[row] + czo);
     }
     return v;
   };
@@ -382,6 +389,10 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, const uint3 bid) 
     c.ok = xo >= 0 && yo >= 0 && zo >= 0;
     if (!c.ok) return;
     const int q = xo + yo + zo;
+    if (!wl_in(q, g.nc, WL_DBG_SWEEP) || !wl_in(xo + yo + (zou >= 0 ? zou : zo), g.nc, WL_DBG_SWEEP)) {
+      c.ok = false;
+      return;
+    }
     c.z = ldf(zf, q);
     if constexpr (!std::is_same<T, float>::value) c.z *= a.zmul;
     const int xu = s_xo[col + 1], yu = s_yo[row + 1];
@@ -547,14 +558,18 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, const uint3 bid) 
           two_sum(a.ph[q + t], vv[t], sh, sl);
           sl += a.pl[q + t];
           fast_two_sum(sh, sl, nh, nl);
-          a.ph[q + t] = nh;
-          a.pl[q + t] = nl;
+          if (wl_in(q + t, g.nc, WL_DBG_SWEEP)) {
+            a.ph[q + t] = nh;
+            a.pl[q + t] = nl;
+          }
         }
       } else if (two && (n0 & 1) == 0) {
         st_pair(xout, q, v0, v1);
       } else {
-        xout[q] = from_f<T>(v0);
-        if (two) xout[q + 1] = from_f<T>(v1);
+        if (wl_in(q + (two ? 1 : 0), g.nc, WL_DBG_SWEEP)) {
+          xout[q] = from_f<T>(v0);
+          if (two) xout[q + 1] = from_f<T>(v1);
+        }
       }
     }
     if (more) load_black(k + 1);
@@ -689,8 +704,10 @@ __global__ void __launch_bounds__(256) k_coarse_cg(CoarseArgs a) {
 #pragma unroll
     for (int c = 0; c < D; ++c) {
       bool has;
-      const long long qu = nb_up(g, c, I[c], q, st[c], has);
-      const long long qm = nb_dn(g, c, I[c], q, st[c]);
+      long long qu = nb_up(g, c, I[c], q, st[c], has);
+      long long qm = nb_dn(g, c, I[c], q, st[c]);
+      if (!wl_in(qu, g.nc, WL_DBG_RESID)) qu = q;
+      if (!wl_in(qm, g.nc, WL_DBG_RESID)) qm = q;
       const double Lu = has ? (double)a.L[c][qu] : 0.0;
       const double Ll = (double)a.L[c][q];
       s += Lu * (v[q] - v[qu]) + Ll * (v[q] - v[qm]);
@@ -818,7 +835,7 @@ __device__ __forceinline__ void correct_body(const CorrArgs& a, const uint3 bid)
       const long long qm = nb_dn(g, c, I[c], q, st[c]);
       const float Ll = __ldg(a.L[c] + q);
       const float ulo = __ldg(a.u_in[c] + q) - s * Ll * dp(q, qm);
-      a.u_out[c][q] = ulo;
+      if (wl_in(q, g.nc, WL_DBG_CORRECT)) a.u_out[c][q] = ulo;
       if (a.cfl) {
         bool has;
         const long long qu = nb_up(g, c, I[c], q, st[c], has);
@@ -923,9 +940,11 @@ __device__ __forceinline__ void correct3_body(const CorrArgs& a, const uint3 bid
     const float lo1 = cur.u1 - s * cur.L1 * dp(wh[1], wl[1], cur.ymh, cur.yml);
     const float lo2 = cur.u2 - s * cur.L2 * dp(wh[1], wl[1], wh[0], wl[0]);
     if (inxy) {
-      a.u_out[0][q] = lo0;
-      a.u_out[1][q] = lo1;
-      a.u_out[2][q] = lo2;
+      if (wl_in(q, g.nc, WL_DBG_CORRECT)) {
+        a.u_out[0][q] = lo0;
+        a.u_out[1][q] = lo1;
+        a.u_out[2][q] = lo2;
+      }
     }
     if (CFL) {
       // corrected upper faces: x from the next lane, y loaded, z from the window
@@ -1920,6 +1939,7 @@ __device__ __forceinline__ int batch_block_p(const BatchGrid& bg, uint3& bid, un
   }
   const unsigned local = (unsigned)(b - bg.start[lo]), gx = bg.gx[lo], gy = bg.gy[lo];
   bid = make_uint3(local % gx, (local / gx) % gy, local / (gx * gy));
+  wl_in(bid.z, (unsigned)(bg.start[lo + 1] - bg.start[lo]) / (gx * gy), WL_DBG_BATCH);
   nb = (unsigned)(bg.start[lo + 1] - bg.start[lo]);
   return bg.slot[lo];
 }
@@ -2073,4 +2093,17 @@ int launch_batch_step_end(const BatchSlot* t, const BatchGrid& bg, cudaStream_t 
   return 0;
 }
 
+}  // namespace wl
+
+namespace wl {
+unsigned dbg_take_poisson() {
+#ifdef WL_DEBUG_BOUNDS
+  unsigned v = 0, z = 0;
+  cudaMemcpyFromSymbol(&v, wl_dbg_bits, sizeof(v));
+  cudaMemcpyToSymbol(wl_dbg_bits, &z, sizeof(z));
+  return v;
+#else
+  return 0u;
+#endif
+}
 }  // namespace wl

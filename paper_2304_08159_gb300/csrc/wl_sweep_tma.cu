@@ -86,6 +86,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
 }
 __device__ __forceinline__ void tma_load(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar,
                                          int rank) {
+  wl_in(x & 3, 1, WL_DBG_TMA);  // the inner coordinate's byte offset must be a multiple of 16
   if (rank == 3)
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -223,7 +224,9 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     ckey = kz;
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-      cv[r] = (kz >= 0 && cxy[r] >= 0)
+      cv[r] = (kz >= 0 && cxy[r] >= 0 &&
+               wl_in((long long)cxy[r] + (long long)a.cn[0] * a.cn[1] * kz, (long long)a.cn[0] * a.cn[1] * a.cn[2],
+                     WL_DBG_COARSE))
                   ? xcm * ld_st(a.xc, a.xctype, (long long)cxy[r] + (long long)a.cn[0] * a.cn[1] * kz)
                   : 0.f;
   };
@@ -298,12 +301,14 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   auto wload_x = [&](int p, float* v) {
     const long long o = wplane(p);
 #pragma unroll
-    for (int r = 0; r < NWX; ++r) v[r] = (o >= 0 && wxo[r] >= 0) ? a.xsrc[o + wxq[r]] : 0.f;
+    for (int r = 0; r < NWX; ++r)
+      v[r] = (o >= 0 && wxo[r] >= 0 && wl_in(o + wxq[r], g.nc, WL_DBG_SWEEP)) ? a.xsrc[o + wxq[r]] : 0.f;
   };
   auto wload_z = [&](int p, float* v) {
     const long long o = wplane(p);
 #pragma unroll
-    for (int r = 0; r < NWZ; ++r) v[r] = (o >= 0 && wzo[r] >= 0) ? a.zsrc[o + wzq[r]] : 0.f;
+    for (int r = 0; r < NWZ; ++r)
+      v[r] = (o >= 0 && wzo[r] >= 0 && wl_in(o + wzq[r], g.nc, WL_DBG_SWEEP)) ? a.zsrc[o + wzq[r]] : 0.f;
   };
   auto wstore_x = [&](int p, const float* v) {
     float* X = smf + Xs(xslot(p));
@@ -565,7 +570,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     if (!a.ph || k >= k1) return;
 #pragma unroll
     for (int r = 0; r < 2; ++r)
-      if (st_own[r]) {
+      if (st_own[r] && wl_in(q0[r] + (D == 3 ? qk * k : 0) + 1, g.nc, WL_DBG_SWEEP)) {
         const long long q = q0[r] + (D == 3 ? qk * k : 0);
         hph[r] = *reinterpret_cast<const float2*>(a.ph + q);
         hpl[r] = *reinterpret_cast<const float2*>(a.pl + q);
@@ -575,6 +580,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       if (!st_own[r]) continue;
+      if (!wl_in(q0[r] + (D == 3 ? qk * k : 0) + 1, g.nc, WL_DBG_SWEEP)) continue;
       const float2 v = *reinterpret_cast<const float2*>(smf + Xk + est[r]);
       const long long q = q0[r] + (D == 3 ? qk * k : 0);
       if (a.ph) {
@@ -863,7 +869,8 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
         div += uyp - U1[c];
         div += uzp - (A0 + LY::oU2)[c];
         zv[h] = div * inv;
-        if (in) a.z[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = zv[h];
+        const long long qz = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k);
+        if (in && wl_in(qz, g.nc, WL_DBG_RESID)) a.z[qz] = zv[h];
       } else {
         zv[h] = (B0 + LY::oZ)[c];
       }
@@ -966,7 +973,8 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
       const int gi = i0 + lane + 32 * h;
       float r = rr[h];
       if (inb[h]) {
-        if (a.rout) a.rout[(long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k)] = r;
+        const long long qr = (long long)gi + (long long)g.n[0] * ((long long)gj + (long long)g.n[1] * k);
+        if (a.rout && wl_in(qr, g.nc, WL_DBG_RESID)) a.rout[qr] = r;
         mbits = max(mbits, __float_as_uint(fabsf(r)));
       } else {
         r = 0.f;
@@ -982,9 +990,10 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
         const int cx = tid & 31, cy = tid >> 5;
         const float sum = s_r[2 * cy][2 * cx] + s_r[2 * cy + 1][2 * cx];
         const int I = (i0 >> 1) + cx, J = (j0 >> 1) + cy, K = k >> 1;
-        if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2])
-          st_st(a.zc, a.zctype, (long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K),
-                sum * a.zcmul);
+        const long long qc = (long long)I + (long long)a.cn[0] * ((long long)J + (long long)a.cn[1] * K);
+        if (I < a.cn[0] && J < a.cn[1] && K < a.cn[2] &&
+            wl_in(qc, (long long)a.cn[0] * a.cn[1] * a.cn[2], WL_DBG_RESID))
+          st_st(a.zc, a.zctype, qc, sum * a.zcmul);
       }
     }
     __syncthreads();
@@ -1196,4 +1205,17 @@ int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStre
   return 0;
 }
 
+}  // namespace wl
+
+namespace wl {
+unsigned dbg_take_sweep() {
+#ifdef WL_DEBUG_BOUNDS
+  unsigned v = 0, z = 0;
+  cudaMemcpyFromSymbol(&v, wl_dbg_bits, sizeof(v));
+  cudaMemcpyToSymbol(wl_dbg_bits, &z, sizeof(z));
+  return v;
+#else
+  return 0u;
+#endif
+}
 }  // namespace wl

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libwl.so")
+# WL_LIB=debug selects the bounds-checked build (libwl_debug.so) for the whole process
+LIB_PATH = os.path.join(HERE, "libwl_debug.so" if os.environ.get("WL_LIB") == "debug" else "libwl.so")
+DEBUG_LIB_PATH = os.path.join(HERE, "libwl_debug.so")
 
 WL_OK = 0
 WL_EINVAL = -1
@@ -23,6 +25,7 @@ WL_ECUDA = -3
 WL_ENONFINITE = -4
 WL_ETIMEOUT = -5
 WL_WNOTCONV = 1
+WL_NODEBUG = 2
 
 WL_FIELD_U = 0
 WL_FIELD_P = 1
@@ -53,6 +56,7 @@ EXPORTS = (
     "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split",
     "wl_state_bytes", "wl_save", "wl_load", "wl_get_metrics",
     "wl_batch_create", "wl_batch_step", "wl_batch_destroy", "wl_batch_last_error", "wl_event_elapsed",
+    "wl_debug_bounds",
 )
 METRIC_RING, METRIC_FIELDS = 1024, 13
 METRICS = ("step", "time", "dt", "vcycles1", "vcycles2", "resid1", "resid2", "cfl", "ke", "maxdiv", "F0", "F1", "F2")
@@ -132,6 +136,7 @@ def load(path: str = LIB_PATH):
         "wl_batch_destroy": (None, [ctypes.c_void_p]),
         "wl_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
         "wl_event_elapsed": (I, [P, P, ctypes.POINTER(ctypes.c_float)]),
+        "wl_debug_bounds": (I, [H, ctypes.POINTER(ctypes.c_uint)]),
         "wl_save": (I, [H, P, ctypes.c_size_t, I]),
         "wl_load": (I, [H, P, ctypes.c_size_t, I]),
     }
@@ -274,6 +279,13 @@ def wl_step_batch(handles, nsteps, stream=None):
     """Advance the sims `handles` (wl_handle values) by nsteps each, together (see include/wl.h)."""
     arr = (ctypes.c_void_p * len(handles))(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
     return load().wl_step_batch(arr, len(handles), int(nsteps), stream)
+
+
+def wl_debug_bounds(h):
+    """(rc, flags) of the bounds-checked build's index checks and canaries (see wl.h)."""
+    f = ctypes.c_uint(0)
+    rc = load().wl_debug_bounds(h, ctypes.byref(f))
+    return rc, f.value
 
 
 def wl_event_elapsed(start, end):

@@ -20,5 +20,5 @@ def _build_native():
     from paper_2304_08159_gb300 import build
     import oracle
 
-    build.build()
+    build.build_all()
     oracle.build()

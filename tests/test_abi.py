@@ -82,3 +82,15 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "liboracle" not in text and "wl_oracle" not in text, f
+
+
+def test_debug_library_exports_the_same_symbols(lib):
+    """The bounds-checked build (libwl_debug.so) exports every declared entry point too."""
+    import ctypes
+
+    from paper_2304_08159_gb300 import build, wl
+
+    build.build(debug=True)
+    dbg = ctypes.CDLL(wl.DEBUG_LIB_PATH)
+    for name in _declared():
+        assert hasattr(dbg, name), name
