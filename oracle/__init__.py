@@ -171,6 +171,8 @@ class Oracle:
             self.lib.or_set_body_nodes(self.h, _dp(nodes))
         self.ncell = int(np.prod(self.dims))
         self.shape = tuple(reversed(self.dims))
+        # body parameters the adjoint differentiates: circle/sphere (R, c_0, ..); torus (R, r, c_x, c_y, c_z)
+        self.n_theta = 5 if kind == 2 else self.D + 1
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -395,28 +397,29 @@ class Oracle:
 
     def force_adjoint(self, p, Fbar):
         """Force of p and its adjoint: (F, pbar, theta-cotangent of the force weights)."""
-        F, pb, tb = np.zeros(3), np.zeros(self.ncell), np.zeros(4)
+        F, pb, tb = np.zeros(3), np.zeros(self.ncell), np.zeros(5)
         fb = np.zeros(3)
         fb[: self.D] = Fbar
         self.lib.or_force_adjoint(self.h, _dp(self._vec(p, 1)), _dp(fb), _dp(F), _dp(pb), _dp(tb))
-        return F[: self.D], pb.reshape(self.shape), tb[: self.D + 1]
+        return F[: self.D], pb.reshape(self.shape), tb[: self.n_theta]
 
     def moments_adjoint(self, mu0bar, Lbar, mu1bar):
-        tb = np.zeros(4)
+        tb = np.zeros(5)
         D = self.D
         self.lib.or_moments_adjoint(self.h, _dp(self._vec(mu0bar, D)), _dp(self._vec(Lbar, D)),
                                     _dp(self._vec(mu1bar, D * D)), _dp(tb))
-        return tb[: D + 1]
+        return tb[: self.n_theta]
 
     def rollout_grad(self, nsteps, dt, gF, tol=1e-12):
         """nsteps steps at fixed dt from the current state (which advances); returns the
         forces after each step (nsteps x D) and dJ/dtheta for J = sum_n gF[n] . F_n,
-        theta = (R, c_0, .., c_{D-1}) of the circle/sphere."""
+        theta = (R, c_0, .., c_{D-1}) of the circle/sphere or (R, r, c_x, c_y, c_z) of the
+        torus."""
         D = self.D
         g = np.ascontiguousarray(gF, dtype=np.float64).reshape(-1)
         assert g.size == nsteps * D
-        F, tb = np.zeros(nsteps * D), np.zeros(4)
+        F, tb = np.zeros(nsteps * D), np.zeros(5)
         rc = self.lib.or_rollout_grad(self.h, int(nsteps), float(dt), float(tol), _dp(g), _dp(F), _dp(tb))
         if rc != 0:
-            raise ValueError("rollout_grad needs a circle/sphere body, nsteps >= 1 and dt > 0")
-        return F.reshape(nsteps, D), tb[: D + 1]
+            raise ValueError("rollout_grad needs a circle/sphere or torus body, nsteps >= 1 and dt > 0")
+        return F.reshape(nsteps, D), tb[: self.n_theta]

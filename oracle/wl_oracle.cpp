@@ -790,7 +790,8 @@ double cfl(const OSim& s) {
 
 // ===========================================================================
 // Reverse-mode derivative (adjoint) of the time step at a fixed dt with respect to the
-// circle/sphere parameters theta = (R, c_0, .., c_{D-1}) (the differentiable-solver
+// body parameters theta (circle/sphere (R, c_0, .., c_{D-1}); torus (R, r, c_0, c_1, c_2):
+// the body enters through its signed distance, Section 2) (the differentiable-solver
 // use of the method, Section 1).  Every routine is the transpose of the forward routine
 // it names, written out from that routine's arithmetic.  Where the forward is not
 // differentiable (the limiter's switch points, the upwind switch at a = 0) the
@@ -1031,18 +1032,58 @@ void project_adjoint(const OSim& s, const vec& x, const vec* ubar_out, const vec
         }
 }
 
-// Derivatives of the circle/sphere distance d = |x - c| - R and normal n = (x - c)/|x - c|
-// at x with respect to theta = (R, c_0, .., c_{D-1}): dd[t], dn[j][t].
-void sdf_theta_grad(const OSim& s, const double* x, double* dd, double dn[3][4]) {
-  double rho2 = 0.0, n[3] = {0.0, 0.0, 0.0};
-  for (int d = 0; d < s.D; ++d) rho2 += (x[d] - s.center[d]) * (x[d] - s.center[d]);
-  const double rho = std::sqrt(rho2);
-  for (int d = 0; d < s.D; ++d) n[d] = rho > 0.0 ? (x[d] - s.center[d]) / rho : 0.0;
-  dd[0] = -1.0;
-  for (int j = 0; j < 3; ++j) dn[j][0] = 0.0;
+// Number of body parameters theta: circle/sphere (R, c_0, .., c_{D-1}); torus
+// (R, r, c_0, c_1, c_2) with R the ring radius in the y-z plane and r the tube radius.
+int n_theta(const OSim& s) { return s.body_kind == 2 ? 5 : s.D + 1; }
+
+// Derivatives of the body's signed distance d and its outward normal n = grad d at x with
+// respect to theta: dd[t], dn[j][t].  Moving the centre by dc moves the field by dc, so
+// dd/dc_k = -n_k and dn_j/dc_k = -H_jk (H the Hessian of d).
+//   circle/sphere: d = |x - c| - R, n = (x - c)/rho, rho = |x - c|;
+//     dd/dR = -1, dn/dR = 0, H_jk = (delta_jk - n_j n_k)/rho.
+//   torus: with (a, b, c) = x - c, rho = sqrt(b^2 + c^2), e = (b, c)/rho, q = rho - R,
+//     s = sqrt(a^2 + q^2): d = s - r, n = (a/s, (q/s) e);
+//     dd/dR = -q/s, dd/dr = -1, dn_0/dR = a q/s^3, dn_e/dR = -(a^2/s^3) e, dn/dr = 0;
+//     H_00 = q^2/s^3, H_0e = -a q e/s^3, H_ee' = e e' a^2/s^3 + (q/s)(delta_ee' - e e')/rho.
+void sdf_theta_grad(const OSim& s, const double* x, double* dd, double dn[3][5]) {
+  for (int t = 0; t < 5; ++t) {
+    dd[t] = 0.0;
+    for (int j = 0; j < 3; ++j) dn[j][t] = 0.0;
+  }
+  double H[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, n[3] = {0.0, 0.0, 0.0};
+  int c0 = 1;  // index of c_0 in theta
+  if (s.body_kind == 2) {
+    const double a = x[0] - s.center[0], b = x[1] - s.center[1], c = x[2] - s.center[2];
+    const double rho = std::sqrt(b * b + c * c), q = rho - s.radius, sd = std::sqrt(a * a + q * q);
+    const double e[3] = {0.0, rho > 0.0 ? b / rho : 0.0, rho > 0.0 ? c / rho : 0.0};
+    if (sd > 0.0) {
+      const double s3 = sd * sd * sd;
+      n[0] = a / sd;
+      n[1] = q / sd * e[1];
+      n[2] = q / sd * e[2];
+      dd[0] = -q / sd;
+      dn[0][0] = a * q / s3;
+      for (int j = 1; j < 3; ++j) dn[j][0] = -(a * a / s3) * e[j];
+      H[0][0] = q * q / s3;
+      for (int j = 1; j < 3; ++j) H[0][j] = H[j][0] = -a * q * e[j] / s3;
+      for (int j = 1; j < 3; ++j)
+        for (int k = 1; k < 3; ++k)
+          H[j][k] = e[j] * e[k] * a * a / s3 + (rho > 0.0 ? (q / sd) * ((j == k ? 1.0 : 0.0) - e[j] * e[k]) / rho : 0.0);
+    }
+    dd[1] = -1.0;
+    c0 = 2;
+  } else {
+    double rho2 = 0.0;
+    for (int d = 0; d < s.D; ++d) rho2 += (x[d] - s.center[d]) * (x[d] - s.center[d]);
+    const double rho = std::sqrt(rho2);
+    for (int d = 0; d < s.D; ++d) n[d] = rho > 0.0 ? (x[d] - s.center[d]) / rho : 0.0;
+    dd[0] = -1.0;
+    for (int j = 0; j < s.D; ++j)
+      for (int k = 0; k < s.D; ++k) H[j][k] = rho > 0.0 ? ((j == k ? 1.0 : 0.0) - n[j] * n[k]) / rho : 0.0;
+  }
   for (int k = 0; k < s.D; ++k) {
-    dd[1 + k] = -n[k];
-    for (int j = 0; j < s.D; ++j) dn[j][1 + k] = rho > 0.0 ? -((j == k ? 1.0 : 0.0) - n[j] * n[k]) / rho : 0.0;
+    dd[c0 + k] = -n[k];
+    for (int j = 0; j < s.D; ++j) dn[j][c0 + k] = -H[j][k];
   }
 }
 
@@ -1080,9 +1121,9 @@ void force_adjoint(const OSim& s, const vec& p, const double* Fbar, double* F, v
         }
         pbar[q] -= gw;
         wg += gw;
-        double ddt[4], dn[3][4];
+        double ddt[5], dn[3][5];
         sdf_theta_grad(s, x, ddt, dn);
-        for (int t = 0; t <= s.D; ++t)
+        for (int t = 0; t < n_theta(s); ++t)
           for (int dd = 0; dd < s.D; ++dd)
             tb[t] -= Fbar[dd] * pp * (dn[dd][t] * K + nrm[dd] * Kp * ddt[t]);
       }
@@ -1107,10 +1148,10 @@ void moments_adjoint(const OSim& s, const vec* mu0bar, const vec* Lbar, const ve
           const double K = 0.5 * (1.0 + std::cos(M_PI * sc));
           const bool bnd = !is_per(s, c) && I[c] == 0;
           const double g0 = mu0bar[c][q] + (bnd ? 0.0 : Lbar[c][q]);
-          double ddt[4], dn[3][4];
+          double ddt[5], dn[3][5];
           sdf_theta_grad(s, x, ddt, dn);
           const double k1 = s.eps * K1(sc), k1p = -sc * K;
-          for (int t = 0; t <= s.D; ++t) {
+          for (int t = 0; t < n_theta(s); ++t) {
             tb[t] += g0 * K / s.eps * ddt[t];
             for (int jj = 0; jj < s.D; ++jj) tb[t] += mu1bar[c][jj][q] * (k1p * nrm[jj] * ddt[t] + k1 * dn[jj][t]);
           }
@@ -1119,7 +1160,7 @@ void moments_adjoint(const OSim& s, const vec* mu0bar, const vec* Lbar, const ve
 
 // nsteps full steps at fixed dt from the current state, then the gradient of
 // J = sum_n gF[n] . F_n (F_n the pressure force after step n) with respect to theta.
-// F receives nsteps * D forces, tb D + 1 values.  The state advances.
+// F receives nsteps * D forces, tb n_theta values.  The state advances.
 void rollout_grad(OSim& s, int nsteps, double dt, double tol, const double* gF, double* F, double* tb) {
   const int D = s.D;
   std::vector<std::vector<vec>> U0(nsteps), UP(nsteps);
@@ -1142,7 +1183,7 @@ void rollout_grad(OSim& s, int nsteps, double dt, double tol, const double* gF, 
     s.nsteps += 1;
   }
   s.dt = dt;
-  for (int t = 0; t <= D; ++t) tb[t] = 0.0;
+  for (int t = 0; t < n_theta(s); ++t) tb[t] = 0.0;
   vec mu0bar[3], Lbar[3], mu1bar[3][3], ub[3];
   for (int c = 0; c < D; ++c) {
     mu0bar[c].assign(s.ncell, 0.0);
@@ -1654,11 +1695,11 @@ void or_project_adjoint(void* h, const double* vin, double w, double dt, double 
 }
 
 // Force of the pressure p (cells) and its adjoint for Fbar: pbar (cells) and the
-// theta-cotangent of the force weights (D + 1 values, circle/sphere only).
+// theta-cotangent of the force weights (n_theta values: circle/sphere D + 1, torus 5).
 void or_force_adjoint(void* h, const double* p, const double* Fbar, double* F, double* pbar, double* tb) {
   OSim* s = (OSim*)h;
   vec pp(p, p + s->ncell), pb;
-  for (int t = 0; t <= s->D; ++t) tb[t] = 0.0;
+  for (int t = 0; t < n_theta(*s); ++t) tb[t] = 0.0;
   force_adjoint(*s, pp, Fbar, F, pb, tb);
   std::memcpy(pbar, pb.data(), s->ncell * sizeof(double));
 }
@@ -1674,14 +1715,15 @@ void or_moments_adjoint(void* h, const double* mu0bar, const double* Lbar, const
       m1[c][j] = (j < s->D) ? vec(mu1bar + (c * s->D + j) * s->ncell, mu1bar + (c * s->D + j + 1) * s->ncell)
                             : vec(s->ncell, 0.0);
   }
-  for (int t = 0; t <= s->D; ++t) tb[t] = 0.0;
+  for (int t = 0; t < n_theta(*s); ++t) tb[t] = 0.0;
   moments_adjoint(*s, m0, Lb, m1, tb);
 }
 
 // Differentiated rollout (rollout_grad): returns 0, or -1 unless the body is a circle/sphere.
 int or_rollout_grad(void* h, int nsteps, double dt, double tol, const double* gF, double* F, double* tb) {
   OSim* s = (OSim*)h;
-  if (s->body_kind != 1 || nsteps < 1 || !(dt > 0.0) || s->exit_bc) return -1;
+  if (!(s->body_kind == 1 || (s->body_kind == 2 && s->D == 3)) || nsteps < 1 || !(dt > 0.0) || s->exit_bc)
+    return -1;
   rollout_grad(*s, nsteps, dt, tol, gF, F, tb);
   return 0;
 }

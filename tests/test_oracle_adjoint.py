@@ -128,6 +128,63 @@ def test_rollout_grad_matches_central_differences(case, nsteps):
     assert np.abs(tb - fd).max() <= 1e-5 * scale, (tb, fd)
 
 
+TORUS = dict(dims=(16, 18, 18), nu=0.04, U=(1.0, 0.05, -0.05), periodic=0,
+             body=dict(kind=2, center=(7.6, 8.7, 9.2), radius=4.3, radius2=1.9))
+
+
+def _J_torus(theta, nsteps, dt, gF):
+    c = dict(TORUS)
+    c["body"] = dict(kind=2, radius=theta[0], radius2=theta[1], center=tuple(theta[2:]))
+    o = _make(c)
+    F, tb = o.rollout_grad(nsteps, dt, gF, tol=1e-13)
+    return float((F * gF).sum()), tb
+
+
+def test_torus_rollout_grad_matches_central_differences():
+    """The torus (ring radius R in the y-z plane, tube radius r, centre c): dJ/d(R, r, c)
+    over a 2-step rollout against central differences of J with the body changed
+    (h = 1e-5), every one of the five components."""
+    nsteps, dt = 2, 0.3
+    gF = np.random.default_rng(12).standard_normal((nsteps, 3))
+    b = TORUS["body"]
+    theta = np.array([b["radius"], b["radius2"]] + list(b["center"]))
+    J0, tb = _J_torus(theta, nsteps, dt, gF)
+    assert tb.shape == (5,)
+    h = 1e-5
+    fd = np.zeros(5)
+    for t in range(5):
+        e = np.zeros(5)
+        e[t] = h
+        fd[t] = (_J_torus(theta + e, nsteps, dt, gF)[0] - _J_torus(theta - e, nsteps, dt, gF)[0]) / (2 * h)
+    print("torus dJ/dtheta", tb, "FD", fd)
+    assert np.abs(tb - fd).max() <= 1e-5 * np.abs(fd).max(), (tb, fd)
+
+
+def test_torus_force_adjoint_theta_matches_central_differences():
+    """The torus force weights' theta part alone (p fixed): every component of every force
+    direction against central differences of the discrete force (h = 1e-6)."""
+    rng = np.random.default_rng(13)
+    b = TORUS["body"]
+    theta = np.array([b["radius"], b["radius2"]] + list(b["center"]))
+    p = rng.standard_normal(tuple(reversed(TORUS["dims"])))
+
+    def make(th):
+        c = dict(TORUS)
+        c["body"] = dict(kind=2, radius=th[0], radius2=th[1], center=tuple(th[2:]))
+        return _make(c)
+
+    for d in range(3):
+        Fbar = np.zeros(3)
+        Fbar[d] = 1.0
+        _, _, tb = make(theta).force_adjoint(p, Fbar)
+        h = 1e-6
+        for t in range(5):
+            e = np.zeros(5)
+            e[t] = h
+            fd = (make(theta + e).force_adjoint(p, Fbar)[0][d] - make(theta - e).force_adjoint(p, Fbar)[0][d]) / (2 * h)
+            assert abs(tb[t] - fd) <= 1e-6 * max(np.abs(tb).max(), 1e-12), (d, t, tb[t], fd)
+
+
 def test_force_adjoint_buoyancy_closed_form():
     """Hydrostatic p = g y around a circle: F_y = -g pi R^2 up to O(eps^2/R^2), so
     dF_y/dR = -2 pi R g and dF_y/dc = 0.  The force adjoint's theta part (p held fixed)
