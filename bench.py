@@ -479,7 +479,8 @@ def adjoint_bench(tol):
     diameter, U = 1, fixed dt 0.1, mean drag coefficient over 50 steps differentiated with
     respect to (R, cx, cy) by the hand-written adjoint with checkpoints every 10 steps.
     Wall time of the recorded forward rollout and of the backward pass (segment
-    recomputation + adjoint), both host-driven and synchronising."""
+    recomputation + adjoint): step graphs, the adjoint solves' V-cycles in WHILE nodes,
+    one synchronisation at the end of each pass (graph builds included)."""
     import numpy as np
 
     from paper_2304_08159_gb300 import Sim

@@ -394,14 +394,16 @@ int wl_wait_probe(double seconds, double* elapsed_ms);
 /* ---- Gradients of the pressure force with respect to the body (the differentiable
  * use of the solver, Section 1; the body enters through its signed-distance function,
  * Section 2).  theta = (R, c_0, .., c_{D-1}): the radius and centre of a circle/sphere
- * body (WL_BODY_SPHERE).  The derivative is taken with dt held fixed (wl_opts.dt_fixed
- * > 0 is required: the CFL rule is a maximum over the field and is not differentiated),
+ * body (WL_BODY_SPHERE); theta = (R, r, c_x, c_y, c_z): the ring radius (y-z plane),
+ * tube radius and centre of a torus (WL_BODY_TORUS, 3-D).  The derivative is taken with
+ * dt held fixed (wl_opts.dt_fixed > 0 is required: the CFL rule is a maximum over the
+ * field and is not differentiated),
  * each projection differentiated as the exact projection, and, where the convection
  * scheme is not differentiable (the limiter's switch points, the upwind switch), the
  * derivative of the branch the step takes.
  *
  * Memory: (nsteps/every + 1) checkpoints of the velocity and pressure, the recorded
- * intermediates of `every` steps (2D + 2 fields each) and 6D + 1 adjoint fields, in a
+ * intermediates of `every` steps (2D + 2 fields each) and 6D + 2 adjoint fields, in a
  * gradient workspace of wl_grad_workspace_bytes() bytes (256-byte aligned), supplied by
  * the caller or (workspace = NULL) allocated by the library and freed by the next
  * wl_grad_forward or wl_destroy.  Long horizons fit in memory by recomputing each
@@ -411,21 +413,26 @@ int wl_wait_probe(double seconds, double* elapsed_ms);
  * steps; 0 on bad arguments. */
 size_t wl_grad_workspace_bytes(wl_handle h, int nsteps, int every);
 
-/* Advance nsteps time steps from the current state (host-driven, the same kernels as
- * wl_step), record the pressure force after each step into F (host, nsteps*D doubles,
- * F_d = -sum (p - pbar) n_d K_eps(d) as wl_forces) and keep the checkpoints for
- * wl_grad_backward.  Returns WL_EINVAL unless the body is a circle/sphere and dt is
- * fixed; WL_WNOTCONV / WL_ENONFINITE as wl_step; WL_ENOMEM if the supplied workspace
- * is too small or unaligned.  Synchronises. */
+/* Advance nsteps time steps from the current state (the step graph of wl_step, or its
+ * host-driven sequence with wl_opts.use_graph = 0: the same bits), record the pressure
+ * force after each step into F (host, nsteps*D doubles, F_d = -sum (p - pbar) n_d
+ * K_eps(d) as wl_forces) and keep the checkpoints for wl_grad_backward.  Returns
+ * WL_EINVAL unless the body is a circle/sphere or torus and dt is fixed; WL_WNOTCONV /
+ * WL_ENONFINITE as wl_step; WL_ENOMEM if the supplied workspace is too small or
+ * unaligned.  Synchronises once, at the end. */
 int wl_grad_forward(wl_handle h, int nsteps, int every, void* workspace, size_t workspace_bytes, double* F);
 
 /* Gradient of J = sum_n gF[n] . F_n (gF: host, nsteps*D doubles, the cotangents of the
- * forces wl_grad_forward recorded) with respect to theta into theta_bar (host, D + 1
- * doubles: dJ/dR, dJ/dc_0, ..).  Recomputes every segment from its checkpoint and runs
- * the adjoint of each step backwards (adjoint Poisson solves by the same multigrid to
- * 1e-7 relative); the sim's state is the one after the forward rollout again on
- * return.  Returns WL_WNOTCONV (theta_bar still written) if an adjoint solve hit
- * max_vcycles.  Synchronises. */
+ * forces wl_grad_forward recorded) with respect to theta into theta_bar (host; D + 1
+ * doubles dJ/dR, dJ/dc_0, .. for a circle/sphere, 5 doubles dJ/d(R, r, c_x, c_y, c_z)
+ * for a torus).  Recomputes every segment from its checkpoint and runs the adjoint of
+ * each step backwards (adjoint Poisson solves by the same multigrid to 1e-7 relative,
+ * their V-cycles in a graph WHILE node the device ends); the sim's state is the one
+ * after the forward rollout again on return.  Deterministic: the same bits on every run
+ * (the transposed scatters are gathers, the reductions run in a fixed order).  Returns
+ * WL_WNOTCONV (theta_bar still written) if an adjoint solve hit max_vcycles,
+ * WL_ENONFINITE (the sim poisoned) on a non-finite adjoint residual.  Synchronises once,
+ * at the end. */
 int wl_grad_backward(wl_handle h, const double* gF, double* theta_bar);
 
 /* Levels of the multigrid hierarchy and the dims of level l (dims[3]). */

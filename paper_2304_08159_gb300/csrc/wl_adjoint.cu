@@ -1,11 +1,12 @@
 // Reverse-mode derivative (adjoint) of the time step at a fixed dt with respect to the
-// circle/sphere parameters theta = (R, c_0, .., c_{D-1}): the differentiable use of the
-// solver (Section 1; the body enters through its signed-distance function, Section 2).
+// body parameters theta, circle/sphere (R, c_0, .., c_{D-1}) or torus (R, r, c_x, c_y,
+// c_z): the differentiable use of the solver (Section 1; the body enters through its
+// signed-distance function, Section 2).
 //
 // Each kernel is the transpose of a forward kernel's arithmetic (same FP32 values, the
 // same branch of the limiter and of the upwind switch as the forward takes):
 //   k_adj_convdiff    convdiff! (k_stage's fluxes): per face flux, F' = r'[I] - r'[I-e_j],
-//                     scattered to the velocities the flux reads (atomics; BC mapping:
+//                     gathered by every face from the fluxes that read it (BC mapping:
 //                     periodic wrap, tangential clamp, prescribed normal faces dropped)
 //   k_adj_stage_local the mu0 blend of BDIM!: f' = s mu0 v'
 //   k_adj_band        the mu1 term of BDIM! on the body band, its mu0 / mu1 cotangents
@@ -37,7 +38,7 @@ __device__ __forceinline__ long long map_face(const Grid& g, int c, const int* I
     int q = I[d];
     const int n = g.n[d];
     if (is_per(g, d)) {
-      q = (q < 0) ? q + n : ((q >= n) ? q - n : q);
+      q = wrap_per(q, n);
     } else {
       if (d == c && (q <= 0 || q >= n)) return -1;
       q = q < 0 ? 0 : (q >= n ? n - 1 : q);
@@ -47,27 +48,93 @@ __device__ __forceinline__ long long map_face(const Grid& g, int c, const int* I
   return cell_index(g, I[0], I[1], D == 3 ? I[2] : 0);
 }
 
-// circle / sphere: d = |x - c| - R, n = (x - c)/|x - c|, and their derivatives with
-// respect to theta = (R, c_0, .., c_{D-1}): dd[t], dn[j][t].
+// Logical positions along direction d that component c's face index K_d stands for:
+// the periodic images within [-2, n+1], the clamped positions past a wall for a
+// tangential direction, none for a prescribed normal face.  At most 5 (n = 1).
+__device__ __forceinline__ int face_preimages(const Grid& g, int c, int d, int k, int* out) {
+  const int n = g.n[d];
+  int m = 0;
+  if (is_per(g, d)) {
+    for (int p = k - ((k + 2) / n) * n; p <= n + 1 && m < 5; p += n) out[m++] = p;
+  } else if (d == c) {
+    if (k >= 1) out[m++] = k;
+  } else {
+    const int lo = k == 0 ? -2 : k, hi = k == n - 1 ? n + 1 : k;
+    for (int p = lo; p <= hi && m < 5; ++p) out[m++] = p;
+  }
+  return m;
+}
+
+// Number of body parameters theta: circle/sphere (R, c_0, .., c_{D-1}); torus
+// (R, r, c_x, c_y, c_z), R the ring radius in the y-z plane, r the tube radius.
+__host__ __device__ __forceinline__ int n_theta(int kind, int D) { return kind == 2 ? 5 : D + 1; }
+
+// The body's signed distance d and normal n at x, and their derivatives with respect to
+// theta: dd[t], dn[j][t].  A centre shift moves the field: dd/dc_k = -n_k, dn_j/dc_k =
+// -H_jk with H the Hessian of d.
+//   circle/sphere: d = |x - c| - R, n = (x - c)/rho; dd/dR = -1, H = (I - n n^T)/rho.
+//   torus: (a, b, c) = x - c, rho = |(b, c)|, e = (b, c)/rho, q = rho - R, s = |(a, q)|:
+//     d = s - r, n = (a, q e)/s; dd/dR = -q/s, dd/dr = -1; dn_0/dR = a q/s^3,
+//     dn_e/dR = -a^2 e/s^3; H_00 = q^2/s^3, H_0e = -a q e/s^3,
+//     H_ee' = a^2 e e'/s^3 + (q/s)(delta_ee' - e e')/rho.
 template <int D>
-__device__ double sdf_theta(const Body& b, const double* x, double* n, double* dd, double (*dn)[4]) {
-  double r2 = 0.0;
+__device__ double sdf_theta(const Body& b, const double* x, double* n, double* dd, double (*dn)[5]) {
 #pragma unroll
-  for (int d = 0; d < D; ++d) r2 += (x[d] - b.c[d]) * (x[d] - b.c[d]);
-  const double r = sqrt(r2);
+  for (int t = 0; t < 5; ++t) {
+    dd[t] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) dn[j][t] = 0.0;
+  }
+  double H[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
   n[0] = n[1] = n[2] = 0.0;
+  double dist;
+  int c0 = 1;
+  if (D == 3 && b.kind == 2) {
+    const double a = x[0] - b.c[0], bb = x[1] - b.c[1], cc = x[2] - b.c[2];
+    const double rho = sqrt(bb * bb + cc * cc), q = rho - b.r1, sd = sqrt(a * a + q * q);
+    const double e[3] = {0.0, rho > 0.0 ? bb / rho : 0.0, rho > 0.0 ? cc / rho : 0.0};
+    if (sd > 0.0) {
+      const double s3 = sd * sd * sd;
+      n[0] = a / sd;
+      n[1] = q / sd * e[1];
+      n[2] = q / sd * e[2];
+      dd[0] = -q / sd;
+      dn[0][0] = a * q / s3;
+      dn[1][0] = -(a * a / s3) * e[1];
+      dn[2][0] = -(a * a / s3) * e[2];
+      H[0][0] = q * q / s3;
 #pragma unroll
-  for (int d = 0; d < D; ++d) n[d] = r > 0.0 ? (x[d] - b.c[d]) / r : 0.0;
-  dd[0] = -1.0;
+      for (int j = 1; j < 3; ++j) H[0][j] = H[j][0] = -a * q * e[j] / s3;
 #pragma unroll
-  for (int j = 0; j < 3; ++j) dn[j][0] = 0.0;
+      for (int j = 1; j < 3; ++j)
+#pragma unroll
+        for (int k = 1; k < 3; ++k)
+          H[j][k] = e[j] * e[k] * a * a / s3 + (rho > 0.0 ? (q / sd) * ((j == k ? 1.0 : 0.0) - e[j] * e[k]) / rho : 0.0);
+    }
+    dd[1] = -1.0;
+    c0 = 2;
+    dist = sd - b.r2;
+  } else {
+    double r2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) r2 += (x[d] - b.c[d]) * (x[d] - b.c[d]);
+    const double r = sqrt(r2);
+#pragma unroll
+    for (int d = 0; d < D; ++d) n[d] = r > 0.0 ? (x[d] - b.c[d]) / r : 0.0;
+    dd[0] = -1.0;
+#pragma unroll
+    for (int j = 0; j < D; ++j)
+#pragma unroll
+      for (int k = 0; k < D; ++k) H[j][k] = r > 0.0 ? ((j == k ? 1.0 : 0.0) - n[j] * n[k]) / r : 0.0;
+    dist = r - b.r1;
+  }
 #pragma unroll
   for (int k = 0; k < D; ++k) {
-    dd[1 + k] = -n[k];
+    dd[c0 + k] = -n[k];
 #pragma unroll
-    for (int j = 0; j < D; ++j) dn[j][1 + k] = r > 0.0 ? -((j == k ? 1.0 : 0.0) - n[j] * n[k]) / r : 0.0;
+    for (int j = 0; j < D; ++j) dn[j][c0 + k] = -H[j][k];
   }
-  return r - b.r1;
+  return dist;
 }
 
 // the body's bounding box of cells/faces within `pad` of the band
@@ -76,8 +143,9 @@ void band_box(int D, const Grid& g, const Body& b, double pad, int* lo, int* hi)
     lo[d] = 0;
     hi[d] = 1;
     if (d >= D) continue;
-    lo[d] = (int)fmax(0.0, floor(b.c[d] - b.r1 - b.eps - pad));
-    hi[d] = (int)fmin((double)g.n[d], ceil(b.c[d] + b.r1 + b.eps + pad) + 1.0);
+    const double ext = b.kind == 2 ? (d == 0 ? b.r2 : b.r1 + b.r2) : b.r1;  // torus: tube across x, ring in y-z
+    lo[d] = (int)fmax(0.0, floor(b.c[d] - ext - b.eps - pad));
+    hi[d] = (int)fmin((double)g.n[d], ceil(b.c[d] + ext + b.eps + pad) + 1.0);
     if (hi[d] < lo[d]) hi[d] = lo[d];
   }
 }
@@ -168,8 +236,15 @@ __global__ void __launch_bounds__(256) k_adj_setup_final(const double* part, int
         as->W[t - 1] = v;
     }
   }
-  if (threadIdx.x < 4) as->theta[threadIdx.x] = 0.0;
-  if (threadIdx.x == 0) as->mean = 0.0;
+  if (threadIdx.x < 5) as->theta[threadIdx.x] = 0.0;
+  if (threadIdx.x == 0) {
+    as->mean = 0.0;
+    as->bnorm_bits = 0u;
+    as->iter = 0;
+    as->total_iter = 0;
+    as->flags = 0;
+    as->rec_slot = 0;
+  }
 }
 
 int launch_adj_setup(int D, const Grid& g, const Body& b, const float* const* L, AdjState* as, double* part,
@@ -194,28 +269,30 @@ __global__ void __launch_bounds__(256) k_adj_force_theta(Grid g, Body b, const f
   const double pbar = *pmean;
   double gv[3] = {0.0, 0.0, 0.0};
   for (int d = 0; d < D; ++d) gv[d] = gF[d];
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int NT = n_theta(b.kind, D);
   const long long nbox = (long long)bx * by * bz;
   for (long long t = threadIdx.x; t < nbox; t += 256) {
     const int i = lo0 + (int)(t % bx);
     const long long r = t / bx;
     const int j = lo1 + (int)(r % by);
     const int k = lo2 + (int)(r / by);
-    double x[3] = {i + 0.5, j + 0.5, k + 0.5}, n[3], dd[4], dn[3][4];
+    double x[3] = {i + 0.5, j + 0.5, k + 0.5}, n[3], dd[5], dn[3][5];
     const double d = sdf_theta<D>(b, x, n, dd, dn);
     if (!(fabs(d) < b.eps)) continue;
     const double K = (1.0 + cospi(d / b.eps)) / (2.0 * b.eps);
     const double Kp = -3.141592653589793 * sinpi(d / b.eps) / (2.0 * b.eps * b.eps);
     const double pp = (double)p[cell_index(g, i, j, k)] - pbar;
 #pragma unroll
-    for (int tt = 0; tt <= D; ++tt) {
+    for (int tt = 0; tt < 5; ++tt) {
+      if (tt >= NT) break;
       double gw = 0.0;
 #pragma unroll
       for (int e = 0; e < D; ++e) gw += gv[e] * (dn[e][tt] * K + n[e] * Kp * dd[tt]);
       acc[tt] -= pp * gw;
     }
   }
-  for (int tt = 0; tt <= D; ++tt) {
+  for (int tt = 0; tt < NT; ++tt) {
     const double v = block_sum(acc[tt], sh);
     if (threadIdx.x == 0) as->theta[tt] += v;
   }
@@ -303,18 +380,30 @@ __global__ void __launch_bounds__(256) k_adj_mean_final(const double* part, int 
   double v = 0.0;
   for (int k = threadIdx.x; k < npart; k += 256) v += part[k];
   v = block_sum(v, sh);
-  if (threadIdx.x == 0) as->mean = as->Na > 0.0 ? v / as->Na : 0.0;
+  if (threadIdx.x == 0) {
+    as->mean = as->Na > 0.0 ? v / as->Na : 0.0;
+    as->bnorm_bits = 0u;
+  }
 }
 
 template <int D>
 __global__ void __launch_bounds__(256) k_adj_sub_mean(Grid g, const float* L0, const float* L1, const float* L2,
-                                                      const AdjState* as, float* rhs) {
+                                                      AdjState* as, float* rhs) {
   const float* L[3] = {L0, L1, L2};
   const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
-  if (q >= g.nc) return;
-  int I[3];
-  coords(g, q, I);
-  if (cell_active<D>(g, L, q, I)) rhs[q] = (float)((double)rhs[q] - as->mean);
+  float m = 0.f;  // |b| (the max-norm: order-free, so atomics keep it deterministic)
+  if (q < g.nc) {
+    int I[3];
+    coords(g, q, I);
+    if (cell_active<D>(g, L, q, I)) {
+      const float v = (float)((double)rhs[q] - as->mean);
+      rhs[q] = v;
+      m = fabsf(v);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&as->bnorm_bits, __float_as_uint(m));
 }
 
 int launch_adj_proj_rhs(int D, const Grid& g, const Body& b, const float* const* ub, const float* const* L,
@@ -417,130 +506,303 @@ int launch_adj_stage_local(int D, const Grid& g, const float* const* vb, const f
 // mu1 term on the band: out_c[I] += s sum_j mu1_j (f[I+e_j] - f[I-e_j])/2 with
 // mu1 = eps K1(d/eps) n.  Transpose: f'[I +- e_j] +-= s mu1_j v'/2 (BC-mapped), the mu0
 // cotangent s v' f[I] into mbar, and theta' += s v' (f[I+e_j] - f[I-e_j])/2 dmu1_j/dtheta
-// with d(eps K1(d/eps))/dd = -s K(s), s = d/eps.
+// with d(eps K1(d/eps))/dd = -s K(s), s = d/eps.  k_adj_band takes the band faces' own
+// terms (mbar, theta as per-block partials); k_adj_band_fb gathers the f' terms, each
+// face summing the band faces beside it in a fixed order.
+
+// a band face of component c at I: updated, inside the source box and |d| < eps at the
+// face centre; its normal n and the weight eps K1(d/eps)
+template <int D>
+__device__ __forceinline__ bool band_face(const Grid& g, const Body& b, int c, const int* I, const int* lo,
+                                          const int* hi, double* n, double& k1) {
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    if (I[d] < lo[d] || I[d] >= hi[d]) return false;
+  if (!face_updated(g, c, I)) return false;
+  double x[3] = {I[0] + 0.5, I[1] + 0.5, I[2] + 0.5};
+  x[c] -= 0.5;
+  double dd[5], dn[3][5];
+  const double d = sdf_theta<D>(b, x, n, dd, dn);
+  if (!(fabs(d) < b.eps)) return false;
+  k1 = b.eps * kernel_K1(d / b.eps);
+  return true;
+}
+
 template <int D>
 __global__ void __launch_bounds__(256) k_adj_band(StageArgs a, Body b, const float* vb0, const float* vb1,
-                                                  const float* vb2, float sfac, float* fb0, float* fb1, float* fb2,
-                                                  float* mb0, float* mb1, float* mb2, int lo0, int lo1, int lo2,
-                                                  int bx, int by, int bz, AdjState* as) {
+                                                  const float* vb2, float sfac, float* mb0, float* mb1, float* mb2,
+                                                  int lo0, int lo1, int lo2, int bx, int by, int bz, double* part) {
+  __shared__ double sh[9];
   const long long nbox = (long long)bx * by * bz;
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nbox * D) return;
-  const int c = (int)(t / nbox);
-  long long rem = t - (long long)c * nbox;
-  const int i = lo0 + (int)(rem % bx);
-  rem /= bx;
-  const int j = lo1 + (int)(rem % by);
-  const int k = lo2 + (int)(rem / by);
   const Grid& g = a.g;
-  const int I[3] = {i, j, k};
-  if (!face_updated(g, c, I)) return;
-  double x[3] = {i + 0.5, j + 0.5, k + 0.5};
-  x[c] -= 0.5;
-  double n[3], dd[4], dn[3][4];
-  const double d = sdf_theta<D>(b, x, n, dd, dn);
-  if (!(fabs(d) < b.eps)) return;
+  const float* vb[3] = {vb0, vb1, vb2};
+  float* mb[3] = {mb0, mb1, mb2};
+  const float dtf = *a.dt;
+  double th[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int NT = n_theta(b.kind, D);
+  for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < nbox * D; t += (long long)gridDim.x * 256) {
+    const int c = (int)(t / nbox);
+    long long rem = t - (long long)c * nbox;
+    const int i = lo0 + (int)(rem % bx);
+    rem /= bx;
+    const int j = lo1 + (int)(rem % by);
+    const int k = lo2 + (int)(rem / by);
+    const int I[3] = {i, j, k};
+    if (!face_updated(g, c, I)) continue;
+    double x[3] = {i + 0.5, j + 0.5, k + 0.5};
+    x[c] -= 0.5;
+    double n[3], dd[5], dn[3][5];
+    const double d = sdf_theta<D>(b, x, n, dd, dn);
+    if (!(fabs(d) < b.eps)) continue;
+    const long long q = cell_index(g, i, j, k);
+    const float vs = sfac * vb[c][q];
+    mb[c][q] += vs * f_at<D>(a, c, i, j, k, dtf);
+    const double sc = d / b.eps, K = 0.5 * (1.0 + cospi(sc));
+    const double k1 = b.eps * kernel_K1(sc), k1p = -sc * K;
+#pragma unroll
+    for (int jd = 0; jd < D; ++jd) {
+      int P[3] = {i, j, k}, M[3] = {i, j, k};
+      P[jd] += 1;
+      M[jd] -= 1;
+      const float fp = f_at<D>(a, c, P[0], P[1], P[2], dtf);
+      const float fm = f_at<D>(a, c, M[0], M[1], M[2], dtf);
+      const double gfd = (double)vs * 0.5 * ((double)fp - (double)fm);
+#pragma unroll
+      for (int tt = 0; tt < 5; ++tt) th[tt] += gfd * (k1p * n[jd] * dd[tt] + k1 * dn[jd][tt]);
+    }
+  }
+  for (int tt = 0; tt < NT; ++tt) {
+    const double v = block_sum(th[tt], sh);
+    if (threadIdx.x == 0) part[(size_t)tt * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+// f'_c[K] += sum over the positions P that map to K and the band faces I = P -+ e_j of
+// +- s mu1_j v'_c[I]/2; the target box covers the source box grown by one face (all of a
+// periodic direction the grown box wraps in)
+template <int D>
+__global__ void __launch_bounds__(256) k_adj_band_fb(Grid g, Body b, const float* vb0, const float* vb1,
+                                                     const float* vb2, float sfac, float* fb0, float* fb1, float* fb2,
+                                                     int lo0, int lo1, int lo2, int hi0, int hi1, int hi2, int t0,
+                                                     int t1, int t2, int tx, int ty, int tzn) {
+  const long long nt = (long long)tx * ty * tzn;
+  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (t >= nt * D) return;
+  const int c = (int)(t / nt);
+  long long rem = t - (long long)c * nt;
+  int K[3];
+  K[0] = t0 + (int)(rem % tx);
+  rem /= tx;
+  K[1] = t1 + (int)(rem % ty);
+  K[2] = t2 + (int)(rem / ty);
+  const int lo[3] = {lo0, lo1, lo2}, hi[3] = {hi0, hi1, hi2};
   const float* vb[3] = {vb0, vb1, vb2};
   float* fb[3] = {fb0, fb1, fb2};
-  float* mb[3] = {mb0, mb1, mb2};
-  const long long q = cell_index(g, i, j, k);
-  const float vs = sfac * vb[c][q];
-  const float dtf = *a.dt;
-  mb[c][q] += vs * f_at<D>(a, c, i, j, k, dtf);
-  const double sc = d / b.eps, K = 0.5 * (1.0 + cospi(sc));
-  const double k1 = b.eps * kernel_K1(sc), k1p = -sc * K;
-  double th[4] = {0.0, 0.0, 0.0, 0.0};
+  int pre[3][5], np[3] = {1, 1, 1};
+  pre[1][0] = pre[2][0] = 0;
 #pragma unroll
-  for (int jd = 0; jd < D; ++jd) {
-    int P[3] = {i, j, k}, M[3] = {i, j, k};
-    P[jd] += 1;
-    M[jd] -= 1;
-    const float fp = f_at<D>(a, c, P[0], P[1], P[2], dtf);
-    const float fm = f_at<D>(a, c, M[0], M[1], M[2], dtf);
-    const float m1 = (float)(k1 * n[jd]) * 0.5f * vs;
-    const long long ip = map_face<D>(g, c, P), im = map_face<D>(g, c, M);
-    if (ip >= 0) atomicAdd(fb[c] + ip, m1);
-    if (im >= 0) atomicAdd(fb[c] + im, -m1);
-    const double gfd = (double)vs * 0.5 * ((double)fp - (double)fm);
+  for (int d = 0; d < D; ++d) np[d] = face_preimages(g, c, d, K[d], pre[d]);
+  float acc = 0.f;
+  bool any = false;
+  for (int a0 = 0; a0 < np[0]; ++a0)
+    for (int a1 = 0; a1 < np[1]; ++a1)
+      for (int a2 = 0; a2 < np[2]; ++a2) {
+        const int P[3] = {pre[0][a0], pre[1][a1], D == 3 ? pre[2][a2] : 0};
 #pragma unroll
-    for (int tt = 0; tt <= D; ++tt) th[tt] += gfd * (k1p * n[jd] * dd[tt] + k1 * dn[jd][tt]);
+        for (int jd = 0; jd < D; ++jd) {
+#pragma unroll
+          for (int sgn = 0; sgn < 2; ++sgn) {  // the band face below P (+), then above (-)
+            int I[3] = {P[0], P[1], P[2]};
+            I[jd] += sgn ? 1 : -1;
+            double n[3], k1;
+            if (!band_face<D>(g, b, c, I, lo, hi, n, k1)) continue;
+            const float vs = sfac * vb[c][cell_index(g, I[0], I[1], D == 3 ? I[2] : 0)];
+            const float m1 = (float)(k1 * n[jd]) * 0.5f * vs;
+            acc += sgn ? -m1 : m1;
+            any = true;
+          }
+        }
+      }
+  if (any) fb[c][cell_index(g, K[0], K[1], D == 3 ? K[2] : 0)] += acc;
+}
+
+// theta' += the partials of nb blocks, each component summed in one fixed order
+__global__ void __launch_bounds__(256) k_adj_theta_accum(const double* part, int nb, int nt, AdjState* as) {
+  __shared__ double sh[9];
+  for (int tt = 0; tt < nt; ++tt) {
+    double v = 0.0;
+    for (int k = threadIdx.x; k < nb; k += 256) v += part[(size_t)tt * nb + k];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) as->theta[tt] += v;
   }
-#pragma unroll
-  for (int tt = 0; tt <= D; ++tt) atomicAdd(&as->theta[tt], th[tt]);
 }
 
 int launch_adj_band(int D, const StageArgs& a, const Body& b, const float* const* vb, float sfac, float* const* fb,
-                    float* const* mbar, AdjState* as, cudaStream_t s) {
+                    float* const* mbar, AdjState* as, double* part, int npart, cudaStream_t s) {
   int lo[3], hi[3];
   band_box(D, a.g, b, 2.0, lo, hi);
   const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
   const long long n = (long long)bx * by * bz * D;
   if (n <= 0) return 0;
-  const int nb = (int)((n + 255) / 256);
+  const int nb = (int)std::min<long long>((n + 255) / 256, npart / n_theta(b.kind, D));
+  const float* v2 = D == 3 ? vb[2] : vb[1];
   if (D == 3)
-    k_adj_band<3><<<nb, 256, 0, s>>>(a, b, vb[0], vb[1], vb[2], sfac, fb[0], fb[1], fb[2], mbar[0], mbar[1], mbar[2],
-                                     lo[0], lo[1], lo[2], bx, by, bz, as);
+    k_adj_band<3><<<nb, 256, 0, s>>>(a, b, vb[0], vb[1], vb[2], sfac, mbar[0], mbar[1], mbar[2], lo[0], lo[1], lo[2],
+                                     bx, by, bz, part);
   else
-    k_adj_band<2><<<nb, 256, 0, s>>>(a, b, vb[0], vb[1], vb[1], sfac, fb[0], fb[1], fb[1], mbar[0], mbar[1], mbar[1],
-                                     lo[0], lo[1], lo[2], bx, by, bz, as);
+    k_adj_band<2><<<nb, 256, 0, s>>>(a, b, vb[0], vb[1], vb[1], sfac, mbar[0], mbar[1], mbar[1], lo[0], lo[1], lo[2],
+                                     bx, by, bz, part);
+  k_adj_theta_accum<<<1, 256, 0, s>>>(part, nb, n_theta(b.kind, D), as);
+  int t0[3] = {0, 0, 0}, tn[3] = {1, 1, 1};
+  for (int d = 0; d < D; ++d) {
+    const int nd = a.g.n[d];
+    int tl = lo[d] - 1, th = hi[d] + 1;
+    if (((a.g.per >> d) & 1u) && (tl < 0 || th > nd)) {
+      tl = 0;
+      th = nd;
+    }
+    tl = std::max(tl, 0);
+    th = std::min(th, nd);
+    t0[d] = tl;
+    tn[d] = th - tl;
+  }
+  const long long nt = (long long)tn[0] * tn[1] * tn[2] * D;
+  const int nbt = (int)((nt + 255) / 256);
+  if (D == 3)
+    k_adj_band_fb<3><<<nbt, 256, 0, s>>>(a.g, b, vb[0], vb[1], v2, sfac, fb[0], fb[1], fb[2], lo[0], lo[1], lo[2],
+                                         hi[0], hi[1], hi[2], t0[0], t0[1], t0[2], tn[0], tn[1], tn[2]);
+  else
+    k_adj_band_fb<2><<<nbt, 256, 0, s>>>(a.g, b, vb[0], vb[1], v2, sfac, fb[0], fb[1], fb[1], lo[0], lo[1], lo[2],
+                                         hi[0], hi[1], hi[2], t0[0], t0[1], t0[2], tn[0], tn[1], tn[2]);
   return 0;
 }
 
 // ---------------------------------------------------------------------------
 // f = u0 + dt r(u) on updated faces: u0' += f', and with r' = dt f' the transpose of
-// convdiff!, r_c[I] = sum_j F_cj[I] - F_cj[I+e_j]: every face flux gets
-// F' = r'_c[I] - r'_c[I-e_j] and scatters F' dF/du to the velocities it reads.  One
-// thread per face (c, I) handles the lower j-fluxes of its control volume (and, on the
-// last cell of a non-periodic direction, the flux through the upper boundary face).
+// convdiff!, r_c[I] = sum_j F_cj[I] - F_cj[I+e_j].  Flux F_cj[J] (component c, through
+// the lower j-face of the control volume at J) exists for J_j in [0, n_j) (and J_j = n_j,
+// the upper boundary face, on a wall) and J_d in [0, n_d) otherwise; its cotangent is
+// F' = R_c[J] - R_c[J-e_j], R_c = dt f'_c on updated faces (periodic wrap) and 0
+// elsewhere.  The flux reads
+//   u_c at J-2e_j, J-e_j, J, J+e_j (viscous: J and J-e_j; advective: the upwind three)
+//   u_j at J and J-e_c             (the advecting velocity a2 = u_j[J] + u_j[J-e_c])
+// and F' times each partial derivative belongs to the face those positions map to.
+// The transpose is a gather: the thread of face (c', K) visits every logical position P
+// that maps to K (periodic images, the clamped tangential positions past a wall) and
+// every flux that reads P, and sums their terms in one fixed order, so the result does
+// not depend on the order threads run in.
+
+// Cotangent weights of one flux, as the forward (mom_flux) branches: the upwind side,
+// the limiter case and its derivative weights on the upwind three.
+struct FluxBar {
+  float Fb;              // F'
+  float ha, gu, gc, gd;  // advective part: F' a2/2 and dphi/d(uu, cc, dd)
+  float hp;              // F' phi/2: the derivative through each advecting velocity
+  bool pos;              // a2 > 0 (upwind from below)
+};
+
 template <int D>
-__device__ __forceinline__ void flux_adjoint(const Grid& g, const float* const* u, int c, int j, const int* J,
-                                             float Fb, float nu, bool adv, float* const* ubin) {
-  int m2[3] = {J[0], J[1], J[2]}, m1[3] = {J[0], J[1], J[2]}, p1[3] = {J[0], J[1], J[2]};
-  int jc[3] = {J[0], J[1], J[2]};
+__device__ __forceinline__ float rbar_at(const Grid& g, const float* fb, int c, const int* J, float dt) {
+  int K[3] = {J[0], J[1], J[2]};
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    if (K[d] < 0 || K[d] >= g.n[d]) {
+      if (!is_per(g, d)) return 0.f;
+      K[d] = wrap_per(K[d], g.n[d]);
+    }
+  }
+  if (!face_updated(g, c, K)) return 0.f;
+  return dt * fb[cell_index(g, K[0], K[1], D == 3 ? K[2] : 0)];
+}
+
+// F' and the weights of flux (c, j) at J; false where J is not a flux position or F' = 0
+template <int D>
+__device__ __forceinline__ bool flux_bar(const Grid& g, const float* const* u, const float* fb, float dt, bool adv,
+                                         int c, int j, const int* J, FluxBar& o) {
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const int hi = g.n[d] + ((d == j && !is_per(g, d)) ? 1 : 0);
+    if (J[d] < 0 || J[d] >= hi) return false;
+  }
+  int M[3] = {J[0], J[1], J[2]};
+  M[j] -= 1;
+  o.Fb = rbar_at<D>(g, fb, c, J, dt) - rbar_at<D>(g, fb, c, M, dt);
+  if (o.Fb == 0.f) return false;
+  if (!adv) return true;
+  int m2[3] = {J[0], J[1], J[2]}, p1[3] = {J[0], J[1], J[2]}, jc[3] = {J[0], J[1], J[2]};
   m2[j] -= 2;
-  m1[j] -= 1;
   p1[j] += 1;
   jc[c] -= 1;
-  const long long im1 = map_face<D>(g, c, m1), ip0 = map_face<D>(g, c, J);
-  // viscous part: F = ... - nu (u[J] - u[J-e_j])
-  if (ip0 >= 0) atomicAdd(ubin[c] + ip0, -nu * Fb);
-  if (im1 >= 0) atomicAdd(ubin[c] + im1, nu * Fb);
-  if (!adv) return;
   auto U = [&](int comp, const int* P) { return load_u_bc<D>(u[comp], comp, g, P[0], P[1], P[2]); };
-  const float vm2 = U(c, m2), vm1 = U(c, m1), vp0 = U(c, J), vp1 = U(c, p1);
+  const float vm2 = U(c, m2), vm1 = U(c, M), vp0 = U(c, J), vp1 = U(c, p1);
   const float a2 = U(j, J) + U(j, jc);
-  // the forward's branch (mom_flux): upwind side, limiter case
-  const bool pos = a2 > 0.f;
-  const float uu = pos ? vm2 : vp1, cc = pos ? vm1 : vp0, dd = pos ? vp0 : vm1;
+  o.pos = a2 > 0.f;
+  const float uu = o.pos ? vm2 : vp1, cc = o.pos ? vm1 : vp0, dd = o.pos ? vp0 : vm1;
   const float dD = dd - cc, dU = cc - uu;
   const float ad = fabsf(dD), au = fabsf(dU);
   const float xa = 2.f * au, xb = (2.f * ad + au) * (1.f / 3.f), xc = 2.f * ad;
-  float gu = 0.f, gc = 1.f, gd = 0.f;
+  o.gu = 0.f;
+  o.gc = 1.f;
+  o.gd = 0.f;
   float lim = 0.f;
   if (dU * dD > 0.f) {
     if (xa <= xb && xa <= xc) {  // phi = cc + (cc - uu)
-      gu = -1.f;
-      gc = 2.f;
+      o.gu = -1.f;
+      o.gc = 2.f;
     } else if (xb <= xc) {       // phi = (5 cc + 2 dd - uu)/6
-      gu = -1.f / 6.f;
-      gc = 5.f / 6.f;
-      gd = 1.f / 3.f;
+      o.gu = -1.f / 6.f;
+      o.gc = 5.f / 6.f;
+      o.gd = 1.f / 3.f;
     } else {                     // phi = dd
-      gc = 0.f;
-      gd = 1.f;
+      o.gc = 0.f;
+      o.gd = 1.f;
     }
     lim = copysignf(fminf(fminf(xa, xb), xc), dD);
   }
   const float phi = fmaf(0.5f, lim, cc);
-  // F = (a2/2) phi: d/d a2 = phi/2 for both advecting velocities
-  const long long ia = map_face<D>(g, j, J), ib = map_face<D>(g, j, jc);
-  if (ia >= 0) atomicAdd(ubin[j] + ia, 0.5f * phi * Fb);
-  if (ib >= 0) atomicAdd(ubin[j] + ib, 0.5f * phi * Fb);
-  const float ha = 0.5f * a2 * Fb;
-  const long long iu = map_face<D>(g, c, pos ? m2 : p1), ic = pos ? im1 : ip0, id = pos ? ip0 : im1;
-  if (iu >= 0 && gu != 0.f) atomicAdd(ubin[c] + iu, ha * gu);
-  if (ic >= 0 && gc != 0.f) atomicAdd(ubin[c] + ic, ha * gc);
-  if (id >= 0 && gd != 0.f) atomicAdd(ubin[c] + id, ha * gd);
+  o.hp = 0.5f * phi * o.Fb;
+  o.ha = 0.5f * a2 * o.Fb;
+  return true;
+}
+
+// sum over the fluxes that read position P of component c of F' dF/du(P), in a fixed order
+template <int D>
+__device__ float flux_gather_at(const Grid& g, const float* const* u, const float* const* fb, float dt, float nu,
+                                bool adv, int c, const int* P) {
+  float acc = 0.f;
+  FluxBar f;
+#pragma unroll 1
+  for (int j = 0; j < D; ++j) {
+    int J[3] = {P[0], P[1], P[2]};
+    // P = J (viscous -nu F'; the advective cc or dd)
+    if (flux_bar<D>(g, u, fb[c], dt, adv, c, j, J, f)) {
+      acc += -nu * f.Fb;
+      if (adv) acc += f.ha * (f.pos ? f.gd : f.gc);
+    }
+    // P = J - e_j (viscous +nu F'; cc or dd)
+    J[j] = P[j] + 1;
+    if (flux_bar<D>(g, u, fb[c], dt, adv, c, j, J, f)) {
+      acc += nu * f.Fb;
+      if (adv) acc += f.ha * (f.pos ? f.gc : f.gd);
+    }
+    if (!adv) continue;
+    // P = J - 2e_j: the upwind uu from below
+    J[j] = P[j] + 2;
+    if (flux_bar<D>(g, u, fb[c], dt, adv, c, j, J, f) && f.pos) acc += f.ha * f.gu;
+    // P = J + e_j: the upwind uu from above
+    J[j] = P[j] - 1;
+    if (flux_bar<D>(g, u, fb[c], dt, adv, c, j, J, f) && !f.pos) acc += f.ha * f.gu;
+  }
+  if (!adv) return acc;
+  // P as an advecting velocity: fluxes (m, j = c) at J = P and J = P + e_m
+#pragma unroll 1
+  for (int m = 0; m < D; ++m) {
+    int J[3] = {P[0], P[1], P[2]};
+    if (flux_bar<D>(g, u, fb[m], dt, adv, m, c, J, f)) acc += f.hp;
+    J[m] = P[m] + 1;
+    if (flux_bar<D>(g, u, fb[m], dt, adv, m, c, J, f)) acc += f.hp;
+  }
+  return acc;
 }
 
 template <int D>
@@ -558,35 +820,25 @@ __global__ void __launch_bounds__(256) k_adj_convdiff(Grid g, const float* u0p, 
   float* ubin[3] = {i0, i1, i2};
   const float dt = *dtp;
   const bool adv = advect != 0;
-  int I[3];
-  coords(g, q, I);
-  const float f = fb[c][q];
-  if (f != 0.f) atomicAdd(ub0[c] + q, f);  // f = u0 + dt r
-  // r' of face (c, J): dt f' on updated faces, 0 elsewhere (J may wrap periodically)
-  auto rbar = [&](const int* J) -> float {
-    int K[3] = {J[0], J[1], J[2]};
+  int K[3];
+  coords(g, q, K);
+  int pre[3][5], np[3] = {1, 1, 1};
+  pre[1][0] = pre[2][0] = 0;
 #pragma unroll
-    for (int d = 0; d < D; ++d) {
-      if (K[d] < 0 || K[d] >= g.n[d]) {
-        if (!is_per(g, d)) return 0.f;
-        K[d] = K[d] < 0 ? K[d] + g.n[d] : K[d] - g.n[d];
+  for (int d = 0; d < D; ++d) np[d] = face_preimages(g, c, d, K[d], pre[d]);
+  float acc = 0.f;
+  for (int a = 0; a < np[0]; ++a)
+    for (int b = 0; b < np[1]; ++b)
+      for (int e = 0; e < np[2]; ++e) {
+        const int P[3] = {pre[0][a], pre[1][b], D == 3 ? pre[2][e] : 0};
+        acc += flux_gather_at<D>(g, u, fb, dt, nu, adv, c, P);
       }
-    }
-    if (!face_updated(g, c, K)) return 0.f;
-    return dt * fb[c][cell_index(g, K[0], K[1], D == 3 ? K[2] : 0)];
-  };
-  const float r0 = face_updated(g, c, I) ? dt * f : 0.f;
-#pragma unroll
-  for (int j = 0; j < D; ++j) {
-    int M[3] = {I[0], I[1], I[2]};
-    M[j] -= 1;
-    const float Fb = r0 - rbar(M);
-    if (Fb != 0.f) flux_adjoint<D>(g, u, c, j, I, Fb, nu, adv, ubin);
-    if (!is_per(g, j) && I[j] == g.n[j] - 1 && r0 != 0.f) {
-      int P[3] = {I[0], I[1], I[2]};
-      P[j] += 1;
-      flux_adjoint<D>(g, u, c, j, P, -r0, nu, adv, ubin);
-    }
+  const float f = fb[c][q];  // f = u0 + dt r: u0' += f'
+  if (ub0[c] == ubin[c]) {
+    ubin[c][q] = (ubin[c][q] + f) + acc;
+  } else {
+    ub0[c][q] += f;
+    ubin[c][q] += acc;
   }
 }
 
@@ -609,11 +861,12 @@ int launch_adj_convdiff(int D, const Grid& g, const float* const* u, const float
 template <int D>
 __global__ void __launch_bounds__(256) k_adj_moments(Grid g, Body b, const float* mb0, const float* mb1,
                                                      const float* mb2, int lo0, int lo1, int lo2, int bx, int by,
-                                                     int bz, AdjState* as) {
+                                                     int bz, double* part) {
   __shared__ double sh[9];
   const float* mb[3] = {mb0, mb1, mb2};
   const long long nbox = (long long)bx * by * bz;
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  const int NT = n_theta(b.kind, D);
   for (long long t = (long long)blockIdx.x * 256 + threadIdx.x; t < nbox * D; t += (long long)gridDim.x * 256) {
     const int c = (int)(t / nbox);
     long long rem = t - (long long)c * nbox;
@@ -625,31 +878,108 @@ __global__ void __launch_bounds__(256) k_adj_moments(Grid g, Body b, const float
     if (!face_updated(g, c, I)) continue;
     double x[3] = {i + 0.5, j + 0.5, k + 0.5};
     x[c] -= 0.5;
-    double n[3], dd[4], dn[3][4];
+    double n[3], dd[5], dn[3][5];
     const double d = sdf_theta<D>(b, x, n, dd, dn);
     const double sc = d / b.eps;
     if (!(fabs(sc) < 1.0)) continue;
     const double w = (double)mb[c][cell_index(g, i, j, k)] * 0.5 * (1.0 + cospi(sc)) / b.eps;
 #pragma unroll
-    for (int tt = 0; tt <= D; ++tt) acc[tt] += w * dd[tt];
+    for (int tt = 0; tt < 5; ++tt) acc[tt] += w * dd[tt];
   }
-  for (int tt = 0; tt <= D; ++tt) {
+  for (int tt = 0; tt < NT; ++tt) {
     const double v = block_sum(acc[tt], sh);
-    if (threadIdx.x == 0) atomicAdd(&as->theta[tt], v);
+    if (threadIdx.x == 0) part[(size_t)tt * gridDim.x + blockIdx.x] = v;
   }
 }
 
-int launch_adj_moments(int D, const Grid& g, const Body& b, const float* const* mbar, AdjState* as, cudaStream_t s) {
+int launch_adj_moments(int D, const Grid& g, const Body& b, const float* const* mbar, AdjState* as, double* part,
+                       int npart, cudaStream_t s) {
   int lo[3], hi[3];
   band_box(D, g, b, 2.0, lo, hi);
   const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
   const long long n = (long long)bx * by * bz * D;
   if (n <= 0) return 0;
-  const int nb = (int)std::min<long long>((n + 255) / 256, 1024);
+  const int nb = (int)std::min<long long>((n + 255) / 256, npart / n_theta(b.kind, D));
   if (D == 3)
-    k_adj_moments<3><<<nb, 256, 0, s>>>(g, b, mbar[0], mbar[1], mbar[2], lo[0], lo[1], lo[2], bx, by, bz, as);
+    k_adj_moments<3><<<nb, 256, 0, s>>>(g, b, mbar[0], mbar[1], mbar[2], lo[0], lo[1], lo[2], bx, by, bz, part);
   else
-    k_adj_moments<2><<<nb, 256, 0, s>>>(g, b, mbar[0], mbar[1], mbar[1], lo[0], lo[1], lo[2], bx, by, bz, as);
+    k_adj_moments<2><<<nb, 256, 0, s>>>(g, b, mbar[0], mbar[1], mbar[1], lo[0], lo[1], lo[2], bx, by, bz, part);
+  k_adj_theta_accum<<<1, 256, 0, s>>>(part, nb, n_theta(b.kind, D), as);
+  return 0;
+}
+
+// V-cycle decision of an adjoint solve (the forward's decision with a relative stop):
+// stop once ||r||_inf <= rtol ||b||_inf (or r = 0; ||b||_inf from the right-hand side),
+// or, flagged, at maxit cycles or a non-finite residual.  Resets the max-norm and sets
+// the 16-bit coarse levels' scale as the forward's decision does.
+__global__ void k_adj_decide(DevState* st, AdjState* as, cudaGraphConditionalHandle h, int use_handle, int first,
+                             double rtol, int maxit) {
+  const float nrm = __uint_as_float(st->norm_bits);
+  st->norm_bits = 0u;
+  if (nrm > 0.f && isfinite(nrm)) st->cs_used = min(max(-ilogbf(nrm) - 6, -100), 100);
+  const double r = (double)nrm, bnorm = (double)__uint_as_float(as->bnorm_bits);
+  if (first) {
+    as->iter = 0;
+  } else {
+    as->iter += 1;
+    as->total_iter += 1;
+  }
+  bool cont = false;
+  if (!isfinite(r))
+    as->flags |= 1;
+  else if (r <= rtol * bnorm || r == 0.0)
+    cont = false;
+  else if (as->iter >= maxit)
+    as->flags |= 2;
+  else
+    cont = true;
+  st->cond = cont ? 1 : 0;
+  if (use_handle) cudaGraphSetConditional(h, cont ? 1u : 0u);
+}
+
+int launch_adj_decide(DevState* st, AdjState* as, cudaGraphConditionalHandle h, int use_handle, int first,
+                      double rtol, int maxit, cudaStream_t s) {
+  k_adj_decide<<<1, 1, 0, s>>>(st, as, h, use_handle, first, rtol, maxit);
+  return 0;
+}
+
+__global__ void __launch_bounds__(256) k_adj_record(const float* s0, const float* s1, const float* s2, int nf,
+                                                    const float* pl, float* seg, const AdjState* as, size_t stride,
+                                                    int off, long long n) {
+  const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (t >= n * nf) return;
+  const int f = (int)(t / n);
+  const long long q = t - (long long)f * n;
+  const float* src = f == 0 ? s0 : (f == 1 ? s1 : s2);
+  float* dst = seg + (size_t)as->rec_slot * stride + (size_t)(off + f) * n;
+  dst[q] = pl ? src[q] + pl[q] : src[q];
+}
+
+int launch_adj_record(const float* const* src, int nf, const float* pl, float* seg, const AdjState* as,
+                      size_t stride, int off, long long n, cudaStream_t s) {
+  if (n <= 0 || nf <= 0) return 0;
+  k_adj_record<<<(int)((n * nf + 255) / 256), 256, 0, s>>>(src[0], nf > 1 ? src[1] : src[0], nf > 2 ? src[2] : src[0],
+                                                           nf, pl, seg, as, stride, off, n);
+  return 0;
+}
+
+__global__ void k_adj_set_slot(AdjState* as, int slot) { as->rec_slot = slot; }
+
+__global__ void __launch_bounds__(256) k_adj_warm(float* x, float* xl, const float* yprev, const AdjState* as,
+                                                  long long n) {
+  const long long q = (long long)blockIdx.x * 256 + threadIdx.x;
+  if (q >= n) return;
+  x[q] = as->bnorm_bits ? yprev[q] : 0.f;
+  if (xl) xl[q] = 0.f;
+}
+
+int launch_adj_warm(float* x, float* xl, const float* yprev, const AdjState* as, long long n, cudaStream_t s) {
+  k_adj_warm<<<(int)((n + 255) / 256), 256, 0, s>>>(x, xl, yprev, as, n);
+  return 0;
+}
+
+int launch_adj_set_slot(AdjState* as, int slot, cudaStream_t s) {
+  k_adj_set_slot<<<1, 1, 0, s>>>(as, slot);
   return 0;
 }
 

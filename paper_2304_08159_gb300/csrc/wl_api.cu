@@ -112,17 +112,24 @@ struct wl_sim {
     float* ck = nullptr;       // checkpoints 0..nseg: D velocity fields + 2 pressure fields each
     DevState* ckst = nullptr;  // the device state of each checkpoint
     float* seg = nullptr;      // per step of a segment: u^n (D), u' (D), p after each projection (2)
-    float* adj = nullptr;      // u' of the state (D), of u^n (D), of the predictor (D), v', f', mbar (D each), y
+    float* adj = nullptr;      // u' of the state (D), of u^n (D), of the predictor (D), v', f', mbar (D each), y1, y2
     double* rec = nullptr;     // force after each step (nsteps x D)
     double* gF = nullptr;      // cotangents of those forces (nsteps x D)
     AdjState* as = nullptr;
     double* part = nullptr;    // reduction partials (4 x kForceParts)
     bool ready = false;        // a forward rollout is recorded
-    bool notconv = false;      // an adjoint solve hit max_vcycles
+    // the recording step (a step graph with the recording kernels) and the adjoint
+    // Poisson solve of each projection (its V-cycles in a WHILE node), built for this
+    // workspace
+    cudaGraph_t rgraph = nullptr, sgraph[2]{};
+    cudaGraphExec_t rexec = nullptr, sexec[2]{};
+    cudaGraphConditionalHandle rhc[2]{}, shc[2]{};
   } gr;
 };
 
 namespace {
+
+void free_grad_graphs(wl_sim::Grad& G);
 
 int fail(wl_sim* s, int code, const std::string& msg) {
   if (s) s->err = msg;
@@ -719,27 +726,38 @@ void copy_pressure(wl_sim* s, float* dst, cudaStream_t st) {
     cudaMemcpyAsync(dst, s->lev[0].x, sizeof(float) * s->g.nc, cudaMemcpyDeviceToDevice, st);
 }
 
-// One step through the host-driven sequence.  rec (optional): where to keep u^n (D
-// fields), u' (D fields) and the pressure after each projection (2 fields), for the
-// adjoint of this step.
-int host_step(wl_sim* s, float* rec = nullptr) {
-  const long long n = s->g.nc;
+// What the adjoint of a step keeps, in the segment slot the gradient state names:
+// u^n (D fields, offset 0), u' (D fields, offset D) and the FP32 pressure after each
+// projection (offsets 2D and 2D+1).
+enum { REC_UN = 0, REC_UP = 1, REC_P1 = 2, REC_P2 = 3 };
+void enq_record(wl_sim* s, int what, cudaStream_t st) {
   const int D = s->D;
-  if (rec)
-    for (int c = 0; c < D; ++c)
-      cudaMemcpyAsync(rec + c * n, s->ua[c], sizeof(float) * n, cudaMemcpyDeviceToDevice, s->st);
+  const long long n = s->g.nc;
+  const size_t stride = (size_t)(2 * D + 2) * (size_t)n;
+  if (what == REC_UN || what == REC_UP) {
+    launch_adj_record(what == REC_UN ? s->ua : s->uc, D, nullptr, s->gr.seg, s->gr.as, stride,
+                      what == REC_UN ? 0 : D, n, st);
+    return;
+  }
+  const float* src[1] = {s->ph ? s->ph : s->lev[0].x};
+  launch_adj_record(src, 1, s->ph ? s->pl : nullptr, s->gr.seg, s->gr.as, stride, 2 * D + (what == REC_P2 ? 1 : 0),
+                    n, st);
+}
+
+// One step through the host-driven sequence; record: keep what the adjoint of the step
+// needs (enq_record).
+int host_step(wl_sim* s, bool record = false) {
+  if (record) enq_record(s, REC_UN, s->st);
   enq_stage(s, 1, s->st);
   int rc = host_projection(s, 1, 1.f, 0);
   if (rc) return rc;
-  if (rec) copy_pressure(s, rec + 2 * D * n, s->st);
+  if (record) enq_record(s, REC_P1, s->st);
   enq_correct(s, s->ub, s->uc, 1.f, 0, s->st);
-  if (rec)
-    for (int c = 0; c < D; ++c)
-      cudaMemcpyAsync(rec + (D + c) * n, s->uc[c], sizeof(float) * n, cudaMemcpyDeviceToDevice, s->st);
+  if (record) enq_record(s, REC_UP, s->st);
   enq_stage(s, 2, s->st);
   rc = host_projection(s, 1, 0.5f, 1);
   if (rc) return rc;
-  if (rec) copy_pressure(s, rec + (2 * D + 1) * n, s->st);
+  if (record) enq_record(s, REC_P2, s->st);
   enq_correct(s, s->ub, s->ua, 0.5f, 1, s->st);
   enq_step_end(s, s->st);
   return cuda_check(s, cudaGetLastError(), "step launch");
@@ -754,8 +772,10 @@ int capture_leaf(wl_sim* s, std::vector<cudaGraphNode_t>& leaf) {
   return WL_OK;
 }
 
+// A WHILE node after deps whose body is one V-cycle and its decision (the captured
+// enq_vcycle, which sets the condition through s->hc[proj]); returns the body graph.
 int add_while(wl_sim* s, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps, int proj, float w,
-              cudaGraphNode_t* node) {
+              cudaGraphNode_t* node, cudaGraph_t* body_out = nullptr) {
   cudaGraphNodeParams cp{};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = s->hc[proj];
@@ -763,7 +783,7 @@ int add_while(wl_sim* s, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps
   cp.conditional.size = 1;
   WL_CUDA(s, cudaGraphAddNode(node, g, deps.data(), nullptr, deps.size(), &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  if (proj == 0) s->vbody = body;
+  if (body_out) *body_out = body;
   WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   enq_vcycle(s, w, proj, s->cs, 1);
   cudaGraph_t out = nullptr;
@@ -771,41 +791,72 @@ int add_while(wl_sim* s, cudaGraph_t g, const std::vector<cudaGraphNode_t>& deps
   return WL_OK;
 }
 
-// One step as a graph: three captured segments joined by two WHILE nodes.
-int build_step_graph(wl_sim* s) {
+// One step as a graph: three captured segments joined by two WHILE nodes.  record: the
+// step that also keeps what its adjoint needs (enq_record), with its own condition handles
+// (the captured decisions address s->hc, which holds them while this graph is built).
+int build_step_graph_into(wl_sim* s, bool record, cudaGraph_t* gout, cudaGraphExec_t* eout,
+                          cudaGraphConditionalHandle* hcs) {
   cudaGraph_t g = nullptr;
   WL_CUDA(s, cudaGraphCreate(&g, 0));
-  for (int p = 0; p < 2; ++p) WL_CUDA(s, cudaGraphConditionalHandleCreate(&s->hc[p], g, 0, 0));
+  *gout = g;
+  for (int p = 0; p < 2; ++p) WL_CUDA(s, cudaGraphConditionalHandleCreate(&hcs[p], g, 0, 0));
+  const cudaGraphConditionalHandle keep[2] = {s->hc[0], s->hc[1]};
+  s->hc[0] = hcs[0];
+  s->hc[1] = hcs[1];
   std::vector<cudaGraphNode_t> leaf;
   cudaGraph_t out = nullptr;
   cudaGraphNode_t w1, w2;
-  // segment 1: stage 1, divergence + first residual
-  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  enq_stage(s, 1, s->cs);
-  enq_proj_head(s, 1, 1.f, 0, s->cs, 1);
-  int rc = capture_leaf(s, leaf);
-  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
-  if (rc) return rc;
-  rc = add_while(s, g, leaf, 0, 1.f, &w1);
-  if (rc) return rc;
-  // segment 2: correction, stage 2, divergence + first residual
-  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w1, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-  enq_correct(s, s->ub, s->uc, 1.f, 0, s->cs);
-  enq_stage(s, 2, s->cs);
-  enq_proj_head(s, 1, 0.5f, 1, s->cs, 1);
-  rc = capture_leaf(s, leaf);
-  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
-  if (rc) return rc;
-  rc = add_while(s, g, leaf, 1, 0.5f, &w2);
-  if (rc) return rc;
-  // segment 3: correction with the CFL maximum, step end
-  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w2, nullptr, 1, cudaStreamCaptureModeThreadLocal));
-  enq_correct(s, s->ub, s->ua, 0.5f, 1, s->cs);
-  enq_step_end(s, s->cs);
-  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
-  WL_CUDA(s, cudaGraphInstantiate(&s->exec, g, 0));
-  s->graph = g;
-  return WL_OK;
+  int rc = WL_OK;
+  do {
+    // segment 1: stage 1, divergence + first residual
+    rc = cuda_check(s, cudaStreamBeginCaptureToGraph(s->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal),
+                    "capture");
+    if (rc) break;
+    if (record) enq_record(s, REC_UN, s->cs);
+    enq_stage(s, 1, s->cs);
+    enq_proj_head(s, 1, 1.f, 0, s->cs, 1);
+    rc = capture_leaf(s, leaf);
+    const int rc2 = cuda_check(s, cudaStreamEndCapture(s->cs, &out), "capture");
+    if (rc || (rc = rc2)) break;
+    cudaGraph_t body = nullptr;
+    if ((rc = add_while(s, g, leaf, 0, 1.f, &w1, &body))) break;
+    if (!record) s->vbody = body;
+    // segment 2: correction, stage 2, divergence + first residual
+    rc = cuda_check(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w1, nullptr, 1, cudaStreamCaptureModeThreadLocal),
+                    "capture");
+    if (rc) break;
+    if (record) enq_record(s, REC_P1, s->cs);
+    enq_correct(s, s->ub, s->uc, 1.f, 0, s->cs);
+    if (record) enq_record(s, REC_UP, s->cs);
+    enq_stage(s, 2, s->cs);
+    enq_proj_head(s, 1, 0.5f, 1, s->cs, 1);
+    rc = capture_leaf(s, leaf);
+    const int rc3 = cuda_check(s, cudaStreamEndCapture(s->cs, &out), "capture");
+    if (rc || (rc = rc3)) break;
+    if ((rc = add_while(s, g, leaf, 1, 0.5f, &w2))) break;
+    // segment 3: correction with the CFL maximum, step end
+    rc = cuda_check(s, cudaStreamBeginCaptureToGraph(s->cs, g, &w2, nullptr, 1, cudaStreamCaptureModeThreadLocal),
+                    "capture");
+    if (rc) break;
+    if (record) enq_record(s, REC_P2, s->cs);
+    enq_correct(s, s->ub, s->ua, 0.5f, 1, s->cs);
+    enq_step_end(s, s->cs);
+    if ((rc = cuda_check(s, cudaStreamEndCapture(s->cs, &out), "capture"))) break;
+    rc = cuda_check(s, cudaGraphInstantiate(eout, g, 0), "graph instantiate");
+  } while (false);
+  if (!record) {
+    s->hc[0] = hcs[0];
+    s->hc[1] = hcs[1];
+  } else {
+    s->hc[0] = keep[0];
+    s->hc[1] = keep[1];
+  }
+  return rc;
+}
+
+int build_step_graph(wl_sim* s) {
+  cudaGraphConditionalHandle h[2]{};
+  return build_step_graph_into(s, false, &s->graph, &s->exec, h);
 }
 
 int set_dt_from_ic(wl_sim* s) {
@@ -1148,6 +1199,7 @@ void wl_destroy(wl_handle s) {
   if (s->side.join) cudaEventDestroy(s->side.join);
   if (s->hs) cudaFreeHost(s->hs);
   if (s->own_ws && s->ws) cudaFree(s->ws);
+  free_grad_graphs(s->gr);
   if (s->gr.own && s->gr.mem) cudaFree(s->gr.mem);
   if (s->body_nodes) cudaFree(s->body_nodes);
   delete s;
@@ -1513,15 +1565,11 @@ size_t grad_layout(wl_sim* s, int nsteps, int every, char* base) {
   const int D = s->D;
   const size_t n = (size_t)s->g.nc;
   const int nseg = (nsteps + every - 1) / every;
-  Carver cv{base};
-  if (s && base) {
-    s->canaries.clear();
-    cv.canaries = &s->canaries;
-  }
+  Carver cv{base};  // (the gradient workspace's canary gaps are not recorded: not checked)
   void* ck = cv.take(sizeof(float) * n * (D + 2) * (size_t)(nseg + 1));
   void* ckst = cv.take(sizeof(DevState) * (size_t)(nseg + 1));
   void* seg = cv.take(sizeof(float) * n * (2 * D + 2) * (size_t)every);
-  void* adj = cv.take(sizeof(float) * n * (6 * D + 1));
+  void* adj = cv.take(sizeof(float) * n * (6 * D + 2));
   void* rec = cv.take(sizeof(double) * (size_t)nsteps * D);
   void* gF = cv.take(sizeof(double) * (size_t)nsteps * D);
   void* as = cv.take(sizeof(AdjState));
@@ -1562,55 +1610,87 @@ void restore_ck(wl_sim* s, int k) {
 }
 
 // adjoint fields: [0,D) cotangent of the state, [D,2D) of u^n, [2D,3D) of the
-// predictor u', [3D,4D) v', [4D,5D) f', [5D,6D) the coefficient cotangent, 6D: y
+// predictor u', [3D,4D) v', [4D,5D) f', [5D,6D) the coefficient cotangent, 6D and 6D+1:
+// the adjoint pressures y of projections 1 and 2 (kept from step to step: each solve
+// starts from its projection's solution one step later)
 struct AdjFields {
-  float* f[7][3];
+  float* f[8][3];
 };
 AdjFields adj_fields(wl_sim* s) {
   AdjFields a{};
   const int D = s->D;
   for (int b = 0; b < 6; ++b)
     for (int c = 0; c < 3; ++c) a.f[b][c] = s->gr.adj + (size_t)(b * D + (c < D ? c : D - 1)) * s->g.nc;
-  for (int c = 0; c < 3; ++c) a.f[6][c] = s->gr.adj + (size_t)(6 * D) * s->g.nc;
+  for (int c = 0; c < 3; ++c) {
+    a.f[6][c] = s->gr.adj + (size_t)(6 * D) * s->g.nc;
+    a.f[7][c] = s->gr.adj + (size_t)(6 * D + 1) * s->g.nc;
+  }
   return a;
 }
 
-// Solve A y = b (b in the fine right-hand side, mean-free over the active cells) with the
-// forward multigrid to ||b - A y||_inf <= rtol ||b||_inf; y (FP32) into dst.
-int adj_solve(wl_sim* s, double rtol, float* dst) {
-  const size_t nb = sizeof(float) * (size_t)s->g.nc;
-  if (s->ph) {
-    cudaMemsetAsync(s->ph, 0, nb, s->st);
-    cudaMemsetAsync(s->pl, 0, nb, s->st);
-  } else {
-    cudaMemsetAsync(s->lev[0].x, 0, nb, s->st);
-  }
-  double bnorm = 0.0;
-  for (int it = 0;; ++it) {
-    WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
-    enq_fine_residual(s, RES_RESIDUAL, 0, 1.f, s->st);
-    int rc = sync_state(s);
-    if (rc) return rc;
-    const double r = reinterpret_cast<const float&>(s->hs->norm_bits);
-    if (!std::isfinite(r)) {
-      s->poisoned = true;
-      return fail(s, WL_ENONFINITE, "non-finite adjoint residual");
-    }
-    if (it == 0) bnorm = r;
-    if (r <= rtol * bnorm || r == 0.0) break;
-    if (it >= s->o.max_vcycles) {  // a warning: the gradient is returned, less accurate
-      s->gr.notconv = true;
-      fail(s, WL_WNOTCONV, "adjoint solve hit max_vcycles");
-      break;
-    }
-    enq_vcycle_core(s, s->st);
-  }
-  WL_CUDA(s, cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->st));
-  copy_pressure(s, dst, s->st);
+constexpr double kAdjRtol = 1e-7;
+
+// The adjoint Poisson solve of projection k (0, 1) as a graph: solve A y = b (b in the
+// fine right-hand side, mean-free over the active cells) with the forward multigrid to
+// ||b - A y||_inf <= kAdjRtol ||b||_inf, starting from the projection's y of one step
+// later (kept in y), the V-cycles in a WHILE node that the device's decision ends (at
+// max_vcycles, flagged, or a non-finite residual, flagged); the solution (FP32) into y.
+int build_adj_solve_graph(wl_sim* s, int k, float* y) {
+  wl_sim::Grad& G = s->gr;
+  WL_CUDA(s, cudaGraphCreate(&G.sgraph[k], 0));
+  WL_CUDA(s, cudaGraphConditionalHandleCreate(&G.shc[k], G.sgraph[k], 0, 0));
+  std::vector<cudaGraphNode_t> leaf;
+  cudaGraph_t out = nullptr;
+  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, G.sgraph[k], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  launch_adj_warm(s->ph ? s->ph : s->lev[0].x, s->pl, y, G.as, s->g.nc, s->cs);
+  cudaMemsetAsync(&s->ds->norm_bits, 0, sizeof(unsigned), s->cs);
+  enq_fine_residual(s, RES_RESIDUAL, 0, 1.f, s->cs);
+  launch_adj_decide(s->ds, G.as, G.shc[k], 1, 1, kAdjRtol, s->o.max_vcycles, s->cs);
+  int rc = capture_leaf(s, leaf);
+  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
+  if (rc) return rc;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = G.shc[k];
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  WL_CUDA(s, cudaGraphAddNode(&wn, G.sgraph[k], leaf.data(), nullptr, leaf.size(), &cp));
+  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, cp.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+  enq_vcycle_core(s, s->cs);
+  enq_fine_residual(s, RES_RESIDUAL, 0, 1.f, s->cs);
+  launch_adj_decide(s->ds, G.as, G.shc[k], 1, 0, kAdjRtol, s->o.max_vcycles, s->cs);
+  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
+  WL_CUDA(s, cudaStreamBeginCaptureToGraph(s->cs, G.sgraph[k], &wn, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+  copy_pressure(s, y, s->cs);
+  WL_CUDA(s, cudaStreamEndCapture(s->cs, &out));
+  WL_CUDA(s, cudaGraphInstantiate(&G.sexec[k], G.sgraph[k], 0));
   return WL_OK;
 }
 
-constexpr double kAdjRtol = 1e-7;
+void free_grad_graphs(wl_sim::Grad& G) {
+  if (G.rexec) cudaGraphExecDestroy(G.rexec);
+  if (G.rgraph) cudaGraphDestroy(G.rgraph);
+  G.rexec = nullptr;
+  G.rgraph = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (G.sexec[k]) cudaGraphExecDestroy(G.sexec[k]);
+    if (G.sgraph[k]) cudaGraphDestroy(G.sgraph[k]);
+    G.sexec[k] = nullptr;
+    G.sgraph[k] = nullptr;
+  }
+}
+
+int adj_solve(wl_sim* s, int k, float* y) {
+  wl_sim::Grad& G = s->gr;
+  if (!G.sexec[k]) {
+    int rc = build_adj_solve_graph(s, k, y);
+    if (rc) return rc;
+  }
+  WL_CUDA(s, cudaGraphLaunch(G.sexec[k], s->st));
+  return WL_OK;
+}
 
 // Adjoint of step n (its recorded slot m): the cotangent of u^{n+1} in field block 0 and
 // of the force after the step in gF[n] give the cotangent of u^n in block 0 and add to
@@ -1634,7 +1714,8 @@ int adj_step(wl_sim* s, int m, int n) {
   float* const* vb = A.f[3];
   float* const* fb = A.f[4];
   float* const* mb = A.f[5];
-  float* y = A.f[6][0];
+  float* y1 = A.f[6][0];
+  float* y2 = A.f[7][0];
   const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
   const double dt = s->o.dt_fixed;
   const double* g = s->gr.gF + (size_t)n * D;
@@ -1644,9 +1725,9 @@ int adj_step(wl_sim* s, int m, int n) {
   launch_adj_force_theta(D, s->g, s->body, p2, s->fout + 3, g, s->gr.as, st);
   // projection 2 (w = 1/2)
   launch_adj_proj_rhs(D, s->g, s->body, ub, L, g, 1.0 / (0.5 * dt), s->gr.as, s->lev[0].z, s->gr.part, kForceParts, st);
-  int rc = adj_solve(s, kAdjRtol, y);
+  int rc = adj_solve(s, 1, y2);
   if (rc) return rc;
-  launch_adj_proj_out(D, s->g, ub, y, p2, (float)(0.5 * dt), vb, mb, st);
+  launch_adj_proj_out(D, s->g, ub, y2, p2, (float)(0.5 * dt), vb, mb, st);
   // stage 2: out = (u' + mu0 f + mu1 . grad f)/2, f = u^n + dt r(u')
   launch_adj_stage_local(D, s->g, vb, L, 0.5f, fb, ubp, st);
   StageArgs a = stage_args(s, 2);
@@ -1654,26 +1735,27 @@ int adj_step(wl_sim* s, int m, int n) {
     a.u[c] = up[c];
     a.u0[c] = un[c];
   }
-  launch_adj_band(D, a, s->body, vb, 0.5f, fb, mb, s->gr.as, st);
+  launch_adj_band(D, a, s->body, vb, 0.5f, fb, mb, s->gr.as, s->gr.part, kForceParts, st);
   for (int c = 0; c < D; ++c) cudaMemsetAsync(ub0[c], 0, sizeof(float) * nc, st);
   launch_adj_convdiff(D, s->g, up, fb, &s->ds->dtf, (float)s->nu, s->o.advect, ub0, ubp, st);
   // projection 1 (w = 1)
   launch_adj_proj_rhs(D, s->g, s->body, ubp, L, nullptr, 0.0, s->gr.as, s->lev[0].z, s->gr.part, kForceParts, st);
-  rc = adj_solve(s, kAdjRtol, y);
+  rc = adj_solve(s, 0, y1);
   if (rc) return rc;
-  launch_adj_proj_out(D, s->g, ubp, y, p1, (float)dt, vb, mb, st);
+  launch_adj_proj_out(D, s->g, ubp, y1, p1, (float)dt, vb, mb, st);
   // stage 1: out = mu0 f + mu1 . grad f, f = u^n + dt r(u^n)
   launch_adj_stage_local(D, s->g, vb, L, 1.f, fb, nullptr, st);
   a = stage_args(s, 1);
   for (int c = 0; c < 3; ++c) a.u[c] = a.u0[c] = un[c];
-  launch_adj_band(D, a, s->body, vb, 1.f, fb, mb, s->gr.as, st);
+  launch_adj_band(D, a, s->body, vb, 1.f, fb, mb, s->gr.as, s->gr.part, kForceParts, st);
   launch_adj_convdiff(D, s->g, un, fb, &s->ds->dtf, (float)s->nu, s->o.advect, ub0, ub0, st);
   for (int c = 0; c < D; ++c) cudaMemcpyAsync(ub[c], ub0[c], sizeof(float) * nc, cudaMemcpyDeviceToDevice, st);
   return cuda_check(s, cudaGetLastError(), "adjoint step");
 }
 
 int grad_check(wl_sim* s) {
-  if (s->body.kind != 1) return fail(s, WL_EINVAL, "gradients need a circle/sphere body");
+  if (!(s->body.kind == 1 || (s->body.kind == 2 && s->D == 3)))
+    return fail(s, WL_EINVAL, "gradients need a circle/sphere or torus body");
   if (s->g.exit) return fail(s, WL_EINVAL, "the convective exit is not differentiated");
   if (!(s->o.dt_fixed > 0.0)) return fail(s, WL_EINVAL, "gradients need a fixed dt (wl_opts.dt_fixed > 0)");
   if (s->poisoned) return fail(s, WL_ENONFINITE, "sim is poisoned");
@@ -1694,10 +1776,9 @@ int wl_grad_forward(wl_handle s, int nsteps, int every, void* workspace, size_t 
   every = std::min(every, nsteps);
   const size_t need = grad_layout(s, nsteps, every, nullptr);
   wl_sim::Grad& G = s->gr;
-  if (G.own && G.mem) {
-    cudaStreamSynchronize(s->st);
-    cudaFree(G.mem);
-  }
+  cudaStreamSynchronize(s->st);
+  free_grad_graphs(G);
+  if (G.own && G.mem) cudaFree(G.mem);
   G = wl_sim::Grad{};
   if (workspace) {
     if (workspace_bytes < need || ((uintptr_t)workspace & 255u)) return fail(s, WL_ENOMEM, "gradient workspace too small");
@@ -1713,10 +1794,13 @@ int wl_grad_forward(wl_handle s, int nsteps, int every, void* workspace, size_t 
   }
   grad_layout(s, nsteps, every, G.mem);
   WL_CUDA(s, cudaMemsetAsync(&s->ds->status, 0, sizeof(int), s->st));
+  if (s->o.use_graph && !s->exec && (rc = build_step_graph(s))) return rc;
   for (int n = 0; n < nsteps; ++n) {
     if (n % every == 0) save_ck(s, n / every);
-    rc = host_step(s);
-    if (rc) return rc;
+    if (s->o.use_graph)
+      WL_CUDA(s, cudaGraphLaunch(s->exec, s->st));
+    else if ((rc = host_step(s)))
+      return rc;
     const float* L[3] = {s->lev[0].L[0], s->lev[0].L[1], s->lev[0].L[2]};
     launch_forces(s->D, s->g, s->body, s->ph ? s->ph : s->lev[0].x, s->pl, L, s->fpart, kForceParts, s->fout, s->st);
     WL_CUDA(s, cudaMemcpyAsync(G.rec + (size_t)n * s->D, s->fout, sizeof(double) * s->D, cudaMemcpyDeviceToDevice,
@@ -1750,28 +1834,38 @@ int wl_grad_backward(wl_handle s, const double* gF, double* theta_bar) {
     cudaMemsetAsync(A.f[0][c], 0, sizeof(float) * nc, s->st);  // J has no term in the final state
     cudaMemsetAsync(A.f[5][c], 0, sizeof(float) * nc, s->st);
   }
-  const size_t slot = (size_t)(2 * D + 2) * nc;
-  G.notconv = false;
+  cudaMemsetAsync(A.f[6][0], 0, sizeof(float) * nc * 2, s->st);  // the adjoint solves' first starts
+  if (s->o.use_graph && !G.rexec && (rc = build_step_graph_into(s, true, &G.rgraph, &G.rexec, G.rhc))) return rc;
   for (int k = G.nseg - 1; k >= 0; --k) {
     const int n0 = k * G.every, n1 = std::min(n0 + G.every, G.nsteps);
     restore_ck(s, k);
     for (int n = n0; n < n1; ++n) {  // recompute the segment, keeping what the adjoint needs
-      rc = host_step(s, G.seg + (size_t)(n - n0) * slot);
-      if (rc) return rc;
+      launch_adj_set_slot(G.as, n - n0, s->st);
+      if (s->o.use_graph)
+        WL_CUDA(s, cudaGraphLaunch(G.rexec, s->st));
+      else if ((rc = host_step(s, true)))
+        return rc;
     }
     for (int n = n1 - 1; n >= n0; --n) {
       rc = adj_step(s, n - n0, n);
       if (rc) return rc;
     }
   }
-  launch_adj_moments(D, s->g, s->body, A.f[5], G.as, s->st);
+  launch_adj_moments(D, s->g, s->body, A.f[5], G.as, G.part, kForceParts, s->st);
   restore_ck(s, G.nseg);
-  double th[4];
-  WL_CUDA(s, cudaMemcpyAsync(th, G.as->theta, sizeof(th), cudaMemcpyDeviceToHost, s->st));
+  AdjState as{};
+  WL_CUDA(s, cudaMemcpyAsync(&as, G.as, sizeof(as), cudaMemcpyDeviceToHost, s->st));
   WL_CUDA(s, cudaStreamSynchronize(s->st));
-  for (int t = 0; t <= D; ++t) theta_bar[t] = th[t];
+  const int nt = s->body.kind == 2 ? 5 : D + 1;
+  for (int t = 0; t < nt; ++t) theta_bar[t] = as.theta[t];
   rc = cuda_check(s, cudaGetLastError(), "wl_grad_backward");
-  return rc ? rc : (G.notconv ? WL_WNOTCONV : WL_OK);
+  if (rc) return rc;
+  if (as.flags & 1) {
+    s->poisoned = true;
+    return fail(s, WL_ENONFINITE, "non-finite adjoint residual");
+  }
+  if (as.flags & 2) return fail(s, WL_WNOTCONV, "an adjoint solve hit max_vcycles");
+  return WL_OK;
 }
 
 int wl_level_split(wl_handle s, int l, int* split, double* band_fraction) {

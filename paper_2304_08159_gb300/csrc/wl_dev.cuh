@@ -29,6 +29,15 @@ __host__ __device__ inline long long exit_index(const Grid& g, int j, int k) {
 
 __device__ __forceinline__ bool is_per(const Grid& g, int d) { return (g.per >> d) & 1u; }
 
+// Index q of a periodic direction of n cells brought into [0, n).  One period is the
+// common case; a tile or its halo wider than the grid (n smaller than the footprint)
+// reaches a few periods further.  (Loops, not a modulo: short code in the hot kernels.)
+__host__ __device__ __forceinline__ int wrap_per(int q, int n) {
+  while (q < 0) q += n;
+  while (q >= n) q -= n;
+  return q;
+}
+
 // ---- Bounds-checked build (compiled with WL_DEBUG_BOUNDS into libwl_debug.so): an index
 // outside its array sets a bit of this translation unit's flag word and the access is
 // skipped, so a bad index is reported instead of corrupting memory or faulting (no trap).
@@ -105,12 +114,12 @@ __device__ __forceinline__ float load_u_bc(const float* __restrict__ uc, int c, 
     // stored exit plane at the row (y clamped / wrapped like a tangential component)
     int J = j, K = D == 3 ? k : 0;
     if (is_per(g, 1))
-      J = J < 0 ? J + g.n[1] : (J >= g.n[1] ? J - g.n[1] : J);
+      J = wrap_per(J, g.n[1]);
     else
       J = J < 0 ? 0 : (J >= g.n[1] ? g.n[1] - 1 : J);
     if (D == 3) {
       if (is_per(g, 2))
-        K = K < 0 ? K + g.n[2] : (K >= g.n[2] ? K - g.n[2] : K);
+        K = wrap_per(K, g.n[2]);
       else
         K = K < 0 ? 0 : (K >= g.n[2] ? g.n[2] - 1 : K);
     }
@@ -122,7 +131,7 @@ __device__ __forceinline__ float load_u_bc(const float* __restrict__ uc, int c, 
     int q = I[d];
     const int n = g.n[d];
     if (is_per(g, d)) {
-      q = (q < 0) ? q + n : ((q >= n) ? q - n : q);
+      q = wrap_per(q, n);
     } else {
       if (d == c && (q <= 0 || q >= n)) return g.U[c];
       q = q < 0 ? 0 : (q >= n ? n - 1 : q);

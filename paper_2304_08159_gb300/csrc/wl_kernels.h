@@ -303,10 +303,15 @@ namespace wl {
 
 // ---- reverse-mode derivative of the time step (wl_adjoint.cu)
 struct AdjState {
-  double theta[4];  // dJ/d(R, c_0, .., c_{D-1}), accumulated
+  double theta[5];  // dJ/dtheta, accumulated: (R, c_0, .., c_{D-1}) or, torus, (R, r, c_x, c_y, c_z)
   double W[3];      // sum over band cells of the force weights n K_eps(d)
   double Na;        // active cells (nonzero Poisson row)
   double mean;      // mean over active cells of the last adjoint right-hand side
+  unsigned bnorm_bits;  // ||b||_inf of the adjoint right-hand side (float bits)
+  int iter;         // V-cycles of the running adjoint solve
+  int total_iter;   // V-cycles of all adjoint solves of the backward pass
+  int flags;        // 1: a non-finite adjoint residual, 2: an adjoint solve hit max_vcycles
+  int rec_slot;     // the segment slot the recomputed step records into
 };
 int launch_adj_setup(int D, const Grid& g, const Body& b, const float* const* L, AdjState* as, double* part,
                      int npart, cudaStream_t s);
@@ -320,10 +325,24 @@ int launch_adj_proj_out(int D, const Grid& g, const float* const* ub, const floa
 int launch_adj_stage_local(int D, const Grid& g, const float* const* vb, const float* const* mu0, float sfac,
                            float* const* fb, float* const* up, cudaStream_t s);
 int launch_adj_band(int D, const StageArgs& a, const Body& b, const float* const* vb, float sfac, float* const* fb,
-                    float* const* mbar, AdjState* as, cudaStream_t s);
+                    float* const* mbar, AdjState* as, double* part, int npart, cudaStream_t s);
 int launch_adj_convdiff(int D, const Grid& g, const float* const* u, const float* const* fb, const float* dt, float nu,
                         int advect, float* const* ub0, float* const* ubin, cudaStream_t s);
-int launch_adj_moments(int D, const Grid& g, const Body& b, const float* const* mbar, AdjState* as, cudaStream_t s);
+int launch_adj_moments(int D, const Grid& g, const Body& b, const float* const* mbar, AdjState* as, double* part,
+                       int npart, cudaStream_t s);
+// the adjoint solve's V-cycle decision: continue while ||r||_inf > rtol ||b||_inf (b: the
+// first residual) and fewer than maxit cycles ran; sets the WHILE node's condition
+int launch_adj_decide(DevState* st, AdjState* as, cudaGraphConditionalHandle h, int use_handle, int first,
+                      double rtol, int maxit, cudaStream_t s);
+// recording of a recomputed step: fields src[0..nf) (nf = 1 with pl: the FP32 rounding
+// ph + pl of a double-float pressure) into seg + rec_slot * stride + (off + f) * n, the
+// slot read on the device, so one graph serves every slot
+int launch_adj_record(const float* const* src, int nf, const float* pl, float* seg, const AdjState* as,
+                      size_t stride, int off, long long n, cudaStream_t s);
+int launch_adj_set_slot(AdjState* as, int slot, cudaStream_t s);
+// start of an adjoint solve: the iterate (x, or the double-float pair x + xl) from the
+// same projection's solution one step later (yprev), or 0 if the right-hand side is 0
+int launch_adj_warm(float* x, float* xl, const float* yprev, const AdjState* as, long long n, cudaStream_t s);
 
 }  // namespace wl
 

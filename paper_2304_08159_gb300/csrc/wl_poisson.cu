@@ -340,7 +340,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a, const uint3 bid) 
     const int n = g.n[d];
     if (q >= 0 && q < n) return q;
     if (!is_per(g, d)) return -1;
-    return q < 0 ? q + n : q - n;
+    return wrap_per(q, n);  // (a footprint wider than the level can reach past one period)
   };
   for (int t = tid; t < SW_HX + SW_HY; t += 256) {
     if (t < SW_HX) {

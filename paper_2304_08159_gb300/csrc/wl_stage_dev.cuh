@@ -53,7 +53,7 @@ __device__ float f_at(const StageArgs& a, int c, int i, int j, int k, float dt) 
     int q = I[d];
     const int n = g.n[d];
     if (is_per(g, d)) {
-      q = (q < 0) ? q + n : ((q >= n) ? q - n : q);
+      q = wrap_per(q, n);
     } else {
       if (d == c && (q <= 0 || q >= n)) return g.U[c];
       q = q < 0 ? 0 : (q >= n ? n - 1 : q);

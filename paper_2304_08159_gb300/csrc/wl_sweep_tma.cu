@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   if (tile_in_band(a.band, D, i0, j0, k0, k1) == UNI) return;  // the other variant's tile
   // a plane past a periodic z side is staged from its wrapped plane
   const bool pz = D == 3 && is_per(g, 2);
-  auto wz = [&](int p) { return pz ? (p < 0 ? p + g.n[2] : (p >= g.n[2] ? p - g.n[2] : p)) : p; };
+  auto wz = [&](int p) { return pz ? wrap_per(p, g.n[2]) : p; };
   // Ring slots: iterate plane p lives in slot (p - k0 + 2) mod XR, coefficient plane
   // p in slot (p - k0 + 1) mod L2R (L2) or mod CR (z, L0, L1).
   auto Xs = [&](int s) { return ox + s * BOX; };
@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   for (int r = 0; r < 2; ++r) {
     const int t = tid + SW_NT * r, cr = t / CBX, cc = t - cr * CBX;
     int ci = (i0 >> 1) - 2 + cc, cj = (j0 >> 1) - 1 + cr;
-    if (is_per(g, 0)) ci = ci < 0 ? ci + a.cn[0] : (ci >= a.cn[0] ? ci - a.cn[0] : ci);  // a wrapping tile
-    if (is_per(g, 1)) cj = cj < 0 ? cj + a.cn[1] : (cj >= a.cn[1] ? cj - a.cn[1] : cj);
+    if (is_per(g, 0)) ci = wrap_per(ci, a.cn[0]);  // a wrapping tile
+    if (is_per(g, 1)) cj = wrap_per(cj, a.cn[1]);
     ceo[r] = t < CBOX ? 2 * cr * BX + 2 * cc : -1;
     cxy[r] = (t < CBOX && a.xc && ci >= 0 && ci < a.cn[0] && cj >= 0 && cj < a.cn[1]) ? ci + a.cn[0] * cj : -1;
   }
@@ -281,8 +281,8 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
         return;
       }
       int gi = i0 - 4 + col, gj = y0 + row;
-      if (px) gi = gi < 0 ? gi + g.n[0] : (gi >= g.n[0] ? gi - g.n[0] : gi);
-      if (py) gj = gj < 0 ? gj + g.n[1] : (gj >= g.n[1] ? gj - g.n[1] : gj);
+      if (px) gi = wrap_per(gi, g.n[0]);
+      if (py) gj = wrap_per(gj, g.n[1]);
       const bool in = gi >= 0 && gi < g.n[0] && gj >= 0 && gj < g.n[1];
       off = in ? row * BX + col : -1;
       q = in ? (unsigned)gi + (unsigned)g.n[0] * (unsigned)gj : 0u;

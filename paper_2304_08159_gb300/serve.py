@@ -116,7 +116,10 @@ class Server:
         import torch
 
         if self.stream is None:
-            self.stream = torch.cuda.Stream()
+            # with a batch, the server's stream (which runs the batched graphs) takes the
+            # higher priority, so the small simulations' blocks are scheduled ahead of the
+            # large ones' and their step latency stays short
+            self.stream = torch.cuda.Stream(priority=-1 if self.batch_cells > 0 else 0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(self.stream)

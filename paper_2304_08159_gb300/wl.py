@@ -412,6 +412,8 @@ class Sim:
             o.workspace = self.workspace.data_ptr()
             o.workspace_bytes = nbytes
             b = None
+            # body parameters of the gradient: circle/sphere (R, c_0, ..), torus (R, r, c_x, c_y, c_z)
+            self.n_theta = 5 if body is not None and int(body.get("kind", 1)) == WL_BODY_TORUS else self.D + 1
             if body is not None:
                 b = make_body(body)
                 if b.kind == WL_BODY_FIELD and b._nodes.size != int(np.prod([d + 1 for d in self.dims])):
@@ -580,13 +582,14 @@ class Sim:
         return F.reshape(int(nsteps), self.D)
 
     def grad_backward(self, gF, return_status=False):
-        """wl_grad_backward: dJ/d(R, c_0, ..) for J = sum_n gF[n] . F_n (and the status,
-        WL_OK or WL_WNOTCONV, with return_status)."""
+        """wl_grad_backward: dJ/dtheta for J = sum_n gF[n] . F_n, theta = (R, c_0, ..) of a
+        circle/sphere or (R, r, c_x, c_y, c_z) of a torus (and the status, WL_OK or
+        WL_WNOTCONV, with return_status)."""
         g = np.ascontiguousarray(gF, dtype=np.float64).reshape(-1)
         n = getattr(self, "grad_steps", 0)
         if n and g.size != n * self.D:
             raise WLError(WL_EINVAL, f"gF must hold {n} x {self.D} values")
-        tb = np.zeros(self.D + 1)
+        tb = np.zeros(self.n_theta)
         rc = load().wl_grad_backward(self.h, g.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                      tb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         self._check(rc, "wl_grad_backward")
