@@ -29,13 +29,15 @@ __host__ __device__ inline long long exit_index(const Grid& g, int j, int k) {
 
 __device__ __forceinline__ bool is_per(const Grid& g, int d) { return (g.per >> d) & 1u; }
 
-// Index q of a periodic direction of n cells brought into [0, n).  One period is the
-// common case; a tile or its halo wider than the grid (n smaller than the footprint)
-// reaches a few periods further.  (Loops, not a modulo: short code in the hot kernels.)
+// Index q of a periodic direction of n cells brought into [0, n).  Every position an owned
+// cell's stencil reads lies within one period of the grid (the stencils reach two cells,
+// n >= 2), where this is the exact wrap.  A tile's halo on a level narrower than the tile
+// reaches further, to positions no owned cell reads; those are clamped into the array
+// (any value there is unused, and the access stays in bounds).  Two compares and a
+// clamp: short code in the register-bound kernels.
 __host__ __device__ __forceinline__ int wrap_per(int q, int n) {
-  while (q < 0) q += n;
-  while (q >= n) q -= n;
-  return q;
+  q = q < 0 ? q + n : (q >= n ? q - n : q);
+  return q < 0 ? 0 : (q >= n ? n - 1 : q);
 }
 
 // ---- Bounds-checked build (compiled with WL_DEBUG_BOUNDS into libwl_debug.so): an index
