@@ -54,6 +54,7 @@ struct LevelBuf {
 
 constexpr int kMaxLevels = 16;
 constexpr long long kTailCells = 4096;  // largest hierarchy tail (cells) run by k_vcycle_tail
+constexpr long long kCtailCells = 1 << 17;  // largest hierarchy tail run by one cluster (k_vcycle_ctail)
 constexpr int kForceParts = 1024;
 constexpr int kMetricRing = WL_METRIC_RING;
 
@@ -90,6 +91,8 @@ struct wl_sim {
   bool resid_tma = false;     // the fine residual uses the TMA-staged kernel
   float* body_nodes = nullptr;  // WL_BODY_FIELD: device copy of the sampled distance
   int tail_lf = 0;            // > 0: levels tail_lf .. nlev-1 run as one block (k_vcycle_tail)
+  int ctail_lf = 0;           // > 0: levels ctail_lf .. nlev-1 run as one cluster (k_vcycle_ctail) ...
+  int ctail_c = 0;            //   of ctail_c blocks
   float* rf = nullptr;        // precision 1: FP32 residual, right-hand side of each correction cycle
   double* G = nullptr;        // dense pseudo-inverse of the coarsest operator (small coarsest levels)
   char* ws = nullptr;
@@ -341,6 +344,7 @@ StageArgs stage_args(wl_sim* s, int stage) {
   a.nu = (float)s->nu;
   a.stage = stage;
   a.advect = s->o.advect;
+  if (s->D == 3) a.tz = stage3_planes(s->g);
   // f of the body's band box goes to the fine level's ping-pong iterate, which is free
   // until the projection's sweeps
   int lo[3], hi[3];
@@ -453,9 +457,13 @@ void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) 
     t.inv_w = 1.f / w;
     t.st = s->ds;
     t.band = L.band;
-    if (s->g.exit && mode == RES_DIVERGENCE) {
-      float* const* ub[3] = {s->ua, s->ub, s->uc};
-      t.uxe = ub[ubuf][0] + s->g.nc;
+    float* const* ub[3] = {s->ua, s->ub, s->uc};
+    if (s->g.exit && mode == RES_DIVERGENCE) t.uxe = ub[ubuf][0] + s->g.nc;
+    t.wsrc[0] = s->ph ? s->ph : L.x;
+    t.wsrc[1] = s->pl;
+    if (mode == RES_DIVERGENCE) {
+      t.wsrc[2] = ub[ubuf][0];
+      t.wsrc[3] = ub[ubuf][1];
     }
     PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st, side_of(s)));
     return;
@@ -605,9 +613,8 @@ void enq_coarsest(wl_sim* s, int l, const float* z, float* x, cudaStream_t st) {
   PROF(s, st, WL_KCLASS_COARSEST, launch_coarse(s->D, a, st));
 }
 
-// the coarse end of a V-cycle (levels tail_lf .. nlev-1) in one block
-TailArgs tail_args(wl_sim* s) {
-  const int lf = s->tail_lf;
+// the coarse end of a V-cycle (levels lf .. nlev-1) in one block or one cluster
+TailArgs tail_args(wl_sim* s, int lf) {
   TailArgs t{};
   t.nl = s->nlev - lf;
   for (int l = 0; l < t.nl; ++l) {
@@ -638,10 +645,17 @@ void enq_vcycle_core(wl_sim* s, cudaStream_t st) {
     }
     return;
   }
+  if (s->ctail_lf > 0) {  // the coarse levels in one cluster
+    const int lf = s->ctail_lf;
+    for (int l = 1; l < lf; ++l) PROF(s, st, WL_KCLASS_RESTRICT, launch_residual(s->D, res_args(s, l, RES_RESTRICT), st));
+    PROF(s, st, WL_KCLASS_SWEEP_COARSE, launch_vcycle_ctail(s->D, tail_args(s, lf), s->ctail_c, st));
+    for (int l = lf - 1; l >= 0; --l) enq_smooth(s, l, st);
+    return;
+  }
   if (s->tail_lf > 0) {  // the small levels in one block
     const int lf = s->tail_lf;
     for (int l = 1; l < lf; ++l) PROF(s, st, WL_KCLASS_RESTRICT, launch_residual(s->D, res_args(s, l, RES_RESTRICT), st));
-    PROF(s, st, WL_KCLASS_SWEEP_COARSE, launch_vcycle_tail(s->D, tail_args(s), st));
+    PROF(s, st, WL_KCLASS_SWEEP_COARSE, launch_vcycle_tail(s->D, tail_args(s, lf), st));
     for (int l = lf - 1; l >= 0; --l) enq_smooth(s, l, st);
     return;
   }
@@ -1111,6 +1125,30 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
         break;
       if (lf + 2 <= s->nlev) s->tail_lf = lf;
     }
+    // the same from a larger level in one thread-block cluster (16 blocks, else 8): its
+    // levels are split between the blocks' shared memories, so tens of thousands of
+    // cells fit, and the sweeps of a level that would take a launch each run between
+    // cluster barriers.  Taken where it covers more levels than the one-block tail, and
+    // with FP32 coarse levels only (a tail keeps its levels in FP32, which would take
+    // levels the 16-bit modes store in 16 bits out of them).
+    if (!std::getenv("WL_NO_CTAIL") && s->o.coarse_precision == WL_COARSE_FP32) {
+      for (int C = 16; C >= 8 && !s->ctail_lf; C -= 8) {
+        int best = 0;
+        long long cl_cells = 0;
+        for (int lf = s->nlev - 1; lf >= lmin; --lf) {
+          cl_cells += s->lev[lf].g.nc;
+          if (cl_cells > kCtailCells || s->nlev - lf > kTailMaxLevels ||
+              vcycle_ctail_smem(ndim, n + lf, s->nlev - lf, C) > kTailSmemMax)
+            break;
+          if (lf + 2 <= s->nlev) best = lf;
+        }
+        if (best > 0 && (s->tail_lf == 0 || best < s->tail_lf) &&
+            vcycle_ctail_cluster(ndim, vcycle_ctail_smem(ndim, n + best, s->nlev - best, C), C) == C) {
+          s->ctail_lf = best;
+          s->ctail_c = C;
+        }
+      }
+    }
   }
   int rc = WL_OK;
   if (cudaMallocHost(&s->hs, sizeof(DevState)) != cudaSuccess) rc = fail(s, WL_ENOMEM, "pinned host state");
@@ -1135,9 +1173,12 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       if (l == 0 && s->rf) ok = ok && make_field_map(&s->srf, s->rf, L.g, ndim, SWEEP_CROWS);
       L.tma = ok;
     }
-    // fine residual: 3-D, no periodic side
+    // fine residual: 3-D; with a periodic x / y side when those sides are whole tiles
+    // and the tiles on them are uniform (they patch their halo; see k_resid_tma)
     LevelBuf& L0 = s->lev[0];
-    bool ok = L0.tma && ndim == 3 && s->g.per == 0;
+    const int rtz0 = sweep_planes_per_block(L0.g, L0.band.on ? RESID_UNI_WAVE_BLOCKS : SWEEP_BLOCKS_PER_SM);
+    bool ok = L0.tma && ndim == 3 && !std::getenv("WL_NO_RESID_TMA") &&
+              (!(s->g.per & 3u) || (sweep_wrap_shape_ok(s->g) && !resid_band_wraps(s->g, rtz0 + (rtz0 & 1), L0.band)));
     // pressure boxes with a 1-row halo: 10 rows from j0-1
     if (ok) ok = make_field_map(&s->mph, s->ph ? s->ph : L0.x, L0.g, ndim, SWEEP_TY + 2);
     if (ok && s->pl) ok = make_field_map(&s->mpl, s->pl, L0.g, ndim, SWEEP_TY + 2);
@@ -1868,6 +1909,13 @@ int wl_grad_backward(wl_handle s, const double* gF, double* theta_bar) {
   return WL_OK;
 }
 
+int wl_kernel_paths(wl_handle s, unsigned* paths) {
+  if (!s || !paths) return WL_EINVAL;
+  *paths = (s->resid_tma ? WL_PATH_RESID_STAGED : 0u) | (s->ctail_lf > 0 ? WL_PATH_CLUSTER_TAIL : 0u) |
+           (s->ctail_lf == 0 && s->tail_lf > 0 ? WL_PATH_BLOCK_TAIL : 0u);
+  return WL_OK;
+}
+
 int wl_level_split(wl_handle s, int l, int* split, double* band_fraction) {
   if (!s || l < 0 || l >= s->nlev) return WL_EINVAL;
   const LevelBuf& L = s->lev[l];
@@ -2043,6 +2091,7 @@ BatchSlot batch_slot(wl_sim* s) {
   b.D = s->D;
   b.stage[0] = stage_args(s, 1);
   b.stage[1] = stage_args(s, 2);
+  b.stage[0].tz = b.stage[1].tz = 0;  // the batched launch's block map takes the default planes
   b.body = s->body;
   int lo[3], hi[3];
   b.band = (s->body.kind != 0 && stage_band_box(s->D, s->g, s->body, lo, hi)) ? 1 : 0;
@@ -2060,7 +2109,7 @@ BatchSlot batch_slot(wl_sim* s) {
   b.post = s->o.post;
   for (int l = 0; l < lf; ++l)
     for (int it = 0; it < s->o.post; ++it) b.sweep[l][it] = smooth_args(s, l, it);
-  b.tail = tail_args(s);
+  b.tail = tail_args(s, s->tail_lf);
   b.corr[0] = corr_args(s, s->ub, s->uc, 1.f, 0);
   b.corr[1] = corr_args(s, s->ub, s->ua, 0.5f, 1);
   b.w[0] = 1.f;

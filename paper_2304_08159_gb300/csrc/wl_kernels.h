@@ -18,7 +18,11 @@ struct StageArgs {
   int advect;
   float* fbox;          // if set: f = u0 + dt r(u) of every face in the body's band box (D blocks of
   int blo[3], bn[3];    //   bn[0]*bn[1]*bn[2] values, box origin blo), kept for the mu1 term
+  int tz;               // 3-D two-cell kernel: planes per block (0: the default 32)
 };
+// planes per block of the 3-D stage kernel for grid g: as many blocks as fill the GPU
+// (small grids), at most 32 planes (the z halo is re-read once per block)
+int stage3_planes(const Grid& g);
 // Faces whose f the mu1 term of BDIM reads: the body's band (|d| < eps) and one face
 // beyond, boxed ([lo, hi) per direction, clamped to the grid); false if the box is empty.
 bool stage_band_box(int D, const Grid& g, const Body& b, int* lo, int* hi);
@@ -148,6 +152,12 @@ struct TailArgs {
 };
 int launch_vcycle_tail(int D, const TailArgs& a, cudaStream_t s);
 size_t vcycle_tail_smem(int D, const int (*n)[3], int nl);
+// the same coarse end in one cluster of C blocks (each keeping slices of every level):
+// shared bytes of the largest block, whether a cluster of C such blocks can run (C or
+// 0; sets the kernel's attributes), and the launch
+size_t vcycle_ctail_smem(int D, const int (*n)[3], int nl, int C);
+int vcycle_ctail_cluster(int D, size_t smem, int C);
+int launch_vcycle_ctail(int D, const TailArgs& a, int C, cudaStream_t s);
 
 struct CoarseArgs {
   const float* z;
@@ -212,8 +222,18 @@ struct ResidTmaArgs {
   BandBox band;        // tiles outside it: coefficients 1 (0 on walls), not loaded
   int t0[3];           // first tile of the launch
   const float* uxe;    // divergence mode with a convective exit: the velocity's exit plane
+  // periodic x / y sides: the fields whose halo cells past such a side a tile patches
+  // (pressure hi or the FP32 pressure, pressure lo, and in divergence mode u_x, u_y)
+  const float* wsrc[4];
 };
 int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a, cudaStream_t s, const SideStream* side);
+// A residual tile (64 x 8 cells at i0, j0) on a periodic x or y side of the grid: its
+// stencil reads halo cells past the side
+__host__ __device__ inline bool resid_tile_wraps_xy(const Grid& g, int i0, int j0) {
+  return ((g.per & 1u) && (i0 == 0 || i0 + 64 >= g.n[0])) || ((g.per & 2u) && (j0 == 0 || j0 + 8 >= g.n[1]));
+}
+// whether a tile of the band box (which loads its coefficients) lies on a periodic x / y side
+bool resid_band_wraps(const Grid& g, int tz, const BandBox& b);
 int launch_wait_probe(uint64_t limit_ns, int* gave_up, cudaStream_t s);
 // planes per block of the sweep kernels for blocks_per_sm resident blocks
 int sweep_planes_per_block(const Grid& g, int blocks_per_sm);

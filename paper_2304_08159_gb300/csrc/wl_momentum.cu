@@ -293,8 +293,9 @@ __device__ __forceinline__ void stage3_body(const StageArgs& a, const uint3 bid)
   const Grid& g = a.g;
   const int tid = threadIdx.x, lane = tid & 31, ty = tid >> 5;
   const int i0 = bid.x * S3_TX, j0 = bid.y * S3_TY;
-  const int k0 = bid.z * S3_TZ;
-  const int k1 = min(k0 + S3_TZ, g.n[2]);
+  const int tzb = a.tz > 0 ? a.tz : S3_TZ;
+  const int k0 = bid.z * tzb;
+  const int k1 = min(k0 + tzb, g.n[2]);
   const int i = i0 + 2 * lane, j = j0 + ty;
   const bool own_cell = (i < g.n[0]) && (j < g.n[1]);  // n_0 even: both cells or neither
   const float dt = *a.dt;
@@ -573,13 +574,43 @@ __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0,
   bdim_band_body<D>(a, b, lo0, lo1, lo2, bx, by, bz, blockIdx);
 }
 
+// Planes per block of k_stage3: 32 when that gives two waves of blocks (3 resident per
+// SM) or more; else the fewest waves times the planes a block stages (its own and the 3
+// of its z halo).
+int stage3_planes(const Grid& g) {
+  static int nsm = 0;
+  if (nsm <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        nsm <= 0) {
+      cudaGetLastError();
+      nsm = 152;
+    }
+  }
+  const long long cols = (long long)((g.n[0] + S3_TX - 1) / S3_TX) * ((g.n[1] + S3_TY - 1) / S3_TY);
+  const long long wave = 3LL * nsm;
+  if (cols * ((g.n[2] + S3_TZ - 1) / S3_TZ) >= 2 * wave) return S3_TZ;
+  int best = S3_TZ;
+  double best_cost = 1e300;
+  for (int tz = S3_TZ; tz >= 4; --tz) {
+    const long long nb = cols * ((g.n[2] + tz - 1) / tz);
+    const double cost = (double)((nb + wave - 1) / wave) * (tz + 3);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = tz;
+    }
+  }
+  return best;
+}
+
 // ---------------------------------------------------------------------------
 int launch_stage(int D, const StageArgs& a, cudaStream_t s) {
   const Grid& g = a.g;
   dim3 blk(256);
   const bool v1 = std::getenv("WL_STAGE_V1") != nullptr;  // the one-cell-per-thread kernel
   if (D == 3 && g.n[0] % 2 == 0 && !v1) {
-    dim3 grd((g.n[0] + S3_TX - 1) / S3_TX, (g.n[1] + S3_TY - 1) / S3_TY, (g.n[2] + S3_TZ - 1) / S3_TZ);
+    const int tz = a.tz > 0 ? a.tz : S3_TZ;
+    dim3 grd((g.n[0] + S3_TX - 1) / S3_TX, (g.n[1] + S3_TY - 1) / S3_TY, (g.n[2] + tz - 1) / tz);
     if (a.advect)
       k_stage3<true><<<grd, blk, 0, s>>>(a);
     else

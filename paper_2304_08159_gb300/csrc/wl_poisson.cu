@@ -14,6 +14,7 @@
 // FP64 conjugate gradients, piecewise-constant prolongation fused into the first
 // smoothing sweep, red-black Gauss-Seidel sweeps (red: i+j+k even, first).  Cells
 // whose row is zero (all faces blocked by the body) carry x = 0.
+#include <cooperative_groups.h>
 #include <type_traits>
 
 #include "wl_dev.cuh"
@@ -1887,6 +1888,266 @@ int launch_vcycle_tail(int D, const TailArgs& a, cudaStream_t s) {
   else
     k_vcycle_tail<2><<<1, kTailThreads, smem, s>>>(a);
   return 0;
+}
+
+// ---------------------------------------------------------------------------
+// k_vcycle_ctail: the coarse end of a V-cycle in one thread-block cluster.  The levels
+// are cut into slices along their slowest direction (z in 3-D, y in 2-D); block r of
+// the C blocks keeps slices [ceil(r n/C), ceil((r+1) n/C)) of every level (the D face
+// coefficients, the right-hand side and the iterate) in its shared memory, and reads
+// a neighbouring slice another block keeps through distributed shared memory.  A
+// cluster barrier separates the phases (load, each restriction, the coarsest solve,
+// each prolongation and each colour of each sweep).  The arithmetic, and its order, is
+// k_vcycle_tail's, so the bits are too; the cluster lets the tail take levels too large
+// for one block (tens of thousands of cells), which otherwise cost a launch per sweep.
+namespace {
+constexpr int kCtailMaxC = 16;
+
+struct CtailLayout {  // per level l and block r: first slice and float offset of its data
+  int lo[kTailMaxLevels][kCtailMaxC + 1];
+  int base[kTailMaxLevels][kCtailMaxC];
+  int zd;             // float offset of the coarsest right-hand side in FP64 (even)
+  int total;          // floats of the largest block's share, zd included
+};
+
+template <int D>
+__host__ __device__ inline void ctail_layout(const int (*n)[3], int nl, int C, CtailLayout& Ly) {
+  int tot_max = 0;
+  for (int r = 0; r < C; ++r) {
+    int off = 0;
+    for (int l = 0; l < nl; ++l) {
+      const int S = D == 3 ? n[l][2] : n[l][1], Z = D == 3 ? n[l][0] * n[l][1] : n[l][0];
+      const int lo = (r * S + C - 1) / C, hi = ((r + 1) * S + C - 1) / C;
+      Ly.lo[l][r] = lo;
+      Ly.lo[l][r + 1] = hi;
+      Ly.base[l][r] = off;
+      off += (D + 2) * (hi - lo) * Z;
+    }
+    off = (off + 1) & ~1;
+    if (off > tot_max) tot_max = off;
+  }
+  // the FP64 coarsest right-hand side sits after the largest share, the same offset in every block
+  const int ncc = n[nl - 1][0] * n[nl - 1][1] * n[nl - 1][2];
+  Ly.zd = tot_max;
+  Ly.total = tot_max + 2 * ncc;
+}
+}  // namespace
+
+size_t vcycle_ctail_smem(int D, const int (*n)[3], int nl, int C) {
+  CtailLayout Ly;
+  if (D == 3)
+    ctail_layout<3>(n, nl, C, Ly);
+  else
+    ctail_layout<2>(n, nl, C, Ly);
+  return sizeof(float) * (size_t)Ly.total;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kTailThreads) k_vcycle_ctail(TailArgs a) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) float tsm[];
+  __shared__ CtailLayout Ly;
+  const int C = (int)cl.num_blocks(), r = (int)cl.block_rank(), tid = threadIdx.x;
+  if (tid == 0) ctail_layout<D>(a.n, a.nl, C, Ly);
+  __syncthreads();
+  auto S_of = [&](int l) { return D == 3 ? a.n[l][2] : a.n[l][1]; };
+  auto Z_of = [&](int l) { return D == 3 ? a.n[l][0] * a.n[l][1] : a.n[l][0]; };
+  // field f (0..D-1 coefficients, D right-hand side, D+1 iterate) of slice s of level l,
+  // in the shared memory of the block that keeps it
+  auto slice = [&](int l, int f, int s) -> float* {
+    const int S = S_of(l), ow = (s * C) / S;
+    const int lo = Ly.lo[l][ow], cnt = Ly.lo[l][ow + 1] - lo, Z = Z_of(l);
+    float* p = tsm + Ly.base[l][ow] + (size_t)f * cnt * Z + (size_t)(s - lo) * Z;
+    return ow == r ? p : cl.map_shared_rank(p, ow);
+  };
+  auto mine = [&](int l, int f) { return tsm + Ly.base[l][r] + (size_t)f * (Ly.lo[l][r + 1] - Ly.lo[l][r]) * Z_of(l); };
+  // load this block's slices: coefficients of every level, the first level's right-hand side
+  for (int l = 0; l < a.nl; ++l) {
+    const int Z = Z_of(l), q0 = Ly.lo[l][r] * Z, nq = (Ly.lo[l][r + 1] - Ly.lo[l][r]) * Z;
+    for (int c = 0; c < D; ++c) {
+      float* b = mine(l, c);
+      for (int q = tid; q < nq; q += kTailThreads) b[q] = ld_st(a.L[l][c], a.st[l], q0 + q);
+    }
+    if (l == 0) {
+      float* z0 = mine(0, D);
+      for (int q = tid; q < nq; q += kTailThreads) z0[q] = a.zmul * ld_st(a.z, a.st[0], q0 + q);
+    }
+  }
+  cl.sync();
+  // restriction down to the coarsest level (child (2I, 2J, 2K) first; z pairs, then x,
+  // then y, as k_vcycle_tail)
+  for (int l = 0; l + 1 < a.nl; ++l) {
+    const int f0 = a.n[l][0], c0 = a.n[l + 1][0], c1 = a.n[l + 1][1];
+    const int Zc = Z_of(l + 1), lo = Ly.lo[l + 1][r], nq = (Ly.lo[l + 1][r + 1] - lo) * Zc;
+    float* zc = mine(l + 1, D);
+    for (int m = tid; m < nq; m += kTailThreads) {
+      const int q = lo * Zc + m;  // the coarse cell's index in its level
+      const int I = q % c0, t = q / c0;
+      float sum;
+      if (D == 3) {
+        const int J = t % c1, K = t / c1;
+        const float* s0 = slice(l, D, 2 * K);
+        const float* s1 = slice(l, D, 2 * K + 1);
+        const int b0 = 2 * I + f0 * 2 * J;
+        const float a00 = s0[b0] + s1[b0];
+        const float a10 = s0[b0 + 1] + s1[b0 + 1];
+        const float a01 = s0[b0 + f0] + s1[b0 + f0];
+        const float a11 = s0[b0 + f0 + 1] + s1[b0 + f0 + 1];
+        sum = (a00 + a10) + (a01 + a11);
+      } else {
+        const int J = t;
+        const float* s0 = slice(l, D, 2 * J);
+        const float* s1 = slice(l, D, 2 * J + 1);
+        sum = (s0[2 * I] + s0[2 * I + 1]) + (s1[2 * I] + s1[2 * I + 1]);
+      }
+      zc[m] = sum;
+    }
+    cl.sync();
+  }
+  // coarsest level: x = G z in FP64, each block its own slices' rows
+  {
+    const int lc = a.nl - 1;
+    const int nc = a.n[lc][0] * a.n[lc][1] * a.n[lc][2], Z = Z_of(lc);
+    double* zd = reinterpret_cast<double*>(tsm + Ly.zd);
+    for (int i = tid; i < nc; i += kTailThreads) zd[i] = (double)slice(lc, D, i / Z)[i % Z];
+    __syncthreads();
+    const int lo = Ly.lo[lc][r], nq = (Ly.lo[lc][r + 1] - lo) * Z;
+    float* xc = mine(lc, D + 1);
+    for (int m = tid; m < nq; m += kTailThreads) {
+      const int i = lo * Z + m;
+      double acc = 0.0;
+#pragma unroll 16
+      for (int jj = 0; jj < nc; ++jj) acc += __ldg(a.G + (long long)jj * nc + i) * zd[jj];
+      xc[m] = (float)acc;
+    }
+    cl.sync();
+  }
+  // up: prolong (piecewise constant) and smooth each level
+  for (int l = a.nl - 2; l >= 0; --l) {
+    const int n0 = a.n[l][0], n1 = a.n[l][1], n2 = a.n[l][2];
+    const int c0 = a.n[l + 1][0], c1 = a.n[l + 1][1];
+    const int S = S_of(l), Z = Z_of(l), lo = Ly.lo[l][r], cnt = Ly.lo[l][r + 1] - lo, nq = cnt * Z;
+    float* xl = mine(l, D + 1);
+    const float* zl = mine(l, D);
+    for (int m = tid; m < nq; m += kTailThreads) {
+      const int q = lo * Z + m;
+      const int i = q % n0, t = q / n0;
+      const int j = t % n1, k = t / n1;
+      const int sc = D == 3 ? (k >> 1) : (j >> 1);
+      const int w = D == 3 ? (i >> 1) + c0 * (j >> 1) : (i >> 1);
+      xl[m] = 0.f + slice(l + 1, D + 1, sc)[w];
+    }
+    (void)c1;
+    cl.sync();
+    const int nd[3] = {n0, n1, n2};
+    const int h0 = n0 >> 1;            // cells of one colour per row (n0 even above the coarsest)
+    const int rows = cnt * (Z / n0);   // this block's rows
+    const int nhalf = rows * h0;
+    for (int sw = 0; sw < a.post; ++sw) {
+      for (int color = 0; color < 2; ++color) {
+        for (int m = tid; m < nhalf; m += kTailThreads) {
+          const int rw = m / h0;
+          const int grow = lo * (Z / n0) + rw;  // the row's index in the level
+          const int j = D == 3 ? grow % n1 : grow, k = D == 3 ? grow / n1 : 0;
+          const int i = 2 * (m - rw * h0) + ((j + k + color) & 1);
+          const int I[3] = {i, j, k};
+          const int sl = D == 3 ? k : j;   // the cell's slice and its place in it
+          const int w = D == 3 ? i + n0 * j : i;
+          const int ml = (sl - lo) * Z + w;
+          float sum = 0.f, dg = 0.f;
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            float Lu = 0.f, xu = 0.f, xd = 0.f;
+            const bool per = (a.per >> d) & 1u;
+            const float* Ld = mine(l, d);
+            if (d < D - 1) {  // a direction within the slice
+              const int st = d == 0 ? 1 : n0;
+              if (I[d] + 1 < nd[d]) {
+                Lu = Ld[ml + st];
+                xu = xl[ml + st];
+              } else if (per) {
+                Lu = Ld[ml - (nd[d] - 1) * st];
+                xu = xl[ml - (nd[d] - 1) * st];
+              }
+              if (I[d] > 0)
+                xd = xl[ml - st];
+              else if (per)
+                xd = xl[ml + (nd[d] - 1) * st];
+            } else {  // across slices
+              if (I[d] + 1 < nd[d]) {
+                Lu = slice(l, d, sl + 1)[w];
+                xu = slice(l, D + 1, sl + 1)[w];
+              } else if (per) {
+                Lu = slice(l, d, 0)[w];
+                xu = slice(l, D + 1, 0)[w];
+              }
+              if (I[d] > 0)
+                xd = slice(l, D + 1, sl - 1)[w];
+              else if (per)
+                xd = slice(l, D + 1, S - 1)[w];
+            }
+            const float Ll = Ld[ml];
+            sum = fmaf(Lu, xu, sum);
+            sum = fmaf(Ll, xd, sum);
+            dg += Lu + Ll;
+          }
+          xl[ml] = (dg > 0.f) ? __fdividef(sum - zl[ml], dg) : 0.f;
+        }
+        cl.sync();
+      }
+    }
+  }
+  {
+    const int Z = Z_of(0), q0 = Ly.lo[0][r] * Z, nq = (Ly.lo[0][r + 1] - Ly.lo[0][r]) * Z;
+    const float* x0 = mine(0, D + 1);
+    for (int q = tid; q < nq; q += kTailThreads) st_st(a.x, a.st[0], q0 + q, x0[q]);
+  }
+}
+
+// cluster size C (8 or 16) whose blocks fit with `smem` bytes each, or 0
+int vcycle_ctail_cluster(int D, size_t smem, int C) {
+  auto fn = D == 3 ? (void*)k_vcycle_ctail<3> : (void*)k_vcycle_ctail<2>;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      (C > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)) {
+    cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(kTailThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclus = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclus, fn, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return nclus >= 1 ? C : 0;
+}
+
+int launch_vcycle_ctail(int D, const TailArgs& a, int C, cudaStream_t s) {
+  const size_t smem = vcycle_ctail_smem(D, a.n, a.nl, C);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(kTailThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if (D == 3) return cudaLaunchKernelEx(&cfg, k_vcycle_ctail<3>, a) == cudaSuccess ? 0 : -1;
+  return cudaLaunchKernelEx(&cfg, k_vcycle_ctail<2>, a) == cudaSuccess ? 0 : -1;
 }
 
 // ph + pl rounded to FP32

@@ -746,8 +746,13 @@ struct ResidLayout {
   static constexpr size_t bytes = ((size_t)SA * ASZ + (size_t)SB * BSZ) * sizeof(float);
 };
 
-template <bool DIV, bool DF, bool UNI>
-__global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_constant__ ResidMaps m, ResidTmaArgs a) {
+// WRAP (uniform tiles only): the tiles on a periodic x or y side, whose halo cells past
+// the side are patched from the wrapped cells (the others' tiles: none).  Planes past a
+// periodic z side are staged from their wrapped planes in every variant.
+template <bool DIV, bool DF, bool UNI, bool WRAP>
+__global__ void __launch_bounds__(256, WRAP ? 4 : UNI ? 5 : 1) k_resid_tma(const __grid_constant__ ResidMaps m,
+                                                                             ResidTmaArgs a) {
+  static_assert(UNI || !WRAP, "wrapping tiles are uniform");
   using LY = ResidLayout<DIV, DF, UNI>;
   constexpr int SA = LY::SA, SB = LY::SB, NBAR = LY::NBAR;
   extern __shared__ unsigned char smem_raw[];
@@ -763,6 +768,8 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
   if (i0 >= g.n[0] || j0 >= g.n[1] || kb >= g.n[2]) return;
   const int ke = min(kb + a.tz, g.n[2]);
   if (tile_in_band(a.band, 3, i0, j0, kb, ke) == UNI) return;  // the other variant's tile
+  if (UNI && resid_tile_wraps_xy(g, i0, j0) != WRAP) return;    // the other launch's tile
+  const bool px = g.per & 1u, py = g.per & 2u, pz = g.per & 4u;
   const int pa_first = kb - 1, pb_first = kb, p_last = ke;
   // column slot / plane slot of plane p (fields at the LY offsets)
   auto A = [&](int p) -> float* { return abase + (size_t)((p - pa_first) % SA) * LY::ASZ; };
@@ -786,11 +793,12 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
     const uint32_t br = bar(p);
     mbar_expect_tx(br, col + (plane ? pln : 0u));
     const int x = i0 - 4;
+    const int pp = pz ? wrap_per(p, g.n[2]) : p;  // a plane past a periodic z side: its wrapped plane
     float* Ap = A(p);
-    tma_load(smem_addr(Ap), &m.ph, x, j0 - 1, p, br, 3);
-    if (DF) tma_load(smem_addr(Ap + LY::oPL), &m.pl, x, j0 - 1, p, br, 3);
-    if (!UNI) tma_load(smem_addr(Ap + LY::oL2), &m.L2, x, j0, p, br, 3);
-    if (DIV) tma_load(smem_addr(Ap + LY::oU2), &m.u2, x, j0, p, br, 3);
+    tma_load(smem_addr(Ap), &m.ph, x, j0 - 1, pp, br, 3);
+    if (DF) tma_load(smem_addr(Ap + LY::oPL), &m.pl, x, j0 - 1, pp, br, 3);
+    if (!UNI) tma_load(smem_addr(Ap + LY::oL2), &m.L2, x, j0, pp, br, 3);
+    if (DIV) tma_load(smem_addr(Ap + LY::oU2), &m.u2, x, j0, pp, br, 3);
     if (plane) {
       float* Bp = B(p);
       if (DIV) {
@@ -805,6 +813,77 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
       }
     }
   };
+  // WRAP: the halo cells past a periodic x / y side that the stencil reads, which the copy
+  // engine zero-fills, hold the wrapped cells' values: the pressure boxes' column 3 / 68
+  // (x = -1 / n0; rows 1..8, the tile's rows) and row 0 / 9 (y = -1 / n1; columns 4..67),
+  // in divergence mode also the x-velocity box's column 68 and the y-velocity box's row 8
+  // (the upper faces at x = n0, y = n1).  Only planes the block computes need them.  The
+  // entries form one list (left, right, top, bottom strips); thread t takes entries t
+  // and t + 256, each with its shared offset (column slot, or for a velocity the plane
+  // slot), its field (0 pressure hi, 1 lo, 2 u_x, 3 u_y) and the wrapped cell's index
+  // in its plane.  A plane's values are read from global memory one plane ahead.
+  constexpr int NE = 2;
+  int we_off[NE], we_f[NE];
+  unsigned we_q[NE];
+  float we_v[NE];
+  if constexpr (WRAP) {
+    const int n0 = g.n[0], n1 = g.n[1], nfp = DF ? 2 : 1;
+    const bool wl = px && i0 == 0, wr = px && i0 + TX >= n0;
+    const bool wt = py && j0 == 0, wb = py && j0 + TY >= n1;
+    const int nl = wl ? nfp * TY : 0, nr = wr ? nfp * TY + (DIV ? TY : 0) : 0;
+    const int nt = wt ? nfp * TX : 0, nb = wb ? nfp * TX + (DIV ? TX : 0) : 0;
+#pragma unroll
+    for (int r = 0; r < NE; ++r) {
+      int t = tid + 256 * r, off = -1, f = 0;
+      unsigned q = 0u;
+      if (t < nl) {  // x = -1: cell n0 - 1 of the row
+        f = t / TY;
+        const int row = t - f * TY;
+        off = (f == 1 ? LY::oPL : 0) + (row + 1) * BX + 3;
+        q = (unsigned)(n0 - 1) + (unsigned)n0 * (unsigned)(j0 + row);
+      } else if ((t -= nl) < nr) {  // x = n0: cell 0 of the row
+        f = t / TY;
+        const int row = t - f * TY;
+        if (f < nfp) {
+          off = (f == 1 ? LY::oPL : 0) + (row + 1) * BX + 4 + TX;
+        } else {
+          f = 2;
+          off = LY::oU0 + row * BX + 4 + TX;
+        }
+        q = (unsigned)n0 * (unsigned)(j0 + row);
+      } else if ((t -= nr) < nt) {  // y = -1: row n1 - 1
+        f = t / TX;
+        const int col = t - f * TX;
+        off = (f == 1 ? LY::oPL : 0) + col + 4;
+        q = (unsigned)(i0 + col) + (unsigned)n0 * (unsigned)(n1 - 1);
+      } else if ((t -= nt) < nb) {  // y = n1: row 0
+        f = t / TX;
+        const int col = t - f * TX;
+        if (f < nfp) {
+          off = (f == 1 ? LY::oPL : 0) + (TY + 1) * BX + col + 4;
+        } else {
+          f = 3;
+          off = LY::oU1 + TY * BX + col + 4;
+        }
+        q = (unsigned)(i0 + col);
+      }
+      we_off[r] = off;
+      we_f[r] = f;
+      we_q[r] = q;
+      we_v[r] = 0.f;
+    }
+  }
+  auto wload = [&](int p) {  // the patch values of plane p (kb <= p < ke)
+    const long long o = (long long)g.n[0] * g.n[1] * p;
+#pragma unroll
+    for (int r = 0; r < NE; ++r)
+      if (we_off[r] >= 0 && wl_in(o + we_q[r], g.nc, WL_DBG_RESID)) we_v[r] = __ldg(a.wsrc[we_f[r]] + o + we_q[r]);
+  };
+  auto wstore = [&](int p) {
+#pragma unroll
+    for (int r = 0; r < NE; ++r)
+      if (we_off[r] >= 0) (we_f[r] >= 2 ? B(p) : A(p))[we_off[r]] = we_v[r];
+  };
   auto bail = [&](int p_fail) {
     if (tid == 0) {
       atomicOr(&a.st->status, 4);
@@ -814,9 +893,14 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
   };
   if (tid == 0)
     for (int p = pa_first; p <= min(pa_first + 2, p_last); ++p) issue(p);
+  if constexpr (WRAP) wload(kb);  // plane kb's patches, read while its copies are in flight
   for (int p = pa_first; p <= kb; ++p) {
     const bool ok = mbar_wait(bar(p), phase(p));
     if (__syncthreads_or(!ok)) return bail(p);
+  }
+  if constexpr (WRAP) {
+    wstore(kb);  // read from the next iteration on, after its barrier
+    if (kb + 1 < ke) wload(kb + 1);
   }
   const float inv = DIV ? a.inv_w * a.st->inv_dtf : 0.f;
   unsigned mbits = 0u;
@@ -825,6 +909,12 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
     {
       const bool ok = mbar_wait(bar(k + 1), phase(k + 1));
       if (__syncthreads_or(!ok)) return bail(k + 1);
+    }
+    if constexpr (WRAP) {
+      // plane k+1's halo (computed next iteration, after its barrier); plane k's compute
+      // below reads only plane k+1's own cells
+      if (k + 1 < ke) wstore(k + 1);
+      if (k + 2 < ke) wload(k + 2);
     }
     // every thread is past plane k-2's column fields and plane k-1's plane fields
     if (tid == 0) {
@@ -860,10 +950,11 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
       if (DIV) {
         const float* U0 = B0 + LY::oU0;
         const float* U1 = B0 + LY::oU1;
-        const float uxp = (gi + 1 < g.n[0]) ? U0[c + 1]
-                                            : ((a.uxe && in) ? __ldg(a.uxe + gj + (long long)g.n[1] * k) : g.U[0]);
-        const float uyp = (gj + 1 < g.n[1]) ? U1[c + BX] : g.U[1];
-        const float uzp = (k + 1 < g.n[2]) ? (Ap + LY::oU2)[c] : g.U[2];
+        const float uxp = (gi + 1 < g.n[0] || px)
+                              ? U0[c + 1]
+                              : ((a.uxe && in) ? __ldg(a.uxe + gj + (long long)g.n[1] * k) : g.U[0]);
+        const float uyp = (gj + 1 < g.n[1] || py) ? U1[c + BX] : g.U[1];
+        const float uzp = (k + 1 < g.n[2] || pz) ? (Ap + LY::oU2)[c] : g.U[2];
         float div = 0.f;
         div += uxp - U0[c];
         div += uyp - U1[c];
@@ -876,12 +967,12 @@ __global__ void __launch_bounds__(256, UNI ? 5 : 1) k_resid_tma(const __grid_con
       }
       // face coefficients: staged, or (UNI) 1 inside the grid and 0 across a wall
       if (UNI) {
-        cf[h][0] = gi + 1 < g.n[0] ? 1.f : 0.f;
-        cf[h][1] = gi > 0 ? 1.f : 0.f;
-        cf[h][2] = gj + 1 < g.n[1] ? 1.f : 0.f;
-        cf[h][3] = gj > 0 ? 1.f : 0.f;
-        cf[h][4] = k + 1 < g.n[2] ? 1.f : 0.f;
-        cf[h][5] = k > 0 ? 1.f : 0.f;
+        cf[h][0] = (gi + 1 < g.n[0] || px) ? 1.f : 0.f;
+        cf[h][1] = (gi > 0 || px) ? 1.f : 0.f;
+        cf[h][2] = (gj + 1 < g.n[1] || py) ? 1.f : 0.f;
+        cf[h][3] = (gj > 0 || py) ? 1.f : 0.f;
+        cf[h][4] = (k + 1 < g.n[2] || pz) ? 1.f : 0.f;
+        cf[h][5] = (k > 0 || pz) ? 1.f : 0.f;
       } else {
         cf[h][0] = L0[c + 1];
         cf[h][1] = L0[c];
@@ -1050,28 +1141,49 @@ double band_tile_fraction(int D, const Grid& g, int tz, const BandBox& b) {
   return band / all;
 }
 
-template <bool DIV, bool DF, bool UNI>
+template <bool DIV, bool DF, bool UNI, bool WRAP>
 void launch_resid_tma_v(const ResidMaps& m, const ResidTmaArgs& a, dim3 grd, cudaStream_t s) {
   const size_t smem = ResidLayout<DIV, DF, UNI>::bytes + ResidLayout<DIV, DF, UNI>::NBAR * sizeof(uint64_t) + 128;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_resid_tma<DIV, DF, UNI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_resid_tma<DIV, DF, UNI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_resid_tma<DIV, DF, UNI, WRAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_resid_tma<DIV, DF, UNI, WRAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     attr = true;
   }
-  k_resid_tma<DIV, DF, UNI><<<grd, 256, smem, s>>>(m, a);
+  k_resid_tma<DIV, DF, UNI, WRAP><<<grd, 256, smem, s>>>(m, a);
 }
+template <bool UNI, bool WRAP>
+void launch_resid_tma_w(const ResidMaps& m, const ResidTmaArgs& a, dim3 grd, cudaStream_t s) {
+  if (a.div && a.df)
+    launch_resid_tma_v<true, true, UNI, WRAP>(m, a, grd, s);
+  else if (a.div)
+    launch_resid_tma_v<true, false, UNI, WRAP>(m, a, grd, s);
+  else if (a.df)
+    launch_resid_tma_v<false, true, UNI, WRAP>(m, a, grd, s);
+  else
+    launch_resid_tma_v<false, false, UNI, WRAP>(m, a, grd, s);
+}
+// the loading tiles, or the uniform ones (with a second launch for the tiles on a
+// periodic x / y side)
 template <bool UNI>
 void launch_resid_tma_u(const ResidMaps& m, const ResidTmaArgs& a, dim3 grd, cudaStream_t s) {
-  if (a.div && a.df)
-    launch_resid_tma_v<true, true, UNI>(m, a, grd, s);
-  else if (a.div)
-    launch_resid_tma_v<true, false, UNI>(m, a, grd, s);
-  else if (a.df)
-    launch_resid_tma_v<false, true, UNI>(m, a, grd, s);
-  else
-    launch_resid_tma_v<false, false, UNI>(m, a, grd, s);
+  launch_resid_tma_w<UNI, false>(m, a, grd, s);
+  if (UNI && (a.g.per & 3u)) launch_resid_tma_w<true, true>(m, a, grd, s);
+}
+
+bool resid_band_wraps(const Grid& g, int tz, const BandBox& b) {
+  if (!(g.per & 3u)) return false;
+  if (!b.on) return true;  // every tile loads its coefficients
+  int lo[3], hi[3];
+  band_tiles(g.n[0], TX, 4, b.lo[0], b.hi[0], lo[0], hi[0]);
+  band_tiles(g.n[1], TY, 2, b.lo[1], b.hi[1], lo[1], hi[1]);
+  band_tiles(g.n[2], tz, 2, b.lo[2], b.hi[2], lo[2], hi[2]);
+  if (hi[0] <= lo[0] || hi[1] <= lo[1] || hi[2] <= lo[2]) return false;
+  for (int tj = lo[1]; tj < hi[1]; ++tj)
+    for (int ti = lo[0]; ti < hi[0]; ++ti)
+      if (resid_tile_wraps_xy(g, ti * TX, tj * TY)) return true;
+  return false;
 }
 
 int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a0, cudaStream_t s, const SideStream* side) {

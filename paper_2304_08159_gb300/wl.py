@@ -39,6 +39,7 @@ WL_FIELD_EXIT = 7
 WL_BODY_NONE = 0
 WL_BODY_SPHERE = 1
 WL_BODY_TORUS = 2
+WL_PATH_RESID_STAGED, WL_PATH_CLUSTER_TAIL, WL_PATH_BLOCK_TAIL = 1, 2, 4
 WL_BODY_FIELD = 3
 
 WL_COARSE_FP32 = 0
@@ -53,7 +54,7 @@ EXPORTS = (
     "wl_project", "wl_gmg_vcycle", "wl_forces", "wl_viscous_force", "wl_get_field", "wl_set_field", "wl_get_dt",
     "wl_set_dt", "wl_get_time", "wl_status", "wl_profile_step", "wl_graph_kernels", "wl_levels", "wl_level_dims",
     "wl_destroy", "wl_last_error", "wl_forces_noalloc", "wl_wait_probe", "wl_step_batch",
-    "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split",
+    "wl_grad_workspace_bytes", "wl_grad_forward", "wl_grad_backward", "wl_level_split", "wl_kernel_paths",
     "wl_state_bytes", "wl_save", "wl_load", "wl_get_metrics",
     "wl_batch_create", "wl_batch_step", "wl_batch_destroy", "wl_batch_last_error", "wl_event_elapsed",
     "wl_debug_bounds",
@@ -129,6 +130,7 @@ def load(path: str = LIB_PATH):
         "wl_grad_forward": (I, [H, I, I, P, ctypes.c_size_t, DP]),
         "wl_grad_backward": (I, [H, DP, DP]),
         "wl_level_split": (I, [H, I, IP, DP]),
+        "wl_kernel_paths": (I, [H, ctypes.POINTER(ctypes.c_uint)]),
         "wl_state_bytes": (ctypes.c_size_t, [H]),
         "wl_get_metrics": (I, [H, DP, I, IP]),
         "wl_batch_create": (I, [ctypes.c_longlong, ctypes.POINTER(ctypes.c_void_p)]),
@@ -594,6 +596,12 @@ class Sim:
                                      tb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         self._check(rc, "wl_grad_backward")
         return (tb, rc) if return_status else tb
+
+    def kernel_paths(self):
+        """Bits of the kernel paths the step takes (wl_kernel_paths: WL_PATH_*)."""
+        v = ctypes.c_uint(0)
+        self._check(load().wl_kernel_paths(self.h, ctypes.byref(v)), "wl_kernel_paths")
+        return v.value
 
     def level_split(self, l=0):
         """(split, band_fraction) of level l's staged kernels (wl_level_split)."""

@@ -343,6 +343,109 @@ def test_vcycle_tail_matches_per_level_kernels(case, monkeypatch):
     assert np.array_equal(a.get(1), b.get(1))
 
 
+CTAIL_CASES = [
+    dict(id="sph96x48x48", dims=(96, 48, 48), nu=0.02, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=1, center=(30.2, 23.7, 24.4), radius=7.0)),
+    dict(id="tgv64", dims=(64, 64, 64), nu=0.01, U=(0.0, 0.0, 0.0), periodic=7, body=None, ic=1),
+    dict(id="zper128x64x64", dims=(128, 64, 64), nu=0.01, U=(1.0, 0.0, 0.0), periodic=4,
+         body=dict(kind=1, center=(40.0, 31.6, 3.0), radius=8.0)),
+    dict(id="odd72x40x56", dims=(72, 40, 56), nu=0.02, U=(0.7, 0.1, 0.0), periodic=2,
+         body=dict(kind=2, center=(24.0, 20.2, 27.7), radius=9.0, radius2=3.0)),
+    dict(id="cyl256x128", dims=(256, 128), nu=0.05, U=(1.0, 0.0), periodic=0,
+         body=dict(kind=1, center=(64.3, 63.8), radius=12.0)),
+    dict(id="per128", dims=(128, 128), nu=0.02, U=(0.0, 0.0), periodic=3, body=None, ic=1),
+    # 16-bit coarse levels: the cluster tail is not taken (it would keep a level the mode
+    # stores in 16 bits in FP32); the one-block tail runs as before
+    dict(id="bf16sph192x96x96", dims=(192, 96, 96), nu=0.02, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=1, center=(60.2, 47.7, 48.4), radius=10.0), kw=dict(coarse_precision="bf16")),
+]
+
+
+@pytest.mark.parametrize("case", CTAIL_CASES, ids=lambda c: c["id"])
+def test_cluster_tail_matches_block_tail_and_per_level(case, monkeypatch):
+    """The coarse levels in one thread-block cluster (k_vcycle_ctail: slices of every
+    level in the blocks' shared memories, neighbour slices through distributed shared
+    memory), in one block (k_vcycle_tail) and level by level: three steps give identical
+    bits, and the cluster takes more levels (fewer coarse launches per step).  With
+    16-bit coarse levels the cluster tail is not taken, and the per-level sweeps store
+    the iterate in 16 bits between sweeps while the block tail keeps it in FP32, so
+    there only the first two agree bitwise."""
+    kw = case.get("kw", {})
+    sims = []
+    for env in (None, "WL_NO_CTAIL", "WL_NO_TAIL"):
+        if env:
+            monkeypatch.setenv(env, "1")
+        sim, _ = make_pair(case, oracle=False, **kw)
+        if env:
+            monkeypatch.delenv(env)
+        if case.get("ic"):
+            sim.set_ic(case["ic"], 1.0)
+        sims.append(sim)
+    launches = [s.profile_step(1)["sweep_coarse"][1] for s in sims]
+    from paper_2304_08159_gb300 import wl
+
+    cluster = [bool(s.kernel_paths() & wl.WL_PATH_CLUSTER_TAIL) for s in sims]
+    assert cluster == ["coarse_precision" not in kw, False, False], cluster
+    for s in sims:
+        s.step(3)
+    a, b, c = sims
+    assert np.array_equal(a.get(0), b.get(0)) and np.array_equal(a.get(1), b.get(1))
+    if "coarse_precision" not in kw:
+        assert np.array_equal(a.get(0), c.get(0)) and np.array_equal(a.get(1), c.get(1))
+    print(f"{case['id']}: coarse sweep launches per step cluster / block / per level {launches}")
+    if "coarse_precision" in kw:
+        assert launches[0] == launches[1] <= launches[2], launches
+    else:
+        assert launches[0] < launches[1] <= launches[2], launches
+    for s in sims:
+        s.close()
+
+
+PERIODIC_RESID_CASES = [
+    dict(id="tgv64", dims=(64, 64, 64), nu=0.01, U=(0.0, 0.0, 0.0), periodic=7, body=None, ic=1),
+    dict(id="tgv128x64x32", dims=(128, 64, 32), nu=0.01, U=(0.0, 0.0, 0.0), periodic=7, body=None, ic=1),
+    # with a body (the uniform-tile split forced on these small grids: the tiles on the
+    # periodic sides are uniform, the band's load their coefficients)
+    dict(id="xyper256x48x24", dims=(256, 48, 24), nu=0.01, U=(0.6, 0.1, 0.0), periodic=3,
+         body=dict(kind=1, center=(128.4, 23.6, 12.2), radius=6.0), env=dict(WL_UNIFORM_ALL="1")),
+    dict(id="yper192x64x32", dims=(192, 64, 32), nu=0.02, U=(1.0, 0.0, 0.0), periodic=2,
+         body=dict(kind=1, center=(60.0, 31.7, 15.6), radius=5.0), env=dict(WL_UNIFORM_ALL="1")),
+    dict(id="tgv64fp32p", dims=(64, 64, 64), nu=0.01, U=(0.0, 0.0, 0.0), periodic=7, body=None, ic=1,
+         kw=dict(precision=0)),
+]
+
+
+@pytest.mark.parametrize("case", PERIODIC_RESID_CASES, ids=lambda c: c["id"])
+def test_periodic_staged_residual_matches_table(case, monkeypatch):
+    """The TMA-staged fine residual / divergence on grids with periodic sides (planes past
+    a periodic z side staged from their wrapped planes; tiles on a periodic x / y side
+    patching their halo from the wrapped cells) against the index-table kernel: three
+    steps give identical bits, and the staged path is the one taken."""
+    kw = case.get("kw", {})
+    for k, v in case.get("env", {}).items():
+        monkeypatch.setenv(k, v)
+    sims = []
+    for env in (None, "WL_NO_RESID_TMA"):
+        if env:
+            monkeypatch.setenv(env, "1")
+        sim, _ = make_pair(case, oracle=False, **kw)
+        if env:
+            monkeypatch.delenv(env)
+        if case.get("ic"):
+            sim.set_ic(case["ic"], 1.0)
+        sims.append(sim)
+    from paper_2304_08159_gb300 import wl
+
+    paths = [s.kernel_paths() & wl.WL_PATH_RESID_STAGED for s in sims]
+    for s in sims:
+        s.step(3)
+    a, b = sims
+    assert np.array_equal(a.get(0), b.get(0)) and np.array_equal(a.get(1), b.get(1))
+    assert paths == [wl.WL_PATH_RESID_STAGED, 0], paths
+    for s in sims:
+        s.close()
+
+
 STAGE3_CASES = [c for c in CASES_3D if c["dims"][0] % 2 == 0] + [
     dict(id="s130x70x40", dims=(130, 70, 40), nu=0.01, U=(1.0, 0.1, -0.05), periodic=0,
          body=dict(kind=1, center=(60.3, 33.2, 19.7), radius=7.0)),
