@@ -1125,30 +1125,6 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
         break;
       if (lf + 2 <= s->nlev) s->tail_lf = lf;
     }
-    // the same from a larger level in one thread-block cluster (16 blocks, else 8): its
-    // levels are split between the blocks' shared memories, so tens of thousands of
-    // cells fit, and the sweeps of a level that would take a launch each run between
-    // cluster barriers.  Taken where it covers more levels than the one-block tail, and
-    // with FP32 coarse levels only (a tail keeps its levels in FP32, which would take
-    // levels the 16-bit modes store in 16 bits out of them).
-    if (!std::getenv("WL_NO_CTAIL") && s->o.coarse_precision == WL_COARSE_FP32) {
-      for (int C = 16; C >= 8 && !s->ctail_lf; C -= 8) {
-        int best = 0;
-        long long cl_cells = 0;
-        for (int lf = s->nlev - 1; lf >= lmin; --lf) {
-          cl_cells += s->lev[lf].g.nc;
-          if (cl_cells > kCtailCells || s->nlev - lf > kTailMaxLevels ||
-              vcycle_ctail_smem(ndim, n + lf, s->nlev - lf, C) > kTailSmemMax)
-            break;
-          if (lf + 2 <= s->nlev) best = lf;
-        }
-        if (best > 0 && (s->tail_lf == 0 || best < s->tail_lf) &&
-            vcycle_ctail_cluster(ndim, vcycle_ctail_smem(ndim, n + best, s->nlev - best, C), C) == C) {
-          s->ctail_lf = best;
-          s->ctail_c = C;
-        }
-      }
-    }
   }
   int rc = WL_OK;
   if (cudaMallocHost(&s->hs, sizeof(DevState)) != cudaSuccess) rc = fail(s, WL_ENOMEM, "pinned host state");
@@ -1187,6 +1163,45 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       for (int c = 0; c < ndim && ok; ++c)
         ok = make_field_map(&s->mu[b][c], bufs[b][c], L0.g, ndim, SWEEP_TY + (c == 1 ? 1 : 0));
     s->resid_tma = ok;
+  }
+  // The coarse end from a larger level in one thread-block cluster (16 blocks, else 8):
+  // its levels are split between the blocks' shared memories, so tens of thousands of
+  // cells fit, and the sweeps of a level that would take a launch each run between
+  // cluster barriers.  Measured: a cluster phase costs about a microsecond, so the
+  // cluster pays where it replaces levels swept by the index-table kernel (periodic
+  // levels narrower than a tile: 12 us a launch) and loses where the staged sweeps run
+  // (a few us a launch inside a graph); taken only where it covers more levels than the
+  // one-block tail and one of them uses the table kernel.  FP32 coarse levels only (a
+  // tail keeps its levels in FP32, which would take levels the 16-bit modes store in
+  // 16 bits out of them).  WL_CTAIL_ALWAYS drops the table-level condition (tests).
+  if (!rc && s->G && s->nlev >= 3 && !std::getenv("WL_NO_TAIL") && !std::getenv("WL_NO_CTAIL") &&
+      s->o.coarse_precision == WL_COARSE_FP32) {
+    int n[kMaxLevels][3];
+    for (int l = 0; l < s->nlev; ++l)
+      for (int d = 0; d < 3; ++d) n[l][d] = s->lev[l].g.n[d];
+    auto table_level = [&](int l) {
+      const LevelBuf& L = s->lev[l];
+      return !(L.tma && (L.tma_tiles > 0 || L.wrap_tma_tiles > 0)) || L.wrap_tiles > 0;
+    };
+    for (int C = 16; C >= 8 && !s->ctail_lf; C -= 8) {
+      int best = 0;
+      long long cl_cells = 0;
+      for (int lf = s->nlev - 1; lf >= 1; --lf) {
+        cl_cells += s->lev[lf].g.nc;
+        if (cl_cells > kCtailCells || s->nlev - lf > kTailMaxLevels ||
+            vcycle_ctail_smem(ndim, n + lf, s->nlev - lf, C) > kTailSmemMax)
+          break;
+        if (lf + 2 <= s->nlev) best = lf;
+      }
+      const int top = s->tail_lf > 0 ? s->tail_lf : s->nlev;
+      bool table = false;
+      for (int l = best; best > 0 && l < top; ++l) table = table || table_level(l);
+      if (best > 0 && best < top && (table || std::getenv("WL_CTAIL_ALWAYS")) &&
+          vcycle_ctail_cluster(ndim, vcycle_ctail_smem(ndim, n + best, s->nlev - best, C), C) == C) {
+        s->ctail_lf = best;
+        s->ctail_c = C;
+      }
+    }
   }
   if (!rc) {
     launch_measure(ndim, s->g, s->body, s->lev[0].L, s->st);

@@ -371,6 +371,7 @@ def test_cluster_tail_matches_block_tail_and_per_level(case, monkeypatch):
     the iterate in 16 bits between sweeps while the block tail keeps it in FP32, so
     there only the first two agree bitwise."""
     kw = case.get("kw", {})
+    monkeypatch.setenv("WL_CTAIL_ALWAYS", "1")  # the cluster also where the staged sweeps would run
     sims = []
     for env in (None, "WL_NO_CTAIL", "WL_NO_TAIL"):
         if env:
@@ -444,6 +445,22 @@ def test_periodic_staged_residual_matches_table(case, monkeypatch):
     assert paths == [wl.WL_PATH_RESID_STAGED, 0], paths
     for s in sims:
         s.close()
+
+
+def test_cluster_tail_taken_over_table_swept_levels():
+    """By default the cluster tail is taken where a level it would cover is swept by the
+    index-table kernel (a periodic level narrower than a tile), not where every such level
+    has the staged sweep (measured there: the per-level launches are cheaper)."""
+    from paper_2304_08159_gb300 import wl
+
+    # taken: the 64^3 vortex (32^3 and 16^3 are narrower than a tile), the y-periodic
+    # 72x40x56 (36x20x28: periodic rows not whole tiles); not taken: walls only, and the 2-D
+    # periodic 128^2 (the level the cluster would add, 64^2, has the staged wrapping sweep)
+    for case, want in ((CTAIL_CASES[1], True), (CTAIL_CASES[3], True), (CTAIL_CASES[0], False),
+                       (CTAIL_CASES[4], False), (CTAIL_CASES[5], False)):
+        sim, _ = make_pair(case, oracle=False)
+        assert bool(sim.kernel_paths() & wl.WL_PATH_CLUSTER_TAIL) == want, case["id"]
+        sim.close()
 
 
 STAGE3_CASES = [c for c in CASES_3D if c["dims"][0] % 2 == 0] + [
