@@ -229,7 +229,11 @@ int wl_gmg_vcycle(wl_handle h, double* resid_inf_out);
 /* Pressure force on the body, F_d = -sum_cells (p - pbar) n_d K_eps(d), with the
  * cosine kernel K_eps = (1 + cos(pi d/eps))/(2 eps) over |d| < eps and pbar the
  * mean pressure over cells with a nonzero Poisson row; accumulated in FP64.
- * F receives D values.  Synchronises. */
+ * F receives D values.  Synchronises.  The paper prints no force formula: this is the
+ * library's reading (and the oracle's), the pressure part of the surface force in the
+ * kernel-smoothed form of the immersed-boundary method Section 2 builds on (BDIM,
+ * Weymouth & Yue 2011): the surface integral of -p n becomes a sum over the cells within
+ * eps of the body, weighted by the kernel of the signed distance. */
 int wl_forces(wl_handle h, double* F);
 
 /* Viscous force on the body of the current velocity, F_i = sum_cells 2 nu S_ij n_j

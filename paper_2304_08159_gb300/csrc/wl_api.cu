@@ -534,7 +534,12 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   // z-blocking for each kernel's own residency: the table kernel (tiles across a periodic
   // side, 16-bit levels) and the staged one (uniform or loading variant)
   a.tz = sweep_planes_per_block(L.g, sweep_table_blocks_per_sm(s->D, L.st));
-  const int tz_staged = sweep_planes_per_block(L.g, L.band.on ? SWEEP_UNI_BLOCKS_PER_SM : SWEEP_BLOCKS_PER_SM);
+  // planes per block of the staged sweep: sized for a wave of 8 blocks per SM on the
+  // coarse levels, of 4 on the fine level (measured: 256x128x128 as the fine level,
+  // 1.85 -> 1.79 ms per step with twice the planes; the same grid as level 1 of the
+  // 512x256x256 sphere lost 0.13 ms per step with them)
+  const int bps = L.band.on ? (l == 0 ? SWEEP_UNI_BLOCKS_PER_SM / 2 : SWEEP_UNI_BLOCKS_PER_SM) : SWEEP_BLOCKS_PER_SM;
+  const int tz_staged = sweep_planes_per_block(L.g, bps);
   // no body: the band box is empty and every coefficient is the level's free-stream value
   a.uni = (L.band.on && L.band.lo[0] >= L.band.hi[0]) ? 1 : 0;
   a.uval = L.uval;
