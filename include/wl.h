@@ -454,12 +454,14 @@ int wl_level_split(wl_handle h, int l, int* split, double* band_fraction);
 /* Which kernel paths the sim's step takes, as bits into *paths: WL_PATH_RESID_STAGED the
  * TMA-staged fine residual / divergence (else the index-table kernel),
  * WL_PATH_CLUSTER_TAIL the coarse levels from some level down in one thread-block
- * cluster, WL_PATH_BLOCK_TAIL the smallest levels in one block (else level by level).
- * The paths give the same bits; for measurement and tests.  No counterpart in the
- * paper. */
+ * cluster, WL_PATH_BLOCK_TAIL the smallest levels in one block (else level by level),
+ * WL_PATH_TALL_TILES the staged sweep on some level in tiles of 64 x 16 cells (else
+ * 64 x 8).  The paths give the same bits; for measurement and tests.  No counterpart in
+ * the paper. */
 #define WL_PATH_RESID_STAGED 1
 #define WL_PATH_CLUSTER_TAIL 2
 #define WL_PATH_BLOCK_TAIL 4
+#define WL_PATH_TALL_TILES 8
 int wl_kernel_paths(wl_handle h, unsigned* paths);
 
 void wl_destroy(wl_handle h);

@@ -45,6 +45,7 @@ struct LevelBuf {
   int tzw;                        // planes per block of its launch
   BandBox band;                   // region whose coefficients may differ from uval (staged kernels)
   float uval;                     // the level's coefficient away from the body: 2^(l (D-2))
+  int ty = SWEEP_TY;              // tile height of the staged sweep's plain tiles (8, or SWEEP_TY16)
   float* z32;                     // a 16-bit level 1: the restricted fine residual in FP32, converted
                                   // (with the scale DevState::cs_used) by level 1's restriction pass
   bool tma;                       // tensor maps below are valid (n_0 % 4 == 0)
@@ -198,6 +199,27 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
       cudaGetLastError();
   }
   return fn;
+}
+
+// Smallest level (cells) that takes 16-row sweep tiles (WL_TY16_MIN_CELLS overrides).
+long long ty16_min_cells() {
+  const char* e = std::getenv("WL_TY16_MIN_CELLS");
+  return e ? std::atoll(e) : (1ll << 20);
+}
+
+// Planes per block of the staged sweep on level l: whole waves of its resident blocks
+// per SM (the fine level's 8-row tiles: waves of 4 of the 8, measured: 256x128x128 as
+// the fine level, 1.85 -> 1.79 ms per step with twice the planes; the same grid as level
+// 1 of the 512x256x256 sphere lost 0.13 ms per step with them).
+int staged_sweep_tz(const LevelBuf& L, int l) {
+  if (L.ty == SWEEP_TY16) {
+    const char* e = std::getenv(l == 0 ? "WL_TY16_BPS0" : "WL_TY16_BPS");
+    const int bps = e ? std::atoi(e) : SWEEP16_UNI_BLOCKS_PER_SM;
+    const long long tiles = (long long)((L.g.n[0] + SWEEP_TX - 1) / SWEEP_TX) * (L.g.n[1] / SWEEP_TY16);
+    return sweep_planes_for_columns(L.g.n[2], tiles, bps > 0 ? bps : SWEEP16_UNI_BLOCKS_PER_SM);
+  }
+  const int bps = L.band.on ? (l == 0 ? SWEEP_UNI_BLOCKS_PER_SM / 2 : SWEEP_UNI_BLOCKS_PER_SM) : SWEEP_BLOCKS_PER_SM;
+  return sweep_planes_per_block(L.g, bps);
 }
 
 // Box of 72 x rows [x 1] floats over a level field (x fastest), zero fill out of
@@ -534,12 +556,8 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
   // z-blocking for each kernel's own residency: the table kernel (tiles across a periodic
   // side, 16-bit levels) and the staged one (uniform or loading variant)
   a.tz = sweep_planes_per_block(L.g, sweep_table_blocks_per_sm(s->D, L.st));
-  // planes per block of the staged sweep: sized for a wave of 8 blocks per SM on the
-  // coarse levels, of 4 on the fine level (measured: 256x128x128 as the fine level,
-  // 1.85 -> 1.79 ms per step with twice the planes; the same grid as level 1 of the
-  // 512x256x256 sphere lost 0.13 ms per step with them)
-  const int bps = L.band.on ? (l == 0 ? SWEEP_UNI_BLOCKS_PER_SM / 2 : SWEEP_UNI_BLOCKS_PER_SM) : SWEEP_BLOCKS_PER_SM;
-  const int tz_staged = sweep_planes_per_block(L.g, bps);
+  // planes per block of the staged sweep (whole waves of its resident blocks)
+  const int tz_staged = staged_sweep_tz(L, l);
   // no body: the band box is empty and every coefficient is the level's free-stream value
   a.uni = (L.band.on && L.band.lo[0] >= L.band.hi[0]) ? 1 : 0;
   a.uval = L.uval;
@@ -581,6 +599,7 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       t.xsrc = a.x_in;
       t.zsrc = refine ? s->rf : L.z;
       t.tzw = L.tzw;
+      t.ty = L.ty;
       PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st, side_of(s)));
       a.only_wrapping = 1;  // tiles crossing a periodic side
       if (L.wrap_tiles > 0) PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
@@ -1080,7 +1099,13 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
         }
       }
       const int tz = sweep_planes_per_block(L.g, SWEEP_UNI_BLOCKS_PER_SM);
-      L.band.on = (split && band_tile_fraction(ndim, L.g, tz, L.band) <= frac_max) ? 1 : 0;
+      L.band.on = (split && band_tile_fraction(ndim, L.g, tz, L.band, SWEEP_TY) <= frac_max) ? 1 : 0;
+      // 16-row tiles on the large split levels that are periodic in neither x nor y: a
+      // warp relaxes twice the cells per plane for the same per-plane bookkeeping
+      L.ty = (ndim == 3 && L.band.on && !(L.g.per & 3u) && L.g.n[1] % SWEEP_TY16 == 0 &&
+              L.g.nc >= ty16_min_cells())
+                 ? SWEEP_TY16
+                 : SWEEP_TY;
       // tiles the staged sweep takes and tiles across a periodic side (launches with
       // no tile of their kind are skipped).  The staged kernel takes the latter too when
       // the periodic sides are whole tiles and all of those tiles are uniform.
@@ -1146,12 +1171,15 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
       }
       // sweep boxes: iterate 12 rows, coefficients 10 (L1: 11); residual boxes: 8 rows
       // (faces of y: 9)
-      bool ok = make_field_map(&L.mx, L.x, L.g, ndim) && make_field_map(&L.mx2, L.x2, L.g, ndim) &&
-                make_field_map(&L.mz, L.z, L.g, ndim, SWEEP_TY) && make_field_map(&L.sz, L.z, L.g, ndim, SWEEP_CROWS);
+      // (the sweep's boxes follow the level's tile height: iterate ty + 4 rows, coefficients
+      // ty + 2, L1 ty + 3)
+      const int crows = L.ty + 2;
+      bool ok = make_field_map(&L.mx, L.x, L.g, ndim, L.ty + 4) && make_field_map(&L.mx2, L.x2, L.g, ndim, L.ty + 4) &&
+                make_field_map(&L.mz, L.z, L.g, ndim, SWEEP_TY) && make_field_map(&L.sz, L.z, L.g, ndim, crows);
       for (int c = 0; c < ndim; ++c)
         ok = ok && make_field_map(&L.mL[c], L.L[c], L.g, ndim, SWEEP_TY + (c == 1 ? 1 : 0)) &&
-             make_field_map(&L.sL[c], L.L[c], L.g, ndim, SWEEP_CROWS + (c == 1 ? 1 : 0));
-      if (l == 0 && s->rf) ok = ok && make_field_map(&s->srf, s->rf, L.g, ndim, SWEEP_CROWS);
+             make_field_map(&L.sL[c], L.L[c], L.g, ndim, crows + (c == 1 ? 1 : 0));
+      if (l == 0 && s->rf) ok = ok && make_field_map(&s->srf, s->rf, L.g, ndim, crows);
       L.tma = ok;
     }
     // fine residual: 3-D; with a periodic x / y side when those sides are whole tiles
@@ -1933,6 +1961,8 @@ int wl_kernel_paths(wl_handle s, unsigned* paths) {
   if (!s || !paths) return WL_EINVAL;
   *paths = (s->resid_tma ? WL_PATH_RESID_STAGED : 0u) | (s->ctail_lf > 0 ? WL_PATH_CLUSTER_TAIL : 0u) |
            (s->ctail_lf == 0 && s->tail_lf > 0 ? WL_PATH_BLOCK_TAIL : 0u);
+  for (int l = 0; l < s->nlev; ++l)
+    if (s->lev[l].tma && s->lev[l].ty == SWEEP_TY16) *paths |= WL_PATH_TALL_TILES;
   return WL_OK;
 }
 
@@ -1942,8 +1972,7 @@ int wl_level_split(wl_handle s, int l, int* split, double* band_fraction) {
   const bool on = L.tma && L.band.on;
   if (split) *split = on ? 1 : 0;
   if (band_fraction)
-    *band_fraction = on ? band_tile_fraction(s->D, L.g, sweep_planes_per_block(L.g, SWEEP_UNI_BLOCKS_PER_SM), L.band)
-                        : 1.0;
+    *band_fraction = on ? band_tile_fraction(s->D, L.g, staged_sweep_tz(L, l), L.band, L.ty) : 1.0;
   return WL_OK;
 }
 

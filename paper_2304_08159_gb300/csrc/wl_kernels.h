@@ -119,6 +119,7 @@ struct SweepTmaArgs {
   const float* xsrc;   //   the staged iterate (has_x)
   const float* zsrc;   //   the staged right-hand side
   int tzw;             // planes per block of the wrapping tiles' launch (its own residency)
+  int ty;              // tile height of the plain tiles: 8, or 16 (SWEEP_TY16; maps with its boxes)
 };
 
 // Dense pseudo-inverse of the coarsest operator (column-major, FP64), used when the
@@ -200,7 +201,7 @@ struct SideStream {
 };
 int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s, const SideStream* side);
 // fraction of a level's sweep tiles (tz planes per block) that meet the band box
-double band_tile_fraction(int D, const Grid& g, int tz, const BandBox& b);
+double band_tile_fraction(int D, const Grid& g, int tz, const BandBox& b, int ty);  // ty: tile height
 
 // TMA-staged fine residual / divergence (3-D, levels with no periodic side)
 struct ResidMaps {
@@ -253,14 +254,20 @@ constexpr int SWEEP_CROWS = SWEEP_TY + 2;
 constexpr int SWEEP_BLOCKS_PER_SM = 4;
 constexpr int SWEEP_UNI_BLOCKS_PER_SM = 8;
 constexpr int SWEEP_WRAP_BLOCKS_PER_SM = 5;  // the wrapping variant (register bound)
+// tiles of 64 x 16 cells (large split levels with no periodic x / y side): shared memory
+// bound, the uniform variant 44 KB per block, the loading one 97 KB
+constexpr int SWEEP_TY16 = 16;
+constexpr int SWEEP16_UNI_BLOCKS_PER_SM = 5;
+constexpr int SWEEP16_BLOCKS_PER_SM = 2;
 // blocks per SM the fine residual's z-blocking assumes for its split launches
 constexpr int RESID_UNI_WAVE_BLOCKS = 6;
-// The tile's staged footprint (x i0-4..i0+67, y j0-2..j0+9, planes k0-2..k1+1)
-// meets the band box (always true without a split).
-__host__ __device__ inline bool tile_in_band(const BandBox& b, int D, int i0, int j0, int k0, int k1) {
+// The tile's staged footprint (x i0-4..i0+67, y j0-2..j0+ty+1, planes k0-2..k1+1)
+// meets the band box (always true without a split).  ty: the tile height.
+__host__ __device__ inline bool tile_in_band(const BandBox& b, int D, int i0, int j0, int k0, int k1,
+                                             int ty = SWEEP_TY) {
   if (!b.on) return true;
   if (i0 - 4 >= b.hi[0] || i0 + SWEEP_TX + 4 <= b.lo[0]) return false;
-  if (j0 - 2 >= b.hi[1] || j0 + SWEEP_TY + 2 <= b.lo[1]) return false;
+  if (j0 - 2 >= b.hi[1] || j0 + ty + 2 <= b.lo[1]) return false;
   if (D == 3 && (k0 - 2 >= b.hi[2] || k1 + 2 <= b.lo[2])) return false;
   return true;
 }

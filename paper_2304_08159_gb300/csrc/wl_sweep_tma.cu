@@ -43,6 +43,17 @@ constexpr int NBB = 2;          // bundle mbarriers (a power of two, > LEAD)
 constexpr int SW_NT = 128;      // sweep threads: 4 warps
 static_assert(NBB > LEAD && (NBB & (NBB - 1)) == 0, "bundle barriers");
 static_assert(BOX * 4 % 128 == 0, "iterate slots keep 128-byte alignment");
+// Sweep boxes for a tile height TYV: 8 rows, or 16 on the large split levels (twice the
+// cells per warp and plane for the same per-plane bookkeeping, a 1-row halo on 16 rows
+// instead of 8).  Iterate box TYV + 4 rows from j0-2; coefficient boxes CROWS rows from
+// j0-1 (L1: one more, the upper face of the last row).
+template <int TYV>
+struct SwGeom {
+  static constexpr int BY = TYV + 4, BOX = BX * BY;
+  static constexpr int CROWS = TYV + 2, L1ROWS = TYV + 3;
+  static constexpr int CSLOT = (BX * CROWS + 31) / 32 * 32, L1SLOT = (BX * L1ROWS + 31) / 32 * 32;
+  static_assert(BOX * 4 % 128 == 0, "iterate slots keep 128-byte alignment");
+};
 constexpr unsigned kWaitLimit = 1u << 21;      // wait attempts
 constexpr unsigned kSuspendNs = 10000;         // longest sleep of one attempt
 constexpr uint64_t kWaitNs = 2000000000ull;    // longest wait (2 s)
@@ -122,13 +133,19 @@ __device__ __forceinline__ void sts(uint32_t a, float v) { asm volatile("st.shar
 // right-hand side are staged, the coefficients are formed from the cell's position
 // (same values, same operation order, same bits), and the smaller rings fit more
 // blocks per SM.  WRAP (uniform only): the tiles whose footprint crosses a periodic x
-// or y side, the others' the tiles that cross none.
-template <int D, bool UNI, bool WRAP>
-__global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
-                                         : UNI ? SWEEP_UNI_BLOCKS_PER_SM
-                                               : SWEEP_BLOCKS_PER_SM)
+// or y side, the others' the tiles that cross none.  TYV: the tile height (8, or 16 on
+// large levels split into band and uniform tiles and periodic in neither x nor y).
+template <int D, bool UNI, bool WRAP, int TYV>
+__global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_SM
+                                         : TYV == 16    ? (UNI ? SWEEP16_UNI_BLOCKS_PER_SM : SWEEP16_BLOCKS_PER_SM)
+                                         : UNI          ? SWEEP_UNI_BLOCKS_PER_SM
+                                                        : SWEEP_BLOCKS_PER_SM)
     k_sweep_tma(const __grid_constant__ SweepMaps m, SweepTmaArgs a) {
   static_assert(UNI || !WRAP, "wrapping tiles are uniform");
+  static_assert(TYV == 8 || (TYV == 16 && !WRAP), "tile heights: 8, or 16 without wrapping");
+  constexpr int TY = TYV, BY = SwGeom<TYV>::BY, BOX = SwGeom<TYV>::BOX;
+  constexpr int CROWS = SwGeom<TYV>::CROWS, L1ROWS = SwGeom<TYV>::L1ROWS;
+  constexpr int CSLOT = SwGeom<TYV>::CSLOT, L1SLOT = SwGeom<TYV>::L1SLOT;
   extern __shared__ float smf[];
   // 128-byte aligned slot rings (iterate, L2, z, L0, L1), then the mbarriers, all
   // addressed by 32-bit float offsets into smf
@@ -143,7 +160,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   if (i0 >= g.n[0] || j0 >= g.n[1] || k0 >= g.n[2]) return;
   const int k1 = (D == 3) ? min(k0 + a.tz, g.n[2]) : 1;
   if (sweep_tile_wraps_xy(g, i0, j0) != WRAP) return;  // the other launch's tile
-  if (tile_in_band(a.band, D, i0, j0, k0, k1) == UNI) return;  // the other variant's tile
+  if (tile_in_band(a.band, D, i0, j0, k0, k1, TY) == UNI) return;  // the other variant's tile
   // a plane past a periodic z side is staged from its wrapped plane
   const bool pz = D == 3 && is_per(g, 2);
   auto wz = [&](int p) { return pz ? wrap_per(p, g.n[2]) : p; };
@@ -197,17 +214,17 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     ld_c(b + 1, bbar(b));
   };
   // iterate := (staged iterate or 0) + prolonged coarse correction, on plane p.  The
-  // box starts at an even cell, so it covers 36 x 6 coarse cells; each thread owns up to
-  // two of them and adds each one's value to its 2 x 2 fine cells.  Two fine planes share
+  // box starts at an even cell, so it covers 36 x (TY/2 + 2) coarse cells; each thread owns
+  // up to NCR of them and adds each one's value to its 2 x 2 fine cells.  Two fine planes share
   // a coarse plane: a thread keeps the values of the last coarse plane it loaded, and
   // the loop loads the next plane's one iteration ahead of their use.
   const float xcm = a.xc_cs ? ldexpf(1.f, -a.st->cs_used) : 1.f;  // removes the coarse levels' scale
   const bool fix = !a.has_x || a.xc;
-  constexpr int CBX = BX / 2, CBOX = CBX * (BY / 2);
-  static_assert(BX % 2 == 0 && BY % 2 == 0 && CBOX <= 2 * SW_NT, "coarse box");
-  int cxy[2], ceo[2];  // coarse in-plane index (-1: outside the grid), fine box offset (-1: none)
+  constexpr int CBX = BX / 2, CBOX = CBX * (BY / 2), NCR = (CBOX + SW_NT - 1) / SW_NT;
+  static_assert(BX % 2 == 0 && BY % 2 == 0, "coarse box");
+  int cxy[NCR], ceo[NCR];  // coarse in-plane index (-1: outside the grid), fine box offset (-1: none)
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < NCR; ++r) {
     const int t = tid + SW_NT * r, cr = t / CBX, cc = t - cr * CBX;
     int ci = (i0 >> 1) - 2 + cc, cj = (j0 >> 1) - 1 + cr;
     if (is_per(g, 0)) ci = wrap_per(ci, a.cn[0]);  // a wrapping tile
@@ -215,7 +232,9 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     ceo[r] = t < CBOX ? 2 * cr * BX + 2 * cc : -1;
     cxy[r] = (t < CBOX && a.xc && ci >= 0 && ci < a.cn[0] && cj >= 0 && cj < a.cn[1]) ? ci + a.cn[0] * cj : -1;
   }
-  float cv[2] = {0.f, 0.f};
+  float cv[NCR];
+#pragma unroll
+  for (int r = 0; r < NCR; ++r) cv[r] = 0.f;
   int ckey = -2;  // coarse plane whose values cv holds (-1: outside the grid)
   auto load_c = [&](int p) {
     const int wp = D == 3 ? wz(p) : p;  // the coarse correction of a wrapped plane
@@ -223,7 +242,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     if (kz == ckey) return;
     ckey = kz;
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < NCR; ++r)
       cv[r] = (kz >= 0 && cxy[r] >= 0 &&
                wl_in((long long)cxy[r] + (long long)a.cn[0] * a.cn[1] * kz, (long long)a.cn[0] * a.cn[1] * a.cn[2],
                      WL_DBG_COARSE))
@@ -233,7 +252,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   auto apply_c = [&](int p) {
     float* X = smf + Xs(xslot(p));
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < NCR; ++r) {
       if (ceo[r] < 0) continue;
       float2* q0 = reinterpret_cast<float2*>(X + ceo[r]);
       float2* q1 = reinterpret_cast<float2*>(X + ceo[r] + BX);
@@ -419,15 +438,18 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     }
     return (dg > 0.f) ? __fdividef(sum - lds(P.z + e), dg) : 0.f;
   };
-  // Red cells of plane p cover the tile plus a 1-cell halo (rows -1..8, columns
-  // -1..64): ten tasks of 32 (two adjacent rows x half the tile's columns) and ten
-  // edge-column cells.  Warp w takes red tasks w and w+4 as a pair, and a third red
-  // task: w+8 for warps 0-1, or five edge cells (rows -1..3 on warp 2, rows 4..8 on
-  // warp 3; lanes 0..4).  Black cells of plane k (rows 0..7): eight tasks, w and w+4
-  // as a pair.  So every warp relaxes one red pair, one red single and one black pair
-  // per plane.  Shared byte offsets into the iterate box, for even and odd planes.
-  uint32_t er[3][2], eb[2][2];
-  uint32_t mr[3][2], mb[2][2];  // UNI: face masks of each task's cell (relax_uni)
+  // Red cells of plane p cover the tile plus a 1-cell halo (rows -1..TY, columns
+  // -1..64): TY+2 tasks of 32 (two adjacent rows x half the tile's columns) and TY+2
+  // edge-column cells.  Warp w takes red tasks w, w+4, .., w+TY-4 (NRH = TY/4 of them,
+  // in pairs), and a last red task: w+TY for warps 0-1, or TY/2+1 edge cells (the upper
+  // half of the rows on warp 2, the lower half on warp 3).  Black cells of plane k (rows
+  // 0..TY-1): TY tasks, w, w+4, .. in pairs.  So every warp relaxes NRH/2 red pairs, one
+  // red single and NRH/2 black pairs per plane (TY 8: one of each; TY 16: two pairs of
+  // each).  Shared byte offsets into the iterate box, for even and odd planes.
+  constexpr int NRH = TY / 4, NEDGE = TY / 2 + 1;
+  static_assert(NRH % 2 == 0, "tasks in pairs");
+  uint32_t er[NRH + 1][2], eb[NRH][2];
+  uint32_t mr[NRH + 1][2], mb[NRH][2];  // UNI: face masks of each task's cell (relax_uni)
   auto xymask = [&](int col, int row) -> uint32_t {
     const int gi = i0 + col, gj = j0 + row;
     const bool px = is_per(g, 0), py = is_per(g, 1);
@@ -436,25 +458,25 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     return (gi > 0 || px ? 1u : 0u) | (gi + 1 < g.n[0] || px ? 2u : 0u) | (gj > 0 || py ? 4u : 0u) |
            (gj + 1 < g.n[1] || py ? 8u : 0u) | (in ? 16u : 0u);
   };
-  const bool third = warp < 2 || lane < 5;  // this lane has a third red cell
+  const bool third = warp < 2 || lane < NEDGE;  // this lane has a last red cell
   {
     const int ib0 = 2 * (lane & 15);
 #pragma unroll
-    for (int h = 0; h < 3; ++h) {
+    for (int h = 0; h <= NRH; ++h) {
       const int t = warp + 4 * h;
       const int jr = 2 * (t >> 1) + (lane >> 4) - 1, jb = jr + 1;
       const int ib = 32 * (t & 1) + ib0;
-      const int je = (warp == 2) ? lane - 1 : lane + 4;  // edge rows (third cell of warps 2, 3)
+      const int je = (warp == 2) ? lane - 1 : lane + NEDGE - 1;  // edge rows (last cell of warps 2, 3)
 #pragma unroll
       for (int par = 0; par < 2; ++par) {
         int cr = ib + ((i0 + j0 + jr + par) & 1), rr = jr;
-        if (h == 2 && warp >= 2) {
+        if (h == NRH && warp >= 2) {
           cr = ((i0 + j0 + je + par) & 1) ? -1 : 64;
           rr = je;
         }
         er[h][par] = 4u * ((rr + 2) * BX + cr + 4);
         if (UNI) mr[h][par] = xymask(cr, rr);
-        if (h < 2) {
+        if (h < NRH) {
           const int cb = ib + ((i0 + j0 + jb + par + 1) & 1);
           eb[h][par] = 4u * ((jb + 2) * BX + cb + 4);
           if (UNI) mb[h][par] = xymask(cb, jb);
@@ -463,18 +485,20 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
     }
   }
   // UNI, tiles that touch a wall: bit t of fast_m is set when every lane's cell of task t
-  // (red 2h+par, black 6+2h+par) is inside the grid with all four x/y faces, so that on
-  // a plane with both z faces the task takes relax_fast (same bits)
+  // (red 2h+par, the last red 2 NRH+par, black BLK+2h+par) is inside the grid with all
+  // four x/y faces, so that on a plane with both z faces the task takes relax_fast (same
+  // bits)
+  constexpr int BLK = 2 * NRH + 2;
   uint32_t fast_m = 0u;
   if (UNI) {
 #pragma unroll
     for (int par = 0; par < 2; ++par) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < NRH; ++h) {
         if (__all_sync(0xffffffffu, mr[h][par] == 31u)) fast_m |= 1u << (2 * h + par);
-        if (__all_sync(0xffffffffu, mb[h][par] == 31u)) fast_m |= 1u << (6 + 2 * h + par);
+        if (__all_sync(0xffffffffu, mb[h][par] == 31u)) fast_m |= 1u << (BLK + 2 * h + par);
       }
-      if (__all_sync(0xffffffffu, !third || mr[2][par] == 31u)) fast_m |= 1u << (4 + par);
+      if (__all_sync(0xffffffffu, !third || mr[NRH][par] == 31u)) fast_m |= 1u << (2 * NRH + par);
     }
   }
   // UNI: z faces and range of plane kk
@@ -487,12 +511,16 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   auto zfull = [&](int kk) { return D == 2 || pz || (kk > 0 && kk + 1 < g.n[2]); };
   // red cells of plane kk (parity par) whose operands are P
   auto red_plane = [&](const Planes& P, int par, int kk) {
-    const uint32_t e0 = par ? er[0][1] : er[0][0], e1 = par ? er[1][1] : er[1][0];
-    const uint32_t e2 = par ? er[2][1] : er[2][0];
+    auto pk = [&](const uint32_t(&v)[2]) { return par ? v[1] : v[0]; };
+    const uint32_t e2 = pk(er[NRH]);
     if (UNI && interior && zfull(kk)) {
-      const float2 v = relax_fast2(P, e0, e1);
-      sts(P.x0 + e0, v.x);
-      sts(P.x0 + e1, v.y);
+#pragma unroll
+      for (int hp = 0; hp < NRH / 2; ++hp) {
+        const uint32_t e0 = pk(er[2 * hp]), e1 = pk(er[2 * hp + 1]);
+        const float2 v = relax_fast2(P, e0, e1);
+        sts(P.x0 + e0, v.x);
+        sts(P.x0 + e1, v.y);
+      }
       if (third) sts(P.x0 + e2, relax_fast(P, e2));
       return;
     }
@@ -500,76 +528,99 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
       const uint32_t fm = (zlo && zhi && kin) ? fast_m >> par : 0u;
-      if ((fm & 5u) == 5u) {
-        const float2 v = relax_fast2(P, e0, e1);
-        sts(P.x0 + e0, v.x);
-        sts(P.x0 + e1, v.y);
-      } else {
-        const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, par ? mr[0][1] : mr[0][0], zlo, zhi, kin);
-        const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mr[1][1] : mr[1][0], zlo, zhi, kin);
-        sts(P.x0 + e0, v0);
-        sts(P.x0 + e1, v1);
+#pragma unroll
+      for (int hp = 0; hp < NRH / 2; ++hp) {
+        const uint32_t e0 = pk(er[2 * hp]), e1 = pk(er[2 * hp + 1]);
+        const uint32_t b0 = 1u << (4 * hp), b1 = 4u << (4 * hp);
+        if ((fm & (b0 | b1)) == (b0 | b1)) {
+          const float2 v = relax_fast2(P, e0, e1);
+          sts(P.x0 + e0, v.x);
+          sts(P.x0 + e1, v.y);
+        } else {
+          const float v0 = (fm & b0) ? relax_fast(P, e0) : relax_uni(P, e0, pk(mr[2 * hp]), zlo, zhi, kin);
+          const float v1 = (fm & b1) ? relax_fast(P, e1) : relax_uni(P, e1, pk(mr[2 * hp + 1]), zlo, zhi, kin);
+          sts(P.x0 + e0, v0);
+          sts(P.x0 + e1, v1);
+        }
       }
       if (third)
-        sts(P.x0 + e2, (fm & 16u) ? relax_fast(P, e2) : relax_uni(P, e2, par ? mr[2][1] : mr[2][0], zlo, zhi, kin));
+        sts(P.x0 + e2, ((fm >> (2 * NRH)) & 1u) ? relax_fast(P, e2) : relax_uni(P, e2, pk(mr[NRH]), zlo, zhi, kin));
       return;
     }
-    const float v0 = relax(P, e0), v1 = relax(P, e1);
-    sts(P.x0 + e0, v0);
-    sts(P.x0 + e1, v1);
+#pragma unroll
+    for (int hp = 0; hp < NRH / 2; ++hp) {
+      const uint32_t e0 = pk(er[2 * hp]), e1 = pk(er[2 * hp + 1]);
+      const float v0 = relax(P, e0), v1 = relax(P, e1);
+      sts(P.x0 + e0, v0);
+      sts(P.x0 + e1, v1);
+    }
     if (third) sts(P.x0 + e2, relax(P, e2));
   };
   // black cells of plane kk (parity par) whose operands are P
   auto black_plane = [&](const Planes& P, int par, int kk) {
-    const uint32_t e0 = par ? eb[0][1] : eb[0][0], e1 = par ? eb[1][1] : eb[1][0];
+    auto pk = [&](const uint32_t(&v)[2]) { return par ? v[1] : v[0]; };
     if (UNI && interior && zfull(kk)) {
-      const float2 v = relax_fast2(P, e0, e1);
-      sts(P.x0 + e0, v.x);
-      sts(P.x0 + e1, v.y);
+#pragma unroll
+      for (int hp = 0; hp < NRH / 2; ++hp) {
+        const uint32_t e0 = pk(eb[2 * hp]), e1 = pk(eb[2 * hp + 1]);
+        const float2 v = relax_fast2(P, e0, e1);
+        sts(P.x0 + e0, v.x);
+        sts(P.x0 + e1, v.y);
+      }
       return;
     }
     if (UNI) {
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
-      const uint32_t fm = (zlo && zhi && kin) ? fast_m >> (6 + par) : 0u;
-      if ((fm & 5u) == 5u) {
-        const float2 v = relax_fast2(P, e0, e1);
-        sts(P.x0 + e0, v.x);
-        sts(P.x0 + e1, v.y);
-        return;
+      const uint32_t fm = (zlo && zhi && kin) ? fast_m >> (BLK + par) : 0u;
+#pragma unroll
+      for (int hp = 0; hp < NRH / 2; ++hp) {
+        const uint32_t e0 = pk(eb[2 * hp]), e1 = pk(eb[2 * hp + 1]);
+        const uint32_t b0 = 1u << (4 * hp), b1 = 4u << (4 * hp);
+        if ((fm & (b0 | b1)) == (b0 | b1)) {
+          const float2 v = relax_fast2(P, e0, e1);
+          sts(P.x0 + e0, v.x);
+          sts(P.x0 + e1, v.y);
+        } else {
+          const float v0 = (fm & b0) ? relax_fast(P, e0) : relax_uni(P, e0, pk(mb[2 * hp]), zlo, zhi, kin);
+          const float v1 = (fm & b1) ? relax_fast(P, e1) : relax_uni(P, e1, pk(mb[2 * hp + 1]), zlo, zhi, kin);
+          sts(P.x0 + e0, v0);
+          sts(P.x0 + e1, v1);
+        }
       }
-      const float v0 = (fm & 1u) ? relax_fast(P, e0) : relax_uni(P, e0, par ? mb[0][1] : mb[0][0], zlo, zhi, kin);
-      const float v1 = (fm & 4u) ? relax_fast(P, e1) : relax_uni(P, e1, par ? mb[1][1] : mb[1][0], zlo, zhi, kin);
-      sts(P.x0 + e0, v0);
-      sts(P.x0 + e1, v1);
       return;
     }
-    const float v0 = relax(P, e0), v1 = relax(P, e1);
-    sts(P.x0 + e0, v0);
-    sts(P.x0 + e1, v1);
+#pragma unroll
+    for (int hp = 0; hp < NRH / 2; ++hp) {
+      const uint32_t e0 = pk(eb[2 * hp]), e1 = pk(eb[2 * hp + 1]);
+      const float v0 = relax(P, e0), v1 = relax(P, e1);
+      sts(P.x0 + e0, v0);
+      sts(P.x0 + e1, v1);
+    }
   };
-  // Write the tile's plane k: 256 column pairs, pair t and t + 128 for thread t;
+  // Write the tile's plane k: 32 TY column pairs, pairs t, t + 128, .. for thread t;
   // pair (tx, ty) is columns 2tx, 2tx+1 of row ty (n0 % 4 == 0, so both columns
   // exist when the first does).
-  bool st_own[2];
-  long long q0[2];
-  int est[2];
+  constexpr int NST = 32 * TY / SW_NT;
+  bool st_own[NST];
+  long long q0[NST];
+  int est[NST];
 #pragma unroll
-  for (int r = 0; r < 2; ++r) {
+  for (int r = 0; r < NST; ++r) {
     const int pos = tid + SW_NT * r, stx = pos & 31, sty = pos >> 5;
     const int gi = i0 + 2 * stx, gj = j0 + sty;
-    st_own[r] = pos < 256 && gi < g.n[0] && gj < g.n[1];
+    st_own[r] = gi < g.n[0] && gj < g.n[1];
     q0[r] = (long long)gi + (long long)g.n[0] * gj;
     est[r] = (sty + 2) * BX + 2 * stx + 4;
   }
   const long long qk = (long long)g.n[0] * g.n[1];
-  float2 hph[2], hpl[2];  // ph, pl of the next plane to store
+  float2 hph[NST], hpl[NST];  // ph, pl of the next plane to store
 #pragma unroll
-  for (int r = 0; r < 2; ++r) hph[r] = hpl[r] = make_float2(0.f, 0.f);
+  for (int r = 0; r < NST; ++r) hph[r] = hpl[r] = make_float2(0.f, 0.f);
   auto prefetch = [&](int k) {
     if (!a.ph || k >= k1) return;
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
+    for (int r = 0; r < NST; ++r)
       if (st_own[r] && wl_in(q0[r] + (D == 3 ? qk * k : 0) + 1, g.nc, WL_DBG_SWEEP)) {
         const long long q = q0[r] + (D == 3 ? qk * k : 0);
         hph[r] = *reinterpret_cast<const float2*>(a.ph + q);
@@ -578,7 +629,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP  ? SWEEP_WRAP_BLOCKS_PER_SM
   };
   auto store = [&](int Xk, int k) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
+    for (int r = 0; r < NST; ++r) {
       if (!st_own[r]) continue;
       if (!wl_in(q0[r] + (D == 3 ? qk * k : 0) + 1, g.nc, WL_DBG_SWEEP)) continue;
       const float2 v = *reinterpret_cast<const float2*>(smf + Xk + est[r]);
@@ -1124,17 +1175,17 @@ static void band_tiles(int n, int w, int pad, int blo, int bhi, int& lo, int& hi
   }
 }
 
-double band_tile_fraction(int D, const Grid& g, int tz, const BandBox& b) {
+double band_tile_fraction(int D, const Grid& g, int tz, const BandBox& b, int ty) {
   int lo[3], hi[3];
   band_tiles(g.n[0], TX, 4, b.lo[0], b.hi[0], lo[0], hi[0]);
-  band_tiles(g.n[1], TY, 2, b.lo[1], b.hi[1], lo[1], hi[1]);
+  band_tiles(g.n[1], ty, 2, b.lo[1], b.hi[1], lo[1], hi[1]);
   if (D == 3)
     band_tiles(g.n[2], tz, 2, b.lo[2], b.hi[2], lo[2], hi[2]);
   else {
     lo[2] = 0;
     hi[2] = 1;
   }
-  const double all = (double)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) *
+  const double all = (double)((g.n[0] + TX - 1) / TX) * ((g.n[1] + ty - 1) / ty) *
                      (D == 3 ? (g.n[2] + tz - 1) / tz : 1);
   double band = 1.0;
   for (int d = 0; d < 3; ++d) band *= std::max(0, hi[d] - lo[d]);
@@ -1220,23 +1271,33 @@ int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a0, cudaStream_t s,
   return 0;
 }
 
+template <int TYV>
 size_t sweep_tma_smem(bool uni) {
-  const size_t rings = uni ? (size_t)XR * BOX + (size_t)CR * CSLOT
-                           : (size_t)XR * BOX + (size_t)L2R * CSLOT + (size_t)CR * (2 * CSLOT + L1SLOT);
+  using G = SwGeom<TYV>;
+  const size_t rings = uni ? (size_t)XR * G::BOX + (size_t)CR * G::CSLOT
+                           : (size_t)XR * G::BOX + (size_t)L2R * G::CSLOT + (size_t)CR * (2 * G::CSLOT + G::L1SLOT);
   return rings * sizeof(float) + (1 + NBB) * sizeof(uint64_t) + 128;
 }
 
-template <int D, bool UNI, bool WRAP = false>
-void launch_sweep_tma_v(const SweepMaps& m, const SweepTmaArgs& a, dim3 grd, cudaStream_t s) {
-  const size_t smem = sweep_tma_smem(UNI);
+template <int D, bool UNI, bool WRAP, int TYV>
+void launch_sweep_tma_t(const SweepMaps& m, const SweepTmaArgs& a, dim3 grd, cudaStream_t s) {
+  const size_t smem = sweep_tma_smem<TYV>(UNI);
   static bool attr = false;
   if (!attr) {  // all of the unified L1/shared storage as shared memory: the blocks per SM are smem-bound
-    cudaFuncSetAttribute(k_sweep_tma<D, UNI, WRAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_sweep_tma<D, UNI, WRAP>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    cudaFuncSetAttribute(k_sweep_tma<D, UNI, WRAP, TYV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_sweep_tma<D, UNI, WRAP, TYV>, cudaFuncAttributePreferredSharedMemoryCarveout,
                          (int)cudaSharedmemCarveoutMaxShared);
     attr = true;
   }
-  k_sweep_tma<D, UNI, WRAP><<<grd, SW_NT, smem, s>>>(m, a);
+  k_sweep_tma<D, UNI, WRAP, TYV><<<grd, SW_NT, smem, s>>>(m, a);
+}
+// tile height 16 (3-D, plain tiles only) or 8
+template <int D, bool UNI, bool WRAP = false>
+void launch_sweep_tma_v(const SweepMaps& m, const SweepTmaArgs& a, dim3 grd, cudaStream_t s) {
+  if constexpr (D == 3 && !WRAP) {
+    if (a.ty == SWEEP_TY16) return launch_sweep_tma_t<D, UNI, WRAP, SWEEP_TY16>(m, a, grd, s);
+  }
+  launch_sweep_tma_t<D, UNI, WRAP, 8>(m, a, grd, s);
 }
 
 namespace {
@@ -1247,8 +1308,10 @@ namespace {
 void launch_plain(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStream_t s, const SideStream* side) {
   const Grid& g = a0.g;
   const int tz = D == 3 ? a0.tz : 1;
-  const dim3 full((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, D == 3 ? (g.n[2] + tz - 1) / tz : 1);
+  const int ty = (D == 3 && a0.ty == SWEEP_TY16) ? SWEEP_TY16 : TY;
+  const dim3 full((g.n[0] + TX - 1) / TX, (g.n[1] + ty - 1) / ty, D == 3 ? (g.n[2] + tz - 1) / tz : 1);
   SweepTmaArgs a = a0;
+  a.ty = ty;
   a.t0[0] = a.t0[1] = a.t0[2] = 0;
   if (!a.band.on) {
     if (D == 3)
@@ -1265,7 +1328,7 @@ void launch_plain(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStream_
   };
   int lo[3], hi[3];
   band_tiles(g.n[0], TX, 4, a.band.lo[0], a.band.hi[0], lo[0], hi[0]);
-  band_tiles(g.n[1], TY, 2, a.band.lo[1], a.band.hi[1], lo[1], hi[1]);
+  band_tiles(g.n[1], ty, 2, a.band.lo[1], a.band.hi[1], lo[1], hi[1]);
   if (D == 3)
     band_tiles(g.n[2], tz, 2, a.band.lo[2], a.band.hi[2], lo[2], hi[2]);
   else {

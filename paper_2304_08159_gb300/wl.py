@@ -39,7 +39,7 @@ WL_FIELD_EXIT = 7
 WL_BODY_NONE = 0
 WL_BODY_SPHERE = 1
 WL_BODY_TORUS = 2
-WL_PATH_RESID_STAGED, WL_PATH_CLUSTER_TAIL, WL_PATH_BLOCK_TAIL = 1, 2, 4
+WL_PATH_RESID_STAGED, WL_PATH_CLUSTER_TAIL, WL_PATH_BLOCK_TAIL, WL_PATH_TALL_TILES = 1, 2, 4, 8
 WL_BODY_FIELD = 3
 
 WL_COARSE_FP32 = 0

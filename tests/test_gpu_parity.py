@@ -527,6 +527,47 @@ def test_uniform_tiles_match_loading_kernels(case, monkeypatch):
 @pytest.mark.parametrize("case", [
     dict(id="s192", dims=(192, 96, 96), nu=0.01, U=(1.0, 0.0, 0.0), periodic=0,
          body=dict(kind=1, center=(60.3, 47.2, 49.7), radius=9.0)),
+    dict(id="channel96", dims=(96, 64, 40), nu=0.01, U=(1.0, 0.2, 0.0), periodic=0, body=None),
+    dict(id="zper128", dims=(128, 48, 64), nu=0.01, U=(1.0, 0.0, 0.0), periodic=4,
+         body=dict(kind=1, center=(40.0, 22.5, 30.0), radius=7.0)),
+    dict(id="torus96", dims=(96, 64, 64), nu=0.02, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=2, center=(30.0, 32.3, 31.8), radius=12.0, radius2=4.0)),
+    dict(id="sdfbox160", dims=(160, 80, 64), nu=0.01, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=3, nodes=sampled_nodes((160, 80, 64), rounded_box((50.3, 40.2, 31.7), (8.0, 6.0, 5.0), 2.0)))),
+], ids=lambda c: c["id"])
+def test_tall_tiles_match_short_tiles(case, monkeypatch):
+    """The staged sweep in tiles of 64 x 16 cells (every level that may take them: split,
+    periodic in neither x nor y, n_1 a multiple of 16) gives the bits of 64 x 8 tiles, with
+    the split forced on every level: band and uniform tiles, the first sweep's coarse
+    correction and the last sweep's double-float fold, walls on every side, a periodic z
+    side, a ragged last tile column (96 = 64 + 32) and z-blocks."""
+    from paper_2304_08159_gb300 import wl
+
+    monkeypatch.setenv("WL_UNIFORM_ALL", "1")
+    monkeypatch.setenv("WL_TY16_MIN_CELLS", "0")
+    a, _ = make_pair(case, oracle=False)
+    monkeypatch.setenv("WL_TY16_MIN_CELLS", str(1 << 40))
+    b, _ = make_pair(case, oracle=False)
+    monkeypatch.delenv("WL_TY16_MIN_CELLS")
+    monkeypatch.delenv("WL_UNIFORM_ALL")
+    assert a.kernel_paths() & wl.WL_PATH_TALL_TILES
+    assert not b.kernel_paths() & wl.WL_PATH_TALL_TILES
+    rng = np.random.default_rng(108)
+    u = _rand_u(a, rng, case["U"], 0.2).astype(np.float32)
+    for sim in (a, b):
+        sim.set(0, u)
+    a.step(4)
+    b.step(4)
+    for sim in (a, b):
+        rc, last, tot, worst = sim.status()
+        assert rc == 0 and worst <= 1e-6, (rc, last, tot, worst)
+    assert np.array_equal(a.get(0), b.get(0))
+    assert np.array_equal(a.get(1), b.get(1))
+
+
+@pytest.mark.parametrize("case", [
+    dict(id="s192", dims=(192, 96, 96), nu=0.01, U=(1.0, 0.0, 0.0), periodic=0,
+         body=dict(kind=1, center=(60.3, 47.2, 49.7), radius=9.0)),
     dict(id="channel128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.2, 0.0), periodic=0, body=None),
     dict(id="yper128", dims=(128, 64, 48), nu=0.01, U=(1.0, 0.0, 0.0), periodic=2,
          body=dict(kind=1, center=(40.0, 30.0, 24.0), radius=6.0)),
