@@ -31,10 +31,6 @@ namespace {
 constexpr int TX = SWEEP_TX, TY = SWEEP_TY;  // tile
 constexpr int BX = TX + 8, BY = TY + 4;  // box: x from i0-4 (aligned), y from j0-2
 constexpr int BOX = BX * BY;          // floats per field per plane
-// sweep: coefficient boxes of CROWS rows from j0-1 (z, L0, L2) and L1ROWS (L1, whose
-// upper face of row 8 is row 9); slots padded to 128-byte multiples
-constexpr int CROWS = SWEEP_CROWS, L1ROWS = SWEEP_CROWS + 1;
-constexpr int CSLOT = (BX * CROWS + 31) / 32 * 32, L1SLOT = (BX * L1ROWS + 31) / 32 * 32;
 constexpr int LEAD = 1;         // bundles staged ahead of the iteration that waits for them
 constexpr int XR = LEAD + 4;    // iterate slots (planes k-1 .. k+2, and LEAD more in flight)
 constexpr int L2R = LEAD + 3;   // L2 slots (planes k .. k+2, and LEAD more in flight)
@@ -369,29 +365,10 @@ __global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_
   // present, 2/3 lower/upper y face, 4 cell inside the grid in x and y; zlo/zhi: lower /
   // upper z face present, kin: plane inside the grid.
   const float uv = a.uval;
-  auto relax_uni = [&](const Planes& P, uint32_t e, uint32_t mxy, bool zlo, bool zhi, bool kin) -> float {
-    if (!(mxy & 16u) || !kin) return 0.f;  // outside the grid: every face reads 0 -> 0
-    const uint32_t x0 = P.x0 + e;
-    const float l0u = (mxy & 2u) ? uv : 0.f, l0d = (mxy & 1u) ? uv : 0.f;
-    const float l1u = (mxy & 8u) ? uv : 0.f, l1d = (mxy & 4u) ? uv : 0.f;
-    float sum = fmaf(l0u, lds<4>(x0), 0.f);
-    sum = fmaf(l0d, lds<-4>(x0), sum);
-    float dg = l0u + l0d;
-    sum = fmaf(l1u, lds<4 * BX>(x0), sum);
-    sum = fmaf(l1d, lds<-4 * BX>(x0), sum);
-    dg += l1u + l1d;
-    if (D == 3) {
-      const float lu = zhi ? uv : 0.f, ll = zlo ? uv : 0.f;
-      sum = fmaf(lu, lds(P.xp + e), sum);
-      sum = fmaf(ll, lds(P.xm + e), sum);
-      dg += lu + ll;
-    }
-    return (dg > 0.f) ? __fdividef(sum - lds(P.z + e), dg) : 0.f;
-  };
   // UNI tile whose x/y footprint touches no wall: on a plane with both z faces
   // (zfull) every cell it relaxes, halo included, has all its faces, each coefficient is
   // uv, so the relaxation is the same FMA chain with uv and the diagonal the constant
-  // 2D uv (the same bits as relax_uni)
+  // 2D uv (the same bits as relax_cnt and as the loading kernel's relax)
   const bool interior = UNI && i0 >= 4 && i0 + TX + 4 <= g.n[0] && j0 >= 2 && j0 + TY + 2 <= g.n[1];
   const float dg_int = D == 3 ? (uv + uv) + (uv + uv) + (uv + uv) : (uv + uv) + (uv + uv);
   auto relax_fast = [&](const Planes& P, uint32_t e) -> float {
@@ -421,6 +398,46 @@ __global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_
     const float2 d = sub2(sum, make_float2(lds(P.z + e0), lds(P.z + e1)));
     return make_float2(__fdividef(d.x, dg_int), __fdividef(d.y, dg_int));
   };
+  // UNI cell of a tile touching a wall: the masked relaxation (coefficient uv on
+  // present faces, 0 on missing ones, as the loading kernel's relax with the level's
+  // coefficients) from the constant-coefficient FMA chain.  A face is missing only where
+  // the neighbour lies outside the grid (non-periodic side), and every such neighbour
+  // holds +0 in the box (zero fill of the copy, or a 0 written by this relaxation for a
+  // cell outside), so each term uv * 0 adds the same +0 as 0 * x would; the running sum
+  // is never -0 (it starts from +0 and an exact cancellation rounds to +0), so the sums
+  // agree bit for bit.  The diagonal is nf uv with nf the cell's present faces: exact,
+  // as the masked sum of 0s and uv is (uv a power of two).  Cells outside the grid give 0.
+  auto dg_of = [&](uint32_t mxy, int nz) { return uv * (float)(__popc(mxy & 15u) + nz); };
+  auto relax_cnt = [&](const Planes& P, uint32_t e, uint32_t mxy, int nz, bool kin) -> float {
+    const uint32_t x0 = P.x0 + e;
+    float sum = fmaf(uv, lds<4>(x0), 0.f);
+    sum = fmaf(uv, lds<-4>(x0), sum);
+    sum = fmaf(uv, lds<4 * BX>(x0), sum);
+    sum = fmaf(uv, lds<-4 * BX>(x0), sum);
+    if (D == 3) {
+      sum = fmaf(uv, lds(P.xp + e), sum);
+      sum = fmaf(uv, lds(P.xm + e), sum);
+    }
+    const float dg = dg_of(mxy, nz);
+    return ((mxy & 16u) && kin && dg > 0.f) ? __fdividef(sum - lds(P.z + e), dg) : 0.f;
+  };
+  auto relax_cnt2 = [&](const Planes& P, uint32_t e0, uint32_t e1, uint32_t m0, uint32_t m1, int nz,
+                        bool kin) -> float2 {
+    const uint32_t a0 = P.x0 + e0, a1 = P.x0 + e1;
+    const float2 u2 = make_float2(uv, uv);
+    float2 sum = fma2(u2, make_float2(lds<4>(a0), lds<4>(a1)), make_float2(0.f, 0.f));
+    sum = fma2(u2, make_float2(lds<-4>(a0), lds<-4>(a1)), sum);
+    sum = fma2(u2, make_float2(lds<4 * BX>(a0), lds<4 * BX>(a1)), sum);
+    sum = fma2(u2, make_float2(lds<-4 * BX>(a0), lds<-4 * BX>(a1)), sum);
+    if (D == 3) {
+      sum = fma2(u2, make_float2(lds(P.xp + e0), lds(P.xp + e1)), sum);
+      sum = fma2(u2, make_float2(lds(P.xm + e0), lds(P.xm + e1)), sum);
+    }
+    const float2 d = sub2(sum, make_float2(lds(P.z + e0), lds(P.z + e1)));
+    const float dg0 = dg_of(m0, nz), dg1 = dg_of(m1, nz);
+    return make_float2(((m0 & 16u) && kin && dg0 > 0.f) ? __fdividef(d.x, dg0) : 0.f,
+                       ((m1 & 16u) && kin && dg1 > 0.f) ? __fdividef(d.y, dg1) : 0.f);
+  };
   auto relax = [&](const Planes& P, uint32_t e) -> float {
     const uint32_t x0 = P.x0 + e, l0 = P.l0 + e, l1 = P.l1 + e;
     const float l0u = lds<4>(l0), l0d = lds(l0), l1u = lds<4 * BX>(l1), l1d = lds(l1);
@@ -449,7 +466,7 @@ __global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_
   constexpr int NRH = TY / 4, NEDGE = TY / 2 + 1;
   static_assert(NRH % 2 == 0, "tasks in pairs");
   uint32_t er[NRH + 1][2], eb[NRH][2];
-  uint32_t mr[NRH + 1][2], mb[NRH][2];  // UNI: face masks of each task's cell (relax_uni)
+  uint32_t mr[NRH + 1][2], mb[NRH][2];  // UNI: face masks of each task's cell (relax_cnt)
   auto xymask = [&](int col, int row) -> uint32_t {
     const int gi = i0 + col, gj = j0 + row;
     const bool px = is_per(g, 0), py = is_per(g, 1);
@@ -524,37 +541,31 @@ __global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_
       if (third) sts(P.x0 + e2, relax_fast(P, e2));
       return;
     }
-    if (UNI) {
+    if constexpr (UNI) {
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
       const uint32_t fm = (zlo && zhi && kin) ? fast_m >> par : 0u;
+      const int nz = D == 3 ? (zlo ? 1 : 0) + (zhi ? 1 : 0) : 0;
 #pragma unroll
       for (int hp = 0; hp < NRH / 2; ++hp) {
         const uint32_t e0 = pk(er[2 * hp]), e1 = pk(er[2 * hp + 1]);
         const uint32_t b0 = 1u << (4 * hp), b1 = 4u << (4 * hp);
-        if ((fm & (b0 | b1)) == (b0 | b1)) {
-          const float2 v = relax_fast2(P, e0, e1);
-          sts(P.x0 + e0, v.x);
-          sts(P.x0 + e1, v.y);
-        } else {
-          const float v0 = (fm & b0) ? relax_fast(P, e0) : relax_uni(P, e0, pk(mr[2 * hp]), zlo, zhi, kin);
-          const float v1 = (fm & b1) ? relax_fast(P, e1) : relax_uni(P, e1, pk(mr[2 * hp + 1]), zlo, zhi, kin);
-          sts(P.x0 + e0, v0);
-          sts(P.x0 + e1, v1);
-        }
+        const float2 v = ((fm & (b0 | b1)) == (b0 | b1)) ? relax_fast2(P, e0, e1)
+                                                          : relax_cnt2(P, e0, e1, pk(mr[2 * hp]), pk(mr[2 * hp + 1]), nz, kin);
+        sts(P.x0 + e0, v.x);
+        sts(P.x0 + e1, v.y);
       }
-      if (third)
-        sts(P.x0 + e2, ((fm >> (2 * NRH)) & 1u) ? relax_fast(P, e2) : relax_uni(P, e2, pk(mr[NRH]), zlo, zhi, kin));
-      return;
-    }
+      if (third) sts(P.x0 + e2, ((fm >> (2 * NRH)) & 1u) ? relax_fast(P, e2) : relax_cnt(P, e2, pk(mr[NRH]), nz, kin));
+    } else {
 #pragma unroll
-    for (int hp = 0; hp < NRH / 2; ++hp) {
-      const uint32_t e0 = pk(er[2 * hp]), e1 = pk(er[2 * hp + 1]);
-      const float v0 = relax(P, e0), v1 = relax(P, e1);
-      sts(P.x0 + e0, v0);
-      sts(P.x0 + e1, v1);
+      for (int hp = 0; hp < NRH / 2; ++hp) {
+        const uint32_t e0 = pk(er[2 * hp]), e1 = pk(er[2 * hp + 1]);
+        const float v0 = relax(P, e0), v1 = relax(P, e1);
+        sts(P.x0 + e0, v0);
+        sts(P.x0 + e1, v1);
+      }
+      if (third) sts(P.x0 + e2, relax(P, e2));
     }
-    if (third) sts(P.x0 + e2, relax(P, e2));
   };
   // black cells of plane kk (parity par) whose operands are P
   auto black_plane = [&](const Planes& P, int par, int kk) {
@@ -569,33 +580,28 @@ __global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_
       }
       return;
     }
-    if (UNI) {
+    if constexpr (UNI) {
       bool zlo, zhi, kin;
       zmask(kk, zlo, zhi, kin);
       const uint32_t fm = (zlo && zhi && kin) ? fast_m >> (BLK + par) : 0u;
+      const int nz = D == 3 ? (zlo ? 1 : 0) + (zhi ? 1 : 0) : 0;
 #pragma unroll
       for (int hp = 0; hp < NRH / 2; ++hp) {
         const uint32_t e0 = pk(eb[2 * hp]), e1 = pk(eb[2 * hp + 1]);
         const uint32_t b0 = 1u << (4 * hp), b1 = 4u << (4 * hp);
-        if ((fm & (b0 | b1)) == (b0 | b1)) {
-          const float2 v = relax_fast2(P, e0, e1);
-          sts(P.x0 + e0, v.x);
-          sts(P.x0 + e1, v.y);
-        } else {
-          const float v0 = (fm & b0) ? relax_fast(P, e0) : relax_uni(P, e0, pk(mb[2 * hp]), zlo, zhi, kin);
-          const float v1 = (fm & b1) ? relax_fast(P, e1) : relax_uni(P, e1, pk(mb[2 * hp + 1]), zlo, zhi, kin);
-          sts(P.x0 + e0, v0);
-          sts(P.x0 + e1, v1);
-        }
+        const float2 v = ((fm & (b0 | b1)) == (b0 | b1)) ? relax_fast2(P, e0, e1)
+                                                          : relax_cnt2(P, e0, e1, pk(mb[2 * hp]), pk(mb[2 * hp + 1]), nz, kin);
+        sts(P.x0 + e0, v.x);
+        sts(P.x0 + e1, v.y);
       }
-      return;
-    }
+    } else {
 #pragma unroll
-    for (int hp = 0; hp < NRH / 2; ++hp) {
-      const uint32_t e0 = pk(eb[2 * hp]), e1 = pk(eb[2 * hp + 1]);
-      const float v0 = relax(P, e0), v1 = relax(P, e1);
-      sts(P.x0 + e0, v0);
-      sts(P.x0 + e1, v1);
+      for (int hp = 0; hp < NRH / 2; ++hp) {
+        const uint32_t e0 = pk(eb[2 * hp]), e1 = pk(eb[2 * hp + 1]);
+        const float v0 = relax(P, e0), v1 = relax(P, e1);
+        sts(P.x0 + e0, v0);
+        sts(P.x0 + e1, v1);
+      }
     }
   };
   // Write the tile's plane k: 32 TY column pairs, pairs t, t + 128, .. for thread t;
