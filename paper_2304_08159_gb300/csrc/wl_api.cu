@@ -204,7 +204,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Smallest level (cells) that takes 16-row sweep tiles (WL_TY16_MIN_CELLS overrides).
 long long ty16_min_cells() {
   const char* e = std::getenv("WL_TY16_MIN_CELLS");
-  return e ? std::atoll(e) : (1ll << 20);
+  return e ? std::atoll(e) : (1ll << 18);
 }
 
 // Planes per block of the staged sweep on level l: whole waves of its resident blocks

@@ -539,6 +539,9 @@ __device__ __forceinline__ void bdim_band_body(const StageArgs& a, const Body& b
   if (!(is_per(g, c) || I[c] >= 1)) return;
   double x[3] = {i + 0.5, j + 0.5, k + 0.5};
   x[c] -= 0.5;
+  // most faces of the box lie well outside the band: an FP32 distance half a cell past
+  // eps skips them before the FP64 evaluation (which alone decides for the others)
+  if (fabsf(body_dist_f<D>(b, x)) > (float)b.eps + 0.5f) return;
   double nrm[3];
   const double d = body_sdf<D>(b, x, nrm);
   if (!(fabs(d) < b.eps)) return;
