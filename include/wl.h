@@ -327,7 +327,13 @@ int wl_status(wl_handle h, int* last_vcycles /*[2]*/, long long* total_vcycles, 
 #define WL_KCLASS_COARSEST 6    /* coarsest-level solve */
 #define WL_KCLASS_CORRECT 7     /* pressure-gradient correction (+ CFL maximum) */
 #define WL_KCLASS_CONTROL 8     /* one-thread control kernels (V-cycle decision, step end) */
-#define WL_KCLASS_COUNT 9
+/* the fine level's split launches, each timed on its own stream while the other runs
+ * beside it (also counted, as the pair's wall time, in SWEEP_FINE / RESID_FINE): */
+#define WL_KCLASS_SWEEP_FINE_UNI 9    /* fine sweep, uniform tiles */
+#define WL_KCLASS_SWEEP_FINE_BANDT 10 /* fine sweep, band tiles */
+#define WL_KCLASS_RESID_FINE_UNI 11   /* fine residual / divergence, uniform tiles */
+#define WL_KCLASS_RESID_FINE_BANDT 12 /* fine residual / divergence, band tiles */
+#define WL_KCLASS_COUNT 13
 
 /* Advance nsteps steps through the host-driven launch sequence (the same kernels
  * as wl_step) with a pair of CUDA events on the sim's stream around every launch,

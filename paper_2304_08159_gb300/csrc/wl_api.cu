@@ -152,21 +152,37 @@ int cuda_check(wl_sim* s, cudaError_t e, const char* what) {
   } while (0)
 
 // Time one launch with a pair of events when profiling (host-driven steps only).
-void prof_begin(wl_sim* s, cudaStream_t st, int cls) {
+size_t prof_begin(wl_sim* s, cudaStream_t st, int cls) {
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   cudaEventRecord(a, st);
   s->prof->emplace_back(cls, a, b);
+  return s->prof->size() - 1;
 }
-void prof_end(wl_sim* s, cudaStream_t st) { cudaEventRecord(std::get<2>(s->prof->back()), st); }
+void prof_end(wl_sim* s, cudaStream_t st, size_t i) { cudaEventRecord(std::get<2>((*s->prof)[i]), st); }
 
-#define PROF(s, st, cls, call)               \
-  do {                                       \
-    if ((s)->prof) prof_begin((s), (st), (cls)); \
-    call;                                    \
-    if ((s)->prof) prof_end((s), (st));      \
+#define PROF(s, st, cls, call)                                 \
+  do {                                                         \
+    const size_t prof_i_ = (s)->prof ? prof_begin((s), (st), (cls)) : 0; \
+    call;                                                      \
+    if ((s)->prof) prof_end((s), (st), prof_i_);               \
   } while (0)
+
+// The fine level's split launches (uniform tiles on the sim's stream, band tiles beside
+// them on the side stream), each timed on its own stream while wl_profile_step runs.
+struct ProfSplit {
+  wl_sim* s;
+  int cls[2];  // uniform, band
+  size_t idx[2];
+};
+void prof_split_hook(void* ctx, int band, int begin, cudaStream_t st) {
+  ProfSplit* h = static_cast<ProfSplit*>(ctx);
+  if (begin)
+    h->idx[band] = prof_begin(h->s, st, h->cls[band]);
+  else
+    prof_end(h->s, st, h->idx[band]);
+}
 
 // Multigrid levels: halve while every direction is even and larger than 4.
 int plan_levels(const int* n, int D, int out[][3]) {
@@ -487,7 +503,11 @@ void enq_fine_residual(wl_sim* s, int mode, int ubuf, float w, cudaStream_t st) 
       t.wsrc[2] = ub[ubuf][0];
       t.wsrc[3] = ub[ubuf][1];
     }
-    PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st, side_of(s)));
+    ProfSplit ps{s, {WL_KCLASS_RESID_FINE_UNI, WL_KCLASS_RESID_FINE_BANDT}, {0, 0}};
+    SideStream sp = s->side;
+    sp.hook = prof_split_hook;
+    sp.ctx = &ps;
+    PROF(s, st, WL_KCLASS_RESID_FINE, launch_resid_tma(m, t, st, (s->prof && side_of(s)) ? &sp : side_of(s)));
     return;
   }
   PROF(s, st, WL_KCLASS_RESID_FINE, launch_residual(s->D, fine_res_args(s, mode, ubuf, w), st));
@@ -600,7 +620,12 @@ void enq_smooth(wl_sim* s, int l, cudaStream_t st) {
       t.zsrc = refine ? s->rf : L.z;
       t.tzw = L.tzw;
       t.ty = L.ty;
-      PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st, side_of(s)));
+      ProfSplit ps{s, {WL_KCLASS_SWEEP_FINE_UNI, WL_KCLASS_SWEEP_FINE_BANDT}, {0, 0}};
+      SideStream sp = s->side;
+      sp.hook = prof_split_hook;
+      sp.ctx = &ps;
+      const SideStream* sd = (s->prof && l == 0 && side_of(s)) ? &sp : side_of(s);
+      PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep_tma(s->D, m, t, st, sd));
       a.only_wrapping = 1;  // tiles crossing a periodic side
       if (L.wrap_tiles > 0) PROF(s, st, l == 0 ? WL_KCLASS_SWEEP_FINE : WL_KCLASS_SWEEP_COARSE, launch_sweep(s->D, a, st));
     } else {

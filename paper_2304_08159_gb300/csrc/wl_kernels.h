@@ -198,6 +198,10 @@ int launch_sweep(int D, const SweepArgs& a, cudaStream_t s);
 struct SideStream {
   cudaStream_t aux;
   cudaEvent_t fork, join;
+  // profiling only: called before (begin 1) and after (begin 0) the uniform (band 0) and
+  // the band-tile (band 1) launch, on the stream that launch goes to
+  void (*hook)(void* ctx, int band, int begin, cudaStream_t st);
+  void* ctx;
 };
 int launch_sweep_tma(int D, const SweepMaps& m, const SweepTmaArgs& a, cudaStream_t s, const SideStream* side);
 // fraction of a level's sweep tiles (tz planes per block) that meet the band box

@@ -1266,8 +1266,12 @@ int launch_resid_tma(const ResidMaps& m, const ResidTmaArgs& a0, cudaStream_t s,
   if (side) {  // the band tiles beside the uniform ones
     cudaEventRecord(side->fork, s);
     cudaStreamWaitEvent(side->aux, side->fork, 0);
+    if (side->hook) side->hook(side->ctx, 1, 1, side->aux);
     launch_resid_tma_u<false>(m, b, grd, side->aux);
+    if (side->hook) side->hook(side->ctx, 1, 0, side->aux);
+    if (side->hook) side->hook(side->ctx, 0, 1, s);
     launch_resid_tma_u<true>(m, a, full, s);
+    if (side->hook) side->hook(side->ctx, 0, 0, s);
     cudaEventRecord(side->join, side->aux);
     cudaStreamWaitEvent(s, side->join, 0);
   } else {
@@ -1357,8 +1361,12 @@ void launch_plain(int D, const SweepMaps& m, const SweepTmaArgs& a0, cudaStream_
   if (side) {  // the band tiles beside the uniform ones
     cudaEventRecord(side->fork, s);
     cudaStreamWaitEvent(side->aux, side->fork, 0);
+    if (side->hook) side->hook(side->ctx, 1, 1, side->aux);
     band(side->aux);
+    if (side->hook) side->hook(side->ctx, 1, 0, side->aux);
+    if (side->hook) side->hook(side->ctx, 0, 1, s);
     uni(s);
+    if (side->hook) side->hook(side->ctx, 0, 0, s);
     cudaEventRecord(side->join, side->aux);
     cudaStreamWaitEvent(s, side->join, 0);
   } else {

@@ -62,7 +62,7 @@ EXPORTS = (
 METRIC_RING, METRIC_FIELDS = 1024, 13
 METRICS = ("step", "time", "dt", "vcycles1", "vcycles2", "resid1", "resid2", "cfl", "ke", "maxdiv", "F0", "F1", "F2")
 KCLASSES = ("stage", "band", "resid_fine", "restrict", "sweep_fine", "sweep_coarse", "coarsest", "correct",
-            "control")
+            "control", "sweep_fine_uni", "sweep_fine_bandt", "resid_fine_uni", "resid_fine_bandt")
 
 
 class WlBody(ctypes.Structure):
