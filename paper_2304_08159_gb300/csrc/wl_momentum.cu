@@ -577,9 +577,10 @@ __global__ void __launch_bounds__(256) k_bdim_band(StageArgs a, Body b, int lo0,
   bdim_band_body<D>(a, b, lo0, lo1, lo2, bx, by, bz, blockIdx);
 }
 
-// Planes per block of k_stage3: 32 when that gives two waves of blocks (3 resident per
-// SM) or more; else the fewest waves times the planes a block stages (its own and the 3
-// of its z halo).
+// Planes per block of k_stage3: the fewest waves of blocks (3 resident per SM) times the
+// planes a block stages (its own and the 3 of its z halo), from 4 to 48 planes
+// (512x256x256: 37 planes, 4 waves of 1792 blocks; 32 planes in 4.5 waves measured the
+// same; the 128^3 vortex: 10 planes, 416 blocks).  WL_STAGE_TZ overrides.
 int stage3_planes(const Grid& g) {
   static int nsm = 0;
   if (nsm <= 0) {
@@ -590,14 +591,14 @@ int stage3_planes(const Grid& g) {
       nsm = 152;
     }
   }
+  if (const char* e = std::getenv("WL_STAGE_TZ")) return std::max(1, std::atoi(e));
   const long long cols = (long long)((g.n[0] + S3_TX - 1) / S3_TX) * ((g.n[1] + S3_TY - 1) / S3_TY);
   const long long wave = 3LL * nsm;
-  if (cols * ((g.n[2] + S3_TZ - 1) / S3_TZ) >= 2 * wave) return S3_TZ;
   int best = S3_TZ;
   double best_cost = 1e300;
-  for (int tz = S3_TZ; tz >= 4; --tz) {
+  for (int tz = 48; tz >= 4; --tz) {
     const long long nb = cols * ((g.n[2] + tz - 1) / tz);
-    const double cost = (double)((nb + wave - 1) / wave) * (tz + 3);
+    const double cost = (double)((nb + wave - 1) / wave) * (std::min(tz, g.n[2]) + 3);
     if (cost < best_cost) {
       best_cost = cost;
       best = tz;
