@@ -1110,7 +1110,11 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
     int lo[3], hi[3];
     const bool body = stage_band_box(ndim, s->g, s->body, lo, hi);
     const bool split = !std::getenv("WL_NO_UNIFORM");
-    const double frac_max = std::getenv("WL_UNIFORM_ALL") ? 2.0 : 0.05;  // WL_UNIFORM_ALL: split every level
+    // The largest band-tile fraction a level splits at: 5 %, 8 % on levels of at least 2^24
+    // cells (measured: the 512x256x256 donut's fine level, 5.2 %: 9.73 -> 7.61 ms per
+    // step split; the 256x128x128 sphere's, 6.9 %: 1.714 -> 1.728 ms).  WL_UNIFORM_ALL:
+    // split every level; WL_SPLIT_MAX: one fraction for every level.
+    const char* sm = std::getenv("WL_SPLIT_MAX");
     for (int l = 0; l < s->nlev; ++l) {
       LevelBuf& L = s->lev[l];
       L.uval = ldexpf(1.f, l * (ndim - 2));
@@ -1124,6 +1128,9 @@ int wl_create(const int* dims, int ndim, double nu, const double* U, const wl_bo
         }
       }
       const int tz = sweep_planes_per_block(L.g, SWEEP_UNI_BLOCKS_PER_SM);
+      const double frac_max = std::getenv("WL_UNIFORM_ALL") ? 2.0
+                              : sm                           ? std::atof(sm)
+                              : (L.g.nc >= (1ll << 24) ? 0.08 : 0.05);
       L.band.on = (split && band_tile_fraction(ndim, L.g, tz, L.band, SWEEP_TY) <= frac_max) ? 1 : 0;
       // 16-row tiles on the large split levels that are periodic in neither x nor y: a
       // warp relaxes twice the cells per plane for the same per-plane bookkeeping

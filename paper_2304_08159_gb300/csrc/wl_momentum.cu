@@ -704,8 +704,10 @@ bool stage_band_box(int D, const Grid& g, const Body& b, int* lo, int* hi) {
       hi[d] = 1;
       continue;
     }
-    lo[d] = (int)fmax(0.0, floor(b.c[d] - ext));
-    hi[d] = (int)fmin((double)g.n[d], ceil(b.c[d] + ext) + 1.0);
+    // the torus's axis is along x: its surface spans c_x +- r there
+    const double e = (b.kind == 2 && d == 0) ? b.r2 + b.eps + 2.0 : ext;
+    lo[d] = (int)fmax(0.0, floor(b.c[d] - e));
+    hi[d] = (int)fmin((double)g.n[d], ceil(b.c[d] + e) + 1.0);
     if (hi[d] <= lo[d]) return false;  // body outside the grid: no band
   }
   return true;
