@@ -94,3 +94,19 @@ def test_debug_library_exports_the_same_symbols(lib):
     dbg = ctypes.CDLL(wl.DEBUG_LIB_PATH)
     for name in _declared():
         assert hasattr(dbg, name), name
+
+
+def test_header_constants_match_binding():
+    """The binding's kernel classes and path bits are the header's, in the header's order."""
+    from paper_2304_08159_gb300 import wl
+
+    text = open(os.path.join(ROOT, "include", "wl.h")).read()
+    classes = dict((n, int(v)) for n, v in re.findall(r"#define WL_KCLASS_([A-Z_]+)\s+(\d+)", text))
+    count = classes.pop("COUNT")
+    assert count == len(wl.KCLASSES) == len(classes)
+    assert sorted(classes.values()) == list(range(count))
+    for name, idx in classes.items():
+        assert wl.KCLASSES[idx] == name.lower(), (name, idx)
+    paths = dict((n, int(v)) for n, v in re.findall(r"#define (WL_PATH_[A-Z_]+)\s+(\d+)", text))
+    for name, bit in paths.items():
+        assert getattr(wl, name) == bit, name
