@@ -317,10 +317,64 @@ __device__ __forceinline__ void stage3_body(const StageArgs& a, const uint3 bid)
     foff[h] = 2 * cp + g.n[0] * row;
     fsh[h] = row * HX + 2 * cp;
   }
+  // A tile on a side (not xy_inner) maps every fetched element to the array as load_u_bc
+  // does.  The x and y part of that mapping is the same on every plane, so it is taken
+  // once: each element's mapped in-plane index, and whether it lies on or past a
+  // boundary in x (component 0 reads U_0 there) or y (component 1 reads U_1); per plane
+  // only z is mapped (component 2 reads U_2 on or past a z boundary).  Same indices and
+  // values as load_u_bc (which the convective exit keeps using).
+  const bool side_map = !xy_inner && !g.exit;
+  int bofs[2] = {0, 0};  // mapped in-plane index of the pair's first element
+  // bits 8h + 2el: x boundary, 8h + 2el + 1: y boundary; bits 8h + 4..5: the second
+  // element's index minus the first's (0: 0, 1: 1, 2: 1 - n_0, a periodic wrap)
+  unsigned bflag = 0u;
+  if (side_map) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + 256 * h, row = e / (HX / 2), col = 2 * (e - row * (HX / 2));
+      int first = 0;
+#pragma unroll
+      for (int el = 0; el < 2; ++el) {
+        int I = i0 - 2 + col + el, J = j0 - 2 + row;
+        bool bx = false, by = false;
+        if (is_per(g, 0)) {
+          I = wrap_per(I, g.n[0]);
+        } else {
+          bx = I <= 0 || I >= g.n[0];
+          I = I < 0 ? 0 : (I >= g.n[0] ? g.n[0] - 1 : I);
+        }
+        if (is_per(g, 1)) {
+          J = wrap_per(J, g.n[1]);
+        } else {
+          by = J <= 0 || J >= g.n[1];
+          J = J < 0 ? 0 : (J >= g.n[1] ? g.n[1] - 1 : J);
+        }
+        const int q = I + g.n[0] * J;
+        if (el == 0) {
+          bofs[h] = q;
+          first = q;
+        } else {
+          const int d = q - first;
+          bflag |= (d == 0 ? 0u : (d == 1 ? 1u : 2u)) << (8 * h + 4);
+        }
+        bflag |= (bx ? 1u : 0u) << (8 * h + 2 * el);
+        bflag |= (by ? 2u : 0u) << (8 * h + 2 * el);
+      }
+    }
+  }
   float2 rv[2][3];
   auto fetch = [&](int kk) {
     const bool inner = xy_inner && kk >= 0 && kk < g.n[2];
     const long long qk = fbase + nxy * kk;
+    int K = kk;
+    bool bz = false;
+    if (is_per(g, 2)) {
+      K = wrap_per(K, g.n[2]);
+    } else {
+      bz = K <= 0 || K >= g.n[2];
+      K = K < 0 ? 0 : (K >= g.n[2] ? g.n[2] - 1 : K);
+    }
+    const long long kb = nxy * K;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int e = tid + 256 * h;
@@ -331,6 +385,21 @@ __device__ __forceinline__ void stage3_body(const StageArgs& a, const uint3 bid)
           rv[h][c] = wl_in(qk + foff[h] + 1, g.nc, WL_DBG_STAGE)
                          ? __ldg(reinterpret_cast<const float2*>(a.u[c] + qk + foff[h]))
                          : make_float2(0.f, 0.f);
+      } else if (side_map) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float v[2];
+          const unsigned dc = (bflag >> (8 * h + 4)) & 3u;
+          const int d1 = dc == 0u ? 0 : (dc == 1u ? 1 : 1 - g.n[0]);
+#pragma unroll
+          for (int el = 0; el < 2; ++el) {
+            const unsigned f = bflag >> (8 * h + 2 * el);
+            const bool bnd = c == 0 ? (f & 1u) != 0 : (c == 1 ? (f & 2u) != 0 : bz);
+            const long long q = kb + bofs[h] + (el ? d1 : 0);
+            v[el] = bnd ? g.U[c] : (wl_in(q, g.nc, WL_DBG_STAGE) ? __ldg(a.u[c] + q) : 0.f);
+          }
+          rv[h][c] = make_float2(v[0], v[1]);
+        }
       } else {
         const int row = e / (HX / 2), col = 2 * (e - row * (HX / 2));
 #pragma unroll
