@@ -3,10 +3,10 @@
 // residual / divergence pass.  Same arithmetic and results as k_sweep and
 // k_residual; the difference is how the data reaches shared memory.
 //
-// A tile of 64 x 8 cells marches up through `tz` planes.  For every plane the five
-// fields it needs (iterate, right-hand side, the three face-coefficient fields) are
-// fetched by the tensor-memory accelerator as 72 x 12 boxes (tile + halo, x start
-// 16-byte aligned) into two rings of plane slots (iterate: planes k-1..k+3;
+// A tile of 64 x 8 cells (64 x 16 on large split levels) marches up through `tz`
+// planes.  For every plane the five fields it needs (iterate, right-hand side, the three
+// face-coefficient fields) are fetched by the tensor-memory accelerator as 72 x 12 boxes
+// (72 x 20; tile + halo, x start 16-byte aligned) into two rings of plane slots (iterate: planes k-1..k+3;
 // coefficients: planes k..k+3), one plane ahead of the plane being relaxed, each
 // staged plane completing on its own mbarrier.  Red (and black) cells are two floats
 // apart, so a warp takes 16 cells from each of two adjacent rows: their red columns
@@ -14,7 +14,8 @@
 // disjoint banks and no shared access conflicts.  Out-of-range elements are
 // zero-filled by the copy engine, which is exactly the value a non-periodic wall
 // needs (face coefficient 0 across it), so the relaxation itself carries no
-// boundary logic.  A tile whose footprint crosses a periodic x or y side takes the
+// boundary logic (tiles that form their coefficients count a cell's faces for its
+// diagonal and sum its zero-filled neighbours like any other).  A tile whose footprint crosses a periodic x or y side takes the
 // wrapping variant (uniform tiles only), which overwrites the zero-filled halo elements
 // past the side with the wrapped cells' values, read from global memory one plane ahead.
 #include <cuda.h>
