@@ -233,18 +233,20 @@ __global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_
 #pragma unroll
   for (int r = 0; r < NCR; ++r) cv[r] = 0.f;
   int ckey = -2;  // coarse plane whose values cv holds (-1: outside the grid)
+  const long long cplane = (long long)a.cn[0] * a.cn[1];
   auto load_c = [&](int p) {
     const int wp = D == 3 ? wz(p) : p;  // the coarse correction of a wrapped plane
     const int kz = (wp >= 0 && wp < g.n[2]) ? (wp >> 1) : -1;
     if (kz == ckey) return;
     ckey = kz;
+    const long long cb = cplane * kz;
 #pragma unroll
-    for (int r = 0; r < NCR; ++r)
-      cv[r] = (kz >= 0 && cxy[r] >= 0 &&
-               wl_in((long long)cxy[r] + (long long)a.cn[0] * a.cn[1] * kz, (long long)a.cn[0] * a.cn[1] * a.cn[2],
-                     WL_DBG_COARSE))
-                  ? xcm * ld_st(a.xc, a.xctype, (long long)cxy[r] + (long long)a.cn[0] * a.cn[1] * kz)
+    for (int r = 0; r < NCR; ++r) {
+      const long long ci = cb + cxy[r];
+      cv[r] = (kz >= 0 && cxy[r] >= 0 && wl_in(ci, cplane * a.cn[2], WL_DBG_COARSE))
+                  ? xcm * ld_st(a.xc, a.xctype, ci)
                   : 0.f;
+    }
   };
   auto apply_c = [&](int p) {
     float* X = smf + Xs(xslot(p));
@@ -253,10 +255,15 @@ __global__ void __launch_bounds__(SW_NT, WRAP           ? SWEEP_WRAP_BLOCKS_PER_
       if (ceo[r] < 0) continue;
       float2* q0 = reinterpret_cast<float2*>(X + ceo[r]);
       float2* q1 = reinterpret_cast<float2*>(X + ceo[r] + BX);
-      const float2 z = make_float2(0.f, 0.f);
-      const float2 v0 = a.has_x ? *q0 : z, v1 = a.has_x ? *q1 : z;
-      *q0 = make_float2(v0.x + cv[r], v0.y + cv[r]);
-      *q1 = make_float2(v1.x + cv[r], v1.y + cv[r]);
+      if (!a.has_x) {  // from zero: each of the 2 x 2 cells is 0 + the coarse value
+        const float c = 0.f + cv[r];
+        *q0 = make_float2(c, c);
+        *q1 = make_float2(c, c);
+      } else {
+        const float2 v0 = *q0, v1 = *q1;
+        *q0 = make_float2(v0.x + cv[r], v0.y + cv[r]);
+        *q1 = make_float2(v1.x + cv[r], v1.y + cv[r]);
+      }
     }
   };
   auto fix_x = [&](int p) {
