@@ -2,7 +2,8 @@
 step and the computed global loads test their index, a bad one flags a bit and is skipped,
 and canaries sit between the workspace's arrays.  Steps of grids that exercise every
 kernel path (walls, periodic sides, a convective exit, ragged and odd sides, the smallest
-legal grids, analytic and sampled bodies, 16-bit levels, batched steps) run through it in
+legal grids, analytic and sampled bodies, 16-bit levels, every level split in 64 x 16
+tiles, batched steps) run through it in
 a child process and must leave no flag and intact canaries, with the same results as the
 release library."""
 import json
@@ -35,6 +36,12 @@ CASES = [
     dict(dims=(2, 2), nu=0.1, U=(0.0, 0.0), periodic=3, body=None),
     dict(dims=(192, 96, 96), nu=0.01, U=(1.0, 0.0, 0.0), periodic=0, body=dict(kind=1, center=(60.3, 47.2, 49.7),
                                                                                radius=9.0), coarse_precision="bf16"),
+    # every level split into band and uniform tiles, in 64 x 16 tiles where allowed
+    dict(dims=(128, 64, 48), nu=0.02, U=(1.0, 0.0, 0.0), periodic=0, body=dict(kind=1, center=(40.3, 31.6, 24.2),
+                                                                              radius=6.0),
+         env={"WL_UNIFORM_ALL": "1", "WL_TY16_MIN_CELLS": "0"}),
+    dict(dims=(96, 64, 40), nu=0.02, U=(1.0, 0.2, 0.0), periodic=4, body=None,
+         env={"WL_UNIFORM_ALL": "1", "WL_TY16_MIN_CELLS": "0"}),
 ]
 
 SCRIPT = r"""
@@ -44,9 +51,14 @@ sys.path.insert(0, ROOT)
 from paper_2304_08159_gb300 import wl
 cases = json.loads(sys.argv[1])
 out = []
+import os
 for c in cases:
     kw = {k: c[k] for k in ("exit_bc", "coarse_precision") if k in c}
+    for k, v in c.get("env", {}).items():
+        os.environ[k] = v
     sim = wl.Sim(c["dims"], c["nu"], c["U"], body=c["body"], periodic=c["periodic"], **kw)
+    for k in c.get("env", {}):
+        del os.environ[k]
     if c.get("ic"):
         sim.set_ic(c["ic"], 1.0)
     sim.step(3)
